@@ -1,0 +1,474 @@
+"""Pins of the FP64 oracle against facts the paper and mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: exact monomial
+integrals, closed-form areas and moments of discs, caps and regular polygons,
+an independent polygon-intersection algorithm, the closed-form matrix of a ball
+that covers the whole mesh, and the L2 errors printed in the paper's Table 1.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2005_10775_gb300 import inputs as I
+
+pytestmark = pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")
+
+DEGREE = {"gauss3": 2, "gauss4": 3, "paper7": 3, "dunavant7": 5, "dunavant16": 8}
+NPTS = {"gauss3": 3, "gauss4": 4, "paper7": 7, "dunavant7": 7, "dunavant16": 16}
+
+
+def _monomial_exact(i, j):
+    # integral of x^i y^j over the reference triangle (0,0),(1,0),(0,1)
+    return math.factorial(i) * math.factorial(j) / math.factorial(i + j + 2)
+
+
+@pytest.mark.parametrize("name", list(DEGREE))
+def test_rule_exactness_and_degree(name):
+    R = O.rule_table(name)
+    assert R.shape[0] == NPTS[name]
+    assert abs(R[:, 3].sum() - 1.0) < 1e-15
+    assert np.all(R[:, :3] >= -1e-15) and np.allclose(R[:, :3].sum(axis=1), 1.0, atol=1e-15)
+    x, y, w = R[:, 1], R[:, 2], R[:, 3] * 0.5
+    d = DEGREE[name]
+    for i in range(d + 1):
+        for j in range(d + 1 - i):
+            assert abs(np.sum(w * x ** i * y ** j) - _monomial_exact(i, j)) < 1e-15, (i, j)
+    # the rule is not exact one degree higher (pins the stated degree)
+    worst = max(abs(np.sum(w * x ** i * y ** (d + 1 - i)) - _monomial_exact(i, d + 1 - i))
+                for i in range(d + 2))
+    assert worst > 1e-8
+
+
+def test_paper7_weights():
+    # Sec. 6.3: centroid 27/60, vertices 3/60, mid-sides 8/60 (relative to the area)
+    R = O.rule_table("paper7")
+    for l0, l1, l2, w in R:
+        lam = sorted([l0, l1, l2])
+        if np.allclose(lam, [1 / 3] * 3):
+            assert w == pytest.approx(27 / 60, abs=1e-16)
+        elif np.allclose(lam, [0, 0, 1]):
+            assert w == pytest.approx(3 / 60, abs=1e-16)
+        else:
+            assert np.allclose(lam, [0, 0.5, 0.5]) and w == pytest.approx(8 / 60, abs=1e-16)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7])
+def test_gauss_legendre(n):
+    x, w = O.gauss_legendre(n)
+    for k in range(2 * n):
+        assert abs(np.sum(w * x ** k) - 1.0 / (k + 1)) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# single-region geometry
+# --------------------------------------------------------------------------
+
+def _area(P):
+    x, y = P[:, 0], P[:, 1]
+    return 0.5 * (np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1)))
+
+
+QUARTER = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+
+
+def test_nocaps_exactcaps_quarter_disc():
+    # x at the right-angle vertex, delta = 0.5: the region is a quarter disc
+    kind, P, caps = O.region(QUARTER, (0.0, 0.0), dict(delta=0.5, ball="nocaps"))
+    assert kind == O.KIND_PARTIAL
+    np.testing.assert_array_equal(P, [[0, 0], [0.5, 0], [0, 0.5]])
+    kind, P, caps = O.region(QUARTER, (0.0, 0.0), dict(delta=0.5, ball="exactcaps"))
+    assert caps.shape == (1, 3)
+    # Eq. (areacap) with chord c = 0.5 sqrt(2): theta = pi/4
+    assert caps[0, 2] == pytest.approx(0.25 * (math.pi / 4 - 0.5), rel=1e-14)
+    assert _area(P) + caps[0, 2] == pytest.approx(math.pi * 0.25 / 4, rel=1e-14)
+    # cap centroid by direct integration of the circular segment beyond x + y = 0.5
+    from scipy.integrate import dblquad
+    r2 = 0.25
+    area, _ = dblquad(lambda y, x: 1.0, 0, 0.5, lambda x: 0.5 - x, lambda x: math.sqrt(r2 - x * x))
+    mx, _ = dblquad(lambda y, x: x, 0, 0.5, lambda x: 0.5 - x, lambda x: math.sqrt(r2 - x * x))
+    assert caps[0, 2] == pytest.approx(area, rel=1e-9)
+    assert caps[0, 0] == pytest.approx(mx / area, rel=1e-9)
+    assert caps[0, 1] == pytest.approx(mx / area, rel=1e-9)
+
+
+def test_approxcaps_quarter_disc():
+    for m in (2, 4, 8):
+        kind, P, caps = O.region(QUARTER, (0.0, 0.0), dict(delta=0.5, ball="approxcaps", cap_m=m))
+        assert P.shape[0] == 3 + (m - 1)
+        th = math.pi / 4
+        omitted = m * 0.5 * 0.25 * (2 * th / m - math.sin(2 * th / m))   # Sec. 4.2.2 with m sub-arcs
+        assert _area(P) == pytest.approx(math.pi * 0.25 / 4 - omitted, rel=1e-14)
+        # every inserted point lies on the circle
+        r = np.hypot(P[3:, 0], P[3:, 1]) if m > 1 else np.array([])
+        assert np.all(np.abs(r - 0.5) < 1e-15)
+
+
+def test_printed_cap_weight_is_half_the_area():
+    kw = dict(delta=0.5, ball="exactcaps")
+    _, _, c1 = O.region(QUARTER, (0.0, 0.0), kw)
+    _, _, c2 = O.region(QUARTER, (0.0, 0.0), dict(kw, cap_printed=1))
+    assert c2[0, 2] == pytest.approx(c1[0, 2] / 2, rel=1e-15)
+
+
+def test_tangent_edge_gives_zero_cap():
+    # edge y = 0 from (-1, 0) to (1, 0), ball centre (0, -0.5), radius 0.5: tangent at (0, 0)
+    T = np.array([[-1.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    kind, P, caps = O.region(T, (0.0, -0.5), dict(delta=0.5, ball="exactcaps"))
+    assert np.all(np.isfinite(caps))
+    assert np.all(caps[:, 2] == 0.0)
+
+
+def test_one_edge_cut_twice():
+    # Sec. 7.1 task 4, Fig. 11c: no vertex inside, one edge crossed twice
+    T = np.array([[-1.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    x = (0.0, -0.3)
+    k0, P0, _ = O.region(T, x, dict(delta=0.5, ball="nocaps"))
+    k1, P1, _ = O.region(T, x, dict(delta=0.5, ball="approxcaps", cap_m=2))
+    k2, P2, c2 = O.region(T, x, dict(delta=0.5, ball="exactcaps"))
+    assert k0 == O.KIND_NONE
+    assert k1 == O.KIND_PARTIAL and P1.shape[0] == 3
+    assert k2 == O.KIND_PARTIAL and P2.shape[0] == 0 and c2.shape[0] == 1
+    # the cap is the segment of the disc above y = 0: half-angle acos(0.3/0.5)
+    th = math.acos(0.6)
+    assert c2[0, 2] == pytest.approx(0.25 * (th - math.sin(th) * math.cos(th)), rel=1e-13)
+
+
+def test_barycenter_closed_ball():
+    # Eq. (baryball) uses <= delta: a barycentre exactly on the sphere is kept
+    T = np.array([[0.0, 0.0], [3.0, 0.0], [0.0, 3.0]])   # barycentre (1, 1)
+    assert O.region(T, (1.0, 0.0), dict(delta=1.0, ball="barycenter"))[0] == O.KIND_WHOLE
+    assert O.region(T, (1.0, -1e-12), dict(delta=1.0, ball="barycenter"))[0] == O.KIND_NONE
+
+
+def _convex_intersection_area(A, B):
+    """Area of two convex ccw polygons' intersection by vertex enumeration
+    (independent of Sutherland-Hodgman): vertices of each inside the other plus
+    all edge-edge crossings, ordered by angle about their mean."""
+    def inside(p, P):
+        n = len(P)
+        for i in range(n):
+            a, b = P[i], P[(i + 1) % n]
+            if (b[0] - a[0]) * (p[1] - a[1]) - (b[1] - a[1]) * (p[0] - a[0]) < -1e-14:
+                return False
+        return True
+    pts = [p for p in A if inside(p, B)] + [p for p in B if inside(p, A)]
+    for i in range(len(A)):
+        p, r = A[i], A[(i + 1) % len(A)] - A[i]
+        for j in range(len(B)):
+            q, s = B[j], B[(j + 1) % len(B)] - B[j]
+            den = r[0] * s[1] - r[1] * s[0]
+            if abs(den) < 1e-300:
+                continue
+            t = ((q[0] - p[0]) * s[1] - (q[1] - p[1]) * s[0]) / den
+            u = ((q[0] - p[0]) * r[1] - (q[1] - p[1]) * r[0]) / den
+            if -1e-14 <= t <= 1 + 1e-14 and -1e-14 <= u <= 1 + 1e-14:
+                pts.append(p + t * r)
+    if len(pts) < 3:
+        return 0.0
+    pts = np.array(pts)
+    c = pts.mean(axis=0)
+    order = np.argsort(np.arctan2(pts[:, 1] - c[1], pts[:, 0] - c[0]))
+    return _area(pts[order])
+
+
+def test_ngon_clip_matches_independent_intersection():
+    rng = np.random.default_rng(7)
+    N, delta = 32, 1.0
+    off = I.ngon_offsets(N, delta)
+    for _ in range(300):
+        x = rng.uniform(-0.2, 0.2, 2)
+        c = rng.uniform(-1.2, 1.2, 2)
+        T = c + rng.uniform(-0.4, 0.4, (3, 2))
+        if _area(T) < 0:
+            T = T[::-1]
+        if abs(_area(T)) < 1e-3:
+            continue
+        kind, P, _ = O.region(T, x, dict(delta=delta, ball="ngon", ngon_off=off))
+        ref = _convex_intersection_area(T, x + off)
+        got = _area(P) if kind else 0.0
+        assert got == pytest.approx(ref, abs=1e-12)
+        if kind:
+            assert _area(P) >= 0  # counter-clockwise
+
+
+def _local_mesh(n=10, hh=0.05, jitter=0.2, seed=3):
+    # mesh centred on the origin so the outer point can be x = (0, 0)
+    m = I.split_square_mesh(-n * hh / 2, n * hh / 2, n, jitter=jitter, seed=seed, omega=(-9, 9))
+    return m
+
+
+def _moments(m, x, cfg):
+    """Sum over all T_b of the inner sums with psi = 1: area, first and second moments about x."""
+    area = 0.0
+    first = np.zeros(2)
+    second = np.zeros((2, 2))
+    for t in m.tri:
+        V = np.stack([m.vx[t], m.vy[t]], axis=1)
+        s0, s1, S2, _ = O.inner(V, x, cfg)
+        area += s0
+        first += s1 @ (V - x)
+        second += (V - x).T @ S2 @ (V - x)
+    return area, first, second
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.2])
+def test_ngon_area_and_moments(jitter):
+    N, delta = 32, 0.2
+    m = _local_mesh(jitter=jitter)
+    cfg = dict(delta=delta, ball="ngon", ngon_off=I.ngon_offsets(N, delta), inner="dunavant7")
+    for x in [(0.0, 0.0), (0.013, -0.021)]:
+        area, first, second = _moments(m, np.array(x), cfg)
+        s = math.sin(2 * math.pi / N)
+        assert area == pytest.approx(0.5 * N * delta ** 2 * s, rel=1e-13)
+        assert np.abs(first).max() < 1e-16
+        J = N * delta ** 4 / 12 * s * (2 + math.cos(2 * math.pi / N))   # polar moment
+        np.testing.assert_allclose(second, 0.5 * J * np.eye(2), rtol=0, atol=1e-13 * J)
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.2])
+def test_exactcaps_and_approxcaps_area(jitter):
+    delta = 0.2
+    m = _local_mesh(jitter=jitter)
+    x = np.array([0.004, 0.011])
+    tot_exact = tot_nocaps = 0.0
+    tot_approx = {2: 0.0, 4: 0.0}
+    expect_approx = {2: math.pi * delta ** 2, 4: math.pi * delta ** 2}
+    for t in m.tri:
+        V = np.stack([m.vx[t], m.vy[t]], axis=1)
+        k, P, caps = O.region(V, x, dict(delta=delta, ball="exactcaps"))
+        if k:
+            tot_exact += (_area(P) if len(P) else 0.0) + caps[:, 2].sum()
+            for cap_area in caps[:, 2]:
+                # invert Eq. (areacap) for the half-angle, then the omitted area of m sub-arcs
+                th = _theta_from_cap(cap_area, delta)
+                for mm in expect_approx:
+                    expect_approx[mm] -= mm * 0.5 * delta ** 2 * (2 * th / mm - math.sin(2 * th / mm))
+        k, P, _ = O.region(V, x, dict(delta=delta, ball="nocaps"))
+        if k:
+            tot_nocaps += _area(P)
+        for mm in tot_approx:
+            k, P, _ = O.region(V, x, dict(delta=delta, ball="approxcaps", cap_m=mm))
+            if k:
+                tot_approx[mm] += _area(P)
+    assert tot_exact == pytest.approx(math.pi * delta ** 2, rel=1e-13)
+    assert tot_nocaps < math.pi * delta ** 2
+    for mm in tot_approx:
+        assert tot_approx[mm] == pytest.approx(expect_approx[mm], rel=1e-12)
+    # Sec. 4.2.2: one triangle per cap cuts the omitted area about four-fold
+    r = (math.pi * delta ** 2 - tot_nocaps) / (math.pi * delta ** 2 - tot_approx[2])
+    assert 3.9 < r < 4.1
+
+
+def _theta_from_cap(a, delta):
+    lo, hi = 0.0, math.pi / 2
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if 0.5 * delta ** 2 * (2 * mid - math.sin(2 * mid)) < a:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_support_nesting():
+    # Sec. 6.2: S^bary, S^nocaps in S^approxcaps in S^exactcaps = S^overlap; the inscribed N-gon too
+    rng = np.random.default_rng(11)
+    delta = 0.3
+    off = I.ngon_offsets(16, delta)
+    nest = ["nocaps", "approxcaps", "exactcaps", "overlap"]
+    for _ in range(3000):
+        x = np.zeros(2)
+        c = rng.uniform(-0.45, 0.45, 2)
+        T = c + rng.uniform(-0.1, 0.1, (3, 2))
+        if _area(T) < 0:
+            T = T[::-1]
+        got = {b: O.region(T, x, dict(delta=delta, ball=b))[0] != 0 for b in nest + ["barycenter"]}
+        got["ngon"] = O.region(T, x, dict(delta=delta, ball="ngon", ngon_off=off))[0] != 0
+        for a, b in zip(nest, nest[1:]):
+            assert (not got[a]) or got[b], (a, b, T)
+        assert (not got["barycenter"]) or got["overlap"]
+        assert (not got["ngon"]) or got["overlap"]
+
+
+@pytest.mark.parametrize("rule", ["gauss3", "dunavant7", "dunavant16"])
+def test_constant_kernel_whole_triangle_moments(rule):
+    # whole T_b, constant psi: the inner sums are exact moments of P1 basis functions
+    T = np.array([[0.1, 0.2], [0.17, 0.21], [0.12, 0.26]])
+    c = 3.7
+    s0, s1, S2, nqp = O.inner(T, (0.13, 0.22), dict(delta=1.0, ball="barycenter", inner=rule, kernel_c=c))
+    A = _area(T)
+    assert nqp == NPTS[rule]
+    assert s0 == pytest.approx(c * A, rel=1e-14)
+    np.testing.assert_allclose(s1, c * A / 3, rtol=1e-14)
+    np.testing.assert_allclose(S2, c * A * (np.ones((3, 3)) + np.eye(3)) / 12, rtol=1e-13)
+
+
+def test_singular_kernel_ngon_closed_forms():
+    # psi = 1/|x-y| over the regular N-gon: int 1/|z| = 2 N a ln(sec(pi/N) + tan(pi/N)),
+    # int |z| = (N a^3 / 3) (sec tan + ln(sec + tan)) at pi/N, a = apothem
+    N, delta = 32, 0.2
+    m = _local_mesh(jitter=0.2)
+    cfg = dict(delta=delta, ball="ngon", ngon_off=I.ngon_offsets(N, delta), inner="dunavant7",
+               kernel="inv_dist", kernel_c=1.0, duffy_n=4)
+    a = delta * math.cos(math.pi / N)
+    phi = math.pi / N
+    sec, tan = 1 / math.cos(phi), math.tan(phi)
+    # x inside a triangle, and x on a mesh vertex (shared by six triangles)
+    for x in [np.array([0.007, -0.004]), np.array([m.vx[60], m.vy[60]])]:
+        s0_tot = 0.0
+        m1 = np.zeros(2)
+        m2 = 0.0
+        for t in m.tri:
+            V = np.stack([m.vx[t], m.vy[t]], axis=1)
+            s0, s1, S2, _ = O.inner(V, x, cfg)
+            s0_tot += s0
+            m1 += s1 @ (V - x)
+            m2 += np.trace((V - x).T @ S2 @ (V - x))
+        assert s0_tot == pytest.approx(2 * N * a * math.log(sec + tan), rel=1e-6)
+        assert np.abs(m1).max() < 1e-7
+        assert m2 == pytest.approx(N * a ** 3 / 3 * (sec * tan + math.log(sec + tan)), rel=1e-7)
+
+
+# --------------------------------------------------------------------------
+# assembled matrix
+# --------------------------------------------------------------------------
+
+def _small(ball, kernel="const", jitter=0.2, **kw):
+    m = I.split_square_mesh(-0.3, 1.3, 8, jitter=jitter, seed=5)
+    delta = 0.45
+    cfg = dict(delta=delta, ball=ball, outer="dunavant7", inner="dunavant7", kernel=kernel,
+               kernel_c=I.const_kernel_c(delta) if kernel == "const" else I.inv_dist_kernel_c(delta))
+    if ball == "ngon":
+        cfg["ngon_off"] = I.ngon_offsets(32, delta)
+    cfg.update(kw)
+    return m, cfg
+
+
+BALLS = ["barycenter", "nocaps", "approxcaps", "exactcaps", "ngon", "overlap"]
+
+
+@pytest.mark.parametrize("ball", BALLS)
+@pytest.mark.parametrize("kernel", ["const", "inv_dist"])
+def test_matrix_symmetric_zero_row_sums_psd(ball, kernel):
+    m, cfg = _small(ball, kernel)
+    out = O.assemble(m, cfg)
+    D = O.to_csr(out).toarray()
+    scale = np.abs(D).sum(axis=1)
+    assert np.all(np.abs(D - D.T) <= 1e-14 * scale[:, None])
+    assert np.all(np.abs(D.sum(axis=1)) <= 1e-14 * scale)
+    ev = np.linalg.eigvalsh(D)
+    assert ev.min() > -1e-12 * ev.max()
+
+
+@pytest.mark.parametrize("ball", ["barycenter", "nocaps", "approxcaps", "exactcaps", "ngon", "overlap"])
+@pytest.mark.parametrize("outer,inner", [("dunavant7", "dunavant7"), ("gauss3", "gauss3"),
+                                         ("dunavant16", "gauss4"), ("paper7", "dunavant16")])
+def test_ball_covering_mesh_closed_form(ball, outer, inner):
+    # delta larger than the mesh: every region is a whole triangle and
+    # D = c (2 |Omega| M - 2 m m^T) with M the P1 mass matrix and m_j = int phi_j
+    m = I.split_square_mesh(0.0, 1.0, 3, jitter=0.2, seed=9, omega=(-1, 2))
+    delta, c = 20.0, 0.37
+    cfg = dict(delta=delta, ball=ball, outer=outer, inner=inner, kernel_c=c)
+    if ball == "ngon":
+        cfg["ngon_off"] = I.ngon_offsets(8, delta)
+    D = O.to_csr(O.assemble(m, cfg)).toarray()
+    J = m.vx.shape[0]
+    M = np.zeros((J, J))
+    mm = np.zeros(J)
+    tot = 0.0
+    for t in m.tri:
+        V = np.stack([m.vx[t], m.vy[t]], axis=1)
+        A = abs(_area(V))
+        tot += A
+        M[np.ix_(t, t)] += A * (np.ones((3, 3)) + np.eye(3)) / 12
+        mm[t] += A / 3
+    ref = c * (2 * tot * M - 2 * np.outer(mm, mm))
+    np.testing.assert_allclose(D, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_row_mask_matches_full_rows():
+    m, cfg = _small("ngon")
+    full = O.to_csr(O.assemble(m, cfg))
+    rows = np.array([3, 40, 57])
+    mask = np.zeros(m.vx.shape[0], np.uint8)
+    mask[rows] = 1
+    part = O.to_csr(O.assemble(m, cfg, row_mask=mask))
+    for r in rows:
+        np.testing.assert_allclose(part[r].toarray(), full[r].toarray(), rtol=0,
+                                   atol=1e-15 * abs(full[r]).max())
+
+
+def test_per_outer_hash_and_records():
+    m, cfg = _small("approxcaps")
+    full = O.assemble(m, cfg, want_rec=True, want_hash=True)
+    rec = full["rec"]
+    assert len(rec) == full["n_inter"]
+    # hash per outer triangle = sum of record hashes; splitmix64 written out independently
+    def mix(z):
+        z = (z + 0x9E3779B97F4A7C15) & (2 ** 64 - 1)
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & (2 ** 64 - 1)
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & (2 ** 64 - 1)
+        return z ^ (z >> 31)
+    h = np.zeros(m.tri.shape[0], dtype=object)
+    for r in rec[:2000]:
+        v = mix(mix((int(r["a"]) << 32) | int(r["b"])) ^ ((int(r["q"]) << 24) | (int(r["kind"]) << 16)
+                                                            | (int(r["nverts"]) << 8) | int(r["ncaps"])))
+        assert v == O.record_hash(r["a"], r["b"], r["q"], r["kind"], r["nverts"], r["ncaps"])
+    a_sub = np.array([0, 5, 77])
+    sub = O.assemble(m, cfg, a_list=a_sub, want_hash=True)
+    np.testing.assert_array_equal(sub["hash_a"][a_sub], full["hash_a"][a_sub])
+    np.testing.assert_array_equal(sub["count_a"][a_sub], full["count_a"][a_sub])
+
+
+# --------------------------------------------------------------------------
+# the paper's own numbers: Table 1 (Sec. 8.1)
+# --------------------------------------------------------------------------
+
+def _table1():
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_table1.txt")
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            b, h, e = line.split()
+            rows[(b, float(h))] = float(e)
+    return rows
+
+
+def _paper_l2(ball, h, **kw):
+    d = 0.1
+    m = I.paper_grid(h)
+    u = I.manufactured_u(m.vx, m.vy)
+    f = I.manufactured_f(m.vx, m.vy)
+    cfg = dict(delta=d, ball=ball, outer="switch47", inner="gauss3", kernel_c=I.const_kernel_c(d))
+    cfg.update(kw)
+    D = O.to_csr(O.assemble(m, cfg))
+    U = O.solve(D, m, f, u)
+    return O.l2_error_omega(m, U, I.manufactured_u)
+
+
+# approxcaps, nocaps (h <= delta/2), overlap and exactcaps with the cap weight as printed in
+# Sec. 5.2 reproduce Table 1 within 15 %; grid details the paper omits (diagonal direction)
+# explain the rest.  The barycenter column is not reproduced (documented reading).
+TABLE1_CASES = [("approxcaps", 0.1, {}), ("approxcaps", 0.05, {}), ("approxcaps", 0.025, {}),
+                ("nocaps", 0.05, {}), ("nocaps", 0.025, {}),
+                ("overlap", 0.1, {}), ("overlap", 0.05, {}), ("overlap", 0.025, {}),
+                ("exactcaps", 0.1, {"cap_printed": 1}), ("exactcaps", 0.05, {"cap_printed": 1}),
+                ("exactcaps", 0.025, {"cap_printed": 1})]
+
+
+@pytest.mark.parametrize("ball,h,kw", TABLE1_CASES)
+def test_paper_table1_l2_error(ball, h, kw):
+    ref = _table1()[(ball, h)]
+    got = _paper_l2(ball, h, **kw)
+    assert got == pytest.approx(ref, rel=0.15)
+
+
+def test_paper_table1_rates():
+    # second-order convergence for the O(h^2) balls (Table 1 rates ~2 at h = 0.05 -> 0.025)
+    for ball, kw in [("approxcaps", {}), ("nocaps", {}), ("exactcaps", {})]:
+        e1 = _paper_l2(ball, 0.05, **kw)
+        e2 = _paper_l2(ball, 0.025, **kw)
+        assert 1.6 < math.log2(e1 / e2) < 2.4, ball
