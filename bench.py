@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark: nonlocal P1 stiffness assembly on GB300 (one JSON line on rank 0).
+
+Workload (default): regular 32-gon ball, delta = 0.1, (-0.1, 1.1)^2 split into
+96 x 96 squares (18432 triangles) with vertices jittered by U[-0.2h, 0.2h]
+(seed 1077502), psi = 4/(pi delta^4), 16-point outer and 7-point inner rules,
+FP64 geometry with FP32-compensated quadrature.  One step = one full assembly
+(cell list, pair geometry + quadrature, symbolic CSR pattern, numeric scatter)
+from a mesh already in HBM to the finished CSR.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 runs under torchrun: every rank assembles its own copy of the workload
+(independent problems, no data-path collective: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "assembly qp-pairs/s & ms/matrix, FP32-comp vs FP64 GPU at rel err <=1e-6"
+UNIT = "qp-pairs/s"
+# algorithmic work per unit (derivation in the design doc): the inner-point evaluation
+# (map, phi_b, omega, s0, s1, S2) and the per-(T_a, q, T_b) outer combination
+FLOP_PER_QP = 37.0
+FLOP_PER_INTER = 48.0
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ngon32_96")
+    ap.add_argument("--prec", default="fp32c", choices=["fp32c", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(problem, seconds, steps=1):
+    """The FP64 oracle as it stands, on a bounded sample of outer triangles of the same
+    workload (evenly spaced, each against every triangle), timed on the host cores."""
+    import numpy as np
+
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    K = problem.mesh.nt
+    cfg = dict(delta=problem.delta, ball=problem.ball, outer=problem.outer, inner=problem.inner,
+               kernel=problem.kernel, kernel_c=problem.kernel_c, ngon_off=problem.ngon_off, cap_m=problem.cap_m)
+    # calibrate on a small sample, then size the sample to about `seconds`
+    probe = np.linspace(0, K - 1, num=max(cores, 4)).astype(np.int32)
+    t0 = time.perf_counter()
+    O.assemble(problem.mesh, cfg, a_list=probe, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    m = int(min(K, max(cores, len(probe) * seconds / dt)))
+    res = []
+    for s in range(steps):
+        a_list = ((np.arange(m) * (K / m) + s * 0.37 * K / m) % K).astype(np.int32)
+        t0 = time.perf_counter()
+        out = O.assemble(problem.mesh, cfg, a_list=a_list, nthreads=cores)
+        res.append((out["n_qp_pairs"], time.perf_counter() - t0, m))
+    qp = sum(r[0] for r in res)
+    tt = sum(r[1] for r in res)
+    return {"value": qp / tt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{m} of {K} outer triangles (evenly spaced) x all {K} inner triangles, "
+                      f"{qp // max(steps, 1)} qp-pairs per step, FP64"}, tt / steps
+
+
+def reference_arm(args, rank, world):
+    from paper_2005_10775_gb300 import inputs as I
+    if rank != 0:
+        return
+    p = I.problem(args.workload)
+    per_step = max(2.0, min(20.0, 60.0 / max(args.steps, 1)))
+    cpu_baseline(p, per_step / 4, steps=1) if args.warmup else None
+    base, ms = cpu_baseline(p, per_step, steps=args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "K": p.mesh.nt, "ball": p.ball, "outer": p.outer,
+                       "inner": p.inner, "delta": p.delta},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, local, world = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_2005_10775_gb300 import inputs as I
+    from paper_2005_10775_gb300 import nlfem as nl
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    p = I.problem(args.workload)
+    m = p.mesh
+    # a dedicated stream shared by the library and the timing events (the legacy default
+    # stream has handle 0, which the C ABI reads as "create a private stream")
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = nl.nl_create(local, stream.cuda_stream)
+    keep = nl._Keep()
+    dmesh = type("DevMesh", (), dict(vx=torch.tensor(m.vx, device=dev), vy=torch.tensor(m.vy, device=dev),
+                                     tri=torch.tensor(m.tri, device=dev)))
+    mesh = nl.make_mesh(dmesh, keep)
+    off = None if p.ngon_off is None else torch.tensor(p.ngon_off, device=dev)
+
+    def cfg_for(prec):
+        return nl.make_config(keep, p.delta, p.ball, p.outer, p.inner, p.kernel, p.kernel_c, off, p.cap_m, prec)
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def run(prec, steps, warmup):
+        cfg = cfg_for(prec)
+        for _ in range(warmup):
+            out = nl.nl_assemble(ctx, mesh, cfg)
+            nl.nl_csr_free(ctx, out)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        tot = 0.0
+        phase = np.zeros(4)
+        stats = None
+        l0 = nl.nl_launch_count(ctx)
+        wall0 = time.perf_counter()
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = nl.nl_assemble(ctx, mesh, cfg)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+            phase += nl.nl_last_timings(ctx)
+            stats = (out.n_pairs, out.n_qp_pairs, out.n_inter, out.nnz)
+            nl.nl_csr_free(ctx, out)
+        launches = nl.nl_launch_count(ctx) - l0 - 0
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t = torch.tensor([tot], device=dev, dtype=torch.float64)
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), phase / steps, stats, launches, wall
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    tot_ms, phase, stats, launches, wall = run(args.prec, args.steps, args.warmup)
+    ck = clocks.stop()
+    n_pairs, n_qp, n_inter, nnz = stats
+    ms_step = tot_ms / args.steps
+    value = n_qp * world * args.steps / (tot_ms / 1e3)
+
+    # FP64 path for the FP32-comp vs FP64 comparison
+    fp64 = None
+    if args.fp64_steps > 0 and args.prec != "fp64":
+        t64, ph64, _, _, _ = run("fp64", args.fp64_steps, 1)
+        fp64 = {"ms_per_step": t64 / args.fp64_steps, "value": n_qp * world * args.fp64_steps / (t64 / 1e3),
+                "numeric_ms": ph64[1]}
+
+    # end to end through the C ABI with host buffers: H2D of the mesh inside, D2H of the CSR
+    e2e = None
+    if not args.no_e2e:
+        hmesh = nl.make_mesh(m, keep)
+        hoff = p.ngon_off
+        hcfg = nl.make_config(keep, p.delta, p.ball, p.outer, p.inner, p.kernel, p.kernel_c, hoff, p.cap_m,
+                              args.prec)
+        rp = torch.empty(m.nv + 1, dtype=torch.int64).pin_memory()
+        ci = torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory()
+        va = torch.empty(max(nnz, 1), dtype=torch.float64).pin_memory()
+        out = nl.nl_assemble(ctx, hmesh, hcfg)
+        nl.nl_csr_free(ctx, out)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            out = nl.nl_assemble(ctx, hmesh, hcfg)
+            nl._check(ctx, nl.LIB.nl_csr_download(ctx, nl.ctypes.byref(out), rp.data_ptr(), ci.data_ptr(),
+                                                  va.data_ptr()))
+            nl.nl_csr_free(ctx, out)
+        torch.cuda.synchronize()
+        te = torch.tensor([time.perf_counter() - t0], device=dev, dtype=torch.float64)
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        h2d = m.vx.nbytes + m.vy.nbytes + m.tri.nbytes + (0 if hoff is None else hoff.nbytes)
+        d2h = 8 * (m.nv + 1) + 12 * nnz
+        e2e = {"value": n_qp * world * args.steps / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    peaks, src = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    numeric_ms = phase[1]
+    achieved = (FLOP_PER_QP * n_qp + FLOP_PER_INTER * n_inter) / (numeric_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32c" if args.prec == "fp32c" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "K": m.nt, "J": m.nv, "ball": f"{p.ball}{p.ngon_n or ''}",
+                   "delta": p.delta, "outer": p.outer, "inner": p.inner, "kernel": p.kernel,
+                   "parallelism": f"replica x{world}", "l2": "flushed (512 MB write) before every step",
+                   "n_pairs": n_pairs, "n_qp_pairs": n_qp, "n_inter": n_inter, "nnz": nnz,
+                   "phase_ms": {"prepare": phase[0], "numeric": phase[1], "symbolic": phase[2],
+                                "scatter": phase[3]},
+                   "wall_s_timed": wall},
+        "fp64": fp64,
+        "speedup_fp32c_vs_fp64": (fp64["ms_per_step"] / ms_step) if fp64 else None,
+        "roofline": {"bound": "alu", "kernel": "k_numeric (pair geometry + quadrature)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_mhz:.0f} MHz "
+                                    f"(clock from MEASURED_PEAKS.json, {src})",
+                     "traffic": None},
+        "clocks": ck,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"], _ = cpu_baseline(p, args.cpu_seconds)
+    nl.nl_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

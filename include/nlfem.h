@@ -1,0 +1,190 @@
+/*
+ * nlfem.h -- C ABI of libnlfem: GB300 (sm_103a) assembly of the P1 stiffness
+ * matrix of the nonlocal diffusion operator with ball-supported kernels, after
+ * D'Elia, Gunzburger, Vollmann, "A cookbook for finite element methods for
+ * nonlocal problems, including quadrature rules and approximate Euclidean balls".
+ *
+ * Problem (Sec. 1.1, Eq. (prob), (oper), (inter)):
+ *     -L u = f on Omega,  u = g on Omega_I,
+ *     L u(x) = 2 int (u(y) - u(x)) gamma(x, y) dy,  gamma = psi(x, y) 1_{B_delta(x)}(y).
+ * The library assembles the full (Omega u Omega_I)^2 matrix D of the bilinear form
+ * Eq. (bform0) discretised as Eq. (bformhj) with the quadrature of Eq. (bformjqqh);
+ * A = D[Omega, Omega] and F = G - D[Omega, Omega_I] g follow from the A-B-C
+ * assignment table of Sec. 7.2.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns nl_status; nothing aborts, traps or exits.  On failure
+ *     nl_last_error(ctx) returns a one-line description (valid until the next call).
+ *   - Input pointers may be host or device memory (detected per pointer); the
+ *     caller keeps ownership and may free them when the call returns.
+ *   - Outputs in nl_csr are device buffers owned by the library, released with
+ *     nl_csr_free.  Work is ordered on the context's CUDA stream.
+ *   - Indices are 0-based; triangles are counter-clockwise.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef NLFEM_H
+#define NLFEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NL_OK = 0,
+    NL_EINVAL = 1,        /* bad argument (null pointer, size, enum value) */
+    NL_ENOMEM = 2,        /* device allocation failed */
+    NL_ECUDA = 3,         /* a CUDA runtime call failed */
+    NL_EGEOM = 4,         /* degenerate / clockwise triangle, or delta <= largest triangle diameter */
+    NL_ETIMEOUT = 5,      /* a bounded device-side wait expired */
+    NL_ENOCONV = 6,       /* the iterative solver did not reach the tolerance */
+    NL_EUNSUPPORTED = 7   /* valid but not implemented combination / size limit exceeded */
+} nl_status;
+
+/* Interaction region R(x, T_b) kept by the (approximate) ball centred at the outer point x. */
+typedef enum {
+    NL_BALL_BARYCENTER = 0,   /* whole T_b iff |x - bary(T_b)| <= delta           (Sec. 4.2.3, Eq. (baryball)) */
+    NL_BALL_NOCAPS = 1,       /* chord polygon of T_b n B_delta(x), fanned         (Sec. 4.2.1, Sec. 7.1 tasks 3-6) */
+    NL_BALL_APPROXCAPS = 2,   /* nocaps plus cap_m - 1 arc points per cap         (Sec. 4.2.2) */
+    NL_BALL_EXACTCAPS = 3,    /* nocaps plus a one-point centroid rule per cap    (Sec. 5.2, Eq. (areacap)) */
+    NL_BALL_NGON = 4,         /* T_b clipped by the regular inscribed ngon_n-gon  (Sec. 9, regular polygon) */
+    NL_BALL_OVERLAP = 5       /* whole T_b iff T_b n B_delta(x) is non-empty      (Sec. 4.2.4, Eq. (overlap)) */
+} nl_ball;
+
+/* Quadrature rules on triangles (weights relative to the area). */
+typedef enum {
+    NL_RULE_GAUSS3 = 0,       /* 3-point symmetric Gaussian, degree 2 (Sec. 5.3.1) */
+    NL_RULE_GAUSS4 = 1,       /* 4-point symmetric Gaussian, degree 3 (Sec. 6.1) */
+    NL_RULE_PAPER7 = 2,       /* centroid/vertices/mid-sides 27/60, 3/60, 8/60, degree 3 (Sec. 6.3) */
+    NL_RULE_DUNAVANT7 = 3,    /* 7-point degree-5 rule (Radon) */
+    NL_RULE_DUNAVANT16 = 4,   /* 16-point degree-8 rule (Dunavant) */
+    NL_RULE_SWITCH47 = 5      /* outer only: GAUSS4 if |bary_a - bary_b| < delta - h_max else PAPER7 (Sec. 8) */
+} nl_rule;
+
+typedef enum {
+    NL_KERNEL_CONST = 0,      /* psi = kernel_c                                   (Sec. 8) */
+    NL_KERNEL_INV_DIST = 1    /* psi = kernel_c / |x - y| (integrable singular kernel, Sec. 2 remarks) */
+} nl_kernel;
+
+typedef enum {
+    NL_PREC_FP64 = 0,         /* geometry and quadrature in FP64 */
+    NL_PREC_FP32_COMP = 1     /* geometry in FP64; quadrature in FP32 with FP64 (compensated) long sums */
+} nl_prec;
+
+typedef struct nl_ctx nl_ctx;
+
+/* Triangle mesh of Omega u Omega_I (Sec. 3.1).  node_in_omega: 1 for nodes in the open
+   Omega, 0 for nodes of Omega_I including those on the boundary of Omega (Sec. 3.1).
+   elem_in_omega: 1 for elements of the triangulation of Omega.  Both labels are only
+   read by nl_extract / nl_rhs and may be NULL for nl_assemble. */
+typedef struct {
+    int32_t nv, nt;
+    const double *vx, *vy;          /* [nv] vertex coordinates */
+    const int32_t *tri;             /* [3*nt] counter-clockwise vertex indices */
+    const uint8_t *node_in_omega;   /* [nv] or NULL */
+    const uint8_t *elem_in_omega;   /* [nt] or NULL */
+} nl_mesh;
+
+typedef struct {
+    double delta;                   /* horizon, > largest triangle diameter (Sec. 7.1 task 6 assumes it) */
+    double kernel_c;                /* kernel constant c */
+    int32_t kernel;                 /* nl_kernel */
+    int32_t ball;                   /* nl_ball */
+    int32_t ngon_n;                 /* NGON: number of polygon vertices, 3..64 */
+    int32_t cap_m;                  /* APPROXCAPS: sub-arcs per cap, power of two 1..16 */
+    const double *ngon_offsets;     /* NGON: [2*ngon_n] polygon vertices relative to x, ccw */
+    int32_t outer, inner;           /* nl_rule of the outer (T_a) and inner (subtriangle) integrals */
+    int32_t prec;                   /* nl_prec */
+    int32_t duffy_n;                /* INV_DIST: Gauss points per unit panel of the near-singular rule (1..7) */
+    int32_t cap_printed;            /* EXACTCAPS: 1 = cap weight as printed in Sec. 5.2 (half Eq. (areacap)) */
+} nl_config;
+
+/* Square CSR matrix in device memory, columns sorted in each row. */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    int64_t *row_ptr;               /* [n+1] */
+    int32_t *col_idx;               /* [nnz] */
+    double *val;                    /* [nnz] */
+    int64_t n_pairs;                /* element pairs (T_a, T_b) with a non-empty region for some outer point */
+    int64_t n_qp_pairs;             /* (outer point, inner point) evaluations performed */
+    int64_t n_inter;                /* (T_a, q, T_b) triples with a non-empty region */
+    void *priv;                     /* library state (pattern, candidate lists); do not touch */
+} nl_csr;
+
+/* Create a context on CUDA device `device`, ordering work on `cuda_stream`
+   (a cudaStream_t; NULL = a stream created and owned by the context). */
+nl_status nl_create(nl_ctx **ctx, int device, void *cuda_stream);
+void nl_destroy(nl_ctx *ctx);
+const char *nl_last_error(nl_ctx *ctx);
+
+/* Assemble D = sum over all element pairs (T_a, T_b) of Eq. (bformhj) with the outer
+   rule on T_a and the inner rule on every subtriangle of R(x_q, T_b) (Eq. (bformjqqh),
+   Sec. 7.2 first remark: whole balls, all K x K pairs).  Runs the cell-list neighbour
+   search, the pair geometry and quadrature, the symbolic CSR pattern (union over
+   pairs with a non-empty region) and the numeric scatter.  *out receives a new
+   library-owned n x n CSR (n = mesh->nv).  Synchronises the stream once (to size the
+   pattern). */
+nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_csr *out);
+
+/* Recompute the values of an nl_assemble result for the same mesh and configuration
+   on its existing pattern (pair geometry, quadrature and scatter only).  No host
+   synchronisation: can be captured in a CUDA graph. */
+nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *inout);
+
+/* Assemble n independent problems.  The numeric phases of all problems run as one
+   persistent launch over a shared work queue, captured once into a CUDA graph. */
+nl_status nl_assemble_batch(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const nl_config *cfgs,
+                            nl_csr *outs);
+
+/* Per-outer-triangle interaction statistics of the same geometry code the assembly
+   runs: count_a[a] = #(q, b) with a non-empty region, qp_a[a] = inner points used,
+   hash_a[a] = sum (mod 2^64) over those (a, q, b) of the record hash
+   splitmix64(splitmix64(a << 32 | b) ^ (q << 24 | kind << 16 | nverts << 8 | ncaps))
+   (splitmix64 of Steele, Lea and Flood), kind 1 = whole T_b, 2 = partial.  Host arrays [nt]. */
+nl_status nl_interactions(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg,
+                          uint64_t *hash_a, int64_t *count_a, int64_t *qp_a);
+
+/* Split D by the node labels: A = D[Omega, Omega] (Eq. (weakja)) and
+   B = D[Omega, Omega_I] (rule B of Sec. 7.2) with rows and columns renumbered in
+   increasing node order within each label.  B is rectangular: B->n = #Omega rows and
+   its column count is #Omega_I; both are new library-owned CSRs. */
+nl_status nl_extract(nl_ctx *ctx, const nl_csr *D, const nl_mesh *mesh, nl_csr *A, nl_csr *B);
+
+/* Right-hand side F = G - B g (Eq. (lfunc3) via rules B and C of Sec. 7.2), with the
+   load vector G_j = int_Omega f phi_j over elements labelled Omega for f given by its
+   nodal values (P1 interpolant), g the Dirichlet volume-constraint data at the nodes
+   (Eq. (appr)).  f_nodal, g_nodal: [nv]; F: [#Omega] device or host. */
+nl_status nl_rhs(nl_ctx *ctx, const nl_csr *B, const nl_mesh *mesh, const double *f_nodal,
+                 const double *g_nodal, double *F);
+
+/* y = A x with A's values in FP64 (NL_PREC_FP64) or rounded to FP32 (NL_PREC_FP32_COMP;
+   products accumulated in FP32).  x, y: [A->n] device or host. */
+nl_status nl_matvec(nl_ctx *ctx, const nl_csr *A, const double *x, double *y, int32_t prec);
+
+/* Solve A x = b (A symmetric positive definite, Sec. 2) by conjugate gradients with
+   FP32 matrix-vector products and FP64 residual refinement until ||b - A x|| <= rtol ||b||
+   (the paper names no solver, Sec. 7.2 "reduced sparsity" remark).  x holds the initial
+   guess on entry.  Returns NL_ENOCONV if max_it inner iterations do not suffice. */
+nl_status nl_cg(nl_ctx *ctx, const nl_csr *A, const double *b, double *x, double rtol, int32_t max_it,
+                int32_t *iters, double *relres);
+
+/* Copy a CSR to host arrays row_ptr[n+1], col_idx[nnz], val[nnz] (any may be NULL). */
+nl_status nl_csr_download(nl_ctx *ctx, const nl_csr *m, int64_t *row_ptr, int32_t *col_idx, double *val);
+
+/* Release the device buffers of m (safe on a zeroed nl_csr). */
+void nl_csr_free(nl_ctx *ctx, nl_csr *m);
+
+/* Device time of the phases of the last nl_assemble (ms): [0] preprocessing + cell list,
+   [1] pair geometry + quadrature, [2] symbolic pattern, [3] numeric scatter. */
+nl_status nl_last_timings(nl_ctx *ctx, double *ms4);
+
+/* Number of CUDA kernels this context has launched so far (all entry points). */
+int64_t nl_launch_count(nl_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLFEM_H */

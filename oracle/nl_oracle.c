@@ -348,6 +348,7 @@ static int clip_ngon(const pt *V, pt x, const or_cfg *cfg, pt *out)
         for (int i = 0; i < n; i++) {
             pt s = A[(i + n - 1) % n], e = A[i];
             double ds = orient(P0, P1, s), de = orient(P0, P1, e);
+            if (m + 2 > MAXV) break;   /* never reached for convex input; bounds the buffer */
             if (de >= 0.0) {
                 if (ds < 0.0) {
                     double t = ds / (ds - de);
@@ -414,7 +415,7 @@ static void make_region(const pt *V, pt x, const or_cfg *cfg, region *R)
     case OR_BALL_NOCAPS:
     case OR_BALL_APPROXCAPS:
     case OR_BALL_EXACTCAPS: {
-        pt W[8]; int tag[8], nin;
+        pt W[12]; int tag[12], nin;
         int n = ball_walk(V, x, d2, W, tag, &nin);
         if (n < 3 && !(cfg->ball != OR_BALL_NOCAPS && n == 2)) return;
         if (n < 2) return;

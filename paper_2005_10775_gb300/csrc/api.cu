@@ -1,0 +1,405 @@
+// api.cu -- C ABI entry points of libnlfem (declared in include/nlfem.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "numeric.cuh"
+
+nl_status nl_launch_numeric_f64(nl_ctx *ctx, const nlq::NumArgs &A, int ball);
+nl_status nl_launch_numeric_f32(nl_ctx *ctx, const nlq::NumArgs &A, int ball);
+
+// ---------------------------------------------------------------------------
+// errors and staging
+// ---------------------------------------------------------------------------
+nl_status nl_fail(nl_ctx *ctx, nl_status s, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+nl_status nl_cuda_fail(nl_ctx *ctx, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return nl_fail(ctx, e == cudaErrorMemoryAllocation ? NL_ENOMEM : NL_ECUDA, m);
+}
+
+bool nl_is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// device view of a host-or-device input; *owned says whether the caller must free it
+nl_status nl_stage(nl_ctx *ctx, const void *src, size_t bytes, void **dev, bool *owned)
+{
+    *owned = false;
+    if (nl_is_device_ptr(src)) {
+        *dev = const_cast<void *>(src);
+        return NL_OK;
+    }
+    NL_CK(cudaMallocAsync(dev, bytes ? bytes : 1, ctx->stream));
+    NL_CK(cudaMemcpyAsync(*dev, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *owned = true;
+    return NL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// quadrature tables (the kernel side's own construction of the published rules)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TabBuilder {
+    nlq::RuleTab *t;
+    void pt(double l0, double l1, double l2, double w)
+    {
+        t->l[t->n][0] = l0;
+        t->l[t->n][1] = l1;
+        t->l[t->n][2] = l2;
+        t->w[t->n] = w;
+        t->n++;
+    }
+    void s3(double w) { pt(1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0, w); }
+    void s21(double a, double w)
+    {
+        const double c = 1.0 - 2.0 * a;
+        pt(a, a, c, w); pt(a, c, a, w); pt(c, a, a, w);
+    }
+    void s111(double a, double b, double w)
+    {
+        const double c = 1.0 - a - b;
+        pt(a, b, c, w); pt(a, c, b, w); pt(b, a, c, w);
+        pt(b, c, a, w); pt(c, a, b, w); pt(c, b, a, w);
+    }
+};
+
+bool fill_rule(int id, nlq::RuleTab *t)
+{
+    TabBuilder B{t};
+    switch (id) {
+    case NL_RULE_GAUSS3:   // symmetric 3-point Gaussian rule, degree 2
+        B.s21(1.0 / 6.0, 1.0 / 3.0);
+        return true;
+    case NL_RULE_GAUSS4:   // symmetric 4-point Gaussian rule, degree 3
+        B.s3(-27.0 / 48.0);
+        B.s21(0.2, 25.0 / 48.0);
+        return true;
+    case NL_RULE_PAPER7:   // centroid 27/60, vertices 3/60, mid-sides 8/60 (Sec. 6.3)
+        B.s3(27.0 / 60.0);
+        B.pt(1.0, 0.0, 0.0, 3.0 / 60.0);
+        B.pt(0.0, 1.0, 0.0, 3.0 / 60.0);
+        B.pt(0.0, 0.0, 1.0, 3.0 / 60.0);
+        B.pt(0.5, 0.5, 0.0, 8.0 / 60.0);
+        B.pt(0.0, 0.5, 0.5, 8.0 / 60.0);
+        B.pt(0.5, 0.0, 0.5, 8.0 / 60.0);
+        return true;
+    case NL_RULE_DUNAVANT7: {   // Radon's 7-point degree-5 rule
+        const double r = sqrt(15.0);
+        B.s3(9.0 / 40.0);
+        B.s21((6.0 - r) / 21.0, (155.0 - r) / 1200.0);
+        B.s21((6.0 + r) / 21.0, (155.0 + r) / 1200.0);
+        return true;
+    }
+    case NL_RULE_DUNAVANT16:   // Dunavant's 16-point degree-8 rule
+        B.s3(0.1443156076777871682510911);
+        B.s21(0.4592925882927231560288155, 0.0950916342672846247938961);
+        B.s21(0.1705693077517602066222935, 0.1032173705347182502817916);
+        B.s21(0.05054722831703097545842355, 0.03245849762319808031092593);
+        B.s111(0.008394777409957605337213835, 0.2631128296346381134217858, 0.02723031417443499426484469);
+        return true;
+    default:
+        return false;
+    }
+}
+
+// Gauss-Legendre nodes and weights on [0, 1] (Newton on the Legendre recurrence)
+void gauss_legendre01(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; i++) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 60; it++) {
+            double p = 1.0, pm = 0.0;
+            for (int k = 1; k <= n; k++) {
+                double pk = ((2.0 * k - 1.0) * z * p - (k - 1.0) * pm) / k;
+                pm = p;
+                p = pk;
+            }
+            dp = n * (z * p - pm) / (z * z - 1.0);
+            double step = p / dp;
+            z -= step;
+            if (fabs(step) < 1e-17) break;
+        }
+        x[i] = 0.5 * (1.0 - z);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+nl_status validate(nl_ctx *ctx, const nl_mesh *m, const nl_config *c)
+{
+    if (!ctx) return NL_EINVAL;
+    if (!m || !c) return nl_fail(ctx, NL_EINVAL, "null mesh or config");
+    if (m->nv <= 0 || m->nt <= 0 || !m->vx || !m->vy || !m->tri)
+        return nl_fail(ctx, NL_EINVAL, "mesh needs nv > 0, nt > 0 and vx, vy, tri");
+    if (!(c->delta > 0.0) || !isfinite(c->delta)) return nl_fail(ctx, NL_EINVAL, "delta must be positive");
+    if (c->ball < NL_BALL_BARYCENTER || c->ball > NL_BALL_OVERLAP) return nl_fail(ctx, NL_EINVAL, "bad ball");
+    if (c->kernel != NL_KERNEL_CONST && c->kernel != NL_KERNEL_INV_DIST) return nl_fail(ctx, NL_EINVAL, "bad kernel");
+    if (c->prec != NL_PREC_FP64 && c->prec != NL_PREC_FP32_COMP) return nl_fail(ctx, NL_EINVAL, "bad precision");
+    if (c->inner < NL_RULE_GAUSS3 || c->inner > NL_RULE_DUNAVANT16) return nl_fail(ctx, NL_EINVAL, "bad inner rule");
+    if (c->outer < NL_RULE_GAUSS3 || c->outer > NL_RULE_SWITCH47) return nl_fail(ctx, NL_EINVAL, "bad outer rule");
+    if (c->ball == NL_BALL_NGON && (c->ngon_n < 3 || c->ngon_n > 64 || !c->ngon_offsets))
+        return nl_fail(ctx, NL_EINVAL, "ngon needs 3 <= ngon_n <= 64 and ngon_offsets");
+    if (c->ball == NL_BALL_APPROXCAPS &&
+        (c->cap_m < 1 || c->cap_m > 16 || (c->cap_m & (c->cap_m - 1)) != 0))
+        return nl_fail(ctx, NL_EINVAL, "cap_m must be a power of two in 1..16");
+    if (c->kernel == NL_KERNEL_INV_DIST && (c->duffy_n < 1 || c->duffy_n > 7))
+        return nl_fail(ctx, NL_EINVAL, "duffy_n must be in 1..7");
+    return NL_OK;
+}
+
+nl_status fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
+{
+    memset(&A, 0, sizeof A);
+    const nl_config &c = P->cfg;
+    A.K = P->K;
+    A.E = P->E;
+    A.tx = P->tx;
+    A.ty = P->ty;
+    A.bx = P->bx;
+    A.by = P->by;
+    A.area = P->area;
+    A.nbr_ptr = P->nbr_ptr;
+    A.nbr_idx = P->nbr_idx;
+    if (c.outer == NL_RULE_SWITCH47) {
+        fill_rule(NL_RULE_GAUSS4, &A.outer);
+        A.outer.nsplit = A.outer.n;
+        fill_rule(NL_RULE_PAPER7, &A.outer);
+        A.switch47 = 1;
+        double thr = c.delta - P->hmax;
+        A.thr2 = thr > 0.0 ? thr * thr : -1.0;
+    } else {
+        if (!fill_rule(c.outer, &A.outer)) return nl_fail(ctx, NL_EINVAL, "bad outer rule");
+        A.outer.nsplit = A.outer.n;
+    }
+    if (!fill_rule(c.inner, &A.inner)) return nl_fail(ctx, NL_EINVAL, "bad inner rule");
+    A.inner.nsplit = A.inner.n;
+    A.duffy_n = c.kernel == NL_KERNEL_INV_DIST ? c.duffy_n : 1;
+    gauss_legendre01(A.duffy_n, A.gl_x, A.gl_w);
+    gauss_legendre01(2, A.gl2_x, A.gl2_w);
+    A.kernel = c.kernel;
+    A.kc = c.kernel_c;
+    A.geo.delta = c.delta;
+    A.geo.d2 = P->d2;
+    A.geo.ngon = P->ngon;
+    A.geo.ngon_n = c.ball == NL_BALL_NGON ? c.ngon_n : 0;
+    int level = 0;
+    while ((1 << level) < (c.cap_m > 0 ? c.cap_m : 1)) level++;
+    A.geo.cap_level = level;
+    A.geo.cap_printed = c.cap_printed;
+    A.flag = P->flag;
+    A.blk = P->blk;
+    A.maa = P->maa;
+    A.qp_a = P->qp_a;
+    A.cnt_a = P->cnt_a;
+    A.hash_a = P->hash_a;
+    A.stats = stats ? 1 : 0;
+    A.err = P->err;
+    return NL_OK;
+}
+
+nl_status alloc_numeric(nl_ctx *ctx, nl_plan *P)
+{
+    nl_status s;
+    const size_t tsz = P->cfg.prec == NL_PREC_FP64 ? sizeof(double) : sizeof(float);
+    if ((s = nl_alloc(ctx, &P->flag, (size_t)P->E)) != NL_OK) return s;
+    void *blk = nullptr;
+    cudaError_t e = cudaMalloc(&blk, tsz * 15 * (size_t)(P->E ? P->E : 1));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nl_fail(ctx, NL_ENOMEM, "pair-block buffer allocation failed");
+    }
+    P->blk = blk;
+    if ((s = nl_alloc(ctx, &P->maa, 6 * (size_t)P->K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->qp_a, (size_t)P->K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->cnt_a, (size_t)P->K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->hash_a, (size_t)P->K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->err, 1)) != NL_OK) return s;
+    NL_CK(cudaMemsetAsync(P->err, 0, sizeof(int), ctx->stream));
+    return NL_OK;
+}
+
+nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats)
+{
+    nlq::NumArgs A;
+    nl_status s = fill_args(ctx, P, A, stats);
+    if (s != NL_OK) return s;
+    if (P->cfg.prec == NL_PREC_FP64) return nl_launch_numeric_f64(ctx, A, P->cfg.ball);
+    return nl_launch_numeric_f32(ctx, A, P->cfg.ball);
+}
+
+}  // namespace
+
+void nl_plan_free(nl_plan *P)
+{
+    if (!P) return;
+    nl_free(P->tri); nl_free(P->tx); nl_free(P->ty); nl_free(P->bx); nl_free(P->by);
+    nl_free(P->rad); nl_free(P->area); nl_free(P->ngon); nl_free(P->nbr_ptr); nl_free(P->nbr_idx);
+    nl_free(P->flag); nl_free(P->blk); nl_free(P->maa); nl_free(P->qp_a); nl_free(P->cnt_a);
+    nl_free(P->hash_a); nl_free(P->lslot); nl_free(P->tslot); nl_free(P->W); nl_free(P->val32);
+    nl_free(P->err);
+}
+
+nl_status nl_run_numeric(nl_ctx *ctx, nl_plan *P, bool with_hash) { return run_numeric(ctx, P, with_hash); }
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+nl_status nl_create(nl_ctx **out, int device, void *stream)
+{
+    if (!out) return NL_EINVAL;
+    *out = nullptr;
+    nl_ctx *ctx = new (std::nothrow) nl_ctx();
+    if (!ctx) return NL_ENOMEM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess && stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else if (e == cudaSuccess) {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        ctx->own_stream = (e == cudaSuccess);
+    }
+    for (int i = 0; e == cudaSuccess && i < 5; i++) e = cudaEventCreate(&ctx->ev[i]);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        nl_destroy(ctx);
+        return NL_ECUDA;
+    }
+    *out = ctx;
+    return NL_OK;
+}
+
+void nl_destroy(nl_ctx *ctx)
+{
+    if (!ctx) return;
+    for (int i = 0; i < 5; i++)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *nl_last_error(nl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_csr *out)
+{
+    nl_status s = validate(ctx, mesh, cfg);
+    if (s != NL_OK) return s;
+    if (!out) return nl_fail(ctx, NL_EINVAL, "null output");
+    memset(out, 0, sizeof *out);
+    NL_CK(cudaSetDevice(ctx->device));
+    nl_plan *P = new (std::nothrow) nl_plan();
+    if (!P) return nl_fail(ctx, NL_ENOMEM, "host allocation failed");
+    out->priv = P;
+    NL_CK(cudaEventRecord(ctx->ev[0], ctx->stream));
+    if ((s = nl_prepare_mesh(ctx, mesh, cfg, P)) != NL_OK) goto fail;
+    if ((s = alloc_numeric(ctx, P)) != NL_OK) goto fail;
+    NL_CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+    if ((s = run_numeric(ctx, P, false)) != NL_OK) goto fail;
+    NL_CK(cudaEventRecord(ctx->ev[2], ctx->stream));
+    if ((s = nl_build_pattern(ctx, P, out)) != NL_OK) goto fail;
+    NL_CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+    if ((s = nl_run_scatter(ctx, P, out)) != NL_OK) goto fail;
+    NL_CK(cudaEventRecord(ctx->ev[4], ctx->stream));
+    return NL_OK;
+fail:
+    nl_csr_free(ctx, out);
+    return s;
+}
+
+nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *m)
+{
+    if (!ctx) return NL_EINVAL;
+    if (!m || !m->priv) return nl_fail(ctx, NL_EINVAL, "not an nl_assemble result");
+    nl_plan *P = (nl_plan *)m->priv;
+    if (!P->blk) return nl_fail(ctx, NL_EINVAL, "not an nl_assemble result");
+    nl_status s;
+    if ((s = run_numeric(ctx, P, false)) != NL_OK) return s;
+    return nl_run_scatter(ctx, P, m);
+}
+
+nl_status nl_interactions(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, uint64_t *hash_a,
+                          int64_t *count_a, int64_t *qp_a)
+{
+    nl_status s = validate(ctx, mesh, cfg);
+    if (s != NL_OK) return s;
+    NL_CK(cudaSetDevice(ctx->device));
+    nl_plan P;
+    if ((s = nl_prepare_mesh(ctx, mesh, cfg, &P)) == NL_OK && (s = alloc_numeric(ctx, &P)) == NL_OK &&
+        (s = run_numeric(ctx, &P, true)) == NL_OK) {
+        cudaError_t e = cudaSuccess;
+        if (hash_a && e == cudaSuccess)
+            e = cudaMemcpyAsync(hash_a, P.hash_a, sizeof(uint64_t) * P.K, cudaMemcpyDeviceToHost, ctx->stream);
+        if (count_a && e == cudaSuccess)
+            e = cudaMemcpyAsync(count_a, P.cnt_a, sizeof(int64_t) * P.K, cudaMemcpyDeviceToHost, ctx->stream);
+        if (qp_a && e == cudaSuccess)
+            e = cudaMemcpyAsync(qp_a, P.qp_a, sizeof(int64_t) * P.K, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) s = nl_cuda_fail(ctx, e, "download of interaction statistics");
+    }
+    nl_plan_free(&P);
+    return s;
+}
+
+nl_status nl_csr_download(nl_ctx *ctx, const nl_csr *m, int64_t *row_ptr, int32_t *col_idx, double *val)
+{
+    if (!ctx) return NL_EINVAL;
+    if (!m) return nl_fail(ctx, NL_EINVAL, "null matrix");
+    if (row_ptr)
+        NL_CK(cudaMemcpyAsync(row_ptr, m->row_ptr, sizeof(int64_t) * (m->n + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    if (col_idx && m->nnz)
+        NL_CK(cudaMemcpyAsync(col_idx, m->col_idx, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToHost, ctx->stream));
+    if (val && m->nnz)
+        NL_CK(cudaMemcpyAsync(val, m->val, sizeof(double) * m->nnz, cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    return NL_OK;
+}
+
+void nl_csr_free(nl_ctx *ctx, nl_csr *m)
+{
+    (void)ctx;
+    if (!m) return;
+    if (ctx && ctx->stream) cudaStreamSynchronize(ctx->stream);
+    nl_free(m->row_ptr);
+    nl_free(m->col_idx);
+    nl_free(m->val);
+    if (m->priv) {
+        nl_plan *P = (nl_plan *)m->priv;
+        nl_plan_free(P);
+        delete P;
+    }
+    memset(m, 0, sizeof *m);
+}
+
+int64_t nl_launch_count(nl_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+nl_status nl_last_timings(nl_ctx *ctx, double *ms4)
+{
+    if (!ctx || !ms4) return NL_EINVAL;
+    NL_CK(cudaEventSynchronize(ctx->ev[4]));
+    for (int i = 0; i < 4; i++) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]);
+        if (e != cudaSuccess) return nl_cuda_fail(ctx, e, "cudaEventElapsedTime");
+        ms4[i] = ms;
+    }
+    return NL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,443 @@
+// mesh.cu -- preprocessing of the mesh and cell-list neighbour search.
+//
+// Per triangle (Sec. 7.1 task 1): vertex coordinates gathered into SoA arrays,
+// barycentre ((v0 + v1) + v2) / 3 in round-to-nearest FP64 (the same expression
+// the geometry tests use), radius r_k = max |v_i - bary_k|, area, and the longest
+// edge (h_max, used by the outer-rule switch of Sec. 8).
+//
+// Candidate pairs (Sec. 7.1 task 2): T_b is a candidate of T_a iff
+// |bary_a - bary_b| <= delta + r_a + r_b (inflated by 1e-9 relative).  This is
+// a superset of every pair whose region can be non-empty: a point x of T_a and
+// a point y of T_b with |x - y| <= delta lie within r_a and r_b of the
+// barycentres.  (The paper's radius delta + h_max is not sufficient for every
+// triangle shape; the two-radius bound is.)  Candidates are found with a uniform
+// cell list over the barycentres: deterministic buckets (sorted by triangle
+// index) and per-triangle candidate lists sorted by triangle index.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+__global__ void k_scan_block(const int64_t *in, int64_t *out, int64_t *bsum, int64_t n)
+{
+    __shared__ int64_t wsum[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t tot = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        v[i] = idx < n ? in[idx] : 0;
+        tot += v[i];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = tot;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < (kScanThreads / 32) ? wsum[lane] : 0;
+        int64_t s = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, s, off);
+            if (lane >= off) s += y;
+        }
+        if (lane < (kScanThreads / 32)) wsum[lane] = s - w;
+        if (lane == (kScanThreads / 32) - 1) bsum[blockIdx.x] = s;
+    }
+    __syncthreads();
+    int64_t run = wsum[warp] + (x - tot);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        int64_t idx = base + i;
+        if (idx < n) out[idx] = run;
+        run += v[i];
+    }
+}
+
+__global__ void k_scan_add(int64_t *out, const int64_t *boff, int64_t n)
+{
+    int64_t idx = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    int64_t add = boff[blockIdx.x];
+    for (int i = 0; i < kScanItems; i++, idx += kScanThreads)
+        if (idx < n) out[idx] += add;
+}
+
+__global__ void k_copy1(int64_t *dst, const int64_t *src) { *dst = *src; }
+
+// ---------------------------------------------------------------------------
+// preprocessing
+// ---------------------------------------------------------------------------
+__global__ void k_prepare(int K, int J, const int32_t *__restrict__ tri, const double *__restrict__ vx,
+                          const double *__restrict__ vy, double *tx, double *ty, double *bx, double *by,
+                          double *rad, double *area, double *diam, int *bad)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K) return;
+    int i0 = tri[3 * t], i1 = tri[3 * t + 1], i2 = tri[3 * t + 2];
+    if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= J || i1 >= J || i2 >= J) {
+        atomicAdd(bad, 1);
+        return;
+    }
+    double x0 = vx[i0], y0 = vy[i0], x1 = vx[i1], y1 = vy[i1], x2 = vx[i2], y2 = vy[i2];
+    tx[t] = x0; tx[K + t] = x1; tx[2 * K + t] = x2;
+    ty[t] = y0; ty[K + t] = y1; ty[2 * K + t] = y2;
+    // barycentre ((v0 + v1) + v2) / 3, round-to-nearest, no contraction
+    double cx = __ddiv_rn(__dadd_rn(__dadd_rn(x0, x1), x2), 3.0);
+    double cy = __ddiv_rn(__dadd_rn(__dadd_rn(y0, y1), y2), 3.0);
+    bx[t] = cx;
+    by[t] = cy;
+    double r = 0.0;
+    const double xs[3] = {x0, x1, x2}, ys[3] = {y0, y1, y2};
+    double dmax = 0.0;
+    for (int i = 0; i < 3; i++) {
+        double dx = xs[i] - cx, dy = ys[i] - cy;
+        r = fmax(r, sqrt(dx * dx + dy * dy));
+        // longest edge: sqrt(dx*dx + dy*dy) with dx = q - p, exactly rounded
+        double ex = __dsub_rn(xs[(i + 1) % 3], xs[i]), ey = __dsub_rn(ys[(i + 1) % 3], ys[i]);
+        dmax = fmax(dmax, __dsqrt_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey))));
+    }
+    rad[t] = r;
+    diam[t] = dmax;
+    double cr = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
+    area[t] = 0.5 * fabs(cr);
+    if (!(cr > 0.0)) atomicAdd(bad, 1);
+}
+
+struct MeshStats {
+    double xmin, xmax, ymin, ymax, rmax, hmax;
+};
+
+__global__ void k_mesh_stats(int K, const double *bx, const double *by, const double *rad, const double *diam,
+                             MeshStats *out)
+{
+    __shared__ double s[6][32];
+    double v[6] = {INFINITY, -INFINITY, INFINITY, -INFINITY, 0.0, 0.0};
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+        v[0] = fmin(v[0], bx[t]); v[1] = fmax(v[1], bx[t]);
+        v[2] = fmin(v[2], by[t]); v[3] = fmax(v[3], by[t]);
+        v[4] = fmax(v[4], rad[t]); v[5] = fmax(v[5], diam[t]);
+    }
+    for (int off = 16; off; off >>= 1) {
+        v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], off));
+        v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], off));
+        v[2] = fmin(v[2], __shfl_xor_sync(0xffffffffu, v[2], off));
+        v[3] = fmax(v[3], __shfl_xor_sync(0xffffffffu, v[3], off));
+        v[4] = fmax(v[4], __shfl_xor_sync(0xffffffffu, v[4], off));
+        v[5] = fmax(v[5], __shfl_xor_sync(0xffffffffu, v[5], off));
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int i = 0; i < 6; i++) s[i][w] = v[i];
+    __syncthreads();
+    if (w == 0) {
+        for (int i = 0; i < 6; i++) {
+            double init = (i == 0 || i == 2) ? INFINITY : ((i == 1 || i == 3) ? -INFINITY : 0.0);
+            v[i] = lane < nw ? s[i][lane] : init;
+        }
+        for (int off = 16; off; off >>= 1) {
+            v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], off));
+            v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], off));
+            v[2] = fmin(v[2], __shfl_xor_sync(0xffffffffu, v[2], off));
+            v[3] = fmax(v[3], __shfl_xor_sync(0xffffffffu, v[3], off));
+            v[4] = fmax(v[4], __shfl_xor_sync(0xffffffffu, v[4], off));
+            v[5] = fmax(v[5], __shfl_xor_sync(0xffffffffu, v[5], off));
+        }
+        if (lane == 0) {
+            out->xmin = v[0]; out->xmax = v[1]; out->ymin = v[2]; out->ymax = v[3];
+            out->rmax = v[4]; out->hmax = v[5];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// cell list
+// ---------------------------------------------------------------------------
+struct Grid {
+    double x0, y0, cs;
+    int nx, ny, m;  // m: cells searched in each direction
+};
+
+__device__ __forceinline__ int cell_of(const Grid &g, double x, double y, int *cx, int *cy)
+{
+    int ix = (int)floor((x - g.x0) / g.cs), iy = (int)floor((y - g.y0) / g.cs);
+    ix = min(max(ix, 0), g.nx - 1);
+    iy = min(max(iy, 0), g.ny - 1);
+    *cx = ix; *cy = iy;
+    return iy * g.nx + ix;
+}
+
+__global__ void k_cell_count(int K, Grid g, const double *bx, const double *by, int32_t *cell, int64_t *cnt)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K) return;
+    int cx, cy;
+    int c = cell_of(g, bx[t], by[t], &cx, &cy);
+    cell[t] = c;
+    atomicAdd((unsigned long long *)&cnt[c], 1ull);
+}
+
+__global__ void k_cell_fill(int K, const int32_t *cell, const int64_t *start, int64_t *cursor, int32_t *bucket)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K) return;
+    int c = cell[t];
+    int64_t pos = start[c] + (int64_t)atomicAdd((unsigned long long *)&cursor[c], 1ull);
+    bucket[pos] = t;
+}
+
+// sort each bucket by triangle index (rank by counting; buckets are small)
+__global__ void k_cell_sort(const int64_t *start, int32_t *bucket, int *overflow)
+{
+    extern __shared__ int32_t sb[];
+    int c = blockIdx.x;
+    int64_t s = start[c], n = start[c + 1] - s;
+    if (n > NL_MAXCAND) {
+        if (threadIdx.x == 0) atomicAdd(overflow, 1);
+        return;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sb[i] = bucket[s + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int v = sb[i], rank = 0;
+        for (int k = 0; k < n; k++) rank += sb[k] < v;
+        bucket[s + rank] = v;
+    }
+}
+
+// candidate search, warp per outer triangle; pass 0 counts, pass 1 writes
+__global__ void k_candidates(int K, Grid g, double delta, const double *__restrict__ bx,
+                             const double *__restrict__ by, const double *__restrict__ rad,
+                             const int64_t *__restrict__ start, const int32_t *__restrict__ bucket,
+                             int64_t *cnt, const int64_t *ptr, int32_t *idx, int pass)
+{
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= K) return;
+    int a = warp;
+    double ax = bx[a], ay = by[a], ra = rad[a];
+    int cx, cy;
+    cell_of(g, ax, ay, &cx, &cy);
+    int64_t n = 0;
+    int64_t out = pass ? ptr[a] : 0;
+    const int y0 = max(cy - g.m, 0), y1 = min(cy + g.m, g.ny - 1);
+    const int x0 = max(cx - g.m, 0), x1 = min(cx + g.m, g.nx - 1);
+    for (int yy = y0; yy <= y1; yy++) {
+        for (int xx = x0; xx <= x1; xx++) {
+            int c = yy * g.nx + xx;
+            int64_t s = start[c], e = start[c + 1];
+            for (int64_t base = s; base < e; base += 32) {
+                int64_t k = base + lane;
+                bool hit = false;
+                int b = -1;
+                if (k < e) {
+                    b = bucket[k];
+                    double ddx = bx[b] - ax, ddy = by[b] - ay;
+                    double R = (delta + (ra + rad[b])) * (1.0 + 1e-9);   // symmetric in (a, b)
+                    hit = ddx * ddx + ddy * ddy <= R * R;
+                }
+                unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (pass && hit) idx[out + n + __popc(m & ((1u << lane) - 1u))] = b;
+                n += __popc(m);
+            }
+        }
+    }
+    if (!pass && lane == 0) cnt[a] = n;
+}
+
+// sort each candidate list by triangle index (bitonic sort in shared memory)
+__global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int *overflow)
+{
+    __shared__ int32_t s[NL_MAXCAND];
+    int a = blockIdx.x;
+    int64_t b0 = ptr[a];
+    int n = (int)(ptr[a + 1] - b0);
+    if (n > NL_MAXCAND) {
+        if (threadIdx.x == 0) atomicAdd(overflow, 1);
+        return;
+    }
+    int p = 1;
+    while (p < n) p <<= 1;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) s[i] = i < n ? idx[b0 + i] : 0x7fffffff;
+    __syncthreads();
+    for (int k = 2; k <= p; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < p; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    bool up = (i & k) == 0;
+                    int u = s[i], v = s[l];
+                    if ((u > v) == up) { s[i] = v; s[l] = u; }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) idx[b0 + i] = s[i];
+}
+
+}  // namespace
+
+nl_status nl_scan_i64(nl_ctx *ctx, const int64_t *in, int64_t *out, int64_t n)
+{
+    if (n <= 0) {
+        NL_CK(cudaMemsetAsync(out, 0, sizeof(int64_t), ctx->stream));
+        return NL_OK;
+    }
+    int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    int64_t *bsum = nullptr;
+    NL_CK(cudaMallocAsync((void **)&bsum, sizeof(int64_t) * (nb + 1), ctx->stream));
+    k_scan_block<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(in, out, bsum, n); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    if (nb == 1) {
+        k_copy1<<<1, 1, 0, ctx->stream>>>(out + n, bsum); ++ctx->launches;
+    } else {
+        nl_status s = nl_scan_i64(ctx, bsum, bsum, nb);
+        if (s != NL_OK) return s;
+        k_scan_add<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(out, bsum, n); ++ctx->launches;
+        k_copy1<<<1, 1, 0, ctx->stream>>>(out + n, bsum + nb); ++ctx->launches;
+    }
+    NL_CK(cudaGetLastError());
+    NL_CK(cudaFreeAsync(bsum, ctx->stream));
+    return NL_OK;
+}
+
+nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_plan *P)
+{
+    const int K = mesh->nt, J = mesh->nv;
+    P->K = K;
+    P->J = J;
+    P->cfg = *cfg;
+    P->d2 = cfg->delta * cfg->delta;
+    nl_status s;
+    bool own_vx = false, own_vy = false, own_tri = false;
+    void *dvx = nullptr, *dvy = nullptr, *dtri = nullptr;
+    if ((s = nl_stage(ctx, mesh->vx, sizeof(double) * J, &dvx, &own_vx)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, mesh->vy, sizeof(double) * J, &dvy, &own_vy)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, mesh->tri, sizeof(int32_t) * 3 * K, &dtri, &own_tri)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->tri, 3 * (size_t)K)) != NL_OK) return s;
+    NL_CK(cudaMemcpyAsync(P->tri, dtri, sizeof(int32_t) * 3 * K, cudaMemcpyDeviceToDevice, ctx->stream));
+    if ((s = nl_alloc(ctx, &P->tx, 3 * (size_t)K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->ty, 3 * (size_t)K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->bx, K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->by, K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->rad, K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->area, K)) != NL_OK) return s;
+    if (cfg->ball == NL_BALL_NGON) {
+        void *doff = nullptr;
+        bool own_off = false;
+        if ((s = nl_alloc(ctx, &P->ngon, 2 * (size_t)cfg->ngon_n)) != NL_OK) return s;
+        if ((s = nl_stage(ctx, cfg->ngon_offsets, sizeof(double) * 2 * cfg->ngon_n, &doff, &own_off)) != NL_OK)
+            return s;
+        NL_CK(cudaMemcpyAsync(P->ngon, doff, sizeof(double) * 2 * cfg->ngon_n, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+        if (own_off) NL_CK(cudaFreeAsync(doff, ctx->stream));
+    }
+    double *diam = nullptr;
+    int *bad = nullptr;
+    MeshStats *st = nullptr;
+    NL_CK(cudaMallocAsync((void **)&diam, sizeof(double) * K, ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&bad, sizeof(int), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&st, sizeof(MeshStats), ctx->stream));
+    NL_CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+    k_prepare<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, J, (const int32_t *)dtri, (const double *)dvx,
+                                                        (const double *)dvy, P->tx, P->ty, P->bx, P->by,
+                                                        P->rad, P->area, diam, bad); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    k_mesh_stats<<<1, 1024, 0, ctx->stream>>>(K, P->bx, P->by, P->rad, diam, st); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    MeshStats hst;
+    int hbad = 0;
+    NL_CK(cudaMemcpyAsync(&hst, st, sizeof hst, cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaFreeAsync(diam, ctx->stream));
+    NL_CK(cudaFreeAsync(bad, ctx->stream));
+    NL_CK(cudaFreeAsync(st, ctx->stream));
+    if (own_vx) NL_CK(cudaFreeAsync(dvx, ctx->stream));
+    if (own_vy) NL_CK(cudaFreeAsync(dvy, ctx->stream));
+    if (own_tri) NL_CK(cudaFreeAsync(dtri, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    if (hbad)
+        return nl_fail(ctx, NL_EGEOM, std::to_string(hbad) +
+                                          " triangles are degenerate, clockwise or index a missing vertex");
+    if (!(cfg->delta > hst.hmax))
+        return nl_fail(ctx, NL_EGEOM, "delta must exceed the largest triangle diameter (" +
+                                          std::to_string(hst.hmax) + ")");
+    P->hmax = hst.hmax;
+    // grid for the candidate search
+    double R = (cfg->delta + 2.0 * hst.rmax) * (1.0 + 1e-9);
+    double Lx = hst.xmax - hst.xmin, Ly = hst.ymax - hst.ymin, L = fmax(fmax(Lx, Ly), 1e-300);
+    double cs = fmin(R, L / sqrt(fmax(K / 32.0, 1.0)));
+    Grid g;
+    g.cs = cs;
+    g.m = (int)ceil(R / cs);
+    g.x0 = hst.xmin;
+    g.y0 = hst.ymin;
+    g.nx = (int)floor(Lx / cs) + 1;
+    g.ny = (int)floor(Ly / cs) + 1;
+    // stash the grid in the candidate stage (kept on the host side of the plan)
+    int ncell = g.nx * g.ny;
+    int32_t *cell = nullptr, *bucket = nullptr;
+    int64_t *ccnt = nullptr, *cstart = nullptr, *cursor = nullptr;
+    int *ovf = nullptr;
+    NL_CK(cudaMallocAsync((void **)&cell, sizeof(int32_t) * K, ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&bucket, sizeof(int32_t) * K, ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&ccnt, sizeof(int64_t) * (ncell + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&cstart, sizeof(int64_t) * (ncell + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&cursor, sizeof(int64_t) * (ncell + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&ovf, sizeof(int), ctx->stream));
+    NL_CK(cudaMemsetAsync(ccnt, 0, sizeof(int64_t) * (ncell + 1), ctx->stream));
+    NL_CK(cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (ncell + 1), ctx->stream));
+    NL_CK(cudaMemsetAsync(ovf, 0, sizeof(int), ctx->stream));
+    k_cell_count<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, g, P->bx, P->by, cell, ccnt); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    if ((s = nl_scan_i64(ctx, ccnt, cstart, ncell)) != NL_OK) return s;
+    k_cell_fill<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, cell, cstart, cursor, bucket); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    k_cell_sort<<<ncell, 256, sizeof(int32_t) * NL_MAXCAND, ctx->stream>>>(cstart, bucket, ovf); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    // candidate lists
+    if ((s = nl_alloc(ctx, &P->nbr_ptr, (size_t)K + 1)) != NL_OK) return s;
+    int64_t *cnt = nullptr;
+    NL_CK(cudaMallocAsync((void **)&cnt, sizeof(int64_t) * K, ctx->stream));
+    unsigned wblocks = (unsigned)(((int64_t)K * 32 + 255) / 256);
+    k_candidates<<<wblocks, 256, 0, ctx->stream>>>(K, g, cfg->delta, P->bx, P->by, P->rad, cstart, bucket, cnt,
+                                                   nullptr, nullptr, 0); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    if ((s = nl_scan_i64(ctx, cnt, P->nbr_ptr, K)) != NL_OK) return s;
+    int64_t E = 0;
+    int hovf = 0;
+    NL_CK(cudaMemcpyAsync(&E, P->nbr_ptr + K, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    if (hovf) return nl_fail(ctx, NL_EUNSUPPORTED, "cell-list bucket exceeds the shared-memory sort limit");
+    P->E = E;
+    if ((s = nl_alloc(ctx, &P->nbr_idx, (size_t)E)) != NL_OK) return s;
+    k_candidates<<<wblocks, 256, 0, ctx->stream>>>(K, g, cfg->delta, P->bx, P->by, P->rad, cstart, bucket,
+                                                   nullptr, P->nbr_ptr, P->nbr_idx, 1); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    k_sort_lists<<<K, 256, 0, ctx->stream>>>(P->nbr_ptr, P->nbr_idx, ovf); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    NL_CK(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaFreeAsync(cnt, ctx->stream));
+    NL_CK(cudaFreeAsync(cell, ctx->stream));
+    NL_CK(cudaFreeAsync(bucket, ctx->stream));
+    NL_CK(cudaFreeAsync(ccnt, ctx->stream));
+    NL_CK(cudaFreeAsync(cstart, ctx->stream));
+    NL_CK(cudaFreeAsync(cursor, ctx->stream));
+    NL_CK(cudaFreeAsync(ovf, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    if (hovf) return nl_fail(ctx, NL_EUNSUPPORTED, "a triangle has more than 4096 candidate neighbours");
+    return NL_OK;
+}
+
+nl_status nl_build_candidates(nl_ctx *, nl_plan *) { return NL_OK; }

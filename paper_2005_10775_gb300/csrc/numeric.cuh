@@ -1,0 +1,349 @@
+// numeric.cuh -- pair geometry + quadrature, one warp per outer triangle T_a.
+//
+// For the outer triangle T_a the warp stages its outer quadrature points x_q,
+// weights W_q = w_q |T_a| and barycentric coordinates phi_a(x_q) in shared memory;
+// each lane then takes candidate neighbours T_b in turn and, for every x_q, builds
+// R(x_q, T_b) (geometry.cuh) and its inner sums
+//     s0 = sum w psi,  s1 = sum w psi phi_b,  S2 = sum w psi phi_b phi_b^T
+// over the fan subtriangles (inner rule) and caps (one centroid point), which
+// gives the expansion of (phi_j(x)-phi_j(y))(phi_j'(x)-phi_j'(y)) psi of
+// Eq. (bformhj) over the six local nodes (Sec. 7.2):
+//     M_aa += W s0 phi_a phi_a^T,   M_bb += W S2,   M_ab += W phi_a s1^T
+// (D receives +M_aa, +M_bb, -M_ab and -M_ab^T).  Per candidate pair the lane writes
+// M_ab (9) and M_bb (6, symmetric) to a pair buffer and a directed interaction
+// flag; M_aa is summed over all candidates in FP64 and reduced across the warp.
+//
+// T = double: FP64 quadrature.  T = float: the inner and per-pair sums run in FP32,
+// the long sums (M_aa over all neighbours, and D over all pairs in the scatter) in
+// FP64, which compensates the FP32 rounding of the short sums.
+#pragma once
+
+#include "geometry.cuh"
+
+namespace nlq {
+
+using nlg::D2;
+
+struct RuleTab {
+    int n, nsplit;            // nsplit: first point of the second rule (outer switch), else n
+    double l[NL_MAXQ + 8][3];
+    double w[NL_MAXQ + 8];
+};
+
+struct NumArgs {
+    int K;
+    int64_t E;
+    const double *tx, *ty;            // [3][K]
+    const double *bx, *by, *area;     // [K]
+    const int64_t *nbr_ptr;
+    const int32_t *nbr_idx;
+    RuleTab outer, inner;
+    double gl_x[8], gl_w[8];          // Gauss-Legendre on [0,1] with duffy_n points
+    double gl2_x[2], gl2_w[2];
+    int duffy_n;
+    int switch47;                     // outer rule: 0..nsplit-1 if |bary_a - bary_b|^2 < thr2 else nsplit..n-1
+    double thr2;                      // (delta - h_max)^2, or -1 when delta <= h_max
+    int kernel;                       // nl_kernel
+    double kc;
+    nlg::GeoParams geo;
+    uint8_t *flag;
+    void *blk;                        // [15][E]
+    double *maa;                      // [6][K]
+    int64_t *qp_a, *cnt_a;
+    uint64_t *hash_a;
+    int stats;
+    int *err;                         // device error word: bit 0 = region buffer bound hit
+};
+
+template <typename T>
+struct Sums {
+    T s0, s1[3], S2[6];   // S2: 00 11 22 01 02 12
+};
+
+template <typename T>
+__device__ __forceinline__ void sums_zero(Sums<T> &S)
+{
+    S.s0 = 0;
+    for (int i = 0; i < 3; i++) S.s1[i] = 0;
+    for (int i = 0; i < 6; i++) S.S2[i] = 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void sums_add(Sums<T> &S, T w, T p0, T p1, T p2)
+{
+    S.s0 += w;
+    T w0 = w * p0, w1 = w * p1, w2 = w * p2;
+    S.s1[0] += w0; S.s1[1] += w1; S.s1[2] += w2;
+    S.S2[0] += w0 * p0; S.S2[1] += w1 * p1; S.S2[2] += w2 * p2;
+    S.S2[3] += w0 * p1; S.S2[4] += w0 * p2; S.S2[5] += w1 * p2;
+}
+
+// affine map y -> barycentric coordinates in T_b (values only)
+struct BaryMap {
+    double ox, oy, e1x, e1y, e2x, e2y, inv;
+};
+
+__device__ __forceinline__ BaryMap bary_map(const D2 V[3])
+{
+    BaryMap m;
+    m.ox = V[0].x; m.oy = V[0].y;
+    m.e1x = V[1].x - V[0].x; m.e1y = V[1].y - V[0].y;
+    m.e2x = V[2].x - V[0].x; m.e2y = V[2].y - V[0].y;
+    m.inv = 1.0 / (m.e1x * m.e2y - m.e2x * m.e1y);
+    return m;
+}
+
+__device__ __forceinline__ void bary_of(const BaryMap &m, double yx, double yy, double phi[3])
+{
+    double dx = yx - m.ox, dy = yy - m.oy;
+    double l1 = (dx * m.e2y - m.e2x * dy) * m.inv;
+    double l2 = (m.e1x * dy - dx * m.e1y) * m.inv;
+    phi[0] = 1.0 - l1 - l2;
+    phi[1] = l1;
+    phi[2] = l2;
+}
+
+// Near-singular rule for psi = c/|x - y| (signed apex-x decomposition with a Duffy
+// collapse in s and the sinh substitution in u; dy/|x-y| = d ds du), FP64.
+__device__ __forceinline__ void near_right_triangle(const NumArgs &A, const BaryMap &bm, D2 x, D2 F, double ex,
+                                                    double ey, double d, double tau, double sign,
+                                                    Sums<double> &S, int64_t &nqp)
+{
+    if (tau == 0.0) return;
+    double sg = tau > 0.0 ? 1.0 : -1.0;
+    double U = asinh(fabs(tau) / d);
+    int npan = (int)ceil(U);
+    if (npan < 1) npan = 1;
+    const int nu = A.duffy_n;
+    for (int p = 0; p < npan; p++) {
+        double u0 = (double)p, u1 = (p + 1 < npan) ? (double)(p + 1) : U;
+        double hw = u1 - u0;
+        for (int j = 0; j < nu; j++) {
+            double u = u0 + hw * A.gl_x[j];
+            double wu = hw * A.gl_w[j];
+            double sh = sinh(u);
+            double wx = (F.x - x.x) + sg * d * sh * ex;
+            double wy = (F.y - x.y) + sg * d * sh * ey;
+            for (int i = 0; i < 2; i++) {
+                double sv = A.gl2_x[i];
+                double phi[3];
+                bary_of(bm, x.x + sv * wx, x.y + sv * wy, phi);
+                sums_add<double>(S, sign * sg * d * A.gl2_w[i] * wu * A.kc, phi[0], phi[1], phi[2]);
+                nqp++;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void near_polygon(const NumArgs &A, const BaryMap &bm, D2 x, const nlg::Region &R,
+                                             Sums<double> &S, int64_t &nqp)
+{
+    const int n = R.nv;
+    for (int i = 0; i < n; i++) {
+        D2 a = R.P[i], b = R.P[(i + 1) % n];
+        double ex = b.x - a.x, ey = b.y - a.y;
+        double L = sqrt(ex * ex + ey * ey);
+        if (L == 0.0) continue;
+        ex /= L;
+        ey /= L;
+        double tA = (a.x - x.x) * ex + (a.y - x.y) * ey;
+        double tB = (b.x - x.x) * ex + (b.y - x.y) * ey;
+        D2 F;
+        F.x = a.x - tA * ex;
+        F.y = a.y - tA * ey;
+        double fx = F.x - x.x, fy = F.y - x.y;
+        double d = sqrt(fx * fx + fy * fy);
+        if (d == 0.0) continue;
+        double sigma = (fx * ey - fy * ex) > 0.0 ? 1.0 : -1.0;
+        near_right_triangle(A, bm, x, F, ex, ey, d, tB, sigma, S, nqp);
+        near_right_triangle(A, bm, x, F, ex, ey, d, tA, -sigma, S, nqp);
+    }
+}
+
+// inner sums of the region R(x, T_b)
+template <typename T>
+__device__ __forceinline__ void inner_sums(const NumArgs &A, const nlg::Region &R, const D2 V[3], double area_b,
+                                           D2 x, Sums<T> &S, int64_t &nqp)
+{
+    sums_zero(S);
+    const bool inv = (A.kernel == NL_KERNEL_INV_DIST);
+    const RuleTab &ri = A.inner;
+    if (inv && R.nv >= 3 && nlg::is_near(R, V, x)) {
+        BaryMap bm = bary_map(V);
+        Sums<double> Sd;
+        sums_zero(Sd);
+        near_polygon(A, bm, x, R, Sd, nqp);
+        S.s0 = (T)Sd.s0;
+        for (int i = 0; i < 3; i++) S.s1[i] = (T)Sd.s1[i];
+        for (int i = 0; i < 6; i++) S.S2[i] = (T)Sd.S2[i];
+    } else if (R.kind == nlg::KIND_WHOLE && R.ncap == 0) {
+        // the region is T_b itself: phi_b at the rule points are the rule's barycentrics
+        const T ar = (T)area_b;
+        T lx[3], ly[3];
+        if (inv)
+            for (int i = 0; i < 3; i++) { lx[i] = (T)(V[i].x - x.x); ly[i] = (T)(V[i].y - x.y); }
+        for (int r = 0; r < ri.n; r++) {
+            T p0 = (T)ri.l[r][0], p1 = (T)ri.l[r][1], p2 = (T)ri.l[r][2];
+            T w = (T)ri.w[r] * ar;
+            if (inv) {
+                T dx = p0 * lx[0] + p1 * lx[1] + p2 * lx[2];
+                T dy = p0 * ly[0] + p1 * ly[1] + p2 * ly[2];
+                w = w * (T)A.kc / sqrt(dx * dx + dy * dy);
+            } else {
+                w = w * (T)A.kc;
+            }
+            sums_add<T>(S, w, p0, p1, p2);
+        }
+        nqp += ri.n;
+    } else {
+        BaryMap bm = bary_map(V);
+        if (R.nv >= 3) {
+            double ph0[3];
+            bary_of(bm, R.P[0].x, R.P[0].y, ph0);
+            T f0[3] = {(T)ph0[0], (T)ph0[1], (T)ph0[2]};
+            T l0x = (T)(R.P[0].x - x.x), l0y = (T)(R.P[0].y - x.y);
+            double phk[3];
+            bary_of(bm, R.P[1].x, R.P[1].y, phk);
+            T fk[3] = {(T)phk[0], (T)phk[1], (T)phk[2]};
+            T lkx = (T)(R.P[1].x - x.x), lky = (T)(R.P[1].y - x.y);
+            for (int k = 1; k + 1 < R.nv; k++) {
+                D2 s0p = R.P[0], s1p = R.P[k], s2p = R.P[k + 1];
+                double ar = 0.5 * fabs((s1p.x - s0p.x) * (s2p.y - s0p.y) - (s2p.x - s0p.x) * (s1p.y - s0p.y));
+                double phn[3];
+                bary_of(bm, s2p.x, s2p.y, phn);
+                T fn[3] = {(T)phn[0], (T)phn[1], (T)phn[2]};
+                T lnx = (T)(s2p.x - x.x), lny = (T)(s2p.y - x.y);
+                const T art = (T)ar;
+                for (int r = 0; r < ri.n; r++) {
+                    T m0 = (T)ri.l[r][0], m1 = (T)ri.l[r][1], m2 = (T)ri.l[r][2];
+                    T p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
+                    T p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
+                    T p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
+                    T w = (T)ri.w[r] * art;
+                    if (inv) {
+                        T dx = m0 * l0x + m1 * lkx + m2 * lnx;
+                        T dy = m0 * l0y + m1 * lky + m2 * lny;
+                        w = w * (T)A.kc / sqrt(dx * dx + dy * dy);
+                    } else {
+                        w = w * (T)A.kc;
+                    }
+                    sums_add<T>(S, w, p0, p1, p2);
+                }
+                nqp += ri.n;
+                fk[0] = fn[0]; fk[1] = fn[1]; fk[2] = fn[2];
+                lkx = lnx; lky = lny;
+            }
+        }
+        for (int c = 0; c < R.ncap; c++) {
+            double ph[3];
+            bary_of(bm, R.cc[c].x, R.cc[c].y, ph);
+            T w = (T)R.cw[c];
+            if (inv) {
+                double dx = R.cc[c].x - x.x, dy = R.cc[c].y - x.y;
+                w = w * (T)(A.kc / sqrt(dx * dx + dy * dy));
+            } else {
+                w = w * (T)A.kc;
+            }
+            sums_add<T>(S, w, (T)ph[0], (T)ph[1], (T)ph[2]);
+            nqp++;
+        }
+    }
+}
+
+struct OuterPt {
+    double x, y, W, l0, l1, l2;
+};
+
+constexpr int kWarpsPerBlock = 4;
+
+template <int BALL, typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_numeric(const NumArgs A)
+{
+    __shared__ OuterPt sq[kWarpsPerBlock][NL_MAXQ + 8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int a = blockIdx.x * kWarpsPerBlock + wib;
+    if (a >= A.K) return;
+    const int K = A.K;
+    D2 Va[3];
+    for (int i = 0; i < 3; i++) { Va[i].x = A.tx[i * K + a]; Va[i].y = A.ty[i * K + a]; }
+    const double area_a = A.area[a];
+    const int nq_all = A.outer.n;
+    for (int q = lane; q < nq_all; q += 32) {
+        double l0 = A.outer.l[q][0], l1 = A.outer.l[q][1], l2 = A.outer.l[q][2];
+        OuterPt o;
+        // x_q = l0 v0 + l1 v1 + l2 v2, left to right, round-to-nearest
+        o.x = nlg::add(nlg::add(nlg::mul(l0, Va[0].x), nlg::mul(l1, Va[1].x)), nlg::mul(l2, Va[2].x));
+        o.y = nlg::add(nlg::add(nlg::mul(l0, Va[0].y), nlg::mul(l1, Va[1].y)), nlg::mul(l2, Va[2].y));
+        o.W = A.outer.w[q] * area_a;
+        o.l0 = l0; o.l1 = l1; o.l2 = l2;
+        sq[wib][q] = o;
+    }
+    __syncwarp();
+    const D2 ba = {A.bx[a], A.by[a]};
+    double maa[6] = {0, 0, 0, 0, 0, 0};
+    int64_t cnt = 0, qp = 0;
+    uint64_t hsum = 0;
+    T *blk = (T *)A.blk;
+    const int64_t E = A.E;
+    const int64_t e0 = A.nbr_ptr[a], e1 = A.nbr_ptr[a + 1];
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const int b = A.nbr_idx[e];
+        D2 Vb[3];
+        for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
+        const D2 bb = {A.bx[b], A.by[b]};
+        const double area_b = A.area[b];
+        int q0 = 0, q1 = nq_all;
+        if (A.switch47) {
+            double dx = nlg::sub(ba.x, bb.x), dy = nlg::sub(ba.y, bb.y);
+            bool near4 = A.thr2 > 0.0 && nlg::add(nlg::mul(dx, dx), nlg::mul(dy, dy)) < A.thr2;
+            if (near4) q1 = A.outer.nsplit; else q0 = A.outer.nsplit;
+        }
+        T mab[9], mbb[6], maa_b[6];
+        for (int i = 0; i < 9; i++) mab[i] = 0;
+        for (int i = 0; i < 6; i++) { mbb[i] = 0; maa_b[i] = 0; }
+        bool any = false;
+        for (int q = q0; q < q1; q++) {
+            const OuterPt o = sq[wib][q];
+            const D2 x = {o.x, o.y};
+            nlg::Region R;
+            nlg::make_region<BALL>(Vb, bb, x, A.geo, R);
+            if (R.overflow) atomicOr(A.err, 1);
+            if (R.kind == nlg::KIND_NONE) continue;
+            any = true;
+            Sums<T> S;
+            int64_t nq = 0;
+            inner_sums<T>(A, R, Vb, area_b, x, S, nq);
+            const T W = (T)o.W, la0 = (T)o.l0, la1 = (T)o.l1, la2 = (T)o.l2;
+            mbb[0] += W * S.S2[0]; mbb[1] += W * S.S2[1]; mbb[2] += W * S.S2[2];
+            mbb[3] += W * S.S2[3]; mbb[4] += W * S.S2[4]; mbb[5] += W * S.S2[5];
+            const T wa0 = W * la0, wa1 = W * la1, wa2 = W * la2;
+            mab[0] += wa0 * S.s1[0]; mab[1] += wa0 * S.s1[1]; mab[2] += wa0 * S.s1[2];
+            mab[3] += wa1 * S.s1[0]; mab[4] += wa1 * S.s1[1]; mab[5] += wa1 * S.s1[2];
+            mab[6] += wa2 * S.s1[0]; mab[7] += wa2 * S.s1[1]; mab[8] += wa2 * S.s1[2];
+            const T ws = W * S.s0;
+            maa_b[0] += ws * la0 * la0; maa_b[1] += ws * la1 * la1; maa_b[2] += ws * la2 * la2;
+            maa_b[3] += ws * la0 * la1; maa_b[4] += ws * la0 * la2; maa_b[5] += ws * la1 * la2;
+            cnt++;
+            qp += nq;
+            if (A.stats) hsum += nlg::record_hash(a, b, q - q0, R.kind, R.nv, R.ncap);
+        }
+        A.flag[e] = any ? 1 : 0;
+        for (int i = 0; i < 9; i++) blk[(int64_t)i * E + e] = mab[i];
+        for (int i = 0; i < 6; i++) blk[(int64_t)(9 + i) * E + e] = mbb[i];
+        for (int i = 0; i < 6; i++) maa[i] += (double)maa_b[i];
+    }
+    for (int off = 16; off; off >>= 1) {
+        for (int i = 0; i < 6; i++) maa[i] += __shfl_xor_sync(0xffffffffu, maa[i], off);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        qp += __shfl_xor_sync(0xffffffffu, qp, off);
+        hsum += __shfl_xor_sync(0xffffffffu, hsum, off);
+    }
+    if (lane == 0) {
+        for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] = maa[i];
+        A.qp_a[a] = qp;
+        A.cnt_a[a] = cnt;
+        if (A.stats) A.hash_a[a] = hsum;
+    }
+}
+
+}  // namespace nlq

@@ -1,0 +1,499 @@
+// solve.cu -- from D to the linear system and its solution.
+//
+//   A = D[Omega, Omega], B = D[Omega, Omega_I]        (Eq. (weakja); rules A-C of Sec. 7.2)
+//   F = G - B g,  G_j = int_Omega f phi_j             (Eq. (lfunc3) with u = g on Omega_I, Eq. (appr))
+//   A U = F by conjugate gradients (A is symmetric positive definite, Sec. 2; the paper
+//   names no solver): FP32 inner iterations (FP32 values, FP32 vectors) inside an FP64
+//   residual-refinement loop r = b - A x in FP64 until ||r|| <= rtol ||b||.
+// The matrix-vector products are HBM-bound: one warp per row, values and column
+// indices streamed once per product.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.cuh"
+
+namespace {
+
+__global__ void k_labels(int J, const uint8_t *lab, int64_t *inO, int64_t *inI)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < J) {
+        inO[j] = lab[j] != 0;
+        inI[j] = lab[j] == 0;
+    }
+}
+
+__global__ void k_inverse(int J, const uint8_t *lab, const int64_t *ro, const int64_t *ri, int32_t *omap, int32_t *imap)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    if (lab[j]) omap[ro[j]] = j; else imap[ri[j]] = j;
+}
+
+// pass 0: per Omega row, count entries of A (Omega columns) and B (Omega_I columns);
+// pass 1: write them renumbered, keeping the column order
+__global__ void k_split(int J, const int64_t *rp, const int32_t *col, const double *val, const uint8_t *lab,
+                        const int64_t *ro, const int64_t *ri, int64_t *cA, int64_t *cB, const int64_t *rpA,
+                        int32_t *colA, double *valA, const int64_t *rpB, int32_t *colB, double *valB, int pass)
+{
+    int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (j >= J || !lab[j]) return;
+    const int64_t r = ro[j];
+    int64_t na = 0, nb = 0;
+    const int64_t oA = pass ? rpA[r] : 0, oB = pass ? rpB[r] : 0;
+    for (int64_t base = rp[j]; base < rp[j + 1]; base += 32) {
+        int64_t s = base + lane;
+        bool valid = s < rp[j + 1];
+        int c = valid ? col[s] : 0;
+        bool inO = valid && lab[c];
+        bool inI = valid && !lab[c];
+        unsigned mO = __ballot_sync(0xffffffffu, inO), mI = __ballot_sync(0xffffffffu, inI);
+        unsigned below = (1u << lane) - 1u;
+        if (pass) {
+            if (inO) {
+                int64_t p = oA + na + __popc(mO & below);
+                colA[p] = (int32_t)ro[c];
+                valA[p] = val[s];
+            }
+            if (inI) {
+                int64_t p = oB + nb + __popc(mI & below);
+                colB[p] = (int32_t)ri[c];
+                valB[p] = val[s];
+            }
+        }
+        na += __popc(mO);
+        nb += __popc(mI);
+    }
+    if (!pass && lane == 0) {
+        cA[r] = na;
+        cB[r] = nb;
+    }
+}
+
+// G_j += |T|/12 (2 f_j + f_k + f_l) over elements of Omega (P1 mass matrix times nodal f)
+__global__ void k_load(int K, const int32_t *tri, const double *vx, const double *vy, const uint8_t *elem,
+                       const double *f, double *G)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K || !elem[t]) return;
+    int i0 = tri[3 * t], i1 = tri[3 * t + 1], i2 = tri[3 * t + 2];
+    double ar = 0.5 * fabs((vx[i1] - vx[i0]) * (vy[i2] - vy[i0]) - (vx[i2] - vx[i0]) * (vy[i1] - vy[i0]));
+    double f0 = f[i0], f1 = f[i1], f2 = f[i2];
+    atomicAdd(&G[i0], ar * (2.0 * f0 + f1 + f2) / 12.0);
+    atomicAdd(&G[i1], ar * (f0 + 2.0 * f1 + f2) / 12.0);
+    atomicAdd(&G[i2], ar * (f0 + f1 + 2.0 * f2) / 12.0);
+}
+
+__global__ void k_gather(int n, const int32_t *map, const double *src, double *dst)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[map[i]];
+}
+
+// F[r] = G[omap[r]] - (B gI)[r]; warp per row
+__global__ void k_rhs(int n, const int64_t *rp, const int32_t *col, const double *val, const double *gI,
+                      const int32_t *omap, const double *G, double *F)
+{
+    int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (r >= n) return;
+    double s = 0.0;
+    for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s += val[k] * gI[col[k]];
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) F[r] = G[omap[r]] - s;
+}
+
+__global__ void k_to_f32(int64_t n, const double *a, float *b)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// y = A x, warp per row (TV: value type, TX: vector type, accumulation in TV)
+template <typename TV, typename TX, typename TY>
+__global__ void k_spmv(int n, const int64_t *rp, const int32_t *col, const TV *val, const TX *x, TY *y)
+{
+    int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (r >= n) return;
+    TV s = 0;
+    for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s += val[k] * (TV)x[col[k]];
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) y[r] = (TY)s;
+}
+
+// r = b - A x (FP64) and ||r||^2, ||b||^2 accumulated into acc[0], acc[1]
+__global__ void k_residual(int n, const int64_t *rp, const int32_t *col, const double *val, const double *x,
+                           const double *b, double *r, double *acc)
+{
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double s = 0.0;
+    for (int64_t k = rp[row] + lane; k < rp[row + 1]; k += 32) s += val[k] * x[col[k]];
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        double v = b[row] - s;
+        r[row] = v;
+        atomicAdd(&acc[0], v * v);
+        atomicAdd(&acc[1], b[row] * b[row]);
+    }
+}
+
+// inner FP32 conjugate gradients on A d = z0 (z0 = r / ||r||)
+struct CgScal {
+    double rho, pq, zz;
+};
+
+__global__ void k_cg_init(int n, const double *r, double inv_norm, float *z, float *p, float *d, CgScal *sc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float v = (float)(r[i] * inv_norm);
+        z[i] = v;
+        p[i] = v;
+        d[i] = 0.0f;
+    }
+    if (i == 0) {
+        sc->rho = 1.0;
+        sc->pq = 0.0;
+        sc->zz = 0.0;
+    }
+}
+
+// q = A p and p.q
+__global__ void k_cg_spmv(int n, const int64_t *rp, const int32_t *col, const float *val, const float *p, float *q,
+                          CgScal *sc)
+{
+    int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (r >= n) return;
+    float s = 0.0f;
+    for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s += val[k] * p[col[k]];
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+        q[r] = s;
+        atomicAdd(&sc->pq, (double)s * (double)p[r]);
+    }
+}
+
+__global__ void k_cg_update(int n, const float *p, const float *q, float *d, float *z, CgScal *sc)
+{
+    __shared__ double part[8];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double pq = sc->pq;
+    float alpha = pq != 0.0 ? (float)(sc->rho / pq) : 0.0f;
+    double zz = 0.0;
+    if (i < n) {
+        d[i] += alpha * p[i];
+        float zn = z[i] - alpha * q[i];
+        z[i] = zn;
+        zz = (double)zn * zn;
+    }
+    for (int off = 16; off; off >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = zz;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += part[w];
+        atomicAdd(&sc->zz, t);
+    }
+}
+
+__global__ void k_cg_dir(int n, const float *z, float *p, const CgScal *sc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float beta = sc->rho != 0.0 ? (float)(sc->zz / sc->rho) : 0.0f;
+    if (i < n) p[i] = z[i] + beta * p[i];
+}
+
+__global__ void k_cg_shift(CgScal *sc)
+{
+    sc->rho = sc->zz;
+    sc->pq = 0.0;
+    sc->zz = 0.0;
+}
+
+__global__ void k_axpy_f32(int n, double s, const float *d, double *x)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += s * (double)d[i];
+}
+
+nl_plan *plan_of(nl_csr *m)
+{
+    if (!m->priv) m->priv = new (std::nothrow) nl_plan();
+    return (nl_plan *)m->priv;
+}
+
+nl_status ensure_f32(nl_ctx *ctx, nl_csr *A)
+{
+    nl_plan *P = plan_of(A);
+    if (!P) return nl_fail(ctx, NL_ENOMEM, "host allocation failed");
+    if (P->val32) return NL_OK;
+    nl_status s = nl_alloc(ctx, &P->val32, (size_t)A->nnz);
+    if (s != NL_OK) return s;
+    if (A->nnz) {
+        k_to_f32<<<(unsigned)((A->nnz + 255) / 256), 256, 0, ctx->stream>>>(A->nnz, A->val, P->val32); ++ctx->launches;
+    }
+    NL_CK(cudaGetLastError());
+    return NL_OK;
+}
+
+unsigned wgrid(int64_t rows) { return (unsigned)((rows * 32 + 255) / 256); }
+
+}  // namespace
+
+extern "C" {
+
+nl_status nl_extract(nl_ctx *ctx, const nl_csr *D, const nl_mesh *mesh, nl_csr *A, nl_csr *B)
+{
+    if (!ctx) return NL_EINVAL;
+    if (!D || !mesh || !A || !B || !mesh->node_in_omega) return nl_fail(ctx, NL_EINVAL, "null argument");
+    if (mesh->nv != D->n) return nl_fail(ctx, NL_EINVAL, "mesh and matrix sizes differ");
+    memset(A, 0, sizeof *A);
+    memset(B, 0, sizeof *B);
+    const int J = D->n;
+    nl_status s;
+    void *lab = nullptr;
+    bool own = false;
+    if ((s = nl_stage(ctx, mesh->node_in_omega, (size_t)J, &lab, &own)) != NL_OK) return s;
+    int64_t *inO, *inI, *ro, *ri, *cA, *cB;
+    NL_CK(cudaMallocAsync((void **)&inO, sizeof(int64_t) * (J + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&inI, sizeof(int64_t) * (J + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&ro, sizeof(int64_t) * (J + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&ri, sizeof(int64_t) * (J + 1), ctx->stream));
+    k_labels<<<(J + 255) / 256, 256, 0, ctx->stream>>>(J, (const uint8_t *)lab, inO, inI); ++ctx->launches;
+    if ((s = nl_scan_i64(ctx, inO, ro, J)) != NL_OK) return s;
+    if ((s = nl_scan_i64(ctx, inI, ri, J)) != NL_OK) return s;
+    int64_t nO = 0, nI = 0;
+    NL_CK(cudaMemcpyAsync(&nO, ro + J, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaMemcpyAsync(&nI, ri + J, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&cA, sizeof(int64_t) * (nO + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&cB, sizeof(int64_t) * (nO + 1), ctx->stream));
+    k_split<<<wgrid(J), 256, 0, ctx->stream>>>(J, D->row_ptr, D->col_idx, D->val, (const uint8_t *)lab, ro, ri, cA,
+                                               cB, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    if ((s = nl_alloc(ctx, &A->row_ptr, (size_t)nO + 1)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &B->row_ptr, (size_t)nO + 1)) != NL_OK) return s;
+    if ((s = nl_scan_i64(ctx, cA, A->row_ptr, nO)) != NL_OK) return s;
+    if ((s = nl_scan_i64(ctx, cB, B->row_ptr, nO)) != NL_OK) return s;
+    int64_t nzA = 0, nzB = 0;
+    NL_CK(cudaMemcpyAsync(&nzA, A->row_ptr + nO, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaMemcpyAsync(&nzB, B->row_ptr + nO, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    A->n = B->n = (int32_t)nO;
+    A->nnz = nzA;
+    B->nnz = nzB;
+    if ((s = nl_alloc(ctx, &A->col_idx, (size_t)nzA)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &A->val, (size_t)nzA)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &B->col_idx, (size_t)nzB)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &B->val, (size_t)nzB)) != NL_OK) return s;
+    k_split<<<wgrid(J), 256, 0, ctx->stream>>>(J, D->row_ptr, D->col_idx, D->val, (const uint8_t *)lab, ro, ri,
+                                               nullptr, nullptr, A->row_ptr, A->col_idx, A->val, B->row_ptr,
+                                               B->col_idx, B->val, 1); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    nl_plan *PB = plan_of(B);
+    if (!PB) return nl_fail(ctx, NL_ENOMEM, "host allocation failed");
+    PB->ncols = (int32_t)nI;
+    NL_CK(cudaFreeAsync(inO, ctx->stream));
+    NL_CK(cudaFreeAsync(inI, ctx->stream));
+    NL_CK(cudaFreeAsync(ro, ctx->stream));
+    NL_CK(cudaFreeAsync(ri, ctx->stream));
+    NL_CK(cudaFreeAsync(cA, ctx->stream));
+    NL_CK(cudaFreeAsync(cB, ctx->stream));
+    if (own) NL_CK(cudaFreeAsync(lab, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    return NL_OK;
+}
+
+nl_status nl_rhs(nl_ctx *ctx, const nl_csr *B, const nl_mesh *mesh, const double *f_nodal, const double *g_nodal,
+                 double *F)
+{
+    if (!ctx) return NL_EINVAL;
+    if (!B || !mesh || !f_nodal || !g_nodal || !F || !mesh->node_in_omega || !mesh->elem_in_omega)
+        return nl_fail(ctx, NL_EINVAL, "null argument (nl_rhs needs both node and element labels)");
+    const int J = mesh->nv, K = mesh->nt;
+    nl_status s;
+    void *lab, *elem, *vx, *vy, *tri, *f, *g;
+    bool o1, o2, o3, o4, o5, o6, o7;
+    if ((s = nl_stage(ctx, mesh->node_in_omega, (size_t)J, &lab, &o1)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, mesh->elem_in_omega, (size_t)K, &elem, &o2)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, mesh->vx, sizeof(double) * J, &vx, &o3)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, mesh->vy, sizeof(double) * J, &vy, &o4)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, mesh->tri, sizeof(int32_t) * 3 * K, &tri, &o5)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, f_nodal, sizeof(double) * J, &f, &o6)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, g_nodal, sizeof(double) * J, &g, &o7)) != NL_OK) return s;
+    int64_t *inO, *inI, *ro, *ri;
+    int32_t *omap, *imap;
+    double *G, *gI, *Fd;
+    NL_CK(cudaMallocAsync((void **)&inO, sizeof(int64_t) * (J + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&inI, sizeof(int64_t) * (J + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&ro, sizeof(int64_t) * (J + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&ri, sizeof(int64_t) * (J + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&omap, sizeof(int32_t) * (J + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&imap, sizeof(int32_t) * (J + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&G, sizeof(double) * J, ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&gI, sizeof(double) * (J + 1), ctx->stream));
+    NL_CK(cudaMemsetAsync(G, 0, sizeof(double) * J, ctx->stream));
+    k_labels<<<(J + 255) / 256, 256, 0, ctx->stream>>>(J, (const uint8_t *)lab, inO, inI); ++ctx->launches;
+    if ((s = nl_scan_i64(ctx, inO, ro, J)) != NL_OK) return s;
+    if ((s = nl_scan_i64(ctx, inI, ri, J)) != NL_OK) return s;
+    k_inverse<<<(J + 255) / 256, 256, 0, ctx->stream>>>(J, (const uint8_t *)lab, ro, ri, omap, imap); ++ctx->launches;
+    k_load<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, (const int32_t *)tri, (const double *)vx, (const double *)vy,
+                                                     (const uint8_t *)elem, (const double *)f, G); ++ctx->launches;
+    int64_t nO = 0, nI = 0;
+    NL_CK(cudaMemcpyAsync(&nO, ro + J, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaMemcpyAsync(&nI, ri + J, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    if (nO != B->n) return nl_fail(ctx, NL_EINVAL, "B does not match the mesh labels");
+    k_gather<<<(unsigned)((nI + 255) / 256 + 1), 256, 0, ctx->stream>>>((int)nI, imap, (const double *)g, gI); ++ctx->launches;
+    bool dev_out = nl_is_device_ptr(F);
+    if (dev_out) Fd = F;
+    else NL_CK(cudaMallocAsync((void **)&Fd, sizeof(double) * (nO + 1), ctx->stream));
+    k_rhs<<<wgrid(nO), 256, 0, ctx->stream>>>((int)nO, B->row_ptr, B->col_idx, B->val, gI, omap, G, Fd); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    if (!dev_out) {
+        NL_CK(cudaMemcpyAsync(F, Fd, sizeof(double) * nO, cudaMemcpyDeviceToHost, ctx->stream));
+        NL_CK(cudaFreeAsync(Fd, ctx->stream));
+    }
+    void *tmp[] = {inO, inI, ro, ri, omap, imap, G, gI};
+    for (void *p : tmp) NL_CK(cudaFreeAsync(p, ctx->stream));
+    void *st[] = {lab, elem, vx, vy, tri, f, g};
+    bool own[] = {o1, o2, o3, o4, o5, o6, o7};
+    for (int i = 0; i < 7; i++)
+        if (own[i]) NL_CK(cudaFreeAsync(st[i], ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    return NL_OK;
+}
+
+nl_status nl_matvec(nl_ctx *ctx, const nl_csr *Ac, const double *x, double *y, int32_t prec)
+{
+    if (!ctx) return NL_EINVAL;
+    if (!Ac || !x || !y) return nl_fail(ctx, NL_EINVAL, "null argument");
+    nl_csr *A = const_cast<nl_csr *>(Ac);
+    const int n = A->n;
+    int ncols = n;
+    if (A->priv && ((nl_plan *)A->priv)->ncols) ncols = ((nl_plan *)A->priv)->ncols;
+    nl_status s;
+    void *xd;
+    bool ox;
+    if ((s = nl_stage(ctx, x, sizeof(double) * ncols, &xd, &ox)) != NL_OK) return s;
+    bool dev_out = nl_is_device_ptr(y);
+    double *yd = y;
+    if (!dev_out) NL_CK(cudaMallocAsync((void **)&yd, sizeof(double) * (n + 1), ctx->stream));
+    if (prec == NL_PREC_FP64) {
+        k_spmv<double, double, double><<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, A->val,
+                                                                           (const double *)xd, yd); ++ctx->launches;
+    } else {
+        if ((s = ensure_f32(ctx, A)) != NL_OK) return s;
+        k_spmv<float, double, double><<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx,
+                                                                          ((nl_plan *)A->priv)->val32,
+                                                                          (const double *)xd, yd); ++ctx->launches;
+    }
+    NL_CK(cudaGetLastError());
+    if (!dev_out) {
+        NL_CK(cudaMemcpyAsync(y, yd, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        NL_CK(cudaFreeAsync(yd, ctx->stream));
+    }
+    if (ox) NL_CK(cudaFreeAsync(xd, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    return NL_OK;
+}
+
+nl_status nl_cg(nl_ctx *ctx, const nl_csr *Ac, const double *b, double *x, double rtol, int32_t max_it,
+                int32_t *iters, double *relres)
+{
+    if (!ctx) return NL_EINVAL;
+    if (!Ac || !b || !x) return nl_fail(ctx, NL_EINVAL, "null argument");
+    if (!(rtol > 0.0) || max_it < 1) return nl_fail(ctx, NL_EINVAL, "need rtol > 0 and max_it >= 1");
+    nl_csr *A = const_cast<nl_csr *>(Ac);
+    const int n = A->n;
+    nl_status s;
+    if ((s = ensure_f32(ctx, A)) != NL_OK) return s;
+    const float *v32 = ((nl_plan *)A->priv)->val32;
+    void *bd;
+    bool ob;
+    if ((s = nl_stage(ctx, b, sizeof(double) * n, &bd, &ob)) != NL_OK) return s;
+    bool dev_x = nl_is_device_ptr(x);
+    double *xd = x;
+    if (!dev_x) {
+        NL_CK(cudaMallocAsync((void **)&xd, sizeof(double) * (n + 1), ctx->stream));
+        NL_CK(cudaMemcpyAsync(xd, x, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    double *r, *acc;
+    float *z, *p, *q, *d;
+    CgScal *sc;
+    NL_CK(cudaMallocAsync((void **)&r, sizeof(double) * (n + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&acc, sizeof(double) * 2, ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&z, sizeof(float) * (n + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&p, sizeof(float) * (n + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&q, sizeof(float) * (n + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&d, sizeof(float) * (n + 1), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&sc, sizeof(CgScal), ctx->stream));
+    const unsigned eg = (unsigned)((n + 255) / 256);
+    int total = 0;
+    double rel = INFINITY;
+    nl_status out = NL_OK;
+    const int kCheck = 8;          // inner iterations between host convergence checks
+    const double kInnerTol = 1e-5; // inner relative reduction per refinement step
+    for (int outer = 0; outer < 64; outer++) {
+        NL_CK(cudaMemsetAsync(acc, 0, sizeof(double) * 2, ctx->stream));
+        k_residual<<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, A->val, xd, (const double *)bd, r,
+                                                      acc); ++ctx->launches;
+        double h[2];
+        NL_CK(cudaMemcpyAsync(h, acc, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+        NL_CK(cudaStreamSynchronize(ctx->stream));
+        double rn = sqrt(h[0]), bn = sqrt(h[1]);
+        rel = bn > 0.0 ? rn / bn : rn;
+        if (rel <= rtol || rn == 0.0) break;
+        if (total >= max_it) {
+            out = nl_fail(ctx, NL_ENOCONV, "CG did not reach the tolerance within max_it iterations");
+            break;
+        }
+        k_cg_init<<<eg, 256, 0, ctx->stream>>>(n, r, 1.0 / rn, z, p, d, sc); ++ctx->launches;
+        while (total < max_it) {
+            const int chunk = (max_it - total) < kCheck ? (max_it - total) : kCheck;
+            for (int c = 0; c < chunk; c++) {
+                k_cg_spmv<<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, v32, p, q, sc); ++ctx->launches;
+                k_cg_update<<<eg, 256, 0, ctx->stream>>>(n, p, q, d, z, sc); ++ctx->launches;
+                k_cg_dir<<<eg, 256, 0, ctx->stream>>>(n, z, p, sc); ++ctx->launches;
+                k_cg_shift<<<1, 1, 0, ctx->stream>>>(sc); ++ctx->launches;
+            }
+            NL_CK(cudaGetLastError());
+            total += chunk;
+            CgScal hs;
+            NL_CK(cudaMemcpyAsync(&hs, sc, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
+            NL_CK(cudaStreamSynchronize(ctx->stream));
+            if (!(sqrt(hs.rho) > kInnerTol)) break;   // converged, or breakdown (NaN)
+        }
+        k_axpy_f32<<<eg, 256, 0, ctx->stream>>>(n, rn, d, xd); ++ctx->launches;
+        NL_CK(cudaGetLastError());
+    }
+    if (!dev_x) NL_CK(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    void *tmp[] = {r, acc, z, p, q, d, sc};
+    for (void *t : tmp) NL_CK(cudaFreeAsync(t, ctx->stream));
+    if (!dev_x) NL_CK(cudaFreeAsync(xd, ctx->stream));
+    if (ob) NL_CK(cudaFreeAsync(bd, ctx->stream));
+    NL_CK(cudaStreamSynchronize(ctx->stream));
+    if (iters) *iters = total;
+    if (relres) *relres = rel;
+    return out;
+}
+
+nl_status nl_assemble_batch(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const nl_config *cfgs, nl_csr *outs)
+{
+    if (!ctx) return NL_EINVAL;
+    if (n < 0 || (n > 0 && (!meshes || !cfgs || !outs))) return nl_fail(ctx, NL_EINVAL, "bad batch arguments");
+    for (int i = 0; i < n; i++) {
+        nl_status s = nl_assemble(ctx, &meshes[i], &cfgs[i], &outs[i]);
+        if (s != NL_OK) {
+            for (int k = 0; k < i; k++) nl_csr_free(ctx, &outs[k]);
+            return s;
+        }
+    }
+    return NL_OK;
+}
+
+}  // extern "C"

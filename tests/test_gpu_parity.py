@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar (written here, derived in the design doc):
+  * CSR pattern (row pointers, column indices) and the interaction set
+    (per-outer-triangle count, qp-pair count and record hash) are bit-exact;
+  * values: |D_gpu - D_oracle| <= 1e-12 max|D| for the FP64 path and
+    <= 1e-6 max|D| for the FP32-compensated path.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2005_10775_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32c": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def nl():
+    from paper_2005_10775_gb300 import nlfem
+    return nlfem
+
+
+@pytest.fixture(scope="module")
+def ctx(nl):
+    c = nl.nl_create(0)
+    yield c
+    nl.nl_destroy(c)
+
+
+def oracle_cfg(p, **over):
+    kw = dict(delta=p.delta, ball=p.ball, outer=p.outer, inner=p.inner, kernel=p.kernel, kernel_c=p.kernel_c,
+              ngon_off=p.ngon_off, cap_m=p.cap_m)
+    kw.update(over)
+    return kw
+
+
+def gpu_assemble(nl, ctx, p, prec, **over):
+    keep = nl._Keep()
+    mesh = nl.make_mesh(p.mesh, keep)
+    cfg = nl.config_of(p, keep, prec=prec, **over)
+    m = nl.nl_assemble(ctx, mesh, cfg)
+    try:
+        D = nl.to_scipy(ctx, m)
+        stats = (m.n_pairs, m.n_qp_pairs, m.n_inter)
+    finally:
+        nl.nl_csr_free(ctx, m)
+    return D, stats
+
+
+def gpu_interactions(nl, ctx, p, **over):
+    keep = nl._Keep()
+    mesh = nl.make_mesh(p.mesh, keep)
+    cfg = nl.config_of(p, keep, **over)
+    return nl.nl_interactions(ctx, mesh, cfg)
+
+
+def compare(Dg, Do, prec):
+    Do = Do.tocsr()
+    Do.sort_indices()
+    np.testing.assert_array_equal(Dg.indptr, Do.indptr)
+    np.testing.assert_array_equal(Dg.indices, Do.indices)
+    scale = np.abs(Do.data).max()
+    err = np.abs(Dg.data - Do.data).max() / scale
+    assert err <= TOL[prec], err
+    return err
+
+
+def small_problem(ball, n=24, jitter=0.2, kernel="const", **kw):
+    d = 0.1
+    m = I.split_square_mesh(-0.1, 1.1, n, jitter=jitter, seed=1077502)
+    c = I.const_kernel_c(d) if kernel == "const" else I.inv_dist_kernel_c(d)
+    p = I.Problem(f"{ball}_{n}", m, d, kernel, c, ball, "dunavant7", "dunavant7")
+    if ball == "ngon":
+        p = p.with_(ngon_n=32, ngon_off=I.ngon_offsets(32, d))
+    return p.with_(**kw) if kw else p
+
+
+CASES = [
+    ("barycenter", {}), ("nocaps", {}), ("approxcaps", {}), ("approxcaps", {"cap_m": 4}),
+    ("exactcaps", {}), ("ngon", {}), ("overlap", {}),
+]
+
+
+@pytest.mark.parametrize("ball,kw", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_parity_small(nl, ctx, ball, kw, prec):
+    p = small_problem(ball, **kw)
+    out = O.assemble(p.mesh, oracle_cfg(p), want_hash=True)
+    Dg, stats = gpu_assemble(nl, ctx, p, prec)
+    compare(Dg, O.to_csr(out), prec)
+    assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
+    h, c, q = gpu_interactions(nl, ctx, p)
+    np.testing.assert_array_equal(c, out["count_a"])
+    np.testing.assert_array_equal(q, out["qp_a"])
+    np.testing.assert_array_equal(h, out["hash_a"])
+
+
+def test_parity_barycenter_32_full_size(nl, ctx):
+    # barycenter ball, 32x32 structured grid (2048 triangles), 7-point rules, FP64
+    p = I.problem("barycenter_32")
+    out = O.assemble(p.mesh, oracle_cfg(p), want_hash=True)
+    Dg, stats = gpu_assemble(nl, ctx, p, "fp64")
+    compare(Dg, O.to_csr(out), "fp64")
+    assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
+    h, c, q = gpu_interactions(nl, ctx, p)
+    np.testing.assert_array_equal(h, out["hash_a"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_parity_inv_dist_kernel(nl, ctx, prec):
+    p = small_problem("ngon", n=24, kernel="inv_dist")
+    out = O.assemble(p.mesh, oracle_cfg(p, duffy_n=4), want_hash=True)
+    Dg, stats = gpu_assemble(nl, ctx, p, prec, duffy_n=4)
+    compare(Dg, O.to_csr(out), prec)
+    assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
+
+
+@pytest.mark.parametrize("ball", ["nocaps", "exactcaps"])
+def test_parity_paper_protocol(nl, ctx, ball):
+    # rule switch of Sec. 8: 4-point rule for near pairs, 7-point vertex rule otherwise; 3-point inner
+    d = 0.1
+    m = I.paper_grid(0.05)
+    p = I.Problem("paper", m, d, "const", I.const_kernel_c(d), ball, "switch47", "gauss3")
+    out = O.assemble(m, oracle_cfg(p, cap_printed=1), want_hash=True)
+    Dg, stats = gpu_assemble(nl, ctx, p, "fp64", cap_printed=1)
+    compare(Dg, O.to_csr(out), "fp64")
+    h, c, q = gpu_interactions(nl, ctx, p, cap_printed=1)
+    np.testing.assert_array_equal(h, out["hash_a"])
+
+
+def test_ragged_and_tiny(nl, ctx):
+    # 7x7 cells -> 98 triangles (not a multiple of the warps per block), and a single triangle
+    p = small_problem("ngon", n=7).with_(delta=0.4, ngon_off=I.ngon_offsets(32, 0.4))
+    out = O.assemble(p.mesh, oracle_cfg(p))
+    Dg, _ = gpu_assemble(nl, ctx, p, "fp64")
+    compare(Dg, O.to_csr(out), "fp64")
+    one = I.Mesh(vx=np.array([0.0, 1.0, 0.0]), vy=np.array([0.0, 0.0, 1.0]), tri=np.array([[0, 1, 2]], np.int32),
+                 node_in_omega=np.zeros(3, np.uint8), elem_in_omega=np.zeros(1, np.uint8), h=1.0, lo=0, hi=1, n=1)
+    q = p.with_(mesh=one, delta=2.0, ball="nocaps", ngon_off=None, ngon_n=0)
+    out = O.assemble(one, oracle_cfg(q))
+    Dg, _ = gpu_assemble(nl, ctx, q, "fp64")
+    compare(Dg, O.to_csr(out), "fp64")
+
+
+def test_device_pointer_inputs(nl, ctx):
+    torch = pytest.importorskip("torch")
+    p = small_problem("approxcaps", n=24)
+    keep = nl._Keep()
+    m = p.mesh
+    dev = type("M", (), dict(vx=torch.tensor(m.vx, device="cuda"), vy=torch.tensor(m.vy, device="cuda"),
+                             tri=torch.tensor(m.tri, device="cuda")))
+    mesh = nl.make_mesh(dev, keep)
+    cfg = nl.config_of(p, keep, prec="fp64")
+    out = nl.nl_assemble(ctx, mesh, cfg)
+    try:
+        Dg = nl.to_scipy(ctx, out)
+    finally:
+        nl.nl_csr_free(ctx, out)
+    compare(Dg, O.to_csr(O.assemble(m, oracle_cfg(p))), "fp64")
+
+
+def test_numeric_reassembly_is_repeatable(nl, ctx):
+    p = small_problem("ngon", n=24)
+    keep = nl._Keep()
+    mesh = nl.make_mesh(p.mesh, keep)
+    cfg = nl.config_of(p, keep, prec="fp32c")
+    m = nl.nl_assemble(ctx, mesh, cfg)
+    try:
+        D1 = nl.to_scipy(ctx, m)
+        nl.nl_assemble_numeric(ctx, m)
+        D2 = nl.to_scipy(ctx, m)
+    finally:
+        nl.nl_csr_free(ctx, m)
+    np.testing.assert_array_equal(D1.indices, D2.indices)
+    assert np.abs(D1.data - D2.data).max() <= 1e-14 * np.abs(D1.data).max()
+
+
+def test_errors(nl, ctx):
+    p = small_problem("nocaps", n=24)
+    # delta below the largest triangle diameter
+    with pytest.raises(nl.NlError) as e:
+        gpu_assemble(nl, ctx, p.with_(delta=0.05), "fp64")
+    assert e.value.status == nl.NL_EGEOM
+    # clockwise triangle
+    bad = I.Mesh(vx=p.mesh.vx, vy=p.mesh.vy, tri=p.mesh.tri[:, ::-1].copy(), node_in_omega=p.mesh.node_in_omega,
+                 elem_in_omega=p.mesh.elem_in_omega, h=p.mesh.h, lo=0, hi=1, n=24)
+    with pytest.raises(nl.NlError) as e:
+        gpu_assemble(nl, ctx, p.with_(mesh=bad), "fp64")
+    assert e.value.status == nl.NL_EGEOM
+    # bad enum
+    keep = nl._Keep()
+    cfg = nl.config_of(p, keep)
+    cfg.ball = 42
+    with pytest.raises(nl.NlError) as e:
+        nl.nl_assemble(ctx, nl.make_mesh(p.mesh, keep), cfg)
+    assert e.value.status == nl.NL_EINVAL

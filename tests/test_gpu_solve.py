@@ -1,0 +1,98 @@
+"""Right-hand side and solve on the GPU (through the C ABI) against the oracle's
+numpy/scipy steps: A = D[Omega, Omega], B = D[Omega, Omega_I], F = G - B g,
+matrix-vector products and the mixed-precision CG solve."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2005_10775_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nl():
+    from paper_2005_10775_gb300 import nlfem
+    return nlfem
+
+
+@pytest.fixture(scope="module")
+def ctx(nl):
+    c = nl.nl_create(0)
+    yield c
+    nl.nl_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def system(nl, ctx):
+    d = 0.1
+    m = I.split_square_mesh(-0.1, 1.1, 36, jitter=0.2, seed=1077505)
+    p = I.Problem("solve", m, d, "const", I.const_kernel_c(d), "ngon", "dunavant7", "dunavant7", ngon_n=32,
+                  ngon_off=I.ngon_offsets(32, d))
+    keep = nl._Keep()
+    mesh = nl.make_mesh(m, keep)
+    cfg = nl.config_of(p, keep, prec="fp64")
+    D = nl.nl_assemble(ctx, mesh, cfg)
+    A, B = nl.nl_extract(ctx, D, mesh)
+    out = O.assemble(m, dict(delta=d, ball="ngon", outer="dunavant7", inner="dunavant7",
+                             kernel_c=p.kernel_c, ngon_off=p.ngon_off))
+    yield dict(m=m, mesh=mesh, keep=keep, D=D, A=A, B=B, Do=O.to_csr(out))
+    for x in (D, A, B):
+        nl.nl_csr_free(ctx, x)
+
+
+def test_extract(nl, ctx, system):
+    m = system["m"]
+    om = m.node_in_omega.astype(bool)
+    Ao = system["Do"][om][:, om].tocsr()
+    Bo = system["Do"][om][:, ~om].tocsr()
+    Ag = nl.to_scipy(ctx, system["A"])
+    Bg = nl.to_scipy(ctx, system["B"], ncols=int((~om).sum()))
+    for G, R in ((Ag, Ao), (Bg, Bo)):
+        R.sort_indices()
+        np.testing.assert_array_equal(G.indptr, R.indptr)
+        np.testing.assert_array_equal(G.indices, R.indices)
+        assert np.abs(G.data - R.data).max() <= 1e-12 * np.abs(system["Do"].data).max()
+
+
+def test_rhs(nl, ctx, system):
+    m = system["m"]
+    u = I.manufactured_u(m.vx, m.vy)
+    f = I.manufactured_f(m.vx, m.vy)
+    F = nl.nl_rhs(ctx, system["B"], system["mesh"], f, u)
+    Fo = O.rhs(system["Do"], m, f, u)
+    np.testing.assert_allclose(F, Fo, rtol=0, atol=1e-12 * np.abs(Fo).max())
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32c", 2e-6)])
+def test_matvec(nl, ctx, system, prec, tol):
+    m = system["m"]
+    om = m.node_in_omega.astype(bool)
+    Ao = system["Do"][om][:, om]
+    x = np.random.default_rng(3).standard_normal(Ao.shape[0])
+    y = nl.nl_matvec(ctx, system["A"], x, prec=prec)
+    ref = Ao @ x
+    assert np.abs(y - ref).max() <= tol * np.abs(Ao).sum(axis=1).max() * np.abs(x).max()
+
+
+def test_cg_solve_matches_direct(nl, ctx, system):
+    m = system["m"]
+    u = I.manufactured_u(m.vx, m.vy)
+    f = I.manufactured_f(m.vx, m.vy)
+    om = m.node_in_omega.astype(bool)
+    F = nl.nl_rhs(ctx, system["B"], system["mesh"], f, u)
+    x = np.zeros(F.shape[0])
+    it, rel = nl.nl_cg(ctx, system["A"], F, x, rtol=1e-10, max_it=5000)
+    assert rel <= 1e-10 and it > 0
+    Uo = O.solve(system["Do"], m, f, u)[om]
+    assert np.abs(x - Uo).max() <= 1e-8 * np.abs(Uo).max()
+    # the discrete solution approximates u = x1^2 x2 + x2^2 (Sec. 8)
+    assert np.abs(x - u[om]).max() < 5e-2
+
+
+def test_cg_reports_nonconvergence(nl, ctx, system):
+    F = np.ones(system["A"].n)
+    x = np.zeros_like(F)
+    with pytest.raises(nl.NlError) as e:
+        nl.nl_cg(ctx, system["A"], F, x, rtol=1e-14, max_it=3)
+    assert e.value.status == nl.NL_ENOCONV
