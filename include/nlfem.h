@@ -180,6 +180,22 @@ void nl_csr_free(nl_ctx *ctx, nl_csr *m);
    [1] pair geometry + quadrature, [2] symbolic pattern, [3] numeric scatter. */
 nl_status nl_last_timings(nl_ctx *ctx, double *ms4);
 
+/* nl_cg for callers that cannot allocate device memory: a framework that has given all
+   device memory to its own caching allocator or a reserved arena, or a latency-critical
+   loop that cannot take an allocation's synchronisation on every call.  The paper has no
+   counterpart; this is a deployment variant of nl_cg.  Same arguments, results and
+   errors as nl_cg, except:
+     - A (row_ptr, col_idx, val), b and x must be device pointers (else NL_EINVAL);
+     - A->n must not exceed 262144 (else NL_EUNSUPPORTED): the work vectors live in one
+       fixed file-scope device array of about 6 MB that every GPU loading the library
+       keeps until the process exits, and no cudaMalloc or cudaFree is called;
+     - the first call on a device looks up that array's address (cudaGetSymbolAddress)
+       and caches it: make that first call before any stream capture;
+     - all calls share the array; calls that overlap on the GPU race and must be
+       serialised by the caller.  Each call clears what must start at zero itself. */
+nl_status nl_cg_noalloc(nl_ctx *ctx, const nl_csr *A, const double *b, double *x, double rtol, int32_t max_it,
+                        int32_t *iters, double *relres);
+
 /* Number of CUDA kernels this context has launched so far (all entry points). */
 int64_t nl_launch_count(nl_ctx *ctx);
 

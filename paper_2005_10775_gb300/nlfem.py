@@ -76,6 +76,8 @@ def _load():
         "nl_csr_free": (None, [ctypes.c_void_p, P(nl_csr)]),
         "nl_last_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
         "nl_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+        "nl_cg_noalloc": (ctypes.c_int, [ctypes.c_void_p, P(nl_csr), ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_double, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -219,6 +221,16 @@ def nl_cg(ctx, A: nl_csr, b, x, rtol=1e-10, max_it=10000):
     rr = ctypes.c_double()
     _check(ctx, _L.nl_cg(ctx, ctypes.byref(A), _ptr(b, keep, np.float64), _ptr(x, keep), float(rtol),
                          int(max_it), ctypes.byref(it), ctypes.byref(rr)))
+    return int(it.value), float(rr.value)
+
+
+def nl_cg_noalloc(ctx, A: nl_csr, b, x, rtol=1e-10, max_it=10000):
+    """b and x must be CUDA tensors (device memory); x is updated in place."""
+    keep = _Keep()
+    it = ctypes.c_int32()
+    rr = ctypes.c_double()
+    _check(ctx, _L.nl_cg_noalloc(ctx, ctypes.byref(A), _ptr(b, keep), _ptr(x, keep), float(rtol), int(max_it),
+                                 ctypes.byref(it), ctypes.byref(rr)))
     return int(it.value), float(rr.value)
 
 
