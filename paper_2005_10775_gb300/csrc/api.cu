@@ -202,6 +202,40 @@ nl_status fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
     while ((1 << level) < (c.cap_m > 0 ? c.cap_m : 1)) level++;
     A.geo.cap_level = level;
     A.geo.cap_printed = c.cap_printed;
+    // FP32 certification data (see geometry.cuh): margin tau = 1e-5 delta
+    const double tau = 1e-5 * c.delta;
+    double rin = c.delta, rout = c.delta;
+    if (c.ball == NL_BALL_NGON) {
+        const int N = c.ngon_n;
+        const double *o = P->ngon_host.data();
+        rin = INFINITY;
+        rout = 0.0;
+        for (int k = 0; k < N; k++) {
+            const int k1 = (k + 1) % N;
+            const double ex = o[2 * k1] - o[2 * k], ey = o[2 * k1 + 1] - o[2 * k + 1];
+            const double el = sqrt(ex * ex + ey * ey);
+            // distance from the centre to the line of edge k (polygon ccw around the centre)
+            const double dk = (o[2 * k] * o[2 * k1 + 1] - o[2 * k + 1] * o[2 * k1]) / (el > 0.0 ? el : 1.0);
+            rin = fmin(rin, dk);
+            rout = fmax(rout, sqrt(o[2 * k] * o[2 * k] + o[2 * k + 1] * o[2 * k + 1]));
+            A.geo.of[k][0] = (float)o[2 * k];
+            A.geo.of[k][1] = (float)o[2 * k + 1];
+            A.geo.ef[k][0] = (float)ex;
+            A.geo.ef[k][1] = (float)ey;
+            A.geo.mk[k] = (float)(el * tau);
+        }
+    }
+    A.geo.tau = (float)tau;
+    // FP32 local coordinates v - x are rounded differences of magnitude <= delta + 4 r_max
+    A.geo.err0 = (float)(4.0 * 5.9604644775390625e-8 * (c.delta + 4.0 * P->rmax));
+    A.geo.rin_m2 = rin - tau > 0.0 ? (float)((rin - tau) * (rin - tau)) : -1.0f;
+    A.geo.rout_p2 = (float)((rout + tau) * (rout + tau));
+    A.geo.b_in2 = (float)((c.delta - tau) * (c.delta - tau));
+    A.geo.b_out2 = (float)((c.delta + tau) * (c.delta + tau));
+    for (int r = 0; r < A.inner.n; r++) {
+        for (int i = 0; i < 3; i++) A.fin_l[r][i] = (float)A.inner.l[r][i];
+        A.fin_w[r] = (float)A.inner.w[r];
+    }
     A.flag = P->flag;
     A.blk = P->blk;
     A.maa = P->maa;

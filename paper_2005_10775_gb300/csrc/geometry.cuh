@@ -31,6 +31,10 @@ struct D2 {
     double x, y;
 };
 
+struct F2 {
+    float x, y;
+};
+
 enum { KIND_NONE = 0, KIND_WHOLE = 1, KIND_PARTIAL = 2 };
 
 __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
@@ -50,6 +54,15 @@ struct GeoParams {
     double delta, d2;
     const double *ngon;   // [2 n] offsets (device)
     int ngon_n, cap_level, cap_printed;
+    // FP32 certification data
+    float tau;            // decision margin (1e-5 delta)
+    float rin_m2;         // (r_in - tau)^2: r_in = delta (disc balls) or the polygon's inradius
+    float rout_p2;        // (delta + tau)^2
+    float b_in2, b_out2;  // barycenter ball: (delta - tau)^2, (delta + tau)^2
+    float of[64][2];      // polygon offsets o_k (FP32)
+    float ef[64][2];      // edges o_{k+1} - o_k (FP32)
+    float mk[64];         // |e_k| tau: margin of the FP32 orientation test of pass k
+    float err0;           // bound on |dl - (v - x)| of the FP32 local coordinates
 };
 
 __device__ __forceinline__ bool in_ball(D2 p, D2 x, double d2)
@@ -170,33 +183,41 @@ __device__ __forceinline__ double orient(D2 a, D2 b, D2 p)
     return sub(mul(sub(b.x, a.x), sub(p.y, a.y)), mul(sub(b.y, a.y), sub(p.x, a.x)));
 }
 
-// Sutherland-Hodgman clip of the ccw triangle V by the regular polygon x + off_k
-__device__ __forceinline__ int clip_ngon(const D2 V[3], D2 x, const GeoParams &g, D2 *out, int *overflow)
+// Sutherland-Hodgman clip of the ccw triangle V by the regular polygon x + off_k.
+// dl: FP32 coordinates of V relative to x; a pass whose every vertex is certified
+// (FP32, margin mk[k]) to be on the kept side is the identity and is skipped.
+__device__ __forceinline__ int clip_ngon(const D2 V[3], const F2 dl[3], D2 x, const GeoParams &g, D2 *out,
+                                         int *overflow)
 {
     D2 A[NL_MAXV], B[NL_MAXV];
+    F2 Af[NL_MAXV];
     int n = 3;
     A[0] = V[0]; A[1] = V[1]; A[2] = V[2];
+    Af[0] = dl[0]; Af[1] = dl[1]; Af[2] = dl[2];
     const int N = g.ngon_n;
-    D2 P0;
-    P0.x = add(x.x, g.ngon[0]);
-    P0.y = add(x.y, g.ngon[1]);
-    const D2 first = P0;
     for (int k = 0; k < N && n > 0; k++) {
-        D2 P1;
-        if (k + 1 < N) {
-            P1.x = add(x.x, g.ngon[2 * (k + 1)]);
-            P1.y = add(x.y, g.ngon[2 * (k + 1) + 1]);
-        } else {
-            P1 = first;
+        // certified identity pass: skip without FP64 work
+        bool sure_in = true;
+        {
+            const float ox = g.of[k][0], oy = g.of[k][1], ex = g.ef[k][0], ey = g.ef[k][1], m = g.mk[k];
+            for (int i = 0; i < n && sure_in; i++)
+                sure_in = (ex * (Af[i].y - oy) - ey * (Af[i].x - ox)) > m;
         }
-        // identity pass (every vertex on the kept side) is skipped: exact
+        if (sure_in) continue;
+        const int k1 = (k + 1 < N) ? k + 1 : 0;
+        D2 P0, P1;
+        P0.x = add(x.x, g.ngon[2 * k]);
+        P0.y = add(x.y, g.ngon[2 * k + 1]);
+        P1.x = add(x.x, g.ngon[2 * k1]);
+        P1.y = add(x.y, g.ngon[2 * k1 + 1]);
         double o[NL_MAXV];
         bool all_in = true;
-        for (int i = 0; i < n; i++) {
-            o[i] = orient(P0, P1, A[i]);
-            all_in = all_in && (o[i] >= 0.0);
-        }
-        if (!all_in) {
+        if (!sure_in)
+            for (int i = 0; i < n; i++) {
+                o[i] = orient(P0, P1, A[i]);
+                all_in = all_in && (o[i] >= 0.0);
+            }
+        if (!sure_in && !all_in) {
             int m = 0;
             for (int i = 0; i < n; i++) {
                 if (m + 2 > NL_MAXV) {
@@ -222,9 +243,12 @@ __device__ __forceinline__ int clip_ngon(const D2 V[3], D2 x, const GeoParams &g
                 }
             }
             n = m;
-            for (int i = 0; i < n; i++) A[i] = B[i];
+            for (int i = 0; i < n; i++) {
+                A[i] = B[i];
+                Af[i].x = (float)(B[i].x - x.x);
+                Af[i].y = (float)(B[i].y - x.y);
+            }
         }
-        P0 = P1;
     }
     for (int i = 0; i < n; i++) out[i] = A[i];
     return n;
@@ -256,7 +280,8 @@ __device__ __forceinline__ bool overlaps(const D2 V[3], D2 x, double d2)
 
 // R(x, T_b) for the ball mode BALL
 template <int BALL>
-__device__ __forceinline__ void make_region(const D2 V[3], D2 bary_b, D2 x, const GeoParams &g, Region &R)
+__device__ __forceinline__ void make_region(const D2 V[3], const F2 dl[3], D2 bary_b, D2 x, const GeoParams &g,
+                                            Region &R)
 {
     R.kind = KIND_NONE;
     R.nv = 0;
@@ -272,7 +297,7 @@ __device__ __forceinline__ void make_region(const D2 V[3], D2 bary_b, D2 x, cons
         return;
     }
     if (BALL == NL_BALL_NGON) {
-        int n = clip_ngon(V, x, g, R.P, &R.overflow);
+        int n = clip_ngon(V, dl, x, g, R.P, &R.overflow);
         if (n >= 3) {
             R.nv = n;
             bool same = (n == 3);
@@ -321,6 +346,127 @@ __device__ __forceinline__ void make_region(const D2 V[3], D2 bary_b, D2 x, cons
         R.nv = (m >= 3) ? m : 0;
     }
     if (R.nv >= 3 || R.ncap > 0) R.kind = (nin == 3 && n == 3) ? KIND_WHOLE : KIND_PARTIAL;
+}
+
+// ---------------------------------------------------------------------------
+// Certified FP32 pre-classification.
+//
+// d[i] = v_i - x in FP32, each within eps_d of the exact difference (the inputs are
+// rounded FP64 differences taken relative to the outer triangle's barycentre).  A
+// decision is taken in FP32 only when the exact value clears the threshold by the
+// margin tau (1e-5 delta, about 100x the FP32 error bound); then the FP64 predicates
+// (whose own error is ~1e-16 delta) decide the same way, so the region equals the
+// one the FP64 geometry would build:
+//   whole  - every vertex at least tau inside the ball (or the polygon's inscribed
+//            circle): every in-ball test is true, no edge root lies in (0, 1), every
+//            polygon half-plane pass is the identity;
+//   empty  - T_b at least tau outside the circle of radius delta (which contains
+//            every approximate ball used here): no vertex inside, no edge root in
+//            [0, 1], and no clip output vertex can survive.
+// Anything else is undecided and goes to the FP64 geometry.
+// ---------------------------------------------------------------------------
+enum { CLS_EMPTY = 0, CLS_WHOLE = 1, CLS_EXACT = 2 };
+
+__device__ __forceinline__ float dist2_origin_triangle(const F2 d[3])
+{
+    // 0 if the origin is inside the ccw triangle, else the squared distance to it
+    float o0 = d[0].x * d[1].y - d[0].y * d[1].x;
+    float o1 = d[1].x * d[2].y - d[1].y * d[2].x;
+    float o2 = d[2].x * d[0].y - d[2].y * d[0].x;
+    if (o0 >= 0.f && o1 >= 0.f && o2 >= 0.f) return 0.f;
+    float best = INFINITY;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        F2 p = d[i], q = d[(i + 1) % 3];
+        float ex = q.x - p.x, ey = q.y - p.y;
+        float t = -(p.x * ex + p.y * ey) / (ex * ex + ey * ey);
+        t = fminf(fmaxf(t, 0.f), 1.f);
+        float cx = p.x + t * ex, cy = p.y + t * ey;
+        best = fminf(best, cx * cx + cy * cy);
+    }
+    return best;
+}
+
+// rin: radius of the disc that lies inside the kept region for sure (delta, or the
+// polygon's inradius); rout: radius of a disc containing it (delta)
+__device__ __forceinline__ int classify_vertices(const F2 d[3], float rin_m2, float rout_p2)
+{
+    float r0 = d[0].x * d[0].x + d[0].y * d[0].y;
+    float r1 = d[1].x * d[1].x + d[1].y * d[1].y;
+    float r2 = d[2].x * d[2].x + d[2].y * d[2].y;
+    if (fmaxf(r0, fmaxf(r1, r2)) <= rin_m2) return CLS_WHOLE;
+    if (fminf(r0, fminf(r1, r2)) > rout_p2 && dist2_origin_triangle(d) > rout_p2) return CLS_EMPTY;
+    return CLS_EXACT;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 Sutherland-Hodgman clip with certified signs (FP32-compensated path).
+//
+// Each vertex carries an absolute bound err on its distance to the vertex the FP64
+// clip holds at the same point of the algorithm.  An orientation o_k(v) computed in
+// FP32 is trusted only if |o| > |e_k| (err + rounding allowance); then its sign is
+// the FP64 sign, every branch of the clip matches the FP64 run, and so do the
+// vertex count and the kind.  A new vertex p = s + t (e - s), t = o_s / (o_s - o_e),
+// inherits err_p = max(err_s, err_e) + |e - s| (u_s + u_e) / (|o_s| + |o_e| - u_s - u_e)
+// + rounding.  Returns the vertex count, or -1 when a sign is not certain (the
+// caller then runs the FP64 clip).  Coordinates are relative to x.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int clip_ngon_f32(const F2 dl[3], float err0, const GeoParams &g, F2 *out, bool *cut,
+                                             int *overflow)
+{
+    F2 A[NL_MAXV], B[NL_MAXV];
+    float eA[NL_MAXV], eB[NL_MAXV];
+    const float kEps = 8.0f * 5.9604645e-8f;   // 8 units of 2^-24
+    int n = 3;
+    for (int i = 0; i < 3; i++) { A[i] = dl[i]; eA[i] = err0; }
+    *cut = false;
+    const int N = g.ngon_n;
+    for (int k = 0; k < N && n > 0; k++) {
+        const float ox = g.of[k][0], oy = g.of[k][1], ex = g.ef[k][0], ey = g.ef[k][1];
+        const float el = g.mk[k] / g.tau;   // |e_k|
+        float o[NL_MAXV], u[NL_MAXV];
+        bool all_in = true;
+        for (int i = 0; i < n; i++) {
+            const float rx = A[i].x - ox, ry = A[i].y - oy;
+            o[i] = ex * ry - ey * rx;
+            u[i] = el * (eA[i] + kEps * (fabsf(rx) + fabsf(ry) + fabsf(A[i].x) + fabsf(A[i].y)));
+            if (!(fabsf(o[i]) > u[i])) return -1;
+            all_in = all_in && (o[i] > 0.f);
+        }
+        if (all_in) continue;
+        *cut = true;
+        int m = 0;
+        for (int i = 0; i < n; i++) {
+            if (m + 2 > NL_MAXV) {
+                *overflow = 1;
+                return -1;
+            }
+            const int ip = (i + n - 1) % n;
+            const float ds = o[ip], de = o[i];
+            const bool e_in = de > 0.f, s_in = ds > 0.f;
+            if (e_in != s_in) {
+                const F2 sp = A[ip], ep = A[i];
+                const float t = ds / (ds - de);
+                const float dx = ep.x - sp.x, dy = ep.y - sp.y;
+                F2 p;
+                p.x = sp.x + t * dx;
+                p.y = sp.y + t * dy;
+                const float den = fabsf(ds) + fabsf(de) - u[ip] - u[i];
+                const float len = fabsf(dx) + fabsf(dy);
+                eB[m] = fmaxf(eA[ip], eA[i]) + len * (u[ip] + u[i]) / den +
+                        kEps * (fabsf(sp.x) + fabsf(sp.y) + fabsf(ep.x) + fabsf(ep.y) + len);
+                B[m++] = p;
+            }
+            if (e_in) {
+                eB[m] = eA[i];
+                B[m++] = A[i];
+            }
+        }
+        n = m;
+        for (int i = 0; i < n; i++) { A[i] = B[i]; eA[i] = eB[i]; }
+    }
+    for (int i = 0; i < n; i++) out[i] = A[i];
+    return n;
 }
 
 // ---- near-singular test (values of psi = c/|x-y| need a special rule) ----

@@ -28,12 +28,13 @@ struct nl_ctx {
 struct nl_plan {
     int K = 0, J = 0;
     nl_config cfg{};
-    double d2 = 0.0, hmax = 0.0;
+    double d2 = 0.0, hmax = 0.0, rmax = 0.0;
     // mesh (device)
     int32_t *tri = nullptr;       // [3K]
     double *tx = nullptr, *ty = nullptr;   // [3][K] vertex coordinates per triangle
     double *bx = nullptr, *by = nullptr, *rad = nullptr, *area = nullptr;  // [K]
     double *ngon = nullptr;       // [2 ngon_n]
+    std::vector<double> ngon_host; // host copy of the polygon offsets
     // candidates
     int64_t E = 0;
     int64_t *nbr_ptr = nullptr;   // [K+1]

@@ -340,6 +340,9 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
             return s;
         NL_CK(cudaMemcpyAsync(P->ngon, doff, sizeof(double) * 2 * cfg->ngon_n, cudaMemcpyDeviceToDevice,
                               ctx->stream));
+        P->ngon_host.resize(2 * (size_t)cfg->ngon_n);
+        NL_CK(cudaMemcpyAsync(P->ngon_host.data(), doff, sizeof(double) * 2 * cfg->ngon_n, cudaMemcpyDeviceToHost,
+                              ctx->stream));
         if (own_off) NL_CK(cudaFreeAsync(doff, ctx->stream));
     }
     double *diam = nullptr;
@@ -373,6 +376,7 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
         return nl_fail(ctx, NL_EGEOM, "delta must exceed the largest triangle diameter (" +
                                           std::to_string(hst.hmax) + ")");
     P->hmax = hst.hmax;
+    P->rmax = hst.rmax;
     // grid for the candidate search
     double R = (cfg->delta + 2.0 * hst.rmax) * (1.0 + 1e-9);
     double Lx = hst.xmax - hst.xmin, Ly = hst.ymax - hst.ymin, L = fmax(fmax(Lx, Ly), 1e-300);

@@ -38,6 +38,7 @@ struct NumArgs {
     const int64_t *nbr_ptr;
     const int32_t *nbr_idx;
     RuleTab outer, inner;
+    float fin_l[NL_MAXQ + 8][3], fin_w[NL_MAXQ + 8];   // inner rule in FP32
     double gl_x[8], gl_w[8];          // Gauss-Legendre on [0,1] with duffy_n points
     double gl2_x[2], gl2_w[2];
     int duffy_n;
@@ -162,6 +163,45 @@ __device__ __forceinline__ void near_polygon(const NumArgs &A, const BaryMap &bm
 
 // inner sums of the region R(x, T_b)
 template <typename T>
+__device__ __forceinline__ T rule_l(const NumArgs &A, int r, int i)
+{
+    if (sizeof(T) == sizeof(float)) return (T)A.fin_l[r][i];
+    return (T)A.inner.l[r][i];
+}
+
+template <typename T>
+__device__ __forceinline__ T rule_w(const NumArgs &A, int r)
+{
+    if (sizeof(T) == sizeof(float)) return (T)A.fin_w[r];
+    return (T)A.inner.w[r];
+}
+
+// inner sums over the whole triangle T_b: phi_b at the rule points are the rule's barycentrics
+template <typename T>
+__device__ __forceinline__ void whole_sums(const NumArgs &A, const D2 V[3], double area_b, D2 x, Sums<T> &S,
+                                           int64_t &nqp)
+{
+    sums_zero(S);
+    const bool inv = (A.kernel == NL_KERNEL_INV_DIST);
+    const int n = A.inner.n;
+    const T ar = (T)area_b * (T)A.kc;
+    T lx[3], ly[3];
+    if (inv)
+        for (int i = 0; i < 3; i++) { lx[i] = (T)(V[i].x - x.x); ly[i] = (T)(V[i].y - x.y); }
+    for (int r = 0; r < n; r++) {
+        T p0 = rule_l<T>(A, r, 0), p1 = rule_l<T>(A, r, 1), p2 = rule_l<T>(A, r, 2);
+        T w = rule_w<T>(A, r) * ar;
+        if (inv) {
+            T dx = p0 * lx[0] + p1 * lx[1] + p2 * lx[2];
+            T dy = p0 * ly[0] + p1 * ly[1] + p2 * ly[2];
+            w = w / sqrt(dx * dx + dy * dy);
+        }
+        sums_add<T>(S, w, p0, p1, p2);
+    }
+    nqp += n;
+}
+
+template <typename T>
 __device__ __forceinline__ void inner_sums(const NumArgs &A, const nlg::Region &R, const D2 V[3], double area_b,
                                            D2 x, Sums<T> &S, int64_t &nqp)
 {
@@ -215,11 +255,11 @@ __device__ __forceinline__ void inner_sums(const NumArgs &A, const nlg::Region &
                 T lnx = (T)(s2p.x - x.x), lny = (T)(s2p.y - x.y);
                 const T art = (T)ar;
                 for (int r = 0; r < ri.n; r++) {
-                    T m0 = (T)ri.l[r][0], m1 = (T)ri.l[r][1], m2 = (T)ri.l[r][2];
+                    T m0 = rule_l<T>(A, r, 0), m1 = rule_l<T>(A, r, 1), m2 = rule_l<T>(A, r, 2);
                     T p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
                     T p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
                     T p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
-                    T w = (T)ri.w[r] * art;
+                    T w = rule_w<T>(A, r) * art;
                     if (inv) {
                         T dx = m0 * l0x + m1 * lkx + m2 * lnx;
                         T dy = m0 * l0y + m1 * lky + m2 * lny;
@@ -250,8 +290,45 @@ __device__ __forceinline__ void inner_sums(const NumArgs &A, const nlg::Region &
     }
 }
 
+// inner sums over a fanned polygon given in FP32 coordinates relative to x (FP32 path)
+__device__ __forceinline__ void poly_sums_f32(const NumArgs &A, const nlg::F2 *P, int n, const nlg::F2 &d0,
+                                              const nlg::F2 &e1, const nlg::F2 &e2, float inv_det,
+                                              Sums<float> &S, int64_t &nqp)
+{
+    sums_zero(S);
+    const int nr = A.inner.n;
+    const float kc = (float)A.kc;
+    auto phi = [&](const nlg::F2 &p, float f[3]) {
+        const float rx = p.x - d0.x, ry = p.y - d0.y;
+        const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
+        const float l2 = (e1.x * ry - rx * e1.y) * inv_det;
+        f[0] = 1.f - l1 - l2;
+        f[1] = l1;
+        f[2] = l2;
+    };
+    float f0[3], fk[3];
+    phi(P[0], f0);
+    phi(P[1], fk);
+    for (int k = 1; k + 1 < n; k++) {
+        const nlg::F2 s0 = P[0], s1 = P[k], s2 = P[k + 1];
+        const float ar = 0.5f * fabsf((s1.x - s0.x) * (s2.y - s0.y) - (s2.x - s0.x) * (s1.y - s0.y)) * kc;
+        float fn[3];
+        phi(s2, fn);
+        for (int r = 0; r < nr; r++) {
+            const float m0 = A.fin_l[r][0], m1 = A.fin_l[r][1], m2 = A.fin_l[r][2];
+            const float p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
+            const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
+            const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
+            sums_add<float>(S, A.fin_w[r] * ar, p0, p1, p2);
+        }
+        nqp += nr;
+        fk[0] = fn[0]; fk[1] = fn[1]; fk[2] = fn[2];
+    }
+}
+
 struct OuterPt {
     double x, y, W, l0, l1, l2;
+    float lx, ly;     // x_q - bary_a in FP32
 };
 
 constexpr int kWarpsPerBlock = 4;
@@ -276,6 +353,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_numeric(const NumArgs A
         o.y = nlg::add(nlg::add(nlg::mul(l0, Va[0].y), nlg::mul(l1, Va[1].y)), nlg::mul(l2, Va[2].y));
         o.W = A.outer.w[q] * area_a;
         o.l0 = l0; o.l1 = l1; o.l2 = l2;
+        o.lx = (float)(o.x - A.bx[a]);
+        o.ly = (float)(o.y - A.by[a]);
         sq[wib][q] = o;
     }
     __syncwarp();
@@ -292,6 +371,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_numeric(const NumArgs A
         for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
         const D2 bb = {A.bx[b], A.by[b]};
         const double area_b = A.area[b];
+        // T_b relative to bary_a in FP32 (rounded FP64 differences)
+        nlg::F2 vl[3];
+        for (int i = 0; i < 3; i++) { vl[i].x = (float)(Vb[i].x - ba.x); vl[i].y = (float)(Vb[i].y - ba.y); }
+        const nlg::F2 bl = {(float)(bb.x - ba.x), (float)(bb.y - ba.y)};
+        // FP32 edge vectors of T_b (for barycentric coordinates of clipped vertices)
+        const nlg::F2 be1 = {(float)(Vb[1].x - Vb[0].x), (float)(Vb[1].y - Vb[0].y)};
+        const nlg::F2 be2 = {(float)(Vb[2].x - Vb[0].x), (float)(Vb[2].y - Vb[0].y)};
+        const float binv = 1.f / (be1.x * be2.y - be2.x * be1.y);
         int q0 = 0, q1 = nq_all;
         if (A.switch47) {
             double dx = nlg::sub(ba.x, bb.x), dy = nlg::sub(ba.y, bb.y);
@@ -305,14 +392,61 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_numeric(const NumArgs A
         for (int q = q0; q < q1; q++) {
             const OuterPt o = sq[wib][q];
             const D2 x = {o.x, o.y};
-            nlg::Region R;
-            nlg::make_region<BALL>(Vb, bb, x, A.geo, R);
-            if (R.overflow) atomicOr(A.err, 1);
-            if (R.kind == nlg::KIND_NONE) continue;
-            any = true;
+            nlg::F2 dl[3];
+            for (int i = 0; i < 3; i++) { dl[i].x = vl[i].x - o.lx; dl[i].y = vl[i].y - o.ly; }
+            int cls;
+            if (BALL == NL_BALL_BARYCENTER) {
+                float bx = bl.x - o.lx, by = bl.y - o.ly, r2 = bx * bx + by * by;
+                cls = r2 <= A.geo.b_in2 ? nlg::CLS_WHOLE : (r2 >= A.geo.b_out2 ? nlg::CLS_EMPTY : nlg::CLS_EXACT);
+            } else if (BALL == NL_BALL_OVERLAP) {
+                float r0 = dl[0].x * dl[0].x + dl[0].y * dl[0].y, r1 = dl[1].x * dl[1].x + dl[1].y * dl[1].y;
+                float r2 = dl[2].x * dl[2].x + dl[2].y * dl[2].y;
+                if (fminf(r0, fminf(r1, r2)) <= A.geo.rin_m2) cls = nlg::CLS_WHOLE;
+                else if (nlg::dist2_origin_triangle(dl) > A.geo.rout_p2) cls = nlg::CLS_EMPTY;
+                else cls = nlg::CLS_EXACT;
+            } else {
+                cls = nlg::classify_vertices(dl, A.geo.rin_m2, A.geo.rout_p2);
+            }
+            if (cls == nlg::CLS_EMPTY) continue;
             Sums<T> S;
             int64_t nq = 0;
-            inner_sums<T>(A, R, Vb, area_b, x, S, nq);
+            int kind = nlg::KIND_WHOLE, nv = 3, ncap = 0;
+            nlg::F2 P32[NL_MAXV];
+            int n32 = -1, ovf32 = 0;
+            bool cut32 = false;
+            if (cls == nlg::CLS_WHOLE && A.kernel == NL_KERNEL_INV_DIST) {
+                // the singular kernel needs the near-field test even on whole triangles
+                nlg::Region R;
+                R.kind = nlg::KIND_WHOLE;
+                R.nv = 3;
+                R.ncap = 0;
+                R.P[0] = Vb[0]; R.P[1] = Vb[1]; R.P[2] = Vb[2];
+                inner_sums<T>(A, R, Vb, area_b, x, S, nq);
+            } else if (cls == nlg::CLS_WHOLE) {
+                whole_sums<T>(A, Vb, area_b, x, S, nq);
+            } else if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON && A.kernel == NL_KERNEL_CONST &&
+                       (n32 = nlg::clip_ngon_f32(dl, A.geo.err0, A.geo, P32, &cut32, &ovf32)) >= 0) {
+                // certified FP32 clip: same vertex count and kind as the FP64 clip
+                if (ovf32) atomicOr(A.err, 1);
+                if (n32 < 3) continue;
+                kind = cut32 ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
+                nv = n32;
+                if (!cut32) whole_sums<T>(A, Vb, area_b, x, S, nq);
+                else poly_sums_f32(A, P32, n32, dl[0], be1, be2, binv, *(Sums<float> *)&S, nq);
+            } else {
+                nlg::Region R;
+                nlg::make_region<BALL>(Vb, dl, bb, x, A.geo, R);
+                if (R.overflow) atomicOr(A.err, 1);
+                if (R.kind == nlg::KIND_NONE) continue;
+                kind = R.kind;
+                nv = R.nv;
+                ncap = R.ncap;
+                if (R.kind == nlg::KIND_WHOLE && R.ncap == 0 && A.kernel != NL_KERNEL_INV_DIST)
+                    whole_sums<T>(A, Vb, area_b, x, S, nq);
+                else
+                    inner_sums<T>(A, R, Vb, area_b, x, S, nq);
+            }
+            any = true;
             const T W = (T)o.W, la0 = (T)o.l0, la1 = (T)o.l1, la2 = (T)o.l2;
             mbb[0] += W * S.S2[0]; mbb[1] += W * S.S2[1]; mbb[2] += W * S.S2[2];
             mbb[3] += W * S.S2[3]; mbb[4] += W * S.S2[4]; mbb[5] += W * S.S2[5];
@@ -325,7 +459,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_numeric(const NumArgs A
             maa_b[3] += ws * la0 * la1; maa_b[4] += ws * la0 * la2; maa_b[5] += ws * la1 * la2;
             cnt++;
             qp += nq;
-            if (A.stats) hsum += nlg::record_hash(a, b, q - q0, R.kind, R.nv, R.ncap);
+            if (A.stats) hsum += nlg::record_hash(a, b, q - q0, kind, nv, ncap);
         }
         A.flag[e] = any ? 1 : 0;
         for (int i = 0; i < 9; i++) blk[(int64_t)i * E + e] = mab[i];
