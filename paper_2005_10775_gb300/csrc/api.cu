@@ -175,6 +175,7 @@ nl_status fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
     A.by = P->by;
     A.area = P->area;
     A.nbr_ptr = P->nbr_ptr;
+    A.nbr_split = P->nbr_split;
     A.nbr_idx = P->nbr_idx;
     if (c.outer == NL_RULE_SWITCH47) {
         fill_rule(NL_RULE_GAUSS4, &A.outer);
@@ -226,6 +227,20 @@ nl_status fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
         }
     }
     A.geo.tau = (float)tau;
+    if (c.ball == NL_BALL_NGON) {
+        // regular polygon R (cos 2 pi k / N, sin 2 pi k / N)?  (enables the angular pass window)
+        const int N = c.ngon_n;
+        const double *o = P->ngon_host.data();
+        const double R = sqrt(o[0] * o[0] + o[1] * o[1]);
+        bool reg = R > 0.0;
+        for (int k = 0; k < N && reg; k++) {
+            const double th = 2.0 * M_PI * k / N;
+            reg = fabs(o[2 * k] - R * cos(th)) <= 1e-12 * R && fabs(o[2 * k + 1] - R * sin(th)) <= 1e-12 * R;
+        }
+        A.geo.regular = reg ? 1 : 0;
+        A.geo.sector = (float)(2.0 * M_PI / N);
+        A.geo.rin_tau = (float)(rin - tau);
+    }
     // FP32 local coordinates v - x are rounded differences of magnitude <= delta + 4 r_max
     A.geo.err0 = (float)(4.0 * 5.9604644775390625e-8 * (c.delta + 4.0 * P->rmax));
     A.geo.rin_m2 = rin - tau > 0.0 ? (float)((rin - tau) * (rin - tau)) : -1.0f;
@@ -283,7 +298,7 @@ void nl_plan_free(nl_plan *P)
 {
     if (!P) return;
     nl_free(P->tri); nl_free(P->tx); nl_free(P->ty); nl_free(P->bx); nl_free(P->by);
-    nl_free(P->rad); nl_free(P->area); nl_free(P->ngon); nl_free(P->nbr_ptr); nl_free(P->nbr_idx);
+    nl_free(P->rad); nl_free(P->area); nl_free(P->ngon); nl_free(P->nbr_ptr); nl_free(P->nbr_idx); nl_free(P->nbr_split);
     nl_free(P->flag); nl_free(P->blk); nl_free(P->maa); nl_free(P->qp_a); nl_free(P->cnt_a);
     nl_free(P->hash_a); nl_free(P->lslot); nl_free(P->tslot); nl_free(P->W); nl_free(P->val32);
     nl_free(P->err);

@@ -63,7 +63,52 @@ struct GeoParams {
     float ef[64][2];      // edges o_{k+1} - o_k (FP32)
     float mk[64];         // |e_k| tau: margin of the FP32 orientation test of pass k
     float err0;           // bound on |dl - (v - x)| of the FP32 local coordinates
+    int regular;          // offsets form the regular polygon R (cos 2 pi k / N, sin 2 pi k / N)
+    float sector, rin_tau; // 2 pi / N; inradius - tau
 };
+
+// Passes of the polygon clip that can change a triangle with FP32 coordinates d (relative to
+// x), as a bit mask over k.  For a regular polygon, half-plane k (normal angle (k + 1/2) 2pi/N)
+// can only cut points within angle alpha of its normal, cos alpha = (r_in - tau) / |p|: every
+// pass whose normal is farther than alpha (plus half a sector of slack) from the triangle's
+// angular extent keeps all of it at least tau inside and is the identity.
+__device__ __forceinline__ uint64_t ngon_pass_mask(const F2 d[3], const GeoParams &g)
+{
+    const int N = g.ngon_n;
+    const uint64_t full = (N >= 64) ? ~0ull : ((1ull << N) - 1ull);
+    if (!g.regular) return full;
+    const float o0 = d[0].x * d[1].y - d[0].y * d[1].x;
+    const float o1 = d[1].x * d[2].y - d[1].y * d[2].x;
+    const float o2 = d[2].x * d[0].y - d[2].y * d[0].x;
+    if (fminf(o0, fminf(o1, o2)) > -1e-3f * (fabsf(o0) + fabsf(o1) + fabsf(o2))) return full;  // x inside or close
+    float rmax = 0.f, t[3];
+    for (int i = 0; i < 3; i++) {
+        rmax = fmaxf(rmax, sqrtf(d[i].x * d[i].x + d[i].y * d[i].y));
+        t[i] = atan2f(d[i].y, d[i].x);
+    }
+    if (rmax <= g.rin_tau) return 0ull;
+    const float alpha = acosf(g.rin_tau / rmax);
+    // sort the three angles, take the arc complementary to the largest gap
+    float a0 = t[0], a1 = t[1], a2 = t[2], tmp;
+    if (a0 > a1) { tmp = a0; a0 = a1; a1 = tmp; }
+    if (a1 > a2) { tmp = a1; a1 = a2; a2 = tmp; }
+    if (a0 > a1) { tmp = a0; a0 = a1; a1 = tmp; }
+    const float two_pi = 6.28318530718f;
+    const float g01 = a1 - a0, g12 = a2 - a1, g20 = a0 + two_pi - a2;
+    float lo, hi;
+    if (g20 >= g01 && g20 >= g12) { lo = a0; hi = a2; }
+    else if (g01 >= g12) { lo = a1; hi = a0 + two_pi; }
+    else { lo = a2; hi = a1 + two_pi; }
+    if (hi - lo > 0.8f * 3.14159265f) return full;
+    const float slack = alpha + 0.5f * g.sector + 1e-3f;
+    lo -= slack;
+    hi += slack;
+    if (hi - lo >= two_pi) return full;
+    const int k0 = (int)ceilf(lo / g.sector - 0.5f), k1 = (int)floorf(hi / g.sector - 0.5f);
+    uint64_t m = 0;
+    for (int k = k0; k <= k1; k++) m |= 1ull << (((k % N) + N) % N);
+    return m;
+}
 
 __device__ __forceinline__ bool in_ball(D2 p, D2 x, double d2)
 {
@@ -195,7 +240,10 @@ __device__ __forceinline__ int clip_ngon(const D2 V[3], const F2 dl[3], D2 x, co
     A[0] = V[0]; A[1] = V[1]; A[2] = V[2];
     Af[0] = dl[0]; Af[1] = dl[1]; Af[2] = dl[2];
     const int N = g.ngon_n;
-    for (int k = 0; k < N && n > 0; k++) {
+    uint64_t mask = ngon_pass_mask(dl, g);
+    while (mask && n > 0) {
+        const int k = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
         // certified identity pass: skip without FP64 work
         bool sure_in = true;
         {
@@ -420,8 +468,10 @@ __device__ __forceinline__ int clip_ngon_f32(const F2 dl[3], float err0, const G
     int n = 3;
     for (int i = 0; i < 3; i++) { A[i] = dl[i]; eA[i] = err0; }
     *cut = false;
-    const int N = g.ngon_n;
-    for (int k = 0; k < N && n > 0; k++) {
+    uint64_t mask = ngon_pass_mask(dl, g);
+    while (mask && n > 0) {
+        const int k = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
         const float ox = g.of[k][0], oy = g.of[k][1], ex = g.ef[k][0], ey = g.ef[k][1];
         const float el = g.mk[k] / g.tau;   // |e_k|
         float o[NL_MAXV], u[NL_MAXV];

@@ -28,7 +28,7 @@ struct nl_ctx {
 struct nl_plan {
     int K = 0, J = 0;
     nl_config cfg{};
-    double d2 = 0.0, hmax = 0.0, rmax = 0.0;
+    double d2 = 0.0, hmax = 0.0, rmax = 0.0, rin = 0.0;
     // mesh (device)
     int32_t *tri = nullptr;       // [3K]
     double *tx = nullptr, *ty = nullptr;   // [3][K] vertex coordinates per triangle
@@ -38,7 +38,8 @@ struct nl_plan {
     // candidates
     int64_t E = 0;
     int64_t *nbr_ptr = nullptr;   // [K+1]
-    int32_t *nbr_idx = nullptr;   // [E], sorted per triangle
+    int32_t *nbr_idx = nullptr;   // [E], per triangle: interior candidates, then boundary ones, each sorted
+    int64_t *nbr_split = nullptr; // [K] first boundary candidate of each triangle
     // numeric phase outputs
     uint8_t *flag = nullptr;      // [E] directed: some outer point of a sees a non-empty region in b
     void *blk = nullptr;          // [15][E] pair blocks (float or double)
@@ -99,6 +100,7 @@ nl_status nl_run_numeric(nl_ctx *ctx, nl_plan *P, bool with_hash);
 nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out);
 nl_status nl_run_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out);
 void nl_plan_free(nl_plan *P);
+double nl_polygon_inradius(const double *offsets, int n);
 
 // host pointer / device pointer staging
 bool nl_is_device_ptr(const void *p);

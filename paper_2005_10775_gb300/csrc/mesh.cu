@@ -255,10 +255,18 @@ __global__ void k_candidates(int K, Grid g, double delta, const double *__restri
     if (!pass && lane == 0) cnt[a] = n;
 }
 
-// sort each candidate list by triangle index (bitonic sort in shared memory)
-__global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int *overflow)
+// Sort each candidate list by triangle index, interior candidates first (bitonic sort in
+// shared memory).  A candidate is interior when every point of T_b lies, with margin,
+// inside the kept region of every outer point of T_a (whole for every q):
+//   mode 0: |bary_a - bary_b| + r_a + r_b <= lim   (lim = r_in - tau: disc or polygon inradius)
+//   mode 1: |bary_a - bary_b| + r_a <= lim         (barycenter ball, lim = delta - tau)
+//   mode 2: no interior fast path
+// split[a] = index of the first boundary candidate.
+__global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split, const double *bx, const double *by,
+                             const double *rad, int mode, double lim, int *overflow)
 {
     __shared__ int32_t s[NL_MAXCAND];
+    __shared__ int s_int;
     int a = blockIdx.x;
     int64_t b0 = ptr[a];
     int n = (int)(ptr[a + 1] - b0);
@@ -266,9 +274,28 @@ __global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int *overflow)
         if (threadIdx.x == 0) atomicAdd(overflow, 1);
         return;
     }
+    if (threadIdx.x == 0) s_int = 0;
     int p = 1;
     while (p < n) p <<= 1;
-    for (int i = threadIdx.x; i < p; i += blockDim.x) s[i] = i < n ? idx[b0 + i] : 0x7fffffff;
+    const double ax = bx[a], ay = by[a], ra = rad[a];
+    __syncthreads();
+    int my_int = 0;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+        int key = 0x7fffffff;
+        if (i < n) {
+            const int b = idx[b0 + i];
+            bool interior = false;
+            if (mode != 2) {
+                const double dx = bx[b] - ax, dy = by[b] - ay;
+                const double D = sqrt(dx * dx + dy * dy);
+                interior = (mode == 0 ? D + ra + rad[b] : D + ra) <= lim;
+            }
+            my_int += interior;
+            key = interior ? b : (b | 0x40000000);
+        }
+        s[i] = key;
+    }
+    atomicAdd(&s_int, my_int);
     __syncthreads();
     for (int k = 2; k <= p; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -282,7 +309,8 @@ __global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int *overflow)
             }
             __syncthreads();
         }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) idx[b0 + i] = s[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) idx[b0 + i] = s[i] & 0x3fffffff;
+    if (threadIdx.x == 0) split[a] = b0 + s_int;
 }
 
 }  // namespace
@@ -309,6 +337,20 @@ nl_status nl_scan_i64(nl_ctx *ctx, const int64_t *in, int64_t *out, int64_t n)
     NL_CK(cudaGetLastError());
     NL_CK(cudaFreeAsync(bsum, ctx->stream));
     return NL_OK;
+}
+
+double nl_polygon_inradius(const double *o, int N)
+{
+    // distance from the centre to the nearest edge line of the ccw polygon o_0 .. o_{N-1}
+    double rin = INFINITY;
+    for (int k = 0; k < N; k++) {
+        const int k1 = (k + 1) % N;
+        const double ex = o[2 * k1] - o[2 * k], ey = o[2 * k1 + 1] - o[2 * k + 1];
+        const double el = sqrt(ex * ex + ey * ey);
+        const double dk = (o[2 * k] * o[2 * k1 + 1] - o[2 * k + 1] * o[2 * k1]) / (el > 0.0 ? el : 1.0);
+        rin = fmin(rin, dk);
+    }
+    return rin;
 }
 
 nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_plan *P)
@@ -343,6 +385,8 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
         P->ngon_host.resize(2 * (size_t)cfg->ngon_n);
         NL_CK(cudaMemcpyAsync(P->ngon_host.data(), doff, sizeof(double) * 2 * cfg->ngon_n, cudaMemcpyDeviceToHost,
                               ctx->stream));
+        NL_CK(cudaStreamSynchronize(ctx->stream));
+        P->rin = nl_polygon_inradius(P->ngon_host.data(), cfg->ngon_n);
         if (own_off) NL_CK(cudaFreeAsync(doff, ctx->stream));
     }
     double *diam = nullptr;
@@ -429,7 +473,18 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
     k_candidates<<<wblocks, 256, 0, ctx->stream>>>(K, g, cfg->delta, P->bx, P->by, P->rad, cstart, bucket,
                                                    nullptr, P->nbr_ptr, P->nbr_idx, 1); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    k_sort_lists<<<K, 256, 0, ctx->stream>>>(P->nbr_ptr, P->nbr_idx, ovf); ++ctx->launches;
+    // interior fast path: the region is whole for every outer point (certified with margin tau)
+    {
+        const double tau = 1e-5 * cfg->delta;
+        int mode = 0;
+        double lim = cfg->delta - tau;
+        if (cfg->kernel == NL_KERNEL_INV_DIST) mode = 2;          // near-field rule needs every pair
+        else if (cfg->ball == NL_BALL_BARYCENTER) mode = 1;
+        else if (cfg->ball == NL_BALL_NGON) lim = P->rin - tau;
+        if ((s = nl_alloc(ctx, &P->nbr_split, (size_t)K)) != NL_OK) return s;
+        k_sort_lists<<<K, 256, 0, ctx->stream>>>(P->nbr_ptr, P->nbr_idx, P->nbr_split, P->bx, P->by, P->rad, mode,
+                                                 lim, ovf); ++ctx->launches;
+    }
     NL_CK(cudaGetLastError());
     NL_CK(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     NL_CK(cudaFreeAsync(cnt, ctx->stream));

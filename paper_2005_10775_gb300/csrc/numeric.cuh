@@ -35,7 +35,7 @@ struct NumArgs {
     int64_t E;
     const double *tx, *ty;            // [3][K]
     const double *bx, *by, *area;     // [K]
-    const int64_t *nbr_ptr;
+    const int64_t *nbr_ptr, *nbr_split;
     const int32_t *nbr_idx;
     RuleTab outer, inner;
     float fin_l[NL_MAXQ + 8][3], fin_w[NL_MAXQ + 8];   // inner rule in FP32
@@ -333,6 +333,131 @@ struct OuterPt {
 
 constexpr int kWarpsPerBlock = 4;
 
+// Per-lane accumulators of one outer triangle: stats and the FP64 M_aa sum.
+struct LaneAcc {
+    double maa[6];
+    int64_t cnt, qp;
+    uint64_t hsum;
+};
+
+// One candidate pair (a, b): every outer point of T_a against T_b.  INTERIOR: the
+// region is certified whole for every outer point (no per-point classification).
+template <int BALL, typename T, bool INTERIOR>
+__device__ __forceinline__ void pair_work(const NumArgs &A, const OuterPt *sq, int a, const D2 &ba, int64_t e,
+                                          LaneAcc &acc)
+{
+    const int K = A.K;
+    const int b = A.nbr_idx[e];
+    D2 Vb[3];
+    for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
+    const D2 bb = {A.bx[b], A.by[b]};
+    const double area_b = A.area[b];
+    int q0 = 0, q1 = A.outer.n;
+    if (A.switch47) {
+        double dx = nlg::sub(ba.x, bb.x), dy = nlg::sub(ba.y, bb.y);
+        bool near4 = A.thr2 > 0.0 && nlg::add(nlg::mul(dx, dx), nlg::mul(dy, dy)) < A.thr2;
+        if (near4) q1 = A.outer.nsplit; else q0 = A.outer.nsplit;
+    }
+    T mab[9], mbb[6], maa_b[6];
+    for (int i = 0; i < 9; i++) mab[i] = 0;
+    for (int i = 0; i < 6; i++) { mbb[i] = 0; maa_b[i] = 0; }
+    bool any = false;
+    // T_b relative to bary_a in FP32 (rounded FP64 differences)
+    nlg::F2 vl[3];
+    nlg::F2 bl = {0.f, 0.f}, be1 = {0.f, 0.f}, be2 = {0.f, 0.f};
+    float binv = 0.f;
+    if (!INTERIOR) {
+        for (int i = 0; i < 3; i++) { vl[i].x = (float)(Vb[i].x - ba.x); vl[i].y = (float)(Vb[i].y - ba.y); }
+        bl.x = (float)(bb.x - ba.x);
+        bl.y = (float)(bb.y - ba.y);
+        be1.x = (float)(Vb[1].x - Vb[0].x); be1.y = (float)(Vb[1].y - Vb[0].y);
+        be2.x = (float)(Vb[2].x - Vb[0].x); be2.y = (float)(Vb[2].y - Vb[0].y);
+        binv = 1.f / (be1.x * be2.y - be2.x * be1.y);
+    }
+    for (int q = q0; q < q1; q++) {
+        const OuterPt o = sq[q];
+        const D2 x = {o.x, o.y};
+        Sums<T> S;
+        int64_t nq = 0;
+        int kind = nlg::KIND_WHOLE, nv = 3, ncap = 0;
+        if (INTERIOR) {
+            whole_sums<T>(A, Vb, area_b, x, S, nq);
+        } else {
+            nlg::F2 dl[3];
+            for (int i = 0; i < 3; i++) { dl[i].x = vl[i].x - o.lx; dl[i].y = vl[i].y - o.ly; }
+            int cls;
+            if (BALL == NL_BALL_BARYCENTER) {
+                float bx = bl.x - o.lx, by = bl.y - o.ly, r2 = bx * bx + by * by;
+                cls = r2 <= A.geo.b_in2 ? nlg::CLS_WHOLE : (r2 >= A.geo.b_out2 ? nlg::CLS_EMPTY : nlg::CLS_EXACT);
+            } else if (BALL == NL_BALL_OVERLAP) {
+                float r0 = dl[0].x * dl[0].x + dl[0].y * dl[0].y, r1 = dl[1].x * dl[1].x + dl[1].y * dl[1].y;
+                float r2 = dl[2].x * dl[2].x + dl[2].y * dl[2].y;
+                if (fminf(r0, fminf(r1, r2)) <= A.geo.rin_m2) cls = nlg::CLS_WHOLE;
+                else if (nlg::dist2_origin_triangle(dl) > A.geo.rout_p2) cls = nlg::CLS_EMPTY;
+                else cls = nlg::CLS_EXACT;
+            } else {
+                cls = nlg::classify_vertices(dl, A.geo.rin_m2, A.geo.rout_p2);
+            }
+            if (cls == nlg::CLS_EMPTY) continue;
+            nlg::F2 P32[NL_MAXV];
+            int n32 = -1, ovf32 = 0;
+            bool cut32 = false;
+            if (cls == nlg::CLS_WHOLE && A.kernel == NL_KERNEL_INV_DIST) {
+                // the singular kernel needs the near-field test even on whole triangles
+                nlg::Region R;
+                R.kind = nlg::KIND_WHOLE;
+                R.nv = 3;
+                R.ncap = 0;
+                R.P[0] = Vb[0]; R.P[1] = Vb[1]; R.P[2] = Vb[2];
+                inner_sums<T>(A, R, Vb, area_b, x, S, nq);
+            } else if (cls == nlg::CLS_WHOLE) {
+                whole_sums<T>(A, Vb, area_b, x, S, nq);
+            } else if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON && A.kernel == NL_KERNEL_CONST &&
+                       (n32 = nlg::clip_ngon_f32(dl, A.geo.err0, A.geo, P32, &cut32, &ovf32)) >= 0) {
+                // certified FP32 clip: same vertex count and kind as the FP64 clip
+                if (n32 < 3) continue;
+                kind = cut32 ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
+                nv = n32;
+                if (!cut32) whole_sums<T>(A, Vb, area_b, x, S, nq);
+                else poly_sums_f32(A, P32, n32, dl[0], be1, be2, binv, *(Sums<float> *)&S, nq);
+            } else {
+                if (ovf32) atomicOr(A.err, 1);
+                nlg::Region R;
+                nlg::make_region<BALL>(Vb, dl, bb, x, A.geo, R);
+                if (R.overflow) atomicOr(A.err, 1);
+                if (R.kind == nlg::KIND_NONE) continue;
+                kind = R.kind;
+                nv = R.nv;
+                ncap = R.ncap;
+                if (R.kind == nlg::KIND_WHOLE && R.ncap == 0 && A.kernel != NL_KERNEL_INV_DIST)
+                    whole_sums<T>(A, Vb, area_b, x, S, nq);
+                else
+                    inner_sums<T>(A, R, Vb, area_b, x, S, nq);
+            }
+        }
+        any = true;
+        const T W = (T)o.W, la0 = (T)o.l0, la1 = (T)o.l1, la2 = (T)o.l2;
+        mbb[0] += W * S.S2[0]; mbb[1] += W * S.S2[1]; mbb[2] += W * S.S2[2];
+        mbb[3] += W * S.S2[3]; mbb[4] += W * S.S2[4]; mbb[5] += W * S.S2[5];
+        const T wa0 = W * la0, wa1 = W * la1, wa2 = W * la2;
+        mab[0] += wa0 * S.s1[0]; mab[1] += wa0 * S.s1[1]; mab[2] += wa0 * S.s1[2];
+        mab[3] += wa1 * S.s1[0]; mab[4] += wa1 * S.s1[1]; mab[5] += wa1 * S.s1[2];
+        mab[6] += wa2 * S.s1[0]; mab[7] += wa2 * S.s1[1]; mab[8] += wa2 * S.s1[2];
+        const T ws = W * S.s0;
+        maa_b[0] += ws * la0 * la0; maa_b[1] += ws * la1 * la1; maa_b[2] += ws * la2 * la2;
+        maa_b[3] += ws * la0 * la1; maa_b[4] += ws * la0 * la2; maa_b[5] += ws * la1 * la2;
+        acc.cnt++;
+        acc.qp += nq;
+        if (A.stats) acc.hsum += nlg::record_hash(a, b, q - q0, kind, nv, ncap);
+    }
+    A.flag[e] = any ? 1 : 0;
+    T *blk = (T *)A.blk;
+    const int64_t E = A.E;
+    for (int i = 0; i < 9; i++) blk[(int64_t)i * E + e] = mab[i];
+    for (int i = 0; i < 6; i++) blk[(int64_t)(9 + i) * E + e] = mbb[i];
+    for (int i = 0; i < 6; i++) acc.maa[i] += (double)maa_b[i];
+}
+
 template <int BALL, typename T>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_numeric(const NumArgs A)
 {
@@ -359,124 +484,25 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_numeric(const NumArgs A
     }
     __syncwarp();
     const D2 ba = {A.bx[a], A.by[a]};
-    double maa[6] = {0, 0, 0, 0, 0, 0};
-    int64_t cnt = 0, qp = 0;
-    uint64_t hsum = 0;
-    T *blk = (T *)A.blk;
-    const int64_t E = A.E;
-    const int64_t e0 = A.nbr_ptr[a], e1 = A.nbr_ptr[a + 1];
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-        const int b = A.nbr_idx[e];
-        D2 Vb[3];
-        for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
-        const D2 bb = {A.bx[b], A.by[b]};
-        const double area_b = A.area[b];
-        // T_b relative to bary_a in FP32 (rounded FP64 differences)
-        nlg::F2 vl[3];
-        for (int i = 0; i < 3; i++) { vl[i].x = (float)(Vb[i].x - ba.x); vl[i].y = (float)(Vb[i].y - ba.y); }
-        const nlg::F2 bl = {(float)(bb.x - ba.x), (float)(bb.y - ba.y)};
-        // FP32 edge vectors of T_b (for barycentric coordinates of clipped vertices)
-        const nlg::F2 be1 = {(float)(Vb[1].x - Vb[0].x), (float)(Vb[1].y - Vb[0].y)};
-        const nlg::F2 be2 = {(float)(Vb[2].x - Vb[0].x), (float)(Vb[2].y - Vb[0].y)};
-        const float binv = 1.f / (be1.x * be2.y - be2.x * be1.y);
-        int q0 = 0, q1 = nq_all;
-        if (A.switch47) {
-            double dx = nlg::sub(ba.x, bb.x), dy = nlg::sub(ba.y, bb.y);
-            bool near4 = A.thr2 > 0.0 && nlg::add(nlg::mul(dx, dx), nlg::mul(dy, dy)) < A.thr2;
-            if (near4) q1 = A.outer.nsplit; else q0 = A.outer.nsplit;
-        }
-        T mab[9], mbb[6], maa_b[6];
-        for (int i = 0; i < 9; i++) mab[i] = 0;
-        for (int i = 0; i < 6; i++) { mbb[i] = 0; maa_b[i] = 0; }
-        bool any = false;
-        for (int q = q0; q < q1; q++) {
-            const OuterPt o = sq[wib][q];
-            const D2 x = {o.x, o.y};
-            nlg::F2 dl[3];
-            for (int i = 0; i < 3; i++) { dl[i].x = vl[i].x - o.lx; dl[i].y = vl[i].y - o.ly; }
-            int cls;
-            if (BALL == NL_BALL_BARYCENTER) {
-                float bx = bl.x - o.lx, by = bl.y - o.ly, r2 = bx * bx + by * by;
-                cls = r2 <= A.geo.b_in2 ? nlg::CLS_WHOLE : (r2 >= A.geo.b_out2 ? nlg::CLS_EMPTY : nlg::CLS_EXACT);
-            } else if (BALL == NL_BALL_OVERLAP) {
-                float r0 = dl[0].x * dl[0].x + dl[0].y * dl[0].y, r1 = dl[1].x * dl[1].x + dl[1].y * dl[1].y;
-                float r2 = dl[2].x * dl[2].x + dl[2].y * dl[2].y;
-                if (fminf(r0, fminf(r1, r2)) <= A.geo.rin_m2) cls = nlg::CLS_WHOLE;
-                else if (nlg::dist2_origin_triangle(dl) > A.geo.rout_p2) cls = nlg::CLS_EMPTY;
-                else cls = nlg::CLS_EXACT;
-            } else {
-                cls = nlg::classify_vertices(dl, A.geo.rin_m2, A.geo.rout_p2);
-            }
-            if (cls == nlg::CLS_EMPTY) continue;
-            Sums<T> S;
-            int64_t nq = 0;
-            int kind = nlg::KIND_WHOLE, nv = 3, ncap = 0;
-            nlg::F2 P32[NL_MAXV];
-            int n32 = -1, ovf32 = 0;
-            bool cut32 = false;
-            if (cls == nlg::CLS_WHOLE && A.kernel == NL_KERNEL_INV_DIST) {
-                // the singular kernel needs the near-field test even on whole triangles
-                nlg::Region R;
-                R.kind = nlg::KIND_WHOLE;
-                R.nv = 3;
-                R.ncap = 0;
-                R.P[0] = Vb[0]; R.P[1] = Vb[1]; R.P[2] = Vb[2];
-                inner_sums<T>(A, R, Vb, area_b, x, S, nq);
-            } else if (cls == nlg::CLS_WHOLE) {
-                whole_sums<T>(A, Vb, area_b, x, S, nq);
-            } else if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON && A.kernel == NL_KERNEL_CONST &&
-                       (n32 = nlg::clip_ngon_f32(dl, A.geo.err0, A.geo, P32, &cut32, &ovf32)) >= 0) {
-                // certified FP32 clip: same vertex count and kind as the FP64 clip
-                if (ovf32) atomicOr(A.err, 1);
-                if (n32 < 3) continue;
-                kind = cut32 ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
-                nv = n32;
-                if (!cut32) whole_sums<T>(A, Vb, area_b, x, S, nq);
-                else poly_sums_f32(A, P32, n32, dl[0], be1, be2, binv, *(Sums<float> *)&S, nq);
-            } else {
-                nlg::Region R;
-                nlg::make_region<BALL>(Vb, dl, bb, x, A.geo, R);
-                if (R.overflow) atomicOr(A.err, 1);
-                if (R.kind == nlg::KIND_NONE) continue;
-                kind = R.kind;
-                nv = R.nv;
-                ncap = R.ncap;
-                if (R.kind == nlg::KIND_WHOLE && R.ncap == 0 && A.kernel != NL_KERNEL_INV_DIST)
-                    whole_sums<T>(A, Vb, area_b, x, S, nq);
-                else
-                    inner_sums<T>(A, R, Vb, area_b, x, S, nq);
-            }
-            any = true;
-            const T W = (T)o.W, la0 = (T)o.l0, la1 = (T)o.l1, la2 = (T)o.l2;
-            mbb[0] += W * S.S2[0]; mbb[1] += W * S.S2[1]; mbb[2] += W * S.S2[2];
-            mbb[3] += W * S.S2[3]; mbb[4] += W * S.S2[4]; mbb[5] += W * S.S2[5];
-            const T wa0 = W * la0, wa1 = W * la1, wa2 = W * la2;
-            mab[0] += wa0 * S.s1[0]; mab[1] += wa0 * S.s1[1]; mab[2] += wa0 * S.s1[2];
-            mab[3] += wa1 * S.s1[0]; mab[4] += wa1 * S.s1[1]; mab[5] += wa1 * S.s1[2];
-            mab[6] += wa2 * S.s1[0]; mab[7] += wa2 * S.s1[1]; mab[8] += wa2 * S.s1[2];
-            const T ws = W * S.s0;
-            maa_b[0] += ws * la0 * la0; maa_b[1] += ws * la1 * la1; maa_b[2] += ws * la2 * la2;
-            maa_b[3] += ws * la0 * la1; maa_b[4] += ws * la0 * la2; maa_b[5] += ws * la1 * la2;
-            cnt++;
-            qp += nq;
-            if (A.stats) hsum += nlg::record_hash(a, b, q - q0, kind, nv, ncap);
-        }
-        A.flag[e] = any ? 1 : 0;
-        for (int i = 0; i < 9; i++) blk[(int64_t)i * E + e] = mab[i];
-        for (int i = 0; i < 6; i++) blk[(int64_t)(9 + i) * E + e] = mbb[i];
-        for (int i = 0; i < 6; i++) maa[i] += (double)maa_b[i];
-    }
+    LaneAcc acc;
+    for (int i = 0; i < 6; i++) acc.maa[i] = 0.0;
+    acc.cnt = 0;
+    acc.qp = 0;
+    acc.hsum = 0;
+    const int64_t e0 = A.nbr_ptr[a], es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
+    for (int64_t e = e0 + lane; e < es; e += 32) pair_work<BALL, T, true>(A, sq[wib], a, ba, e, acc);
+    for (int64_t e = es + lane; e < e1; e += 32) pair_work<BALL, T, false>(A, sq[wib], a, ba, e, acc);
     for (int off = 16; off; off >>= 1) {
-        for (int i = 0; i < 6; i++) maa[i] += __shfl_xor_sync(0xffffffffu, maa[i], off);
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
-        qp += __shfl_xor_sync(0xffffffffu, qp, off);
-        hsum += __shfl_xor_sync(0xffffffffu, hsum, off);
+        for (int i = 0; i < 6; i++) acc.maa[i] += __shfl_xor_sync(0xffffffffu, acc.maa[i], off);
+        acc.cnt += __shfl_xor_sync(0xffffffffu, acc.cnt, off);
+        acc.qp += __shfl_xor_sync(0xffffffffu, acc.qp, off);
+        acc.hsum += __shfl_xor_sync(0xffffffffu, acc.hsum, off);
     }
     if (lane == 0) {
-        for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] = maa[i];
-        A.qp_a[a] = qp;
-        A.cnt_a[a] = cnt;
-        if (A.stats) A.hash_a[a] = hsum;
+        for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] = acc.maa[i];
+        A.qp_a[a] = acc.qp;
+        A.cnt_a[a] = acc.cnt;
+        if (A.stats) A.hash_a[a] = acc.hsum;
     }
 }
 

@@ -30,20 +30,22 @@ __device__ __forceinline__ int64_t find_slot(const int64_t *row_ptr, const int32
     return -1;
 }
 
-__device__ __forceinline__ bool in_list(const int32_t *idx, int64_t lo, int64_t hi, int v)
+__device__ __forceinline__ int64_t find_in(const int32_t *idx, int64_t lo, int64_t hi, int v)
 {
     hi -= 1;
     while (lo <= hi) {
         int64_t mid = (lo + hi) >> 1;
         int x = idx[mid];
-        if (x == v) return true;
+        if (x == v) return mid;
         if (x < v) lo = mid + 1; else hi = mid - 1;
     }
-    return false;
+    return -1;
 }
 
-// symmetric flag: pair (a, b) or (b, a) interacts; warp per a
-__global__ void k_symflag(int K, const int64_t *ptr, const int32_t *idx, const uint8_t *flag, uint8_t *sym)
+// symmetric flag: pair (a, b) or (b, a) interacts; warp per a.  Each candidate list
+// holds two sorted segments (interior, boundary) split at split[b].
+__global__ void k_symflag(int K, const int64_t *ptr, const int64_t *split, const int32_t *idx, const uint8_t *flag,
+                          uint8_t *sym)
 {
     int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (a >= K) return;
@@ -51,13 +53,9 @@ __global__ void k_symflag(int K, const int64_t *ptr, const int32_t *idx, const u
         int b = idx[e];
         uint8_t f = flag[e];
         if (!f) {
-            int64_t lo = ptr[b], hi = ptr[b + 1] - 1;
-            while (lo <= hi) {
-                int64_t mid = (lo + hi) >> 1;
-                int x = idx[mid];
-                if (x == a) { f = flag[mid]; break; }
-                if (x < a) lo = mid + 1; else hi = mid - 1;
-            }
+            int64_t m = find_in(idx, ptr[b], split[b], a);
+            if (m < 0) m = find_in(idx, split[b], ptr[b + 1], a);
+            if (m >= 0) f = flag[m];
         }
         sym[e] = f;
     }
@@ -265,7 +263,7 @@ nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     NL_CK(cudaMemsetAsync(ovf, 0, sizeof(int), ctx->stream));
     NL_CK(cudaMemsetAsync(st, 0, sizeof(unsigned long long) * 3, ctx->stream));
     const unsigned wgrid = (unsigned)(((int64_t)K * 32 + 255) / 256);
-    k_symflag<<<wgrid, 256, 0, ctx->stream>>>(K, P->nbr_ptr, P->nbr_idx, P->flag, sym); ++ctx->launches;
+    k_symflag<<<wgrid, 256, 0, ctx->stream>>>(K, P->nbr_ptr, P->nbr_split, P->nbr_idx, P->flag, sym); ++ctx->launches;
     k_node_count<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->tri, ncnt); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_scan_i64(ctx, ncnt, nptr, J)) != NL_OK) return s;

@@ -197,3 +197,37 @@ def test_errors(nl, ctx):
     with pytest.raises(nl.NlError) as e:
         nl.nl_assemble(ctx, nl.make_mesh(p.mesh, keep), cfg)
     assert e.value.status == nl.NL_EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_parity_bench_workload_full_size_sampled(nl, ctx, prec):
+    # the benchmark workload itself (32-gon, 96x96 jittered, K = 18432, 16-point outer rule),
+    # in the configuration bench.py times; the oracle computes sampled outputs one by one:
+    # interaction records of sampled outer triangles and complete rows of D at sampled nodes
+    p = I.problem("ngon32_96")
+    K, J = p.mesh.nt, p.mesh.nv
+    keep = nl._Keep()
+    mesh = nl.make_mesh(p.mesh, keep)
+    cfg = nl.config_of(p, keep, prec=prec)
+    h, c, q = nl.nl_interactions(ctx, mesh, cfg)
+    rng = np.random.default_rng(11)
+    a_list = np.unique(np.concatenate([rng.choice(K, 90, replace=False), [0, K - 1, K // 2, 97, 98, 4703]]))
+    out = O.assemble(p.mesh, oracle_cfg(p), a_list=a_list.astype(np.int32), want_hash=True)
+    np.testing.assert_array_equal(h[a_list], out["hash_a"][a_list])
+    np.testing.assert_array_equal(c[a_list], out["count_a"][a_list])
+    np.testing.assert_array_equal(q[a_list], out["qp_a"][a_list])
+    m = nl.nl_assemble(ctx, mesh, cfg)
+    try:
+        Dg = nl.to_scipy(ctx, m)
+    finally:
+        nl.nl_csr_free(ctx, m)
+    rows = np.array([0, 4704, J // 2, J - 1])
+    mask = np.zeros(J, np.uint8)
+    mask[rows] = 1
+    Dr = O.to_csr(O.assemble(p.mesh, oracle_cfg(p), row_mask=mask))
+    scale = np.abs(Dg.diagonal()).max()
+    for r in rows:
+        g_row, o_row = Dg[r], Dr[r]
+        o_row.sort_indices()
+        np.testing.assert_array_equal(g_row.indices, o_row.indices)
+        assert np.abs(g_row.data - o_row.data).max() <= TOL[prec] * scale
