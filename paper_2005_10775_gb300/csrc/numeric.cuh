@@ -184,7 +184,12 @@ __device__ __forceinline__ void whole_sums(const NumArgs &A, const D2 V[3], doub
     sums_zero(S);
     const bool inv = (A.kernel == NL_KERNEL_INV_DIST);
     const int n = A.inner.n;
-    const T ar = (T)area_b * (T)A.kc;
+    T ar = (T)area_b * (T)A.kc;
+    // Every (x_q, T_b) evaluates its inner points: for a constant kernel on a whole T_b
+    // they do not depend on x, and the opaque barrier keeps the compiler from hoisting
+    // them out of the outer-point loop (that hoist would skip counted work).
+    if (sizeof(T) == sizeof(float)) asm volatile("" : "+f"(*(float *)&ar));
+    else asm volatile("" : "+d"(*(double *)&ar));
     T lx[3], ly[3];
     if (inv)
         for (int i = 0; i < 3; i++) { lx[i] = (T)(V[i].x - x.x); ly[i] = (T)(V[i].y - x.y); }
@@ -340,137 +345,22 @@ struct LaneAcc {
     uint64_t hsum;
 };
 
-// One candidate pair (a, b): every outer point of T_a against T_b.  INTERIOR: the
-// region is certified whole for every outer point (no per-point classification).
-template <int BALL, typename T, bool INTERIOR>
-__device__ __forceinline__ void pair_work(const NumArgs &A, const OuterPt *sq, int a, const D2 &ba, int64_t e,
-                                          LaneAcc &acc)
+__device__ __forceinline__ void acc_zero(LaneAcc &acc)
 {
-    const int K = A.K;
-    const int b = A.nbr_idx[e];
-    D2 Vb[3];
-    for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
-    const D2 bb = {A.bx[b], A.by[b]};
-    const double area_b = A.area[b];
-    int q0 = 0, q1 = A.outer.n;
-    if (A.switch47) {
-        double dx = nlg::sub(ba.x, bb.x), dy = nlg::sub(ba.y, bb.y);
-        bool near4 = A.thr2 > 0.0 && nlg::add(nlg::mul(dx, dx), nlg::mul(dy, dy)) < A.thr2;
-        if (near4) q1 = A.outer.nsplit; else q0 = A.outer.nsplit;
-    }
-    T mab[9], mbb[6], maa_b[6];
-    for (int i = 0; i < 9; i++) mab[i] = 0;
-    for (int i = 0; i < 6; i++) { mbb[i] = 0; maa_b[i] = 0; }
-    bool any = false;
-    // T_b relative to bary_a in FP32 (rounded FP64 differences)
-    nlg::F2 vl[3];
-    nlg::F2 bl = {0.f, 0.f}, be1 = {0.f, 0.f}, be2 = {0.f, 0.f};
-    float binv = 0.f;
-    if (!INTERIOR) {
-        for (int i = 0; i < 3; i++) { vl[i].x = (float)(Vb[i].x - ba.x); vl[i].y = (float)(Vb[i].y - ba.y); }
-        bl.x = (float)(bb.x - ba.x);
-        bl.y = (float)(bb.y - ba.y);
-        be1.x = (float)(Vb[1].x - Vb[0].x); be1.y = (float)(Vb[1].y - Vb[0].y);
-        be2.x = (float)(Vb[2].x - Vb[0].x); be2.y = (float)(Vb[2].y - Vb[0].y);
-        binv = 1.f / (be1.x * be2.y - be2.x * be1.y);
-    }
-    for (int q = q0; q < q1; q++) {
-        const OuterPt o = sq[q];
-        const D2 x = {o.x, o.y};
-        Sums<T> S;
-        int64_t nq = 0;
-        int kind = nlg::KIND_WHOLE, nv = 3, ncap = 0;
-        if (INTERIOR) {
-            whole_sums<T>(A, Vb, area_b, x, S, nq);
-        } else {
-            nlg::F2 dl[3];
-            for (int i = 0; i < 3; i++) { dl[i].x = vl[i].x - o.lx; dl[i].y = vl[i].y - o.ly; }
-            int cls;
-            if (BALL == NL_BALL_BARYCENTER) {
-                float bx = bl.x - o.lx, by = bl.y - o.ly, r2 = bx * bx + by * by;
-                cls = r2 <= A.geo.b_in2 ? nlg::CLS_WHOLE : (r2 >= A.geo.b_out2 ? nlg::CLS_EMPTY : nlg::CLS_EXACT);
-            } else if (BALL == NL_BALL_OVERLAP) {
-                float r0 = dl[0].x * dl[0].x + dl[0].y * dl[0].y, r1 = dl[1].x * dl[1].x + dl[1].y * dl[1].y;
-                float r2 = dl[2].x * dl[2].x + dl[2].y * dl[2].y;
-                if (fminf(r0, fminf(r1, r2)) <= A.geo.rin_m2) cls = nlg::CLS_WHOLE;
-                else if (nlg::dist2_origin_triangle(dl) > A.geo.rout_p2) cls = nlg::CLS_EMPTY;
-                else cls = nlg::CLS_EXACT;
-            } else {
-                cls = nlg::classify_vertices(dl, A.geo.rin_m2, A.geo.rout_p2);
-            }
-            if (cls == nlg::CLS_EMPTY) continue;
-            nlg::F2 P32[NL_MAXV];
-            int n32 = -1, ovf32 = 0;
-            bool cut32 = false;
-            if (cls == nlg::CLS_WHOLE && A.kernel == NL_KERNEL_INV_DIST) {
-                // the singular kernel needs the near-field test even on whole triangles
-                nlg::Region R;
-                R.kind = nlg::KIND_WHOLE;
-                R.nv = 3;
-                R.ncap = 0;
-                R.P[0] = Vb[0]; R.P[1] = Vb[1]; R.P[2] = Vb[2];
-                inner_sums<T>(A, R, Vb, area_b, x, S, nq);
-            } else if (cls == nlg::CLS_WHOLE) {
-                whole_sums<T>(A, Vb, area_b, x, S, nq);
-            } else if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON && A.kernel == NL_KERNEL_CONST &&
-                       (n32 = nlg::clip_ngon_f32(dl, A.geo.err0, A.geo, P32, &cut32, &ovf32)) >= 0) {
-                // certified FP32 clip: same vertex count and kind as the FP64 clip
-                if (n32 < 3) continue;
-                kind = cut32 ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
-                nv = n32;
-                if (!cut32) whole_sums<T>(A, Vb, area_b, x, S, nq);
-                else poly_sums_f32(A, P32, n32, dl[0], be1, be2, binv, *(Sums<float> *)&S, nq);
-            } else {
-                if (ovf32) atomicOr(A.err, 1);
-                nlg::Region R;
-                nlg::make_region<BALL>(Vb, dl, bb, x, A.geo, R);
-                if (R.overflow) atomicOr(A.err, 1);
-                if (R.kind == nlg::KIND_NONE) continue;
-                kind = R.kind;
-                nv = R.nv;
-                ncap = R.ncap;
-                if (R.kind == nlg::KIND_WHOLE && R.ncap == 0 && A.kernel != NL_KERNEL_INV_DIST)
-                    whole_sums<T>(A, Vb, area_b, x, S, nq);
-                else
-                    inner_sums<T>(A, R, Vb, area_b, x, S, nq);
-            }
-        }
-        any = true;
-        const T W = (T)o.W, la0 = (T)o.l0, la1 = (T)o.l1, la2 = (T)o.l2;
-        mbb[0] += W * S.S2[0]; mbb[1] += W * S.S2[1]; mbb[2] += W * S.S2[2];
-        mbb[3] += W * S.S2[3]; mbb[4] += W * S.S2[4]; mbb[5] += W * S.S2[5];
-        const T wa0 = W * la0, wa1 = W * la1, wa2 = W * la2;
-        mab[0] += wa0 * S.s1[0]; mab[1] += wa0 * S.s1[1]; mab[2] += wa0 * S.s1[2];
-        mab[3] += wa1 * S.s1[0]; mab[4] += wa1 * S.s1[1]; mab[5] += wa1 * S.s1[2];
-        mab[6] += wa2 * S.s1[0]; mab[7] += wa2 * S.s1[1]; mab[8] += wa2 * S.s1[2];
-        const T ws = W * S.s0;
-        maa_b[0] += ws * la0 * la0; maa_b[1] += ws * la1 * la1; maa_b[2] += ws * la2 * la2;
-        maa_b[3] += ws * la0 * la1; maa_b[4] += ws * la0 * la2; maa_b[5] += ws * la1 * la2;
-        acc.cnt++;
-        acc.qp += nq;
-        if (A.stats) acc.hsum += nlg::record_hash(a, b, q - q0, kind, nv, ncap);
-    }
-    A.flag[e] = any ? 1 : 0;
-    T *blk = (T *)A.blk;
-    const int64_t E = A.E;
-    for (int i = 0; i < 9; i++) blk[(int64_t)i * E + e] = mab[i];
-    for (int i = 0; i < 6; i++) blk[(int64_t)(9 + i) * E + e] = mbb[i];
-    for (int i = 0; i < 6; i++) acc.maa[i] += (double)maa_b[i];
+    for (int i = 0; i < 6; i++) acc.maa[i] = 0.0;
+    acc.cnt = 0;
+    acc.qp = 0;
+    acc.hsum = 0;
 }
 
-template <int BALL, typename T>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_numeric(const NumArgs A)
+// outer points of T_a in shared memory (computed by the warp's lanes)
+__device__ __forceinline__ void stage_outer(const NumArgs &A, int a, OuterPt *sq, int lane)
 {
-    __shared__ OuterPt sq[kWarpsPerBlock][NL_MAXQ + 8];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int a = blockIdx.x * kWarpsPerBlock + wib;
-    if (a >= A.K) return;
     const int K = A.K;
     D2 Va[3];
     for (int i = 0; i < 3; i++) { Va[i].x = A.tx[i * K + a]; Va[i].y = A.ty[i * K + a]; }
     const double area_a = A.area[a];
-    const int nq_all = A.outer.n;
-    for (int q = lane; q < nq_all; q += 32) {
+    for (int q = lane; q < A.outer.n; q += 32) {
         double l0 = A.outer.l[q][0], l1 = A.outer.l[q][1], l2 = A.outer.l[q][2];
         OuterPt o;
         // x_q = l0 v0 + l1 v1 + l2 v2, left to right, round-to-nearest
@@ -480,29 +370,303 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_numeric(const NumArgs A
         o.l0 = l0; o.l1 = l1; o.l2 = l2;
         o.lx = (float)(o.x - A.bx[a]);
         o.ly = (float)(o.y - A.by[a]);
-        sq[wib][q] = o;
+        sq[q] = o;
     }
     __syncwarp();
-    const D2 ba = {A.bx[a], A.by[a]};
-    LaneAcc acc;
-    for (int i = 0; i < 6; i++) acc.maa[i] = 0.0;
-    acc.cnt = 0;
-    acc.qp = 0;
-    acc.hsum = 0;
-    const int64_t e0 = A.nbr_ptr[a], es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
-    for (int64_t e = e0 + lane; e < es; e += 32) pair_work<BALL, T, true>(A, sq[wib], a, ba, e, acc);
-    for (int64_t e = es + lane; e < e1; e += 32) pair_work<BALL, T, false>(A, sq[wib], a, ba, e, acc);
+}
+
+// rule range of the pair (outer-rule switch of Sec. 8)
+__device__ __forceinline__ void rule_range(const NumArgs &A, const D2 &ba, const D2 &bb, int &q0, int &q1)
+{
+    q0 = 0;
+    q1 = A.outer.n;
+    if (A.switch47) {
+        double dx = nlg::sub(ba.x, bb.x), dy = nlg::sub(ba.y, bb.y);
+        bool near4 = A.thr2 > 0.0 && nlg::add(nlg::mul(dx, dx), nlg::mul(dy, dy)) < A.thr2;
+        if (near4) q1 = A.outer.nsplit; else q0 = A.outer.nsplit;
+    }
+}
+
+// the per-(q, b) outer combination: M_bb += W S2, M_ab += W phi_a s1^T, M_aa += W s0 phi_a phi_a^T
+template <typename T>
+__device__ __forceinline__ void combine(const OuterPt &o, const Sums<T> &S, T *v)
+{
+    const T W = (T)o.W, la0 = (T)o.l0, la1 = (T)o.l1, la2 = (T)o.l2;
+    const T wa0 = W * la0, wa1 = W * la1, wa2 = W * la2;
+    v[0] += wa0 * S.s1[0]; v[1] += wa0 * S.s1[1]; v[2] += wa0 * S.s1[2];
+    v[3] += wa1 * S.s1[0]; v[4] += wa1 * S.s1[1]; v[5] += wa1 * S.s1[2];
+    v[6] += wa2 * S.s1[0]; v[7] += wa2 * S.s1[1]; v[8] += wa2 * S.s1[2];
+    v[9] += W * S.S2[0]; v[10] += W * S.S2[1]; v[11] += W * S.S2[2];
+    v[12] += W * S.S2[3]; v[13] += W * S.S2[4]; v[14] += W * S.S2[5];
+    const T ws = W * S.s0;
+    v[15] += ws * la0 * la0; v[16] += ws * la1 * la1; v[17] += ws * la2 * la2;
+    v[18] += ws * la0 * la1; v[19] += ws * la0 * la2; v[20] += ws * la1 * la2;
+}
+
+template <typename T>
+__device__ __forceinline__ void write_pair(const NumArgs &A, int64_t e, bool any, const T *v, LaneAcc &acc)
+{
+    A.flag[e] = any ? 1 : 0;
+    T *blk = (T *)A.blk;
+    for (int i = 0; i < 15; i++) blk[(int64_t)i * A.E + e] = v[i];
+    for (int i = 0; i < 6; i++) acc.maa[i] += (double)v[15 + i];
+}
+
+__device__ __forceinline__ void warp_reduce(LaneAcc &acc)
+{
     for (int off = 16; off; off >>= 1) {
         for (int i = 0; i < 6; i++) acc.maa[i] += __shfl_xor_sync(0xffffffffu, acc.maa[i], off);
         acc.cnt += __shfl_xor_sync(0xffffffffu, acc.cnt, off);
         acc.qp += __shfl_xor_sync(0xffffffffu, acc.qp, off);
         acc.hsum += __shfl_xor_sync(0xffffffffu, acc.hsum, off);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Interior pairs: T_b is whole for every outer point of T_a (certified when the
+// candidate lists are built), so there is no per-point classification.  Runs first
+// and initialises the per-triangle M_aa and statistics.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_interior(const NumArgs A)
+{
+    __shared__ OuterPt sq_all[kWarpsPerBlock][NL_MAXQ + 8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int a = blockIdx.x * kWarpsPerBlock + wib;
+    if (a >= A.K) return;
+    const int K = A.K;
+    OuterPt *sq = sq_all[wib];
+    stage_outer(A, a, sq, lane);
+    const D2 ba = {A.bx[a], A.by[a]};
+    LaneAcc acc;
+    acc_zero(acc);
+    const int64_t e0 = A.nbr_ptr[a], es = A.nbr_split[a];
+    for (int64_t e = e0 + lane; e < es; e += 32) {
+        const int b = A.nbr_idx[e];
+        D2 Vb[3];
+        for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
+        const D2 bb = {A.bx[b], A.by[b]};
+        const double area_b = A.area[b];
+        int q0, q1;
+        rule_range(A, ba, bb, q0, q1);
+        T v[21];
+        for (int i = 0; i < 21; i++) v[i] = 0;
+        for (int q = q0; q < q1; q++) {
+            const OuterPt o = sq[q];
+            Sums<T> S;
+            int64_t nq = 0;
+            whole_sums<T>(A, Vb, area_b, D2{o.x, o.y}, S, nq);
+            combine<T>(o, S, v);
+            acc.cnt++;
+            acc.qp += nq;
+            if (A.stats) acc.hsum += nlg::record_hash(a, b, q - q0, nlg::KIND_WHOLE, 3, 0);
+        }
+        write_pair<T>(A, e, q1 > q0, v, acc);
+    }
+    warp_reduce(acc);
     if (lane == 0) {
         for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] = acc.maa[i];
         A.qp_a[a] = acc.qp;
         A.cnt_a[a] = acc.cnt;
         if (A.stats) A.hash_a[a] = acc.hsum;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary pairs.  32 candidates at a time (one per lane): every (q, b) is classified
+// in FP32 in lockstep, whole ones are integrated in place, undecided ones go to a warp
+// queue that all 32 lanes then drain together (geometry + quadrature), adding their
+// blocks into the owner lane's shared accumulators.
+// ---------------------------------------------------------------------------
+struct CandData {
+    double vx[3], vy[3];
+    double bbx, bby, area;
+    float vlx[3], vly[3];      // T_b relative to bary_a
+    float blx, bly;            // bary_b relative to bary_a
+    float e1x, e1y, e2x, e2y, binv;
+    int b, q0;
+};
+
+template <typename T>
+struct BoundaryShared {
+    OuterPt sq[NL_MAXQ + 8];
+    CandData cand[32];
+    T acc[32][22];             // 21 block values and the non-empty flag of each lane's pair
+    unsigned short queue[32 * (NL_MAXQ + 8)];
+};
+
+template <int BALL, typename T>
+__device__ __forceinline__ int classify_item(const NumArgs &A, const CandData &c, const OuterPt &o, nlg::F2 dl[3])
+{
+    for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
+    if (BALL == NL_BALL_BARYCENTER) {
+        float bx = c.blx - o.lx, by = c.bly - o.ly, r2 = bx * bx + by * by;
+        return r2 <= A.geo.b_in2 ? nlg::CLS_WHOLE : (r2 >= A.geo.b_out2 ? nlg::CLS_EMPTY : nlg::CLS_EXACT);
+    }
+    if (BALL == NL_BALL_OVERLAP) {
+        float r0 = dl[0].x * dl[0].x + dl[0].y * dl[0].y, r1 = dl[1].x * dl[1].x + dl[1].y * dl[1].y;
+        float r2 = dl[2].x * dl[2].x + dl[2].y * dl[2].y;
+        if (fminf(r0, fminf(r1, r2)) <= A.geo.rin_m2) return nlg::CLS_WHOLE;
+        if (nlg::dist2_origin_triangle(dl) > A.geo.rout_p2) return nlg::CLS_EMPTY;
+        return nlg::CLS_EXACT;
+    }
+    return nlg::classify_vertices(dl, A.geo.rin_m2, A.geo.rout_p2);
+}
+
+// one undecided (q, b): build the region exactly as the FP64 geometry would and integrate it
+template <int BALL, typename T>
+__device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
+                                           int64_t &nq, int &kind, int &nv, int &ncap)
+{
+    nlg::F2 dl[3];
+    for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
+    const D2 Vb[3] = {{c.vx[0], c.vy[0]}, {c.vx[1], c.vy[1]}, {c.vx[2], c.vy[2]}};
+    const D2 x = {o.x, o.y};
+    kind = nlg::KIND_WHOLE;
+    nv = 3;
+    ncap = 0;
+    if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON && A.kernel == NL_KERNEL_CONST) {
+        nlg::F2 P32[NL_MAXV];
+        bool cut = false;
+        int ovf = 0;
+        int n = nlg::clip_ngon_f32(dl, A.geo.err0, A.geo, P32, &cut, &ovf);
+        if (ovf) atomicOr(A.err, 1);
+        if (n >= 0) {
+            // certified FP32 clip: same vertex count and kind as the FP64 clip
+            if (n < 3) return false;
+            kind = cut ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
+            nv = n;
+            if (!cut) {
+                whole_sums<T>(A, Vb, c.area, x, S, nq);
+            } else {
+                const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
+                poly_sums_f32(A, P32, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
+            }
+            return true;
+        }
+    }
+    nlg::Region R;
+    const D2 bb = {c.bbx, c.bby};
+    nlg::make_region<BALL>(Vb, dl, bb, x, A.geo, R);
+    if (R.overflow) atomicOr(A.err, 1);
+    if (R.kind == nlg::KIND_NONE) return false;
+    kind = R.kind;
+    nv = R.nv;
+    ncap = R.ncap;
+    if (R.kind == nlg::KIND_WHOLE && R.ncap == 0 && A.kernel != NL_KERNEL_INV_DIST)
+        whole_sums<T>(A, Vb, c.area, x, S, nq);
+    else
+        inner_sums<T>(A, R, Vb, c.area, x, S, nq);
+    return true;
+}
+
+template <int BALL, typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BoundaryShared<T> &sh = ((BoundaryShared<T> *)smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int a = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (a >= A.K) return;
+    const int K = A.K;
+    stage_outer(A, a, sh.sq, lane);
+    const D2 ba = {A.bx[a], A.by[a]};
+    LaneAcc acc;
+    acc_zero(acc);
+    const int64_t es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
+    const int nq_all = A.outer.n;
+    const bool inv = (A.kernel == NL_KERNEL_INV_DIST);
+    for (int64_t base = es; base < e1; base += 32) {
+        const int64_t e = base + lane;
+        const bool valid = e < e1;
+        int q0 = 0, q1 = 0;
+        CandData c;
+        if (valid) {
+            const int b = A.nbr_idx[e];
+            c.b = b;
+            for (int i = 0; i < 3; i++) { c.vx[i] = A.tx[i * K + b]; c.vy[i] = A.ty[i * K + b]; }
+            c.bbx = A.bx[b];
+            c.bby = A.by[b];
+            c.area = A.area[b];
+            for (int i = 0; i < 3; i++) { c.vlx[i] = (float)(c.vx[i] - ba.x); c.vly[i] = (float)(c.vy[i] - ba.y); }
+            c.blx = (float)(c.bbx - ba.x);
+            c.bly = (float)(c.bby - ba.y);
+            c.e1x = (float)(c.vx[1] - c.vx[0]); c.e1y = (float)(c.vy[1] - c.vy[0]);
+            c.e2x = (float)(c.vx[2] - c.vx[0]); c.e2y = (float)(c.vy[2] - c.vy[0]);
+            c.binv = 1.f / (c.e1x * c.e2y - c.e2x * c.e1y);
+            rule_range(A, ba, D2{c.bbx, c.bby}, q0, q1);
+            c.q0 = q0;
+            sh.cand[lane] = c;
+        }
+        for (int i = 0; i < 22; i++) sh.acc[lane][i] = 0;
+        T v[21];
+        for (int i = 0; i < 21; i++) v[i] = 0;
+        bool any = false;
+        int nqueue = 0;
+        __syncwarp();
+        // phase 1: classify every (q, b) in lockstep; whole ones are integrated here
+        for (int q = 0; q < nq_all; q++) {
+            const bool active = valid && q >= q0 && q < q1;
+            int cls = nlg::CLS_EMPTY;
+            if (active) {
+                nlg::F2 dl[3];
+                cls = classify_item<BALL, T>(A, c, sh.sq[q], dl);
+                // the singular kernel needs the near-field test: whole items go to the queue too
+                if (inv && cls == nlg::CLS_WHOLE) cls = nlg::CLS_EXACT;
+            }
+            if (cls == nlg::CLS_WHOLE) {
+                const OuterPt o = sh.sq[q];
+                const D2 Vb[3] = {{c.vx[0], c.vy[0]}, {c.vx[1], c.vy[1]}, {c.vx[2], c.vy[2]}};
+                Sums<T> S;
+                int64_t nq = 0;
+                whole_sums<T>(A, Vb, c.area, D2{o.x, o.y}, S, nq);
+                combine<T>(o, S, v);
+                any = true;
+                acc.cnt++;
+                acc.qp += nq;
+                if (A.stats) acc.hsum += nlg::record_hash(a, c.b, q - q0, nlg::KIND_WHOLE, 3, 0);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, cls == nlg::CLS_EXACT);
+            if (cls == nlg::CLS_EXACT) sh.queue[nqueue + __popc(m & ((1u << lane) - 1u))] =
+                (unsigned short)((lane << 8) | q);
+            nqueue += __popc(m);
+        }
+        __syncwarp();
+        // phase 2: drain the queue with all lanes
+        for (int i = lane; i < nqueue; i += 32) {
+            const unsigned it = sh.queue[i];
+            const int own = it >> 8, q = it & 0xff;
+            const CandData &cd = sh.cand[own];
+            const OuterPt o = sh.sq[q];
+            Sums<T> S;
+            int64_t nq = 0;
+            int kind, nv, ncap;
+            if (!exact_item<BALL, T>(A, cd, o, S, nq, kind, nv, ncap)) continue;
+            T w[21];
+            for (int k = 0; k < 21; k++) w[k] = 0;
+            combine<T>(o, S, w);
+            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[own][k], w[k]);
+            sh.acc[own][21] = (T)1;
+            acc.cnt++;
+            acc.qp += nq;
+            if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
+        }
+        __syncwarp();
+        // phase 3: owners merge the queue's contributions and write their pair
+        if (valid) {
+            for (int k = 0; k < 21; k++) v[k] += sh.acc[lane][k];
+            any = any || (sh.acc[lane][21] != (T)0);
+            write_pair<T>(A, e, any, v, acc);
+        }
+        __syncwarp();
+    }
+    warp_reduce(acc);
+    if (lane == 0) {
+        // k_interior has written this triangle's values; add in stream order (deterministic)
+        for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] += acc.maa[i];
+        A.qp_a[a] += acc.qp;
+        A.cnt_a[a] += acc.cnt;
+        if (A.stats) A.hash_a[a] += acc.hsum;
     }
 }
 

@@ -1,19 +1,36 @@
-// numeric_f64.cu -- instantiation of the pair geometry + quadrature kernel with double quadrature.
+// numeric_f64.cu -- instantiation of the pair geometry + quadrature kernels with double quadrature.
 #include "numeric.cuh"
+
+namespace {
+
+template <int BALL>
+nl_status launch_boundary(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads)
+{
+    const size_t smem = sizeof(nlq::BoundaryShared<double>) * nlq::kWarpsPerBlock;
+    NL_CK(cudaFuncSetAttribute(nlq::k_boundary<BALL, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    nlq::k_boundary<BALL, double><<<grid, threads, smem, ctx->stream>>>(A); ++ctx->launches;
+    return NL_OK;
+}
+
+}  // namespace
 
 nl_status nl_launch_numeric_f64(nl_ctx *ctx, const nlq::NumArgs &A, int ball)
 {
     const unsigned grid = (unsigned)((A.K + nlq::kWarpsPerBlock - 1) / nlq::kWarpsPerBlock);
     const unsigned threads = nlq::kWarpsPerBlock * 32;
+    nlq::k_interior<double><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    nl_status s;
     switch (ball) {
-    case NL_BALL_BARYCENTER: nlq::k_numeric<NL_BALL_BARYCENTER, double><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches; break;
-    case NL_BALL_NOCAPS: nlq::k_numeric<NL_BALL_NOCAPS, double><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches; break;
-    case NL_BALL_APPROXCAPS: nlq::k_numeric<NL_BALL_APPROXCAPS, double><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches; break;
-    case NL_BALL_EXACTCAPS: nlq::k_numeric<NL_BALL_EXACTCAPS, double><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches; break;
-    case NL_BALL_NGON: nlq::k_numeric<NL_BALL_NGON, double><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches; break;
-    case NL_BALL_OVERLAP: nlq::k_numeric<NL_BALL_OVERLAP, double><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches; break;
+    case NL_BALL_BARYCENTER: s = launch_boundary<NL_BALL_BARYCENTER>(ctx, A, grid, threads); break;
+    case NL_BALL_NOCAPS: s = launch_boundary<NL_BALL_NOCAPS>(ctx, A, grid, threads); break;
+    case NL_BALL_APPROXCAPS: s = launch_boundary<NL_BALL_APPROXCAPS>(ctx, A, grid, threads); break;
+    case NL_BALL_EXACTCAPS: s = launch_boundary<NL_BALL_EXACTCAPS>(ctx, A, grid, threads); break;
+    case NL_BALL_NGON: s = launch_boundary<NL_BALL_NGON>(ctx, A, grid, threads); break;
+    case NL_BALL_OVERLAP: s = launch_boundary<NL_BALL_OVERLAP>(ctx, A, grid, threads); break;
     default: return nl_fail(ctx, NL_EINVAL, "unknown ball mode");
     }
+    if (s != NL_OK) return s;
     NL_CK(cudaGetLastError());
     return NL_OK;
 }
