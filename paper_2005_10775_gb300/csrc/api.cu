@@ -238,6 +238,10 @@ nl_status fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
             reg = fabs(o[2 * k] - R * cos(th)) <= 1e-12 * R && fabs(o[2 * k + 1] - R * sin(th)) <= 1e-12 * R;
         }
         A.geo.regular = reg ? 1 : 0;
+        double m1 = 0.0;
+        for (int k = 0; k < N; k++) m1 = fmax(m1, fabs(o[2 * k]) + fabs(o[2 * k + 1]));
+        A.geo.r2 = (float)(2.0 * m1);
+        A.geo.o1max = (float)m1;
         A.geo.sector = (float)(2.0 * M_PI / N);
         A.geo.rin_tau = (float)(rin - tau);
     }

@@ -64,6 +64,8 @@ struct GeoParams {
     float mk[64];         // |e_k| tau: margin of the FP32 orientation test of pass k
     float err0;           // bound on |dl - (v - x)| of the FP32 local coordinates
     int regular;          // offsets form the regular polygon R (cos 2 pi k / N, sin 2 pi k / N)
+    float r2;             // 2 max_k |o_k|_1
+    float o1max;          // max_k |o_k|_1
     float sector, rin_tau; // 2 pi / N; inradius - tau
 };
 
@@ -479,7 +481,8 @@ __device__ __forceinline__ int clip_ngon_f32(const F2 dl[3], float err0, const G
         for (int i = 0; i < n; i++) {
             const float rx = A[i].x - ox, ry = A[i].y - oy;
             o[i] = ex * ry - ey * rx;
-            u[i] = el * (eA[i] + kEps * (fabsf(rx) + fabsf(ry) + fabsf(A[i].x) + fabsf(A[i].y)));
+            // |rx| + |ry| <= |A|_1 + |o_k|_1 <= |A|_1 + 2 R: a pass-independent rounding allowance
+            u[i] = el * (eA[i] + kEps * (2.f * (fabsf(A[i].x) + fabsf(A[i].y)) + g.r2));
             if (!(fabsf(o[i]) > u[i])) return -1;
             all_in = all_in && (o[i] > 0.f);
         }
@@ -516,6 +519,89 @@ __device__ __forceinline__ int clip_ngon_f32(const F2 dl[3], float err0, const G
         for (int i = 0; i < n; i++) { A[i] = B[i]; eA[i] = eB[i]; }
     }
     for (int i = 0; i < n; i++) out[i] = A[i];
+    return n;
+}
+
+// The same certified FP32 clip with its two vertex buffers in shared memory (one
+// column per lane, [slot][lane]: no bank conflicts) and a capacity of kClipCap
+// vertices (a triangle cut kClipCap - 3 times); more vertices return -1 and the
+// caller takes the FP64 clip.  Orientations are recomputed instead of stored.
+//
+// Error bound of o = e x (a - o_k) evaluated in FP32 (u = 2^-24), against the same
+// expression on the FP64 vertex A*, offset O* and edge E*:
+//   |o - E* x (A* - O*)| <= |e| (|a - A*| + |o_k - O*| + 1.5 u |a - o_k|_1 + 3 u |a - o_k|_1)
+//                        <= |e| (err_a + 1.5 u |o_k|_1 + 4.5 u |r|_1),   r = a - o_k.
+// The test uses twice that: |e| (err_a + 3 u |o_k|_1 + 9 u |r|_1).
+constexpr int kClipCap = 8;
+
+struct ClipBuf {
+    float x[2][kClipCap][32], y[2][kClipCap][32], e[2][kClipCap][32];
+};
+
+__device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, const GeoParams &g, ClipBuf &cb,
+                                                int lane, int *which, bool *cut)
+{
+    const float kU9 = 9.0f * 5.9604645e-8f;    // 9 u
+    const float kU3o = 3.0f * 5.9604645e-8f * g.o1max;   // 3 u max_k |o_k|_1
+    int cur = 0, n = 3;
+    for (int i = 0; i < 3; i++) {
+        cb.x[0][i][lane] = dl[i].x;
+        cb.y[0][i][lane] = dl[i].y;
+        cb.e[0][i][lane] = err0;
+    }
+    *cut = false;
+    uint64_t mask = ngon_pass_mask(dl, g);
+    while (mask && n > 0) {
+        const int k = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        const float ox = g.of[k][0], oy = g.of[k][1], ex = g.ef[k][0], ey = g.ef[k][1];
+        const float el = g.mk[k] / g.tau;   // |e_k|
+        bool all_in = true;
+        for (int i = 0; i < n; i++) {
+            const float rx = cb.x[cur][i][lane] - ox, ry = cb.y[cur][i][lane] - oy;
+            const float o = ex * ry - ey * rx;
+            const float u = el * (cb.e[cur][i][lane] + kU3o + kU9 * (fabsf(rx) + fabsf(ry)));
+            if (!(fabsf(o) > u)) return -1;
+            all_in = all_in && (o > 0.f);
+        }
+        if (all_in) continue;
+        *cut = true;
+        const int nxt = cur ^ 1;
+        int m = 0;
+        float sx = cb.x[cur][n - 1][lane], sy = cb.y[cur][n - 1][lane], se = cb.e[cur][n - 1][lane];
+        float so = ex * (sy - oy) - ey * (sx - ox);
+        float su = el * (se + kU3o + kU9 * (fabsf(sx - ox) + fabsf(sy - oy)));
+        for (int i = 0; i < n; i++) {
+            const float px = cb.x[cur][i][lane], py = cb.y[cur][i][lane], pe = cb.e[cur][i][lane];
+            const float po = ex * (py - oy) - ey * (px - ox);
+            const float pu = el * (pe + kU3o + kU9 * (fabsf(px - ox) + fabsf(py - oy)));
+            const bool p_in = po > 0.f, s_in = so > 0.f;
+            if (p_in != s_in) {
+                if (m >= kClipCap) return -1;
+                const float t = so / (so - po);
+                const float dx = px - sx, dy = py - sy;
+                const float den = fabsf(so) + fabsf(po) - su - pu;
+                const float len = fabsf(dx) + fabsf(dy);
+                cb.x[nxt][m][lane] = sx + t * dx;
+                cb.y[nxt][m][lane] = sy + t * dy;
+                // p = s + t (q - s): interpolated error, the error of t times |q - s|, and rounding
+                cb.e[nxt][m][lane] = fmaxf(se, pe) + len * (su + pu) / den +
+                                     4.f * 5.9604645e-8f * (fabsf(sx) + fabsf(sy) + len);
+                m++;
+            }
+            if (p_in) {
+                if (m >= kClipCap) return -1;
+                cb.x[nxt][m][lane] = px;
+                cb.y[nxt][m][lane] = py;
+                cb.e[nxt][m][lane] = pe;
+                m++;
+            }
+            sx = px; sy = py; se = pe; so = po; su = pu;
+        }
+        cur = nxt;
+        n = m;
+    }
+    *which = cur;
     return n;
 }
 

@@ -178,13 +178,13 @@ __device__ __forceinline__ T rule_w(const NumArgs &A, int r)
 
 // inner sums over the whole triangle T_b: phi_b at the rule points are the rule's barycentrics
 template <typename T>
-__device__ __forceinline__ void whole_sums(const NumArgs &A, const D2 V[3], double area_b, D2 x, Sums<T> &S,
+__device__ __forceinline__ void whole_sums(const NumArgs &A, const D2 V[3], T area_kc, D2 x, Sums<T> &S,
                                            int64_t &nqp)
 {
     sums_zero(S);
     const bool inv = (A.kernel == NL_KERNEL_INV_DIST);
     const int n = A.inner.n;
-    T ar = (T)area_b * (T)A.kc;
+    T ar = area_kc;
     // Every (x_q, T_b) evaluates its inner points: for a constant kernel on a whole T_b
     // they do not depend on x, and the opaque barrier keeps the compiler from hoisting
     // them out of the outer-point loop (that hoist would skip counted work).
@@ -331,9 +331,49 @@ __device__ __forceinline__ void poly_sums_f32(const NumArgs &A, const nlg::F2 *P
     }
 }
 
+// inner sums over a fanned polygon held in a shared clip buffer (FP32 path)
+__device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBuf &cb, int which, int lane, int n,
+                                             const nlg::F2 &d0, const nlg::F2 &e1, const nlg::F2 &e2, float inv_det,
+                                             Sums<float> &S, int64_t &nqp)
+{
+    sums_zero(S);
+    const int nr = A.inner.n;
+    const float kc = (float)A.kc;
+    auto phi = [&](float px, float py, float f[3]) {
+        const float rx = px - d0.x, ry = py - d0.y;
+        const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
+        const float l2 = (e1.x * ry - rx * e1.y) * inv_det;
+        f[0] = 1.f - l1 - l2;
+        f[1] = l1;
+        f[2] = l2;
+    };
+    const float x0 = cb.x[which][0][lane], y0 = cb.y[which][0][lane];
+    float xk = cb.x[which][1][lane], yk = cb.y[which][1][lane];
+    float f0[3], fk[3];
+    phi(x0, y0, f0);
+    phi(xk, yk, fk);
+    for (int k = 1; k + 1 < n; k++) {
+        const float xn = cb.x[which][k + 1][lane], yn = cb.y[which][k + 1][lane];
+        const float ar = 0.5f * fabsf((xk - x0) * (yn - y0) - (xn - x0) * (yk - y0)) * kc;
+        float fn[3];
+        phi(xn, yn, fn);
+        for (int r = 0; r < nr; r++) {
+            const float m0 = A.fin_l[r][0], m1 = A.fin_l[r][1], m2 = A.fin_l[r][2];
+            const float p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
+            const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
+            const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
+            sums_add<float>(S, A.fin_w[r] * ar, p0, p1, p2);
+        }
+        nqp += nr;
+        fk[0] = fn[0]; fk[1] = fn[1]; fk[2] = fn[2];
+        xk = xn; yk = yn;
+    }
+}
+
 struct OuterPt {
     double x, y, W, l0, l1, l2;
     float lx, ly;     // x_q - bary_a in FP32
+    float Wf, l0f, l1f, l2f;   // FP32 copies (no FP64 conversions in the FP32 path)
 };
 
 constexpr int kWarpsPerBlock = 4;
@@ -370,6 +410,8 @@ __device__ __forceinline__ void stage_outer(const NumArgs &A, int a, OuterPt *sq
         o.l0 = l0; o.l1 = l1; o.l2 = l2;
         o.lx = (float)(o.x - A.bx[a]);
         o.ly = (float)(o.y - A.by[a]);
+        o.Wf = (float)o.W;
+        o.l0f = (float)l0; o.l1f = (float)l1; o.l2f = (float)l2;
         sq[q] = o;
     }
     __syncwarp();
@@ -391,7 +433,9 @@ __device__ __forceinline__ void rule_range(const NumArgs &A, const D2 &ba, const
 template <typename T>
 __device__ __forceinline__ void combine(const OuterPt &o, const Sums<T> &S, T *v)
 {
-    const T W = (T)o.W, la0 = (T)o.l0, la1 = (T)o.l1, la2 = (T)o.l2;
+    const bool f32 = sizeof(T) == sizeof(float);
+    const T W = f32 ? (T)o.Wf : (T)o.W, la0 = f32 ? (T)o.l0f : (T)o.l0;
+    const T la1 = f32 ? (T)o.l1f : (T)o.l1, la2 = f32 ? (T)o.l2f : (T)o.l2;
     const T wa0 = W * la0, wa1 = W * la1, wa2 = W * la2;
     v[0] += wa0 * S.s1[0]; v[1] += wa0 * S.s1[1]; v[2] += wa0 * S.s1[2];
     v[3] += wa1 * S.s1[0]; v[4] += wa1 * S.s1[1]; v[5] += wa1 * S.s1[2];
@@ -447,6 +491,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_interior(const NumArgs 
         for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
         const D2 bb = {A.bx[b], A.by[b]};
         const double area_b = A.area[b];
+        const T akc = (T)(area_b * A.kc);
         int q0, q1;
         rule_range(A, ba, bb, q0, q1);
         T v[21];
@@ -455,7 +500,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_interior(const NumArgs 
             const OuterPt o = sq[q];
             Sums<T> S;
             int64_t nq = 0;
-            whole_sums<T>(A, Vb, area_b, D2{o.x, o.y}, S, nq);
+            whole_sums<T>(A, Vb, akc, D2{o.x, o.y}, S, nq);
             combine<T>(o, S, v);
             acc.cnt++;
             acc.qp += nq;
@@ -480,7 +525,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_interior(const NumArgs 
 // ---------------------------------------------------------------------------
 struct CandData {
     double vx[3], vy[3];
-    double bbx, bby, area;
+    double bbx, bby, area, akc;    // area and area * kernel constant
     float vlx[3], vly[3];      // T_b relative to bary_a
     float blx, bly;            // bary_b relative to bary_a
     float e1x, e1y, e2x, e2y, binv;
@@ -492,7 +537,9 @@ struct BoundaryShared {
     OuterPt sq[NL_MAXQ + 8];
     CandData cand[32];
     T acc[32][22];             // 21 block values and the non-empty flag of each lane's pair
-    unsigned short queue[32 * (NL_MAXQ + 8)];
+    unsigned short queue[32 * (NL_MAXQ + 8)];    // undecided items (owner lane << 8 | q)
+    unsigned short wqueue[32 * (NL_MAXQ + 8)];   // whole items
+    nlg::ClipBuf clip;         // per-lane FP32 clip buffers
 };
 
 template <int BALL, typename T>
@@ -515,8 +562,44 @@ __device__ __forceinline__ int classify_item(const NumArgs &A, const CandData &c
 
 // one undecided (q, b): build the region exactly as the FP64 geometry would and integrate it
 template <int BALL, typename T>
+__device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
+                                             int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb,
+                                             int lane);
+
+template <int BALL, typename T>
 __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
-                                           int64_t &nq, int &kind, int &nv, int &ncap)
+                                           int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb, int lane)
+{
+    if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON && A.kernel == NL_KERNEL_CONST) {
+        nlg::F2 dl[3];
+        for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
+        bool cut = false;
+        int which = 0;
+        const int n = nlg::clip_ngon_f32_sh(dl, A.geo.err0, A.geo, cb, lane, &which, &cut);
+        if (n >= 0) {
+            // certified FP32 clip: same vertex count and kind as the FP64 clip
+            if (n < 3) return false;
+            kind = cut ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
+            nv = n;
+            ncap = 0;
+            if (!cut) {
+                const D2 Vb[3] = {{c.vx[0], c.vy[0]}, {c.vx[1], c.vy[1]}, {c.vx[2], c.vy[2]}};
+                whole_sums<T>(A, Vb, (T)c.akc, D2{o.x, o.y}, S, nq);
+            } else {
+                const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
+                poly_sums_sh(A, cb, which, lane, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
+            }
+            return true;
+        }
+    }
+    return exact_item_fp64<BALL, T>(A, c, o, S, nq, kind, nv, ncap, cb, lane);
+}
+
+// undecided item through the FP64 geometry (the region exactly as FP64 builds it)
+template <int BALL, typename T>
+__device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
+                                             int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb,
+                                             int lane)
 {
     nlg::F2 dl[3];
     for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
@@ -525,26 +608,6 @@ __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, 
     kind = nlg::KIND_WHOLE;
     nv = 3;
     ncap = 0;
-    if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON && A.kernel == NL_KERNEL_CONST) {
-        nlg::F2 P32[NL_MAXV];
-        bool cut = false;
-        int ovf = 0;
-        int n = nlg::clip_ngon_f32(dl, A.geo.err0, A.geo, P32, &cut, &ovf);
-        if (ovf) atomicOr(A.err, 1);
-        if (n >= 0) {
-            // certified FP32 clip: same vertex count and kind as the FP64 clip
-            if (n < 3) return false;
-            kind = cut ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
-            nv = n;
-            if (!cut) {
-                whole_sums<T>(A, Vb, c.area, x, S, nq);
-            } else {
-                const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
-                poly_sums_f32(A, P32, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
-            }
-            return true;
-        }
-    }
     nlg::Region R;
     const D2 bb = {c.bbx, c.bby};
     nlg::make_region<BALL>(Vb, dl, bb, x, A.geo, R);
@@ -553,10 +616,20 @@ __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, 
     kind = R.kind;
     nv = R.nv;
     ncap = R.ncap;
-    if (R.kind == nlg::KIND_WHOLE && R.ncap == 0 && A.kernel != NL_KERNEL_INV_DIST)
-        whole_sums<T>(A, Vb, c.area, x, S, nq);
-    else
+    if (R.kind == nlg::KIND_WHOLE && R.ncap == 0 && A.kernel != NL_KERNEL_INV_DIST) {
+        whole_sums<T>(A, Vb, (T)c.akc, x, S, nq);
+    } else if (sizeof(T) == sizeof(float) && A.kernel == NL_KERNEL_CONST && R.ncap == 0 && R.nv <= nlg::kClipCap) {
+        // FP32 quadrature on the FP64 polygon (coordinates relative to x)
+        for (int i = 0; i < R.nv; i++) {
+            cb.x[0][i][lane] = (float)(R.P[i].x - x.x);
+            cb.y[0][i][lane] = (float)(R.P[i].y - x.y);
+        }
+        const nlg::F2 d0 = {(float)(Vb[0].x - x.x), (float)(Vb[0].y - x.y)};
+        const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
+        poly_sums_sh(A, cb, 0, lane, R.nv, d0, e1, e2, c.binv, *(Sums<float> *)&S, nq);
+    } else {
         inner_sums<T>(A, R, Vb, c.area, x, S, nq);
+    }
     return true;
 }
 
@@ -588,6 +661,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
             c.bbx = A.bx[b];
             c.bby = A.by[b];
             c.area = A.area[b];
+            c.akc = c.area * A.kc;
             for (int i = 0; i < 3; i++) { c.vlx[i] = (float)(c.vx[i] - ba.x); c.vly[i] = (float)(c.vy[i] - ba.y); }
             c.blx = (float)(c.bbx - ba.x);
             c.bly = (float)(c.bby - ba.y);
@@ -599,40 +673,49 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
             sh.cand[lane] = c;
         }
         for (int i = 0; i < 22; i++) sh.acc[lane][i] = 0;
-        T v[21];
-        for (int i = 0; i < 21; i++) v[i] = 0;
-        bool any = false;
         int nqueue = 0;
         __syncwarp();
-        // phase 1: classify every (q, b) in lockstep; whole ones are integrated here
+        // phase 1: classify every (q, b) in lockstep; queue whole and undecided items
+        int nwhole = 0;
         for (int q = 0; q < nq_all; q++) {
             const bool active = valid && q >= q0 && q < q1;
             int cls = nlg::CLS_EMPTY;
             if (active) {
                 nlg::F2 dl[3];
                 cls = classify_item<BALL, T>(A, c, sh.sq[q], dl);
-                // the singular kernel needs the near-field test: whole items go to the queue too
+                // the singular kernel needs the near-field test: whole items take the exact path
                 if (inv && cls == nlg::CLS_WHOLE) cls = nlg::CLS_EXACT;
             }
-            if (cls == nlg::CLS_WHOLE) {
-                const OuterPt o = sh.sq[q];
-                const D2 Vb[3] = {{c.vx[0], c.vy[0]}, {c.vx[1], c.vy[1]}, {c.vx[2], c.vy[2]}};
-                Sums<T> S;
-                int64_t nq = 0;
-                whole_sums<T>(A, Vb, c.area, D2{o.x, o.y}, S, nq);
-                combine<T>(o, S, v);
-                any = true;
-                acc.cnt++;
-                acc.qp += nq;
-                if (A.stats) acc.hsum += nlg::record_hash(a, c.b, q - q0, nlg::KIND_WHOLE, 3, 0);
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, cls == nlg::CLS_EXACT);
-            if (cls == nlg::CLS_EXACT) sh.queue[nqueue + __popc(m & ((1u << lane) - 1u))] =
-                (unsigned short)((lane << 8) | q);
-            nqueue += __popc(m);
+            const unsigned mw = __ballot_sync(0xffffffffu, cls == nlg::CLS_WHOLE);
+            const unsigned me = __ballot_sync(0xffffffffu, cls == nlg::CLS_EXACT);
+            const unsigned below = (1u << lane) - 1u;
+            const unsigned short item = (unsigned short)((lane << 8) | q);
+            if (cls == nlg::CLS_WHOLE) sh.wqueue[nwhole + __popc(mw & below)] = item;
+            if (cls == nlg::CLS_EXACT) sh.queue[nqueue + __popc(me & below)] = item;
+            nwhole += __popc(mw);
+            nqueue += __popc(me);
         }
         __syncwarp();
-        // phase 2: drain the queue with all lanes
+        // phase 2a: whole items with all lanes
+        for (int i = lane; i < nwhole; i += 32) {
+            const unsigned it = sh.wqueue[i];
+            const int own = it >> 8, q = it & 0xff;
+            const CandData &cd = sh.cand[own];
+            const OuterPt o = sh.sq[q];
+            const D2 Vb[3] = {{cd.vx[0], cd.vy[0]}, {cd.vx[1], cd.vy[1]}, {cd.vx[2], cd.vy[2]}};
+            Sums<T> S;
+            int64_t nq = 0;
+            whole_sums<T>(A, Vb, (T)cd.akc, D2{o.x, o.y}, S, nq);
+            T w[21];
+            for (int k = 0; k < 21; k++) w[k] = 0;
+            combine<T>(o, S, w);
+            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[own][k], w[k]);
+            sh.acc[own][21] = (T)1;
+            acc.cnt++;
+            acc.qp += nq;
+            if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
+        }
+        // phase 2b: undecided items with all lanes
         for (int i = lane; i < nqueue; i += 32) {
             const unsigned it = sh.queue[i];
             const int own = it >> 8, q = it & 0xff;
@@ -641,7 +724,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
             Sums<T> S;
             int64_t nq = 0;
             int kind, nv, ncap;
-            if (!exact_item<BALL, T>(A, cd, o, S, nq, kind, nv, ncap)) continue;
+            if (!exact_item<BALL, T>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane)) continue;
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
@@ -654,9 +737,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
         __syncwarp();
         // phase 3: owners merge the queue's contributions and write their pair
         if (valid) {
-            for (int k = 0; k < 21; k++) v[k] += sh.acc[lane][k];
-            any = any || (sh.acc[lane][21] != (T)0);
-            write_pair<T>(A, e, any, v, acc);
+            T v[21];
+            for (int k = 0; k < 21; k++) v[k] = sh.acc[lane][k];
+            write_pair<T>(A, e, sh.acc[lane][21] != (T)0, v, acc);
         }
         __syncwarp();
     }
