@@ -50,6 +50,7 @@ struct nl_plan {
     int64_t *lslot = nullptr;     // [6][K] slots of the upper local pairs of each triangle
     int64_t *tslot = nullptr;     // [nnz] slot of the transposed entry
     double *W = nullptr;          // [nnz] one-sided accumulation, D = W + W^T
+    int64_t max_row = 0;          // longest row of the pattern
     // extracted sub-matrix state (nl_extract)
     float *val32 = nullptr;       // FP32 copy of the values (nl_matvec / nl_cg), lazily built
     int32_t ncols = 0;            // column count of a rectangular result (nl_extract's B)

@@ -81,7 +81,7 @@ __global__ void k_copy1(int64_t *dst, const int64_t *src) { *dst = *src; }
 // ---------------------------------------------------------------------------
 __global__ void k_prepare(int K, int J, const int32_t *__restrict__ tri, const double *__restrict__ vx,
                           const double *__restrict__ vy, double *tx, double *ty, double *bx, double *by,
-                          double *rad, double *area, double *diam, int *bad)
+                          double *rad, double *area, double *diam, float4 *cf, int *bad)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= K) return;
@@ -110,6 +110,7 @@ __global__ void k_prepare(int K, int J, const int32_t *__restrict__ tri, const d
     }
     rad[t] = r;
     diam[t] = dmax;
+    cf[t] = make_float4((float)cx, (float)cy, (float)r, 0.f);   // FP32 copy for the candidate filters
     double cr = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
     area[t] = 0.5 * fabs(cr);
     if (!(cr > 0.0)) atomicAdd(bad, 1);
@@ -216,16 +217,18 @@ __global__ void k_cell_sort(const int64_t *start, int32_t *bucket, int *overflow
     }
 }
 
-// candidate search, warp per outer triangle; pass 0 counts, pass 1 writes
-__global__ void k_candidates(int K, Grid g, double delta, const double *__restrict__ bx,
-                             const double *__restrict__ by, const double *__restrict__ rad,
+// candidate search, warp per outer triangle; pass 0 counts, pass 1 writes.  The test is
+// evaluated in FP32 on a radius inflated by 1e-5 (relative), far above the FP32 rounding of
+// the coordinates: a superset of the exact condition, symmetric in (a, b).
+__global__ void k_candidates(int K, Grid g, float delta, const float4 *__restrict__ cf,
                              const int64_t *__restrict__ start, const int32_t *__restrict__ bucket,
                              int64_t *cnt, const int64_t *ptr, int32_t *idx, int pass)
 {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= K) return;
     int a = warp;
-    double ax = bx[a], ay = by[a], ra = rad[a];
+    const float4 ca = cf[a];
+    const float ax = ca.x, ay = ca.y, ra = ca.z;
     int cx, cy;
     cell_of(g, ax, ay, &cx, &cy);
     int64_t n = 0;
@@ -242,8 +245,9 @@ __global__ void k_candidates(int K, Grid g, double delta, const double *__restri
                 int b = -1;
                 if (k < e) {
                     b = bucket[k];
-                    double ddx = bx[b] - ax, ddy = by[b] - ay;
-                    double R = (delta + (ra + rad[b])) * (1.0 + 1e-9);   // symmetric in (a, b)
+                    const float4 cb = cf[b];
+                    const float ddx = cb.x - ax, ddy = cb.y - ay;
+                    const float R = (delta + (ra + cb.z)) * (1.0f + 1e-5f);   // symmetric in (a, b)
                     hit = ddx * ddx + ddy * ddy <= R * R;
                 }
                 unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -258,12 +262,12 @@ __global__ void k_candidates(int K, Grid g, double delta, const double *__restri
 // Sort each candidate list by triangle index, interior candidates first (bitonic sort in
 // shared memory).  A candidate is interior when every point of T_b lies, with margin,
 // inside the kept region of every outer point of T_a (whole for every q):
-//   mode 0: |bary_a - bary_b| + r_a + r_b <= lim   (lim = r_in - tau: disc or polygon inradius)
-//   mode 1: |bary_a - bary_b| + r_a <= lim         (barycenter ball, lim = delta - tau)
+//   mode 0: |bary_a - bary_b| + r_a + r_b <= lim   (lim = r_in - 2 tau: disc or polygon inradius)
+//   mode 1: |bary_a - bary_b| + r_a <= lim         (barycenter ball, lim = delta - 2 tau)
 //   mode 2: no interior fast path
 // split[a] = index of the first boundary candidate.
-__global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split, const double *bx, const double *by,
-                             const double *rad, int mode, double lim, int *overflow)
+__global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split, const float4 *cf, int mode,
+                             float lim, int *overflow)
 {
     __shared__ int32_t s[NL_MAXCAND];
     __shared__ int s_int;
@@ -277,7 +281,7 @@ __global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split, c
     if (threadIdx.x == 0) s_int = 0;
     int p = 1;
     while (p < n) p <<= 1;
-    const double ax = bx[a], ay = by[a], ra = rad[a];
+    const float4 ca = cf[a];
     __syncthreads();
     int my_int = 0;
     for (int i = threadIdx.x; i < p; i += blockDim.x) {
@@ -286,9 +290,11 @@ __global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split, c
             const int b = idx[b0 + i];
             bool interior = false;
             if (mode != 2) {
-                const double dx = bx[b] - ax, dy = by[b] - ay;
-                const double D = sqrt(dx * dx + dy * dy);
-                interior = (mode == 0 ? D + ra + rad[b] : D + ra) <= lim;
+                // FP32 with lim already reduced by 1e-5 delta (far above the FP32 rounding): conservative
+                const float4 cb = cf[b];
+                const float dx = cb.x - ca.x, dy = cb.y - ca.y;
+                const float D = sqrtf(dx * dx + dy * dy);
+                interior = (mode == 0 ? D + ca.z + cb.z : D + ca.z) <= lim;
             }
             my_int += interior;
             key = interior ? b : (b | 0x40000000);
@@ -396,9 +402,11 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
     NL_CK(cudaMallocAsync((void **)&bad, sizeof(int), ctx->stream));
     NL_CK(cudaMallocAsync((void **)&st, sizeof(MeshStats), ctx->stream));
     NL_CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+    float4 *cf = nullptr;
+    NL_CK(cudaMallocAsync((void **)&cf, sizeof(float4) * K, ctx->stream));
     k_prepare<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, J, (const int32_t *)dtri, (const double *)dvx,
                                                         (const double *)dvy, P->tx, P->ty, P->bx, P->by,
-                                                        P->rad, P->area, diam, bad); ++ctx->launches;
+                                                        P->rad, P->area, diam, cf, bad); ++ctx->launches;
     NL_CK(cudaGetLastError());
     k_mesh_stats<<<1, 1024, 0, ctx->stream>>>(K, P->bx, P->by, P->rad, diam, st); ++ctx->launches;
     NL_CK(cudaGetLastError());
@@ -422,7 +430,7 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
     P->hmax = hst.hmax;
     P->rmax = hst.rmax;
     // grid for the candidate search
-    double R = (cfg->delta + 2.0 * hst.rmax) * (1.0 + 1e-9);
+    double R = (cfg->delta + 2.0 * hst.rmax) * (1.0 + 2e-5);
     double Lx = hst.xmax - hst.xmin, Ly = hst.ymax - hst.ymin, L = fmax(fmax(Lx, Ly), 1e-300);
     double cs = fmin(R, L / sqrt(fmax(K / 32.0, 1.0)));
     Grid g;
@@ -458,8 +466,8 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
     int64_t *cnt = nullptr;
     NL_CK(cudaMallocAsync((void **)&cnt, sizeof(int64_t) * K, ctx->stream));
     unsigned wblocks = (unsigned)(((int64_t)K * 32 + 255) / 256);
-    k_candidates<<<wblocks, 256, 0, ctx->stream>>>(K, g, cfg->delta, P->bx, P->by, P->rad, cstart, bucket, cnt,
-                                                   nullptr, nullptr, 0); ++ctx->launches;
+    k_candidates<<<wblocks, 256, 0, ctx->stream>>>(K, g, (float)cfg->delta, cf, cstart, bucket, cnt, nullptr,
+                                                   nullptr, 0); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_scan_i64(ctx, cnt, P->nbr_ptr, K)) != NL_OK) return s;
     int64_t E = 0;
@@ -470,24 +478,25 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
     if (hovf) return nl_fail(ctx, NL_EUNSUPPORTED, "cell-list bucket exceeds the shared-memory sort limit");
     P->E = E;
     if ((s = nl_alloc(ctx, &P->nbr_idx, (size_t)E)) != NL_OK) return s;
-    k_candidates<<<wblocks, 256, 0, ctx->stream>>>(K, g, cfg->delta, P->bx, P->by, P->rad, cstart, bucket,
-                                                   nullptr, P->nbr_ptr, P->nbr_idx, 1); ++ctx->launches;
+    k_candidates<<<wblocks, 256, 0, ctx->stream>>>(K, g, (float)cfg->delta, cf, cstart, bucket, nullptr,
+                                                   P->nbr_ptr, P->nbr_idx, 1); ++ctx->launches;
     NL_CK(cudaGetLastError());
     // interior fast path: the region is whole for every outer point (certified with margin tau)
     {
         const double tau = 1e-5 * cfg->delta;
         int mode = 0;
-        double lim = cfg->delta - tau;
+        double lim = cfg->delta - 2.0 * tau;
         if (cfg->kernel == NL_KERNEL_INV_DIST) mode = 2;          // near-field rule needs every pair
         else if (cfg->ball == NL_BALL_BARYCENTER) mode = 1;
-        else if (cfg->ball == NL_BALL_NGON) lim = P->rin - tau;
+        else if (cfg->ball == NL_BALL_NGON) lim = P->rin - 2.0 * tau;
         if ((s = nl_alloc(ctx, &P->nbr_split, (size_t)K)) != NL_OK) return s;
-        k_sort_lists<<<K, 256, 0, ctx->stream>>>(P->nbr_ptr, P->nbr_idx, P->nbr_split, P->bx, P->by, P->rad, mode,
-                                                 lim, ovf); ++ctx->launches;
+        k_sort_lists<<<K, 256, 0, ctx->stream>>>(P->nbr_ptr, P->nbr_idx, P->nbr_split, cf, mode, (float)lim,
+                                                 ovf); ++ctx->launches;
     }
     NL_CK(cudaGetLastError());
     NL_CK(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     NL_CK(cudaFreeAsync(cnt, ctx->stream));
+    NL_CK(cudaFreeAsync(cf, ctx->stream));
     NL_CK(cudaFreeAsync(cell, ctx->stream));
     NL_CK(cudaFreeAsync(bucket, ctx->stream));
     NL_CK(cudaFreeAsync(ccnt, ctx->stream));

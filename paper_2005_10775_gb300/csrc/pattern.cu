@@ -172,39 +172,78 @@ __global__ void k_tslot(int J, const int64_t *row_ptr, const int32_t *col, int64
     for (int64_t s = row_ptr[j] + lane; s < row_ptr[j + 1]; s += 32) tslot[s] = find_slot(row_ptr, col, col[s], j);
 }
 
-// one-sided numeric scatter, warp per outer triangle
+// One-sided numeric scatter, warp per outer triangle.  The -M_ab contributions of all
+// of T_a's pairs land in the three rows of T_a's nodes: the warp accumulates them in
+// shared memory (columns of those rows staged there, `cap` per row) and adds each row
+// entry to W once, instead of one FP64 atomic per pair and entry.  The upper M_bb of
+// every pair and T_a's own M_aa go straight to W through the local slot map.
 template <typename T>
 __global__ void k_scatter(int K, int64_t E, const int32_t *tri, const int64_t *ptr, const int32_t *idx,
                           const uint8_t *flag, const T *blk, const double *maa, const int64_t *lslot,
-                          const int64_t *row_ptr, const int32_t *col, double *W, int *err)
+                          const int64_t *row_ptr, const int32_t *col, double *W, int *err, int cap)
 {
-    int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int a = blockIdx.x * (blockDim.x >> 5) + wib;
+    int32_t *scol = (int32_t *)(smem_raw + (size_t)wib * 3 * cap * (sizeof(int32_t) + sizeof(T)));
+    T *sacc = (T *)(scol + 3 * cap);
     if (a >= K) return;
-    const int a0 = tri[3 * a], a1 = tri[3 * a + 1], a2 = tri[3 * a + 2];
-    const int ar[3] = {a0, a1, a2};
+    const int ar[3] = {tri[3 * a], tri[3 * a + 1], tri[3 * a + 2]};
+    int64_t r0[3];
+    int len[3];
+    bool cached[3];
+    for (int i = 0; i < 3; i++) {
+        r0[i] = row_ptr[ar[i]];
+        len[i] = (int)(row_ptr[ar[i] + 1] - r0[i]);
+        cached[i] = len[i] <= cap;
+        if (cached[i])
+            for (int k = lane; k < len[i]; k += 32) {
+                scol[i * cap + k] = col[r0[i] + k];
+                sacc[i * cap + k] = (T)0;
+            }
+    }
+    __syncwarp();
     for (int64_t e = ptr[a] + lane; e < ptr[a + 1]; e += 32) {
         if (!flag[e]) continue;
         const int b = idx[e];
         const int bn[3] = {tri[3 * b], tri[3 * b + 1], tri[3 * b + 2]};
         for (int i = 0; i < 3; i++)
             for (int k = 0; k < 3; k++) {
-                double v = (double)blk[(int64_t)(3 * i + k) * E + e];
-                int64_t s = find_slot(row_ptr, col, ar[i], bn[k]);
-                if (s >= 0) atomicAdd(&W[s], -v); else atomicOr(err, 2);
+                const T v = blk[(int64_t)(3 * i + k) * E + e];
+                if (cached[i]) {
+                    int lo = 0, hi = len[i] - 1, pos = -1;
+                    while (lo <= hi) {
+                        const int mid = (lo + hi) >> 1;
+                        const int c = scol[i * cap + mid];
+                        if (c == bn[k]) { pos = mid; break; }
+                        if (c < bn[k]) lo = mid + 1; else hi = mid - 1;
+                    }
+                    if (pos >= 0) atomicAdd(&sacc[i * cap + pos], -v); else atomicOr(err, 2);
+                } else {
+                    const int64_t sl = find_slot(row_ptr, col, ar[i], bn[k]);
+                    if (sl >= 0) atomicAdd(&W[sl], -(double)v); else atomicOr(err, 2);
+                }
             }
         for (int p = 0; p < 6; p++) {
             double v = (double)blk[(int64_t)(9 + p) * E + e];
             if (p < 3) v *= 0.5;
-            int64_t s = lslot[(int64_t)p * K + b];
-            if (s >= 0) atomicAdd(&W[s], v); else atomicOr(err, 2);
+            const int64_t sl = lslot[(int64_t)p * K + b];
+            if (sl >= 0) atomicAdd(&W[sl], v); else atomicOr(err, 2);
         }
     }
+    __syncwarp();
+    for (int i = 0; i < 3; i++)
+        if (cached[i])
+            for (int k = lane; k < len[i]; k += 32) {
+                const T v = sacc[i * cap + k];
+                if (v != (T)0) atomicAdd(&W[r0[i] + k], (double)v);
+            }
     if (lane == 0)
         for (int p = 0; p < 6; p++) {
             double v = maa[(int64_t)p * K + a];
             if (p < 3) v *= 0.5;
-            int64_t s = lslot[(int64_t)p * K + a];
-            if (s >= 0) atomicAdd(&W[s], v); else atomicOr(err, 2);
+            const int64_t sl = lslot[(int64_t)p * K + a];
+            if (sl >= 0) atomicAdd(&W[sl], v); else atomicOr(err, 2);
         }
 }
 
@@ -215,6 +254,15 @@ __global__ void k_symmetrize(int64_t nnz, const double *W, const int64_t *tslot,
     int64_t t = tslot[s];
     if (t >= 0) val[s] = W[s] + W[t];
     else atomicOr(err, 4);
+}
+
+__global__ void k_row_max(int J, const int64_t *rcnt, unsigned long long *out)
+{
+    unsigned long long m = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < J; j += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)rcnt[j]);
+    for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&out[3], m);
 }
 
 __global__ void k_sum_stats(int K, int64_t E, const uint8_t *flag, const int64_t *qp, const int64_t *cnt,
@@ -257,11 +305,11 @@ nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     NL_CK(cudaMallocAsync((void **)&rcnt, sizeof(int64_t) * (J + 1), ctx->stream));
     NL_CK(cudaMallocAsync((void **)&ntri, sizeof(int32_t) * 3 * (size_t)K, ctx->stream));
     NL_CK(cudaMallocAsync((void **)&ovf, sizeof(int), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&st, sizeof(unsigned long long) * 3, ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&st, sizeof(unsigned long long) * 4, ctx->stream));
     NL_CK(cudaMemsetAsync(ncnt, 0, sizeof(int64_t) * (J + 1), ctx->stream));
     NL_CK(cudaMemsetAsync(ncur, 0, sizeof(int64_t) * (J + 1), ctx->stream));
     NL_CK(cudaMemsetAsync(ovf, 0, sizeof(int), ctx->stream));
-    NL_CK(cudaMemsetAsync(st, 0, sizeof(unsigned long long) * 3, ctx->stream));
+    NL_CK(cudaMemsetAsync(st, 0, sizeof(unsigned long long) * 4, ctx->stream));
     const unsigned wgrid = (unsigned)(((int64_t)K * 32 + 255) / 256);
     k_symflag<<<wgrid, 256, 0, ctx->stream>>>(K, P->nbr_ptr, P->nbr_split, P->nbr_idx, P->flag, sym); ++ctx->launches;
     k_node_count<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->tri, ncnt); ++ctx->launches;
@@ -276,10 +324,11 @@ nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     if ((s = nl_alloc(ctx, &out->row_ptr, (size_t)J + 1)) != NL_OK) return s;
     if ((s = nl_scan_i64(ctx, rcnt, out->row_ptr, J)) != NL_OK) return s;
     k_sum_stats<<<256, 256, 0, ctx->stream>>>(K, P->E, P->flag, P->qp_a, P->cnt_a, st); ++ctx->launches;
+    k_row_max<<<64, 256, 0, ctx->stream>>>(J, rcnt, st); ++ctx->launches;
     NL_CK(cudaGetLastError());
     int64_t nnz = 0;
     int hovf = 0, herr = 0;
-    unsigned long long hst[3];
+    unsigned long long hst[4];
     NL_CK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     NL_CK(cudaMemcpyAsync(&nnz, out->row_ptr + J, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
     NL_CK(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -293,6 +342,7 @@ nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     out->n_pairs = (int64_t)hst[0];
     out->n_qp_pairs = (int64_t)hst[1];
     out->n_inter = (int64_t)hst[2];
+    P->max_row = (int64_t)hst[3];
     if ((s = nl_alloc(ctx, &out->col_idx, (size_t)nnz)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &out->val, (size_t)nnz)) != NL_OK) return s;
     k_rows<<<J, kRowThreads, smem, ctx->stream>>>(J, nptr, ntri, P->tri, P->nbr_ptr, P->nbr_idx, sym, nullptr,
@@ -316,22 +366,32 @@ nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     return NL_OK;
 }
 
-nl_status nl_run_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out)
+template <typename T>
+static nl_status launch_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out)
 {
     const int K = P->K;
-    NL_CK(cudaMemsetAsync(P->W, 0, sizeof(double) * (size_t)out->nnz, ctx->stream));
-    const unsigned wgrid = (unsigned)(((int64_t)K * 32 + 255) / 256);
-    if (P->cfg.prec == NL_PREC_FP64) {
-        k_scatter<double><<<wgrid, 256, 0, ctx->stream>>>(K, P->E, P->tri, P->nbr_ptr, P->nbr_idx, P->flag,
-                                                          (const double *)P->blk, P->maa, P->lslot, out->row_ptr,
-                                                          out->col_idx, P->W, P->err); ++ctx->launches;
+    int cap = (int)(((P->max_row > 0 ? P->max_row : 1) + 3) & ~3LL);   // multiple of 4: keeps the T array aligned
+    int warps = 4;
+    while (warps > 1 && (size_t)warps * 3 * cap * (sizeof(int32_t) + sizeof(T)) > 96 * 1024) warps >>= 1;
+    size_t smem = (size_t)warps * 3 * cap * (sizeof(int32_t) + sizeof(T));
+    if (smem > 96 * 1024) {   // very long rows: stage none, search in global memory
+        cap = 0;
+        smem = 0;
     }
-    else {
-        k_scatter<float><<<wgrid, 256, 0, ctx->stream>>>(K, P->E, P->tri, P->nbr_ptr, P->nbr_idx, P->flag,
-                                                         (const float *)P->blk, P->maa, P->lslot, out->row_ptr,
-                                                         out->col_idx, P->W, P->err); ++ctx->launches;
-    }
+    NL_CK(cudaFuncSetAttribute(k_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(96 * 1024)));
+    const unsigned grid = (unsigned)((K + warps - 1) / warps);
+    k_scatter<T><<<grid, 32 * warps, smem, ctx->stream>>>(K, P->E, P->tri, P->nbr_ptr, P->nbr_idx, P->flag,
+                                                           (const T *)P->blk, P->maa, P->lslot, out->row_ptr,
+                                                           out->col_idx, P->W, P->err, cap); ++ctx->launches;
     NL_CK(cudaGetLastError());
+    return NL_OK;
+}
+
+nl_status nl_run_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out)
+{
+    NL_CK(cudaMemsetAsync(P->W, 0, sizeof(double) * (size_t)out->nnz, ctx->stream));
+    nl_status s = P->cfg.prec == NL_PREC_FP64 ? launch_scatter<double>(ctx, P, out) : launch_scatter<float>(ctx, P, out);
+    if (s != NL_OK) return s;
     if (out->nnz > 0) {
         k_symmetrize<<<(unsigned)((out->nnz + 255) / 256), 256, 0, ctx->stream>>>(out->nnz, P->W, P->tslot,
                                                                                  out->val, P->err); ++ctx->launches;
