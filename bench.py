@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--solve", action="store_true",
+                    help="after the assembly, extract A, form F and solve A U = F by CG (u = |x|^2)")
     return ap.parse_args()
 
 
@@ -144,6 +146,49 @@ def cpu_baseline(problem, seconds, steps=1):
     return {"value": qp / tt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{m} of {K} outer triangles (evenly spaced) x all {K} inner triangles, "
                       f"{qp // max(steps, 1)} qp-pairs per step, FP64"}, tt / steps
+
+
+def solve_phase(nl, ctx, m, p, prec, stream, dev, keep):
+    """A = D[Omega, Omega], F = G - D[Omega, Omega_I] g and the CG solve to 1e-10 for u = |x|^2
+    (f = -4), timed with CUDA events on the library's stream; one FP32 SpMV timed for GB/s."""
+    import numpy as np
+    import torch
+    hmesh = nl.make_mesh(m, keep)
+    dcfg = nl.make_config(keep, p.delta, p.ball, p.outer, p.inner, p.kernel, p.kernel_c, p.ngon_off, p.cap_m, prec)
+    D = nl.nl_assemble(ctx, hmesh, dcfg)
+    u = m.vx ** 2 + m.vy ** 2
+    f = np.full_like(u, -4.0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    A, B = nl.nl_extract(ctx, D, hmesh)
+    F = torch.tensor(nl.nl_rhs(ctx, B, hmesh, f, u), device=dev)
+    ev[1].record(stream)
+    x = torch.zeros_like(F)
+    it, rel = nl.nl_cg(ctx, A, F, x, rtol=1e-10, max_it=20000)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    om = m.node_in_omega.astype(bool)
+    err = float(np.abs(x.cpu().numpy() - u[om]).max())
+    # one FP32 matrix-vector product (the CG inner loop's kernel): bytes = values + columns + x + y
+    y = torch.empty_like(F)
+    nl.nl_matvec(ctx, A, x, y, prec="fp32c")
+    reps = 20
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        nl.nl_matvec(ctx, A, x, y, prec="fp32c")
+    e1.record(stream)
+    e1.synchronize()
+    spmv_ms = e0.elapsed_time(e1) / reps
+    spmv_bytes = A.nnz * 8 + (A.n + 1) * 8 + 2 * A.n * 8
+    out = {"J_omega": int(A.n), "nnz_A": int(A.nnz), "extract_rhs_ms": ev[0].elapsed_time(ev[1]),
+           "cg_ms": ev[1].elapsed_time(ev[2]), "cg_inner_iterations": it, "relres": rel,
+           "max_nodal_error_vs_u": err, "spmv_fp32_ms": spmv_ms,
+           "spmv_fp32_GBps": spmv_bytes / (spmv_ms * 1e-3) / 1e9}
+    for z in (D, A, B):
+        nl.nl_csr_free(ctx, z)
+    return out
 
 
 def reference_arm(args, rank, world):
@@ -282,6 +327,10 @@ def main():
         e2e = {"value": n_qp * world * args.steps / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    solve = None
+    if args.solve:
+        solve = solve_phase(nl, ctx, m, p, args.prec, stream, dev, keep)
+
     peaks, src = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
@@ -306,6 +355,7 @@ def main():
                                     f"(clock from MEASURED_PEAKS.json, {src})",
                      "traffic": None},
         "clocks": ck,
+        "solve": solve,
         "gpu_launches": int(launches),
         "e2e": e2e,
     }

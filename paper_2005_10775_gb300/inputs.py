@@ -157,8 +157,9 @@ def problem(name: str) -> Problem:
     ngon32_96       : (-0.1,1.1)^2, 96x96 jittered +-0.2h (seed 1077502), delta 0.1,
                       regular 32-gon, 16-point outer, 7-point inner, constant kernel.
     singular_128    : (-0.05,1.05)^2, 128x128 jittered (seed 1077503), delta 0.05,
-                      32-gon, psi = 3/(pi delta^3)/|x-y|.
-    solve_220       : (-0.05,1.05)^2, 220x220 jittered (seed 1077505), delta 0.05, 32-gon.
+                      32-gon, psi = 3/(pi delta^3)/|x-y|, 16-point outer, 7-point inner.
+    solve_220       : (-0.05,1.05)^2, 220x220 jittered (seed 1077505), delta 0.05, 32-gon,
+                      16-point outer, 7-point inner (assembly followed by the CG solve).
     Small variants (suffix _small) keep the structure at sizes the oracle finishes in
     seconds.
     """
@@ -175,20 +176,16 @@ def problem(name: str) -> Problem:
         return Problem(name, m, d, "const", const_kernel_c(d), "ngon", "dunavant16", "dunavant7",
                        ngon_n=32, ngon_off=ngon_offsets(32, d))
     if name in ("singular_128", "singular_small"):
-        dd = 0.05
-        n = 128 if name == "singular_128" else 16
-        lo, hi = (-0.05, 1.05)
+        dd, lo, hi, n = 0.05, -0.05, 1.05, 128
         if name == "singular_small":
-            dd = 0.2
-            lo, hi = (-0.2, 1.2)
-            n = 14
+            dd, lo, hi, n = 0.2, -0.2, 1.2, 16
         m = split_square_mesh(lo, hi, n, jitter=0.2, seed=1077503)
         return Problem(name, m, dd, "inv_dist", inv_dist_kernel_c(dd), "ngon", "dunavant16", "dunavant7",
                        ngon_n=32, ngon_off=ngon_offsets(32, dd))
     if name in ("solve_220",):
         dd = 0.05
         m = split_square_mesh(-0.05, 1.05, 220, jitter=0.2, seed=1077505)
-        return Problem(name, m, dd, "const", const_kernel_c(dd), "ngon", "dunavant7", "dunavant7",
+        return Problem(name, m, dd, "const", const_kernel_c(dd), "ngon", "dunavant16", "dunavant7",
                        ngon_n=32, ngon_off=ngon_offsets(32, dd))
     raise KeyError(name)
 

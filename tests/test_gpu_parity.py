@@ -231,3 +231,35 @@ def test_parity_bench_workload_full_size_sampled(nl, ctx, prec):
         o_row.sort_indices()
         np.testing.assert_array_equal(g_row.indices, o_row.indices)
         assert np.abs(g_row.data - o_row.data).max() <= TOL[prec] * scale
+
+
+@pytest.mark.parametrize("prec", ["fp32c", "fp64"])
+def test_parity_singular_workload_full_size_sampled(nl, ctx, prec):
+    # integrable singular kernel 3/(pi delta^3)/|x-y|, delta 0.05, 128x128 jittered (K = 32768):
+    # the near-singular rule runs on every pair near the outer point; sampled outputs from the oracle
+    p = I.problem("singular_128")
+    K, J = p.mesh.nt, p.mesh.nv
+    keep = nl._Keep()
+    mesh = nl.make_mesh(p.mesh, keep)
+    cfg = nl.config_of(p, keep, prec=prec, duffy_n=4)
+    h, c, q = nl.nl_interactions(ctx, mesh, cfg)
+    rng = np.random.default_rng(5)
+    a_list = np.unique(np.concatenate([rng.choice(K, 40, replace=False), [0, K - 1, K // 2]]))
+    out = O.assemble(p.mesh, oracle_cfg(p, duffy_n=4), a_list=a_list.astype(np.int32), want_hash=True)
+    np.testing.assert_array_equal(h[a_list], out["hash_a"][a_list])
+    np.testing.assert_array_equal(q[a_list], out["qp_a"][a_list])
+    m = nl.nl_assemble(ctx, mesh, cfg)
+    try:
+        Dg = nl.to_scipy(ctx, m)
+    finally:
+        nl.nl_csr_free(ctx, m)
+    rows = np.array([J // 2 + 7, J - 1])
+    mask = np.zeros(J, np.uint8)
+    mask[rows] = 1
+    Dr = O.to_csr(O.assemble(p.mesh, oracle_cfg(p, duffy_n=4), row_mask=mask))
+    scale = np.abs(Dg.diagonal()).max()
+    for r in rows:
+        g_row, o_row = Dg[r], Dr[r]
+        o_row.sort_indices()
+        np.testing.assert_array_equal(g_row.indices, o_row.indices)
+        assert np.abs(g_row.data - o_row.data).max() <= TOL[prec] * scale

@@ -96,3 +96,32 @@ def test_cg_reports_nonconvergence(nl, ctx, system):
     with pytest.raises(nl.NlError) as e:
         nl.nl_cg(ctx, system["A"], F, x, rtol=1e-14, max_it=3)
     assert e.value.status == nl.NL_ENOCONV
+
+
+TABLE1 = {("approxcaps", 0.05): 5.84e-04, ("approxcaps", 0.025): 1.67e-04,
+          ("nocaps", 0.05): 3.92e-03, ("nocaps", 0.025): 1.04e-03}
+
+
+@pytest.mark.parametrize("ball,h", list(TABLE1))
+def test_paper_table1_end_to_end_on_gpu(nl, ctx, ball, h):
+    # Sec. 8: the whole pipeline on the GPU (assembly with the paper's rule protocol, extraction,
+    # right-hand side, CG) reproduces the L2 errors printed in Table 1 (values in tests/golden)
+    d = 0.1
+    m = I.paper_grid(h)
+    p = I.Problem("paper", m, d, "const", I.const_kernel_c(d), ball, "switch47", "gauss3")
+    keep = nl._Keep()
+    mesh = nl.make_mesh(m, keep)
+    D = nl.nl_assemble(ctx, mesh, nl.config_of(p, keep, prec="fp32c"))
+    A, B = nl.nl_extract(ctx, D, mesh)
+    try:
+        u = I.manufactured_u(m.vx, m.vy)
+        F = nl.nl_rhs(ctx, B, mesh, I.manufactured_f(m.vx, m.vy), u)
+        x = np.zeros(A.n)
+        nl.nl_cg(ctx, A, F, x, rtol=1e-10, max_it=20000)
+    finally:
+        for z in (D, A, B):
+            nl.nl_csr_free(ctx, z)
+    U = u.copy()
+    U[m.node_in_omega.astype(bool)] = x
+    err = O.l2_error_omega(m, U, I.manufactured_u)
+    assert err == pytest.approx(TABLE1[(ball, h)], rel=0.15)

@@ -472,3 +472,20 @@ def test_paper_table1_rates():
         e1 = _paper_l2(ball, 0.05, **kw)
         e2 = _paper_l2(ball, 0.025, **kw)
         assert 1.6 < math.log2(e1 / e2) < 2.4, ball
+
+
+def test_singular_kernel_second_order_convergence():
+    # psi = 3/(pi delta^3)/|x-y| has second moment 2 (like 4/(pi delta^4)), so L u = Laplacian u for
+    # the paper's cubic u (Sec. 8): the manufactured solve converges at second order in h
+    d = 0.2
+    errs = []
+    for n in (12, 24):
+        m = I.split_square_mesh(-0.2, 1.2, n)
+        u = I.manufactured_u(m.vx, m.vy)
+        f = I.manufactured_f(m.vx, m.vy)
+        cfg = dict(delta=d, ball="ngon", outer="dunavant7", inner="dunavant7", kernel="inv_dist",
+                   kernel_c=I.inv_dist_kernel_c(d), ngon_off=I.ngon_offsets(64, d), duffy_n=4)
+        U = O.solve(O.to_csr(O.assemble(m, cfg)), m, f, u)
+        errs.append(O.l2_error_omega(m, U, I.manufactured_u))
+    rate = math.log2(errs[0] / errs[1])
+    assert 1.6 < rate < 2.6, (errs, rate)
