@@ -605,6 +605,17 @@ __device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, cons
     return n;
 }
 
+// Near field of the singular kernel for a whole T_b: near iff dist(x, T_b) < diam(T_b).
+// FP32 decides when the two differ by more than eta (1e-5 delta, far above the FP32
+// error of either); otherwise the FP64 test decides.  Returns 0 far, 1 near, -1 undecided.
+__device__ __forceinline__ int near_f32(const F2 dl[3], float diamf, float eta)
+{
+    const float dist = sqrtf(dist2_origin_triangle(dl));
+    if (dist > diamf + eta) return 0;
+    if (dist < diamf - eta) return 1;
+    return -1;
+}
+
 // ---- near-singular test (values of psi = c/|x-y| need a special rule) ----
 __device__ __forceinline__ D2 closest_on_seg(D2 a, D2 b, D2 x)
 {

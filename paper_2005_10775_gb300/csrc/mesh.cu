@@ -265,9 +265,10 @@ __global__ void k_candidates(int K, Grid g, float delta, const float4 *__restric
 //   mode 0: |bary_a - bary_b| + r_a + r_b <= lim   (lim = r_in - 2 tau: disc or polygon inradius)
 //   mode 1: |bary_a - bary_b| + r_a <= lim         (barycenter ball, lim = delta - 2 tau)
 //   mode 2: no interior fast path
+//   mode 3: mode 0 and |bary_a - bary_b| - r_a - 3 r_b > far_margin (singular kernel: no near field)
 // split[a] = index of the first boundary candidate.
 __global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split, const float4 *cf, int mode,
-                             float lim, int *overflow)
+                             float lim, float far_margin, int *overflow)
 {
     __shared__ int32_t s[NL_MAXCAND];
     __shared__ int s_int;
@@ -294,7 +295,10 @@ __global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split, c
                 const float4 cb = cf[b];
                 const float dx = cb.x - ca.x, dy = cb.y - ca.y;
                 const float D = sqrtf(dx * dx + dy * dy);
-                interior = (mode == 0 ? D + ca.z + cb.z : D + ca.z) <= lim;
+                interior = (mode == 1 ? D + ca.z : D + ca.z + cb.z) <= lim;
+                // singular kernel: also far from the near field for every outer point
+                // (distance >= D - r_a - r_b >= 2 r_b >= diameter of T_b)
+                if (mode == 3) interior = interior && (D - ca.z - 3.0f * cb.z > far_margin);
             }
             my_int += interior;
             key = interior ? b : (b | 0x40000000);
@@ -486,12 +490,12 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
         const double tau = 1e-5 * cfg->delta;
         int mode = 0;
         double lim = cfg->delta - 2.0 * tau;
-        if (cfg->kernel == NL_KERNEL_INV_DIST) mode = 2;          // near-field rule needs every pair
-        else if (cfg->ball == NL_BALL_BARYCENTER) mode = 1;
+        if (cfg->ball == NL_BALL_BARYCENTER) mode = 1;
         else if (cfg->ball == NL_BALL_NGON) lim = P->rin - 2.0 * tau;
+        if (cfg->kernel == NL_KERNEL_INV_DIST) mode = cfg->ball == NL_BALL_BARYCENTER ? 2 : 3;
         if ((s = nl_alloc(ctx, &P->nbr_split, (size_t)K)) != NL_OK) return s;
         k_sort_lists<<<K, 256, 0, ctx->stream>>>(P->nbr_ptr, P->nbr_idx, P->nbr_split, cf, mode, (float)lim,
-                                                 ovf); ++ctx->launches;
+                                                 (float)(2.0 * tau), ovf); ++ctx->launches;
     }
     NL_CK(cudaGetLastError());
     NL_CK(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));

@@ -104,17 +104,44 @@ __device__ __forceinline__ void bary_of(const BaryMap &m, double yx, double yy, 
     phi[2] = l2;
 }
 
+// The discrete choices of the near-singular rule for edge (P_a, P_b) and outer point x,
+// in FP64 with the expression order of the rule's definition (no contraction): the foot
+// distance d (a zero-area piece is skipped) and the signed positions tA, tB of the end
+// points along the edge (a zero-length piece is skipped, ceil(asinh(|t| / d)) panels).
+struct NearEdge64 {
+    double d, tA, tB;
+};
+
+__device__ __forceinline__ NearEdge64 near_edge64(D2 pa, D2 pb, D2 x)
+{
+    using namespace nlg;
+    double ex = sub(pb.x, pa.x), ey = sub(pb.y, pa.y);
+    const double L = __dsqrt_rn(add(mul(ex, ex), mul(ey, ey)));
+    NearEdge64 r;
+    if (L == 0.0) { r.d = 0.0; r.tA = r.tB = 0.0; return r; }
+    ex = dvd(ex, L);
+    ey = dvd(ey, L);
+    r.tA = add(mul(sub(pa.x, x.x), ex), mul(sub(pa.y, x.y), ey));
+    r.tB = add(mul(sub(pb.x, x.x), ex), mul(sub(pb.y, x.y), ey));
+    const double fx = sub(sub(pa.x, mul(r.tA, ex)), x.x), fy = sub(sub(pa.y, mul(r.tA, ey)), x.y);
+    r.d = __dsqrt_rn(add(mul(fx, fx), mul(fy, fy)));
+    return r;
+}
+
+__device__ __forceinline__ int near_panels64(double tau, double d)
+{
+    int n = (int)ceil(asinh(fabs(tau) / d));
+    return n < 1 ? 1 : n;
+}
+
 // Near-singular rule for psi = c/|x - y| (signed apex-x decomposition with a Duffy
 // collapse in s and the sinh substitution in u; dy/|x-y| = d ds du), FP64.
 __device__ __forceinline__ void near_right_triangle(const NumArgs &A, const BaryMap &bm, D2 x, D2 F, double ex,
-                                                    double ey, double d, double tau, double sign,
+                                                    double ey, double d, double tau, double sign, int npan,
                                                     Sums<double> &S, int64_t &nqp)
 {
-    if (tau == 0.0) return;
     double sg = tau > 0.0 ? 1.0 : -1.0;
-    double U = asinh(fabs(tau) / d);
-    int npan = (int)ceil(U);
-    if (npan < 1) npan = 1;
+    double U = fmax(asinh(fabs(tau) / d), (double)(npan - 1));
     const int nu = A.duffy_n;
     for (int p = 0; p < npan; p++) {
         double u0 = (double)p, u1 = (p + 1 < npan) ? (double)(p + 1) : U;
@@ -142,6 +169,8 @@ __device__ __forceinline__ void near_polygon(const NumArgs &A, const BaryMap &bm
     const int n = R.nv;
     for (int i = 0; i < n; i++) {
         D2 a = R.P[i], b = R.P[(i + 1) % n];
+        const NearEdge64 q = near_edge64(a, b, x);
+        if (q.d == 0.0) continue;
         double ex = b.x - a.x, ey = b.y - a.y;
         double L = sqrt(ex * ex + ey * ey);
         if (L == 0.0) continue;
@@ -154,10 +183,9 @@ __device__ __forceinline__ void near_polygon(const NumArgs &A, const BaryMap &bm
         F.y = a.y - tA * ey;
         double fx = F.x - x.x, fy = F.y - x.y;
         double d = sqrt(fx * fx + fy * fy);
-        if (d == 0.0) continue;
         double sigma = (fx * ey - fy * ex) > 0.0 ? 1.0 : -1.0;
-        near_right_triangle(A, bm, x, F, ex, ey, d, tB, sigma, S, nqp);
-        near_right_triangle(A, bm, x, F, ex, ey, d, tA, -sigma, S, nqp);
+        if (q.tB != 0.0) near_right_triangle(A, bm, x, F, ex, ey, d, tB, sigma, near_panels64(q.tB, q.d), S, nqp);
+        if (q.tA != 0.0) near_right_triangle(A, bm, x, F, ex, ey, d, tA, -sigma, near_panels64(q.tA, q.d), S, nqp);
     }
 }
 
@@ -179,7 +207,7 @@ __device__ __forceinline__ T rule_w(const NumArgs &A, int r)
 // inner sums over the whole triangle T_b: phi_b at the rule points are the rule's barycentrics
 template <typename T>
 __device__ __forceinline__ void whole_sums(const NumArgs &A, const D2 V[3], T area_kc, D2 x, Sums<T> &S,
-                                           int64_t &nqp)
+                                           int64_t &nqp, const nlg::F2 *dl = nullptr)
 {
     sums_zero(S);
     const bool inv = (A.kernel == NL_KERNEL_INV_DIST);
@@ -191,8 +219,12 @@ __device__ __forceinline__ void whole_sums(const NumArgs &A, const D2 V[3], T ar
     if (sizeof(T) == sizeof(float)) asm volatile("" : "+f"(*(float *)&ar));
     else asm volatile("" : "+d"(*(double *)&ar));
     T lx[3], ly[3];
-    if (inv)
-        for (int i = 0; i < 3; i++) { lx[i] = (T)(V[i].x - x.x); ly[i] = (T)(V[i].y - x.y); }
+    if (inv) {
+        if (sizeof(T) == sizeof(float) && dl)   // FP32 coordinates relative to x (no FP64 work)
+            for (int i = 0; i < 3; i++) { lx[i] = (T)dl[i].x; ly[i] = (T)dl[i].y; }
+        else
+            for (int i = 0; i < 3; i++) { lx[i] = (T)(V[i].x - x.x); ly[i] = (T)(V[i].y - x.y); }
+    }
     for (int r = 0; r < n; r++) {
         T p0 = rule_l<T>(A, r, 0), p1 = rule_l<T>(A, r, 1), p2 = rule_l<T>(A, r, 2);
         T w = rule_w<T>(A, r) * ar;
@@ -362,11 +394,90 @@ __device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBu
             const float p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
             const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
             const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
-            sums_add<float>(S, A.fin_w[r] * ar, p0, p1, p2);
+            float w = A.fin_w[r] * ar;
+            if (A.kernel == NL_KERNEL_INV_DIST) {   // psi = c / |y - x|, coordinates relative to x
+                const float yx = m0 * x0 + m1 * xk + m2 * xn, yy = m0 * y0 + m1 * yk + m2 * yn;
+                w *= rsqrtf(yx * yx + yy * yy);
+            }
+            sums_add<float>(S, w, p0, p1, p2);
         }
         nqp += nr;
         fk[0] = fn[0]; fk[1] = fn[1]; fk[2] = fn[2];
         xk = xn; yk = yn;
+    }
+}
+
+// FP32 version of the near-singular rule (FP32-compensated path) for the whole triangle
+// with FP32 vertices dl relative to x: the same signed apex-x decomposition, Duffy collapse
+// and sinh substitution.  Its discrete choices are taken in FP64 (near_edge64) whenever
+// FP32 is within 1e-4 of a threshold, so the evaluated points are those of the FP64 rule.
+__device__ __forceinline__ void near_whole_f32(const NumArgs &A, const nlg::F2 dl[3], const D2 V[3], D2 x,
+                                               const nlg::F2 &e1, const nlg::F2 &e2, float inv_det,
+                                               Sums<float> &S, int64_t &nqp)
+{
+    sums_zero(S);
+    const float kc = (float)A.kc;
+    const int nu = A.duffy_n;
+    for (int i = 0; i < 3; i++) {
+        const nlg::F2 a = dl[i], b = dl[(i + 1) % 3];
+        float ex = b.x - a.x, ey = b.y - a.y;
+        const float L = sqrtf(ex * ex + ey * ey);
+        ex /= L;
+        ey /= L;
+        const float tA = a.x * ex + a.y * ey, tB = b.x * ex + b.y * ey;
+        const float Fx = a.x - tA * ex, Fy = a.y - tA * ey;
+        const float d = sqrtf(Fx * Fx + Fy * Fy);
+        const float UA = asinhf(fabsf(tA) / d), UB = asinhf(fabsf(tB) / d);
+        const float th = 1e-4f * L;
+        // U = asinh(|t| / d) moves by at most dt/|t| + dd/d; the FP32 coordinates carry an
+        // absolute error below 1e-6 M (M = max(|a|, |b|) + L), asinhf a few ulp
+        const float M = fmaxf(fmaxf(fabsf(a.x) + fabsf(a.y), fabsf(b.x) + fabsf(b.y)), L) + L;
+        auto near_int = [&](float U, float t) {
+            const float eps = 1e-6f * M * (1.f / d + 1.f / fabsf(t)) + 1e-5f * fmaxf(U, 1.f);
+            return fabsf(U - rintf(U)) < eps;
+        };
+        bool skip_edge = false, skipA = false, skipB = false;
+        int npA, npB;
+        if (!(d >= th) || !(fabsf(tA) >= th) || !(fabsf(tB) >= th) || near_int(UA, tA) || near_int(UB, tB)) {
+            const NearEdge64 q = near_edge64(V[i], V[(i + 1) % 3], x);
+            skip_edge = (q.d == 0.0);
+            skipA = (q.tA == 0.0);
+            skipB = (q.tB == 0.0);
+            npA = skip_edge || skipA ? 0 : near_panels64(q.tA, q.d);
+            npB = skip_edge || skipB ? 0 : near_panels64(q.tB, q.d);
+        } else {
+            npA = (int)ceilf(UA);
+            npB = (int)ceilf(UB);
+            npA = npA < 1 ? 1 : npA;
+            npB = npB < 1 ? 1 : npB;
+        }
+        if (skip_edge || d == 0.f) continue;
+        const float sigma = (Fx * ey - Fy * ex) > 0.f ? 1.f : -1.f;
+        for (int side = 0; side < 2; side++) {
+            const float tau = side == 0 ? tB : tA, U = side == 0 ? UB : UA;
+            const int npan = side == 0 ? npB : npA;
+            if ((side == 0 ? skipB : skipA) || npan == 0) continue;
+            const float sign = side == 0 ? sigma : -sigma;
+            const float sg = tau > 0.f ? 1.f : -1.f;
+            for (int pnl = 0; pnl < npan; pnl++) {
+                const float u0 = (float)pnl, u1 = (pnl + 1 < npan) ? (float)(pnl + 1) : fmaxf(U, u0);
+                const float hw = u1 - u0;
+                for (int j = 0; j < nu; j++) {
+                    const float u = u0 + hw * (float)A.gl_x[j];
+                    const float wu = hw * (float)A.gl_w[j];
+                    const float sh = sinhf(u);
+                    const float wx = Fx + sg * d * sh * ex, wy = Fy + sg * d * sh * ey;
+                    for (int k = 0; k < 2; k++) {
+                        const float sv = (float)A.gl2_x[k];
+                        const float rx = sv * wx - dl[0].x, ry = sv * wy - dl[0].y;
+                        const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
+                        const float l2 = (e1.x * ry - rx * e1.y) * inv_det;
+                        sums_add<float>(S, sign * sg * d * (float)A.gl2_w[k] * wu * kc, 1.f - l1 - l2, l1, l2);
+                        nqp++;
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -494,13 +605,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_interior(const NumArgs 
         const T akc = (T)(area_b * A.kc);
         int q0, q1;
         rule_range(A, ba, bb, q0, q1);
+        const bool inv = A.kernel == NL_KERNEL_INV_DIST;
+        nlg::F2 vl[3];
+        if (inv)
+            for (int i = 0; i < 3; i++) { vl[i].x = (float)(Vb[i].x - ba.x); vl[i].y = (float)(Vb[i].y - ba.y); }
         T v[21];
         for (int i = 0; i < 21; i++) v[i] = 0;
         for (int q = q0; q < q1; q++) {
             const OuterPt o = sq[q];
             Sums<T> S;
             int64_t nq = 0;
-            whole_sums<T>(A, Vb, akc, D2{o.x, o.y}, S, nq);
+            nlg::F2 dl[3];
+            if (inv)
+                for (int i = 0; i < 3; i++) { dl[i].x = vl[i].x - o.lx; dl[i].y = vl[i].y - o.ly; }
+            whole_sums<T>(A, Vb, akc, D2{o.x, o.y}, S, nq, inv ? dl : nullptr);
             combine<T>(o, S, v);
             acc.cnt++;
             acc.qp += nq;
@@ -532,15 +650,26 @@ struct CandData {
     int b, q0;
 };
 
+// longest edge of T_b in FP32 (the near field of the singular kernel)
+__device__ __forceinline__ float cand_diam(const CandData &c)
+{
+    const float e3x = c.e2x - c.e1x, e3y = c.e2y - c.e1y;
+    return sqrtf(fmaxf(fmaxf(c.e1x * c.e1x + c.e1y * c.e1y, c.e2x * c.e2x + c.e2y * c.e2y), e3x * e3x + e3y * e3y));
+}
+
 template <typename T>
 struct BoundaryShared {
     OuterPt sq[NL_MAXQ + 8];
     CandData cand[32];
     T acc[32][22];             // 21 block values and the non-empty flag of each lane's pair
     unsigned short queue[32 * (NL_MAXQ + 8)];    // undecided items (owner lane << 8 | q)
-    unsigned short wqueue[32 * (NL_MAXQ + 8)];   // whole items
+    // whole items from the front; whole items in the singular kernel's near field from the back
+    // (a batch holds at most 32 x n_q items in all)
+    unsigned short wqueue[32 * (NL_MAXQ + 8)];
     nlg::ClipBuf clip;         // per-lane FP32 clip buffers
 };
+
+constexpr int kQueueCap = 32 * (NL_MAXQ + 8);
 
 template <int BALL, typename T>
 __device__ __forceinline__ int classify_item(const NumArgs &A, const CandData &c, const OuterPt &o, nlg::F2 dl[3])
@@ -570,9 +699,13 @@ template <int BALL, typename T>
 __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
                                            int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb, int lane)
 {
-    if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON && A.kernel == NL_KERNEL_CONST) {
+    if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON) {
         nlg::F2 dl[3];
         for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
+        // the singular kernel's near field needs the FP64 path; a region inside T_b is far
+        // when T_b is (certified in FP32)
+        if (A.kernel == NL_KERNEL_INV_DIST && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
+            return exact_item_fp64<BALL, T>(A, c, o, S, nq, kind, nv, ncap, cb, lane);
         bool cut = false;
         int which = 0;
         const int n = nlg::clip_ngon_f32_sh(dl, A.geo.err0, A.geo, cb, lane, &which, &cut);
@@ -584,7 +717,7 @@ __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, 
             ncap = 0;
             if (!cut) {
                 const D2 Vb[3] = {{c.vx[0], c.vy[0]}, {c.vx[1], c.vy[1]}, {c.vx[2], c.vy[2]}};
-                whole_sums<T>(A, Vb, (T)c.akc, D2{o.x, o.y}, S, nq);
+                whole_sums<T>(A, Vb, (T)c.akc, D2{o.x, o.y}, S, nq, dl);
             } else {
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
                 poly_sums_sh(A, cb, which, lane, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
@@ -618,7 +751,8 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
     ncap = R.ncap;
     if (R.kind == nlg::KIND_WHOLE && R.ncap == 0 && A.kernel != NL_KERNEL_INV_DIST) {
         whole_sums<T>(A, Vb, (T)c.akc, x, S, nq);
-    } else if (sizeof(T) == sizeof(float) && A.kernel == NL_KERNEL_CONST && R.ncap == 0 && R.nv <= nlg::kClipCap) {
+    } else if (sizeof(T) == sizeof(float) && R.ncap == 0 && R.nv <= nlg::kClipCap &&
+               (A.kernel == NL_KERNEL_CONST || !nlg::is_near(R, Vb, x))) {
         // FP32 quadrature on the FP64 polygon (coordinates relative to x)
         for (int i = 0; i < R.nv; i++) {
             cb.x[0][i][lane] = (float)(R.P[i].x - x.x);
@@ -633,7 +767,8 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
     return true;
 }
 
-template <int BALL, typename T>
+// INV: the kernel is psi = c/|x - y| (near-field split), else the constant kernel
+template <int BALL, typename T, bool INV>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -648,7 +783,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
     acc_zero(acc);
     const int64_t es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
     const int nq_all = A.outer.n;
-    const bool inv = (A.kernel == NL_KERNEL_INV_DIST);
+    const bool inv = INV;
     for (int64_t base = es; base < e1; base += 32) {
         const int64_t e = base + lane;
         const bool valid = e < e1;
@@ -676,24 +811,31 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
         int nqueue = 0;
         __syncwarp();
         // phase 1: classify every (q, b) in lockstep; queue whole and undecided items
-        int nwhole = 0;
+        int nwhole = 0, nnear = 0;
         for (int q = 0; q < nq_all; q++) {
             const bool active = valid && q >= q0 && q < q1;
             int cls = nlg::CLS_EMPTY;
             if (active) {
                 nlg::F2 dl[3];
                 cls = classify_item<BALL, T>(A, c, sh.sq[q], dl);
-                // the singular kernel needs the near-field test: whole items take the exact path
-                if (inv && cls == nlg::CLS_WHOLE) cls = nlg::CLS_EXACT;
+                // singular kernel: whole items in the near field take the near rule (certified
+                // in FP32; undecided ones the FP64 path)
+                if (inv && cls == nlg::CLS_WHOLE) {
+                    const int nr = nlg::near_f32(dl, cand_diam(c), A.geo.tau);
+                    cls = nr == 0 ? nlg::CLS_WHOLE : (nr == 1 && sizeof(T) == sizeof(float) ? 3 : nlg::CLS_EXACT);
+                }
             }
             const unsigned mw = __ballot_sync(0xffffffffu, cls == nlg::CLS_WHOLE);
             const unsigned me = __ballot_sync(0xffffffffu, cls == nlg::CLS_EXACT);
+            const unsigned mn = __ballot_sync(0xffffffffu, cls == 3);
             const unsigned below = (1u << lane) - 1u;
             const unsigned short item = (unsigned short)((lane << 8) | q);
             if (cls == nlg::CLS_WHOLE) sh.wqueue[nwhole + __popc(mw & below)] = item;
             if (cls == nlg::CLS_EXACT) sh.queue[nqueue + __popc(me & below)] = item;
+            if (cls == 3) sh.wqueue[kQueueCap - 1 - (nnear + __popc(mn & below))] = item;
             nwhole += __popc(mw);
             nqueue += __popc(me);
+            nnear += __popc(mn);
         }
         __syncwarp();
         // phase 2a: whole items with all lanes
@@ -705,7 +847,32 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
             const D2 Vb[3] = {{cd.vx[0], cd.vy[0]}, {cd.vx[1], cd.vy[1]}, {cd.vx[2], cd.vy[2]}};
             Sums<T> S;
             int64_t nq = 0;
-            whole_sums<T>(A, Vb, (T)cd.akc, D2{o.x, o.y}, S, nq);
+            nlg::F2 dl[3];
+            if (INV)
+                for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
+            whole_sums<T>(A, Vb, (T)cd.akc, D2{o.x, o.y}, S, nq, INV ? dl : nullptr);
+            T w[21];
+            for (int k = 0; k < 21; k++) w[k] = 0;
+            combine<T>(o, S, w);
+            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[own][k], w[k]);
+            sh.acc[own][21] = (T)1;
+            acc.cnt++;
+            acc.qp += nq;
+            if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
+        }
+        // phase 2c: whole items in the singular kernel's near field (FP32 near rule)
+        for (int i = lane; INV && i < nnear; i += 32) {
+            const unsigned it = sh.wqueue[kQueueCap - 1 - i];
+            const int own = it >> 8, q = it & 0xff;
+            const CandData &cd = sh.cand[own];
+            const OuterPt o = sh.sq[q];
+            const D2 Vb[3] = {{cd.vx[0], cd.vy[0]}, {cd.vx[1], cd.vy[1]}, {cd.vx[2], cd.vy[2]}};
+            nlg::F2 dl[3];
+            for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
+            Sums<T> S;
+            int64_t nq = 0;
+            const nlg::F2 e1 = {cd.e1x, cd.e1y}, e2 = {cd.e2x, cd.e2y};
+            near_whole_f32(A, dl, Vb, D2{o.x, o.y}, e1, e2, cd.binv, *(Sums<float> *)&S, nq);
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);

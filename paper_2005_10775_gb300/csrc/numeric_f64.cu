@@ -3,13 +3,21 @@
 
 namespace {
 
+template <int BALL, bool INV>
+nl_status launch_boundary_k(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads)
+{
+    const size_t smem = sizeof(nlq::BoundaryShared<double>) * nlq::kWarpsPerBlock;
+    NL_CK(cudaFuncSetAttribute(nlq::k_boundary<BALL, double, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem));
+    nlq::k_boundary<BALL, double, INV><<<grid, threads, smem, ctx->stream>>>(A); ++ctx->launches;
+    return NL_OK;
+}
+
 template <int BALL>
 nl_status launch_boundary(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads)
 {
-    const size_t smem = sizeof(nlq::BoundaryShared<double>) * nlq::kWarpsPerBlock;
-    NL_CK(cudaFuncSetAttribute(nlq::k_boundary<BALL, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    nlq::k_boundary<BALL, double><<<grid, threads, smem, ctx->stream>>>(A); ++ctx->launches;
-    return NL_OK;
+    if (A.kernel == NL_KERNEL_INV_DIST) return launch_boundary_k<BALL, true>(ctx, A, grid, threads);
+    return launch_boundary_k<BALL, false>(ctx, A, grid, threads);
 }
 
 }  // namespace

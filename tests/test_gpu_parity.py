@@ -109,13 +109,19 @@ def test_parity_barycenter_32_full_size(nl, ctx):
     np.testing.assert_array_equal(h, out["hash_a"])
 
 
+@pytest.mark.parametrize("ball", ["ngon", "approxcaps", "nocaps", "barycenter"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
-def test_parity_inv_dist_kernel(nl, ctx, prec):
-    p = small_problem("ngon", n=24, kernel="inv_dist")
+def test_parity_inv_dist_kernel(nl, ctx, ball, prec):
+    # psi = c/|x-y|: far pairs, pairs in the near field of the outer point and cut pairs all
+    # evaluate the points of the oracle's rule (same counts and hashes)
+    p = small_problem(ball, n=24, kernel="inv_dist")
     out = O.assemble(p.mesh, oracle_cfg(p, duffy_n=4), want_hash=True)
     Dg, stats = gpu_assemble(nl, ctx, p, prec, duffy_n=4)
     compare(Dg, O.to_csr(out), prec)
     assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
+    h, c, q = gpu_interactions(nl, ctx, p, duffy_n=4)
+    np.testing.assert_array_equal(q, out["qp_a"])
+    np.testing.assert_array_equal(h, out["hash_a"])
 
 
 @pytest.mark.parametrize("ball", ["nocaps", "exactcaps"])
