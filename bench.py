@@ -148,6 +148,207 @@ def cpu_baseline(problem, seconds, steps=1):
                       f"{qp // max(steps, 1)} qp-pairs per step, FP64"}, tt / steps
 
 
+def cpu_baseline_batch(problems, seconds):
+    """The FP64 oracle on a bounded sample of the batched workload: a few evenly spaced
+    outer triangles of every problem (each against every triangle of its mesh)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+
+    def cfg(p):
+        return dict(delta=p.delta, ball=p.ball, outer=p.outer, inner=p.inner, kernel=p.kernel,
+                    kernel_c=p.kernel_c, ngon_off=p.ngon_off, cap_m=p.cap_m)
+    p0 = problems[0]
+    probe = np.linspace(0, p0.mesh.nt - 1, num=max(cores, 4)).astype(np.int32)
+    t0 = time.perf_counter()
+    O.assemble(p0.mesh, cfg(p0), a_list=probe, nthreads=cores)
+    per_a = max(time.perf_counter() - t0, 1e-3) / len(probe) / p0.mesh.nt   # seconds per outer triangle per K
+    per_round = per_a * sum(p.mesh.nt for p in problems)
+    k = max(1, int(seconds / per_round))
+    qp, tt, na = 0, 0.0, 0
+    for p in problems:
+        K = p.mesh.nt
+        a_list = np.linspace(0, K - 1, num=min(k * max(cores, 1), K)).astype(np.int32)
+        t0 = time.perf_counter()
+        out = O.assemble(p.mesh, cfg(p), a_list=a_list, nthreads=cores)
+        tt += time.perf_counter() - t0
+        qp += out["n_qp_pairs"]
+        na += len(a_list)
+        if tt > 2.0 * seconds:
+            break
+    return {"value": qp / tt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{na} outer triangles spread evenly over the problems of the batch, each against every "
+                      f"triangle of its mesh, {qp} qp-pairs, FP64"}, tt
+
+
+def batch_bench(args, nl, ctx, stream, dev, world, dist, rank):
+    """The batched workload: 64 independent assemblies (delta 0.05 .. 0.2, K 2450 .. 38088,
+    nocaps / approxcaps) in one nl_assemble_batch, against 64 sequential nl_assemble calls;
+    re-assembly by the captured graph (nl_batch_run) against 64 nl_assemble_numeric calls."""
+    import numpy as np
+    import torch
+
+    from paper_2005_10775_gb300 import inputs as I
+    probs = I.batch_problems()
+    keep = nl._Keep()
+
+    def dev_mesh(m):
+        return nl.make_mesh(type("DevMesh", (), dict(vx=torch.tensor(m.vx, device=dev),
+                                                     vy=torch.tensor(m.vy, device=dev),
+                                                     tri=torch.tensor(m.tri, device=dev))), keep)
+    meshes = [dev_mesh(p.mesh) for p in probs]
+
+    def cfgs_for(prec):
+        return [nl.config_of(p, keep, prec=prec) for p in probs]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        t = torch.tensor([tot], device=dev, dtype=torch.float64)
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()) / steps
+
+    state = {}
+
+    def batch_once(cfgs, keep_out=False):
+        outs = nl.nl_assemble_batch(ctx, meshes, cfgs)
+        state["stats"] = [(o.n_pairs, o.n_qp_pairs, o.n_inter, o.nnz) for o in outs]
+        state["phase"] = nl.nl_last_timings(ctx)
+        if keep_out:
+            return outs
+        for o in outs:
+            nl.nl_csr_free(ctx, o)
+
+    def seq_once(cfgs):
+        for mh, c in zip(meshes, cfgs):
+            o = nl.nl_assemble(ctx, mh, c)
+            nl.nl_csr_free(ctx, o)
+
+    cfgs = cfgs_for(args.prec)
+    # first batch of this shape: the autotuner picks the schedule (kept in the context)
+    h, outs = nl.nl_batch_create(ctx, meshes, cfgs)
+    tune = nl.nl_batch_get_info(h)
+    for _ in range(args.warmup):
+        batch_once(cfgs)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    l0 = nl.nl_launch_count(ctx)
+    phases = np.zeros(4)
+
+    def batch_step():
+        batch_once(cfgs)
+        phases[:] += state["phase"]
+    ms_batch = timed(batch_step, args.steps, 0)
+    launches = nl.nl_launch_count(ctx) - l0
+    ck = clocks.stop()
+    phases /= args.steps
+    stats = np.array(state["stats"], dtype=np.int64)
+    n_qp = int(stats[:, 1].sum())
+    n_inter = int(stats[:, 2].sum())
+    ms_seq = timed(lambda: seq_once(cfgs), max(1, args.steps // 2), 1)
+    # re-assembly of the values: one graph launch against 64 numeric calls
+    ms_replay = timed(lambda: nl.nl_batch_run(ctx, h), args.steps, 1)
+
+    def seq_numeric():
+        for o in outs:
+            nl.nl_assemble_numeric(ctx, o)
+    ms_seq_num = timed(seq_numeric, args.steps, 1)
+    nl.nl_batch_destroy(ctx, h)
+    for o in outs:
+        nl.nl_csr_free(ctx, o)
+    fp64 = None
+    if args.fp64_steps > 0 and args.prec != "fp64":
+        c64 = cfgs_for("fp64")
+        ms64 = timed(lambda: batch_once(c64), args.fp64_steps, 1)
+        fp64 = {"ms_per_step": ms64, "value": n_qp * world / (ms64 / 1e3), "numeric_ms": state["phase"][1]}
+    e2e = None
+    if not args.no_e2e:
+        hmeshes = [nl.make_mesh(p.mesh, keep) for p in probs]
+        hcfgs = [nl.config_of(p, keep, prec=args.prec) for p in probs]
+        nnzs = [int(s[3]) for s in state["stats"]] if state.get("stats") else [1] * len(probs)
+        bufs = [(torch.empty(p.mesh.nv + 1, dtype=torch.int64).pin_memory(),
+                 torch.empty(max(z, 1), dtype=torch.int32).pin_memory(),
+                 torch.empty(max(z, 1), dtype=torch.float64).pin_memory()) for p, z in zip(probs, nnzs)]
+
+        def e2e_once():
+            os_ = nl.nl_assemble_batch(ctx, hmeshes, hcfgs)
+            for o, (rp, ci, va) in zip(os_, bufs):
+                nl._check(ctx, nl.LIB.nl_csr_download(ctx, nl.ctypes.byref(o), rp.data_ptr(), ci.data_ptr(),
+                                                      va.data_ptr()))
+                nl.nl_csr_free(ctx, o)
+        e2e_once()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_once()
+        torch.cuda.synchronize()
+        te = torch.tensor([(time.perf_counter() - t0) / args.steps], device=dev, dtype=torch.float64)
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        h2d = sum(p.mesh.vx.nbytes + p.mesh.vy.nbytes + p.mesh.tri.nbytes for p in probs)
+        d2h = sum(8 * (p.mesh.nv + 1) + 12 * z for p, z in zip(probs, nnzs))
+        e2e = {"value": n_qp * world / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    peaks, src = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    achieved = (FLOP_PER_QP * n_qp + FLOP_PER_INTER * n_inter) / (phases[1] / 1e3) / 1e12
+    Ks = [p.mesh.nt for p in probs]
+    line = {
+        "metric": METRIC, "value": n_qp * world / (ms_batch / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32c" if args.prec == "fp32c" else "f64",
+        "data": "synthetic",
+        "config": {"workload": "batch64", "problems": len(probs), "K_total": int(sum(Ks)), "K_min": min(Ks),
+                   "K_max": max(Ks), "deltas": list(I.BATCH_DELTAS), "balls": "nocaps / approxcaps (m=2)",
+                   "outer": "dunavant7", "inner": "dunavant7", "kernel": "const",
+                   "parallelism": f"replica x{world}", "l2": "flushed (512 MB write) before every step",
+                   "n_qp_pairs": n_qp, "n_inter": n_inter, "nnz_total": int(stats[:, 3].sum()),
+                   "phase_ms": {"prepare": phases[0], "numeric": phases[1], "symbolic": phases[2],
+                                "scatter": phases[3]},
+                   "schedule": tune},
+        "sequential": {"ms_per_step": ms_seq, "value": n_qp * world / (ms_seq / 1e3),
+                       "what": "64 nl_assemble calls, one after the other"},
+        "speedup_batch_vs_sequential": ms_seq / ms_batch,
+        "reassembly": {"graph_ms": ms_replay, "sequential_numeric_ms": ms_seq_num,
+                       "speedup": ms_seq_num / ms_replay,
+                       "what": "values on unchanged meshes: one nl_batch_run graph launch vs 64 "
+                               "nl_assemble_numeric calls"},
+        "fp64": fp64,
+        "speedup_fp32c_vs_fp64": (fp64["ms_per_step"] / ms_batch) if fp64 else None,
+        "roofline": {"bound": "alu", "kernel": "k_numeric_batch (pair geometry + quadrature, all problems)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_mhz:.0f} MHz "
+                                    f"(clock from MEASURED_PEAKS.json, {src})",
+                     "traffic": None},
+        "clocks": ck,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"], _ = cpu_baseline_batch(probs, args.cpu_seconds)
+    return line
+
+
 def solve_phase(nl, ctx, m, p, prec, stream, dev, keep):
     """A = D[Omega, Omega], F = G - D[Omega, Omega_I] g and the CG solve to 1e-10 for u = |x|^2
     (f = -4), timed with CUDA events on the library's stream; one FP32 SpMV timed for GB/s."""
@@ -195,15 +396,25 @@ def reference_arm(args, rank, world):
     from paper_2005_10775_gb300 import inputs as I
     if rank != 0:
         return
-    p = I.problem(args.workload)
     per_step = max(2.0, min(20.0, 60.0 / max(args.steps, 1)))
-    cpu_baseline(p, per_step / 4, steps=1) if args.warmup else None
-    base, ms = cpu_baseline(p, per_step, steps=args.steps)
+    if args.workload == "batch64":
+        probs = I.batch_problems()
+        tt = 0.0
+        for _ in range(args.steps):
+            base, t = cpu_baseline_batch(probs, per_step)
+            tt += t
+        ms = tt / args.steps
+        conf = {"workload": "batch64", "problems": len(probs), "K_total": sum(q.mesh.nt for q in probs)}
+    else:
+        p = I.problem(args.workload)
+        cpu_baseline(p, per_step / 4, steps=1) if args.warmup else None
+        base, ms = cpu_baseline(p, per_step, steps=args.steps)
+        conf = {"workload": args.workload, "K": p.mesh.nt, "ball": p.ball, "outer": p.outer, "inner": p.inner,
+                "delta": p.delta}
     line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "K": p.mesh.nt, "ball": p.ball, "outer": p.outer,
-                       "inner": p.inner, "delta": p.delta},
+            "config": conf,
             "cpu_baseline": base,
             "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -227,13 +438,21 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    p = I.problem(args.workload)
-    m = p.mesh
     # a dedicated stream shared by the library and the timing events (the legacy default
     # stream has handle 0, which the C ABI reads as "create a private stream")
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = nl.nl_create(local, stream.cuda_stream)
+    if args.workload == "batch64":
+        line = batch_bench(args, nl, ctx, stream, dev, world, dist, rank)
+        nl.nl_destroy(ctx)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+    p = I.problem(args.workload)
+    m = p.mesh
     keep = nl._Keep()
     dmesh = type("DevMesh", (), dict(vx=torch.tensor(m.vx, device=dev), vy=torch.tensor(m.vy, device=dev),
                                      tri=torch.tensor(m.tri, device=dev)))

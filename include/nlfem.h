@@ -124,8 +124,9 @@ const char *nl_last_error(nl_ctx *ctx);
    Sec. 7.2 first remark: whole balls, all K x K pairs).  Runs the cell-list neighbour
    search, the pair geometry and quadrature, the symbolic CSR pattern (union over
    pairs with a non-empty region) and the numeric scatter.  *out receives a new
-   library-owned n x n CSR (n = mesh->nv).  Synchronises the stream once (to size the
-   pattern). */
+   library-owned n x n CSR (n = mesh->nv).  Synchronises the stream three times (to
+   size the candidate-search grid, the candidate lists and the pattern); device memory
+   comes from the device's stream-ordered pool on the context's stream. */
 nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_csr *out);
 
 /* Recompute the values of an nl_assemble result for the same mesh and configuration
@@ -133,8 +134,57 @@ nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl
    synchronisation: can be captured in a CUDA graph. */
 nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *inout);
 
-/* Assemble n independent problems.  The numeric phases of all problems run as one
-   persistent launch over a shared work queue, captured once into a CUDA graph. */
+/* ---- batches of independent problems ----
+   Many assemblies of uneven size, delta, ball and rule at once.  Every problem is
+   assembled exactly as nl_assemble would (same interaction set and pattern, values
+   equal up to the order of the FP64 scatter additions), but the batch:
+     - runs each preparation and symbolic stage for all problems before synchronising,
+       so the whole batch waits on the host three times, not three times per problem;
+     - runs the numeric phase (pair geometry + quadrature) of all problems in one pair
+       of persistent launches (interior candidates, then boundary candidates) per value
+       type x kernel type present: their warps take work items (a run of outer triangles
+       of one problem) from a global counter, and the ball mode is dispatched per item,
+       so nocaps and approxcaps problems share them;
+     - scatters all problems in one launch per value type;
+     - captures the numeric phase + scatter of the whole batch in a CUDA graph that
+       nl_batch_run replays (re-assembly of the values on unchanged meshes).
+   The work-item order and size are picked by a built-in autotuner: the first batch of
+   a given shape (sizes, candidate counts, balls, rules, precisions) times a few
+   schedules of the numeric launch and keeps the fastest in the context; later batches
+   of the same shape reuse it.  Every schedule yields the same values: each outer
+   triangle's blocks are produced by one warp in a fixed order. */
+typedef struct nl_batch nl_batch;
+
+enum { NL_BATCH_NO_TUNE = 1 };   /* nl_batch_create flag: default schedule, no timing runs */
+enum { NL_SCHED_DEFAULT = 0, NL_SCHED_TUNED = 1, NL_SCHED_CACHED = 2 };
+
+typedef struct {
+    int32_t chunk;        /* outer triangles per work item */
+    int32_t order;        /* 0: problems in input order; 1: costliest problems first (estimated
+                             candidates x outer points x inner points per triangle) */
+    int32_t blocks;       /* persistent grid of the first boundary-candidate launch (blocks of 128 threads) */
+    int32_t launches;     /* numeric launches per run: one interior launch per value type, one boundary
+                             launch per value type x ball x kernel type */
+    int32_t source;       /* NL_SCHED_*: how the schedule was chosen */
+    int32_t n_tried;      /* schedules timed by the autotuner in this nl_batch_create */
+    double tuned_ms;      /* numeric phase of the batch with the chosen schedule (NL_SCHED_TUNED) */
+    double default_ms;    /* the same with the default schedule (NL_SCHED_TUNED) */
+} nl_batch_info;
+
+/* Assemble problems i = 0..n-1 (meshes[i], cfgs[i]) into outs[i] (library-owned, freed
+   with nl_csr_free like an nl_assemble result) and return a handle that can re-run the
+   numeric assembly of the whole batch.  The outs must stay allocated while the handle
+   lives.  Errors: those of nl_assemble for the first failing problem (outs all zeroed),
+   NL_EINVAL for n < 1 or null arrays. */
+nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const nl_config *cfgs, nl_csr *outs,
+                          int32_t flags, nl_batch **batch);
+/* Replay the captured numeric phase + scatter of every problem of the batch (one graph
+   launch, stream-ordered, no host synchronisation). */
+nl_status nl_batch_run(nl_ctx *ctx, nl_batch *batch);
+nl_status nl_batch_get_info(const nl_batch *batch, nl_batch_info *info);
+/* Release the handle (not the outs). */
+void nl_batch_destroy(nl_ctx *ctx, nl_batch *batch);
+/* nl_batch_create + nl_batch_destroy: assemble n independent problems. */
 nl_status nl_assemble_batch(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const nl_config *cfgs,
                             nl_csr *outs);
 
@@ -173,11 +223,15 @@ nl_status nl_cg(nl_ctx *ctx, const nl_csr *A, const double *b, double *x, double
 /* Copy a CSR to host arrays row_ptr[n+1], col_idx[nnz], val[nnz] (any may be NULL). */
 nl_status nl_csr_download(nl_ctx *ctx, const nl_csr *m, int64_t *row_ptr, int32_t *col_idx, double *val);
 
-/* Release the device buffers of m (safe on a zeroed nl_csr). */
+/* Release the device buffers of m (safe on a zeroed nl_csr).  Stream-ordered on the
+   context's stream: work already queued there that uses m finishes first; work on
+   other streams must be complete (or ordered before the call) by the caller. */
 void nl_csr_free(nl_ctx *ctx, nl_csr *m);
 
-/* Device time of the phases of the last nl_assemble (ms): [0] preprocessing + cell list,
-   [1] pair geometry + quadrature, [2] symbolic pattern, [3] numeric scatter. */
+/* Device time of the phases of the last nl_assemble or nl_batch_create (ms):
+   [0] preprocessing + cell list (for a batch: of all problems, plus the autotuner's
+   timing runs when it ran), [1] pair geometry + quadrature, [2] symbolic pattern,
+   [3] numeric scatter. */
 nl_status nl_last_timings(nl_ctx *ctx, double *ms4);
 
 /* nl_cg for callers that cannot allocate device memory: a framework that has given all

@@ -141,7 +141,9 @@ void gauss_legendre01(int n, double *x, double *w)
     }
 }
 
-nl_status validate(nl_ctx *ctx, const nl_mesh *m, const nl_config *c)
+}  // namespace
+
+nl_status nl_validate(nl_ctx *ctx, const nl_mesh *m, const nl_config *c)
 {
     if (!ctx) return NL_EINVAL;
     if (!m || !c) return nl_fail(ctx, NL_EINVAL, "null mesh or config");
@@ -163,7 +165,7 @@ nl_status validate(nl_ctx *ctx, const nl_mesh *m, const nl_config *c)
     return NL_OK;
 }
 
-nl_status fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
+nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
 {
     memset(&A, 0, sizeof A);
     const nl_config &c = P->cfg;
@@ -194,6 +196,7 @@ nl_status fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
     gauss_legendre01(A.duffy_n, A.gl_x, A.gl_w);
     gauss_legendre01(2, A.gl2_x, A.gl2_w);
     A.kernel = c.kernel;
+    A.ball = c.ball;
     A.kc = c.kernel_c;
     A.geo.delta = c.delta;
     A.geo.d2 = P->d2;
@@ -252,8 +255,8 @@ nl_status fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
     A.geo.b_in2 = (float)((c.delta - tau) * (c.delta - tau));
     A.geo.b_out2 = (float)((c.delta + tau) * (c.delta + tau));
     for (int r = 0; r < A.inner.n; r++) {
-        for (int i = 0; i < 3; i++) A.fin_l[r][i] = (float)A.inner.l[r][i];
-        A.fin_w[r] = (float)A.inner.w[r];
+        A.fin[r] = make_float4((float)A.inner.l[r][0], (float)A.inner.l[r][1], (float)A.inner.l[r][2],
+                               (float)A.inner.w[r]);
     }
     A.flag = P->flag;
     A.blk = P->blk;
@@ -266,17 +269,13 @@ nl_status fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
     return NL_OK;
 }
 
-nl_status alloc_numeric(nl_ctx *ctx, nl_plan *P)
+nl_status nl_alloc_numeric(nl_ctx *ctx, nl_plan *P)
 {
     nl_status s;
     const size_t tsz = P->cfg.prec == NL_PREC_FP64 ? sizeof(double) : sizeof(float);
     if ((s = nl_alloc(ctx, &P->flag, (size_t)P->E)) != NL_OK) return s;
-    void *blk = nullptr;
-    cudaError_t e = cudaMalloc(&blk, tsz * 15 * (size_t)(P->E ? P->E : 1));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return nl_fail(ctx, NL_ENOMEM, "pair-block buffer allocation failed");
-    }
+    unsigned char *blk = nullptr;
+    if ((s = nl_alloc(ctx, &blk, tsz * 15 * (size_t)(P->E ? P->E : 1))) != NL_OK) return s;
     P->blk = blk;
     if ((s = nl_alloc(ctx, &P->maa, 6 * (size_t)P->K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->qp_a, (size_t)P->K)) != NL_OK) return s;
@@ -287,10 +286,12 @@ nl_status alloc_numeric(nl_ctx *ctx, nl_plan *P)
     return NL_OK;
 }
 
+namespace {
+
 nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats)
 {
     nlq::NumArgs A;
-    nl_status s = fill_args(ctx, P, A, stats);
+    nl_status s = nl_fill_args(ctx, P, A, stats);
     if (s != NL_OK) return s;
     if (P->cfg.prec == NL_PREC_FP64) return nl_launch_numeric_f64(ctx, A, P->cfg.ball);
     return nl_launch_numeric_f32(ctx, A, P->cfg.ball);
@@ -298,14 +299,37 @@ nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats)
 
 }  // namespace
 
-void nl_plan_free(nl_plan *P)
+void nl_plan_free(nl_plan *P, cudaStream_t s)
 {
     if (!P) return;
-    nl_free(P->tri); nl_free(P->tx); nl_free(P->ty); nl_free(P->bx); nl_free(P->by);
-    nl_free(P->rad); nl_free(P->area); nl_free(P->ngon); nl_free(P->nbr_ptr); nl_free(P->nbr_idx); nl_free(P->nbr_split);
-    nl_free(P->flag); nl_free(P->blk); nl_free(P->maa); nl_free(P->qp_a); nl_free(P->cnt_a);
-    nl_free(P->hash_a); nl_free(P->lslot); nl_free(P->tslot); nl_free(P->W); nl_free(P->val32);
-    nl_free(P->err);
+    nl_free(P->tri, s); nl_free(P->tx, s); nl_free(P->ty, s); nl_free(P->bx, s); nl_free(P->by, s);
+    nl_free(P->rad, s); nl_free(P->area, s); nl_free(P->ngon, s); nl_free(P->nbr_ptr, s); nl_free(P->nbr_idx, s);
+    nl_free(P->nbr_split, s); nl_free(P->flag, s); nl_free(P->blk, s); nl_free(P->maa, s); nl_free(P->qp_a, s);
+    nl_free(P->cnt_a, s); nl_free(P->hash_a, s); nl_free(P->lslot, s); nl_free(P->tslot, s); nl_free(P->W, s);
+    nl_free(P->val32, s); nl_free(P->err, s);
+}
+
+nl_status nl_host_slots(nl_ctx *ctx, int n, nl_host_slot **out)
+{
+    if (n < 1) n = 1;
+    if (ctx->nslots < n) {
+        // the stream may still be copying into the old slots
+        NL_CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->slots) cudaFreeHost(ctx->slots);
+        ctx->slots = nullptr;
+        ctx->nslots = 0;
+        const int cap = n < 64 ? 64 : n;
+        cudaError_t e = cudaMallocHost((void **)&ctx->slots, sizeof(nl_host_slot) * (size_t)cap);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ctx->slots = nullptr;
+            return nl_fail(ctx, NL_ENOMEM, "pinned host allocation failed");
+        }
+        ctx->nslots = cap;
+    }
+    memset(ctx->slots, 0, sizeof(nl_host_slot) * (size_t)n);
+    *out = ctx->slots;
+    return NL_OK;
 }
 
 nl_status nl_run_numeric(nl_ctx *ctx, nl_plan *P, bool with_hash) { return run_numeric(ctx, P, with_hash); }
@@ -330,6 +354,21 @@ nl_status nl_create(nl_ctx **out, int device, void *stream)
         ctx->own_stream = (e == cudaSuccess);
     }
     for (int i = 0; e == cudaSuccess && i < 5; i++) e = cudaEventCreate(&ctx->ev[i]);
+    if (e == cudaSuccess) {
+        // keep freed pool memory cached by this process (up to 8 GiB) instead of handing it
+        // back to the driver at every synchronisation: later assemblies allocate without
+        // driver calls.  This is a property of the process's pool, not of the device.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t thr = 0;
+            if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) == cudaSuccess &&
+                thr < (uint64_t(8) << 30)) {
+                thr = uint64_t(8) << 30;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+        }
+        cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         nl_destroy(ctx);
@@ -344,6 +383,9 @@ void nl_destroy(nl_ctx *ctx)
     if (!ctx) return;
     for (int i = 0; i < 5; i++)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->slots) cudaFreeHost(ctx->slots);
+    nl_tune_cache_free(ctx->tune);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -352,7 +394,7 @@ const char *nl_last_error(nl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null c
 
 nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_csr *out)
 {
-    nl_status s = validate(ctx, mesh, cfg);
+    nl_status s = nl_validate(ctx, mesh, cfg);
     if (s != NL_OK) return s;
     if (!out) return nl_fail(ctx, NL_EINVAL, "null output");
     memset(out, 0, sizeof *out);
@@ -360,18 +402,43 @@ nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl
     nl_plan *P = new (std::nothrow) nl_plan();
     if (!P) return nl_fail(ctx, NL_ENOMEM, "host allocation failed");
     out->priv = P;
-    NL_CK(cudaEventRecord(ctx->ev[0], ctx->stream));
-    if ((s = nl_prepare_mesh(ctx, mesh, cfg, P)) != NL_OK) goto fail;
-    if ((s = alloc_numeric(ctx, P)) != NL_OK) goto fail;
-    NL_CK(cudaEventRecord(ctx->ev[1], ctx->stream));
+    nl_host_slot *h = nullptr;
+    nl_prep *T = nullptr;
+    nl_pat *Q = nullptr;
+    cudaError_t e;
+    if ((s = nl_host_slots(ctx, 1, &h)) != NL_OK) goto fail;
+    T = nl_prep_new();
+    Q = nl_pat_new();
+    if (!T || !Q) {
+        s = nl_fail(ctx, NL_ENOMEM, "host allocation failed");
+        goto fail;
+    }
+    // three host synchronisations: candidate-search grid, candidate count, pattern size
+    if ((e = cudaEventRecord(ctx->ev[0], ctx->stream)) != cudaSuccess) goto cuda_fail;
+    if ((s = nl_prepare_a(ctx, mesh, cfg, P, T, h)) != NL_OK) goto fail;
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) goto cuda_fail;
+    if ((s = nl_prepare_b(ctx, P, T, h)) != NL_OK) goto fail;
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) goto cuda_fail;
+    if ((s = nl_prepare_c(ctx, P, T, h)) != NL_OK) goto fail;
+    if ((s = nl_alloc_numeric(ctx, P)) != NL_OK) goto fail;
+    if ((e = cudaEventRecord(ctx->ev[1], ctx->stream)) != cudaSuccess) goto cuda_fail;
     if ((s = run_numeric(ctx, P, false)) != NL_OK) goto fail;
-    NL_CK(cudaEventRecord(ctx->ev[2], ctx->stream));
-    if ((s = nl_build_pattern(ctx, P, out)) != NL_OK) goto fail;
-    NL_CK(cudaEventRecord(ctx->ev[3], ctx->stream));
+    if ((e = cudaEventRecord(ctx->ev[2], ctx->stream)) != cudaSuccess) goto cuda_fail;
+    if ((s = nl_pattern_a(ctx, P, out, Q, h)) != NL_OK) goto fail;
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) goto cuda_fail;
+    if ((s = nl_prepare_check(ctx, h)) != NL_OK) goto fail;
+    if ((s = nl_pattern_b(ctx, P, out, Q, h)) != NL_OK) goto fail;
+    if ((e = cudaEventRecord(ctx->ev[3], ctx->stream)) != cudaSuccess) goto cuda_fail;
     if ((s = nl_run_scatter(ctx, P, out)) != NL_OK) goto fail;
-    NL_CK(cudaEventRecord(ctx->ev[4], ctx->stream));
+    if ((e = cudaEventRecord(ctx->ev[4], ctx->stream)) != cudaSuccess) goto cuda_fail;
+    nl_prep_delete(T, ctx->stream);
+    nl_pat_delete(Q, ctx->stream);
     return NL_OK;
+cuda_fail:
+    s = nl_cuda_fail(ctx, e, "stream operation");
 fail:
+    nl_prep_delete(T, ctx->stream);
+    nl_pat_delete(Q, ctx->stream);
     nl_csr_free(ctx, out);
     return s;
 }
@@ -390,11 +457,11 @@ nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *m)
 nl_status nl_interactions(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, uint64_t *hash_a,
                           int64_t *count_a, int64_t *qp_a)
 {
-    nl_status s = validate(ctx, mesh, cfg);
+    nl_status s = nl_validate(ctx, mesh, cfg);
     if (s != NL_OK) return s;
     NL_CK(cudaSetDevice(ctx->device));
     nl_plan P;
-    if ((s = nl_prepare_mesh(ctx, mesh, cfg, &P)) == NL_OK && (s = alloc_numeric(ctx, &P)) == NL_OK &&
+    if ((s = nl_prepare_mesh(ctx, mesh, cfg, &P)) == NL_OK && (s = nl_alloc_numeric(ctx, &P)) == NL_OK &&
         (s = run_numeric(ctx, &P, true)) == NL_OK) {
         cudaError_t e = cudaSuccess;
         if (hash_a && e == cudaSuccess)
@@ -406,7 +473,7 @@ nl_status nl_interactions(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) s = nl_cuda_fail(ctx, e, "download of interaction statistics");
     }
-    nl_plan_free(&P);
+    nl_plan_free(&P, ctx->stream);
     return s;
 }
 
@@ -426,15 +493,15 @@ nl_status nl_csr_download(nl_ctx *ctx, const nl_csr *m, int64_t *row_ptr, int32_
 
 void nl_csr_free(nl_ctx *ctx, nl_csr *m)
 {
-    (void)ctx;
     if (!m) return;
-    if (ctx && ctx->stream) cudaStreamSynchronize(ctx->stream);
-    nl_free(m->row_ptr);
-    nl_free(m->col_idx);
-    nl_free(m->val);
-    if (m->priv) {
-        nl_plan *P = (nl_plan *)m->priv;
-        nl_plan_free(P);
+    nl_plan *P = (nl_plan *)m->priv;
+    // stream-ordered: work already queued on the context's stream finishes first
+    cudaStream_t s = ctx ? ctx->stream : (P ? P->stream : nullptr);
+    nl_free(m->row_ptr, s);
+    nl_free(m->col_idx, s);
+    nl_free(m->val, s);
+    if (P) {
+        nl_plan_free(P, s);
         delete P;
     }
     memset(m, 0, sizeof *m);

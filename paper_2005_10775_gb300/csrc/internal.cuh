@@ -14,6 +14,21 @@
 #define NL_MAXCAND 4096     // candidate neighbours per triangle (sorted in shared memory)
 #define NL_HASH_CAP 8192    // per-row column hash set (shared memory) in the symbolic phase
 
+// Small results of the device phases that the host needs (sizes, statistics, error
+// words).  The phases copy them, stream-ordered, into pinned slots owned by the
+// context; the host reads a slot only after synchronising the stream, so a batch of
+// problems needs one synchronisation per phase instead of one per problem.
+struct nl_host_slot {
+    double mesh[6];               // xmin, xmax, ymin, ymax, r_max, h_max
+    int64_t E;                    // candidate pairs
+    int64_t nnz;                  // pattern entries
+    unsigned long long pat[4];    // pairs, qp-pairs, interactions, longest row
+    int bad;                      // degenerate / clockwise / out-of-range triangles
+    int ovf;                      // cell-list or candidate-list overflow
+    int row_ovf;                  // pattern row overflow
+    int err;                      // numeric-phase error word
+};
+
 struct nl_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -22,10 +37,17 @@ struct nl_ctx {
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     double last_ms[4] = {0, 0, 0, 0};
     int64_t launches = 0;         // kernels this context has launched (nl_launch_count)
+    nl_host_slot *slots = nullptr;  // pinned
+    int nslots = 0;
+    struct nl_tune_cache *tune = nullptr;   // batch schedules picked by the autotuner (batch.cu)
 };
+
+// pinned host slots for n problems (grown on demand; invalidates earlier slot pointers)
+nl_status nl_host_slots(nl_ctx *ctx, int n, nl_host_slot **out);
 
 // Device-resident state of one assembled problem (held by nl_csr.priv).
 struct nl_plan {
+    cudaStream_t stream = nullptr;   // stream the buffers were allocated on (freed stream-ordered)
     int K = 0, J = 0;
     nl_config cfg{};
     double d2 = 0.0, hmax = 0.0, rmax = 0.0, rin = 0.0;
@@ -68,25 +90,27 @@ nl_status nl_cuda_fail(nl_ctx *ctx, cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return nl_cuda_fail(ctx, e_, #call);       \
     } while (0)
 
-// Device allocation that reports failures as NL_ENOMEM.
+// Device allocation from the device's stream-ordered pool, on the context's stream
+// (no device synchronisation); failures are reported as NL_ENOMEM.
 template <class T>
 inline nl_status nl_alloc(nl_ctx *ctx, T **p, size_t n)
 {
     *p = nullptr;
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    cudaError_t e = cudaMallocAsync((void **)p, n * sizeof(T), ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
-        return nl_fail(ctx, NL_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+        return nl_fail(ctx, NL_ENOMEM, "device allocation of " + std::to_string(n * sizeof(T)) + " bytes failed");
     }
     return NL_OK;
 }
 
+// stream-ordered release of an nl_alloc buffer
 template <class T>
-inline void nl_free(T *&p)
+inline void nl_free(T *&p, cudaStream_t s)
 {
-    if (p) cudaFree((void *)p);
+    if (p) cudaFreeAsync((void *)p, s);
     p = nullptr;
 }
 
@@ -94,13 +118,68 @@ inline void nl_free(T *&p)
 // out[i] = sum_{k<i} in[i]; out[n] = total.  in and out may alias.
 nl_status nl_scan_i64(nl_ctx *ctx, const int64_t *in, int64_t *out, int64_t n);
 
+// argument checks of one problem (api.cu)
+nl_status nl_validate(nl_ctx *ctx, const nl_mesh *m, const nl_config *c);
+
 // ---- phases ----
+// The preparation and the symbolic phase are split into stages that only enqueue
+// work on ctx->stream and stream-ordered copies into a host slot; the caller
+// synchronises the stream between two stages (once for a whole batch).
+struct nl_prep;   // temporaries between the preparation stages (mesh.cu)
+nl_prep *nl_prep_new();
+void nl_prep_delete(nl_prep *T, cudaStream_t s);
+// A: inputs, per-triangle data, mesh statistics -> slot
+nl_status nl_prepare_a(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_plan *P, nl_prep *T,
+                       nl_host_slot *h);
+// B (slot A read): validation, cell list, candidate counts -> slot
+nl_status nl_prepare_b(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_host_slot *h);
+// C (slot B read): candidate lists, interior/boundary split; overflow -> slot (checked by nl_prepare_check)
+nl_status nl_prepare_c(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_host_slot *h);
+nl_status nl_prepare_check(nl_ctx *ctx, const nl_host_slot *h);
+// all stages with a synchronisation between them
 nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_plan *P);
-nl_status nl_build_candidates(nl_ctx *ctx, nl_plan *P);
-nl_status nl_run_numeric(nl_ctx *ctx, nl_plan *P, bool with_hash);
+
+struct nl_pat;    // temporaries between the symbolic stages (pattern.cu)
+nl_pat *nl_pat_new();
+void nl_pat_delete(nl_pat *T, cudaStream_t s);
+// A (after the numeric phase): symmetric flags, row counts, row pointers; nnz and statistics -> slot
+nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_slot *h);
+// B (slot A read): column indices, slot maps, value buffers
+nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl_host_slot *h);
 nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out);
+
+nl_status nl_run_numeric(nl_ctx *ctx, nl_plan *P, bool with_hash);
+nl_status nl_alloc_numeric(nl_ctx *ctx, nl_plan *P);
 nl_status nl_run_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out);
-void nl_plan_free(nl_plan *P);
+
+// ---- batched scatter (pattern.cu): the scatter of every problem of a batch ----
+struct ScatterArgs {   // one problem
+    int K, J;
+    int64_t E;
+    const int32_t *tri;
+    const int64_t *ptr;
+    const int32_t *idx;
+    const uint8_t *flag;
+    const void *blk;
+    const double *maa;
+    const int64_t *lslot, *row_ptr;
+    const int32_t *col;
+    double *W;
+    const int64_t *tslot;
+    double *val;
+    int *err;
+};
+// W = 0 over all problems (zoff: prefix sums of nnz, device, n + 1 entries; total = zoff[n])
+nl_status nl_launch_zero_batch(nl_ctx *ctx, const ScatterArgs *dS, const int64_t *dzoff, int n, int64_t total);
+// scatter of the problems in dS (all of one value type; koff: prefix sums of K; max_row: longest row)
+nl_status nl_launch_scatter_batch(nl_ctx *ctx, bool f64, const ScatterArgs *dS, const int64_t *dkoff, int n,
+                                  int64_t totalK, int64_t max_row, bool set_attr);
+// val = W + W^T over all problems
+nl_status nl_launch_symmetrize_batch(nl_ctx *ctx, const ScatterArgs *dS, const int64_t *dzoff, int n,
+                                     int64_t total);
+// the autotuner's cache of batch schedules (batch.cu)
+void nl_tune_cache_free(struct nl_tune_cache *c);
+void nl_plan_free(nl_plan *P, cudaStream_t s);   // stream-ordered release of the plan's buffers
 double nl_polygon_inradius(const double *offsets, int n);
 
 // host pointer / device pointer staging

@@ -15,6 +15,9 @@
 // index) and per-triangle candidate lists sorted by triangle index.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <string.h>
+
+#include <new>
 
 #include "internal.cuh"
 
@@ -363,21 +366,65 @@ double nl_polygon_inradius(const double *o, int N)
     return rin;
 }
 
-nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_plan *P)
+struct nl_prep {
+    void *dvx = nullptr, *dvy = nullptr, *dtri = nullptr;
+    bool own_vx = false, own_vy = false, own_tri = false;
+    double *diam = nullptr;
+    int *bad = nullptr;
+    MeshStats *st = nullptr;
+    float4 *cf = nullptr;
+    Grid g{};
+    int ncell = 0;
+    int32_t *cell = nullptr, *bucket = nullptr;
+    int64_t *ccnt = nullptr, *cstart = nullptr, *cursor = nullptr, *cnt = nullptr;
+    int *ovf = nullptr;
+};
+
+nl_prep *nl_prep_new() { return new (std::nothrow) nl_prep(); }
+
+namespace {
+template <class T>
+void free_async(T *&p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync((void *)p, s);
+    p = nullptr;
+}
+
+void prep_release(nl_prep *T, cudaStream_t s)
+{
+    void *vx = T->own_vx ? T->dvx : nullptr, *vy = T->own_vy ? T->dvy : nullptr;
+    void *tr = T->own_tri ? T->dtri : nullptr;
+    free_async(vx, s); free_async(vy, s); free_async(tr, s);
+    T->dvx = T->dvy = T->dtri = nullptr;
+    T->own_vx = T->own_vy = T->own_tri = false;
+    free_async(T->diam, s); free_async(T->bad, s); free_async(T->st, s); free_async(T->cf, s);
+    free_async(T->cell, s); free_async(T->bucket, s); free_async(T->ccnt, s); free_async(T->cstart, s);
+    free_async(T->cursor, s); free_async(T->cnt, s); free_async(T->ovf, s);
+}
+}  // namespace
+
+void nl_prep_delete(nl_prep *T, cudaStream_t s)
+{
+    if (!T) return;
+    prep_release(T, s);
+    delete T;
+}
+
+nl_status nl_prepare_a(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_plan *P, nl_prep *T,
+                       nl_host_slot *h)
 {
     const int K = mesh->nt, J = mesh->nv;
+    P->stream = ctx->stream;
     P->K = K;
     P->J = J;
     P->cfg = *cfg;
     P->d2 = cfg->delta * cfg->delta;
     nl_status s;
-    bool own_vx = false, own_vy = false, own_tri = false;
-    void *dvx = nullptr, *dvy = nullptr, *dtri = nullptr;
-    if ((s = nl_stage(ctx, mesh->vx, sizeof(double) * J, &dvx, &own_vx)) != NL_OK) return s;
-    if ((s = nl_stage(ctx, mesh->vy, sizeof(double) * J, &dvy, &own_vy)) != NL_OK) return s;
-    if ((s = nl_stage(ctx, mesh->tri, sizeof(int32_t) * 3 * K, &dtri, &own_tri)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, mesh->vx, sizeof(double) * J, &T->dvx, &T->own_vx)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, mesh->vy, sizeof(double) * J, &T->dvy, &T->own_vy)) != NL_OK) return s;
+    if ((s = nl_stage(ctx, mesh->tri, sizeof(int32_t) * 3 * K, &T->dtri, &T->own_tri)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->tri, 3 * (size_t)K)) != NL_OK) return s;
-    NL_CK(cudaMemcpyAsync(P->tri, dtri, sizeof(int32_t) * 3 * K, cudaMemcpyDeviceToDevice, ctx->stream));
+    NL_CK(cudaMemcpyAsync(P->tri, T->dtri, sizeof(int32_t) * 3 * K, cudaMemcpyDeviceToDevice, ctx->stream));
     if ((s = nl_alloc(ctx, &P->tx, 3 * (size_t)K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->ty, 3 * (size_t)K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->bx, K)) != NL_OK) return s;
@@ -385,48 +432,54 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
     if ((s = nl_alloc(ctx, &P->rad, K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->area, K)) != NL_OK) return s;
     if (cfg->ball == NL_BALL_NGON) {
-        void *doff = nullptr;
-        bool own_off = false;
-        if ((s = nl_alloc(ctx, &P->ngon, 2 * (size_t)cfg->ngon_n)) != NL_OK) return s;
-        if ((s = nl_stage(ctx, cfg->ngon_offsets, sizeof(double) * 2 * cfg->ngon_n, &doff, &own_off)) != NL_OK)
-            return s;
-        NL_CK(cudaMemcpyAsync(P->ngon, doff, sizeof(double) * 2 * cfg->ngon_n, cudaMemcpyDeviceToDevice,
-                              ctx->stream));
+        const size_t nb = sizeof(double) * 2 * cfg->ngon_n;
         P->ngon_host.resize(2 * (size_t)cfg->ngon_n);
-        NL_CK(cudaMemcpyAsync(P->ngon_host.data(), doff, sizeof(double) * 2 * cfg->ngon_n, cudaMemcpyDeviceToHost,
-                              ctx->stream));
-        NL_CK(cudaStreamSynchronize(ctx->stream));
+        if ((s = nl_alloc(ctx, &P->ngon, 2 * (size_t)cfg->ngon_n)) != NL_OK) return s;
+        if (nl_is_device_ptr(cfg->ngon_offsets)) {
+            NL_CK(cudaMemcpyAsync(P->ngon, cfg->ngon_offsets, nb, cudaMemcpyDeviceToDevice, ctx->stream));
+            NL_CK(cudaMemcpyAsync(P->ngon_host.data(), cfg->ngon_offsets, nb, cudaMemcpyDeviceToHost, ctx->stream));
+            NL_CK(cudaStreamSynchronize(ctx->stream));
+        } else {
+            memcpy(P->ngon_host.data(), cfg->ngon_offsets, nb);
+            NL_CK(cudaMemcpyAsync(P->ngon, P->ngon_host.data(), nb, cudaMemcpyHostToDevice, ctx->stream));
+        }
         P->rin = nl_polygon_inradius(P->ngon_host.data(), cfg->ngon_n);
-        if (own_off) NL_CK(cudaFreeAsync(doff, ctx->stream));
     }
-    double *diam = nullptr;
-    int *bad = nullptr;
-    MeshStats *st = nullptr;
-    NL_CK(cudaMallocAsync((void **)&diam, sizeof(double) * K, ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&bad, sizeof(int), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&st, sizeof(MeshStats), ctx->stream));
-    NL_CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
-    float4 *cf = nullptr;
-    NL_CK(cudaMallocAsync((void **)&cf, sizeof(float4) * K, ctx->stream));
-    k_prepare<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, J, (const int32_t *)dtri, (const double *)dvx,
-                                                        (const double *)dvy, P->tx, P->ty, P->bx, P->by,
-                                                        P->rad, P->area, diam, cf, bad); ++ctx->launches;
+    NL_CK(cudaMallocAsync((void **)&T->diam, sizeof(double) * K, ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&T->bad, sizeof(int), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&T->st, sizeof(MeshStats), ctx->stream));
+    NL_CK(cudaMemsetAsync(T->bad, 0, sizeof(int), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&T->cf, sizeof(float4) * K, ctx->stream));
+    k_prepare<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, J, (const int32_t *)T->dtri, (const double *)T->dvx,
+                                                        (const double *)T->dvy, P->tx, P->ty, P->bx, P->by,
+                                                        P->rad, P->area, T->diam, T->cf, T->bad); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    k_mesh_stats<<<1, 1024, 0, ctx->stream>>>(K, P->bx, P->by, P->rad, diam, st); ++ctx->launches;
+    k_mesh_stats<<<1, 1024, 0, ctx->stream>>>(K, P->bx, P->by, P->rad, T->diam, T->st); ++ctx->launches;
     NL_CK(cudaGetLastError());
+    static_assert(sizeof(MeshStats) == sizeof(h->mesh), "mesh statistics slot");
+    NL_CK(cudaMemcpyAsync(h->mesh, T->st, sizeof(MeshStats), cudaMemcpyDeviceToHost, ctx->stream));
+    NL_CK(cudaMemcpyAsync(&h->bad, T->bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    return NL_OK;
+}
+
+nl_status nl_prepare_b(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_host_slot *h)
+{
+    const int K = P->K;
+    const nl_config *cfg = &P->cfg;
+    cudaStream_t st = ctx->stream;
+    // the staged inputs and the statistics buffers are no longer needed
+    {
+        void *vx = T->own_vx ? T->dvx : nullptr, *vy = T->own_vy ? T->dvy : nullptr;
+        void *tr = T->own_tri ? T->dtri : nullptr;
+        free_async(vx, st); free_async(vy, st); free_async(tr, st);
+        T->dvx = T->dvy = T->dtri = nullptr;
+        T->own_vx = T->own_vy = T->own_tri = false;
+        free_async(T->diam, st); free_async(T->bad, st); free_async(T->st, st);
+    }
     MeshStats hst;
-    int hbad = 0;
-    NL_CK(cudaMemcpyAsync(&hst, st, sizeof hst, cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaMemcpyAsync(&hbad, bad, sizeof hbad, cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaFreeAsync(diam, ctx->stream));
-    NL_CK(cudaFreeAsync(bad, ctx->stream));
-    NL_CK(cudaFreeAsync(st, ctx->stream));
-    if (own_vx) NL_CK(cudaFreeAsync(dvx, ctx->stream));
-    if (own_vy) NL_CK(cudaFreeAsync(dvy, ctx->stream));
-    if (own_tri) NL_CK(cudaFreeAsync(dtri, ctx->stream));
-    NL_CK(cudaStreamSynchronize(ctx->stream));
-    if (hbad)
-        return nl_fail(ctx, NL_EGEOM, std::to_string(hbad) +
+    memcpy(&hst, h->mesh, sizeof hst);
+    if (h->bad)
+        return nl_fail(ctx, NL_EGEOM, std::to_string(h->bad) +
                                           " triangles are degenerate, clockwise or index a missing vertex");
     if (!(cfg->delta > hst.hmax))
         return nl_fail(ctx, NL_EGEOM, "delta must exceed the largest triangle diameter (" +
@@ -437,53 +490,58 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
     double R = (cfg->delta + 2.0 * hst.rmax) * (1.0 + 2e-5);
     double Lx = hst.xmax - hst.xmin, Ly = hst.ymax - hst.ymin, L = fmax(fmax(Lx, Ly), 1e-300);
     double cs = fmin(R, L / sqrt(fmax(K / 32.0, 1.0)));
-    Grid g;
+    Grid &g = T->g;
     g.cs = cs;
     g.m = (int)ceil(R / cs);
     g.x0 = hst.xmin;
     g.y0 = hst.ymin;
     g.nx = (int)floor(Lx / cs) + 1;
     g.ny = (int)floor(Ly / cs) + 1;
-    // stash the grid in the candidate stage (kept on the host side of the plan)
-    int ncell = g.nx * g.ny;
-    int32_t *cell = nullptr, *bucket = nullptr;
-    int64_t *ccnt = nullptr, *cstart = nullptr, *cursor = nullptr;
-    int *ovf = nullptr;
-    NL_CK(cudaMallocAsync((void **)&cell, sizeof(int32_t) * K, ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&bucket, sizeof(int32_t) * K, ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ccnt, sizeof(int64_t) * (ncell + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&cstart, sizeof(int64_t) * (ncell + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&cursor, sizeof(int64_t) * (ncell + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ovf, sizeof(int), ctx->stream));
-    NL_CK(cudaMemsetAsync(ccnt, 0, sizeof(int64_t) * (ncell + 1), ctx->stream));
-    NL_CK(cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (ncell + 1), ctx->stream));
-    NL_CK(cudaMemsetAsync(ovf, 0, sizeof(int), ctx->stream));
-    k_cell_count<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, g, P->bx, P->by, cell, ccnt); ++ctx->launches;
+    const int ncell = g.nx * g.ny;
+    T->ncell = ncell;
+    NL_CK(cudaMallocAsync((void **)&T->cell, sizeof(int32_t) * K, st));
+    NL_CK(cudaMallocAsync((void **)&T->bucket, sizeof(int32_t) * K, st));
+    NL_CK(cudaMallocAsync((void **)&T->ccnt, sizeof(int64_t) * (ncell + 1), st));
+    NL_CK(cudaMallocAsync((void **)&T->cstart, sizeof(int64_t) * (ncell + 1), st));
+    NL_CK(cudaMallocAsync((void **)&T->cursor, sizeof(int64_t) * (ncell + 1), st));
+    NL_CK(cudaMallocAsync((void **)&T->ovf, sizeof(int), st));
+    NL_CK(cudaMemsetAsync(T->ccnt, 0, sizeof(int64_t) * (ncell + 1), st));
+    NL_CK(cudaMemsetAsync(T->cursor, 0, sizeof(int64_t) * (ncell + 1), st));
+    NL_CK(cudaMemsetAsync(T->ovf, 0, sizeof(int), st));
+    k_cell_count<<<(K + 255) / 256, 256, 0, st>>>(K, g, P->bx, P->by, T->cell, T->ccnt); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    if ((s = nl_scan_i64(ctx, ccnt, cstart, ncell)) != NL_OK) return s;
-    k_cell_fill<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, cell, cstart, cursor, bucket); ++ctx->launches;
+    nl_status s;
+    if ((s = nl_scan_i64(ctx, T->ccnt, T->cstart, ncell)) != NL_OK) return s;
+    k_cell_fill<<<(K + 255) / 256, 256, 0, st>>>(K, T->cell, T->cstart, T->cursor, T->bucket); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    k_cell_sort<<<ncell, 256, sizeof(int32_t) * NL_MAXCAND, ctx->stream>>>(cstart, bucket, ovf); ++ctx->launches;
+    k_cell_sort<<<ncell, 256, sizeof(int32_t) * NL_MAXCAND, st>>>(T->cstart, T->bucket, T->ovf); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    // candidate lists
+    // candidate counts and their prefix sum
     if ((s = nl_alloc(ctx, &P->nbr_ptr, (size_t)K + 1)) != NL_OK) return s;
-    int64_t *cnt = nullptr;
-    NL_CK(cudaMallocAsync((void **)&cnt, sizeof(int64_t) * K, ctx->stream));
-    unsigned wblocks = (unsigned)(((int64_t)K * 32 + 255) / 256);
-    k_candidates<<<wblocks, 256, 0, ctx->stream>>>(K, g, (float)cfg->delta, cf, cstart, bucket, cnt, nullptr,
-                                                   nullptr, 0); ++ctx->launches;
+    NL_CK(cudaMallocAsync((void **)&T->cnt, sizeof(int64_t) * K, st));
+    const unsigned wblocks = (unsigned)(((int64_t)K * 32 + 255) / 256);
+    k_candidates<<<wblocks, 256, 0, st>>>(K, g, (float)cfg->delta, T->cf, T->cstart, T->bucket, T->cnt, nullptr,
+                                          nullptr, 0); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    if ((s = nl_scan_i64(ctx, cnt, P->nbr_ptr, K)) != NL_OK) return s;
-    int64_t E = 0;
-    int hovf = 0;
-    NL_CK(cudaMemcpyAsync(&E, P->nbr_ptr + K, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaStreamSynchronize(ctx->stream));
-    if (hovf) return nl_fail(ctx, NL_EUNSUPPORTED, "cell-list bucket exceeds the shared-memory sort limit");
+    if ((s = nl_scan_i64(ctx, T->cnt, P->nbr_ptr, K)) != NL_OK) return s;
+    NL_CK(cudaMemcpyAsync(&h->E, P->nbr_ptr + K, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    NL_CK(cudaMemcpyAsync(&h->ovf, T->ovf, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return NL_OK;
+}
+
+nl_status nl_prepare_c(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_host_slot *h)
+{
+    const int K = P->K;
+    const nl_config *cfg = &P->cfg;
+    cudaStream_t st = ctx->stream;
+    if (h->ovf) return nl_fail(ctx, NL_EUNSUPPORTED, "cell-list bucket exceeds the shared-memory sort limit");
+    const int64_t E = h->E;
     P->E = E;
+    nl_status s;
     if ((s = nl_alloc(ctx, &P->nbr_idx, (size_t)E)) != NL_OK) return s;
-    k_candidates<<<wblocks, 256, 0, ctx->stream>>>(K, g, (float)cfg->delta, cf, cstart, bucket, nullptr,
-                                                   P->nbr_ptr, P->nbr_idx, 1); ++ctx->launches;
+    const unsigned wblocks = (unsigned)(((int64_t)K * 32 + 255) / 256);
+    k_candidates<<<wblocks, 256, 0, st>>>(K, T->g, (float)cfg->delta, T->cf, T->cstart, T->bucket, nullptr,
+                                          P->nbr_ptr, P->nbr_idx, 1); ++ctx->launches;
     NL_CK(cudaGetLastError());
     // interior fast path: the region is whole for every outer point (certified with margin tau)
     {
@@ -494,22 +552,41 @@ nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
         else if (cfg->ball == NL_BALL_NGON) lim = P->rin - 2.0 * tau;
         if (cfg->kernel == NL_KERNEL_INV_DIST) mode = cfg->ball == NL_BALL_BARYCENTER ? 2 : 3;
         if ((s = nl_alloc(ctx, &P->nbr_split, (size_t)K)) != NL_OK) return s;
-        k_sort_lists<<<K, 256, 0, ctx->stream>>>(P->nbr_ptr, P->nbr_idx, P->nbr_split, cf, mode, (float)lim,
-                                                 (float)(2.0 * tau), ovf); ++ctx->launches;
+        k_sort_lists<<<K, 256, 0, st>>>(P->nbr_ptr, P->nbr_idx, P->nbr_split, T->cf, mode, (float)lim,
+                                        (float)(2.0 * tau), T->ovf); ++ctx->launches;
     }
     NL_CK(cudaGetLastError());
-    NL_CK(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaFreeAsync(cnt, ctx->stream));
-    NL_CK(cudaFreeAsync(cf, ctx->stream));
-    NL_CK(cudaFreeAsync(cell, ctx->stream));
-    NL_CK(cudaFreeAsync(bucket, ctx->stream));
-    NL_CK(cudaFreeAsync(ccnt, ctx->stream));
-    NL_CK(cudaFreeAsync(cstart, ctx->stream));
-    NL_CK(cudaFreeAsync(cursor, ctx->stream));
-    NL_CK(cudaFreeAsync(ovf, ctx->stream));
-    NL_CK(cudaStreamSynchronize(ctx->stream));
-    if (hovf) return nl_fail(ctx, NL_EUNSUPPORTED, "a triangle has more than 4096 candidate neighbours");
+    NL_CK(cudaMemcpyAsync(&h->ovf, T->ovf, sizeof(int), cudaMemcpyDeviceToHost, st));
+    prep_release(T, st);
     return NL_OK;
 }
 
-nl_status nl_build_candidates(nl_ctx *, nl_plan *) { return NL_OK; }
+nl_status nl_prepare_check(nl_ctx *ctx, const nl_host_slot *h)
+{
+    if (h->ovf) return nl_fail(ctx, NL_EUNSUPPORTED, "a triangle has more than 4096 candidate neighbours");
+    return NL_OK;
+}
+
+nl_status nl_prepare_mesh(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_plan *P)
+{
+    nl_host_slot *h = nullptr;
+    nl_status s = nl_host_slots(ctx, 1, &h);
+    if (s != NL_OK) return s;
+    nl_prep *T = nl_prep_new();
+    if (!T) return nl_fail(ctx, NL_ENOMEM, "host allocation failed");
+    if ((s = nl_prepare_a(ctx, mesh, cfg, P, T, h)) == NL_OK) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) s = nl_cuda_fail(ctx, e, "cudaStreamSynchronize");
+    }
+    if (s == NL_OK && (s = nl_prepare_b(ctx, P, T, h)) == NL_OK) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) s = nl_cuda_fail(ctx, e, "cudaStreamSynchronize");
+    }
+    if (s == NL_OK && (s = nl_prepare_c(ctx, P, T, h)) == NL_OK) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) s = nl_cuda_fail(ctx, e, "cudaStreamSynchronize");
+    }
+    if (s == NL_OK) s = nl_prepare_check(ctx, h);
+    nl_prep_delete(T, ctx->stream);
+    return s;
+}

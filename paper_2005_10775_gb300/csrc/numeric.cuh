@@ -38,13 +38,14 @@ struct NumArgs {
     const int64_t *nbr_ptr, *nbr_split;
     const int32_t *nbr_idx;
     RuleTab outer, inner;
-    float fin_l[NL_MAXQ + 8][3], fin_w[NL_MAXQ + 8];   // inner rule in FP32
+    float4 fin[NL_MAXQ + 8];          // inner rule in FP32: barycentrics (x, y, z) and weight (w)
     double gl_x[8], gl_w[8];          // Gauss-Legendre on [0,1] with duffy_n points
     double gl2_x[2], gl2_w[2];
     int duffy_n;
     int switch47;                     // outer rule: 0..nsplit-1 if |bary_a - bary_b|^2 < thr2 else nsplit..n-1
     double thr2;                      // (delta - h_max)^2, or -1 when delta <= h_max
     int kernel;                       // nl_kernel
+    int ball;                         // nl_ball (run-time dispatch of the batched kernel)
     double kc;
     nlg::GeoParams geo;
     uint8_t *flag;
@@ -190,18 +191,16 @@ __device__ __forceinline__ void near_polygon(const NumArgs &A, const BaryMap &bm
 }
 
 // inner sums of the region R(x, T_b)
+// one inner rule point: barycentrics and weight (FP32 path: one 128-bit load)
 template <typename T>
-__device__ __forceinline__ T rule_l(const NumArgs &A, int r, int i)
+__device__ __forceinline__ void rule_pt(const NumArgs &A, int r, T &p0, T &p1, T &p2, T &w)
 {
-    if (sizeof(T) == sizeof(float)) return (T)A.fin_l[r][i];
-    return (T)A.inner.l[r][i];
-}
-
-template <typename T>
-__device__ __forceinline__ T rule_w(const NumArgs &A, int r)
-{
-    if (sizeof(T) == sizeof(float)) return (T)A.fin_w[r];
-    return (T)A.inner.w[r];
+    if (sizeof(T) == sizeof(float)) {
+        const float4 f = A.fin[r];
+        p0 = (T)f.x; p1 = (T)f.y; p2 = (T)f.z; w = (T)f.w;
+    } else {
+        p0 = (T)A.inner.l[r][0]; p1 = (T)A.inner.l[r][1]; p2 = (T)A.inner.l[r][2]; w = (T)A.inner.w[r];
+    }
 }
 
 // inner sums over the whole triangle T_b: phi_b at the rule points are the rule's barycentrics
@@ -226,8 +225,9 @@ __device__ __forceinline__ void whole_sums(const NumArgs &A, const D2 V[3], T ar
             for (int i = 0; i < 3; i++) { lx[i] = (T)(V[i].x - x.x); ly[i] = (T)(V[i].y - x.y); }
     }
     for (int r = 0; r < n; r++) {
-        T p0 = rule_l<T>(A, r, 0), p1 = rule_l<T>(A, r, 1), p2 = rule_l<T>(A, r, 2);
-        T w = rule_w<T>(A, r) * ar;
+        T p0, p1, p2, w;
+        rule_pt<T>(A, r, p0, p1, p2, w);
+        w *= ar;
         if (inv) {
             T dx = p0 * lx[0] + p1 * lx[1] + p2 * lx[2];
             T dy = p0 * ly[0] + p1 * ly[1] + p2 * ly[2];
@@ -292,11 +292,12 @@ __device__ __forceinline__ void inner_sums(const NumArgs &A, const nlg::Region &
                 T lnx = (T)(s2p.x - x.x), lny = (T)(s2p.y - x.y);
                 const T art = (T)ar;
                 for (int r = 0; r < ri.n; r++) {
-                    T m0 = rule_l<T>(A, r, 0), m1 = rule_l<T>(A, r, 1), m2 = rule_l<T>(A, r, 2);
+                    T m0, m1, m2, w;
+                    rule_pt<T>(A, r, m0, m1, m2, w);
                     T p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
                     T p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
                     T p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
-                    T w = rule_w<T>(A, r) * art;
+                    w *= art;
                     if (inv) {
                         T dx = m0 * l0x + m1 * lkx + m2 * lnx;
                         T dy = m0 * l0y + m1 * lky + m2 * lny;
@@ -352,11 +353,12 @@ __device__ __forceinline__ void poly_sums_f32(const NumArgs &A, const nlg::F2 *P
         float fn[3];
         phi(s2, fn);
         for (int r = 0; r < nr; r++) {
-            const float m0 = A.fin_l[r][0], m1 = A.fin_l[r][1], m2 = A.fin_l[r][2];
+            const float4 f = A.fin[r];
+            const float m0 = f.x, m1 = f.y, m2 = f.z;
             const float p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
             const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
             const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
-            sums_add<float>(S, A.fin_w[r] * ar, p0, p1, p2);
+            sums_add<float>(S, f.w * ar, p0, p1, p2);
         }
         nqp += nr;
         fk[0] = fn[0]; fk[1] = fn[1]; fk[2] = fn[2];
@@ -390,11 +392,12 @@ __device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBu
         float fn[3];
         phi(xn, yn, fn);
         for (int r = 0; r < nr; r++) {
-            const float m0 = A.fin_l[r][0], m1 = A.fin_l[r][1], m2 = A.fin_l[r][2];
+            const float4 f = A.fin[r];
+            const float m0 = f.x, m1 = f.y, m2 = f.z;
             const float p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
             const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
             const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
-            float w = A.fin_w[r] * ar;
+            float w = f.w * ar;
             if (A.kernel == NL_KERNEL_INV_DIST) {   // psi = c / |y - x|, coordinates relative to x
                 const float yx = m0 * x0 + m1 * xk + m2 * xn, yy = m0 * y0 + m1 * yk + m2 * yn;
                 w *= rsqrtf(yx * yx + yy * yy);
@@ -583,21 +586,19 @@ __device__ __forceinline__ void warp_reduce(LaneAcc &acc)
 // and initialises the per-triangle M_aa and statistics.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_interior(const NumArgs A)
+__device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const OuterPt *sq, int lane, LaneAcc &acc)
 {
-    __shared__ OuterPt sq_all[kWarpsPerBlock][NL_MAXQ + 8];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int a = blockIdx.x * kWarpsPerBlock + wib;
-    if (a >= A.K) return;
     const int K = A.K;
-    OuterPt *sq = sq_all[wib];
-    stage_outer(A, a, sq, lane);
     const D2 ba = {A.bx[a], A.by[a]};
-    LaneAcc acc;
-    acc_zero(acc);
     const int64_t e0 = A.nbr_ptr[a], es = A.nbr_split[a];
     for (int64_t e = e0 + lane; e < es; e += 32) {
         const int b = A.nbr_idx[e];
+#ifdef NL_CHECKS
+        if (b < 0 || b >= K) {   // debug build: bad candidate recorded (bit 16) and skipped
+            atomicOr(A.err, 16);
+            continue;
+        }
+#endif
         D2 Vb[3];
         for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
         const D2 bb = {A.bx[b], A.by[b]};
@@ -626,13 +627,43 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_interior(const NumArgs 
         }
         write_pair<T>(A, e, q1 > q0, v, acc);
     }
+}
+
+// warp reduction of the outer triangle's accumulators and their store (add: onto the
+// values an earlier kernel stored, in stream order)
+__device__ __forceinline__ void finish_outer(const NumArgs &A, int a, LaneAcc &acc, int lane, bool add)
+{
     warp_reduce(acc);
     if (lane == 0) {
-        for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] = acc.maa[i];
-        A.qp_a[a] = acc.qp;
-        A.cnt_a[a] = acc.cnt;
-        if (A.stats) A.hash_a[a] = acc.hsum;
+        const int K = A.K;
+        if (add) {
+            for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] += acc.maa[i];
+            A.qp_a[a] += acc.qp;
+            A.cnt_a[a] += acc.cnt;
+            if (A.stats) A.hash_a[a] += acc.hsum;
+        } else {
+            for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] = acc.maa[i];
+            A.qp_a[a] = acc.qp;
+            A.cnt_a[a] = acc.cnt;
+            if (A.stats) A.hash_a[a] = acc.hsum;
+        }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_interior(const NumArgs A)
+{
+    __shared__ OuterPt sq_all[kWarpsPerBlock][NL_MAXQ + 8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int a = blockIdx.x * kWarpsPerBlock + wib;
+    if (a >= A.K) return;
+    OuterPt *sq = sq_all[wib];
+    stage_outer(A, a, sq, lane);
+    __syncwarp();
+    LaneAcc acc;
+    acc_zero(acc);
+    interior_outer<T>(A, a, sq, lane, acc);
+    finish_outer(A, a, acc, lane, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -767,20 +798,14 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
     return true;
 }
 
-// INV: the kernel is psi = c/|x - y| (near-field split), else the constant kernel
+// The boundary candidates of outer triangle a (outer points staged in sh.sq).
+// INV: the kernel is psi = c/|x - y| (near-field split), else the constant kernel.
 template <int BALL, typename T, bool INV>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs A)
+__device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, BoundaryShared<T> &sh, int lane,
+                                               LaneAcc &acc)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    BoundaryShared<T> &sh = ((BoundaryShared<T> *)smem_raw)[threadIdx.x >> 5];
-    const int lane = threadIdx.x & 31;
-    const int a = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (a >= A.K) return;
     const int K = A.K;
-    stage_outer(A, a, sh.sq, lane);
     const D2 ba = {A.bx[a], A.by[a]};
-    LaneAcc acc;
-    acc_zero(acc);
     const int64_t es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
     const int nq_all = A.outer.n;
     const bool inv = INV;
@@ -790,7 +815,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
         int q0 = 0, q1 = 0;
         CandData c;
         if (valid) {
-            const int b = A.nbr_idx[e];
+            int b = A.nbr_idx[e];
+#ifdef NL_CHECKS
+            if (b < 0 || b >= K) {   // debug build: bad candidate recorded (bit 16), replaced by a
+                atomicOr(A.err, 16);
+                b = a;
+            }
+#endif
             c.b = b;
             for (int i = 0; i < 3; i++) { c.vx[i] = A.tx[i * K + b]; c.vy[i] = A.ty[i * K + b]; }
             c.bbx = A.bx[b];
@@ -910,14 +941,128 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
         }
         __syncwarp();
     }
-    warp_reduce(acc);
-    if (lane == 0) {
-        // k_interior has written this triangle's values; add in stream order (deterministic)
-        for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] += acc.maa[i];
-        A.qp_a[a] += acc.qp;
-        A.cnt_a[a] += acc.cnt;
-        if (A.stats) A.hash_a[a] += acc.hsum;
+}
+
+template <int BALL, typename T, bool INV>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BoundaryShared<T> &sh = ((BoundaryShared<T> *)smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int a = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (a >= A.K) return;
+    stage_outer(A, a, sh.sq, lane);
+    __syncwarp();
+    LaneAcc acc;
+    acc_zero(acc);
+    boundary_outer<BALL, T, INV>(A, a, sh, lane, acc);
+    // k_interior has written this triangle's values; add in stream order (deterministic)
+    finish_outer(A, a, acc, lane, true);
+}
+
+// ---------------------------------------------------------------------------
+// Batched numeric phase: many independent problems in a few persistent launches: the
+// interior candidates of every problem (k_interior_batch), then the boundary
+// candidates of the problems of each ball mode (k_boundary_batch<BALL>), with the
+// register and shared-memory budgets of k_interior and k_boundary.  A work item is a
+// run of consecutive outer triangles of one problem; each warp takes the next item
+// from the launch's global counter.  The outputs of every problem are those of
+// k_interior + k_boundary: each triangle's values are produced by one warp in the same
+// order, whatever the schedule.
+// ---------------------------------------------------------------------------
+struct BatchItem {
+    int p;        // problem
+    int a0, a1;   // outer triangles a0 .. a1-1
+};
+
+// next work item of the calling warp (lane 0 takes it from the counter)
+__device__ __forceinline__ int next_item(int *counter, int lane)
+{
+    int it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1);
+    return __shfl_sync(0xffffffffu, it, 0);
+}
+
+// interior candidates of every problem (stores M_aa and the statistics, as k_interior)
+template <typename T>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_interior_batch(const NumArgs *__restrict__ As, const BatchItem *__restrict__ items, int n_items, int *counter)
+{
+    __shared__ OuterPt sq_all[kWarpsPerBlock][NL_MAXQ + 8];
+    const int lane = threadIdx.x & 31;
+    OuterPt *sq = sq_all[threadIdx.x >> 5];
+    for (int it = next_item(counter, lane); it < n_items; it = next_item(counter, lane)) {
+        const BatchItem w = items[it];
+        const NumArgs &A = As[w.p];
+#ifdef NL_CHECKS
+        if (w.a0 < 0 || w.a1 > A.K || A.nbr_ptr[w.a0] < 0 || A.nbr_ptr[w.a1] > A.E) {
+            atomicOr(A.err, 32);   // debug build: bad work item recorded (bit 32) and skipped
+            continue;
+        }
+#endif
+        for (int a = w.a0; a < w.a1; a++) {
+            stage_outer(A, a, sq, lane);
+            __syncwarp();
+            LaneAcc acc;
+            acc_zero(acc);
+            interior_outer<T>(A, a, sq, lane, acc);
+            finish_outer(A, a, acc, lane, false);
+            __syncwarp();
+        }
+    }
+}
+
+// boundary candidates of the problems with ball mode BALL (adds onto k_interior_batch's
+// values, as k_boundary adds onto k_interior's)
+template <int BALL, typename T, bool INV>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_boundary_batch(const NumArgs *__restrict__ As, const BatchItem *__restrict__ items, int n_items, int *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BoundaryShared<T> &sh = ((BoundaryShared<T> *)smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    for (int it = next_item(counter, lane); it < n_items; it = next_item(counter, lane)) {
+        const BatchItem w = items[it];
+        const NumArgs &A = As[w.p];
+#ifdef NL_CHECKS
+        if (w.a0 < 0 || w.a1 > A.K || A.nbr_ptr[w.a0] < 0 || A.nbr_ptr[w.a1] > A.E) {
+            atomicOr(A.err, 32);   // debug build: bad work item recorded (bit 32) and skipped
+            continue;
+        }
+#endif
+        for (int a = w.a0; a < w.a1; a++) {
+            stage_outer(A, a, sh.sq, lane);
+            __syncwarp();
+            LaneAcc acc;
+            acc_zero(acc);
+            boundary_outer<BALL, T, INV>(A, a, sh, lane, acc);
+            finish_outer(A, a, acc, lane, true);
+            __syncwarp();
+        }
     }
 }
 
 }  // namespace nlq
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+// kernel arguments of one assembled problem (api.cu)
+nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats);
+
+// persistent batched numeric launches over problems whose arguments are in dA (device
+// array; items index it), of one value type (numeric_batch_f32/f64.cu); *counter must
+// be zero when the launch starts
+nl_status nl_launch_interior_batch_f32(nl_ctx *ctx, const nlq::NumArgs *dA, const nlq::BatchItem *items,
+                                       int n_items, int *counter, int blocks);
+nl_status nl_launch_interior_batch_f64(nl_ctx *ctx, const nlq::NumArgs *dA, const nlq::BatchItem *items,
+                                       int n_items, int *counter, int blocks);
+nl_status nl_launch_boundary_batch_f32(nl_ctx *ctx, int ball, bool inv, const nlq::NumArgs *dA,
+                                       const nlq::BatchItem *items, int n_items, int *counter, int blocks,
+                                       bool set_attr);
+nl_status nl_launch_boundary_batch_f64(nl_ctx *ctx, int ball, bool inv, const nlq::NumArgs *dA,
+                                       const nlq::BatchItem *items, int n_items, int *counter, int blocks,
+                                       bool set_attr);
+// resident blocks per SM of the interior launch (ball < 0) or of a boundary launch
+nl_status nl_batch_occupancy_f32(nl_ctx *ctx, int ball, bool inv, int *per_sm);
+nl_status nl_batch_occupancy_f64(nl_ctx *ctx, int ball, bool inv, int *per_sm);

@@ -1,0 +1,78 @@
+// numeric_batch_f64.cu -- instantiation of the persistent batched numeric kernels with double
+// quadrature: one interior launch for every problem of a batch with this value type, one
+// boundary launch per ball mode x kernel type present.
+#include "numeric.cuh"
+
+namespace {
+
+constexpr size_t kBoundarySmem = sizeof(nlq::BoundaryShared<double>) * nlq::kWarpsPerBlock;
+
+template <int BALL, bool INV>
+nl_status boundary(nl_ctx *ctx, const nlq::NumArgs *dA, const nlq::BatchItem *items, int n_items, int *counter,
+                   int blocks, bool set_attr, int *per_sm)
+{
+    if (per_sm) {
+        NL_CK(cudaFuncSetAttribute(nlq::k_boundary_batch<BALL, double, INV>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoundarySmem));
+        NL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, nlq::k_boundary_batch<BALL, double, INV>,
+                                                            nlq::kWarpsPerBlock * 32, kBoundarySmem));
+        return NL_OK;
+    }
+    if (set_attr)
+        NL_CK(cudaFuncSetAttribute(nlq::k_boundary_batch<BALL, double, INV>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBoundarySmem));
+    nlq::k_boundary_batch<BALL, double, INV><<<blocks, nlq::kWarpsPerBlock * 32, kBoundarySmem, ctx->stream>>>(
+        dA, items, n_items, counter);
+    ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    return NL_OK;
+}
+
+template <bool INV>
+nl_status boundary_ball(nl_ctx *ctx, int ball, const nlq::NumArgs *dA, const nlq::BatchItem *items, int n_items,
+                        int *counter, int blocks, bool set_attr, int *per_sm)
+{
+    switch (ball) {
+    case NL_BALL_BARYCENTER:
+        return boundary<NL_BALL_BARYCENTER, INV>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
+    case NL_BALL_NOCAPS: return boundary<NL_BALL_NOCAPS, INV>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
+    case NL_BALL_APPROXCAPS:
+        return boundary<NL_BALL_APPROXCAPS, INV>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
+    case NL_BALL_EXACTCAPS:
+        return boundary<NL_BALL_EXACTCAPS, INV>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
+    case NL_BALL_NGON: return boundary<NL_BALL_NGON, INV>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
+    case NL_BALL_OVERLAP:
+        return boundary<NL_BALL_OVERLAP, INV>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
+    default: return nl_fail(ctx, NL_EINVAL, "unknown ball mode");
+    }
+}
+
+}  // namespace
+
+nl_status nl_launch_interior_batch_f64(nl_ctx *ctx, const nlq::NumArgs *dA, const nlq::BatchItem *items,
+                                       int n_items, int *counter, int blocks)
+{
+    nlq::k_interior_batch<double><<<blocks, nlq::kWarpsPerBlock * 32, 0, ctx->stream>>>(dA, items, n_items, counter);
+    ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    return NL_OK;
+}
+
+nl_status nl_launch_boundary_batch_f64(nl_ctx *ctx, int ball, bool inv, const nlq::NumArgs *dA,
+                                       const nlq::BatchItem *items, int n_items, int *counter, int blocks,
+                                       bool set_attr)
+{
+    return inv ? boundary_ball<true>(ctx, ball, dA, items, n_items, counter, blocks, set_attr, nullptr)
+               : boundary_ball<false>(ctx, ball, dA, items, n_items, counter, blocks, set_attr, nullptr);
+}
+
+nl_status nl_batch_occupancy_f64(nl_ctx *ctx, int ball, bool inv, int *per_sm)
+{
+    if (ball < 0) {
+        NL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, nlq::k_interior_batch<double>,
+                                                            nlq::kWarpsPerBlock * 32, 0));
+        return NL_OK;
+    }
+    return inv ? boundary_ball<true>(ctx, ball, nullptr, nullptr, 0, nullptr, 0, false, per_sm)
+               : boundary_ball<false>(ctx, ball, nullptr, nullptr, 0, nullptr, 0, false, per_sm);
+}

@@ -14,6 +14,8 @@
 // come from the final W + W^T pass through the transposed-slot map.
 #include <cuda_runtime.h>
 
+#include <new>
+
 #include "internal.cuh"
 
 namespace {
@@ -178,17 +180,26 @@ __global__ void k_tslot(int J, const int64_t *row_ptr, const int32_t *col, int64
 // entry to W once, instead of one FP64 atomic per pair and entry.  The upper M_bb of
 // every pair and T_a's own M_aa go straight to W through the local slot map.
 template <typename T>
-__global__ void k_scatter(int K, int64_t E, const int32_t *tri, const int64_t *ptr, const int32_t *idx,
-                          const uint8_t *flag, const T *blk, const double *maa, const int64_t *lslot,
-                          const int64_t *row_ptr, const int32_t *col, double *W, int *err, int cap)
+__device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int32_t *tri, const int64_t *ptr,
+                                              const int32_t *idx, const uint8_t *flag, const T *blk,
+                                              const double *maa, const int64_t *lslot, const int64_t *row_ptr,
+                                              const int32_t *col, double *W, int *err, int cap, int a, int lane,
+                                              int32_t *scol, T *sacc)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int a = blockIdx.x * (blockDim.x >> 5) + wib;
-    int32_t *scol = (int32_t *)(smem_raw + (size_t)wib * 3 * cap * (sizeof(int32_t) + sizeof(T)));
-    T *sacc = (T *)(scol + 3 * cap);
-    if (a >= K) return;
     const int ar[3] = {tri[3 * a], tri[3 * a + 1], tri[3 * a + 2]};
+#ifdef NL_CHECKS
+    // debug build: indices checked, a bad one recorded (bit 64) and its access skipped
+    const int64_t nnz_chk = row_ptr[J];
+    for (int i = 0; i < 3; i++)
+        if (ar[i] < 0 || ar[i] >= J) {
+            atomicOr(err, 64);
+            return;
+        }
+    if (ptr[a] < 0 || ptr[a + 1] > E || ptr[a] > ptr[a + 1]) {
+        atomicOr(err, 64);
+        return;
+    }
+#endif
     int64_t r0[3];
     int len[3];
     bool cached[3];
@@ -206,7 +217,19 @@ __global__ void k_scatter(int K, int64_t E, const int32_t *tri, const int64_t *p
     for (int64_t e = ptr[a] + lane; e < ptr[a + 1]; e += 32) {
         if (!flag[e]) continue;
         const int b = idx[e];
+#ifdef NL_CHECKS
+        if (b < 0 || b >= K) {
+            atomicOr(err, 64);
+            continue;
+        }
+#endif
         const int bn[3] = {tri[3 * b], tri[3 * b + 1], tri[3 * b + 2]};
+#ifdef NL_CHECKS
+        if (bn[0] < 0 || bn[0] >= J || bn[1] < 0 || bn[1] >= J || bn[2] < 0 || bn[2] >= J) {
+            atomicOr(err, 64);
+            continue;
+        }
+#endif
         for (int i = 0; i < 3; i++)
             for (int k = 0; k < 3; k++) {
                 const T v = blk[(int64_t)(3 * i + k) * E + e];
@@ -221,6 +244,12 @@ __global__ void k_scatter(int K, int64_t E, const int32_t *tri, const int64_t *p
                     if (pos >= 0) atomicAdd(&sacc[i * cap + pos], -v); else atomicOr(err, 2);
                 } else {
                     const int64_t sl = find_slot(row_ptr, col, ar[i], bn[k]);
+#ifdef NL_CHECKS
+                    if (sl >= nnz_chk) {
+                        atomicOr(err, 64);
+                        continue;
+                    }
+#endif
                     if (sl >= 0) atomicAdd(&W[sl], -(double)v); else atomicOr(err, 2);
                 }
             }
@@ -228,6 +257,12 @@ __global__ void k_scatter(int K, int64_t E, const int32_t *tri, const int64_t *p
             double v = (double)blk[(int64_t)(9 + p) * E + e];
             if (p < 3) v *= 0.5;
             const int64_t sl = lslot[(int64_t)p * K + b];
+#ifdef NL_CHECKS
+            if (sl >= nnz_chk) {
+                atomicOr(err, 64);
+                continue;
+            }
+#endif
             if (sl >= 0) atomicAdd(&W[sl], v); else atomicOr(err, 2);
         }
     }
@@ -245,6 +280,73 @@ __global__ void k_scatter(int K, int64_t E, const int32_t *tri, const int64_t *p
             const int64_t sl = lslot[(int64_t)p * K + a];
             if (sl >= 0) atomicAdd(&W[sl], v); else atomicOr(err, 2);
         }
+}
+
+template <typename T>
+__global__ void k_scatter(int K, int J, int64_t E, const int32_t *tri, const int64_t *ptr, const int32_t *idx,
+                          const uint8_t *flag, const T *blk, const double *maa, const int64_t *lslot,
+                          const int64_t *row_ptr, const int32_t *col, double *W, int *err, int cap)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int a = blockIdx.x * (blockDim.x >> 5) + wib;
+    int32_t *scol = (int32_t *)(smem_raw + (size_t)wib * 3 * cap * (sizeof(int32_t) + sizeof(T)));
+    T *sacc = (T *)(scol + 3 * cap);
+    if (a >= K) return;
+    scatter_outer<T>(K, J, E, tri, ptr, idx, flag, blk, maa, lslot, row_ptr, col, W, err, cap, a, lane, scol, sacc);
+}
+
+// ---- batched scatter: every problem of a batch in one launch per value type ----
+// off: prefix sums over the problems (of K for the scatter, of nnz for the others);
+// the problem of global index g is the last p with off[p] <= g.
+__device__ __forceinline__ int batch_problem(const int64_t *off, int n, int64_t g)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void k_scatter_batch(const ScatterArgs *__restrict__ S, const int64_t *__restrict__ koff, int n, int cap)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    if (g >= koff[n]) return;
+    int32_t *scol = (int32_t *)(smem_raw + (size_t)wib * 3 * cap * (sizeof(int32_t) + sizeof(T)));
+    T *sacc = (T *)(scol + 3 * cap);
+    const int p = batch_problem(koff, n, g);
+    const ScatterArgs &A = S[p];
+    scatter_outer<T>(A.K, A.J, A.E, A.tri, A.ptr, A.idx, A.flag, (const T *)A.blk, A.maa, A.lslot, A.row_ptr, A.col,
+                     A.W, A.err, cap, (int)(g - koff[p]), lane, scol, sacc);
+}
+
+__global__ void k_zero_batch(const ScatterArgs *__restrict__ S, const int64_t *__restrict__ zoff, int n)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= zoff[n]) return;
+    const int p = batch_problem(zoff, n, g);
+    S[p].W[g - zoff[p]] = 0.0;
+}
+
+__global__ void k_symmetrize_batch(const ScatterArgs *__restrict__ S, const int64_t *__restrict__ zoff, int n)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= zoff[n]) return;
+    const int p = batch_problem(zoff, n, g);
+    const ScatterArgs &A = S[p];
+    const int64_t sl = g - zoff[p], t = A.tslot[sl];
+#ifdef NL_CHECKS
+    if (t >= zoff[p + 1] - zoff[p]) {
+        atomicOr(A.err, 64);
+        return;
+    }
+#endif
+    if (t >= 0) A.val[sl] = A.W[sl] + A.W[t];
+    else atomicOr(A.err, 4);
 }
 
 __global__ void k_symmetrize(int64_t nnz, const double *W, const int64_t *tslot, double *val, int *err)
@@ -289,81 +391,117 @@ __global__ void k_sum_stats(int K, int64_t E, const uint8_t *flag, const int64_t
 
 }  // namespace
 
-nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out)
-{
-    const int K = P->K, J = P->J;
-    nl_status s;
+struct nl_pat {
     uint8_t *sym = nullptr;
     int64_t *ncnt = nullptr, *nptr = nullptr, *ncur = nullptr, *rcnt = nullptr;
     int32_t *ntri = nullptr;
     int *ovf = nullptr;
     unsigned long long *st = nullptr;
-    NL_CK(cudaMallocAsync((void **)&sym, P->E ? P->E : 1, ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ncnt, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&nptr, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ncur, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&rcnt, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ntri, sizeof(int32_t) * 3 * (size_t)K, ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ovf, sizeof(int), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&st, sizeof(unsigned long long) * 4, ctx->stream));
-    NL_CK(cudaMemsetAsync(ncnt, 0, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMemsetAsync(ncur, 0, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMemsetAsync(ovf, 0, sizeof(int), ctx->stream));
-    NL_CK(cudaMemsetAsync(st, 0, sizeof(unsigned long long) * 4, ctx->stream));
+};
+
+nl_pat *nl_pat_new() { return new (std::nothrow) nl_pat(); }
+
+namespace {
+template <class T>
+void free_async(T *&p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync((void *)p, s);
+    p = nullptr;
+}
+}  // namespace
+
+void nl_pat_delete(nl_pat *T, cudaStream_t s)
+{
+    if (!T) return;
+    free_async(T->sym, s); free_async(T->ncnt, s); free_async(T->nptr, s); free_async(T->ncur, s);
+    free_async(T->rcnt, s); free_async(T->ntri, s); free_async(T->ovf, s); free_async(T->st, s);
+    delete T;
+}
+
+nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_slot *h)
+{
+    const int K = P->K, J = P->J;
+    cudaStream_t st = ctx->stream;
+    nl_status s;
+    NL_CK(cudaMallocAsync((void **)&T->sym, P->E ? P->E : 1, st));
+    NL_CK(cudaMallocAsync((void **)&T->ncnt, sizeof(int64_t) * (J + 1), st));
+    NL_CK(cudaMallocAsync((void **)&T->nptr, sizeof(int64_t) * (J + 1), st));
+    NL_CK(cudaMallocAsync((void **)&T->ncur, sizeof(int64_t) * (J + 1), st));
+    NL_CK(cudaMallocAsync((void **)&T->rcnt, sizeof(int64_t) * (J + 1), st));
+    NL_CK(cudaMallocAsync((void **)&T->ntri, sizeof(int32_t) * 3 * (size_t)K, st));
+    NL_CK(cudaMallocAsync((void **)&T->ovf, sizeof(int), st));
+    NL_CK(cudaMallocAsync((void **)&T->st, sizeof(unsigned long long) * 4, st));
+    NL_CK(cudaMemsetAsync(T->ncnt, 0, sizeof(int64_t) * (J + 1), st));
+    NL_CK(cudaMemsetAsync(T->ncur, 0, sizeof(int64_t) * (J + 1), st));
+    NL_CK(cudaMemsetAsync(T->ovf, 0, sizeof(int), st));
+    NL_CK(cudaMemsetAsync(T->st, 0, sizeof(unsigned long long) * 4, st));
     const unsigned wgrid = (unsigned)(((int64_t)K * 32 + 255) / 256);
-    k_symflag<<<wgrid, 256, 0, ctx->stream>>>(K, P->nbr_ptr, P->nbr_split, P->nbr_idx, P->flag, sym); ++ctx->launches;
-    k_node_count<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->tri, ncnt); ++ctx->launches;
+    k_symflag<<<wgrid, 256, 0, st>>>(K, P->nbr_ptr, P->nbr_split, P->nbr_idx, P->flag, T->sym); ++ctx->launches;
+    k_node_count<<<(K + 255) / 256, 256, 0, st>>>(K, P->tri, T->ncnt); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    if ((s = nl_scan_i64(ctx, ncnt, nptr, J)) != NL_OK) return s;
-    k_node_fill<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->tri, nptr, ncur, ntri); ++ctx->launches;
+    if ((s = nl_scan_i64(ctx, T->ncnt, T->nptr, J)) != NL_OK) return s;
+    k_node_fill<<<(K + 255) / 256, 256, 0, st>>>(K, P->tri, T->nptr, T->ncur, T->ntri); ++ctx->launches;
     const size_t smem = sizeof(int32_t) * (NL_HASH_CAP + kListCap);
     NL_CK(cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_rows<<<J, kRowThreads, smem, ctx->stream>>>(J, nptr, ntri, P->tri, P->nbr_ptr, P->nbr_idx, sym, rcnt,
-                                                   nullptr, nullptr, ovf, 0); ++ctx->launches;
+    k_rows<<<J, kRowThreads, smem, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx, T->sym, T->rcnt,
+                                         nullptr, nullptr, T->ovf, 0); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_alloc(ctx, &out->row_ptr, (size_t)J + 1)) != NL_OK) return s;
-    if ((s = nl_scan_i64(ctx, rcnt, out->row_ptr, J)) != NL_OK) return s;
-    k_sum_stats<<<256, 256, 0, ctx->stream>>>(K, P->E, P->flag, P->qp_a, P->cnt_a, st); ++ctx->launches;
-    k_row_max<<<64, 256, 0, ctx->stream>>>(J, rcnt, st); ++ctx->launches;
+    if ((s = nl_scan_i64(ctx, T->rcnt, out->row_ptr, J)) != NL_OK) return s;
+    k_sum_stats<<<256, 256, 0, st>>>(K, P->E, P->flag, P->qp_a, P->cnt_a, T->st); ++ctx->launches;
+    k_row_max<<<64, 256, 0, st>>>(J, T->rcnt, T->st); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    int64_t nnz = 0;
-    int hovf = 0, herr = 0;
-    unsigned long long hst[4];
-    NL_CK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaMemcpyAsync(&nnz, out->row_ptr + J, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaMemcpyAsync(&hovf, ovf, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaMemcpyAsync(hst, st, sizeof hst, cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaStreamSynchronize(ctx->stream));
-    if (hovf) return nl_fail(ctx, NL_EUNSUPPORTED, "a matrix row has more than 4095 columns");
-    if (herr) return nl_fail(ctx, NL_EUNSUPPORTED, "a region exceeded the vertex buffer (error word " +
-                                                     std::to_string(herr) + ")");
+    NL_CK(cudaMemcpyAsync(&h->err, P->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NL_CK(cudaMemcpyAsync(&h->nnz, out->row_ptr + J, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    NL_CK(cudaMemcpyAsync(&h->row_ovf, T->ovf, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NL_CK(cudaMemcpyAsync(h->pat, T->st, sizeof h->pat, cudaMemcpyDeviceToHost, st));
+    return NL_OK;
+}
+
+nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl_host_slot *h)
+{
+    const int K = P->K, J = P->J;
+    cudaStream_t st = ctx->stream;
+    nl_status s;
+    if (h->row_ovf) return nl_fail(ctx, NL_EUNSUPPORTED, "a matrix row has more than 4095 columns");
+    if (h->err) return nl_fail(ctx, NL_EUNSUPPORTED, "a region exceeded the vertex buffer (error word " +
+                                                       std::to_string(h->err) + ")");
+    const int64_t nnz = h->nnz;
     out->n = J;
     out->nnz = nnz;
-    out->n_pairs = (int64_t)hst[0];
-    out->n_qp_pairs = (int64_t)hst[1];
-    out->n_inter = (int64_t)hst[2];
-    P->max_row = (int64_t)hst[3];
+    out->n_pairs = (int64_t)h->pat[0];
+    out->n_qp_pairs = (int64_t)h->pat[1];
+    out->n_inter = (int64_t)h->pat[2];
+    P->max_row = (int64_t)h->pat[3];
     if ((s = nl_alloc(ctx, &out->col_idx, (size_t)nnz)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &out->val, (size_t)nnz)) != NL_OK) return s;
-    k_rows<<<J, kRowThreads, smem, ctx->stream>>>(J, nptr, ntri, P->tri, P->nbr_ptr, P->nbr_idx, sym, nullptr,
-                                                   out->row_ptr, out->col_idx, ovf, 1); ++ctx->launches;
+    const size_t smem = sizeof(int32_t) * (NL_HASH_CAP + kListCap);
+    k_rows<<<J, kRowThreads, smem, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx, T->sym, nullptr,
+                                         out->row_ptr, out->col_idx, T->ovf, 1); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_alloc(ctx, &P->lslot, 6 * (size_t)K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->tslot, (size_t)nnz)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->W, (size_t)nnz)) != NL_OK) return s;
-    k_local_slots<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->tri, out->row_ptr, out->col_idx, P->lslot); ++ctx->launches;
-    k_tslot<<<(unsigned)(((int64_t)J * 32 + 255) / 256), 256, 0, ctx->stream>>>(J, out->row_ptr, out->col_idx,
-                                                                              P->tslot); ++ctx->launches;
+    k_local_slots<<<(K + 255) / 256, 256, 0, st>>>(K, P->tri, out->row_ptr, out->col_idx, P->lslot); ++ctx->launches;
+    k_tslot<<<(unsigned)(((int64_t)J * 32 + 255) / 256), 256, 0, st>>>(J, out->row_ptr, out->col_idx, P->tslot);
+    ++ctx->launches;
     NL_CK(cudaGetLastError());
-    NL_CK(cudaFreeAsync(sym, ctx->stream));
-    NL_CK(cudaFreeAsync(ncnt, ctx->stream));
-    NL_CK(cudaFreeAsync(nptr, ctx->stream));
-    NL_CK(cudaFreeAsync(ncur, ctx->stream));
-    NL_CK(cudaFreeAsync(rcnt, ctx->stream));
-    NL_CK(cudaFreeAsync(ntri, ctx->stream));
-    NL_CK(cudaFreeAsync(ovf, ctx->stream));
-    NL_CK(cudaFreeAsync(st, ctx->stream));
     return NL_OK;
+}
+
+nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out)
+{
+    nl_host_slot *h = nullptr;
+    nl_status s = nl_host_slots(ctx, 1, &h);
+    if (s != NL_OK) return s;
+    nl_pat *T = nl_pat_new();
+    if (!T) return nl_fail(ctx, NL_ENOMEM, "host allocation failed");
+    if ((s = nl_pattern_a(ctx, P, out, T, h)) == NL_OK) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        s = e == cudaSuccess ? nl_pattern_b(ctx, P, out, T, h) : nl_cuda_fail(ctx, e, "cudaStreamSynchronize");
+    }
+    nl_pat_delete(T, ctx->stream);
+    return s;
 }
 
 template <typename T>
@@ -380,7 +518,7 @@ static nl_status launch_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     }
     NL_CK(cudaFuncSetAttribute(k_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(96 * 1024)));
     const unsigned grid = (unsigned)((K + warps - 1) / warps);
-    k_scatter<T><<<grid, 32 * warps, smem, ctx->stream>>>(K, P->E, P->tri, P->nbr_ptr, P->nbr_idx, P->flag,
+    k_scatter<T><<<grid, 32 * warps, smem, ctx->stream>>>(K, P->J, P->E, P->tri, P->nbr_ptr, P->nbr_idx, P->flag,
                                                            (const T *)P->blk, P->maa, P->lslot, out->row_ptr,
                                                            out->col_idx, P->W, P->err, cap); ++ctx->launches;
     NL_CK(cudaGetLastError());
@@ -398,4 +536,50 @@ nl_status nl_run_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     }
     NL_CK(cudaGetLastError());
     return NL_OK;
+}
+
+// ---- batched scatter launches ----
+nl_status nl_launch_zero_batch(nl_ctx *ctx, const ScatterArgs *dS, const int64_t *dzoff, int n, int64_t total)
+{
+    if (total <= 0) return NL_OK;
+    k_zero_batch<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(dS, dzoff, n); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    return NL_OK;
+}
+
+nl_status nl_launch_symmetrize_batch(nl_ctx *ctx, const ScatterArgs *dS, const int64_t *dzoff, int n,
+                                     int64_t total)
+{
+    if (total <= 0) return NL_OK;
+    k_symmetrize_batch<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(dS, dzoff, n); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    return NL_OK;
+}
+
+template <typename T>
+static nl_status launch_scatter_batch(nl_ctx *ctx, const ScatterArgs *dS, const int64_t *dkoff, int n,
+                                      int64_t totalK, int64_t max_row, bool set_attr)
+{
+    if (totalK <= 0) return NL_OK;
+    int cap = (int)(((max_row > 0 ? max_row : 1) + 3) & ~3LL);
+    int warps = 4;
+    while (warps > 1 && (size_t)warps * 3 * cap * (sizeof(int32_t) + sizeof(T)) > 96 * 1024) warps >>= 1;
+    size_t smem = (size_t)warps * 3 * cap * (sizeof(int32_t) + sizeof(T));
+    if (smem > 96 * 1024) {
+        cap = 0;
+        smem = 0;
+    }
+    if (set_attr)
+        NL_CK(cudaFuncSetAttribute(k_scatter_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(96 * 1024)));
+    const unsigned grid = (unsigned)((totalK + warps - 1) / warps);
+    k_scatter_batch<T><<<grid, 32 * warps, smem, ctx->stream>>>(dS, dkoff, n, cap); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    return NL_OK;
+}
+
+nl_status nl_launch_scatter_batch(nl_ctx *ctx, bool f64, const ScatterArgs *dS, const int64_t *dkoff, int n,
+                                  int64_t totalK, int64_t max_row, bool set_attr)
+{
+    return f64 ? launch_scatter_batch<double>(ctx, dS, dkoff, n, totalK, max_row, set_attr)
+               : launch_scatter_batch<float>(ctx, dS, dkoff, n, totalK, max_row, set_attr);
 }

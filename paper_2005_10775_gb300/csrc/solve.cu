@@ -482,18 +482,4 @@ nl_status nl_cg(nl_ctx *ctx, const nl_csr *Ac, const double *b, double *x, doubl
     return out;
 }
 
-nl_status nl_assemble_batch(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const nl_config *cfgs, nl_csr *outs)
-{
-    if (!ctx) return NL_EINVAL;
-    if (n < 0 || (n > 0 && (!meshes || !cfgs || !outs))) return nl_fail(ctx, NL_EINVAL, "bad batch arguments");
-    for (int i = 0; i < n; i++) {
-        nl_status s = nl_assemble(ctx, &meshes[i], &cfgs[i], &outs[i]);
-        if (s != NL_OK) {
-            for (int k = 0; k < i; k++) nl_csr_free(ctx, &outs[k]);
-            return s;
-        }
-    }
-    return NL_OK;
-}
-
 }  // extern "C"

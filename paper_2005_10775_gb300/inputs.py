@@ -190,6 +190,45 @@ def problem(name: str) -> Problem:
     raise KeyError(name)
 
 
+BATCH_DELTAS = (0.05, 0.075, 0.1, 0.15, 0.2)
+
+
+def batch_cells(delta: float, kmin: int = 2000, kmax: int = 40000, mmin: int = 3, mmax: int = 9):
+    """Cells per side n of the meshes over (-delta, 1 + delta)^2 with delta / h = m an
+    integer in [mmin, mmax] and K = 2 n^2 in [kmin, kmax]: n = m (1 + 2 delta) / delta."""
+    out = []
+    for m in range(mmin, mmax + 1):
+        x = m * (1.0 + 2.0 * delta) / delta
+        n = int(round(x))
+        if abs(x - n) < 1e-9 and kmin <= 2 * n * n <= kmax:
+            out.append(n)
+    return out
+
+
+def batch_problems(count: int = 64, seed: int = 1077600, kmin: int = 2000, kmax: int = 40000,
+                   mmax: int = 9) -> list[Problem]:
+    """The batched workload: `count` independent assemblies of uneven size and delta.
+
+    Problem i: delta = BATCH_DELTAS[i % 5]; a mesh over (-delta, 1 + delta)^2 whose cells
+    per side make delta / h an integer and K in [kmin, kmax] (drawn with a seeded PCG64
+    among the admissible sizes); structured if i is even, else jittered +-0.2 h with seed
+    seed + i; the paper's nocaps ball if i % 4 < 2, else approxcaps with one arc point per
+    cap (m = 2); 7-point rules (degree 5) outer and inner; constant kernel 4 / (pi delta^4).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        d = BATCH_DELTAS[i % len(BATCH_DELTAS)]
+        opts = batch_cells(d, kmin, kmax, 3, mmax)
+        n = int(opts[int(rng.integers(len(opts)))])
+        jit = 0.0 if i % 2 == 0 else 0.2
+        m = split_square_mesh(-d, 1.0 + d, n, jitter=jit, seed=seed + i if jit else None)
+        ball = "nocaps" if i % 4 < 2 else "approxcaps"
+        out.append(Problem(f"batch{i}", m, d, "const", const_kernel_c(d), ball, "dunavant7", "dunavant7",
+                           cap_m=2))
+    return out
+
+
 def paper_grid(h: float) -> Mesh:
     """Uniform grid of Sec. 8 / Table 1: (-0.1, 1.1)^2 with cell size h (delta = 0.1)."""
     n = int(round(1.2 / h))

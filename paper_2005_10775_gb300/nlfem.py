@@ -48,6 +48,16 @@ class nl_csr(ctypes.Structure):
                 ("n_qp_pairs", ctypes.c_int64), ("n_inter", ctypes.c_int64), ("priv", ctypes.c_void_p)]
 
 
+class nl_batch_info(ctypes.Structure):
+    _fields_ = [("chunk", ctypes.c_int32), ("order", ctypes.c_int32), ("blocks", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("source", ctypes.c_int32), ("n_tried", ctypes.c_int32),
+                ("tuned_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+
+NL_BATCH_NO_TUNE = 1
+SCHED_SOURCES = {0: "default", 1: "tuned", 2: "cached"}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
@@ -62,6 +72,11 @@ def _load():
         "nl_assemble_numeric": (ctypes.c_int, [ctypes.c_void_p, P(nl_csr)]),
         "nl_assemble_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, P(nl_mesh), P(nl_config),
                                              P(nl_csr)]),
+        "nl_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, P(nl_mesh), P(nl_config), P(nl_csr),
+                                           ctypes.c_int32, P(ctypes.c_void_p)]),
+        "nl_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+        "nl_batch_get_info": (ctypes.c_int, [ctypes.c_void_p, P(nl_batch_info)]),
+        "nl_batch_destroy": (None, [ctypes.c_void_p, ctypes.c_void_p]),
         "nl_interactions": (ctypes.c_int, [ctypes.c_void_p, P(nl_mesh), P(nl_config), ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
         "nl_extract": (ctypes.c_int, [ctypes.c_void_p, P(nl_csr), P(nl_mesh), P(nl_csr), P(nl_csr)]),
@@ -180,6 +195,36 @@ def nl_assemble_batch(ctx, meshes, cfgs):
     O = (nl_csr * n)()
     _check(ctx, _L.nl_assemble_batch(ctx, n, M, C, O))
     return list(O)
+
+
+def nl_batch_create(ctx, meshes, cfgs, flags: int = 0):
+    """Returns (handle, [nl_csr] * n); the matrices stay valid after nl_batch_destroy
+    and are freed with nl_csr_free."""
+    n = len(meshes)
+    M = (nl_mesh * n)(*meshes)
+    C = (nl_config * n)(*cfgs)
+    O = (nl_csr * n)()
+    h = ctypes.c_void_p()
+    _check(ctx, _L.nl_batch_create(ctx, n, M, C, O, flags, ctypes.byref(h)))
+    return h, list(O)
+
+
+def nl_batch_run(ctx, batch) -> None:
+    _check(ctx, _L.nl_batch_run(ctx, batch))
+
+
+def nl_batch_get_info(batch) -> dict:
+    info = nl_batch_info()
+    st = _L.nl_batch_get_info(batch, ctypes.byref(info))
+    if st != NL_OK:
+        raise NlError(st, "nl_batch_get_info")
+    d = {k: getattr(info, k) for k, _ in nl_batch_info._fields_}
+    d["source"] = SCHED_SOURCES.get(d["source"], str(d["source"]))
+    return d
+
+
+def nl_batch_destroy(ctx, batch) -> None:
+    _L.nl_batch_destroy(ctx, batch)
 
 
 def nl_interactions(ctx, mesh: nl_mesh, cfg: nl_config):

@@ -49,9 +49,11 @@ def test_struct_layouts_match_c(tmp_path):
 #include "nlfem.h"
 #define P(T, f) printf(#T "." #f " %zu\\n", offsetof(T, f));
 int main(void) {
-    printf("nl_mesh %zu\\nnl_config %zu\\nnl_csr %zu\\n", sizeof(nl_mesh), sizeof(nl_config), sizeof(nl_csr));
+    printf("nl_mesh %zu\\nnl_config %zu\\nnl_csr %zu\\nnl_batch_info %zu\\n", sizeof(nl_mesh), sizeof(nl_config),
+           sizeof(nl_csr), sizeof(nl_batch_info));
     P(nl_mesh, elem_in_omega) P(nl_config, ngon_offsets) P(nl_config, cap_printed)
     P(nl_config, prec) P(nl_csr, val) P(nl_csr, priv) P(nl_csr, n_qp_pairs)
+    P(nl_batch_info, source) P(nl_batch_info, tuned_ms) P(nl_batch_info, default_ms)
     return 0;
 }
 """)
@@ -61,6 +63,7 @@ int main(void) {
     assert int(got["nl_mesh"]) == ctypes.sizeof(nlfem.nl_mesh)
     assert int(got["nl_config"]) == ctypes.sizeof(nlfem.nl_config)
     assert int(got["nl_csr"]) == ctypes.sizeof(nlfem.nl_csr)
+    assert int(got["nl_batch_info"]) == ctypes.sizeof(nlfem.nl_batch_info)
     for key, val in got.items():
         if "." in key:
             t, f = key.split(".")
