@@ -607,6 +607,112 @@ __device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, cons
 
 // Near field of the singular kernel for a whole T_b: near iff dist(x, T_b) < diam(T_b).
 // FP32 decides when the two differ by more than eta (1e-5 delta, far above the FP32
+// ---------------------------------------------------------------------------
+// FP32 region of the disc balls nocaps and approxcaps (Sec. 4.2.1, 4.2.2) with certified
+// discrete choices.  d[i] = v_i - x in FP32 (within err0 of the exact differences).
+// The FP64 walk (ball_walk) is decided by three kinds of predicates, each certified here
+// with the margin tau = 1e-5 delta (rin_m2 = (delta - tau)^2, rout_p2 = (delta + tau)^2):
+//   * vertex in the closed ball: |d|^2 <= rin_m2 -> in, > rout_p2 -> out;
+//   * roots of an edge p -> q in (0, 1): with both end points certified, in -> in has none,
+//     in -> out exactly one (the larger root, an exit), out -> in exactly one (the smaller
+//     root, an entry); out -> out has two (entry, exit) when the segment passes within
+//     delta - tau of x, none when it stays farther than delta + tau;
+//   * anything closer to a threshold is undecided: return -1 (the FP64 walk decides).
+// Then the walk emits the same points in the same order as the FP64 walk (vertex if
+// inside, then the edge's roots by increasing parameter; approxcaps inserts the dyadic arc
+// points between every exit and the next entry), so the vertex count and the kind equal
+// the FP64 ones; the coordinates are FP32 values.  Returns the vertex count (0 when the
+// region is empty or degenerate), writes P[0..n) and *kind.
+// ---------------------------------------------------------------------------
+constexpr int kBallCap = 16;   // FP32 region vertices (nocaps <= 6; approxcaps 6 + 3 (m - 1))
+
+template <int BALL>
+__device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g, F2 P[kBallCap], int *kind)
+{
+    const float delta = (float)g.delta, d2f = delta * delta;
+    bool ins[3];
+    int nin = 0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float r = d[i].x * d[i].x + d[i].y * d[i].y;
+        if (r <= g.rin_m2) ins[i] = true;
+        else if (r > g.rout_p2) ins[i] = false;
+        else return -1;
+        nin += ins[i];
+    }
+    F2 W[6];
+    int tag[6];   // 0 vertex, 1 entry, 2 exit
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const F2 p = d[i], q = d[(i + 1) % 3];
+        if (ins[i]) { W[n] = p; tag[n] = 0; n++; }
+        const bool qin = ins[(i + 1) % 3];
+        if (ins[i] && qin) continue;
+        const float ex = q.x - p.x, ey = q.y - p.y;
+        const float a = ex * ex + ey * ey, b = p.x * ex + p.y * ey, c = p.x * p.x + p.y * p.y - d2f;
+        int nr;
+        if (!ins[i] && !qin) {
+            // out -> out: closest point of the segment to x
+            const float t = fminf(fmaxf(-b / a, 0.f), 1.f);
+            const float cx = p.x + t * ex, cy = p.y + t * ey, r = cx * cx + cy * cy;
+            if (r <= g.rin_m2) nr = 2;
+            else if (r > g.rout_p2) nr = 0;
+            else return -1;
+        } else {
+            nr = 1;
+        }
+        if (nr == 0) continue;
+        // roots of a l^2 + 2 b l + c = 0 without cancellation
+        const float sq = sqrtf(fmaxf(b * b - a * c, 0.f));
+        const float tt = b > 0.f ? -(b + sq) : (sq - b);
+        float l1 = tt / a, l2 = c / tt;
+        if (l1 > l2) { const float z = l1; l1 = l2; l2 = z; }
+        if (nr == 2 || !ins[i]) {   // entry at the smaller root
+            W[n].x = p.x + l1 * ex; W[n].y = p.y + l1 * ey; tag[n] = 1; n++;
+        }
+        if (nr == 2 || ins[i]) {    // exit at the larger root
+            W[n].x = p.x + l2 * ex; W[n].y = p.y + l2 * ey; tag[n] = 2; n++;
+        }
+    }
+    if (BALL == NL_BALL_NOCAPS) {
+        if (n < 3) return 0;
+        for (int i = 0; i < n; i++) P[i] = W[i];
+        *kind = (nin == 3 && n == 3) ? KIND_WHOLE : KIND_PARTIAL;
+        return n;
+    }
+    // approxcaps
+    if (n < 2) return 0;
+    const int level = g.cap_level, per = (1 << level) - 1;
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        const int j = (i + 1) % n;
+        if (m + 1 > kBallCap) return -1;
+        P[m++] = W[i];
+        if (tag[i] == 2 && tag[j] == 1) {
+            if (m + per > kBallCap) return -1;
+            // dyadic bisection of the arc from W[i] to W[j]: point k of 2^level sub-arcs is
+            // built from its two neighbours of the coarser level
+            F2 pts[kBallCap + 1];
+            pts[0] = W[i];
+            pts[1 << level] = W[j];
+            for (int l = level - 1; l >= 0; l--) {
+                const int step = 1 << l;
+                for (int k = step; k < (1 << level); k += 2 * step) {
+                    const float ux = pts[k - step].x + pts[k + step].x, uy = pts[k - step].y + pts[k + step].y;
+                    const float sc = delta * rsqrtf(ux * ux + uy * uy);
+                    pts[k].x = ux * sc;
+                    pts[k].y = uy * sc;
+                }
+            }
+            for (int k = 1; k < (1 << level); k++) P[m++] = pts[k];
+        }
+    }
+    if (m < 3) return 0;
+    *kind = (nin == 3 && n == 3) ? KIND_WHOLE : KIND_PARTIAL;
+    return m;
+}
+
 // error of either); otherwise the FP64 test decides.  Returns 0 far, 1 near, -1 undecided.
 __device__ __forceinline__ int near_f32(const F2 dl[3], float diamf, float eta)
 {

@@ -358,7 +358,12 @@ __device__ __forceinline__ void poly_sums_f32(const NumArgs &A, const nlg::F2 *P
             const float p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
             const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
             const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
-            sums_add<float>(S, f.w * ar, p0, p1, p2);
+            float w = f.w * ar;
+            if (A.kernel == NL_KERNEL_INV_DIST) {   // psi = c / |y - x|, coordinates relative to x
+                const float yx = m0 * s0.x + m1 * s1.x + m2 * s2.x, yy = m0 * s0.y + m1 * s1.y + m2 * s2.y;
+                w *= rsqrtf(yx * yx + yy * yy);
+            }
+            sums_add<float>(S, w, p0, p1, p2);
         }
         nqp += nr;
         fk[0] = fn[0]; fk[1] = fn[1]; fk[2] = fn[2];
@@ -752,6 +757,30 @@ __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, 
             } else {
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
                 poly_sums_sh(A, cb, which, lane, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
+            }
+            return true;
+        }
+    }
+    if (sizeof(T) == sizeof(float) && (BALL == NL_BALL_NOCAPS || BALL == NL_BALL_APPROXCAPS)) {
+        nlg::F2 dl[3];
+        for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
+        if (A.kernel == NL_KERNEL_INV_DIST && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
+            return exact_item_fp64<BALL, T>(A, c, o, S, nq, kind, nv, ncap, cb, lane);
+        nlg::F2 P[nlg::kBallCap];
+        int k = nlg::KIND_PARTIAL;
+        const int n = nlg::ball_region_f32<BALL>(dl, A.geo, P, &k);
+        if (n >= 0) {
+            // certified FP32 walk: same vertex count and kind as the FP64 walk
+            if (n < 3) return false;
+            kind = k;
+            nv = n;
+            ncap = 0;
+            if (k == nlg::KIND_WHOLE) {
+                const D2 Vb[3] = {{c.vx[0], c.vy[0]}, {c.vx[1], c.vy[1]}, {c.vx[2], c.vy[2]}};
+                whole_sums<T>(A, Vb, (T)c.akc, D2{o.x, o.y}, S, nq, dl);
+            } else {
+                const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
+                poly_sums_f32(A, P, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
             }
             return true;
         }

@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(int J, const int64_t *nt_p
         if (threadIdx.x == 0) cnt[j] = n;
         return;
     }
+    __syncthreads();   // every thread has read the column count before the counter is reused
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < NL_HASH_CAP; i += blockDim.x)

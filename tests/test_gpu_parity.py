@@ -92,7 +92,8 @@ def test_parity_small(nl, ctx, ball, kw, prec):
     Dg, stats = gpu_assemble(nl, ctx, p, prec)
     compare(Dg, O.to_csr(out), prec)
     assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
-    h, c, q = gpu_interactions(nl, ctx, p)
+    # the interaction records of the same precision's path (FP32 paths certify their regions)
+    h, c, q = gpu_interactions(nl, ctx, p, prec=prec)
     np.testing.assert_array_equal(c, out["count_a"])
     np.testing.assert_array_equal(q, out["qp_a"])
     np.testing.assert_array_equal(h, out["hash_a"])
@@ -119,21 +120,22 @@ def test_parity_inv_dist_kernel(nl, ctx, ball, prec):
     Dg, stats = gpu_assemble(nl, ctx, p, prec, duffy_n=4)
     compare(Dg, O.to_csr(out), prec)
     assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
-    h, c, q = gpu_interactions(nl, ctx, p, duffy_n=4)
+    h, c, q = gpu_interactions(nl, ctx, p, prec=prec, duffy_n=4)
     np.testing.assert_array_equal(q, out["qp_a"])
     np.testing.assert_array_equal(h, out["hash_a"])
 
 
-@pytest.mark.parametrize("ball", ["nocaps", "exactcaps"])
-def test_parity_paper_protocol(nl, ctx, ball):
+@pytest.mark.parametrize("ball", ["nocaps", "approxcaps", "exactcaps"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_parity_paper_protocol(nl, ctx, ball, prec):
     # rule switch of Sec. 8: 4-point rule for near pairs, 7-point vertex rule otherwise; 3-point inner
     d = 0.1
     m = I.paper_grid(0.05)
     p = I.Problem("paper", m, d, "const", I.const_kernel_c(d), ball, "switch47", "gauss3")
     out = O.assemble(m, oracle_cfg(p, cap_printed=1), want_hash=True)
-    Dg, stats = gpu_assemble(nl, ctx, p, "fp64", cap_printed=1)
-    compare(Dg, O.to_csr(out), "fp64")
-    h, c, q = gpu_interactions(nl, ctx, p, cap_printed=1)
+    Dg, stats = gpu_assemble(nl, ctx, p, prec, cap_printed=1)
+    compare(Dg, O.to_csr(out), prec)
+    h, c, q = gpu_interactions(nl, ctx, p, prec=prec, cap_printed=1)
     np.testing.assert_array_equal(h, out["hash_a"])
 
 
