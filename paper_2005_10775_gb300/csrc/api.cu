@@ -230,6 +230,7 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
         }
     }
     A.geo.tau = (float)tau;
+    A.geo.inv_tau = (float)(1.0 / tau);
     if (c.ball == NL_BALL_NGON) {
         // regular polygon R (cos 2 pi k / N, sin 2 pi k / N)?  (enables the angular pass window)
         const int N = c.ngon_n;

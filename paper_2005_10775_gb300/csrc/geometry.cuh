@@ -56,6 +56,7 @@ struct GeoParams {
     int ngon_n, cap_level, cap_printed;
     // FP32 certification data
     float tau;            // decision margin (1e-5 delta)
+    float inv_tau;        // 1 / tau
     float rin_m2;         // (r_in - tau)^2: r_in = delta (disc balls) or the polygon's inradius
     float rout_p2;        // (delta + tau)^2
     float b_in2, b_out2;  // barycenter ball: (delta - tau)^2, (delta + tau)^2
@@ -69,11 +70,27 @@ struct GeoParams {
     float sector, rin_tau; // 2 pi / N; inradius - tau
 };
 
+// atan2 from the arctangent polynomial of Abramowitz & Stegun 4.4.49 (Hastings): on [0, 1]
+// its error is at most 1e-5 rad; with the octant reduction and the FP32 rounding the
+// angle is within 2e-5 rad of atan2(y, x).
+__device__ __forceinline__ float atan2_poly(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float a = mx > 0.f ? __fdividef(mn, mx) : 0.f, s = a * a;
+    float r = a * (0.9998660f + s * (-0.3302995f + s * (0.1801410f + s * (-0.0851330f + s * 0.0208351f))));
+    if (ay > ax) r = 1.57079632679f - r;
+    if (x < 0.f) r = 3.14159265359f - r;
+    return y < 0.f ? -r : r;
+}
+
 // Passes of the polygon clip that can change a triangle with FP32 coordinates d (relative to
-// x), as a bit mask over k.  For a regular polygon, half-plane k (normal angle (k + 1/2) 2pi/N)
-// can only cut points within angle alpha of its normal, cos alpha = (r_in - tau) / |p|: every
-// pass whose normal is farther than alpha (plus half a sector of slack) from the triangle's
-// angular extent keeps all of it at least tau inside and is the identity.
+// x), as a bit mask over k.  For a regular polygon, half-plane k (outward normal at angle
+// (k + 1/2) 2pi/N, at distance r_in) holds every point p with |p| cos(angle(p) - phi_k) <=
+// r_in - tau inside by tau; for a point of T_b (|p| <= r_max, angle within the triangle's
+// angular extent when x is outside T_b) that holds whenever phi_k is farther than alpha,
+// cos alpha = (r_in - tau) / r_max, from the extent.  Passes outside the extent widened by
+// alpha (and 2e-3 rad for the angle errors, about 100x their bound) are the identity.
 __device__ __forceinline__ uint64_t ngon_pass_mask(const F2 d[3], const GeoParams &g)
 {
     const int N = g.ngon_n;
@@ -86,10 +103,11 @@ __device__ __forceinline__ uint64_t ngon_pass_mask(const F2 d[3], const GeoParam
     float rmax = 0.f, t[3];
     for (int i = 0; i < 3; i++) {
         rmax = fmaxf(rmax, sqrtf(d[i].x * d[i].x + d[i].y * d[i].y));
-        t[i] = atan2f(d[i].y, d[i].x);
+        t[i] = atan2_poly(d[i].y, d[i].x);
     }
     if (rmax <= g.rin_tau) return 0ull;
-    const float alpha = acosf(g.rin_tau / rmax);
+    const float cz = g.rin_tau / rmax;
+    const float alpha = atan2_poly(sqrtf(fmaxf(1.f - cz * cz, 0.f)), cz);   // acos(cz)
     // sort the three angles, take the arc complementary to the largest gap
     float a0 = t[0], a1 = t[1], a2 = t[2], tmp;
     if (a0 > a1) { tmp = a0; a0 = a1; a1 = tmp; }
@@ -102,7 +120,7 @@ __device__ __forceinline__ uint64_t ngon_pass_mask(const F2 d[3], const GeoParam
     else if (g01 >= g12) { lo = a1; hi = a0 + two_pi; }
     else { lo = a2; hi = a1 + two_pi; }
     if (hi - lo > 0.8f * 3.14159265f) return full;
-    const float slack = alpha + 0.5f * g.sector + 1e-3f;
+    const float slack = alpha + 2e-3f;
     lo -= slack;
     hi += slack;
     if (hi - lo >= two_pi) return full;
@@ -461,71 +479,13 @@ __device__ __forceinline__ int classify_vertices(const F2 d[3], float rin_m2, fl
 // + rounding.  Returns the vertex count, or -1 when a sign is not certain (the
 // caller then runs the FP64 clip).  Coordinates are relative to x.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int clip_ngon_f32(const F2 dl[3], float err0, const GeoParams &g, F2 *out, bool *cut,
-                                             int *overflow)
-{
-    F2 A[NL_MAXV], B[NL_MAXV];
-    float eA[NL_MAXV], eB[NL_MAXV];
-    const float kEps = 8.0f * 5.9604645e-8f;   // 8 units of 2^-24
-    int n = 3;
-    for (int i = 0; i < 3; i++) { A[i] = dl[i]; eA[i] = err0; }
-    *cut = false;
-    uint64_t mask = ngon_pass_mask(dl, g);
-    while (mask && n > 0) {
-        const int k = __ffsll((long long)mask) - 1;
-        mask &= mask - 1;
-        const float ox = g.of[k][0], oy = g.of[k][1], ex = g.ef[k][0], ey = g.ef[k][1];
-        const float el = g.mk[k] / g.tau;   // |e_k|
-        float o[NL_MAXV], u[NL_MAXV];
-        bool all_in = true;
-        for (int i = 0; i < n; i++) {
-            const float rx = A[i].x - ox, ry = A[i].y - oy;
-            o[i] = ex * ry - ey * rx;
-            // |rx| + |ry| <= |A|_1 + |o_k|_1 <= |A|_1 + 2 R: a pass-independent rounding allowance
-            u[i] = el * (eA[i] + kEps * (2.f * (fabsf(A[i].x) + fabsf(A[i].y)) + g.r2));
-            if (!(fabsf(o[i]) > u[i])) return -1;
-            all_in = all_in && (o[i] > 0.f);
-        }
-        if (all_in) continue;
-        *cut = true;
-        int m = 0;
-        for (int i = 0; i < n; i++) {
-            if (m + 2 > NL_MAXV) {
-                *overflow = 1;
-                return -1;
-            }
-            const int ip = (i + n - 1) % n;
-            const float ds = o[ip], de = o[i];
-            const bool e_in = de > 0.f, s_in = ds > 0.f;
-            if (e_in != s_in) {
-                const F2 sp = A[ip], ep = A[i];
-                const float t = ds / (ds - de);
-                const float dx = ep.x - sp.x, dy = ep.y - sp.y;
-                F2 p;
-                p.x = sp.x + t * dx;
-                p.y = sp.y + t * dy;
-                const float den = fabsf(ds) + fabsf(de) - u[ip] - u[i];
-                const float len = fabsf(dx) + fabsf(dy);
-                eB[m] = fmaxf(eA[ip], eA[i]) + len * (u[ip] + u[i]) / den +
-                        kEps * (fabsf(sp.x) + fabsf(sp.y) + fabsf(ep.x) + fabsf(ep.y) + len);
-                B[m++] = p;
-            }
-            if (e_in) {
-                eB[m] = eA[i];
-                B[m++] = A[i];
-            }
-        }
-        n = m;
-        for (int i = 0; i < n; i++) { A[i] = B[i]; eA[i] = eB[i]; }
-    }
-    for (int i = 0; i < n; i++) out[i] = A[i];
-    return n;
-}
 
 // The same certified FP32 clip with its two vertex buffers in shared memory (one
 // column per lane, [slot][lane]: no bank conflicts) and a capacity of kClipCap
 // vertices (a triangle cut kClipCap - 3 times); more vertices return -1 and the
-// caller takes the FP64 clip.  Orientations are recomputed instead of stored.
+// caller takes the FP64 clip.  One loop per pass certifies every orientation and builds
+// the clipped list at the same time; a pass that keeps every vertex is the identity and
+// its copy is dropped.
 //
 // Error bound of o = e x (a - o_k) evaluated in FP32 (u = 2^-24), against the same
 // expression on the FP64 vertex A*, offset O* and edge E*:
@@ -555,19 +515,10 @@ __device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, cons
         const int k = __ffsll((long long)mask) - 1;
         mask &= mask - 1;
         const float ox = g.of[k][0], oy = g.of[k][1], ex = g.ef[k][0], ey = g.ef[k][1];
-        const float el = g.mk[k] / g.tau;   // |e_k|
-        bool all_in = true;
-        for (int i = 0; i < n; i++) {
-            const float rx = cb.x[cur][i][lane] - ox, ry = cb.y[cur][i][lane] - oy;
-            const float o = ex * ry - ey * rx;
-            const float u = el * (cb.e[cur][i][lane] + kU3o + kU9 * (fabsf(rx) + fabsf(ry)));
-            if (!(fabsf(o) > u)) return -1;
-            all_in = all_in && (o > 0.f);
-        }
-        if (all_in) continue;
-        *cut = true;
+        const float el = g.mk[k] * g.inv_tau;   // |e_k|
         const int nxt = cur ^ 1;
         int m = 0;
+        bool all_in = true;
         float sx = cb.x[cur][n - 1][lane], sy = cb.y[cur][n - 1][lane], se = cb.e[cur][n - 1][lane];
         float so = ex * (sy - oy) - ey * (sx - ox);
         float su = el * (se + kU3o + kU9 * (fabsf(sx - ox) + fabsf(sy - oy)));
@@ -575,18 +526,22 @@ __device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, cons
             const float px = cb.x[cur][i][lane], py = cb.y[cur][i][lane], pe = cb.e[cur][i][lane];
             const float po = ex * (py - oy) - ey * (px - ox);
             const float pu = el * (pe + kU3o + kU9 * (fabsf(px - ox) + fabsf(py - oy)));
+            if (!(fabsf(po) > pu)) return -1;
             const bool p_in = po > 0.f, s_in = so > 0.f;
+            all_in = all_in && p_in;
             if (p_in != s_in) {
                 if (m >= kClipCap) return -1;
-                const float t = so / (so - po);
+                // t by the fast division (within 2 ulp): its error is in the rounding term
+                const float t = __fdividef(so, so - po);
                 const float dx = px - sx, dy = py - sy;
-                const float den = fabsf(so) + fabsf(po) - su - pu;
+                const float den = fabsf(so) + fabsf(po) - su - pu;   // > 0: both signs certified
                 const float len = fabsf(dx) + fabsf(dy);
                 cb.x[nxt][m][lane] = sx + t * dx;
                 cb.y[nxt][m][lane] = sy + t * dy;
-                // p = s + t (q - s): interpolated error, the error of t times |q - s|, and rounding
-                cb.e[nxt][m][lane] = fmaxf(se, pe) + len * (su + pu) / den +
-                                     4.f * 5.9604645e-8f * (fabsf(sx) + fabsf(sy) + len);
+                // p = s + t (q - s): interpolated error, the error of t times |q - s| (its
+                // quotient rounded up by 1e-6 relative), and rounding
+                cb.e[nxt][m][lane] = fmaxf(se, pe) + __fdividef(len * (su + pu), den) * 1.000001f +
+                                     6.f * 5.9604645e-8f * (fabsf(sx) + fabsf(sy) + len);
                 m++;
             }
             if (p_in) {
@@ -598,6 +553,8 @@ __device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, cons
             }
             sx = px; sy = py; se = pe; so = po; su = pu;
         }
+        if (all_in) continue;   // identity pass: keep the current list
+        *cut = true;
         cur = nxt;
         n = m;
     }
