@@ -63,6 +63,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def max_over_ranks(x, dev, dist=None):
+    """The largest value of x over the ranks (every rank gets it): the job's time is
+    that of its slowest rank.  x is a float; dev the device of the reduction buffer."""
+    import torch
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds_local, world, dev, dist=None):
+    """Whole-job throughput of N replicas: the units all ranks processed divided by the
+    slowest rank's time (weak scaling: every rank does the same work)."""
+    return units_per_rank * world / max_over_ranks(seconds_local, dev, dist)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -224,10 +240,7 @@ def batch_bench(args, nl, ctx, stream, dev, world, dist, rank):
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-        t = torch.tensor([tot], device=dev, dtype=torch.float64)
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()) / steps
+        return max_over_ranks(tot, dev, dist) / steps
 
     state = {}
 
@@ -305,12 +318,10 @@ def batch_bench(args, nl, ctx, stream, dev, world, dist, rank):
         for _ in range(args.steps):
             e2e_once()
         torch.cuda.synchronize()
-        te = torch.tensor([(time.perf_counter() - t0) / args.steps], device=dev, dtype=torch.float64)
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_value = job_throughput(n_qp, (time.perf_counter() - t0) / args.steps, world, dev, dist)
         h2d = sum(p.mesh.vx.nbytes + p.mesh.vy.nbytes + p.mesh.tri.nbytes for p in probs)
         d2h = sum(8 * (p.mesh.nv + 1) + 12 * z for p, z in zip(probs, nnzs))
-        e2e = {"value": n_qp * world / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
     peaks, src = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -500,10 +511,7 @@ def main():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        t = torch.tensor([tot], device=dev, dtype=torch.float64)
-        if dist:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), phase / steps, stats, launches, wall
+        return max_over_ranks(tot, dev, dist), phase / steps, stats, launches, wall
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -542,12 +550,10 @@ def main():
                                                   va.data_ptr()))
             nl.nl_csr_free(ctx, out)
         torch.cuda.synchronize()
-        te = torch.tensor([time.perf_counter() - t0], device=dev, dtype=torch.float64)
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_value = job_throughput(n_qp * args.steps, time.perf_counter() - t0, world, dev, dist)
         h2d = m.vx.nbytes + m.vy.nbytes + m.tri.nbytes + (0 if hoff is None else hoff.nbytes)
         d2h = 8 * (m.nv + 1) + 12 * nnz
-        e2e = {"value": n_qp * world * args.steps / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
     solve = None
