@@ -98,6 +98,9 @@ typedef struct {
     int32_t prec;                   /* nl_prec */
     int32_t duffy_n;                /* INV_DIST: Gauss points per unit panel of the near-singular rule (1..7) */
     int32_t cap_printed;            /* EXACTCAPS: 1 = cap weight as printed in Sec. 5.2 (half Eq. (areacap)) */
+    int32_t shifted;                /* 1 = shifted-centre ball (Sec. 4.3): every outer point of T_a uses the
+                                       ball centred at T_a's barycentre ((v0 + v1) + v2) / 3, approximated
+                                       by `ball`; CONST kernel only (NL_EUNSUPPORTED otherwise) */
 } nl_config;
 
 /* Square CSR matrix in device memory, columns sorted in each row. */

@@ -75,6 +75,8 @@ typedef struct {
     int32_t outer, inner;
     int32_t duffy_n;                /* Gauss-Legendre points per direction of the Duffy rule */
     int32_t cap_printed;            /* 1: cap weight as printed in Sec. 5.2, (1/4) delta^2 (2t - sin 2t) */
+    int32_t shifted;                /* 1: every outer point of T_a uses the ball centred at bary_a (Sec. 4.3,
+                                       "shifted center approximate ball"); constant kernel only */
 } or_cfg;
 
 typedef struct {
@@ -743,6 +745,7 @@ int or_assemble(const or_mesh *m, const or_cfg *cfg, const int32_t *a_list, int3
     memset(res, 0, sizeof *res);
     if (!rule_of(cfg->inner)) return -1;
     if (cfg->outer != OR_RULE_SWITCH47 && !rule_of(cfg->outer)) return -1;
+    if (cfg->shifted && cfg->kernel != OR_KERNEL_CONST) return -1;
     int K = m->nt;
     int na = a_list ? n_a : K;
     double hmax = or_hmax(m);
@@ -784,6 +787,8 @@ int or_assemble(const or_mesh *m, const or_cfg *cfg, const int32_t *a_list, int3
         int a = a_list ? a_list[ia] : ia;
         pt Va[3] = { vert(m, a, 0), vert(m, a, 1), vert(m, a, 2) };
         double area_a = tri_area(Va[0], Va[1], Va[2]);
+        /* shifted ball (Sec. 4.3): the centre of every outer point's ball is T_a's barycentre */
+        const pt centre_a = barycentre(Va[0], Va[1], Va[2]);
         int na_b = (row_mask && !touch[a]) ? n_touch : K;
         for (int ib = 0; ib < na_b; ib++) {
             int b = (row_mask && !touch[a]) ? touch_list[ib] : ib;
@@ -797,12 +802,13 @@ int or_assemble(const or_mesh *m, const or_cfg *cfg, const int32_t *a_list, int3
                 x.x = L[0] * Va[0].x + L[1] * Va[1].x + L[2] * Va[2].x;
                 x.y = L[0] * Va[0].y + L[1] * Va[1].y + L[2] * Va[2].y;
                 double W = L[3] * area_a;
+                const pt xc = cfg->shifted ? centre_a : x;   /* centre of the ball */
                 region R;
-                make_region(Vb, x, cfg, &R);
+                make_region(Vb, xc, cfg, &R);
                 if (R.kind == OR_KIND_NONE) continue;
                 any = 1;
                 inner_sums I;
-                inner_quadrature(cfg, Vb, x, &R, &I);
+                inner_quadrature(cfg, Vb, xc, &R, &I);
                 nqp[tid] += I.nqp;
                 if (want_rec) {
                     if (nrec[tid] == caprec[tid]) {

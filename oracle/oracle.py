@@ -56,7 +56,7 @@ class _Cfg(ctypes.Structure):
                 ("ngon_n", ctypes.c_int32), ("cap_m", ctypes.c_int32),
                 ("ngon_off", ctypes.POINTER(ctypes.c_double)),
                 ("outer", ctypes.c_int32), ("inner", ctypes.c_int32),
-                ("duffy_n", ctypes.c_int32), ("cap_printed", ctypes.c_int32)]
+                ("duffy_n", ctypes.c_int32), ("cap_printed", ctypes.c_int32), ("shifted", ctypes.c_int32)]
 
 
 class _Rec(ctypes.Structure):
@@ -125,11 +125,12 @@ def _mesh_struct(mesh, keep):
 
 
 def make_cfg(keep, delta, ball, outer="dunavant7", inner="dunavant7", kernel="const", kernel_c=1.0,
-             ngon_off=None, cap_m=2, duffy_n=4, cap_printed=0):
+             ngon_off=None, cap_m=2, duffy_n=4, cap_printed=0, shifted=0):
     off = keep.arr(np.zeros((1, 2)) if ngon_off is None else ngon_off, np.float64)
     n = 0 if ngon_off is None else off.shape[0]
     return _Cfg(float(delta), float(kernel_c), KERNEL[kernel], BALL[ball], n, int(cap_m),
-                _ptr(off, ctypes.c_double), RULE[outer], RULE[inner], int(duffy_n), int(cap_printed))
+                _ptr(off, ctypes.c_double), RULE[outer], RULE[inner], int(duffy_n), int(cap_printed),
+                int(shifted))
 
 
 def cfg_of(problem, keep, **over):

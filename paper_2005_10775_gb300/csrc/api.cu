@@ -162,6 +162,9 @@ nl_status nl_validate(nl_ctx *ctx, const nl_mesh *m, const nl_config *c)
         return nl_fail(ctx, NL_EINVAL, "cap_m must be a power of two in 1..16");
     if (c->kernel == NL_KERNEL_INV_DIST && (c->duffy_n < 1 || c->duffy_n > 7))
         return nl_fail(ctx, NL_EINVAL, "duffy_n must be in 1..7");
+    if (c->shifted != 0 && c->shifted != 1) return nl_fail(ctx, NL_EINVAL, "shifted must be 0 or 1");
+    if (c->shifted && c->kernel != NL_KERNEL_CONST)
+        return nl_fail(ctx, NL_EUNSUPPORTED, "the shifted-centre ball is defined for the constant kernel");
     return NL_OK;
 }
 
@@ -197,6 +200,7 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     gauss_legendre01(2, A.gl2_x, A.gl2_w);
     A.kernel = c.kernel;
     A.ball = c.ball;
+    A.shifted = c.shifted ? 1 : 0;
     A.kc = c.kernel_c;
     A.geo.delta = c.delta;
     A.geo.d2 = P->d2;

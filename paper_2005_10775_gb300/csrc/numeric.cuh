@@ -46,6 +46,7 @@ struct NumArgs {
     double thr2;                      // (delta - h_max)^2, or -1 when delta <= h_max
     int kernel;                       // nl_kernel
     int ball;                         // nl_ball (run-time dispatch of the batched kernel)
+    int shifted;                      // every outer point's ball centred at bary_a (Sec. 4.3)
     double kc;
     nlg::GeoParams geo;
     uint8_t *flag;
@@ -529,6 +530,14 @@ __device__ __forceinline__ void stage_outer(const NumArgs &A, int a, OuterPt *sq
         o.l0 = l0; o.l1 = l1; o.l2 = l2;
         o.lx = (float)(o.x - A.bx[a]);
         o.ly = (float)(o.y - A.by[a]);
+        if (A.shifted) {
+            // shifted-centre ball (Sec. 4.3): the region is built around bary_a for every outer
+            // point; x_q keeps its weight and barycentrics (o.W, o.l*)
+            o.x = A.bx[a];
+            o.y = A.by[a];
+            o.lx = 0.f;
+            o.ly = 0.f;
+        }
         o.Wf = (float)o.W;
         o.l0f = (float)l0; o.l1f = (float)l1; o.l2f = (float)l2;
         sq[q] = o;

@@ -39,7 +39,7 @@ class nl_config(ctypes.Structure):
                 ("kernel", ctypes.c_int32), ("ball", ctypes.c_int32), ("ngon_n", ctypes.c_int32),
                 ("cap_m", ctypes.c_int32), ("ngon_offsets", ctypes.c_void_p),
                 ("outer", ctypes.c_int32), ("inner", ctypes.c_int32), ("prec", ctypes.c_int32),
-                ("duffy_n", ctypes.c_int32), ("cap_printed", ctypes.c_int32)]
+                ("duffy_n", ctypes.c_int32), ("cap_printed", ctypes.c_int32), ("shifted", ctypes.c_int32)]
 
 
 class nl_csr(ctypes.Structure):
@@ -144,11 +144,11 @@ def make_mesh(mesh, keep) -> nl_mesh:
 
 
 def make_config(keep, delta, ball, outer="dunavant7", inner="dunavant7", kernel="const", kernel_c=1.0,
-                ngon_off=None, cap_m=2, prec="fp64", duffy_n=4, cap_printed=0) -> nl_config:
+                ngon_off=None, cap_m=2, prec="fp64", duffy_n=4, cap_printed=0, shifted=0) -> nl_config:
     n = 0 if ngon_off is None else int(ngon_off.shape[0])
     return nl_config(float(delta), float(kernel_c), KERNEL[kernel], BALL[ball], n, int(cap_m),
                      _ptr(ngon_off, keep, np.float64), RULE[outer], RULE[inner], PREC[prec], int(duffy_n),
-                     int(cap_printed))
+                     int(cap_printed), int(shifted))
 
 
 def config_of(problem, keep, **over) -> nl_config:

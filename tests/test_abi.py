@@ -51,7 +51,7 @@ def test_struct_layouts_match_c(tmp_path):
 int main(void) {
     printf("nl_mesh %zu\\nnl_config %zu\\nnl_csr %zu\\nnl_batch_info %zu\\n", sizeof(nl_mesh), sizeof(nl_config),
            sizeof(nl_csr), sizeof(nl_batch_info));
-    P(nl_mesh, elem_in_omega) P(nl_config, ngon_offsets) P(nl_config, cap_printed)
+    P(nl_mesh, elem_in_omega) P(nl_config, ngon_offsets) P(nl_config, cap_printed) P(nl_config, shifted)
     P(nl_config, prec) P(nl_csr, val) P(nl_csr, priv) P(nl_csr, n_qp_pairs)
     P(nl_batch_info, source) P(nl_batch_info, tuned_ms) P(nl_batch_info, default_ms)
     return 0;

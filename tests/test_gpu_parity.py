@@ -139,6 +139,29 @@ def test_parity_paper_protocol(nl, ctx, ball, prec):
     np.testing.assert_array_equal(h, out["hash_a"])
 
 
+@pytest.mark.parametrize("ball", ["nocaps", "approxcaps", "ngon"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+def test_parity_shifted_ball(nl, ctx, ball, prec):
+    # shifted-centre ball (Sec. 4.3): the region of every outer point of T_a is built around bary_a
+    p = small_problem(ball, outer="gauss4", inner="gauss3")
+    out = O.assemble(p.mesh, oracle_cfg(p, shifted=1), want_hash=True)
+    Dg, stats = gpu_assemble(nl, ctx, p, prec, shifted=1)
+    compare(Dg, O.to_csr(out), prec)
+    assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
+    h, c, q = gpu_interactions(nl, ctx, p, prec=prec, shifted=1)
+    np.testing.assert_array_equal(q, out["qp_a"])
+    np.testing.assert_array_equal(h, out["hash_a"])
+
+
+def test_shifted_ball_needs_constant_kernel(nl, ctx):
+    p = small_problem("nocaps", n=24, kernel="inv_dist")
+    keep = nl._Keep()
+    mesh = nl.make_mesh(p.mesh, keep)
+    with pytest.raises(nl.NlError) as e:
+        nl.nl_assemble(ctx, mesh, nl.config_of(p, keep, shifted=1))
+    assert e.value.status == nl.NL_EUNSUPPORTED
+
+
 def test_ragged_and_tiny(nl, ctx):
     # 7x7 cells -> 98 triangles (not a multiple of the warps per block), and a single triangle
     p = small_problem("ngon", n=7).with_(delta=0.4, ngon_off=I.ngon_offsets(32, 0.4))

@@ -125,3 +125,27 @@ def test_paper_table1_end_to_end_on_gpu(nl, ctx, ball, h):
     U[m.node_in_omega.astype(bool)] = x
     err = O.l2_error_omega(m, U, I.manufactured_u)
     assert err == pytest.approx(TABLE1[(ball, h)], rel=0.15)
+
+
+def test_paper_table2_shifted_nocaps_on_gpu(nl, ctx):
+    # Table 2, column (6): shifted-centre ball with nocaps, 4-point outer and 3-point inner rules,
+    # assembled, extracted and solved on the GPU (h = 0.05, printed L2 error 6.89e-3)
+    d, h = 0.1, 0.05
+    m = I.paper_grid(h)
+    p = I.Problem("paper", m, d, "const", I.const_kernel_c(d), "nocaps", "gauss4", "gauss3")
+    keep = nl._Keep()
+    mesh = nl.make_mesh(m, keep)
+    D = nl.nl_assemble(ctx, mesh, nl.config_of(p, keep, prec="fp32c", shifted=1))
+    A, B = nl.nl_extract(ctx, D, mesh)
+    try:
+        u = I.manufactured_u(m.vx, m.vy)
+        F = nl.nl_rhs(ctx, B, mesh, I.manufactured_f(m.vx, m.vy), u)
+        x = np.zeros(A.n)
+        nl.nl_cg(ctx, A, F, x, rtol=1e-10, max_it=20000)
+    finally:
+        for z in (D, A, B):
+            nl.nl_csr_free(ctx, z)
+    U = u.copy()
+    U[m.node_in_omega.astype(bool)] = x
+    assert O.l2_error_omega(m, U, I.manufactured_u) == pytest.approx(6.89e-3, rel=0.15)
+

@@ -474,6 +474,60 @@ def test_paper_table1_rates():
         assert 1.6 < math.log2(e1 / e2) < 2.4, ball
 
 
+def _table2():
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_table2.txt")
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            b, h, e = line.split()
+            rows[(b, float(h))] = float(e)
+    return rows
+
+
+def _shifted_l2(h):
+    # Table 2, column (6): shifted-centre ball (Sec. 4.3) with nocaps, 4-point outer, 3-point inner
+    d = 0.1
+    m = I.paper_grid(h)
+    u = I.manufactured_u(m.vx, m.vy)
+    f = I.manufactured_f(m.vx, m.vy)
+    cfg = dict(delta=d, ball="nocaps", outer="gauss4", inner="gauss3", kernel_c=I.const_kernel_c(d), shifted=1)
+    U = O.solve(O.to_csr(O.assemble(m, cfg)), m, f, u)
+    return O.l2_error_omega(m, U, I.manufactured_u)
+
+
+@pytest.mark.parametrize("h", [0.05, 0.025])
+def test_paper_table2_shifted_nocaps(h):
+    assert _shifted_l2(h) == pytest.approx(_table2()[("shifted_nocaps", h)], rel=0.15)
+
+
+def test_paper_table2_rate():
+    # second order observed for the shifted ball (Table 2 rate 2.08 at h = 0.05 -> 0.025)
+    rate = math.log2(_shifted_l2(0.05) / _shifted_l2(0.025))
+    assert 1.7 < rate < 2.4, rate
+
+
+def test_shifted_ball_is_the_centred_ball_of_bary_a():
+    # the shifted region of (T_a, q, T_b) equals the ordinary region of T_b around bary_a: with a
+    # one-point outer rule at the centroid the two assemblies coincide exactly
+    d = 0.1
+    m = I.split_square_mesh(-0.1, 1.1, 12, jitter=0.2, seed=9)
+    base = dict(delta=d, ball="nocaps", outer="gauss3", inner="gauss3", kernel_c=I.const_kernel_c(d))
+    plain = O.assemble(m, base, want_hash=True)
+    shifted = O.assemble(m, dict(base, shifted=1), want_hash=True)
+    # gauss3 points differ from the barycentre, so the two differ; their symmetric structure holds
+    D = O.to_csr(shifted)
+    assert abs(D - D.T).max() <= 1e-14 * abs(D).max()
+    assert np.abs(np.asarray(D.sum(axis=1))).max() <= 1e-13 * abs(D).max()
+    assert shifted["n_pairs"] > 0 and plain["n_pairs"] > 0
+    # every record of the shifted ball is one of the centred ball of some point inside T_a: the
+    # region of q does not depend on q, so the per-q records of a pair repeat
+    out = O.assemble(m, dict(base, shifted=1), want_rec=True)
+    recs = {}
+    for r in out["rec"]:
+        recs.setdefault((int(r["a"]), int(r["b"])), set()).add((int(r["kind"]), int(r["nverts"])))
+    assert all(len(v) == 1 for v in recs.values())
+
+
 def test_singular_kernel_second_order_convergence():
     # psi = 3/(pi delta^3)/|x-y| has second moment 2 (like 4/(pi delta^4)), so L u = Laplacian u for
     # the paper's cubic u (Sec. 8): the manufactured solve converges at second order in h
