@@ -49,7 +49,14 @@ typedef enum {
     NL_BALL_APPROXCAPS = 2,   /* nocaps plus cap_m - 1 arc points per cap         (Sec. 4.2.2) */
     NL_BALL_EXACTCAPS = 3,    /* nocaps plus a one-point centroid rule per cap    (Sec. 5.2, Eq. (areacap)) */
     NL_BALL_NGON = 4,         /* T_b clipped by the regular inscribed ngon_n-gon  (Sec. 9, regular polygon) */
-    NL_BALL_OVERLAP = 5       /* whole T_b iff T_b n B_delta(x) is non-empty      (Sec. 4.2.4, Eq. (overlap)) */
+    NL_BALL_OVERLAP = 5,      /* whole T_b iff T_b n B_delta(x) is non-empty      (Sec. 4.2.4, Eq. (overlap)) */
+    /* barycenter ball for the inner integral, with the outer integral over T_a restricted to its
+       support T_a n B_delta(bary_b), approximated by nocaps / approxcaps (cap_m) of that ball around
+       bary_b and integrated with the outer rule on each fan subtriangle (Sec. 6.2, barycenter case;
+       Table 3).  One interaction record per pair (q = 0, the support's kind and vertex count);
+       qp-pairs = outer points x inner points.  CONST kernel, not shifted. */
+    NL_BALL_BARY_NOCAPS = 6,
+    NL_BALL_BARY_APPROXCAPS = 7
 } nl_ball;
 
 /* Quadrature rules on triangles (weights relative to the area). */

@@ -56,7 +56,10 @@
 
 /* ---- enums (the oracle's own; mapped from strings by oracle/oracle.py) ---- */
 enum { OR_BALL_BARYCENTER = 0, OR_BALL_NOCAPS = 1, OR_BALL_APPROXCAPS = 2,
-       OR_BALL_EXACTCAPS = 3, OR_BALL_NGON = 4, OR_BALL_OVERLAP = 5 };
+       OR_BALL_EXACTCAPS = 3, OR_BALL_NGON = 4, OR_BALL_OVERLAP = 5,
+       /* barycenter ball with the outer integral over T_a n B_delta(bary_b) only (Sec. 6.2,
+          barycenter case; Table 3): that support approximated by nocaps / approxcaps */
+       OR_BALL_BARY_NOCAPS = 6, OR_BALL_BARY_APPROXCAPS = 7 };
 enum { OR_RULE_GAUSS3 = 0, OR_RULE_GAUSS4 = 1, OR_RULE_PAPER7 = 2,
        OR_RULE_DUNAVANT7 = 3, OR_RULE_DUNAVANT16 = 4, OR_RULE_SWITCH47 = 5 };
 enum { OR_KERNEL_CONST = 0, OR_KERNEL_INV_DIST = 1 };
@@ -393,6 +396,8 @@ static int overlaps(const pt *V, pt x, double d2)
     return in;
 }
 
+static void disc_region(const pt *V, pt x, const or_cfg *cfg, int ball, region *R);
+
 /* R(x, T_b) for the selected ball (Sec. 4, Sec. 5.2, Sec. 9) */
 static void make_region(const pt *V, pt x, const or_cfg *cfg, region *R)
 {
@@ -416,17 +421,39 @@ static void make_region(const pt *V, pt x, const or_cfg *cfg, region *R)
     }
     case OR_BALL_NOCAPS:
     case OR_BALL_APPROXCAPS:
-    case OR_BALL_EXACTCAPS: {
+    case OR_BALL_EXACTCAPS:
+        disc_region(V, x, cfg, cfg->ball, R);
+        return;
+    case OR_BALL_NGON: {
+        int n = clip_ngon(V, x, cfg, R->P);
+        if (n >= 3) {
+            R->nverts = n;
+            int same = (n == 3);
+            for (int i = 0; same && i < 3; i++)
+                same = (R->P[i].x == V[i].x && R->P[i].y == V[i].y);
+            R->kind = same ? OR_KIND_WHOLE : OR_KIND_PARTIAL;
+        }
+        return;
+    }
+    }
+}
+
+/* the nocaps / approxcaps / exactcaps region of triangle V around the ball B_delta(x) */
+static void disc_region(const pt *V, pt x, const or_cfg *cfg, int ball, region *R)
+{
+    double delta = cfg->delta, d2 = delta * delta;
+    R->kind = OR_KIND_NONE; R->nverts = 0; R->ncaps = 0;
+    {
         pt W[12]; int tag[12], nin;
         int n = ball_walk(V, x, d2, W, tag, &nin);
-        if (n < 3 && !(cfg->ball != OR_BALL_NOCAPS && n == 2)) return;
+        if (n < 3 && !(ball != OR_BALL_NOCAPS && n == 2)) return;
         if (n < 2) return;
-        if (cfg->ball == OR_BALL_NOCAPS || cfg->ball == OR_BALL_EXACTCAPS) {
+        if (ball == OR_BALL_NOCAPS || ball == OR_BALL_EXACTCAPS) {
             if (n >= 3) {
                 for (int i = 0; i < n; i++) R->P[i] = W[i];
                 R->nverts = n;
             }
-            if (cfg->ball == OR_BALL_EXACTCAPS) {
+            if (ball == OR_BALL_EXACTCAPS) {
                 for (int i = 0; i < n; i++) {
                     int j = (i + 1) % n;
                     if (tag[i] == 2 && tag[j] == 1) {
@@ -449,19 +476,6 @@ static void make_region(const pt *V, pt x, const or_cfg *cfg, region *R)
         }
         if (R->nverts >= 3 || R->ncaps > 0)
             R->kind = (nin == 3 && n == 3) ? OR_KIND_WHOLE : OR_KIND_PARTIAL;
-        return;
-    }
-    case OR_BALL_NGON: {
-        int n = clip_ngon(V, x, cfg, R->P);
-        if (n >= 3) {
-            R->nverts = n;
-            int same = (n == 3);
-            for (int i = 0; same && i < 3; i++)
-                same = (R->P[i].x == V[i].x && R->P[i].y == V[i].y);
-            R->kind = same ? OR_KIND_WHOLE : OR_KIND_PARTIAL;
-        }
-        return;
-    }
     }
 }
 
@@ -746,6 +760,8 @@ int or_assemble(const or_mesh *m, const or_cfg *cfg, const int32_t *a_list, int3
     if (!rule_of(cfg->inner)) return -1;
     if (cfg->outer != OR_RULE_SWITCH47 && !rule_of(cfg->outer)) return -1;
     if (cfg->shifted && cfg->kernel != OR_KERNEL_CONST) return -1;
+    const int bary_outer = (cfg->ball == OR_BALL_BARY_NOCAPS || cfg->ball == OR_BALL_BARY_APPROXCAPS);
+    if (bary_outer && (cfg->kernel != OR_KERNEL_CONST || cfg->shifted)) return -1;
     int K = m->nt;
     int na = a_list ? n_a : K;
     double hmax = or_hmax(m);
@@ -796,7 +812,62 @@ int or_assemble(const or_mesh *m, const or_cfg *cfg, const int32_t *a_list, int3
             const or_rule *ro = outer_rule(m, cfg, a, b, hmax);
             double Maa[3][3] = {{0}}, Mbb[3][3] = {{0}}, Mab[3][3] = {{0}};
             int any = 0;
-            for (int q = 0; q < ro->n; q++) {
+            if (bary_outer) {
+                /* Sec. 6.2, barycenter case: the outer integrand is supported on
+                   S = T_a n B_delta(bary_b) and the inner integral is over the whole T_b.  S is
+                   approximated by nocaps / approxcaps around bary_b, fanned from its first point,
+                   and the outer rule is applied on every subtriangle (the experiment of Table 3).
+                   One interaction record per pair; qp-pairs = outer points x inner points. */
+                const pt cb = barycentre(Vb[0], Vb[1], Vb[2]);
+                region S;
+                disc_region(Va, cb, cfg, cfg->ball == OR_BALL_BARY_NOCAPS ? OR_BALL_NOCAPS : OR_BALL_APPROXCAPS, &S);
+                if (S.kind == OR_KIND_NONE || S.nverts < 3) continue;
+                region Rb;
+                Rb.kind = OR_KIND_WHOLE; Rb.nverts = 3; Rb.ncaps = 0;
+                for (int i = 0; i < 3; i++) Rb.P[i] = Vb[i];
+                inner_sums I;
+                inner_quadrature(cfg, Vb, cb, &Rb, &I);   /* constant kernel: the same for every x */
+                int64_t nout = 0;
+                for (int k = 1; k + 1 < S.nverts; k++) {
+                    const pt S0 = S.P[0], S1 = S.P[k], S2p = S.P[k + 1];
+                    const double area = tri_area(S0, S1, S2p);
+                    for (int q = 0; q < ro->n; q++) {
+                        const double *L = ro->p[q];
+                        pt x;
+                        x.x = L[0] * S0.x + L[1] * S1.x + L[2] * S2p.x;
+                        x.y = L[0] * S0.y + L[1] * S1.y + L[2] * S2p.y;
+                        const double W = L[3] * area;
+                        double la[3];
+                        barycentric(Va, x, la);   /* phi_a at the outer point */
+                        for (int i = 0; i < 3; i++)
+                            for (int k2 = 0; k2 < 3; k2++) {
+                                Maa[i][k2] += W * I.s0 * la[i] * la[k2];
+                                Mbb[i][k2] += W * I.S2[i][k2];
+                                Mab[i][k2] += W * la[i] * I.s1[k2];
+                            }
+                        nout++;
+                    }
+                }
+                any = 1;
+                nqp[tid] += nout * I.nqp;
+                if (want_rec) {
+                    if (nrec[tid] == caprec[tid]) {
+                        caprec[tid] = caprec[tid] ? 2 * caprec[tid] : 4096;
+                        recs[tid] = (or_record *)realloc(recs[tid], sizeof(or_record) * caprec[tid]);
+                    }
+                    or_record *r = &recs[tid][nrec[tid]++];
+                    r->a = a; r->b = b; r->q = 0; r->kind = (int8_t)S.kind;
+                    r->nverts = (int8_t)S.nverts; r->ncaps = 0;
+                } else {
+                    nrec[tid]++;
+                }
+                if (want_hash) {
+                    res->hash_a[a] += record_hash(a, b, 0, S.kind, S.nverts, 0);
+                    res->count_a[a] += 1;
+                    res->qp_a[a] += nout * I.nqp;
+                }
+            }
+            for (int q = 0; !bary_outer && q < ro->n; q++) {
                 const double *L = ro->p[q];
                 pt x;
                 x.x = L[0] * Va[0].x + L[1] * Va[1].x + L[2] * Va[2].x;

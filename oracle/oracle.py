@@ -27,7 +27,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "nl_oracle.c")
 SO = os.path.join(HERE, "_build", "libnl_oracle.so")
 
-BALL = {"barycenter": 0, "nocaps": 1, "approxcaps": 2, "exactcaps": 3, "ngon": 4, "overlap": 5}
+BALL = {"barycenter": 0, "nocaps": 1, "approxcaps": 2, "exactcaps": 3, "ngon": 4, "overlap": 5,
+        "bary_nocaps": 6, "bary_approxcaps": 7}
 RULE = {"gauss3": 0, "gauss4": 1, "paper7": 2, "dunavant7": 3, "dunavant16": 4, "switch47": 5}
 KERNEL = {"const": 0, "inv_dist": 1}
 KIND_NONE, KIND_WHOLE, KIND_PARTIAL = 0, 1, 2

@@ -150,14 +150,14 @@ nl_status nl_validate(nl_ctx *ctx, const nl_mesh *m, const nl_config *c)
     if (m->nv <= 0 || m->nt <= 0 || !m->vx || !m->vy || !m->tri)
         return nl_fail(ctx, NL_EINVAL, "mesh needs nv > 0, nt > 0 and vx, vy, tri");
     if (!(c->delta > 0.0) || !isfinite(c->delta)) return nl_fail(ctx, NL_EINVAL, "delta must be positive");
-    if (c->ball < NL_BALL_BARYCENTER || c->ball > NL_BALL_OVERLAP) return nl_fail(ctx, NL_EINVAL, "bad ball");
+    if (c->ball < NL_BALL_BARYCENTER || c->ball > NL_BALL_BARY_APPROXCAPS) return nl_fail(ctx, NL_EINVAL, "bad ball");
     if (c->kernel != NL_KERNEL_CONST && c->kernel != NL_KERNEL_INV_DIST) return nl_fail(ctx, NL_EINVAL, "bad kernel");
     if (c->prec != NL_PREC_FP64 && c->prec != NL_PREC_FP32_COMP) return nl_fail(ctx, NL_EINVAL, "bad precision");
     if (c->inner < NL_RULE_GAUSS3 || c->inner > NL_RULE_DUNAVANT16) return nl_fail(ctx, NL_EINVAL, "bad inner rule");
     if (c->outer < NL_RULE_GAUSS3 || c->outer > NL_RULE_SWITCH47) return nl_fail(ctx, NL_EINVAL, "bad outer rule");
     if (c->ball == NL_BALL_NGON && (c->ngon_n < 3 || c->ngon_n > 64 || !c->ngon_offsets))
         return nl_fail(ctx, NL_EINVAL, "ngon needs 3 <= ngon_n <= 64 and ngon_offsets");
-    if (c->ball == NL_BALL_APPROXCAPS &&
+    if ((c->ball == NL_BALL_APPROXCAPS || c->ball == NL_BALL_BARY_APPROXCAPS) &&
         (c->cap_m < 1 || c->cap_m > 16 || (c->cap_m & (c->cap_m - 1)) != 0))
         return nl_fail(ctx, NL_EINVAL, "cap_m must be a power of two in 1..16");
     if (c->kernel == NL_KERNEL_INV_DIST && (c->duffy_n < 1 || c->duffy_n > 7))
@@ -165,6 +165,9 @@ nl_status nl_validate(nl_ctx *ctx, const nl_mesh *m, const nl_config *c)
     if (c->shifted != 0 && c->shifted != 1) return nl_fail(ctx, NL_EINVAL, "shifted must be 0 or 1");
     if (c->shifted && c->kernel != NL_KERNEL_CONST)
         return nl_fail(ctx, NL_EUNSUPPORTED, "the shifted-centre ball is defined for the constant kernel");
+    if ((c->ball == NL_BALL_BARY_NOCAPS || c->ball == NL_BALL_BARY_APPROXCAPS) &&
+        (c->kernel != NL_KERNEL_CONST || c->shifted))
+        return nl_fail(ctx, NL_EUNSUPPORTED, "the outer-support barycenter balls take the constant kernel, unshifted");
     return NL_OK;
 }
 
@@ -201,6 +204,7 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     A.kernel = c.kernel;
     A.ball = c.ball;
     A.shifted = c.shifted ? 1 : 0;
+    A.outer_support = (c.ball == NL_BALL_BARY_NOCAPS || c.ball == NL_BALL_BARY_APPROXCAPS) ? 1 : 0;
     A.kc = c.kernel_c;
     A.geo.delta = c.delta;
     A.geo.d2 = P->d2;
@@ -262,6 +266,9 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     for (int r = 0; r < A.inner.n; r++) {
         A.fin[r] = make_float4((float)A.inner.l[r][0], (float)A.inner.l[r][1], (float)A.inner.l[r][2],
                                (float)A.inner.w[r]);
+    for (int q = 0; q < A.outer.n; q++)
+        A.fout[q] = make_float4((float)A.outer.l[q][0], (float)A.outer.l[q][1], (float)A.outer.l[q][2],
+                                (float)A.outer.w[q]);
     }
     A.flag = P->flag;
     A.blk = P->blk;

@@ -548,7 +548,9 @@ nl_status nl_prepare_c(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_host_slot *h)
         const double tau = 1e-5 * cfg->delta;
         int mode = 0;
         double lim = cfg->delta - 2.0 * tau;
-        if (cfg->ball == NL_BALL_BARYCENTER) mode = 1;
+        if (cfg->ball == NL_BALL_BARYCENTER || cfg->ball == NL_BALL_BARY_NOCAPS ||
+            cfg->ball == NL_BALL_BARY_APPROXCAPS)
+            mode = 1;   // whole T_b (and whole support T_a) iff |bary_a - bary_b| + r_a <= delta
         else if (cfg->ball == NL_BALL_NGON) lim = P->rin - 2.0 * tau;
         if (cfg->kernel == NL_KERNEL_INV_DIST) mode = cfg->ball == NL_BALL_BARYCENTER ? 2 : 3;
         if ((s = nl_alloc(ctx, &P->nbr_split, (size_t)K)) != NL_OK) return s;

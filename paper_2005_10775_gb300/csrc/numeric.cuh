@@ -39,6 +39,7 @@ struct NumArgs {
     const int32_t *nbr_idx;
     RuleTab outer, inner;
     float4 fin[NL_MAXQ + 8];          // inner rule in FP32: barycentrics (x, y, z) and weight (w)
+    float4 fout[NL_MAXQ + 8];         // outer rule in FP32 (the outer-support composite rule)
     double gl_x[8], gl_w[8];          // Gauss-Legendre on [0,1] with duffy_n points
     double gl2_x[2], gl2_w[2];
     int duffy_n;
@@ -47,6 +48,7 @@ struct NumArgs {
     int kernel;                       // nl_kernel
     int ball;                         // nl_ball (run-time dispatch of the batched kernel)
     int shifted;                      // every outer point's ball centred at bary_a (Sec. 4.3)
+    int outer_support;                // barycenter ball with the outer integral over T_a n B(bary_b)
     double kc;
     nlg::GeoParams geo;
     uint8_t *flag;
@@ -635,9 +637,15 @@ __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const Ou
                 for (int i = 0; i < 3; i++) { dl[i].x = vl[i].x - o.lx; dl[i].y = vl[i].y - o.ly; }
             whole_sums<T>(A, Vb, akc, D2{o.x, o.y}, S, nq, inv ? dl : nullptr);
             combine<T>(o, S, v);
-            acc.cnt++;
             acc.qp += nq;
-            if (A.stats) acc.hsum += nlg::record_hash(a, b, q - q0, nlg::KIND_WHOLE, 3, 0);
+            if (!A.outer_support) {
+                acc.cnt++;
+                if (A.stats) acc.hsum += nlg::record_hash(a, b, q - q0, nlg::KIND_WHOLE, 3, 0);
+            }
+        }
+        if (A.outer_support && q1 > q0) {   // one record per pair: the support is all of T_a
+            acc.cnt++;
+            if (A.stats) acc.hsum += nlg::record_hash(a, b, 0, nlg::KIND_WHOLE, 3, 0);
         }
         write_pair<T>(A, e, q1 > q0, v, acc);
     }
@@ -981,6 +989,128 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
     }
 }
 
+// Boundary candidates of the outer-support barycenter balls (Sec. 6.2, barycenter case; the
+// experiment of Table 3).  One lane per candidate T_b: the inner integral is over the whole T_b
+// (the same sums for every outer point of the constant kernel), and the outer integrand lives on
+// S = T_a n B_delta(bary_b), built by the disc walk of T_a around bary_b (nocaps / approxcaps;
+// certified FP32 walk, else the FP64 walk), fanned from its first point; the outer rule runs on
+// every subtriangle with phi_a taken at each outer point.  One record per pair with a non-empty S.
+template <int BALL, typename T>
+__device__ __forceinline__ void support_boundary(const NumArgs &A, int a, int lane, LaneAcc &acc)
+{
+    constexpr int DISC = (BALL == NL_BALL_BARY_NOCAPS) ? NL_BALL_NOCAPS : NL_BALL_APPROXCAPS;
+    const int K = A.K;
+    const D2 ba = {A.bx[a], A.by[a]};
+    D2 Va[3];
+    for (int i = 0; i < 3; i++) { Va[i].x = A.tx[i * K + a]; Va[i].y = A.ty[i * K + a]; }
+    nlg::F2 va[3];   // T_a relative to bary_a
+    for (int i = 0; i < 3; i++) { va[i].x = (float)(Va[i].x - ba.x); va[i].y = (float)(Va[i].y - ba.y); }
+    const float f1x = va[1].x - va[0].x, f1y = va[1].y - va[0].y, f2x = va[2].x - va[0].x, f2y = va[2].y - va[0].y;
+    const float finv = 1.f / (f1x * f2y - f2x * f1y);
+    const BaryMap bma = bary_map(Va);
+    const int64_t es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
+    for (int64_t e = es + lane; e < e1; e += 32) {
+        const int b = A.nbr_idx[e];
+        D2 Vb[3];
+        for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
+        const D2 bb = {A.bx[b], A.by[b]};
+        int q0, q1;
+        rule_range(A, ba, bb, q0, q1);
+        Sums<T> S;
+        int64_t nq_in = 0;
+        whole_sums<T>(A, Vb, (T)(A.area[b] * A.kc), bb, S, nq_in);
+        T v[21];
+        for (int i = 0; i < 21; i++) v[i] = 0;
+        int kind = nlg::KIND_NONE, nv = 0;
+        int64_t nout = 0;
+        bool done = false;
+        if (sizeof(T) == sizeof(float)) {
+            const float cbx = (float)(bb.x - ba.x), cby = (float)(bb.y - ba.y);
+            nlg::F2 d[3];   // T_a relative to bary_b
+            for (int i = 0; i < 3; i++) { d[i].x = va[i].x - cbx; d[i].y = va[i].y - cby; }
+            nlg::F2 P[nlg::kBallCap];
+            int k = nlg::KIND_PARTIAL;
+            const int n = nlg::ball_region_f32<DISC>(d, A.geo, P, &k);
+            if (n >= 0) {
+                done = true;
+                if (n >= 3) {
+                    kind = k;
+                    nv = n;
+                    for (int t = 1; t + 1 < n; t++) {
+                        const nlg::F2 s0 = P[0], s1 = P[t], s2 = P[t + 1];
+                        const float ar = 0.5f * fabsf((s1.x - s0.x) * (s2.y - s0.y) - (s2.x - s0.x) * (s1.y - s0.y));
+                        for (int q = q0; q < q1; q++) {
+                            const float4 f = A.fout[q];
+                            // the outer point relative to bary_a, and phi_a there
+                            const float xr = f.x * s0.x + f.y * s1.x + f.z * s2.x + cbx - va[0].x;
+                            const float yr = f.x * s0.y + f.y * s1.y + f.z * s2.y + cby - va[0].y;
+                            const float l1 = (xr * f2y - f2x * yr) * finv, l2 = (f1x * yr - xr * f1y) * finv;
+                            OuterPt o;
+                            o.Wf = f.w * ar;
+                            o.l0f = 1.f - l1 - l2;
+                            o.l1f = l1;
+                            o.l2f = l2;
+                            combine<T>(o, S, v);
+                            nout++;
+                        }
+                    }
+                }
+            }
+        }
+        if (!done) {
+            nlg::Region R;
+            const nlg::F2 dl_unused[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            nlg::make_region<DISC>(Va, dl_unused, bb, bb, A.geo, R);
+            if (R.overflow) atomicOr(A.err, 1);
+            if (R.kind != nlg::KIND_NONE && R.nv >= 3) {
+                kind = R.kind;
+                nv = R.nv;
+                for (int t = 1; t + 1 < R.nv; t++) {
+                    const D2 s0 = R.P[0], s1 = R.P[t], s2 = R.P[t + 1];
+                    const double ar = 0.5 * fabs((s1.x - s0.x) * (s2.y - s0.y) - (s2.x - s0.x) * (s1.y - s0.y));
+                    for (int q = q0; q < q1; q++) {
+                        const double l0 = A.outer.l[q][0], l1 = A.outer.l[q][1], l2 = A.outer.l[q][2];
+                        const double x = l0 * s0.x + l1 * s1.x + l2 * s2.x, y = l0 * s0.y + l1 * s1.y + l2 * s2.y;
+                        double phi[3];
+                        bary_of(bma, x, y, phi);
+                        OuterPt o;
+                        o.W = A.outer.w[q] * ar;
+                        o.l0 = phi[0];
+                        o.l1 = phi[1];
+                        o.l2 = phi[2];
+                        o.Wf = (float)o.W;
+                        o.l0f = (float)phi[0];
+                        o.l1f = (float)phi[1];
+                        o.l2f = (float)phi[2];
+                        combine<T>(o, S, v);
+                        nout++;
+                    }
+                }
+            }
+        }
+        write_pair<T>(A, e, nout > 0, v, acc);
+        if (nout > 0) {
+            acc.cnt++;
+            acc.qp += nout * nq_in;
+            if (A.stats) acc.hsum += nlg::record_hash(a, b, 0, kind, nv, 0);
+        }
+    }
+}
+
+// boundary candidates of outer triangle a for the ball mode BALL
+template <int BALL, typename T, bool INV>
+__device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundaryShared<T> &sh, int lane, LaneAcc &acc)
+{
+    if constexpr (BALL == NL_BALL_BARY_NOCAPS || BALL == NL_BALL_BARY_APPROXCAPS) {
+        (void)sh;
+        support_boundary<BALL, T>(A, a, lane, acc);
+    } else {
+        stage_outer(A, a, sh.sq, lane);
+        __syncwarp();
+        boundary_outer<BALL, T, INV>(A, a, sh, lane, acc);
+    }
+}
+
 template <int BALL, typename T, bool INV>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs A)
 {
@@ -989,11 +1119,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs 
     const int lane = threadIdx.x & 31;
     const int a = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     if (a >= A.K) return;
-    stage_outer(A, a, sh.sq, lane);
-    __syncwarp();
     LaneAcc acc;
     acc_zero(acc);
-    boundary_outer<BALL, T, INV>(A, a, sh, lane, acc);
+    boundary_any<BALL, T, INV>(A, a, sh, lane, acc);
     // k_interior has written this triangle's values; add in stream order (deterministic)
     finish_outer(A, a, acc, lane, true);
 }
@@ -1069,11 +1197,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         }
 #endif
         for (int a = w.a0; a < w.a1; a++) {
-            stage_outer(A, a, sh.sq, lane);
-            __syncwarp();
             LaneAcc acc;
             acc_zero(acc);
-            boundary_outer<BALL, T, INV>(A, a, sh, lane, acc);
+            boundary_any<BALL, T, INV>(A, a, sh, lane, acc);
             finish_outer(A, a, acc, lane, true);
             __syncwarp();
         }

@@ -43,6 +43,10 @@ nl_status boundary_ball(nl_ctx *ctx, int ball, const nlq::NumArgs *dA, const nlq
     case NL_BALL_NGON: return boundary<NL_BALL_NGON, INV>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
     case NL_BALL_OVERLAP:
         return boundary<NL_BALL_OVERLAP, INV>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
+    case NL_BALL_BARY_NOCAPS:
+        return boundary<NL_BALL_BARY_NOCAPS, false>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
+    case NL_BALL_BARY_APPROXCAPS:
+        return boundary<NL_BALL_BARY_APPROXCAPS, false>(ctx, dA, items, n_items, counter, blocks, set_attr, per_sm);
     default: return nl_fail(ctx, NL_EINVAL, "unknown ball mode");
     }
 }

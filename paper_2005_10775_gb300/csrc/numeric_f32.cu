@@ -36,6 +36,8 @@ nl_status nl_launch_numeric_f32(nl_ctx *ctx, const nlq::NumArgs &A, int ball)
     case NL_BALL_EXACTCAPS: s = launch_boundary<NL_BALL_EXACTCAPS>(ctx, A, grid, threads); break;
     case NL_BALL_NGON: s = launch_boundary<NL_BALL_NGON>(ctx, A, grid, threads); break;
     case NL_BALL_OVERLAP: s = launch_boundary<NL_BALL_OVERLAP>(ctx, A, grid, threads); break;
+    case NL_BALL_BARY_NOCAPS: s = launch_boundary_k<NL_BALL_BARY_NOCAPS, false>(ctx, A, grid, threads); break;
+    case NL_BALL_BARY_APPROXCAPS: s = launch_boundary_k<NL_BALL_BARY_APPROXCAPS, false>(ctx, A, grid, threads); break;
     default: return nl_fail(ctx, NL_EINVAL, "unknown ball mode");
     }
     if (s != NL_OK) return s;

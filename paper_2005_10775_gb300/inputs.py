@@ -53,7 +53,7 @@ def split_square_mesh(lo: float, hi: float, n: int, jitter: float = 0.0,
     """Uniform n x n split-square grid over (lo, hi)^2.
 
     jitter: amplitude as a fraction of h (0.2 -> U[-0.2h, 0.2h]).
-    warp_y_square: apply (x1, x2) -> (x1, x2^2) to vertices inside Omega
+    warp_y_square: apply (x1, x2) -> (x1, x2^2) to the grid rows inside 0 < x2 < 1
     (grid (b) of Sec. 8, Fig. 12b).
     """
     h = (hi - lo) / n
@@ -80,8 +80,11 @@ def split_square_mesh(lo: float, hi: float, n: int, jitter: float = 0.0,
         x = np.where(fix_x, x, x + dx)
         y = np.where(fix_y, y, y + dy)
     if warp_y_square:
-        inside = (x > o0 + tol) & (x < o1 - tol) & (y > o0 + tol) & (y < o1 - tol)
-        y = np.where(inside, y * y, y)
+        # grid (b) of Sec. 8: x2 -> x2^2 on every grid row strictly between the lines x2 = 0 and
+        # x2 = 1 (the layer columns too, so the grid stays a tensor product; the printed h_min and
+        # h_max of Table 4(b) are those of this grid)
+        rows = (y > o0 + tol) & (y < o1 - tol)
+        y = np.where(rows, y * y, y)
     vid = lambda i, j: j * (n + 1) + i  # noqa: E731
     ci, cj = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
     ci = ci.ravel()
@@ -229,10 +232,11 @@ def batch_problems(count: int = 64, seed: int = 1077600, kmin: int = 2000, kmax:
     return out
 
 
-def paper_grid(h: float) -> Mesh:
-    """Uniform grid of Sec. 8 / Table 1: (-0.1, 1.1)^2 with cell size h (delta = 0.1)."""
+def paper_grid(h: float, warped: bool = False) -> Mesh:
+    """Uniform grid (a) of Sec. 8 / Table 1: (-0.1, 1.1)^2 with cell size h (delta = 0.1); with
+    warped=True the nonuniform grid (b) of Table 4, x2 -> x2^2 on the rows inside (0, 1)."""
     n = int(round(1.2 / h))
-    return split_square_mesh(-0.1, 1.1, n)
+    return split_square_mesh(-0.1, 1.1, n, warp_y_square=warped)
 
 
 def manufactured_u(x, y):

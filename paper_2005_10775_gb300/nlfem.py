@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libnlfem.so")
 
 NL_OK, NL_EINVAL, NL_ENOMEM, NL_ECUDA, NL_EGEOM, NL_ETIMEOUT, NL_ENOCONV, NL_EUNSUPPORTED = range(8)
-BALL = {"barycenter": 0, "nocaps": 1, "approxcaps": 2, "exactcaps": 3, "ngon": 4, "overlap": 5}
+BALL = {"barycenter": 0, "nocaps": 1, "approxcaps": 2, "exactcaps": 3, "ngon": 4, "overlap": 5,
+        "bary_nocaps": 6, "bary_approxcaps": 7}
 RULE = {"gauss3": 0, "gauss4": 1, "paper7": 2, "dunavant7": 3, "dunavant16": 4, "switch47": 5}
 KERNEL = {"const": 0, "inv_dist": 1}
 PREC = {"fp64": 0, "fp32c": 1}

@@ -38,6 +38,7 @@ def mixed_batch():
         (0.1, 26, 0.2, "barycenter", "const", "fp32c"),
         (0.2, 17, 0.2, "ngon", "inv_dist", "fp32c"),
         (0.15, 20, 0.2, "nocaps", "inv_dist", "fp64"),
+        (0.2, 15, 0.2, "bary_approxcaps", "const", "fp32c"),
     ]
     for i, (d, n, jit, ball, kernel, prec) in enumerate(specs):
         m = I.split_square_mesh(-d, 1 + d, n, jitter=jit, seed=1077700 + i if jit else None)
@@ -115,7 +116,7 @@ def test_batch_graph_replay_reproduces_values(nl, ctx, mixed):
 def test_batch_schedule_info_and_cache(nl, ctx, mixed):
     info = nl.nl_batch_get_info(mixed["h"])
     assert info["source"] in ("tuned", "cached")
-    assert info["launches"] == 8 and info["blocks"] > 0
+    assert info["launches"] == 9 and info["blocks"] > 0
     assert info["chunk"] in (1, 2, 4, 8) and info["order"] in (0, 1)
     # the same batch shape again: the schedule comes from the context's cache
     h2, outs2 = nl.nl_batch_create(ctx, mixed["meshes"], mixed["cfgs"])

@@ -81,6 +81,7 @@ def small_problem(ball, n=24, jitter=0.2, kernel="const", **kw):
 CASES = [
     ("barycenter", {}), ("nocaps", {}), ("approxcaps", {}), ("approxcaps", {"cap_m": 4}),
     ("exactcaps", {}), ("ngon", {}), ("overlap", {}),
+    ("bary_nocaps", {}), ("bary_approxcaps", {}),
 ]
 
 

@@ -149,3 +149,27 @@ def test_paper_table2_shifted_nocaps_on_gpu(nl, ctx):
     U[m.node_in_omega.astype(bool)] = x
     assert O.l2_error_omega(m, U, I.manufactured_u) == pytest.approx(6.89e-3, rel=0.15)
 
+
+@pytest.mark.parametrize("ball,ref", [("bary_nocaps", 7.47e-3), ("bary_approxcaps", 9.68e-3)])
+def test_paper_table3_on_gpu(nl, ctx, ball, ref):
+    # Table 3, columns (7) and (8): barycenter ball with the outer integral over its support,
+    # 4-point outer (on T_a or each support subtriangle) and 3-point inner rules, h = 0.05
+    d, h = 0.1, 0.05
+    m = I.paper_grid(h)
+    p = I.Problem("paper", m, d, "const", I.const_kernel_c(d), ball, "gauss4", "gauss3", cap_m=2)
+    keep = nl._Keep()
+    mesh = nl.make_mesh(m, keep)
+    D = nl.nl_assemble(ctx, mesh, nl.config_of(p, keep, prec="fp32c"))
+    A, B = nl.nl_extract(ctx, D, mesh)
+    try:
+        u = I.manufactured_u(m.vx, m.vy)
+        F = nl.nl_rhs(ctx, B, mesh, I.manufactured_f(m.vx, m.vy), u)
+        x = np.zeros(A.n)
+        nl.nl_cg(ctx, A, F, x, rtol=1e-10, max_it=20000)
+    finally:
+        for z in (D, A, B):
+            nl.nl_csr_free(ctx, z)
+    U = u.copy()
+    U[m.node_in_omega.astype(bool)] = x
+    assert O.l2_error_omega(m, U, I.manufactured_u) == pytest.approx(ref, rel=0.05)
+

@@ -354,6 +354,10 @@ BALLS = ["barycenter", "nocaps", "approxcaps", "exactcaps", "ngon", "overlap"]
 @pytest.mark.parametrize("kernel", ["const", "inv_dist"])
 def test_matrix_symmetric_zero_row_sums_psd(ball, kernel):
     m, cfg = _small(ball, kernel)
+    _structure(m, cfg)
+
+
+def _structure(m, cfg):
     out = O.assemble(m, cfg)
     D = O.to_csr(out).toarray()
     scale = np.abs(D).sum(axis=1)
@@ -361,6 +365,13 @@ def test_matrix_symmetric_zero_row_sums_psd(ball, kernel):
     assert np.all(np.abs(D.sum(axis=1)) <= 1e-14 * scale)
     ev = np.linalg.eigvalsh(D)
     assert ev.min() > -1e-12 * ev.max()
+
+
+@pytest.mark.parametrize("ball", ["bary_nocaps", "bary_approxcaps"])
+def test_outer_support_matrix_structure(ball):
+    m, cfg = _small("barycenter", "const")
+    cfg = dict(cfg, ball=ball, cap_m=2)
+    _structure(m, cfg)
 
 
 @pytest.mark.parametrize("ball", ["barycenter", "nocaps", "approxcaps", "exactcaps", "ngon", "overlap"])
@@ -526,6 +537,62 @@ def test_shifted_ball_is_the_centred_ball_of_bary_a():
     for r in out["rec"]:
         recs.setdefault((int(r["a"]), int(r["b"])), set()).add((int(r["kind"]), int(r["nverts"])))
     assert all(len(v) == 1 for v in recs.values())
+
+
+def _golden(name):
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            rows[(f[0], float(f[1]))] = float(f[2])
+    return rows
+
+
+def _composite_l2(ball, h, warped=False):
+    # Table 3 / 4: barycenter ball with the outer integral over T_a n B_delta(bary_b)
+    d = 0.1
+    m = I.paper_grid(h, warped=warped)
+    u = I.manufactured_u(m.vx, m.vy)
+    f = I.manufactured_f(m.vx, m.vy)
+    cfg = dict(delta=d, ball=ball, outer="gauss4", inner="gauss3", kernel_c=I.const_kernel_c(d))
+    U = O.solve(O.to_csr(O.assemble(m, cfg)), m, f, u)
+    return O.l2_error_omega(m, U, I.manufactured_u)
+
+
+@pytest.mark.parametrize("ball", ["bary_nocaps", "bary_approxcaps"])
+@pytest.mark.parametrize("h,tol", [(0.1, 0.15), (0.05, 0.05), (0.025, 0.05)])
+def test_paper_table3_barycenter_outer_support(ball, h, tol):
+    assert _composite_l2(ball, h) == pytest.approx(_golden("paper_table3.txt")[(ball, h)], rel=tol)
+
+
+@pytest.mark.parametrize("ball", ["bary_nocaps", "bary_approxcaps"])
+def test_paper_table4b_rates_on_the_nonuniform_grid(ball):
+    # grid (b): the printed h_min / h_max are those of the warped grid; second-order rates as printed
+    m = I.paper_grid(0.1, warped=True)
+    v = np.stack([m.vx, m.vy], 1)[m.tri]
+    diam = np.max([np.linalg.norm(v[:, (i + 1) % 3] - v[:, i], axis=1) for i in range(3)], axis=0)
+    assert round(float(diam.min()), 3) == 0.1 and round(float(diam.max()), 4) == 0.2147
+    e1, e2 = _composite_l2(ball, 0.05, warped=True), _composite_l2(ball, 0.025, warped=True)
+    printed = _golden("paper_table4b.txt")
+    assert 1.6 < math.log2(e1 / e2) < 2.4
+    assert math.log2(printed[(ball, 0.05)] / printed[(ball, 0.025)]) > 1.8
+    assert 0.3 < e2 / printed[(ball, 0.025)] < 3.0
+
+
+@pytest.mark.parametrize("ball", ["nocaps", "approxcaps"])
+def test_shifted_ball_equals_barycenter_outer_support(ball):
+    # For the constant kernel the integrand (phi(x) - phi(y))(phi'(x) - phi'(y)) psi has degree <= 2
+    # in x and in y, so rules of degree >= 2 integrate it exactly: pair (b, a) of the outer-support
+    # composite and pair (a, b) of the shifted ball integrate the same product set
+    # T_a x (T_b n B_delta(bary_a)), and the two assembled matrices agree to rounding.
+    d = 0.1
+    m = I.split_square_mesh(-0.1, 1.1, 16, jitter=0.2, seed=5)
+    base = dict(delta=d, outer="gauss4", inner="gauss3", kernel_c=I.const_kernel_c(d))
+    A = O.to_csr(O.assemble(m, dict(base, ball=ball, shifted=1)))
+    B = O.to_csr(O.assemble(m, dict(base, ball="bary_" + ball)))
+    assert A.nnz == B.nnz
+    assert abs(A - B).max() <= 1e-13 * abs(A).max()
 
 
 def test_singular_kernel_second_order_convergence():
