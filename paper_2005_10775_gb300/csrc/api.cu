@@ -197,6 +197,8 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
         A.outer.nsplit = A.outer.n;
     }
     if (!fill_rule(c.inner, &A.inner)) return nl_fail(ctx, NL_EINVAL, "bad inner rule");
+    if (A.outer.n > NL_MAXQ || A.inner.n > NL_MAXQ)
+        return nl_fail(ctx, NL_EUNSUPPORTED, "rules of more than NL_MAXQ points");   // the kernels' stage sizes
     A.inner.nsplit = A.inner.n;
     A.duffy_n = c.kernel == NL_KERNEL_INV_DIST ? c.duffy_n : 1;
     gauss_legendre01(A.duffy_n, A.gl_x, A.gl_w);

@@ -422,7 +422,7 @@ __device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBu
 // with FP32 vertices dl relative to x: the same signed apex-x decomposition, Duffy collapse
 // and sinh substitution.  Its discrete choices are taken in FP64 (near_edge64) whenever
 // FP32 is within 1e-4 of a threshold, so the evaluated points are those of the FP64 rule.
-__device__ __forceinline__ void near_whole_f32(const NumArgs &A, const nlg::F2 dl[3], const D2 V[3], D2 x,
+__device__ __forceinline__ void near_whole_f32(const NumArgs &A, const nlg::F2 dl[3], int tb, D2 x,
                                                const nlg::F2 &e1, const nlg::F2 &e2, float inv_det,
                                                Sums<float> &S, int64_t &nqp)
 {
@@ -450,7 +450,10 @@ __device__ __forceinline__ void near_whole_f32(const NumArgs &A, const nlg::F2 d
         bool skip_edge = false, skipA = false, skipB = false;
         int npA, npB;
         if (!(d >= th) || !(fabsf(tA) >= th) || !(fabsf(tB) >= th) || near_int(UA, tA) || near_int(UB, tB)) {
-            const NearEdge64 q = near_edge64(V[i], V[(i + 1) % 3], x);
+            // the FP64 vertices of T_b (edge i) from global memory
+            const int i1 = (i + 1) % 3;
+            const D2 Vi = {A.tx[i * A.K + tb], A.ty[i * A.K + tb]}, Vj = {A.tx[i1 * A.K + tb], A.ty[i1 * A.K + tb]};
+            const NearEdge64 q = near_edge64(Vi, Vj, x);
             skip_edge = (q.d == 0.0);
             skipA = (q.tA == 0.0);
             skipB = (q.tB == 0.0);
@@ -694,14 +697,37 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_interior(const NumArgs 
 // queue that all 32 lanes then drain together (geometry + quadrature), adding their
 // blocks into the owner lane's shared accumulators.
 // ---------------------------------------------------------------------------
+// FP32 data of a candidate T_b (64 bytes a lane, in shared memory); the rare FP64 paths
+// read T_b's FP64 vertices, barycentre and area from global memory (cand_fp64).
 struct CandData {
-    double vx[3], vy[3];
-    double bbx, bby, area, akc;    // area and area * kernel constant
     float vlx[3], vly[3];      // T_b relative to bary_a
     float blx, bly;            // bary_b relative to bary_a
     float e1x, e1y, e2x, e2y, binv;
+    float akcf;                // |T_b| times the kernel constant
     int b, q0;
 };
+
+struct CandFp64 {
+    D2 V[3], bb;
+    double area;
+};
+
+__device__ __forceinline__ CandFp64 cand_fp64(const NumArgs &A, int b)
+{
+    CandFp64 c;
+    for (int i = 0; i < 3; i++) { c.V[i].x = A.tx[i * A.K + b]; c.V[i].y = A.ty[i * A.K + b]; }
+    c.bb.x = A.bx[b];
+    c.bb.y = A.by[b];
+    c.area = A.area[b];
+    return c;
+}
+
+// |T_b| kc in the quadrature type
+template <typename T>
+__device__ __forceinline__ T cand_akc(const NumArgs &A, const CandData &c)
+{
+    return sizeof(T) == sizeof(float) ? (T)c.akcf : (T)(A.area[c.b] * A.kc);
+}
 
 // longest edge of T_b in FP32 (the near field of the singular kernel)
 __device__ __forceinline__ float cand_diam(const CandData &c)
@@ -710,19 +736,21 @@ __device__ __forceinline__ float cand_diam(const CandData &c)
     return sqrtf(fmaxf(fmaxf(c.e1x * c.e1x + c.e1y * c.e1y, c.e2x * c.e2x + c.e2y * c.e2y), e3x * e3x + e3y * e3y));
 }
 
+// Per-warp shared memory of the boundary kernel, sized for outer rules of at most NL_MAXQ
+// points (14.2 KB with float sums: four 4-warp blocks fit an SM).
 template <typename T>
 struct BoundaryShared {
-    OuterPt sq[NL_MAXQ + 8];
+    OuterPt sq[NL_MAXQ];
     CandData cand[32];
     T acc[32][22];             // 21 block values and the non-empty flag of each lane's pair
-    unsigned short queue[32 * (NL_MAXQ + 8)];    // undecided items (owner lane << 8 | q)
+    unsigned short queue[32 * NL_MAXQ];    // undecided items (owner lane << 8 | q)
     // whole items from the front; whole items in the singular kernel's near field from the back
     // (a batch holds at most 32 x n_q items in all)
-    unsigned short wqueue[32 * (NL_MAXQ + 8)];
+    unsigned short wqueue[32 * NL_MAXQ];
     nlg::ClipBuf clip;         // per-lane FP32 clip buffers
 };
 
-constexpr int kQueueCap = 32 * (NL_MAXQ + 8);
+constexpr int kQueueCap = 32 * NL_MAXQ;
 
 template <int BALL, typename T>
 __device__ __forceinline__ int classify_item(const NumArgs &A, const CandData &c, const OuterPt &o, nlg::F2 dl[3])
@@ -769,8 +797,8 @@ __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, 
             nv = n;
             ncap = 0;
             if (!cut) {
-                const D2 Vb[3] = {{c.vx[0], c.vy[0]}, {c.vx[1], c.vy[1]}, {c.vx[2], c.vy[2]}};
-                whole_sums<T>(A, Vb, (T)c.akc, D2{o.x, o.y}, S, nq, dl);
+                const D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};   // unused: FP32 coordinates dl
+                whole_sums<T>(A, Vb, cand_akc<T>(A, c), D2{o.x, o.y}, S, nq, dl);
             } else {
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
                 poly_sums_sh(A, cb, which, lane, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
@@ -793,8 +821,8 @@ __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, 
             nv = n;
             ncap = 0;
             if (k == nlg::KIND_WHOLE) {
-                const D2 Vb[3] = {{c.vx[0], c.vy[0]}, {c.vx[1], c.vy[1]}, {c.vx[2], c.vy[2]}};
-                whole_sums<T>(A, Vb, (T)c.akc, D2{o.x, o.y}, S, nq, dl);
+                const D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};   // unused: FP32 coordinates dl
+                whole_sums<T>(A, Vb, cand_akc<T>(A, c), D2{o.x, o.y}, S, nq, dl);
             } else {
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
                 poly_sums_f32(A, P, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
@@ -813,21 +841,21 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
 {
     nlg::F2 dl[3];
     for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
-    const D2 Vb[3] = {{c.vx[0], c.vy[0]}, {c.vx[1], c.vy[1]}, {c.vx[2], c.vy[2]}};
+    const CandFp64 c64 = cand_fp64(A, c.b);
+    const D2 *Vb = c64.V;
     const D2 x = {o.x, o.y};
     kind = nlg::KIND_WHOLE;
     nv = 3;
     ncap = 0;
     nlg::Region R;
-    const D2 bb = {c.bbx, c.bby};
-    nlg::make_region<BALL>(Vb, dl, bb, x, A.geo, R);
+    nlg::make_region<BALL>(Vb, dl, c64.bb, x, A.geo, R);
     if (R.overflow) atomicOr(A.err, 1);
     if (R.kind == nlg::KIND_NONE) return false;
     kind = R.kind;
     nv = R.nv;
     ncap = R.ncap;
     if (R.kind == nlg::KIND_WHOLE && R.ncap == 0 && A.kernel != NL_KERNEL_INV_DIST) {
-        whole_sums<T>(A, Vb, (T)c.akc, x, S, nq);
+        whole_sums<T>(A, Vb, (T)(c64.area * A.kc), x, S, nq);
     } else if (sizeof(T) == sizeof(float) && R.ncap == 0 && R.nv <= nlg::kClipCap &&
                (A.kernel == NL_KERNEL_CONST || !nlg::is_near(R, Vb, x))) {
         // FP32 quadrature on the FP64 polygon (coordinates relative to x)
@@ -839,7 +867,7 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
         const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
         poly_sums_sh(A, cb, 0, lane, R.nv, d0, e1, e2, c.binv, *(Sums<float> *)&S, nq);
     } else {
-        inner_sums<T>(A, R, Vb, c.area, x, S, nq);
+        inner_sums<T>(A, R, Vb, c64.area, x, S, nq);
     }
     return true;
 }
@@ -869,18 +897,17 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             }
 #endif
             c.b = b;
-            for (int i = 0; i < 3; i++) { c.vx[i] = A.tx[i * K + b]; c.vy[i] = A.ty[i * K + b]; }
-            c.bbx = A.bx[b];
-            c.bby = A.by[b];
-            c.area = A.area[b];
-            c.akc = c.area * A.kc;
-            for (int i = 0; i < 3; i++) { c.vlx[i] = (float)(c.vx[i] - ba.x); c.vly[i] = (float)(c.vy[i] - ba.y); }
-            c.blx = (float)(c.bbx - ba.x);
-            c.bly = (float)(c.bby - ba.y);
-            c.e1x = (float)(c.vx[1] - c.vx[0]); c.e1y = (float)(c.vy[1] - c.vy[0]);
-            c.e2x = (float)(c.vx[2] - c.vx[0]); c.e2y = (float)(c.vy[2] - c.vy[0]);
+            double vx[3], vy[3];
+            for (int i = 0; i < 3; i++) { vx[i] = A.tx[i * K + b]; vy[i] = A.ty[i * K + b]; }
+            const D2 bb = {A.bx[b], A.by[b]};
+            c.akcf = (float)(A.area[b] * A.kc);
+            for (int i = 0; i < 3; i++) { c.vlx[i] = (float)(vx[i] - ba.x); c.vly[i] = (float)(vy[i] - ba.y); }
+            c.blx = (float)(bb.x - ba.x);
+            c.bly = (float)(bb.y - ba.y);
+            c.e1x = (float)(vx[1] - vx[0]); c.e1y = (float)(vy[1] - vy[0]);
+            c.e2x = (float)(vx[2] - vx[0]); c.e2y = (float)(vy[2] - vy[0]);
             c.binv = 1.f / (c.e1x * c.e2y - c.e2x * c.e1y);
-            rule_range(A, ba, D2{c.bbx, c.bby}, q0, q1);
+            rule_range(A, ba, bb, q0, q1);
             c.q0 = q0;
             sh.cand[lane] = c;
         }
@@ -921,13 +948,16 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             const int own = it >> 8, q = it & 0xff;
             const CandData &cd = sh.cand[own];
             const OuterPt o = sh.sq[q];
-            const D2 Vb[3] = {{cd.vx[0], cd.vy[0]}, {cd.vx[1], cd.vy[1]}, {cd.vx[2], cd.vy[2]}};
+            // FP64 vertices only where the FP64 quadrature of the singular kernel needs them
+            D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+            if (INV && sizeof(T) == sizeof(double))
+                for (int k = 0; k < 3; k++) { Vb[k].x = A.tx[k * K + cd.b]; Vb[k].y = A.ty[k * K + cd.b]; }
             Sums<T> S;
             int64_t nq = 0;
             nlg::F2 dl[3];
             if (INV)
                 for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
-            whole_sums<T>(A, Vb, (T)cd.akc, D2{o.x, o.y}, S, nq, INV ? dl : nullptr);
+            whole_sums<T>(A, Vb, cand_akc<T>(A, cd), D2{o.x, o.y}, S, nq, INV ? dl : nullptr);
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
@@ -943,13 +973,12 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             const int own = it >> 8, q = it & 0xff;
             const CandData &cd = sh.cand[own];
             const OuterPt o = sh.sq[q];
-            const D2 Vb[3] = {{cd.vx[0], cd.vy[0]}, {cd.vx[1], cd.vy[1]}, {cd.vx[2], cd.vy[2]}};
             nlg::F2 dl[3];
             for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
             Sums<T> S;
             int64_t nq = 0;
             const nlg::F2 e1 = {cd.e1x, cd.e1y}, e2 = {cd.e2x, cd.e2y};
-            near_whole_f32(A, dl, Vb, D2{o.x, o.y}, e1, e2, cd.binv, *(Sums<float> *)&S, nq);
+            near_whole_f32(A, dl, cd.b, D2{o.x, o.y}, e1, e2, cd.binv, *(Sums<float> *)&S, nq);
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
@@ -1111,8 +1140,14 @@ __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundarySh
     }
 }
 
+// resident 4-warp blocks per SM: four with float sums and the integrable kernel (registers
+// capped at 128, a few spills), three otherwise (the singular near path and the double
+// sums lose more to spills than they gain from the fourth block)
+template <typename T, bool INV>
+constexpr int kBoundaryBlocksPerSm = (sizeof(T) == sizeof(float) && !INV) ? 4 : 3;
+
 template <int BALL, typename T, bool INV>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_boundary(const NumArgs A)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, INV>) k_boundary(const NumArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BoundaryShared<T> &sh = ((BoundaryShared<T> *)smem_raw)[threadIdx.x >> 5];
@@ -1181,7 +1216,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 // boundary candidates of the problems with ball mode BALL (adds onto k_interior_batch's
 // values, as k_boundary adds onto k_interior's)
 template <int BALL, typename T, bool INV>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, INV>)
     k_boundary_batch(const NumArgs *__restrict__ As, const BatchItem *__restrict__ items, int n_items, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
