@@ -100,13 +100,13 @@ __device__ __forceinline__ uint64_t ngon_pass_mask(const F2 d[3], const GeoParam
     const float o1 = d[1].x * d[2].y - d[1].y * d[2].x;
     const float o2 = d[2].x * d[0].y - d[2].y * d[0].x;
     if (fminf(o0, fminf(o1, o2)) > -1e-3f * (fabsf(o0) + fabsf(o1) + fabsf(o2))) return full;  // x inside or close
-    float rmax = 0.f, t[3];
+    float r2max = 0.f, t[3];
     for (int i = 0; i < 3; i++) {
-        rmax = fmaxf(rmax, sqrtf(d[i].x * d[i].x + d[i].y * d[i].y));
+        r2max = fmaxf(r2max, d[i].x * d[i].x + d[i].y * d[i].y);
         t[i] = atan2_poly(d[i].y, d[i].x);
     }
-    if (rmax <= g.rin_tau) return 0ull;
-    const float cz = g.rin_tau / rmax;
+    if (r2max <= g.rin_tau * g.rin_tau) return 0ull;
+    const float cz = g.rin_tau * rsqrtf(r2max);   // its few-ulp error is far inside the slack
     const float alpha = atan2_poly(sqrtf(fmaxf(1.f - cz * cz, 0.f)), cz);   // acos(cz)
     // sort the three angles, take the arc complementary to the largest gap
     float a0 = t[0], a1 = t[1], a2 = t[2], tmp;
@@ -124,10 +124,16 @@ __device__ __forceinline__ uint64_t ngon_pass_mask(const F2 d[3], const GeoParam
     lo -= slack;
     hi += slack;
     if (hi - lo >= two_pi) return full;
-    const int k0 = (int)ceilf(lo / g.sector - 0.5f), k1 = (int)floorf(hi / g.sector - 0.5f);
-    uint64_t m = 0;
-    for (int k = k0; k <= k1; k++) m |= 1ull << (((k % N) + N) % N);
-    return m;
+    // passes k0..k1 (mod N) as a window of cnt bits rotated to k0 mod N
+    const float isec = __fdividef(1.f, g.sector);
+    const int k0 = (int)ceilf(lo * isec - 0.5f), k1 = (int)floorf(hi * isec - 0.5f);
+    const int cnt = k1 - k0 + 1;
+    if (cnt <= 0) return 0ull;
+    if (cnt >= N) return full;
+    int s = k0 % N;
+    if (s < 0) s += N;
+    const uint64_t w = (1ull << cnt) - 1ull;
+    return ((w << s) | (s ? (w >> (N - s)) : 0ull)) & full;
 }
 
 __device__ __forceinline__ bool in_ball(D2 p, D2 x, double d2)
