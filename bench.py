@@ -38,8 +38,7 @@ FLOP_PER_INTER = 48.0
 SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) of the numeric phase (k_interior + k_boundary) of one
 # assembly, from one ncu capture of the current kernels (profiles/k_boundary_<workload>.md)
-NCU_TRAFFIC = {"ngon32_96": (690.8e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_interior + k_boundary, "
-                                      "profiles/k_boundary_ngon32_96.md")}
+NCU_TRAFFIC = {}
 
 
 def parse():
@@ -503,7 +502,7 @@ def main():
             e1.synchronize()
             tot += e0.elapsed_time(e1)
             phase += nl.nl_last_timings(ctx)
-            stats = (out.n_pairs, out.n_qp_pairs, out.n_inter, out.nnz)
+            stats = (out.n_pairs, out.n_qp_pairs, out.n_inter, out.nnz, nl.nl_last_fp64_items(ctx))
             nl.nl_csr_free(ctx, out)
         launches = nl.nl_launch_count(ctx) - l0 - 0
         torch.cuda.synchronize()
@@ -517,7 +516,7 @@ def main():
     clocks.start()
     tot_ms, phase, stats, launches, wall = run(args.prec, args.steps, args.warmup)
     ck = clocks.stop()
-    n_pairs, n_qp, n_inter, nnz = stats
+    n_pairs, n_qp, n_inter, nnz, n_fp64 = stats
     ms_step = tot_ms / args.steps
     value = n_qp * world * args.steps / (tot_ms / 1e3)
 
@@ -573,6 +572,7 @@ def main():
                    "delta": p.delta, "outer": p.outer, "inner": p.inner, "kernel": p.kernel,
                    "parallelism": f"replica x{world}", "l2": "flushed (512 MB write) before every step",
                    "n_pairs": n_pairs, "n_qp_pairs": n_qp, "n_inter": n_inter, "nnz": nnz,
+                   "fp64_items": n_fp64,
                    "phase_ms": {"prepare": phase[0], "numeric": phase[1], "symbolic": phase[2],
                                 "scatter": phase[3]},
                    "wall_s_timed": wall},

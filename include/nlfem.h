@@ -263,6 +263,16 @@ nl_status nl_cg_noalloc(nl_ctx *ctx, const nl_csr *A, const double *b, double *x
 /* Number of CUDA kernels this context has launched so far (all entry points). */
 int64_t nl_launch_count(nl_ctx *ctx);
 
+/* Items (x_q, T_b) of the last nl_assemble or nl_interactions on the FP32-compensated
+   path whose region the FP64 geometry built: FP32 choices it could not certify, the
+   singular kernel's near field, balls without an FP32 region.  The boundary kernel
+   queues them and a second kernel integrates the queue with every lane busy; a full
+   queue (capacity E/16, at least 4096; NL_DEFER_CAP in the environment overrides it, 0
+   disables the queue) leaves the excess to the boundary kernel's own lanes.  Their
+   blocks are added with FP32 atomics, so FP32-path values may differ between runs in
+   the last bits.  0 for the FP64 path; -1 for a null context. */
+int64_t nl_last_fp64_items(nl_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -280,6 +280,10 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     A.hash_a = P->hash_a;
     A.stats = stats ? 1 : 0;
     A.err = P->err;
+    A.defer = nullptr;
+    A.defer_n = nullptr;
+    A.defer_cap = 0;
+    A.prob = 0;
     return NL_OK;
 }
 
@@ -308,6 +312,17 @@ nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats)
     nl_status s = nl_fill_args(ctx, P, A, stats);
     if (s != NL_OK) return s;
     if (P->cfg.prec == NL_PREC_FP64) return nl_launch_numeric_f64(ctx, A, P->cfg.ball);
+    if (!P->defer) {
+        const int cap = nl_defer_cap(P->E);
+        nlq::DeferItem *q = nullptr;
+        if ((s = nl_alloc(ctx, &q, (size_t)cap)) != NL_OK) return s;
+        P->defer = q;
+        if ((s = nl_alloc(ctx, &P->defer_n, 1)) != NL_OK) return s;
+        P->defer_cap = cap;
+    }
+    A.defer = (nlq::DeferItem *)P->defer;
+    A.defer_n = P->defer_n;
+    A.defer_cap = P->defer_cap;
     return nl_launch_numeric_f32(ctx, A, P->cfg.ball);
 }
 
@@ -320,7 +335,7 @@ void nl_plan_free(nl_plan *P, cudaStream_t s)
     nl_free(P->rad, s); nl_free(P->area, s); nl_free(P->ngon, s); nl_free(P->nbr_ptr, s); nl_free(P->nbr_idx, s);
     nl_free(P->nbr_split, s); nl_free(P->flag, s); nl_free(P->blk, s); nl_free(P->maa, s); nl_free(P->qp_a, s);
     nl_free(P->cnt_a, s); nl_free(P->hash_a, s); nl_free(P->lslot, s); nl_free(P->tslot, s); nl_free(P->W, s);
-    nl_free(P->val32, s); nl_free(P->err, s);
+    nl_free(P->val32, s); nl_free(P->err, s); nl_free(P->defer, s); nl_free(P->defer_n, s);
 }
 
 nl_status nl_host_slots(nl_ctx *ctx, int n, nl_host_slot **out)
@@ -406,6 +421,8 @@ void nl_destroy(nl_ctx *ctx)
 
 const char *nl_last_error(nl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+int64_t nl_last_fp64_items(nl_ctx *ctx) { return ctx ? ctx->last_fp64_items : -1; }
+
 nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_csr *out)
 {
     nl_status s = nl_validate(ctx, mesh, cfg);
@@ -438,8 +455,13 @@ nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl
     if ((e = cudaEventRecord(ctx->ev[1], ctx->stream)) != cudaSuccess) goto cuda_fail;
     if ((s = run_numeric(ctx, P, false)) != NL_OK) goto fail;
     if ((e = cudaEventRecord(ctx->ev[2], ctx->stream)) != cudaSuccess) goto cuda_fail;
+    h->deferred = 0;
+    if (P->defer_n &&
+        (e = cudaMemcpyAsync(&h->deferred, P->defer_n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+        goto cuda_fail;
     if ((s = nl_pattern_a(ctx, P, out, Q, h)) != NL_OK) goto fail;
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) goto cuda_fail;
+    ctx->last_fp64_items = h->deferred;
     if ((s = nl_prepare_check(ctx, h)) != NL_OK) goto fail;
     if ((s = nl_pattern_b(ctx, P, out, Q, h)) != NL_OK) goto fail;
     if ((e = cudaEventRecord(ctx->ev[3], ctx->stream)) != cudaSuccess) goto cuda_fail;
@@ -484,7 +506,11 @@ nl_status nl_interactions(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg
             e = cudaMemcpyAsync(count_a, P.cnt_a, sizeof(int64_t) * P.K, cudaMemcpyDeviceToHost, ctx->stream);
         if (qp_a && e == cudaSuccess)
             e = cudaMemcpyAsync(qp_a, P.qp_a, sizeof(int64_t) * P.K, cudaMemcpyDeviceToHost, ctx->stream);
+        int deferred = 0;
+        if (P.defer_n && e == cudaSuccess)
+            e = cudaMemcpyAsync(&deferred, P.defer_n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        ctx->last_fp64_items = deferred;
         if (e != cudaSuccess) s = nl_cuda_fail(ctx, e, "download of interaction statistics");
     }
     nl_plan_free(&P, ctx->stream);

@@ -53,7 +53,15 @@ struct Launch {                    // one persistent numeric launch
     nlq::BatchItem *items = nullptr;
     int n_items = 0, cap_items = 0;
     int blocks = 0;
+    nlq::DeferItem *defer = nullptr;   // float boundary launches: queue of the FP64-decided items
+    int defer_cap = 0;
 };
+
+// does a boundary launch of this value type and ball queue items for the deferred kernel?
+bool uses_queue(bool f64, int ball)
+{
+    return !f64 && ball >= 0 && ball != NL_BALL_BARY_NOCAPS && ball != NL_BALL_BARY_APPROXCAPS;
+}
 
 struct ScatterGroup {              // one scatter launch: problems of one value type
     bool f64 = false;
@@ -79,7 +87,7 @@ struct nl_batch {
     std::vector<nl_csr *> out;
     std::vector<PrecGroup> pgroups;
     std::vector<Launch> launches;
-    int *counters = nullptr;       // one per launch
+    int *counters = nullptr;       // two per launch: work items taken, deferred items queued
     std::vector<ScatterGroup> sgroups;
     std::vector<ScatterArgs> host_S_all;
     std::vector<int64_t> host_zoff;
@@ -115,7 +123,10 @@ void release(nl_batch *b, cudaStream_t s)
     b->exec = nullptr;
     b->graph = nullptr;
     for (PrecGroup &g : b->pgroups) free_async(g.dA, s);
-    for (Launch &l : b->launches) free_async(l.items, s);
+    for (Launch &l : b->launches) {
+        free_async(l.items, s);
+        free_async(l.defer, s);
+    }
     free_async(b->counters, s);
     for (ScatterGroup &g : b->sgroups) {
         free_async(g.dS, s);
@@ -205,8 +216,9 @@ nl_status build_items(nl_ctx *ctx, nl_batch *b, const Sched &sc)
 
 nl_status launch_numeric(nl_ctx *ctx, nl_batch *b, bool set_attr)
 {
-    NL_CK(cudaMemsetAsync(b->counters, 0, sizeof(int) * b->launches.size(), ctx->stream));
-    for (size_t k = 0; k < b->launches.size(); k++) {
+    const size_t nl = b->launches.size();
+    NL_CK(cudaMemsetAsync(b->counters, 0, sizeof(int) * 2 * nl, ctx->stream));
+    for (size_t k = 0; k < nl; k++) {
         const Launch &l = b->launches[k];
         if (!l.n_items) continue;
         const PrecGroup &g = b->pgroups[l.prec];
@@ -220,6 +232,8 @@ nl_status launch_numeric(nl_ctx *ctx, nl_batch *b, bool set_attr)
                                                      set_attr)
                       : nl_launch_boundary_batch_f32(ctx, l.ball, l.inv, g.dA, l.items, l.n_items, c, l.blocks,
                                                      set_attr);
+        if (s == NL_OK && l.defer)
+            s = nl_launch_deferred_batch_f32(ctx, l.ball, g.dA, l.defer, b->counters + nl + k, l.defer_cap);
         if (s != NL_OK) return s;
     }
     return NL_OK;
@@ -438,17 +452,38 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
         return fail(nl_fail(ctx, NL_ECUDA, "cudaDeviceGetAttribute"));
-    for (PrecGroup &g : b->pgroups) {
+    const size_t nlaunch = b->launches.size();
+    if ((s = nl_alloc(ctx, &b->counters, 2 * nlaunch)) != NL_OK) return fail(s);
+    // one deferred-item queue per float boundary launch, sized by its problems' candidate pairs
+    for (Launch &l : b->launches) {
+        if (!uses_queue(b->pgroups[l.prec].f64, l.ball)) continue;
+        int64_t E = 0;
+        for (int i : l.probs) E += b->P[i]->E;
+        l.defer_cap = nl_defer_cap(E);
+        if ((s = nl_alloc(ctx, &l.defer, (size_t)l.defer_cap)) != NL_OK) return fail(s);
+    }
+    for (int pg = 0; pg < (int)b->pgroups.size(); pg++) {
+        PrecGroup &g = b->pgroups[pg];
         std::vector<nlq::NumArgs> &args = g.host;
         args.resize(g.probs.size());
-        for (size_t k = 0; k < g.probs.size(); k++)
+        for (size_t k = 0; k < g.probs.size(); k++) {
             if ((s = nl_fill_args(ctx, b->P[g.probs[k]], args[k], false)) != NL_OK) return fail(s);
+            for (size_t j = 0; j < nlaunch; j++) {
+                const Launch &l = b->launches[j];
+                if (l.prec != pg || !l.defer ||
+                    std::find(l.probs.begin(), l.probs.end(), g.probs[k]) == l.probs.end())
+                    continue;
+                args[k].defer = l.defer;
+                args[k].defer_n = b->counters + nlaunch + j;
+                args[k].defer_cap = l.defer_cap;
+                args[k].prob = (int)k;
+            }
+        }
         if ((s = nl_alloc(ctx, &g.dA, args.size())) != NL_OK) return fail(s);
         if (cudaMemcpyAsync(g.dA, args.data(), sizeof(nlq::NumArgs) * args.size(), cudaMemcpyHostToDevice, st) !=
             cudaSuccess)
             return fail(nl_fail(ctx, NL_ECUDA, "upload of the kernel arguments"));
     }
-    if ((s = nl_alloc(ctx, &b->counters, b->launches.size())) != NL_OK) return fail(s);
     for (Launch &l : b->launches) {
         int per_sm = 0;
         s = b->pgroups[l.prec].f64 ? nl_batch_occupancy_f64(ctx, l.ball, l.inv, &per_sm)

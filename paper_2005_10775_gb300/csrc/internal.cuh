@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <stdlib.h>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,7 @@ struct nl_host_slot {
     int ovf;                      // cell-list or candidate-list overflow
     int row_ovf;                  // pattern row overflow
     int err;                      // numeric-phase error word
+    int deferred;                 // FP32 path: items the FP64 geometry decided
 };
 
 struct nl_ctx {
@@ -40,6 +42,7 @@ struct nl_ctx {
     nl_host_slot *slots = nullptr;  // pinned
     int nslots = 0;
     struct nl_tune_cache *tune = nullptr;   // batch schedules picked by the autotuner (batch.cu)
+    int64_t last_fp64_items = 0;  // nl_last_fp64_items
 };
 
 // pinned host slots for n problems (grown on demand; invalidates earlier slot pointers)
@@ -77,6 +80,11 @@ struct nl_plan {
     float *val32 = nullptr;       // FP32 copy of the values (nl_matvec / nl_cg), lazily built
     int32_t ncols = 0;            // column count of a rectangular result (nl_extract's B)
     int *err = nullptr;           // device error word of the numeric phase and the scatter
+    // FP32 path: queue of the items the FP64 geometry decides (nlq::DeferItem), allocated at
+    // the first numeric run, and its fill count
+    void *defer = nullptr;
+    int *defer_n = nullptr;
+    int defer_cap = 0;
     int64_t blk_elems() const { return 15 * E; }
 };
 
@@ -89,6 +97,23 @@ nl_status nl_cuda_fail(nl_ctx *ctx, cudaError_t e, const char *what);
         cudaError_t e_ = (call);                                          \
         if (e_ != cudaSuccess) return nl_cuda_fail(ctx, e_, #call);       \
     } while (0)
+
+// capacity of a deferred-item queue for E candidate pairs: the FP64 items are a small
+// fraction of the exact items (about 0.1 % on jittered meshes); a full queue only sends
+// the excess back to the boundary kernel's own lanes
+inline int nl_defer_cap(int64_t E)
+{
+    // NL_DEFER_CAP in the environment sets the capacity (0: no queue, every such item inline)
+    const char *v = getenv("NL_DEFER_CAP");
+    if (v && *v) {
+        const long long c = strtoll(v, nullptr, 10);
+        return c < 0 ? 0 : (int)(c > (1ll << 24) ? (1ll << 24) : c);
+    }
+    int64_t c = E / 16;
+    if (c < 4096) c = 4096;
+    if (c > (int64_t(1) << 24)) c = int64_t(1) << 24;
+    return (int)c;
+}
 
 // Device allocation from the device's stream-ordered pool, on the context's stream
 // (no device synchronisation); failures are reported as NL_ENOMEM.

@@ -30,6 +30,16 @@ struct RuleTab {
     double w[NL_MAXQ + 8];
 };
 
+// An undecided (q, b) item of the FP32 path whose region the FP64 geometry has to build
+// (an uncertified FP32 choice, the singular kernel's near field, a ball without an FP32
+// region).  The boundary kernel queues it instead of running the FP64 code in one lane of
+// an otherwise idle warp; k_deferred then integrates the queue with every lane busy.
+struct DeferItem {
+    int64_t e;     // candidate pair (T_a, T_b)
+    int32_t a;     // outer triangle T_a
+    int32_t qp;    // outer point q (bits 0-7) and problem index in a batched launch (bits 8-31)
+};
+
 struct NumArgs {
     int K;
     int64_t E;
@@ -58,6 +68,10 @@ struct NumArgs {
     uint64_t *hash_a;
     int stats;
     int *err;                         // device error word: bit 0 = region buffer bound hit
+    DeferItem *defer;                 // FP32 path: queue of the items the FP64 geometry decides (null: inline)
+    int *defer_n;                     // its fill count (zeroed before the boundary launch; may exceed the cap)
+    int defer_cap;
+    int prob;                         // index of this problem in a batched launch's argument array
 };
 
 template <typename T>
@@ -518,6 +532,31 @@ __device__ __forceinline__ void acc_zero(LaneAcc &acc)
     acc.hsum = 0;
 }
 
+// outer point q of T_a (vertices Va, area area_a)
+__device__ __forceinline__ OuterPt outer_point(const NumArgs &A, int a, const D2 Va[3], double area_a, int q)
+{
+    double l0 = A.outer.l[q][0], l1 = A.outer.l[q][1], l2 = A.outer.l[q][2];
+    OuterPt o;
+    // x_q = l0 v0 + l1 v1 + l2 v2, left to right, round-to-nearest
+    o.x = nlg::add(nlg::add(nlg::mul(l0, Va[0].x), nlg::mul(l1, Va[1].x)), nlg::mul(l2, Va[2].x));
+    o.y = nlg::add(nlg::add(nlg::mul(l0, Va[0].y), nlg::mul(l1, Va[1].y)), nlg::mul(l2, Va[2].y));
+    o.W = A.outer.w[q] * area_a;
+    o.l0 = l0; o.l1 = l1; o.l2 = l2;
+    o.lx = (float)(o.x - A.bx[a]);
+    o.ly = (float)(o.y - A.by[a]);
+    if (A.shifted) {
+        // shifted-centre ball (Sec. 4.3): the region is built around bary_a for every outer
+        // point; x_q keeps its weight and barycentrics (o.W, o.l*)
+        o.x = A.bx[a];
+        o.y = A.by[a];
+        o.lx = 0.f;
+        o.ly = 0.f;
+    }
+    o.Wf = (float)o.W;
+    o.l0f = (float)l0; o.l1f = (float)l1; o.l2f = (float)l2;
+    return o;
+}
+
 // outer points of T_a in shared memory (computed by the warp's lanes)
 __device__ __forceinline__ void stage_outer(const NumArgs &A, int a, OuterPt *sq, int lane)
 {
@@ -525,28 +564,7 @@ __device__ __forceinline__ void stage_outer(const NumArgs &A, int a, OuterPt *sq
     D2 Va[3];
     for (int i = 0; i < 3; i++) { Va[i].x = A.tx[i * K + a]; Va[i].y = A.ty[i * K + a]; }
     const double area_a = A.area[a];
-    for (int q = lane; q < A.outer.n; q += 32) {
-        double l0 = A.outer.l[q][0], l1 = A.outer.l[q][1], l2 = A.outer.l[q][2];
-        OuterPt o;
-        // x_q = l0 v0 + l1 v1 + l2 v2, left to right, round-to-nearest
-        o.x = nlg::add(nlg::add(nlg::mul(l0, Va[0].x), nlg::mul(l1, Va[1].x)), nlg::mul(l2, Va[2].x));
-        o.y = nlg::add(nlg::add(nlg::mul(l0, Va[0].y), nlg::mul(l1, Va[1].y)), nlg::mul(l2, Va[2].y));
-        o.W = A.outer.w[q] * area_a;
-        o.l0 = l0; o.l1 = l1; o.l2 = l2;
-        o.lx = (float)(o.x - A.bx[a]);
-        o.ly = (float)(o.y - A.by[a]);
-        if (A.shifted) {
-            // shifted-centre ball (Sec. 4.3): the region is built around bary_a for every outer
-            // point; x_q keeps its weight and barycentrics (o.W, o.l*)
-            o.x = A.bx[a];
-            o.y = A.by[a];
-            o.lx = 0.f;
-            o.ly = 0.f;
-        }
-        o.Wf = (float)o.W;
-        o.l0f = (float)l0; o.l1f = (float)l1; o.l2f = (float)l2;
-        sq[q] = o;
-    }
+    for (int q = lane; q < A.outer.n; q += 32) sq[q] = outer_point(A, a, Va, area_a, q);
     __syncwarp();
 }
 
@@ -712,6 +730,26 @@ struct CandFp64 {
     double area;
 };
 
+// FP32 data of candidate T_b relative to bary_a (ba) and the outer-rule range [c.q0, q1) of the pair
+__device__ __forceinline__ void load_cand(const NumArgs &A, int b, const D2 &ba, CandData &c, int &q1)
+{
+    const int K = A.K;
+    c.b = b;
+    double vx[3], vy[3];
+    for (int i = 0; i < 3; i++) { vx[i] = A.tx[i * K + b]; vy[i] = A.ty[i * K + b]; }
+    const D2 bb = {A.bx[b], A.by[b]};
+    c.akcf = (float)(A.area[b] * A.kc);
+    for (int i = 0; i < 3; i++) { c.vlx[i] = (float)(vx[i] - ba.x); c.vly[i] = (float)(vy[i] - ba.y); }
+    c.blx = (float)(bb.x - ba.x);
+    c.bly = (float)(bb.y - ba.y);
+    c.e1x = (float)(vx[1] - vx[0]); c.e1y = (float)(vy[1] - vy[0]);
+    c.e2x = (float)(vx[2] - vx[0]); c.e2y = (float)(vy[2] - vy[0]);
+    c.binv = 1.f / (c.e1x * c.e2y - c.e2x * c.e1y);
+    int q0;
+    rule_range(A, ba, bb, q0, q1);
+    c.q0 = q0;
+}
+
 __device__ __forceinline__ CandFp64 cand_fp64(const NumArgs &A, int b)
 {
     CandFp64 c;
@@ -776,9 +814,12 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
                                              int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb,
                                              int lane);
 
+// FP32 region and quadrature of one undecided (q, b): 1 done (S holds its sums), 0 empty
+// region, -1 the FP64 geometry decides (the singular kernel's near field, an uncertified
+// FP32 choice, FP64 sums or a ball without an FP32 region)
 template <int BALL, typename T>
-__device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
-                                           int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb, int lane)
+__device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
+                                              int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb, int lane)
 {
     if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON) {
         nlg::F2 dl[3];
@@ -786,13 +827,13 @@ __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, 
         // the singular kernel's near field needs the FP64 path; a region inside T_b is far
         // when T_b is (certified in FP32)
         if (A.kernel == NL_KERNEL_INV_DIST && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
-            return exact_item_fp64<BALL, T>(A, c, o, S, nq, kind, nv, ncap, cb, lane);
+            return -1;
         bool cut = false;
         int which = 0;
         const int n = nlg::clip_ngon_f32_sh(dl, A.geo.err0, A.geo, cb, lane, &which, &cut);
         if (n >= 0) {
             // certified FP32 clip: same vertex count and kind as the FP64 clip
-            if (n < 3) return false;
+            if (n < 3) return 0;
             kind = cut ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
             nv = n;
             ncap = 0;
@@ -803,20 +844,20 @@ __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, 
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
                 poly_sums_sh(A, cb, which, lane, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
             }
-            return true;
+            return 1;
         }
     }
     if (sizeof(T) == sizeof(float) && (BALL == NL_BALL_NOCAPS || BALL == NL_BALL_APPROXCAPS)) {
         nlg::F2 dl[3];
         for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
         if (A.kernel == NL_KERNEL_INV_DIST && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
-            return exact_item_fp64<BALL, T>(A, c, o, S, nq, kind, nv, ncap, cb, lane);
+            return -1;
         nlg::F2 P[nlg::kBallCap];
         int k = nlg::KIND_PARTIAL;
         const int n = nlg::ball_region_f32<BALL>(dl, A.geo, P, &k);
         if (n >= 0) {
             // certified FP32 walk: same vertex count and kind as the FP64 walk
-            if (n < 3) return false;
+            if (n < 3) return 0;
             kind = k;
             nv = n;
             ncap = 0;
@@ -827,10 +868,10 @@ __device__ __forceinline__ bool exact_item(const NumArgs &A, const CandData &c, 
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
                 poly_sums_f32(A, P, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
             }
-            return true;
+            return 1;
         }
     }
-    return exact_item_fp64<BALL, T>(A, c, o, S, nq, kind, nv, ncap, cb, lane);
+    return -1;
 }
 
 // undecided item through the FP64 geometry (the region exactly as FP64 builds it)
@@ -872,6 +913,18 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
     return true;
 }
 
+// Queue an item for k_deferred: false (the caller runs the FP64 code itself) for FP64 sums,
+// without a queue, or when the queue is full.
+template <typename T>
+__device__ __forceinline__ bool defer_item(const NumArgs &A, int64_t e, int a, int q)
+{
+    if (sizeof(T) != sizeof(float) || !A.defer) return false;
+    const int slot = atomicAdd(A.defer_n, 1);
+    if (slot >= A.defer_cap) return false;
+    A.defer[slot] = DeferItem{e, a, (A.prob << 8) | q};
+    return true;
+}
+
 // The boundary candidates of outer triangle a (outer points staged in sh.sq).
 // INV: the kernel is psi = c/|x - y| (near-field split), else the constant kernel.
 template <int BALL, typename T, bool INV>
@@ -896,19 +949,8 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
                 b = a;
             }
 #endif
-            c.b = b;
-            double vx[3], vy[3];
-            for (int i = 0; i < 3; i++) { vx[i] = A.tx[i * K + b]; vy[i] = A.ty[i * K + b]; }
-            const D2 bb = {A.bx[b], A.by[b]};
-            c.akcf = (float)(A.area[b] * A.kc);
-            for (int i = 0; i < 3; i++) { c.vlx[i] = (float)(vx[i] - ba.x); c.vly[i] = (float)(vy[i] - ba.y); }
-            c.blx = (float)(bb.x - ba.x);
-            c.bly = (float)(bb.y - ba.y);
-            c.e1x = (float)(vx[1] - vx[0]); c.e1y = (float)(vy[1] - vy[0]);
-            c.e2x = (float)(vx[2] - vx[0]); c.e2y = (float)(vy[2] - vy[0]);
-            c.binv = 1.f / (c.e1x * c.e2y - c.e2x * c.e1y);
-            rule_range(A, ba, bb, q0, q1);
-            c.q0 = q0;
+            load_cand(A, b, ba, c, q1);
+            q0 = c.q0;
             sh.cand[lane] = c;
         }
         for (int i = 0; i < 22; i++) sh.acc[lane][i] = 0;
@@ -997,7 +1039,12 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             Sums<T> S;
             int64_t nq = 0;
             int kind, nv, ncap;
-            if (!exact_item<BALL, T>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane)) continue;
+            int r = exact_item_f32<BALL, T>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane);
+            if (r < 0) {
+                if (defer_item<T>(A, base + own, a, q)) continue;
+                r = exact_item_fp64<BALL, T>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane) ? 1 : 0;
+            }
+            if (r == 0) continue;
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
@@ -1157,7 +1204,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, I
     LaneAcc acc;
     acc_zero(acc);
     boundary_any<BALL, T, INV>(A, a, sh, lane, acc);
-    // k_interior has written this triangle's values; add in stream order (deterministic)
+    // k_interior has written this triangle's values; add in stream order
     finish_outer(A, a, acc, lane, true);
 }
 
@@ -1241,6 +1288,70 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, I
     }
 }
 
+// ---------------------------------------------------------------------------
+// Deferred items of the FP32 path (after the boundary launch, in stream order): each
+// thread takes one queued (q, b), builds its region with the FP64 geometry, integrates it
+// in FP32 and adds its block onto the pair's stored values, M_aa and the statistics.
+// ---------------------------------------------------------------------------
+template <int BALL>
+__device__ __forceinline__ void deferred_item(const NumArgs &A, const DeferItem &d, nlg::ClipBuf &cb, int lane)
+{
+    const int K = A.K, a = d.a, q = d.qp & 0xff;
+    const int64_t e = d.e;
+#ifdef NL_CHECKS
+    if (a < 0 || a >= K || e < 0 || e >= A.E || q >= A.outer.n) {   // debug build: bad item (bit 64), skipped
+        atomicOr(A.err, 64);
+        return;
+    }
+#endif
+    const int b = A.nbr_idx[e];
+    D2 Va[3];
+    for (int i = 0; i < 3; i++) { Va[i].x = A.tx[i * K + a]; Va[i].y = A.ty[i * K + a]; }
+    const OuterPt o = outer_point(A, a, Va, A.area[a], q);
+    const D2 ba = {A.bx[a], A.by[a]};
+    CandData c;
+    int q1;
+    load_cand(A, b, ba, c, q1);
+    Sums<float> S;
+    int64_t nq = 0;
+    int kind, nv, ncap;
+    if (!exact_item_fp64<BALL, float>(A, c, o, S, nq, kind, nv, ncap, cb, lane)) return;
+    float w[21];
+    for (int k = 0; k < 21; k++) w[k] = 0.f;
+    combine<float>(o, S, w);
+    float *blk = (float *)A.blk;
+    for (int k = 0; k < 15; k++) atomicAdd(&blk[(int64_t)k * A.E + e], w[k]);
+    for (int k = 0; k < 6; k++) atomicAdd(&A.maa[(int64_t)k * K + a], (double)w[15 + k]);
+    A.flag[e] = 1;
+    atomicAdd((unsigned long long *)&A.qp_a[a], (unsigned long long)nq);
+    atomicAdd((unsigned long long *)&A.cnt_a[a], 1ull);
+    if (A.stats)
+        atomicAdd((unsigned long long *)&A.hash_a[a],
+                  (unsigned long long)nlg::record_hash(a, b, q - c.q0, kind, nv, ncap));
+}
+
+template <int BALL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_deferred(const NumArgs A)
+{
+    __shared__ nlg::ClipBuf cb[kWarpsPerBlock];
+    const int n = min(*A.defer_n, A.defer_cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        deferred_item<BALL>(A, A.defer[i], cb[threadIdx.x >> 5], threadIdx.x & 31);
+}
+
+// the queue of one batched boundary launch (items of its problems, As indexed by qp >> 8)
+template <int BALL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_deferred_batch(const NumArgs *__restrict__ As, const DeferItem *__restrict__ items, const int *count, int cap)
+{
+    __shared__ nlg::ClipBuf cb[kWarpsPerBlock];
+    const int n = min(*count, cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const DeferItem d = items[i];
+        deferred_item<BALL>(As[d.qp >> 8], d, cb[threadIdx.x >> 5], threadIdx.x & 31);
+    }
+}
+
 }  // namespace nlq
 
 // ---------------------------------------------------------------------------
@@ -1262,6 +1373,11 @@ nl_status nl_launch_boundary_batch_f32(nl_ctx *ctx, int ball, bool inv, const nl
 nl_status nl_launch_boundary_batch_f64(nl_ctx *ctx, int ball, bool inv, const nlq::NumArgs *dA,
                                        const nlq::BatchItem *items, int n_items, int *counter, int blocks,
                                        bool set_attr);
+// the deferred items of one float boundary launch (queue `items`, fill count *count)
+nl_status nl_launch_deferred_batch_f32(nl_ctx *ctx, int ball, const nlq::NumArgs *dA, const nlq::DeferItem *items,
+                                       const int *count, int cap);
+// grid of the deferred-item kernels: two blocks per SM (a grid-stride loop covers any count)
+nl_status nl_deferred_blocks(nl_ctx *ctx, int *blocks);
 // resident blocks per SM of the interior launch (ball < 0) or of a boundary launch
 nl_status nl_batch_occupancy_f32(nl_ctx *ctx, int ball, bool inv, int *per_sm);
 nl_status nl_batch_occupancy_f64(nl_ctx *ctx, int ball, bool inv, int *per_sm);

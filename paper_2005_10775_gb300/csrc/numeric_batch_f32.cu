@@ -70,6 +70,33 @@ nl_status nl_launch_boundary_batch_f32(nl_ctx *ctx, int ball, bool inv, const nl
                : boundary_ball<false>(ctx, ball, dA, items, n_items, counter, blocks, set_attr, nullptr);
 }
 
+nl_status nl_launch_deferred_batch_f32(nl_ctx *ctx, int ball, const nlq::NumArgs *dA, const nlq::DeferItem *items,
+                                       const int *count, int cap)
+{
+    int blocks = 0;
+    nl_status s = nl_deferred_blocks(ctx, &blocks);
+    if (s != NL_OK) return s;
+    const unsigned threads = nlq::kWarpsPerBlock * 32;
+    switch (ball) {
+    case NL_BALL_BARYCENTER:
+        nlq::k_deferred_batch<NL_BALL_BARYCENTER><<<blocks, threads, 0, ctx->stream>>>(dA, items, count, cap); break;
+    case NL_BALL_NOCAPS:
+        nlq::k_deferred_batch<NL_BALL_NOCAPS><<<blocks, threads, 0, ctx->stream>>>(dA, items, count, cap); break;
+    case NL_BALL_APPROXCAPS:
+        nlq::k_deferred_batch<NL_BALL_APPROXCAPS><<<blocks, threads, 0, ctx->stream>>>(dA, items, count, cap); break;
+    case NL_BALL_EXACTCAPS:
+        nlq::k_deferred_batch<NL_BALL_EXACTCAPS><<<blocks, threads, 0, ctx->stream>>>(dA, items, count, cap); break;
+    case NL_BALL_NGON:
+        nlq::k_deferred_batch<NL_BALL_NGON><<<blocks, threads, 0, ctx->stream>>>(dA, items, count, cap); break;
+    case NL_BALL_OVERLAP:
+        nlq::k_deferred_batch<NL_BALL_OVERLAP><<<blocks, threads, 0, ctx->stream>>>(dA, items, count, cap); break;
+    default: return nl_fail(ctx, NL_EINVAL, "no deferred items for this ball mode");
+    }
+    ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    return NL_OK;
+}
+
 nl_status nl_batch_occupancy_f32(nl_ctx *ctx, int ball, bool inv, int *per_sm)
 {
     if (ball < 0) {

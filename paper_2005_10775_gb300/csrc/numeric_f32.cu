@@ -6,10 +6,23 @@ namespace {
 template <int BALL, bool INV>
 nl_status launch_boundary_k(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads)
 {
+    // the outer-support balls integrate their candidates without the item queue
+    constexpr bool kQueue = BALL != NL_BALL_BARY_NOCAPS && BALL != NL_BALL_BARY_APPROXCAPS;
+    const bool defer = kQueue && A.defer;
+    if (defer) NL_CK(cudaMemsetAsync(A.defer_n, 0, sizeof(int), ctx->stream));
     const size_t smem = sizeof(nlq::BoundaryShared<float>) * nlq::kWarpsPerBlock;
     NL_CK(cudaFuncSetAttribute(nlq::k_boundary<BALL, float, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem));
     nlq::k_boundary<BALL, float, INV><<<grid, threads, smem, ctx->stream>>>(A); ++ctx->launches;
+    if constexpr (kQueue) {
+        if (defer) {
+            NL_CK(cudaGetLastError());
+            int blocks = 0;
+            nl_status s = nl_deferred_blocks(ctx, &blocks);
+            if (s != NL_OK) return s;
+            nlq::k_deferred<BALL><<<blocks, threads, 0, ctx->stream>>>(A); ++ctx->launches;
+        }
+    }
     return NL_OK;
 }
 
@@ -21,6 +34,14 @@ nl_status launch_boundary(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, uns
 }
 
 }  // namespace
+
+nl_status nl_deferred_blocks(nl_ctx *ctx, int *blocks)
+{
+    int nsm = 0;
+    NL_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    *blocks = 2 * (nsm > 0 ? nsm : 1);
+    return NL_OK;
+}
 
 nl_status nl_launch_numeric_f32(nl_ctx *ctx, const nlq::NumArgs &A, int ball)
 {

@@ -92,6 +92,7 @@ def _load():
         "nl_csr_free": (None, [ctypes.c_void_p, P(nl_csr)]),
         "nl_last_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
         "nl_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+        "nl_last_fp64_items": (ctypes.c_int64, [ctypes.c_void_p]),
         "nl_cg_noalloc": (ctypes.c_int, [ctypes.c_void_p, P(nl_csr), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_double, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_double)]),
     }
@@ -300,6 +301,12 @@ def nl_last_timings(ctx):
 
 def nl_launch_count(ctx) -> int:
     return int(_L.nl_launch_count(ctx))
+
+
+def nl_last_fp64_items(ctx) -> int:
+    """Items of the last FP32-path nl_assemble / nl_interactions whose region the FP64
+    geometry built (queued for the deferred kernel, or inline when the queue was full)."""
+    return int(_L.nl_last_fp64_items(ctx))
 
 
 def to_scipy(ctx, m: nl_csr, ncols=None):

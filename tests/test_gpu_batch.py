@@ -108,9 +108,12 @@ def test_batch_graph_replay_reproduces_values(nl, ctx, mixed):
     for _ in range(2):
         nl.nl_batch_run(ctx, mixed["h"])
     assert nl.nl_launch_count(ctx) > n0
-    for b, o in zip(before, mixed["outs"]):
+    # FP64 values agree up to the order of the FP64 scatter's atomic adds; FP32 pair blocks
+    # also take the FP64-decided items' blocks by FP32 atomic adds, in any order
+    for b, o, (_, prec) in zip(before, mixed["outs"], mixed["probs"]):
         after = nl.to_scipy(ctx, o).data
-        assert np.abs(after - b).max() <= 1e-14 * np.abs(b).max()
+        tol = 1e-14 if prec == "fp64" else 1e-6
+        assert np.abs(after - b).max() <= tol * np.abs(b).max()
 
 
 def test_batch_schedule_info_and_cache(nl, ctx, mixed):
