@@ -36,9 +36,10 @@ UNIT = "qp-pairs/s"
 FLOP_PER_QP = 37.0
 FLOP_PER_INTER = 48.0
 SMS, FP32_LANES = 152, 128
-# DRAM bytes (read + write) of the numeric phase (k_interior + k_boundary) of one
-# assembly, from one ncu capture of the current kernels (profiles/k_boundary_<workload>.md)
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) of the numeric phase (k_interior + k_boundary + k_deferred) of
+# one assembly, from one ncu capture of the current kernels (profiles/k_boundary_<workload>.md)
+NCU_TRAFFIC = {"ngon32_96": (722.4e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_interior + k_boundary "
+                                      "+ k_deferred, profiles/k_boundary_ngon32_96.md")}
 
 
 def parse():
@@ -349,7 +350,9 @@ def batch_bench(args, nl, ctx, stream, dev, world, dist, rank):
                                "nl_assemble_numeric calls"},
         "fp64": fp64,
         "speedup_fp32c_vs_fp64": (fp64["ms_per_step"] / ms_batch) if fp64 else None,
-        "roofline": {"bound": "alu", "kernel": "k_numeric_batch (pair geometry + quadrature, all problems)",
+        "roofline": {"bound": "alu",
+                     "kernel": "k_interior_batch + k_boundary_batch + k_deferred_batch (pair geometry + quadrature, "
+                               "all problems)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_mhz:.0f} MHz "
                                     f"(clock from MEASURED_PEAKS.json, {src})",
@@ -578,7 +581,7 @@ def main():
                    "wall_s_timed": wall},
         "fp64": fp64,
         "speedup_fp32c_vs_fp64": (fp64["ms_per_step"] / ms_step) if fp64 else None,
-        "roofline": {"bound": "alu", "kernel": "k_interior + k_boundary (pair geometry + quadrature)",
+        "roofline": {"bound": "alu", "kernel": "k_interior + k_boundary + k_deferred (pair geometry + quadrature)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_mhz:.0f} MHz "
                                     f"(clock from MEASURED_PEAKS.json, {src})",
