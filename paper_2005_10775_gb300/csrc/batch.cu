@@ -532,6 +532,7 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
             a.flag = P->flag;
             a.blk = P->blk;
             a.maa = P->maa;
+            a.mbb = P->mbb;
             a.lslot = P->lslot;
             a.row_ptr = outs[i].row_ptr;
             a.col = outs[i].col_idx;

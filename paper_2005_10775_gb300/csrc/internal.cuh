@@ -73,6 +73,7 @@ struct nl_plan {
     uint64_t *hash_a = nullptr;   // [K]
     // pattern
     int64_t *lslot = nullptr;     // [6][K] slots of the upper local pairs of each triangle
+    double *mbb = nullptr;        // [6][K] per-triangle sum of the pairs' upper M_bb (zero between scatters)
     int64_t *tslot = nullptr;     // [nnz] slot of the transposed entry
     double *W = nullptr;          // [nnz] one-sided accumulation, D = W + W^T
     int64_t max_row = 0;          // longest row of the pattern
@@ -187,6 +188,7 @@ struct ScatterArgs {   // one problem
     const uint8_t *flag;
     const void *blk;
     const double *maa;
+    double *mbb;
     const int64_t *lslot, *row_ptr;
     const int32_t *col;
     double *W;

@@ -8,10 +8,9 @@
 // T whose pair interacts in either direction (every triangle interacts with itself).
 //
 // Numeric scatter: D = W + W^T with the one-sided accumulator W receiving, per
-// interacting pair, -M_ab at (a_i, b_k) and the upper triangle of M_bb (diagonal
-// halved), and per outer triangle the upper triangle of M_aa (diagonal halved).
-// That is 9 + 6 FP64 atomics per pair instead of 27, and the transposed blocks
-// come from the final W + W^T pass through the transposed-slot map.
+// interacting pair, -M_ab at (a_i, b_k), and per triangle the upper triangles of M_aa
+// and of the summed M_bb of its pairs (diagonals halved).  The transposed blocks come
+// from the final W + W^T pass through the transposed-slot map.
 #include <cuda_runtime.h>
 
 #include <new>
@@ -177,15 +176,50 @@ __global__ void k_tslot(int J, const int64_t *row_ptr, const int32_t *col, int64
 
 // One-sided numeric scatter, warp per outer triangle.  The -M_ab contributions of all
 // of T_a's pairs land in the three rows of T_a's nodes: the warp accumulates them in
-// shared memory (columns of those rows staged there, `cap` per row) and adds each row
-// entry to W once, instead of one FP64 atomic per pair and entry.  The upper M_bb of
-// every pair and T_a's own M_aa go straight to W through the local slot map.
+// shared memory (`cap` entries per row) and adds each row entry to W once, instead of
+// one FP64 atomic per pair and entry.  The columns of the three rows are indexed by a
+// shared hash table (key: column node; value: the column's position in each of the
+// three rows, 10 bits each), so each node of T_b costs one lookup for all three rows.
+// The upper M_bb of every pair is summed per triangle b (mbb, FP64 atomics); k_local_blocks
+// then adds M_aa + M_bb of every triangle through the local slot map.
+constexpr unsigned kPosAbsent = 1023u;   // 10-bit position field: column not in that row
+constexpr int kMaxCachedRow = 1022;
+
+__device__ __forceinline__ unsigned col_hash(int c, int hbits)
+{
+    return ((unsigned)c * 2654435761u) >> (32 - hbits);
+}
+
+// insert column c (or find it): its slot, or -1 when the table is full
+__device__ __forceinline__ int hash_insert(int32_t *key, int H, int hbits, int c)
+{
+    unsigned h = col_hash(c, hbits);
+    for (int t = 0; t < H; t++) {
+        const int old = atomicCAS(&key[h], -1, c);
+        if (old == -1 || old == c) return (int)h;
+        h = (h + 1) & (unsigned)(H - 1);
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int hash_find(const int32_t *key, int H, int hbits, int c)
+{
+    unsigned h = col_hash(c, hbits);
+    for (int t = 0; t < H; t++) {
+        const int k = key[h];
+        if (k == c) return (int)h;
+        if (k == -1) return -1;
+        h = (h + 1) & (unsigned)(H - 1);
+    }
+    return -1;
+}
+
 template <typename T>
 __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int32_t *tri, const int64_t *ptr,
-                                              const int32_t *idx, const uint8_t *flag, const T *blk,
-                                              const double *maa, const int64_t *lslot, const int64_t *row_ptr,
-                                              const int32_t *col, double *W, int *err, int cap, int a, int lane,
-                                              int32_t *scol, T *sacc)
+                                              const int32_t *idx, const uint8_t *flag, const T *blk, double *mbb,
+                                              const int64_t *row_ptr, const int32_t *col, double *W, int *err,
+                                              int cap, int hbits, int a, int lane, T *sacc, int32_t *skey,
+                                              uint32_t *spk)
 {
     const int ar[3] = {tri[3 * a], tri[3 * a + 1], tri[3 * a + 2]};
 #ifdef NL_CHECKS
@@ -201,23 +235,41 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
         return;
     }
 #endif
+    const int H = 1 << hbits;
     int64_t r0[3];
     int len[3];
-    bool cached[3];
     for (int i = 0; i < 3; i++) {
         r0[i] = row_ptr[ar[i]];
         len[i] = (int)(row_ptr[ar[i] + 1] - r0[i]);
-        cached[i] = len[i] <= cap;
-        if (cached[i])
-            for (int k = lane; k < len[i]; k += 32) {
-                scol[i * cap + k] = col[r0[i] + k];
-                sacc[i * cap + k] = (T)0;
-            }
     }
-    __syncwarp();
+    bool cached = cap > 0 && len[0] <= cap && len[1] <= cap && len[2] <= cap;
+    if (cached) {
+        for (int k = lane; k < H; k += 32) {
+            skey[k] = -1;
+            spk[k] = 0xffffffffu;
+        }
+        for (int k = lane; k < 3 * cap; k += 32) sacc[k] = (T)0;
+        __syncwarp();
+        bool full = false;
+        for (int i = 0; i < 3; i++)
+            for (int k = lane; k < len[i]; k += 32) {
+                const int sl = hash_insert(skey, H, hbits, col[r0[i] + k]);
+                if (sl < 0) {
+                    full = true;
+                    continue;
+                }
+                atomicAnd(&spk[sl], ~((kPosAbsent ^ (unsigned)k) << (10 * i)));
+            }
+        cached = !__any_sync(0xffffffffu, full);   // a full table: this triangle searches in global memory
+        __syncwarp();
+    }
     for (int64_t e = ptr[a] + lane; e < ptr[a + 1]; e += 32) {
-        if (!flag[e]) continue;
+        // every load of the pair first (independent of the flag): one round trip, not a chain
+        const uint8_t f = flag[e];
         const int b = idx[e];
+        T v[15];
+        for (int p = 0; p < 15; p++) v[p] = blk[(int64_t)p * E + e];
+        if (!f) continue;
 #ifdef NL_CHECKS
         if (b < 0 || b >= K) {
             atomicOr(err, 64);
@@ -231,19 +283,17 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
             continue;
         }
 #endif
-        for (int i = 0; i < 3; i++)
-            for (int k = 0; k < 3; k++) {
-                const T v = blk[(int64_t)(3 * i + k) * E + e];
-                if (cached[i]) {
-                    int lo = 0, hi = len[i] - 1, pos = -1;
-                    while (lo <= hi) {
-                        const int mid = (lo + hi) >> 1;
-                        const int c = scol[i * cap + mid];
-                        if (c == bn[k]) { pos = mid; break; }
-                        if (c < bn[k]) lo = mid + 1; else hi = mid - 1;
-                    }
-                    if (pos >= 0) atomicAdd(&sacc[i * cap + pos], -v); else atomicOr(err, 2);
-                } else {
+        for (int p = 0; p < 6; p++) atomicAdd(&mbb[(int64_t)p * K + b], (double)v[9 + p]);
+        for (int k = 0; k < 3; k++) {
+            if (cached) {
+                const int sl = hash_find(skey, H, hbits, bn[k]);
+                const unsigned pk = sl >= 0 ? spk[sl] : 0xffffffffu;
+                for (int i = 0; i < 3; i++) {
+                    const unsigned pos = (pk >> (10 * i)) & kPosAbsent;
+                    if (pos < (unsigned)len[i]) atomicAdd(&sacc[i * cap + pos], -v[3 * i + k]); else atomicOr(err, 2);
+                }
+            } else {
+                for (int i = 0; i < 3; i++) {
                     const int64_t sl = find_slot(row_ptr, col, ar[i], bn[k]);
 #ifdef NL_CHECKS
                     if (sl >= nnz_chk) {
@@ -251,50 +301,73 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
                         continue;
                     }
 #endif
-                    if (sl >= 0) atomicAdd(&W[sl], -(double)v); else atomicOr(err, 2);
+                    if (sl >= 0) atomicAdd(&W[sl], -(double)v[3 * i + k]); else atomicOr(err, 2);
                 }
             }
-        for (int p = 0; p < 6; p++) {
-            double v = (double)blk[(int64_t)(9 + p) * E + e];
-            if (p < 3) v *= 0.5;
-            const int64_t sl = lslot[(int64_t)p * K + b];
-#ifdef NL_CHECKS
-            if (sl >= nnz_chk) {
-                atomicOr(err, 64);
-                continue;
-            }
-#endif
-            if (sl >= 0) atomicAdd(&W[sl], v); else atomicOr(err, 2);
         }
     }
     __syncwarp();
-    for (int i = 0; i < 3; i++)
-        if (cached[i])
+    if (cached)
+        for (int i = 0; i < 3; i++)
             for (int k = lane; k < len[i]; k += 32) {
                 const T v = sacc[i * cap + k];
                 if (v != (T)0) atomicAdd(&W[r0[i] + k], (double)v);
             }
-    if (lane == 0)
-        for (int p = 0; p < 6; p++) {
-            double v = maa[(int64_t)p * K + a];
-            if (p < 3) v *= 0.5;
-            const int64_t sl = lslot[(int64_t)p * K + a];
-            if (sl >= 0) atomicAdd(&W[sl], v); else atomicOr(err, 2);
-        }
+}
+
+// M_aa + M_bb of every triangle into W through its local slots (diagonal halved: D = W + W^T),
+// leaving mbb zeroed for the next scatter
+__device__ __forceinline__ void local_block(int K, int t, const double *maa, double *mbb, const int64_t *lslot,
+                                            double *W, int *err)
+{
+    for (int p = 0; p < 6; p++) {
+        double v = maa[(int64_t)p * K + t] + mbb[(int64_t)p * K + t];
+        mbb[(int64_t)p * K + t] = 0.0;
+        if (p < 3) v *= 0.5;
+        const int64_t sl = lslot[(int64_t)p * K + t];
+        if (sl >= 0) atomicAdd(&W[sl], v); else atomicOr(err, 2);
+    }
+}
+
+__global__ void k_local_blocks(int K, const double *maa, double *mbb, const int64_t *lslot, double *W, int *err)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < K) local_block(K, t, maa, mbb, lslot, W, err);
+}
+
+// shared memory of one warp of the scatter: row accumulators [3][cap] (T), hash keys and
+// packed positions [H] (cap a multiple of 4 keeps the int arrays aligned after a float array)
+template <typename T>
+__host__ __device__ constexpr size_t scatter_warp_bytes(int cap, int hbits)
+{
+    return cap > 0 ? 3 * (size_t)cap * sizeof(T) + ((size_t)8 << hbits) : 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void scatter_warp_smem(unsigned char *raw, int wib, int cap, int hbits, T *&sacc,
+                                                  int32_t *&skey, uint32_t *&spk)
+{
+    unsigned char *base = raw + (size_t)wib * scatter_warp_bytes<T>(cap, hbits);
+    sacc = (T *)base;
+    skey = (int32_t *)(base + 3 * (size_t)cap * sizeof(T));
+    spk = (uint32_t *)(skey + (1 << hbits));
 }
 
 template <typename T>
 __global__ void k_scatter(int K, int J, int64_t E, const int32_t *tri, const int64_t *ptr, const int32_t *idx,
-                          const uint8_t *flag, const T *blk, const double *maa, const int64_t *lslot,
-                          const int64_t *row_ptr, const int32_t *col, double *W, int *err, int cap)
+                          const uint8_t *flag, const T *blk, double *mbb, const int64_t *row_ptr, const int32_t *col,
+                          double *W, int *err, int cap, int hbits)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int a = blockIdx.x * (blockDim.x >> 5) + wib;
-    int32_t *scol = (int32_t *)(smem_raw + (size_t)wib * 3 * cap * (sizeof(int32_t) + sizeof(T)));
-    T *sacc = (T *)(scol + 3 * cap);
+    T *sacc;
+    int32_t *skey;
+    uint32_t *spk;
+    scatter_warp_smem<T>(smem_raw, wib, cap, hbits, sacc, skey, spk);
     if (a >= K) return;
-    scatter_outer<T>(K, J, E, tri, ptr, idx, flag, blk, maa, lslot, row_ptr, col, W, err, cap, a, lane, scol, sacc);
+    scatter_outer<T>(K, J, E, tri, ptr, idx, flag, blk, mbb, row_ptr, col, W, err, cap, hbits, a, lane, sacc, skey,
+                     spk);
 }
 
 // ---- batched scatter: every problem of a batch in one launch per value type ----
@@ -311,18 +384,31 @@ __device__ __forceinline__ int batch_problem(const int64_t *off, int n, int64_t 
 }
 
 template <typename T>
-__global__ void k_scatter_batch(const ScatterArgs *__restrict__ S, const int64_t *__restrict__ koff, int n, int cap)
+__global__ void k_scatter_batch(const ScatterArgs *__restrict__ S, const int64_t *__restrict__ koff, int n, int cap,
+                                int hbits)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     if (g >= koff[n]) return;
-    int32_t *scol = (int32_t *)(smem_raw + (size_t)wib * 3 * cap * (sizeof(int32_t) + sizeof(T)));
-    T *sacc = (T *)(scol + 3 * cap);
+    T *sacc;
+    int32_t *skey;
+    uint32_t *spk;
+    scatter_warp_smem<T>(smem_raw, wib, cap, hbits, sacc, skey, spk);
     const int p = batch_problem(koff, n, g);
     const ScatterArgs &A = S[p];
-    scatter_outer<T>(A.K, A.J, A.E, A.tri, A.ptr, A.idx, A.flag, (const T *)A.blk, A.maa, A.lslot, A.row_ptr, A.col,
-                     A.W, A.err, cap, (int)(g - koff[p]), lane, scol, sacc);
+    scatter_outer<T>(A.K, A.J, A.E, A.tri, A.ptr, A.idx, A.flag, (const T *)A.blk, A.mbb, A.row_ptr, A.col, A.W,
+                     A.err, cap, hbits, (int)(g - koff[p]), lane, sacc, skey, spk);
+}
+
+// M_aa + M_bb of every triangle of every problem (koff: prefix sums of K)
+__global__ void k_local_blocks_batch(const ScatterArgs *__restrict__ S, const int64_t *__restrict__ koff, int n)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= koff[n]) return;
+    const int p = batch_problem(koff, n, g);
+    const ScatterArgs &A = S[p];
+    local_block(A.K, (int)(g - koff[p]), A.maa, A.mbb, A.lslot, A.W, A.err);
 }
 
 __global__ void k_zero_batch(const ScatterArgs *__restrict__ S, const int64_t *__restrict__ zoff, int n)
@@ -481,6 +567,8 @@ nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl
                                          out->row_ptr, out->col_idx, T->ovf, 1); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_alloc(ctx, &P->lslot, 6 * (size_t)K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->mbb, 6 * (size_t)K)) != NL_OK) return s;
+    NL_CK(cudaMemsetAsync(P->mbb, 0, sizeof(double) * 6 * (size_t)K, st));   // k_local_blocks re-zeroes it
     if ((s = nl_alloc(ctx, &P->tslot, (size_t)nnz)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->W, (size_t)nnz)) != NL_OK) return s;
     k_local_slots<<<(K + 255) / 256, 256, 0, st>>>(K, P->tri, out->row_ptr, out->col_idx, P->lslot); ++ctx->launches;
@@ -505,23 +593,45 @@ nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     return s;
 }
 
+// Shared-memory plan of the scatter for rows of at most max_row columns: cap per row (a
+// multiple of 4), a hash table of 2^hbits >= 1.25 cap slots (the three rows of a triangle's
+// nodes share most columns: their union is about 1.15 rows, a load near 0.9 at worst; a
+// triangle whose union does not fit searches in global memory), and the warps per block
+// that fit 96 KB; cap = 0 (every triangle searches in global memory) when one warp does not
+// fit or the rows are too long for the 10-bit positions.
+template <typename T>
+static void scatter_plan(int64_t max_row, int *cap, int *hbits, int *warps, size_t *smem)
+{
+    int c = (int)(((max_row > 0 ? max_row : 1) + 3) & ~3LL);
+    int hb = 6;
+    while ((4 << hb) < 5 * c) hb++;
+    int w = 4;
+    while (w > 1 && w * scatter_warp_bytes<T>(c, hb) > 96 * 1024) w >>= 1;
+    if (max_row > kMaxCachedRow || w * scatter_warp_bytes<T>(c, hb) > 96 * 1024) {
+        c = 0;
+        hb = 6;
+    }
+    *cap = c;
+    *hbits = hb;
+    *warps = w;
+    *smem = (size_t)w * scatter_warp_bytes<T>(c, hb);
+}
+
 template <typename T>
 static nl_status launch_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out)
 {
     const int K = P->K;
-    int cap = (int)(((P->max_row > 0 ? P->max_row : 1) + 3) & ~3LL);   // multiple of 4: keeps the T array aligned
-    int warps = 4;
-    while (warps > 1 && (size_t)warps * 3 * cap * (sizeof(int32_t) + sizeof(T)) > 96 * 1024) warps >>= 1;
-    size_t smem = (size_t)warps * 3 * cap * (sizeof(int32_t) + sizeof(T));
-    if (smem > 96 * 1024) {   // very long rows: stage none, search in global memory
-        cap = 0;
-        smem = 0;
-    }
+    int cap, hbits, warps;
+    size_t smem;
+    scatter_plan<T>(P->max_row, &cap, &hbits, &warps, &smem);
     NL_CK(cudaFuncSetAttribute(k_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(96 * 1024)));
     const unsigned grid = (unsigned)((K + warps - 1) / warps);
     k_scatter<T><<<grid, 32 * warps, smem, ctx->stream>>>(K, P->J, P->E, P->tri, P->nbr_ptr, P->nbr_idx, P->flag,
-                                                           (const T *)P->blk, P->maa, P->lslot, out->row_ptr,
-                                                           out->col_idx, P->W, P->err, cap); ++ctx->launches;
+                                                           (const T *)P->blk, P->mbb, out->row_ptr, out->col_idx,
+                                                           P->W, P->err, cap, hbits); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    k_local_blocks<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->maa, P->mbb, P->lslot, P->W, P->err);
+    ++ctx->launches;
     NL_CK(cudaGetLastError());
     return NL_OK;
 }
@@ -562,18 +672,16 @@ static nl_status launch_scatter_batch(nl_ctx *ctx, const ScatterArgs *dS, const 
                                       int64_t totalK, int64_t max_row, bool set_attr)
 {
     if (totalK <= 0) return NL_OK;
-    int cap = (int)(((max_row > 0 ? max_row : 1) + 3) & ~3LL);
-    int warps = 4;
-    while (warps > 1 && (size_t)warps * 3 * cap * (sizeof(int32_t) + sizeof(T)) > 96 * 1024) warps >>= 1;
-    size_t smem = (size_t)warps * 3 * cap * (sizeof(int32_t) + sizeof(T));
-    if (smem > 96 * 1024) {
-        cap = 0;
-        smem = 0;
-    }
+    int cap, hbits, warps;
+    size_t smem;
+    scatter_plan<T>(max_row, &cap, &hbits, &warps, &smem);
     if (set_attr)
         NL_CK(cudaFuncSetAttribute(k_scatter_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(96 * 1024)));
     const unsigned grid = (unsigned)((totalK + warps - 1) / warps);
-    k_scatter_batch<T><<<grid, 32 * warps, smem, ctx->stream>>>(dS, dkoff, n, cap); ++ctx->launches;
+    k_scatter_batch<T><<<grid, 32 * warps, smem, ctx->stream>>>(dS, dkoff, n, cap, hbits); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    k_local_blocks_batch<<<(unsigned)((totalK + 255) / 256), 256, 0, ctx->stream>>>(dS, dkoff, n);
+    ++ctx->launches;
     NL_CK(cudaGetLastError());
     return NL_OK;
 }
