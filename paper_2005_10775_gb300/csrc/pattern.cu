@@ -81,76 +81,130 @@ __global__ void k_node_fill(int K, const int32_t *tri, const int64_t *start, int
 }
 
 constexpr int kRowThreads = 256;
-constexpr int kListCap = NL_HASH_CAP / 2;
+constexpr int kListCap = NL_HASH_CAP / 2;   // longest row (columns) the pattern accepts, plus one
 
-// block per row: hash set of the row's columns in shared memory.
-// pass 0: count; pass 1: write sorted columns at row_ptr[j].
+// insert c into the shared hash set tab (mask + 1 slots): 1 new, 0 present, -1 set full
+__device__ __forceinline__ int set_insert(int32_t *tab, unsigned mask, int c)
+{
+    unsigned h = ((unsigned)c * 2654435761u) & mask;
+    for (unsigned t = 0; t <= mask; t++) {
+        const int old = atomicCAS(&tab[h], -1, c);
+        if (old == -1) return 1;
+        if (old == c) return 0;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// Block per row j: the distinct nodes of the interacting candidates of the triangles around
+// node j, in a shared hash set of 2^hbits slots.  Rows come from `list` (its length at *nlist,
+// grid-stride) or are the block indices.  pass 0 counts (a row whose set fills up is appended
+// to ovf_list for a second count with a larger set, or, without ovf_list, counted as an
+// overflow); pass 1 writes the sorted columns at row_ptr[j] (lst: 2^lbits slots).  Each thread
+// issues the loads of four candidates before inserting their nodes.
 __global__ void __launch_bounds__(kRowThreads) k_rows(int J, const int64_t *nt_ptr, const int32_t *ntri,
                                                       const int32_t *tri, const int64_t *ptr, const int32_t *idx,
-                                                      const uint8_t *sym, int64_t *cnt, const int64_t *row_ptr,
-                                                      int32_t *col, int *overflow, int pass)
+                                                      const uint8_t *sym, int hbits, int lbits, const int *list,
+                                                      const int *nlist, int64_t *cnt, const int64_t *row_ptr,
+                                                      int32_t *col, int *ovf_list, int *ovf_n, int *overflow,
+                                                      int pass)
 {
     extern __shared__ int32_t sm[];
-    int32_t *tab = sm;                    // [NL_HASH_CAP]
-    int32_t *lst = sm + NL_HASH_CAP;      // [kListCap]
+    const int H = 1 << hbits;
+    const unsigned mask = (unsigned)H - 1u;
+    int32_t *tab = sm;        // [H]
+    int32_t *lst = sm + H;    // [2^lbits] (pass 1)
     __shared__ int s_n, s_ovf;
-    const int j = blockIdx.x;
-    for (int i = threadIdx.x; i < NL_HASH_CAP; i += blockDim.x) tab[i] = -1;
-    if (threadIdx.x == 0) { s_n = 0; s_ovf = 0; }
-    __syncthreads();
-    for (int64_t q = nt_ptr[j]; q < nt_ptr[j + 1]; q++) {
-        const int T = ntri[q];
-        for (int64_t e = ptr[T] + threadIdx.x; e < ptr[T + 1]; e += blockDim.x) {
-            if (!sym[e]) continue;
-            const int c = idx[e];
-            for (int i = 0; i < 3; i++) {
-                const int v = tri[3 * c + i];
-                unsigned h = ((unsigned)v * 2654435761u) & (NL_HASH_CAP - 1);
-                for (int probe = 0; probe < NL_HASH_CAP; probe++) {
-                    int old = atomicCAS(&tab[h], -1, v);
-                    if (old == -1) {
-                        if (atomicAdd(&s_n, 1) >= kListCap - 1) s_ovf = 1;
-                        break;
-                    }
-                    if (old == v) break;
-                    h = (h + 1) & (NL_HASH_CAP - 1);
+    const int nrows = list ? *nlist : J;
+    const int lane = threadIdx.x & 31;
+    for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int j = list ? list[r] : r;
+        for (int i = threadIdx.x; i < H; i += blockDim.x) tab[i] = -1;
+        if (threadIdx.x == 0) {
+            s_n = 0;
+            s_ovf = 0;
+        }
+        __syncthreads();
+        int mine = 0;
+        bool full = false;
+        for (int64_t q = nt_ptr[j]; q < nt_ptr[j + 1]; q++) {
+            const int T = ntri[q];
+            const int64_t e1 = ptr[T + 1];
+            for (int64_t eb = ptr[T] + threadIdx.x; eb < e1; eb += 4 * (int64_t)blockDim.x) {
+                int c[4];
+                bool ok[4];
+                for (int u = 0; u < 4; u++) {
+                    const int64_t e = eb + (int64_t)u * blockDim.x;
+                    ok[u] = e < e1;
+                    c[u] = ok[u] ? idx[e] : 0;
+                    ok[u] = ok[u] && sym[e];
                 }
+                int v[4][3];
+                for (int u = 0; u < 4; u++)
+                    for (int i = 0; i < 3; i++) v[u][i] = ok[u] ? tri[3 * c[u] + i] : -1;
+                for (int u = 0; u < 4; u++)
+                    if (ok[u])
+                        for (int i = 0; i < 3; i++) {
+                            const int st = set_insert(tab, mask, v[u][i]);
+                            mine += st > 0;
+                            full = full || st < 0;
+                        }
             }
         }
-    }
-    __syncthreads();
-    if (s_ovf) {
-        if (threadIdx.x == 0) atomicAdd(overflow, 1);
-        return;
-    }
-    const int n = s_n;
-    if (pass == 0) {
-        if (threadIdx.x == 0) cnt[j] = n;
-        return;
-    }
-    __syncthreads();   // every thread has read the column count before the counter is reused
-    if (threadIdx.x == 0) s_n = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < NL_HASH_CAP; i += blockDim.x)
-        if (tab[i] >= 0) lst[atomicAdd(&s_n, 1)] = tab[i];
-    int p = 1;
-    while (p < n) p <<= 1;
-    for (int i = n + threadIdx.x; i < p; i += blockDim.x) lst[i] = 0x7fffffff;
-    __syncthreads();
-    for (int k = 2; k <= p; k <<= 1)
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int i = threadIdx.x; i < p; i += blockDim.x) {
-                int l = i ^ jj;
-                if (l > i) {
-                    bool up = (i & k) == 0;
-                    int u = lst[i], v = lst[l];
-                    if ((u > v) == up) { lst[i] = v; lst[l] = u; }
-                }
+        // block totals: one shared atomic per warp
+        for (int off = 16; off; off >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, off);
+        const bool wfull = __any_sync(0xffffffffu, full);
+        if (lane == 0) {
+            atomicAdd(&s_n, mine);
+            if (wfull) s_ovf = 1;
+        }
+        __syncthreads();
+        const int n = s_n;
+        const bool ovf = s_ovf != 0 || n >= kListCap;
+        if (ovf) {
+            if (threadIdx.x == 0) {
+                if (ovf_list) ovf_list[atomicAdd(ovf_n, 1)] = j;
+                else atomicAdd(overflow, 1);
             }
+        } else if (pass == 0) {
+            if (threadIdx.x == 0) cnt[j] = n;
+        } else {
+            __syncthreads();   // every thread has read the column count before the counter is reused
+            if (threadIdx.x == 0) s_n = 0;
             __syncthreads();
+            for (int i0 = 0; i0 < H; i0 += blockDim.x) {
+                const int i = i0 + threadIdx.x;
+                const int val = i < H ? tab[i] : -1;
+                const unsigned bal = __ballot_sync(0xffffffffu, val >= 0);
+                int base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&s_n, __popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (val >= 0) lst[base + __popc(bal & ((1u << lane) - 1u))] = val;
+            }
+            int p = 1;
+            while (p < n) p <<= 1;
+            for (int i = n + threadIdx.x; i < p; i += blockDim.x) lst[i] = 0x7fffffff;
+            __syncthreads();
+            for (int k = 2; k <= p; k <<= 1)
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+                        const int l = i ^ jj;
+                        if (l > i) {
+                            const bool up = (i & k) == 0;
+                            const int u = lst[i], w = lst[l];
+                            if ((u > w) == up) {
+                                lst[i] = w;
+                                lst[l] = u;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            const int64_t o = row_ptr[j];
+            for (int i = threadIdx.x; i < n; i += blockDim.x) col[o + i] = lst[i];
         }
-    const int64_t o = row_ptr[j];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) col[o + i] = lst[i];
+        __syncthreads();   // the set and the counters are reused by the next row
+    }
 }
 
 // slots of the six upper local pairs (00, 11, 22, 01, 02, 12) of each triangle
@@ -483,6 +537,7 @@ struct nl_pat {
     int64_t *ncnt = nullptr, *nptr = nullptr, *ncur = nullptr, *rcnt = nullptr;
     int32_t *ntri = nullptr;
     int *ovf = nullptr;
+    int *olist = nullptr, *on = nullptr;   // rows whose first count filled its hash set
     unsigned long long *st = nullptr;
 };
 
@@ -502,7 +557,16 @@ void nl_pat_delete(nl_pat *T, cudaStream_t s)
     if (!T) return;
     free_async(T->sym, s); free_async(T->ncnt, s); free_async(T->nptr, s); free_async(T->ncur, s);
     free_async(T->rcnt, s); free_async(T->ntri, s); free_async(T->ovf, s); free_async(T->st, s);
+    free_async(T->olist, s); free_async(T->on, s);
     delete T;
+}
+
+// log2 of the smallest power of two >= n, within [64, NL_HASH_CAP]
+static int row_set_bits(int64_t n)
+{
+    int b = 6;
+    while ((int64_t(1) << b) < n && (1 << b) < NL_HASH_CAP) b++;
+    return b;
 }
 
 nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_slot *h)
@@ -517,6 +581,9 @@ nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_
     NL_CK(cudaMallocAsync((void **)&T->rcnt, sizeof(int64_t) * (J + 1), st));
     NL_CK(cudaMallocAsync((void **)&T->ntri, sizeof(int32_t) * 3 * (size_t)K, st));
     NL_CK(cudaMallocAsync((void **)&T->ovf, sizeof(int), st));
+    NL_CK(cudaMallocAsync((void **)&T->olist, sizeof(int) * (J + 1), st));
+    NL_CK(cudaMallocAsync((void **)&T->on, sizeof(int), st));
+    NL_CK(cudaMemsetAsync(T->on, 0, sizeof(int), st));
     NL_CK(cudaMallocAsync((void **)&T->st, sizeof(unsigned long long) * 4, st));
     NL_CK(cudaMemsetAsync(T->ncnt, 0, sizeof(int64_t) * (J + 1), st));
     NL_CK(cudaMemsetAsync(T->ncur, 0, sizeof(int64_t) * (J + 1), st));
@@ -528,10 +595,19 @@ nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_
     NL_CK(cudaGetLastError());
     if ((s = nl_scan_i64(ctx, T->ncnt, T->nptr, J)) != NL_OK) return s;
     k_node_fill<<<(K + 255) / 256, 256, 0, st>>>(K, P->tri, T->nptr, T->ncur, T->ntri); ++ctx->launches;
-    const size_t smem = sizeof(int32_t) * (NL_HASH_CAP + kListCap);
-    NL_CK(cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_rows<<<J, kRowThreads, smem, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx, T->sym, T->rcnt,
-                                         nullptr, nullptr, T->ovf, 0); ++ctx->launches;
+    NL_CK(cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(int32_t) * (NL_HASH_CAP + kListCap))));
+    // first count with a set of about 3x the expected row (0.6 x the candidates per triangle);
+    // rows that fill it are counted again with the full set
+    const int hb0 = row_set_bits(P->K > 0 ? 2 * P->E / P->K : 1);
+    k_rows<<<J, kRowThreads, sizeof(int32_t) << hb0, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx,
+                                                           T->sym, hb0, 0, nullptr, nullptr, T->rcnt, nullptr,
+                                                           nullptr, T->olist, T->on, T->ovf, 0); ++ctx->launches;
+    NL_CK(cudaGetLastError());
+    const int hbf = row_set_bits(NL_HASH_CAP);
+    k_rows<<<256, kRowThreads, sizeof(int32_t) << hbf, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx,
+                                                            T->sym, hbf, 0, T->olist, T->on, T->rcnt, nullptr,
+                                                            nullptr, nullptr, nullptr, T->ovf, 0); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_alloc(ctx, &out->row_ptr, (size_t)J + 1)) != NL_OK) return s;
     if ((s = nl_scan_i64(ctx, T->rcnt, out->row_ptr, J)) != NL_OK) return s;
@@ -562,9 +638,12 @@ nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl
     P->max_row = (int64_t)h->pat[3];
     if ((s = nl_alloc(ctx, &out->col_idx, (size_t)nnz)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &out->val, (size_t)nnz)) != NL_OK) return s;
-    const size_t smem = sizeof(int32_t) * (NL_HASH_CAP + kListCap);
-    k_rows<<<J, kRowThreads, smem, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx, T->sym, nullptr,
-                                         out->row_ptr, out->col_idx, T->ovf, 1); ++ctx->launches;
+    // every row has at most max_row columns: a set of 2 max_row slots never fills
+    const int hb1 = row_set_bits(2 * P->max_row), lb1 = row_set_bits(P->max_row);
+    const size_t smem1 = sizeof(int32_t) * (((size_t)1 << hb1) + ((size_t)1 << lb1));
+    k_rows<<<J, kRowThreads, smem1, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx, T->sym, hb1, lb1,
+                                          nullptr, nullptr, nullptr, out->row_ptr, out->col_idx, nullptr, nullptr,
+                                          T->ovf, 1); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_alloc(ctx, &P->lslot, 6 * (size_t)K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->mbb, 6 * (size_t)K)) != NL_OK) return s;
