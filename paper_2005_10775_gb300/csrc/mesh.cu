@@ -262,67 +262,153 @@ __global__ void k_candidates(int K, Grid g, float delta, const float4 *__restric
     if (!pass && lane == 0) cnt[a] = n;
 }
 
-// Sort each candidate list by triangle index, interior candidates first (bitonic sort in
-// shared memory).  A candidate is interior when every point of T_b lies, with margin,
-// inside the kept region of every outer point of T_a (whole for every q):
+// Sort each candidate list by triangle index, interior candidates first.  A candidate is
+// interior when every point of T_b lies, with margin, inside the kept region of every outer
+// point of T_a (whole for every q):
 //   mode 0: |bary_a - bary_b| + r_a + r_b <= lim   (lim = r_in - 2 tau: disc or polygon inradius)
 //   mode 1: |bary_a - bary_b| + r_a <= lim         (barycenter ball, lim = delta - 2 tau)
 //   mode 2: no interior fast path
 //   mode 3: mode 0 and |bary_a - bary_b| - r_a - 3 r_b > far_margin (singular kernel: no near field)
-// split[a] = index of the first boundary candidate.
-__global__ void k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split, const float4 *cf, int mode,
-                             float lim, float far_margin, int *overflow)
+// split[a] = index of the first boundary candidate.  Candidate indices of a mesh numbered
+// with any locality span far fewer than kSortBits values: the list is then sorted by setting
+// one bit per candidate in an interior and a boundary bitmap and writing the set bits in
+// order (prefix counts over the words); a wider span takes a bitonic sort.
+constexpr int kSortThreads = 256;
+constexpr int kSortWords = 2048;   // 65536 bits per bitmap
+
+__device__ __forceinline__ bool interior_cand(const float4 &ca, const float4 &cb, int mode, float lim,
+                                              float far_margin)
+{
+    if (mode == 2) return false;
+    // FP32 with lim already reduced by 1e-5 delta (far above the FP32 rounding): conservative
+    const float dx = cb.x - ca.x, dy = cb.y - ca.y;
+    const float D = sqrtf(dx * dx + dy * dy);
+    bool in = (mode == 1 ? D + ca.z : D + ca.z + cb.z) <= lim;
+    // singular kernel: also far from the near field for every outer point
+    // (distance >= D - r_a - r_b >= 2 r_b >= diameter of T_b)
+    if (mode == 3) in = in && (D - ca.z - 3.0f * cb.z > far_margin);
+    return in;
+}
+
+// exclusive block prefix sum of v (kSortThreads threads); *total = the sum
+__device__ __forceinline__ int block_scan(int v, int *wsum, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = lane < kSortThreads / 32 ? wsum[lane] : 0;
+        int t = w;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += y;
+        }
+        if (lane < kSortThreads / 32) wsum[lane] = t - w;
+        if (lane == kSortThreads / 32 - 1) wsum[kSortThreads / 32] = t;
+    }
+    __syncthreads();
+    const int r = wsum[warp] + x - v;
+    *total = wsum[kSortThreads / 32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split,
+                                                             const float4 *cf, int mode, float lim, float far_margin,
+                                                             int *overflow)
 {
     __shared__ int32_t s[NL_MAXCAND];
-    __shared__ int s_int;
-    int a = blockIdx.x;
-    int64_t b0 = ptr[a];
-    int n = (int)(ptr[a + 1] - b0);
+    __shared__ uint32_t bm[2][kSortWords];
+    __shared__ int wsum[kSortThreads / 32 + 1];
+    __shared__ int s_lo, s_hi, s_int;
+    const int a = blockIdx.x;
+    const int64_t b0 = ptr[a];
+    const int n = (int)(ptr[a + 1] - b0);
     if (n > NL_MAXCAND) {
         if (threadIdx.x == 0) atomicAdd(overflow, 1);
         return;
     }
-    if (threadIdx.x == 0) s_int = 0;
-    int p = 1;
-    while (p < n) p <<= 1;
+    if (threadIdx.x == 0) {
+        s_lo = 0x7fffffff;
+        s_hi = -1;
+        s_int = 0;
+    }
     const float4 ca = cf[a];
     __syncthreads();
-    int my_int = 0;
-    for (int i = threadIdx.x; i < p; i += blockDim.x) {
-        int key = 0x7fffffff;
-        if (i < n) {
-            const int b = idx[b0 + i];
-            bool interior = false;
-            if (mode != 2) {
-                // FP32 with lim already reduced by 1e-5 delta (far above the FP32 rounding): conservative
-                const float4 cb = cf[b];
-                const float dx = cb.x - ca.x, dy = cb.y - ca.y;
-                const float D = sqrtf(dx * dx + dy * dy);
-                interior = (mode == 1 ? D + ca.z : D + ca.z + cb.z) <= lim;
-                // singular kernel: also far from the near field for every outer point
-                // (distance >= D - r_a - r_b >= 2 r_b >= diameter of T_b)
-                if (mode == 3) interior = interior && (D - ca.z - 3.0f * cb.z > far_margin);
-            }
-            my_int += interior;
-            key = interior ? b : (b | 0x40000000);
-        }
-        s[i] = key;
+    // classify: interior candidates carry bit 30 clear, boundary ones set
+    int lo = 0x7fffffff, hi = -1, my_int = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int b = idx[b0 + i];
+        const bool in = interior_cand(ca, cf[b], mode, lim, far_margin);
+        my_int += in;
+        s[i] = in ? b : (b | 0x40000000);
+        lo = min(lo, b);
+        hi = max(hi, b);
     }
-    atomicAdd(&s_int, my_int);
+    for (int off = 16; off; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+        my_int += __shfl_xor_sync(0xffffffffu, my_int, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&s_lo, lo);
+        atomicMax(&s_hi, hi);
+        atomicAdd(&s_int, my_int);
+    }
     __syncthreads();
-    for (int k = 2; k <= p; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < p; i += blockDim.x) {
-                int l = i ^ j;
-                if (l > i) {
-                    bool up = (i & k) == 0;
-                    int u = s[i], v = s[l];
-                    if ((u > v) == up) { s[i] = v; s[l] = u; }
-                }
-            }
-            __syncthreads();
+    lo = s_lo;
+    const int span = n > 0 ? s_hi - lo + 1 : 0;
+    if (span <= kSortWords * 32) {
+        const int nw = (span + 31) >> 5;
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) bm[0][w] = bm[1][w] = 0u;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int key = s[i], o = (key & 0x3fffffff) - lo;
+            atomicOr(&bm[key >> 30][o >> 5], 1u << (o & 31));
         }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) idx[b0 + i] = s[i] & 0x3fffffff;
+        __syncthreads();
+        // each thread owns a run of consecutive words of both bitmaps
+        const int per = (nw + kSortThreads - 1) / kSortThreads;
+        const int w0 = min(nw, (int)threadIdx.x * per), w1 = min(nw, w0 + per);
+        int c0 = 0, c1 = 0;
+        for (int w = w0; w < w1; w++) {
+            c0 += __popc(bm[0][w]);
+            c1 += __popc(bm[1][w]);
+        }
+        int t0 = 0, t1 = 0;
+        int p0 = block_scan(c0, wsum, &t0);
+        int p1 = block_scan(c1, wsum, &t1) + t0;
+        for (int w = w0; w < w1; w++) {
+            for (uint32_t m = bm[0][w]; m; m &= m - 1) idx[b0 + p0++] = lo + (w << 5) + __ffs(m) - 1;
+            for (uint32_t m = bm[1][w]; m; m &= m - 1) idx[b0 + p1++] = lo + (w << 5) + __ffs(m) - 1;
+        }
+    } else {
+        int p = 1;
+        while (p < n) p <<= 1;
+        for (int i = n + threadIdx.x; i < p; i += blockDim.x) s[i] = 0x7fffffff;
+        __syncthreads();
+        for (int k = 2; k <= p; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < p; i += blockDim.x) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const bool up = (i & k) == 0;
+                        const int u = s[i], v = s[l];
+                        if ((u > v) == up) {
+                            s[i] = v;
+                            s[l] = u;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) idx[b0 + i] = s[i] & 0x3fffffff;
+    }
     if (threadIdx.x == 0) split[a] = b0 + s_int;
 }
 
@@ -554,7 +640,7 @@ nl_status nl_prepare_c(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_host_slot *h)
         else if (cfg->ball == NL_BALL_NGON) lim = P->rin - 2.0 * tau;
         if (cfg->kernel == NL_KERNEL_INV_DIST) mode = cfg->ball == NL_BALL_BARYCENTER ? 2 : 3;
         if ((s = nl_alloc(ctx, &P->nbr_split, (size_t)K)) != NL_OK) return s;
-        k_sort_lists<<<K, 256, 0, st>>>(P->nbr_ptr, P->nbr_idx, P->nbr_split, T->cf, mode, (float)lim,
+        k_sort_lists<<<K, kSortThreads, 0, st>>>(P->nbr_ptr, P->nbr_idx, P->nbr_split, T->cf, mode, (float)lim,
                                         (float)(2.0 * tau), T->ovf); ++ctx->launches;
     }
     NL_CK(cudaGetLastError());
