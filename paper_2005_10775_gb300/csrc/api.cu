@@ -182,6 +182,7 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     A.bx = P->bx;
     A.by = P->by;
     A.area = P->area;
+    A.akc = P->akc;
     A.nbr_ptr = P->nbr_ptr;
     A.nbr_split = P->nbr_split;
     A.nbr_idx = P->nbr_idx;
@@ -332,7 +333,7 @@ void nl_plan_free(nl_plan *P, cudaStream_t s)
 {
     if (!P) return;
     nl_free(P->tri, s); nl_free(P->tx, s); nl_free(P->ty, s); nl_free(P->bx, s); nl_free(P->by, s);
-    nl_free(P->rad, s); nl_free(P->area, s); nl_free(P->ngon, s); nl_free(P->nbr_ptr, s); nl_free(P->nbr_idx, s);
+    nl_free(P->rad, s); nl_free(P->area, s); nl_free(P->akc, s); nl_free(P->ngon, s); nl_free(P->nbr_ptr, s); nl_free(P->nbr_idx, s);
     nl_free(P->nbr_split, s); nl_free(P->flag, s); nl_free(P->blk, s); nl_free(P->maa, s); nl_free(P->qp_a, s);
     nl_free(P->cnt_a, s); nl_free(P->hash_a, s); nl_free(P->lslot, s); nl_free(P->mbb, s); nl_free(P->tslot, s); nl_free(P->W, s);
     nl_free(P->val32, s); nl_free(P->err, s); nl_free(P->defer, s); nl_free(P->defer_n, s);

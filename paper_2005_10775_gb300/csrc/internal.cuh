@@ -58,6 +58,7 @@ struct nl_plan {
     int32_t *tri = nullptr;       // [3K]
     double *tx = nullptr, *ty = nullptr;   // [3][K] vertex coordinates per triangle
     double *bx = nullptr, *by = nullptr, *rad = nullptr, *area = nullptr;  // [K]
+    float *akc = nullptr;         // [K] |T| times the kernel constant, rounded to FP32
     double *ngon = nullptr;       // [2 ngon_n]
     std::vector<double> ngon_host; // host copy of the polygon offsets
     // candidates

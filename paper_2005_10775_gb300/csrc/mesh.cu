@@ -84,7 +84,7 @@ __global__ void k_copy1(int64_t *dst, const int64_t *src) { *dst = *src; }
 // ---------------------------------------------------------------------------
 __global__ void k_prepare(int K, int J, const int32_t *__restrict__ tri, const double *__restrict__ vx,
                           const double *__restrict__ vy, double *tx, double *ty, double *bx, double *by,
-                          double *rad, double *area, double *diam, float4 *cf, int *bad)
+                          double *rad, double *area, double *diam, float4 *cf, double kc, float *akc, int *bad)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= K) return;
@@ -116,6 +116,7 @@ __global__ void k_prepare(int K, int J, const int32_t *__restrict__ tri, const d
     cf[t] = make_float4((float)cx, (float)cy, (float)r, 0.f);   // FP32 copy for the candidate filters
     double cr = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
     area[t] = 0.5 * fabs(cr);
+    akc[t] = (float)(0.5 * fabs(cr) * kc);
     if (!(cr > 0.0)) atomicAdd(bad, 1);
 }
 
@@ -517,6 +518,7 @@ nl_status nl_prepare_a(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, n
     if ((s = nl_alloc(ctx, &P->by, K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->rad, K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->area, K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->akc, K)) != NL_OK) return s;
     if (cfg->ball == NL_BALL_NGON) {
         const size_t nb = sizeof(double) * 2 * cfg->ngon_n;
         P->ngon_host.resize(2 * (size_t)cfg->ngon_n);
@@ -538,7 +540,8 @@ nl_status nl_prepare_a(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, n
     NL_CK(cudaMallocAsync((void **)&T->cf, sizeof(float4) * K, ctx->stream));
     k_prepare<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, J, (const int32_t *)T->dtri, (const double *)T->dvx,
                                                         (const double *)T->dvy, P->tx, P->ty, P->bx, P->by,
-                                                        P->rad, P->area, T->diam, T->cf, T->bad); ++ctx->launches;
+                                                        P->rad, P->area, T->diam, T->cf, cfg->kernel_c, P->akc,
+                                                        T->bad); ++ctx->launches;
     NL_CK(cudaGetLastError());
     k_mesh_stats<<<1, 1024, 0, ctx->stream>>>(K, P->bx, P->by, P->rad, T->diam, T->st); ++ctx->launches;
     NL_CK(cudaGetLastError());

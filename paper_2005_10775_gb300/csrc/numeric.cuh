@@ -45,6 +45,7 @@ struct NumArgs {
     int64_t E;
     const double *tx, *ty;            // [3][K]
     const double *bx, *by, *area;     // [K]
+    const float *akc;                 // [K] |T| kc in FP32
     const int64_t *nbr_ptr, *nbr_split;
     const int32_t *nbr_idx;
     RuleTab outer, inner;
@@ -517,16 +518,22 @@ struct OuterPt {
 
 constexpr int kWarpsPerBlock = 4;
 
-// Per-lane accumulators of one outer triangle: stats and the FP64 M_aa sum.
+// Per-lane accumulators of one outer triangle: stats and the M_aa sum, in FP64 for double
+// blocks and as compensated FP32 sums (Kahan: value mf, compensation mc) for float blocks.
 struct LaneAcc {
     double maa[6];
+    float mf[6], mc[6];
     int64_t cnt, qp;
     uint64_t hsum;
 };
 
 __device__ __forceinline__ void acc_zero(LaneAcc &acc)
 {
-    for (int i = 0; i < 6; i++) acc.maa[i] = 0.0;
+    for (int i = 0; i < 6; i++) {
+        acc.maa[i] = 0.0;
+        acc.mf[i] = 0.f;
+        acc.mc[i] = 0.f;
+    }
     acc.cnt = 0;
     acc.qp = 0;
     acc.hsum = 0;
@@ -604,11 +611,21 @@ __device__ __forceinline__ void write_pair(const NumArgs &A, int64_t e, bool any
     A.flag[e] = any ? 1 : 0;
     T *blk = (T *)A.blk;
     for (int i = 0; i < 15; i++) blk[(int64_t)i * A.E + e] = v[i];
-    for (int i = 0; i < 6; i++) acc.maa[i] += (double)v[15 + i];
+    if (sizeof(T) == sizeof(float)) {
+        for (int i = 0; i < 6; i++) {
+            const float y = (float)v[15 + i] - acc.mc[i];
+            const float t = acc.mf[i] + y;
+            acc.mc[i] = (t - acc.mf[i]) - y;
+            acc.mf[i] = t;
+        }
+    } else {
+        for (int i = 0; i < 6; i++) acc.maa[i] += (double)v[15 + i];
+    }
 }
 
 __device__ __forceinline__ void warp_reduce(LaneAcc &acc)
 {
+    for (int i = 0; i < 6; i++) acc.maa[i] += (double)acc.mf[i] - (double)acc.mc[i];
     for (int off = 16; off; off >>= 1) {
         for (int i = 0; i < 6; i++) acc.maa[i] += __shfl_xor_sync(0xffffffffu, acc.maa[i], off);
         acc.cnt += __shfl_xor_sync(0xffffffffu, acc.cnt, off);
@@ -636,14 +653,14 @@ __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const Ou
             continue;
         }
 #endif
-        D2 Vb[3];
-        for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
-        const D2 bb = {A.bx[b], A.by[b]};
-        const double area_b = A.area[b];
-        const T akc = (T)(area_b * A.kc);
-        int q0, q1;
-        rule_range(A, ba, bb, q0, q1);
         const bool inv = A.kernel == NL_KERNEL_INV_DIST;
+        // the FP64 vertices only where the quadrature uses them (singular kernel)
+        D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+        if (inv)
+            for (int i = 0; i < 3; i++) { Vb[i].x = A.tx[i * K + b]; Vb[i].y = A.ty[i * K + b]; }
+        const T akc = sizeof(T) == sizeof(float) ? (T)A.akc[b] : (T)(A.area[b] * A.kc);
+        int q0 = 0, q1 = A.outer.n;
+        if (A.switch47) rule_range(A, ba, D2{A.bx[b], A.by[b]}, q0, q1);
         nlg::F2 vl[3];
         if (inv)
             for (int i = 0; i < 3; i++) { vl[i].x = (float)(Vb[i].x - ba.x); vl[i].y = (float)(Vb[i].y - ba.y); }
@@ -738,7 +755,7 @@ __device__ __forceinline__ void load_cand(const NumArgs &A, int b, const D2 &ba,
     double vx[3], vy[3];
     for (int i = 0; i < 3; i++) { vx[i] = A.tx[i * K + b]; vy[i] = A.ty[i * K + b]; }
     const D2 bb = {A.bx[b], A.by[b]};
-    c.akcf = (float)(A.area[b] * A.kc);
+    c.akcf = A.akc[b];
     for (int i = 0; i < 3; i++) { c.vlx[i] = (float)(vx[i] - ba.x); c.vly[i] = (float)(vy[i] - ba.y); }
     c.blx = (float)(bb.x - ba.x);
     c.bly = (float)(bb.y - ba.y);
