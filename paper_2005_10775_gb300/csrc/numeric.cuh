@@ -1006,7 +1006,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             const unsigned it = sh.wqueue[i];
             const int own = it >> 8, q = it & 0xff;
             const CandData &cd = sh.cand[own];
-            const OuterPt o = sh.sq[q];
+            const OuterPt &o = sh.sq[q];
             // FP64 vertices only where the FP64 quadrature of the singular kernel needs them
             D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
             if (INV && sizeof(T) == sizeof(double))
@@ -1031,7 +1031,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             const unsigned it = sh.wqueue[kQueueCap - 1 - i];
             const int own = it >> 8, q = it & 0xff;
             const CandData &cd = sh.cand[own];
-            const OuterPt o = sh.sq[q];
+            const OuterPt &o = sh.sq[q];
             nlg::F2 dl[3];
             for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
             Sums<T> S;
@@ -1052,7 +1052,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             const unsigned it = sh.queue[i];
             const int own = it >> 8, q = it & 0xff;
             const CandData &cd = sh.cand[own];
-            const OuterPt o = sh.sq[q];
+            const OuterPt &o = sh.sq[q];
             Sums<T> S;
             int64_t nq = 0;
             int kind, nv, ncap;
