@@ -336,3 +336,35 @@ def test_parity_singular_workload_full_size_sampled(nl, ctx, prec):
         o_row.sort_indices()
         np.testing.assert_array_equal(g_row.indices, o_row.indices)
         assert np.abs(g_row.data - o_row.data).max() <= TOL[prec] * scale
+
+
+def test_parity_solve_workload_full_size_sampled(nl, ctx):
+    # the assembly of the solve workload (32-gon, delta 0.05, 220x220 jittered, K = 96800,
+    # delta/h = 10), FP32-compensated as the bench times it; sampled outputs from the oracle
+    p = I.problem("solve_220")
+    K, J = p.mesh.nt, p.mesh.nv
+    keep = nl._Keep()
+    mesh = nl.make_mesh(p.mesh, keep)
+    cfg = nl.config_of(p, keep, prec="fp32c")
+    h, c, q = nl.nl_interactions(ctx, mesh, cfg)
+    rng = np.random.default_rng(23)
+    a_list = np.unique(np.concatenate([rng.choice(K, 30, replace=False), [0, K - 1, K // 2 + 221]]))
+    out = O.assemble(p.mesh, oracle_cfg(p), a_list=a_list.astype(np.int32), want_hash=True)
+    np.testing.assert_array_equal(h[a_list], out["hash_a"][a_list])
+    np.testing.assert_array_equal(c[a_list], out["count_a"][a_list])
+    np.testing.assert_array_equal(q[a_list], out["qp_a"][a_list])
+    m = nl.nl_assemble(ctx, mesh, cfg)
+    try:
+        Dg = nl.to_scipy(ctx, m)
+    finally:
+        nl.nl_csr_free(ctx, m)
+    rows = np.array([J // 2 + 3, 221 * 7 + 5, J - 2])
+    mask = np.zeros(J, np.uint8)
+    mask[rows] = 1
+    Dr = O.to_csr(O.assemble(p.mesh, oracle_cfg(p), row_mask=mask))
+    scale = np.abs(Dg.diagonal()).max()
+    for r in rows:
+        g_row, o_row = Dg[r], Dr[r]
+        o_row.sort_indices()
+        np.testing.assert_array_equal(g_row.indices, o_row.indices)
+        assert np.abs(g_row.data - o_row.data).max() <= TOL["fp32c"] * scale
