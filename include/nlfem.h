@@ -220,7 +220,9 @@ nl_status nl_rhs(nl_ctx *ctx, const nl_csr *B, const nl_mesh *mesh, const double
                  const double *g_nodal, double *F);
 
 /* y = A x with A's values in FP64 (NL_PREC_FP64) or rounded to FP32 (NL_PREC_FP32_COMP;
-   products accumulated in FP32).  x, y: [A->n] device or host. */
+   products accumulated in FP32).  x, y: [A->n] device or host.  With device x and y the
+   call is stream-ordered (it returns without waiting, and may be captured in a CUDA graph);
+   with a host x or y it returns once y is complete. */
 nl_status nl_matvec(nl_ctx *ctx, const nl_csr *A, const double *x, double *y, int32_t prec);
 
 /* Solve A x = b (A symmetric positive definite, Sec. 2) by conjugate gradients with

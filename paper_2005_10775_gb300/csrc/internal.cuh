@@ -80,6 +80,7 @@ struct nl_plan {
     int64_t max_row = 0;          // longest row of the pattern
     // extracted sub-matrix state (nl_extract)
     float *val32 = nullptr;       // FP32 copy of the values (nl_matvec / nl_cg), lazily built
+    float *x32 = nullptr;         // [ncols] nl_matvec's x rounded to FP32
     int32_t ncols = 0;            // column count of a rectangular result (nl_extract's B)
     int *err = nullptr;           // device error word of the numeric phase and the scatter
     // FP32 path: queue of the items the FP64 geometry decides (nlq::DeferItem), allocated at

@@ -93,21 +93,39 @@ __global__ void k_na_clear(NaScal *sc)
     sc->bb = 0.0;
 }
 
+// sum of v over the block's warps (lane 0 of each warp holds its warp's v), added to *dst by
+// one atomic per block (an atomic per row on one address would serialise the launch)
+__device__ __forceinline__ void na_block_add(double v, double *dst)
+{
+    __shared__ double part[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += part[i];
+        atomicAdd(dst, t);
+    }
+    __syncthreads();
+}
+
 // r = b - A x in FP64, with ||r||^2 and ||b||^2; warp per row
 __global__ void k_na_residual(int n, const int64_t *rp, const int32_t *col, const double *val, const double *x,
                               const double *b, double *r, NaScal *sc)
 {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (row >= n) return;
-    double s = 0.0;
-    for (int64_t k = rp[row] + lane; k < rp[row + 1]; k += 32) s += val[k] * x[col[k]];
-    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-        double v = b[row] - s;
-        r[row] = v;
-        atomicAdd(&sc->rr, v * v);
-        atomicAdd(&sc->bb, b[row] * b[row]);
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    double rr = 0.0, bb = 0.0;
+    if (row < n) {
+        double s = 0.0;
+        for (int64_t k = rp[row] + lane; k < rp[row + 1]; k += 32) s += val[k] * x[col[k]];
+        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        const double v = b[row] - s;
+        if (lane == 0) r[row] = v;
+        rr = v * v;
+        bb = b[row] * b[row];
     }
+    na_block_add(rr, &sc->rr);
+    na_block_add(bb, &sc->bb);
 }
 
 __global__ void k_na_init(int n, const double *r, double inv_norm, float *z, float *p, float *d, NaScal *sc)
@@ -130,15 +148,16 @@ __global__ void k_na_init(int n, const double *r, double inv_norm, float *z, flo
 __global__ void k_na_spmv(int n, const int64_t *rp, const int32_t *col, const double *val, const float *p, float *q,
                           NaScal *sc)
 {
-    int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (r >= n) return;
-    float s = 0.0f;
-    for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s += (float)val[k] * p[col[k]];
-    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-        q[r] = s;
-        atomicAdd(&sc->pq, (double)s * (double)p[r]);
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    double pq = 0.0;
+    if (r < n) {
+        float s = 0.0f;
+        for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s += (float)val[k] * p[col[k]];
+        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) q[r] = s;
+        pq = (double)s * (double)p[r];
     }
+    na_block_add(pq, &sc->pq);
 }
 
 __global__ void k_na_update(int n, const float *p, const float *q, float *d, float *z, NaScal *sc)

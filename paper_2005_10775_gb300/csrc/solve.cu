@@ -111,33 +111,72 @@ __global__ void k_to_f32(int64_t n, const double *a, float *b)
     if (i < n) b[i] = (float)a[i];
 }
 
+// this lane's part of row [b, e) of A times x: lane l takes entries l, l + 32, ... (each load
+// instruction of the warp reads 32 consecutive entries, and the gathers of x touch the few
+// cache lines of 32 consecutive columns), four entries a lane in flight before their gathers
+template <typename TV, typename TX>
+__device__ __forceinline__ TV row_dot(const TV *__restrict__ val, const int32_t *__restrict__ col,
+                                      const TX *__restrict__ x, int64_t b, int64_t e, int lane)
+{
+    TV s = 0;
+    for (int64_t k0 = b + lane; k0 < e; k0 += 128) {
+        TV v[4];
+        int c[4];
+        for (int u = 0; u < 4; u++) {
+            const int64_t k = k0 + 32 * u;
+            v[u] = k < e ? val[k] : (TV)0;
+            c[u] = k < e ? col[k] : -1;
+        }
+        for (int u = 0; u < 4; u++)
+            if (c[u] >= 0) s += v[u] * (TV)x[c[u]];
+    }
+    return s;
+}
+
 // y = A x, warp per row (TV: value type, TX: vector type, accumulation in TV)
 template <typename TV, typename TX, typename TY>
-__global__ void k_spmv(int n, const int64_t *rp, const int32_t *col, const TV *val, const TX *x, TY *y)
+__global__ void k_spmv(int n, const int64_t *rp, const int32_t *__restrict__ col, const TV *__restrict__ val,
+                       const TX *__restrict__ x, TY *y)
 {
     int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (r >= n) return;
-    TV s = 0;
-    for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s += val[k] * (TV)x[col[k]];
+    TV s = row_dot<TV, TX>(val, col, x, rp[r], rp[r + 1], lane);
     for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) y[r] = (TY)s;
 }
 
 // r = b - A x (FP64) and ||r||^2, ||b||^2 accumulated into acc[0], acc[1]
-__global__ void k_residual(int n, const int64_t *rp, const int32_t *col, const double *val, const double *x,
-                           const double *b, double *r, double *acc)
+// sum of v over the block's warps (lane 0 of each warp holds its warp's v), added to *dst by
+// one atomic per block: one address taking an atomic per row would serialise the launch
+__device__ __forceinline__ void block_atomic_add(double v, double *dst)
 {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (row >= n) return;
-    double s = 0.0;
-    for (int64_t k = rp[row] + lane; k < rp[row + 1]; k += 32) s += val[k] * x[col[k]];
-    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-        double v = b[row] - s;
-        r[row] = v;
-        atomicAdd(&acc[0], v * v);
-        atomicAdd(&acc[1], b[row] * b[row]);
+    __shared__ double part[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += part[i];
+        atomicAdd(dst, t);
     }
+    __syncthreads();
+}
+
+__global__ void k_residual(int n, const int64_t *rp, const int32_t *__restrict__ col, const double *__restrict__ val,
+                           const double *__restrict__ x, const double *b, double *r, double *acc)
+{
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    double rr = 0.0, bb = 0.0;
+    if (row < n) {
+        double s = row_dot<double, double>(val, col, x, rp[row], rp[row + 1], lane);
+        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        const double v = b[row] - s;
+        if (lane == 0) r[row] = v;
+        rr = v * v;
+        bb = b[row] * b[row];
+    }
+    block_atomic_add(rr, &acc[0]);
+    block_atomic_add(bb, &acc[1]);
 }
 
 // inner FP32 conjugate gradients on A d = z0 (z0 = r / ||r||)
@@ -162,18 +201,18 @@ __global__ void k_cg_init(int n, const double *r, double inv_norm, float *z, flo
 }
 
 // q = A p and p.q
-__global__ void k_cg_spmv(int n, const int64_t *rp, const int32_t *col, const float *val, const float *p, float *q,
-                          CgScal *sc)
+__global__ void k_cg_spmv(int n, const int64_t *rp, const int32_t *__restrict__ col, const float *__restrict__ val,
+                          const float *__restrict__ p, float *q, CgScal *sc)
 {
-    int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (r >= n) return;
-    float s = 0.0f;
-    for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s += val[k] * p[col[k]];
-    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-        q[r] = s;
-        atomicAdd(&sc->pq, (double)s * (double)p[r]);
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    double pq = 0.0;
+    if (r < n) {
+        float s = row_dot<float, float>(val, col, p, rp[r], rp[r + 1], lane);
+        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) q[r] = s;
+        pq = (double)s * (double)p[r];
     }
+    block_atomic_add(pq, &sc->pq);
 }
 
 __global__ void k_cg_update(int n, const float *p, const float *q, float *d, float *z, CgScal *sc)
@@ -384,12 +423,21 @@ nl_status nl_matvec(nl_ctx *ctx, const nl_csr *Ac, const double *x, double *y, i
     if (!dev_out) NL_CK(cudaMallocAsync((void **)&yd, sizeof(double) * (n + 1), ctx->stream));
     if (prec == NL_PREC_FP64) {
         k_spmv<double, double, double><<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, A->val,
-                                                                           (const double *)xd, yd); ++ctx->launches;
+                                                                           (const double *)xd, yd);
+        ++ctx->launches;
     } else {
         if ((s = ensure_f32(ctx, A)) != NL_OK) return s;
-        k_spmv<float, double, double><<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx,
-                                                                          ((nl_plan *)A->priv)->val32,
-                                                                          (const double *)xd, yd); ++ctx->launches;
+        nl_plan *P = (nl_plan *)A->priv;
+        // x rounded to FP32 once (the products use FP32 operands either way): no FP64
+        // conversion per stored entry
+        if (!P->x32 && (s = nl_alloc(ctx, &P->x32, (size_t)ncols)) != NL_OK) return s;
+        if (ncols > 0) {
+            k_to_f32<<<(unsigned)((ncols + 255) / 256), 256, 0, ctx->stream>>>(ncols, (const double *)xd, P->x32);
+            ++ctx->launches;
+        }
+        k_spmv<float, float, double><<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, P->val32,
+                                                                         P->x32, yd);
+        ++ctx->launches;
     }
     NL_CK(cudaGetLastError());
     if (!dev_out) {
@@ -397,7 +445,8 @@ nl_status nl_matvec(nl_ctx *ctx, const nl_csr *Ac, const double *x, double *y, i
         NL_CK(cudaFreeAsync(yd, ctx->stream));
     }
     if (ox) NL_CK(cudaFreeAsync(xd, ctx->stream));
-    NL_CK(cudaStreamSynchronize(ctx->stream));
+    // host buffers: the copies must be complete when the call returns; device buffers: stream-ordered
+    if (!dev_out || ox) NL_CK(cudaStreamSynchronize(ctx->stream));
     return NL_OK;
 }
 
@@ -455,7 +504,8 @@ nl_status nl_cg(nl_ctx *ctx, const nl_csr *Ac, const double *b, double *x, doubl
         while (total < max_it) {
             const int chunk = (max_it - total) < kCheck ? (max_it - total) : kCheck;
             for (int c = 0; c < chunk; c++) {
-                k_cg_spmv<<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, v32, p, q, sc); ++ctx->launches;
+                k_cg_spmv<<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, v32, p, q, sc);
+                ++ctx->launches;
                 k_cg_update<<<eg, 256, 0, ctx->stream>>>(n, p, q, d, z, sc); ++ctx->launches;
                 k_cg_dir<<<eg, 256, 0, ctx->stream>>>(n, z, p, sc); ++ctx->launches;
                 k_cg_shift<<<1, 1, 0, ctx->stream>>>(sc); ++ctx->launches;
