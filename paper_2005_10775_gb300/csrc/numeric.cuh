@@ -797,7 +797,8 @@ template <typename T>
 struct BoundaryShared {
     OuterPt sq[NL_MAXQ];
     CandData cand[32];
-    T acc[32][22];             // 21 block values and the non-empty flag of each lane's pair
+    T acc[22][32];             // 21 block values and the non-empty flag of each lane's pair,
+                               // value-major: the owners of one atomic instruction hit distinct banks
     unsigned short queue[32 * NL_MAXQ];    // undecided items (owner lane << 8 | q)
     // whole items from the front; whole items in the singular kernel's near field from the back
     // (a batch holds at most 32 x n_q items in all)
@@ -970,7 +971,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             q0 = c.q0;
             sh.cand[lane] = c;
         }
-        for (int i = 0; i < 22; i++) sh.acc[lane][i] = 0;
+        for (int i = 0; i < 22; i++) sh.acc[i][lane] = 0;
         int nqueue = 0;
         __syncwarp();
         // phase 1: classify every (q, b) in lockstep; queue whole and undecided items
@@ -1020,8 +1021,8 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
-            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[own][k], w[k]);
-            sh.acc[own][21] = (T)1;
+            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
+            sh.acc[21][own] = (T)1;
             acc.cnt++;
             acc.qp += nq;
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
@@ -1041,8 +1042,8 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
-            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[own][k], w[k]);
-            sh.acc[own][21] = (T)1;
+            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
+            sh.acc[21][own] = (T)1;
             acc.cnt++;
             acc.qp += nq;
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
@@ -1065,8 +1066,8 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
-            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[own][k], w[k]);
-            sh.acc[own][21] = (T)1;
+            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
+            sh.acc[21][own] = (T)1;
             acc.cnt++;
             acc.qp += nq;
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
@@ -1075,8 +1076,8 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         // phase 3: owners merge the queue's contributions and write their pair
         if (valid) {
             T v[21];
-            for (int k = 0; k < 21; k++) v[k] = sh.acc[lane][k];
-            write_pair<T>(A, e, sh.acc[lane][21] != (T)0, v, acc);
+            for (int k = 0; k < 21; k++) v[k] = sh.acc[k][lane];
+            write_pair<T>(A, e, sh.acc[21][lane] != (T)0, v, acc);
         }
         __syncwarp();
     }
