@@ -1002,6 +1002,18 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             nnear += __popc(mn);
         }
         __syncwarp();
+        // Float sums: the whole items of one owner sit at neighbouring outer points, and up to
+        // four of them share a round; spreading the outer points over three accumulator copies
+        // (two in the clip buffers, unused until phase 2b) cuts the shared atomics that collide
+        // on one address.  The copies are folded into acc before phase 2b.
+        constexpr bool kCopies = sizeof(T) == sizeof(float);
+        T (*extra)[22][32] = reinterpret_cast<T (*)[22][32]>(&sh.clip);
+        if (kCopies && nwhole > 32)
+            for (int k = 0; k < 21; k++) {
+                extra[0][k][lane] = (T)0;
+                extra[1][k][lane] = (T)0;
+            }
+        __syncwarp();
         // phase 2a: whole items with all lanes
         for (int i = lane; i < nwhole; i += 32) {
             const unsigned it = sh.wqueue[i];
@@ -1021,12 +1033,18 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
-            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
+            const int cp = (kCopies && nwhole > 32) ? q % 3 : 0;
+            T (*dst)[32] = cp == 0 ? sh.acc : extra[cp - 1];
+            for (int k = 0; k < 21; k++) atomicAdd(&dst[k][own], w[k]);
             sh.acc[21][own] = (T)1;
             acc.cnt++;
             acc.qp += nq;
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
         }
+        __syncwarp();
+        if (kCopies && nwhole > 32)
+            for (int k = 0; k < 21; k++) sh.acc[k][lane] += extra[0][k][lane] + extra[1][k][lane];
+        __syncwarp();
         // phase 2c: whole items in the singular kernel's near field (FP32 near rule)
         for (int i = lane; INV && i < nnear; i += 32) {
             const unsigned it = sh.wqueue[kQueueCap - 1 - i];
