@@ -1084,8 +1084,27 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
-            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
-            sh.acc[21][own] = (T)1;
+            // A round holds items of a few neighbouring outer points, so one candidate often owns
+            // several of them: the converged lanes with the same owner sum their blocks by
+            // shuffles, and one lane per owner adds to the shared accumulator.
+            const unsigned am = __activemask();
+            const unsigned peers = __match_any_sync(am, own);
+            const int m = __popc(peers), leader = __ffs(peers) - 1;
+            const int mmax = (int)__reduce_max_sync(am, (unsigned)m);
+            for (int t = 1; t < mmax; t++) {
+                unsigned rest = peers;
+                for (int j = 0; j < t && rest; j++) rest &= rest - 1;
+                const bool take = lane == leader && t < m;
+                const int src = take ? __ffs(rest) - 1 : lane;
+                for (int k = 0; k < 21; k++) {
+                    const T x = __shfl_sync(am, w[k], src);
+                    if (take) w[k] += x;
+                }
+            }
+            if (lane == leader) {
+                for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
+                sh.acc[21][own] = (T)1;
+            }
             acc.cnt++;
             acc.qp += nq;
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
