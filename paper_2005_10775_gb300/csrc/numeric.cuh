@@ -1084,13 +1084,15 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
-            // A round holds items of a few neighbouring outer points, so one candidate often owns
-            // several of them: the converged lanes with the same owner sum their blocks by
-            // shuffles, and one lane per owner adds to the shared accumulator.
+            // N-gon: a round holds items of a few outer points, so one candidate often owns
+            // several of them; the converged lanes with the same owner sum their blocks by
+            // shuffles, and one lane per owner adds to the shared accumulator.  (The disc balls'
+            // cheaper regions do not repay the shuffles.)
+            constexpr bool kAggregate = BALL == NL_BALL_NGON;
             const unsigned am = __activemask();
-            const unsigned peers = __match_any_sync(am, own);
+            const unsigned peers = kAggregate ? __match_any_sync(am, own) : (1u << lane);
             const int m = __popc(peers), leader = __ffs(peers) - 1;
-            const int mmax = (int)__reduce_max_sync(am, (unsigned)m);
+            const int mmax = kAggregate ? (int)__reduce_max_sync(am, (unsigned)m) : 1;
             for (int t = 1; t < mmax; t++) {
                 unsigned rest = peers;
                 for (int j = 0; j < t && rest; j++) rest &= rest - 1;
