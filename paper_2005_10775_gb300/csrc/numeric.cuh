@@ -931,6 +931,32 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
     return true;
 }
 
+// Add a block w (21 values) to owner own's column of the shared accumulator.  The converged
+// lanes with the same owner first sum their blocks by shuffles (the leader takes its peers'
+// values one by one), so one lane per owner adds: no shared atomics colliding on one address.
+template <typename T>
+__device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane, T *w)
+{
+    const unsigned am = __activemask();
+    const unsigned peers = __match_any_sync(am, own);
+    const int m = __popc(peers), leader = __ffs(peers) - 1;
+    const int mmax = (int)__reduce_max_sync(am, (unsigned)m);
+    for (int t = 1; t < mmax; t++) {
+        unsigned rest = peers;
+        for (int j = 0; j < t && rest; j++) rest &= rest - 1;
+        const bool take = lane == leader && t < m;
+        const int src = take ? __ffs(rest) - 1 : lane;
+        for (int k = 0; k < 21; k++) {
+            const T x = __shfl_sync(am, w[k], src);
+            if (take) w[k] += x;
+        }
+    }
+    if (lane == leader) {
+        for (int k = 0; k < 21; k++) atomicAdd(&accum[k][own], w[k]);
+        accum[21][own] = (T)1;
+    }
+}
+
 // Queue an item for k_deferred: false (the caller runs the FP64 code itself) for FP64 sums,
 // without a queue, or when the queue is full.
 template <typename T>
@@ -1060,8 +1086,9 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
-            for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
-            sh.acc[21][own] = (T)1;
+            // an owner lies in the near field of several outer points of one round: the lanes
+            // with the same owner sum their blocks by shuffles, one lane per owner adds
+            warp_owner_add<T>(sh.acc, own, lane, w);
             acc.cnt++;
             acc.qp += nq;
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
@@ -1085,25 +1112,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
             // N-gon: a round holds items of a few outer points, so one candidate often owns
-            // several of them; the converged lanes with the same owner sum their blocks by
-            // shuffles, and one lane per owner adds to the shared accumulator.  (The disc balls'
-            // cheaper regions do not repay the shuffles.)
-            constexpr bool kAggregate = BALL == NL_BALL_NGON;
-            const unsigned am = __activemask();
-            const unsigned peers = kAggregate ? __match_any_sync(am, own) : (1u << lane);
-            const int m = __popc(peers), leader = __ffs(peers) - 1;
-            const int mmax = kAggregate ? (int)__reduce_max_sync(am, (unsigned)m) : 1;
-            for (int t = 1; t < mmax; t++) {
-                unsigned rest = peers;
-                for (int j = 0; j < t && rest; j++) rest &= rest - 1;
-                const bool take = lane == leader && t < m;
-                const int src = take ? __ffs(rest) - 1 : lane;
-                for (int k = 0; k < 21; k++) {
-                    const T x = __shfl_sync(am, w[k], src);
-                    if (take) w[k] += x;
-                }
-            }
-            if (lane == leader) {
+            // several of them (the disc balls' cheaper regions do not repay the shuffles)
+            if (BALL == NL_BALL_NGON) {
+                warp_owner_add<T>(sh.acc, own, lane, w);
+            } else {
                 for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
                 sh.acc[21][own] = (T)1;
             }
