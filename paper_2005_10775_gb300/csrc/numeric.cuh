@@ -931,13 +931,14 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
     return true;
 }
 
-// Add a block w (21 values) to owner own's column of the shared accumulator.  The converged
-// lanes with the same owner first sum their blocks by shuffles (the leader takes its peers'
+// Add a block w (21 values) to owner own's column of the shared accumulator; am = the lanes of
+// the round that add a block (all of them call this).  Lanes with the same owner first sum
+// their blocks by shuffles (the leader takes its peers'
 // values one by one), so one lane per owner adds: no shared atomics colliding on one address.
 template <typename T>
-__device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane, T *w)
+__device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane, T *w, unsigned am)
 {
-    const unsigned am = __activemask();
+    __syncwarp(am);
     const unsigned peers = __match_any_sync(am, own);
     const int m = __popc(peers), leader = __ffs(peers) - 1;
     const int mmax = (int)__reduce_max_sync(am, (unsigned)m);
@@ -1073,6 +1074,8 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         __syncwarp();
         // phase 2c: whole items in the singular kernel's near field (FP32 near rule)
         for (int i = lane; INV && i < nnear; i += 32) {
+            const int left = nnear - (i - lane);   // items of this round
+            const unsigned rmask = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
             const unsigned it = sh.wqueue[kQueueCap - 1 - i];
             const int own = it >> 8, q = it & 0xff;
             const CandData &cd = sh.cand[own];
@@ -1088,7 +1091,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             combine<T>(o, S, w);
             // an owner lies in the near field of several outer points of one round: the lanes
             // with the same owner sum their blocks by shuffles, one lane per owner adds
-            warp_owner_add<T>(sh.acc, own, lane, w);
+            warp_owner_add<T>(sh.acc, own, lane, w, rmask);
             acc.cnt++;
             acc.qp += nq;
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
@@ -1114,7 +1117,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             // N-gon: a round holds items of a few outer points, so one candidate often owns
             // several of them (the disc balls' cheaper regions do not repay the shuffles)
             if (BALL == NL_BALL_NGON) {
-                warp_owner_add<T>(sh.acc, own, lane, w);
+                warp_owner_add<T>(sh.acc, own, lane, w, __activemask());   // the lanes converged here
             } else {
                 for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
                 sh.acc[21][own] = (T)1;
