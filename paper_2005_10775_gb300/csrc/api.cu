@@ -204,12 +204,22 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     A.duffy_n = c.kernel == NL_KERNEL_INV_DIST ? c.duffy_n : 1;
     gauss_legendre01(A.duffy_n, A.gl_x, A.gl_w);
     gauss_legendre01(2, A.gl2_x, A.gl2_w);
+    for (int j = 0; j < 8; j++) {
+        A.glf_x[j] = j < A.duffy_n ? (float)A.gl_x[j] : 0.f;
+        A.glf_w[j] = j < A.duffy_n ? (float)A.gl_w[j] : 0.f;
+    }
+    for (int j = 0; j < 2; j++) {
+        A.gl2f_x[j] = (float)A.gl2_x[j];
+        A.gl2f_w[j] = (float)A.gl2_w[j];
+    }
     A.kernel = c.kernel;
     A.ball = c.ball;
     A.shifted = c.shifted ? 1 : 0;
     A.outer_support = (c.ball == NL_BALL_BARY_NOCAPS || c.ball == NL_BALL_BARY_APPROXCAPS) ? 1 : 0;
     A.kc = c.kernel_c;
+    A.kcf = (float)c.kernel_c;
     A.geo.delta = c.delta;
+    A.geo.deltaf = (float)c.delta;
     A.geo.d2 = P->d2;
     A.geo.ngon = P->ngon;
     A.geo.ngon_n = c.ball == NL_BALL_NGON ? c.ngon_n : 0;

@@ -68,6 +68,7 @@ struct GeoParams {
     float r2;             // 2 max_k |o_k|_1
     float o1max;          // max_k |o_k|_1
     float sector, rin_tau; // 2 pi / N; inradius - tau
+    float deltaf;          // delta in FP32
 };
 
 // atan2 from the arctangent polynomial of Abramowitz & Stegun 4.4.49 (Hastings): on [0, 1]
@@ -592,7 +593,7 @@ constexpr int kBallCap = 16;   // FP32 region vertices (nocaps <= 6; approxcaps 
 template <int BALL>
 __device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g, F2 P[kBallCap], int *kind)
 {
-    const float delta = (float)g.delta, d2f = delta * delta;
+    const float delta = g.deltaf, d2f = delta * delta;
     bool ins[3];
     int nin = 0;
 #pragma unroll

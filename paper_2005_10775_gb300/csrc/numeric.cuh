@@ -53,6 +53,9 @@ struct NumArgs {
     float4 fout[NL_MAXQ + 8];         // outer rule in FP32 (the outer-support composite rule)
     double gl_x[8], gl_w[8];          // Gauss-Legendre on [0,1] with duffy_n points
     double gl2_x[2], gl2_w[2];
+    float glf_x[8], glf_w[8];         // the same rules in FP32 (no FP64 conversions in the FP32 path)
+    float gl2f_x[2], gl2f_w[2];
+    float kcf;                        // kc in FP32
     int duffy_n;
     int switch47;                     // outer rule: 0..nsplit-1 if |bary_a - bary_b|^2 < thr2 else nsplit..n-1
     double thr2;                      // (delta - h_max)^2, or -1 when delta <= h_max
@@ -353,7 +356,7 @@ __device__ __forceinline__ void poly_sums_f32(const NumArgs &A, const nlg::F2 *P
 {
     sums_zero(S);
     const int nr = A.inner.n;
-    const float kc = (float)A.kc;
+    const float kc = A.kcf;
     auto phi = [&](const nlg::F2 &p, float f[3]) {
         const float rx = p.x - d0.x, ry = p.y - d0.y;
         const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
@@ -395,7 +398,7 @@ __device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBu
 {
     sums_zero(S);
     const int nr = A.inner.n;
-    const float kc = (float)A.kc;
+    const float kc = A.kcf;
     auto phi = [&](float px, float py, float f[3]) {
         const float rx = px - d0.x, ry = py - d0.y;
         const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
@@ -442,7 +445,7 @@ __device__ __forceinline__ void near_whole_f32(const NumArgs &A, const nlg::F2 d
                                                Sums<float> &S, int64_t &nqp)
 {
     sums_zero(S);
-    const float kc = (float)A.kc;
+    const float kc = A.kcf;
     const int nu = A.duffy_n;
     for (int i = 0; i < 3; i++) {
         const nlg::F2 a = dl[i], b = dl[(i + 1) % 3];
@@ -492,16 +495,16 @@ __device__ __forceinline__ void near_whole_f32(const NumArgs &A, const nlg::F2 d
                 const float u0 = (float)pnl, u1 = (pnl + 1 < npan) ? (float)(pnl + 1) : fmaxf(U, u0);
                 const float hw = u1 - u0;
                 for (int j = 0; j < nu; j++) {
-                    const float u = u0 + hw * (float)A.gl_x[j];
-                    const float wu = hw * (float)A.gl_w[j];
+                    const float u = u0 + hw * A.glf_x[j];
+                    const float wu = hw * A.glf_w[j];
                     const float sh = sinhf(u);
                     const float wx = Fx + sg * d * sh * ex, wy = Fy + sg * d * sh * ey;
                     for (int k = 0; k < 2; k++) {
-                        const float sv = (float)A.gl2_x[k];
+                        const float sv = A.gl2f_x[k];
                         const float rx = sv * wx - dl[0].x, ry = sv * wy - dl[0].y;
                         const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
                         const float l2 = (e1.x * ry - rx * e1.y) * inv_det;
-                        sums_add<float>(S, sign * sg * d * (float)A.gl2_w[k] * wu * kc, 1.f - l1 - l2, l1, l2);
+                        sums_add<float>(S, sign * sg * d * A.gl2f_w[k] * wu * kc, 1.f - l1 - l2, l1, l2);
                         nqp++;
                     }
                 }
