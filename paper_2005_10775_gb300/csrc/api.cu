@@ -183,6 +183,7 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     A.by = P->by;
     A.area = P->area;
     A.akc = P->akc;
+    A.hl = P->hl;
     A.nbr_ptr = P->nbr_ptr;
     A.nbr_split = P->nbr_split;
     A.nbr_idx = P->nbr_idx;
@@ -270,7 +271,9 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
         A.geo.sector = (float)(2.0 * M_PI / N);
         A.geo.rin_tau = (float)(rin - tau);
     }
-    // FP32 local coordinates v - x are rounded differences of magnitude <= delta + 4 r_max
+    // FP32 local coordinates d = v - x: (v - bary_a) from FP32 hi + lo pairs (within 2u |v - bary_a|,
+    // |v - bary_a| <= delta + 3 r_max), minus (x - bary_a) rounded from FP64 (within u r_max), rounded
+    // (u |d|, |d| <= delta + 4 r_max): in all u (3 delta + 11 r_max) <= 4u (delta + 4 r_max)
     A.geo.err0 = (float)(4.0 * 5.9604644775390625e-8 * (c.delta + 4.0 * P->rmax));
     A.geo.rin_m2 = rin - tau > 0.0 ? (float)((rin - tau) * (rin - tau)) : -1.0f;
     A.geo.rout_p2 = (float)((rout + tau) * (rout + tau));
@@ -343,7 +346,7 @@ void nl_plan_free(nl_plan *P, cudaStream_t s)
 {
     if (!P) return;
     nl_free(P->tri, s); nl_free(P->tx, s); nl_free(P->ty, s); nl_free(P->bx, s); nl_free(P->by, s);
-    nl_free(P->rad, s); nl_free(P->area, s); nl_free(P->akc, s); nl_free(P->ngon, s); nl_free(P->nbr_ptr, s); nl_free(P->nbr_idx, s);
+    nl_free(P->rad, s); nl_free(P->area, s); nl_free(P->akc, s); nl_free(P->hl, s); nl_free(P->ngon, s); nl_free(P->nbr_ptr, s); nl_free(P->nbr_idx, s);
     nl_free(P->nbr_split, s); nl_free(P->flag, s); nl_free(P->blk, s); nl_free(P->maa, s); nl_free(P->qp_a, s);
     nl_free(P->cnt_a, s); nl_free(P->hash_a, s); nl_free(P->lslot, s); nl_free(P->mbb, s); nl_free(P->tslot, s); nl_free(P->W, s);
     nl_free(P->val32, s); nl_free(P->x32, s); nl_free(P->err, s); nl_free(P->defer, s); nl_free(P->defer_n, s);

@@ -59,6 +59,7 @@ struct nl_plan {
     double *tx = nullptr, *ty = nullptr;   // [3][K] vertex coordinates per triangle
     double *bx = nullptr, *by = nullptr, *rad = nullptr, *area = nullptr;  // [K]
     float *akc = nullptr;         // [K] |T| times the kernel constant, rounded to FP32
+    float *hl = nullptr;          // [16][K] vertex coordinates and barycentre as FP32 hi + lo pairs
     double *ngon = nullptr;       // [2 ngon_n]
     std::vector<double> ngon_host; // host copy of the polygon offsets
     // candidates

@@ -120,6 +120,30 @@ __global__ void k_prepare(int K, int J, const int32_t *__restrict__ tri, const d
     if (!(cr > 0.0)) atomicAdd(bad, 1);
 }
 
+// Every FP64 coordinate v as an FP32 pair hi = fl32(v), lo = fl32(v - hi) (v - hi is exact in
+// FP64), so that FP32 differences of nearby points keep their FP64 accuracy: rows 0-2 / 3-5 hold
+// hi / lo of the vertices' x, rows 6-8 / 9-11 of their y, rows 12-15 bary x hi, lo, y hi, lo.
+__global__ void k_hilo(int K, const double *tx, const double *ty, const double *bx, const double *by, float *hl)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= K) return;
+    auto put = [&](int row, double v) {
+        const float h = (float)v;
+        hl[(int64_t)row * K + t] = h;
+        hl[(int64_t)(row + 3) * K + t] = (float)(v - (double)h);
+    };
+    for (int i = 0; i < 3; i++) {
+        put(i, tx[(int64_t)i * K + t]);
+        put(6 + i, ty[(int64_t)i * K + t]);
+    }
+    const double b[2] = {bx[t], by[t]};
+    for (int i = 0; i < 2; i++) {
+        const float h = (float)b[i];
+        hl[(int64_t)(12 + 2 * i) * K + t] = h;
+        hl[(int64_t)(13 + 2 * i) * K + t] = (float)(b[i] - (double)h);
+    }
+}
+
 struct MeshStats {
     double xmin, xmax, ymin, ymax, rmax, hmax;
 };
@@ -519,6 +543,7 @@ nl_status nl_prepare_a(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, n
     if ((s = nl_alloc(ctx, &P->rad, K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->area, K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->akc, K)) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &P->hl, 16 * (size_t)K)) != NL_OK) return s;
     if (cfg->ball == NL_BALL_NGON) {
         const size_t nb = sizeof(double) * 2 * cfg->ngon_n;
         P->ngon_host.resize(2 * (size_t)cfg->ngon_n);
@@ -542,6 +567,7 @@ nl_status nl_prepare_a(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, n
                                                         (const double *)T->dvy, P->tx, P->ty, P->bx, P->by,
                                                         P->rad, P->area, T->diam, T->cf, cfg->kernel_c, P->akc,
                                                         T->bad); ++ctx->launches;
+    k_hilo<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->tx, P->ty, P->bx, P->by, P->hl); ++ctx->launches;
     NL_CK(cudaGetLastError());
     k_mesh_stats<<<1, 1024, 0, ctx->stream>>>(K, P->bx, P->by, P->rad, T->diam, T->st); ++ctx->launches;
     NL_CK(cudaGetLastError());

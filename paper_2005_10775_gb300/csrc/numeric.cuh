@@ -46,6 +46,7 @@ struct NumArgs {
     const double *tx, *ty;            // [3][K]
     const double *bx, *by, *area;     // [K]
     const float *akc;                 // [K] |T| kc in FP32
+    const float *hl;                  // [16][K] coordinates as FP32 hi + lo pairs (k_hilo)
     const int64_t *nbr_ptr, *nbr_split;
     const int32_t *nbr_idx;
     RuleTab outer, inner;
@@ -750,23 +751,44 @@ struct CandFp64 {
     double area;
 };
 
-// FP32 data of candidate T_b relative to bary_a (ba) and the outer-rule range [c.q0, q1) of the pair
-__device__ __forceinline__ void load_cand(const NumArgs &A, int b, const D2 &ba, CandData &c, int &q1)
+// bary_a as FP32 hi + lo pairs (x hi, x lo, y hi, y lo)
+__device__ __forceinline__ float4 bary_hilo(const NumArgs &A, int a)
 {
-    const int K = A.K;
+    const int64_t K = A.K;
+    return make_float4(A.hl[12 * K + a], A.hl[13 * K + a], A.hl[14 * K + a], A.hl[15 * K + a]);
+}
+
+// FP32 data of candidate T_b relative to bary_a (ba, and bah its hi + lo pairs) and the
+// outer-rule range [c.q0, q1) of the pair.  Each FP32 difference is (hi - hi) + (lo - lo): within
+// 2u of the difference of the FP64 values (u = 2^-24), with no FP64 arithmetic.
+__device__ __forceinline__ void load_cand(const NumArgs &A, int b, const D2 &ba, const float4 &bah, CandData &c,
+                                          int &q1)
+{
+    const int64_t K = A.K;
+    const float *H = A.hl;
     c.b = b;
-    double vx[3], vy[3];
-    for (int i = 0; i < 3; i++) { vx[i] = A.tx[i * K + b]; vy[i] = A.ty[i * K + b]; }
-    const D2 bb = {A.bx[b], A.by[b]};
+    float xh[3], xl[3], yh[3], yl[3];
+    for (int i = 0; i < 3; i++) {
+        xh[i] = H[i * K + b];
+        xl[i] = H[(3 + i) * K + b];
+        yh[i] = H[(6 + i) * K + b];
+        yl[i] = H[(9 + i) * K + b];
+    }
     c.akcf = A.akc[b];
-    for (int i = 0; i < 3; i++) { c.vlx[i] = (float)(vx[i] - ba.x); c.vly[i] = (float)(vy[i] - ba.y); }
-    c.blx = (float)(bb.x - ba.x);
-    c.bly = (float)(bb.y - ba.y);
-    c.e1x = (float)(vx[1] - vx[0]); c.e1y = (float)(vy[1] - vy[0]);
-    c.e2x = (float)(vx[2] - vx[0]); c.e2y = (float)(vy[2] - vy[0]);
+    for (int i = 0; i < 3; i++) {
+        c.vlx[i] = (xh[i] - bah.x) + (xl[i] - bah.y);
+        c.vly[i] = (yh[i] - bah.z) + (yl[i] - bah.w);
+    }
+    c.blx = (H[12 * K + b] - bah.x) + (H[13 * K + b] - bah.y);
+    c.bly = (H[14 * K + b] - bah.z) + (H[15 * K + b] - bah.w);
+    c.e1x = (xh[1] - xh[0]) + (xl[1] - xl[0]);
+    c.e1y = (yh[1] - yh[0]) + (yl[1] - yl[0]);
+    c.e2x = (xh[2] - xh[0]) + (xl[2] - xl[0]);
+    c.e2y = (yh[2] - yh[0]) + (yl[2] - yl[0]);
     c.binv = 1.f / (c.e1x * c.e2y - c.e2x * c.e1y);
-    int q0;
-    rule_range(A, ba, bb, q0, q1);
+    int q0 = 0;
+    q1 = A.outer.n;
+    if (A.switch47) rule_range(A, ba, D2{A.bx[b], A.by[b]}, q0, q1);
     c.q0 = q0;
 }
 
@@ -981,6 +1003,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
 {
     const int K = A.K;
     const D2 ba = {A.bx[a], A.by[a]};
+    const float4 bah = bary_hilo(A, a);
     const int64_t es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
     const int nq_all = A.outer.n;
     const bool inv = INV;
@@ -997,7 +1020,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
                 b = a;
             }
 #endif
-            load_cand(A, b, ba, c, q1);
+            load_cand(A, b, ba, bah, c, q1);
             q0 = c.q0;
             sh.cand[lane] = c;
         }
@@ -1386,7 +1409,7 @@ __device__ __forceinline__ void deferred_item(const NumArgs &A, const DeferItem 
     const D2 ba = {A.bx[a], A.by[a]};
     CandData c;
     int q1;
-    load_cand(A, b, ba, c, q1);
+    load_cand(A, b, ba, bary_hilo(A, a), c, q1);
     Sums<float> S;
     int64_t nq = 0;
     int kind, nv, ncap;
