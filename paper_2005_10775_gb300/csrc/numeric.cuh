@@ -609,22 +609,29 @@ __device__ __forceinline__ void combine(const OuterPt &o, const Sums<T> &S, T *v
     v[18] += ws * la0 * la1; v[19] += ws * la0 * la2; v[20] += ws * la1 * la2;
 }
 
+// M_aa contributions m[0..5] into the lane's sums of its outer triangle
+template <typename T>
+__device__ __forceinline__ void maa_add(LaneAcc &acc, const T *m)
+{
+    if (sizeof(T) == sizeof(float)) {
+        for (int i = 0; i < 6; i++) {
+            const float y = (float)m[i] - acc.mc[i];
+            const float t = acc.mf[i] + y;
+            acc.mc[i] = (t - acc.mf[i]) - y;
+            acc.mf[i] = t;
+        }
+    } else {
+        for (int i = 0; i < 6; i++) acc.maa[i] += (double)m[i];
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void write_pair(const NumArgs &A, int64_t e, bool any, const T *v, LaneAcc &acc)
 {
     A.flag[e] = any ? 1 : 0;
     T *blk = (T *)A.blk;
     for (int i = 0; i < 15; i++) blk[(int64_t)i * A.E + e] = v[i];
-    if (sizeof(T) == sizeof(float)) {
-        for (int i = 0; i < 6; i++) {
-            const float y = (float)v[15 + i] - acc.mc[i];
-            const float t = acc.mf[i] + y;
-            acc.mc[i] = (t - acc.mf[i]) - y;
-            acc.mf[i] = t;
-        }
-    } else {
-        for (int i = 0; i < 6; i++) acc.maa[i] += (double)v[15 + i];
-    }
+    maa_add<T>(acc, v + 15);
 }
 
 __device__ __forceinline__ void warp_reduce(LaneAcc &acc)
@@ -822,7 +829,8 @@ template <typename T>
 struct BoundaryShared {
     OuterPt sq[NL_MAXQ];
     CandData cand[32];
-    T acc[22][32];             // 21 block values and the non-empty flag of each lane's pair,
+    T acc[22][32];             // 21 block values and the non-empty flag of each lane's pair (for
+                               // the disc balls rows 15-20, M_aa, are per integrating lane instead),
                                // value-major: the owners of one atomic instruction hit distinct banks
     unsigned short queue[32 * NL_MAXQ];    // undecided items (owner lane << 8 | q)
     // whole items from the front; whole items in the singular kernel's near field from the back
@@ -956,11 +964,11 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
     return true;
 }
 
-// Add a block w (21 values) to owner own's column of the shared accumulator; am = the lanes of
+// Add a block w (its first NV values) to owner own's column of the shared accumulator; am = the lanes of
 // the round that add a block (all of them call this).  Lanes with the same owner first sum
 // their blocks by shuffles (the leader takes its peers'
 // values one by one), so one lane per owner adds: no shared atomics colliding on one address.
-template <typename T>
+template <typename T, int NV>
 __device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane, T *w, unsigned am)
 {
     __syncwarp(am);
@@ -972,13 +980,13 @@ __device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane
         for (int j = 0; j < t && rest; j++) rest &= rest - 1;
         const bool take = lane == leader && t < m;
         const int src = take ? __ffs(rest) - 1 : lane;
-        for (int k = 0; k < 21; k++) {
+        for (int k = 0; k < NV; k++) {
             const T x = __shfl_sync(am, w[k], src);
             if (take) w[k] += x;
         }
     }
     if (lane == leader) {
-        for (int k = 0; k < 21; k++) atomicAdd(&accum[k][own], w[k]);
+        for (int k = 0; k < NV; k++) atomicAdd(&accum[k][own], w[k]);
         accum[21][own] = (T)1;
     }
 }
@@ -1005,6 +1013,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
     const D2 ba = {A.bx[a], A.by[a]};
     const float4 bah = bary_hilo(A, a);
     const int64_t es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
+    // M_aa belongs to the outer triangle, not to the pair: except for the N-gon (whose rounds
+    // aggregate whole blocks by shuffles), each lane sums the M_aa of the items it integrates in
+    // its own column of rows 15-20 (plain adds), and only M_ab and M_bb take shared atomics
+    constexpr bool kLaneMaa = BALL != NL_BALL_NGON;
     const int nq_all = A.outer.n;
     const bool inv = INV;
     for (int64_t base = es; base < e1; base += 32) {
@@ -1088,7 +1100,12 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             combine<T>(o, S, w);
             const int cp = (kCopies && nwhole > 32) ? q % 3 : 0;
             T (*dst)[32] = cp == 0 ? sh.acc : extra[cp - 1];
-            for (int k = 0; k < 21; k++) atomicAdd(&dst[k][own], w[k]);
+            if (kLaneMaa) {
+                for (int k = 0; k < 15; k++) atomicAdd(&dst[k][own], w[k]);
+                for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
+            } else {
+                for (int k = 0; k < 21; k++) atomicAdd(&dst[k][own], w[k]);
+            }
             sh.acc[21][own] = (T)1;
             acc.cnt++;
             acc.qp += nq;
@@ -1117,7 +1134,9 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             combine<T>(o, S, w);
             // an owner lies in the near field of several outer points of one round: the lanes
             // with the same owner sum their blocks by shuffles, one lane per owner adds
-            warp_owner_add<T>(sh.acc, own, lane, w, rmask);
+            if (kLaneMaa)
+                for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
+            warp_owner_add<T, kLaneMaa ? 15 : 21>(sh.acc, own, lane, w, rmask);
             acc.cnt++;
             acc.qp += nq;
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
@@ -1143,9 +1162,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             // N-gon: a round holds items of a few outer points, so one candidate often owns
             // several of them (the disc balls' cheaper regions do not repay the shuffles)
             if (BALL == NL_BALL_NGON) {
-                warp_owner_add<T>(sh.acc, own, lane, w, __activemask());   // the lanes converged here
+                warp_owner_add<T, 21>(sh.acc, own, lane, w, __activemask());   // the lanes converged here
             } else {
-                for (int k = 0; k < 21; k++) atomicAdd(&sh.acc[k][own], w[k]);
+                for (int k = 0; k < 15; k++) atomicAdd(&sh.acc[k][own], w[k]);
+                for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
                 sh.acc[21][own] = (T)1;
             }
             acc.cnt++;
@@ -1158,6 +1178,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T v[21];
             for (int k = 0; k < 21; k++) v[k] = sh.acc[k][lane];
             write_pair<T>(A, e, sh.acc[21][lane] != (T)0, v, acc);
+        } else if (kLaneMaa) {   // a lane without a candidate in this batch may have integrated items
+            T m[6];
+            for (int k = 0; k < 6; k++) m[k] = sh.acc[15 + k][lane];
+            maa_add<T>(acc, m);
         }
         __syncwarp();
     }
