@@ -721,9 +721,9 @@ __device__ __forceinline__ void finish_outer(const NumArgs &A, int a, LaneAcc &a
     }
 }
 
-// five resident 4-warp blocks per SM with float sums (96 registers), four with double sums
+// five resident 4-warp blocks per SM with float sums (96 registers); double sums unconstrained
 template <typename T>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float) ? 5 : 4) k_interior(const NumArgs A)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float) ? 5 : 1) k_interior(const NumArgs A)
 {
     __shared__ OuterPt sq_all[kWarpsPerBlock][NL_MAXQ + 8];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1356,7 +1356,7 @@ __device__ __forceinline__ int next_item(int *counter, int lane)
 
 // interior candidates of every problem (stores M_aa and the statistics, as k_interior)
 template <typename T>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float) ? 5 : 4)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float) ? 5 : 1)
     k_interior_batch(const NumArgs *__restrict__ As, const BatchItem *__restrict__ items, int n_items, int *counter)
 {
     __shared__ OuterPt sq_all[kWarpsPerBlock][NL_MAXQ + 8];
