@@ -464,13 +464,33 @@ __device__ __forceinline__ float dist2_origin_triangle(const F2 d[3])
 
 // rin: radius of the disc that lies inside the kept region for sure (delta, or the
 // polygon's inradius); rout: radius of a disc containing it (delta)
+// The triangle with vertices d (relative to the origin, every vertex farther than sqrt(r2))
+// lies farther than sqrt(r2) from the origin: the origin is outside it and no edge comes closer.
+// An edge p -> q whose closest point is interior (0 < n = -p.e < e.e) is at squared distance
+// |p|^2 - n^2 / e.e; the test multiplies through by e.e (no division).
+__device__ __forceinline__ bool triangle_beyond(const F2 d[3], float r2)
+{
+    const float o0 = d[0].x * d[1].y - d[0].y * d[1].x;
+    const float o1 = d[1].x * d[2].y - d[1].y * d[2].x;
+    const float o2 = d[2].x * d[0].y - d[2].y * d[0].x;
+    if (o0 >= 0.f && o1 >= 0.f && o2 >= 0.f) return false;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const F2 p = d[i], q = d[(i + 1) % 3];
+        const float ex = q.x - p.x, ey = q.y - p.y;
+        const float n = -(p.x * ex + p.y * ey), ee = ex * ex + ey * ey;
+        if (n > 0.f && n < ee && (p.x * p.x + p.y * p.y) * ee - n * n <= r2 * ee) return false;
+    }
+    return true;
+}
+
 __device__ __forceinline__ int classify_vertices(const F2 d[3], float rin_m2, float rout_p2)
 {
     float r0 = d[0].x * d[0].x + d[0].y * d[0].y;
     float r1 = d[1].x * d[1].x + d[1].y * d[1].y;
     float r2 = d[2].x * d[2].x + d[2].y * d[2].y;
     if (fmaxf(r0, fmaxf(r1, r2)) <= rin_m2) return CLS_WHOLE;
-    if (fminf(r0, fminf(r1, r2)) > rout_p2 && dist2_origin_triangle(d) > rout_p2) return CLS_EMPTY;
+    if (fminf(r0, fminf(r1, r2)) > rout_p2 && triangle_beyond(d, rout_p2)) return CLS_EMPTY;
     return CLS_EXACT;
 }
 
