@@ -637,20 +637,23 @@ __device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g
         const float a = ex * ex + ey * ey, b = p.x * ex + p.y * ey, c = p.x * p.x + p.y * p.y - d2f;
         int nr;
         if (!ins[i] && !qin) {
-            // out -> out: closest point of the segment to x
-            const float t = fminf(fmaxf(-b / a, 0.f), 1.f);
-            const float cx = p.x + t * ex, cy = p.y + t * ey, r = cx * cx + cy * cy;
-            if (r <= g.rin_m2) nr = 2;
-            else if (r > g.rout_p2) nr = 0;
+            // out -> out: the closest point of the segment to x is interior when 0 < -b < a, at
+            // squared distance |p|^2 - b^2 / a (compared multiplied through by a); at an end
+            // point it is that (outside) vertex
+            const float pa = (p.x * p.x + p.y * p.y) * a - b * b;
+            if (!(-b > 0.f && -b < a)) nr = 0;
+            else if (pa <= g.rin_m2 * a) nr = 2;
+            else if (pa > g.rout_p2 * a) nr = 0;
             else return -1;
         } else {
             nr = 1;
         }
         if (nr == 0) continue;
-        // roots of a l^2 + 2 b l + c = 0 without cancellation
+        // roots of a l^2 + 2 b l + c = 0 without cancellation (coordinates only: the fast
+        // division's few-ulp error stays in the FP32 values)
         const float sq = sqrtf(fmaxf(b * b - a * c, 0.f));
         const float tt = b > 0.f ? -(b + sq) : (sq - b);
-        float l1 = tt / a, l2 = c / tt;
+        float l1 = __fdividef(tt, a), l2 = __fdividef(c, tt);
         if (l1 > l2) { const float z = l1; l1 = l2; l2 = z; }
         if (nr == 2 || !ins[i]) {   // entry at the smaller root
             W[n].x = p.x + l1 * ex; W[n].y = p.y + l1 * ey; tag[n] = 1; n++;
