@@ -703,9 +703,28 @@ __device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g
 // error of either); otherwise the FP64 test decides.  Returns 0 far, 1 near, -1 undecided.
 __device__ __forceinline__ int near_f32(const F2 dl[3], float diamf, float eta)
 {
-    const float dist = sqrtf(dist2_origin_triangle(dl));
-    if (dist > diamf + eta) return 0;
-    if (dist < diamf - eta) return 1;
+    // dist = min over the edges of the distance from x (the origin) to the edge, 0 when x is
+    // inside; each edge's squared distance is compared multiplied through by |e|^2 (no division)
+    const float F = diamf + eta, Nr = diamf - eta, F2v = F * F, N2v = Nr > 0.f ? Nr * Nr : 0.f;
+    const float o0 = dl[0].x * dl[1].y - dl[0].y * dl[1].x;
+    const float o1 = dl[1].x * dl[2].y - dl[1].y * dl[2].x;
+    const float o2 = dl[2].x * dl[0].y - dl[2].y * dl[0].x;
+    if (o0 >= 0.f && o1 >= 0.f && o2 >= 0.f) return Nr > 0.f ? 1 : -1;   // x inside: dist 0
+    bool all_far = true, any_near = false;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const F2 p = dl[i], q = dl[(i + 1) % 3];
+        const float ex = q.x - p.x, ey = q.y - p.y;
+        const float n = -(p.x * ex + p.y * ey), ee = ex * ex + ey * ey;
+        float num, den;   // squared distance num / den
+        if (n <= 0.f) { num = p.x * p.x + p.y * p.y; den = 1.f; }
+        else if (n >= ee) { num = q.x * q.x + q.y * q.y; den = 1.f; }
+        else { num = (p.x * p.x + p.y * p.y) * ee - n * n; den = ee; }
+        all_far = all_far && num > F2v * den;
+        any_near = any_near || num < N2v * den;
+    }
+    if (all_far) return 0;
+    if (any_near) return 1;
     return -1;
 }
 

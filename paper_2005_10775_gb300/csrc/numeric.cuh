@@ -869,7 +869,7 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
 // FP32 region and quadrature of one undecided (q, b): 1 done (S holds its sums), 0 empty
 // region, -1 the FP64 geometry decides (the singular kernel's near field, an uncertified
 // FP32 choice, FP64 sums or a ball without an FP32 region)
-template <int BALL, typename T>
+template <int BALL, typename T, bool INV>
 __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
                                               int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb, int lane)
 {
@@ -878,7 +878,7 @@ __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &
         for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
         // the singular kernel's near field needs the FP64 path; a region inside T_b is far
         // when T_b is (certified in FP32)
-        if (A.kernel == NL_KERNEL_INV_DIST && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
+        if (INV && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
             return -1;
         bool cut = false;
         int which = 0;
@@ -902,7 +902,7 @@ __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &
     if (sizeof(T) == sizeof(float) && (BALL == NL_BALL_NOCAPS || BALL == NL_BALL_APPROXCAPS)) {
         nlg::F2 dl[3];
         for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
-        if (A.kernel == NL_KERNEL_INV_DIST && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
+        if (INV && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
             return -1;
         nlg::F2 P[nlg::kBallCap];
         int k = nlg::KIND_PARTIAL;
@@ -1151,7 +1151,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             Sums<T> S;
             int64_t nq = 0;
             int kind, nv, ncap;
-            int r = exact_item_f32<BALL, T>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane);
+            int r = exact_item_f32<BALL, T, INV>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane);
             if (r < 0) {
                 if (defer_item<T>(A, base + own, a, q)) continue;
                 r = exact_item_fp64<BALL, T>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane) ? 1 : 0;
