@@ -740,9 +740,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float
 
 // ---------------------------------------------------------------------------
 // Boundary pairs.  32 candidates at a time (one per lane): every (q, b) is classified
-// in FP32 in lockstep, whole ones are integrated in place, undecided ones go to a warp
-// queue that all 32 lanes then drain together (geometry + quadrature), adding their
-// blocks into the owner lane's shared accumulators.
+// in FP32 in lockstep; whole items, near-field items (singular kernel) and undecided items
+// go to warp queues that all 32 lanes then drain together (geometry + quadrature), adding
+// their blocks into the owner lane's column of a shared accumulator.  Items whose region
+// the FP64 geometry has to build are queued for k_deferred instead.
 // ---------------------------------------------------------------------------
 // FP32 data of a candidate T_b (64 bytes a lane, in shared memory); the rare FP64 paths
 // read T_b's FP64 vertices, barycentre and area from global memory (cand_fp64).
