@@ -1311,11 +1311,10 @@ __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundarySh
     }
 }
 
-// resident 4-warp blocks per SM: four with float sums and the integrable kernel (registers
-// capped at 128, a few spills), three otherwise (the singular near path and the double
-// sums lose more to spills than they gain from the fourth block)
+// resident 4-warp blocks per SM: four with float sums (registers capped at 128, a few hundred
+// bytes of spills), three with double sums
 template <typename T, bool INV>
-constexpr int kBoundaryBlocksPerSm = (sizeof(T) == sizeof(float) && !INV) ? 4 : 3;
+constexpr int kBoundaryBlocksPerSm = sizeof(T) == sizeof(float) ? 4 : 3;
 
 template <int BALL, typename T, bool INV>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, INV>) k_boundary(const NumArgs A)
