@@ -31,8 +31,9 @@ if ROOT not in sys.path:
 
 METRIC = "assembly qp-pairs/s & ms/matrix, FP32-comp vs FP64 GPU at rel err <=1e-6"
 UNIT = "qp-pairs/s"
-# algorithmic work per unit (derivation in the design doc): the inner-point evaluation
-# (map, phi_b, omega, s0, s1, S2) and the per-(T_a, q, T_b) outer combination
+# algorithmic work per unit, counted from the quadrature of Secs. 5-6 and the local
+# blocks of Sec. 7.2: the inner-point
+# evaluation (map, phi_b, omega, s0, s1, S2) and the per-(T_a, q, T_b) outer combination
 FLOP_PER_QP = 37.0
 FLOP_PER_INTER = 48.0
 SMS, FP32_LANES = 152, 128

@@ -8,7 +8,7 @@ Meshes follow the paper's setting (Sec. 3.1 and Sec. 8): Omega = (0,1)^2 with
 an interaction layer Omega_I around it, covered by a uniform split-square grid
 (grid (a) of Sec. 8, nested refinement), optionally with seeded vertex jitter.
 
-Readings of details the paper leaves open (listed in the design doc):
+Readings of details the paper leaves open:
   * every square cell is split by its lower-left -> upper-right diagonal and
     both triangles are counter-clockwise;
   * jitter moves each coordinate by U[-j h, j h] (numpy PCG64, given seed);

@@ -1,6 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Bar (written here, derived in the design doc):
+Bar (the FP64 bar is the FP64 path's rounding; the FP32 bar is the FP32
+unit round-off times the quadrature's term count, with margin):
   * CSR pattern (row pointers, column indices) and the interaction set
     (per-outer-triangle count, qp-pair count and record hash) are bit-exact;
   * values: |D_gpu - D_oracle| <= 1e-12 max|D| for the FP64 path and
