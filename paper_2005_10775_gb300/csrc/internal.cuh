@@ -20,7 +20,7 @@
 // context; the host reads a slot only after synchronising the stream, so a batch of
 // problems needs one synchronisation per phase instead of one per problem.
 struct nl_host_slot {
-    double mesh[6];               // xmin, xmax, ymin, ymax, r_max, h_max
+    unsigned long long mesh[6];   // order-preserving keys: xmin, ymin, xmax, ymax, r_max, h_max
     int64_t E;                    // candidate pairs
     int64_t nnz;                  // pattern entries
     unsigned long long pat[4];    // pairs, qp-pairs, interactions, longest row

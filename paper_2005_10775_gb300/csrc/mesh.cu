@@ -148,45 +148,50 @@ struct MeshStats {
     double xmin, xmax, ymin, ymax, rmax, hmax;
 };
 
-__global__ void k_mesh_stats(int K, const double *bx, const double *by, const double *rad, const double *diam,
-                             MeshStats *out)
+// Order-preserving map of a double to an unsigned key (so that integer atomics take minima
+// and maxima) and its inverse.
+enum { kStatXmin, kStatYmin, kStatXmax, kStatYmax, kStatRmax, kStatHmax, kStats };
+__device__ __forceinline__ unsigned long long stat_key(double d)
 {
-    __shared__ double s[6][32];
-    double v[6] = {INFINITY, -INFINITY, INFINITY, -INFINITY, 0.0, 0.0};
-    for (int t = threadIdx.x; t < K; t += blockDim.x) {
-        v[0] = fmin(v[0], bx[t]); v[1] = fmax(v[1], bx[t]);
-        v[2] = fmin(v[2], by[t]); v[3] = fmax(v[3], by[t]);
-        v[4] = fmax(v[4], rad[t]); v[5] = fmax(v[5], diam[t]);
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u >> 63) ? ~u : (u | (1ull << 63));
+}
+inline double stat_value(unsigned long long k)
+{
+    const unsigned long long u = (k >> 63) ? (k & ~(1ull << 63)) : ~k;
+    double d;
+    memcpy(&d, &u, sizeof d);
+    return d;
+}
+
+// bounding box of the barycenters, largest barycenter radius and largest diameter; block sums
+// in shared memory, one atomic per block and statistic (keys preset: minima ~0, maxima 0)
+__global__ void k_mesh_stats(int K, const double *bx, const double *by, const double *rad, const double *diam,
+                             unsigned long long *key)
+{
+    __shared__ double s[kStats][32];
+    double v[kStats] = {INFINITY, INFINITY, -INFINITY, -INFINITY, 0.0, 0.0};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < K; t += gridDim.x * blockDim.x) {
+        const double x = bx[t], y = by[t];
+        v[kStatXmin] = fmin(v[kStatXmin], x); v[kStatXmax] = fmax(v[kStatXmax], x);
+        v[kStatYmin] = fmin(v[kStatYmin], y); v[kStatYmax] = fmax(v[kStatYmax], y);
+        v[kStatRmax] = fmax(v[kStatRmax], rad[t]); v[kStatHmax] = fmax(v[kStatHmax], diam[t]);
     }
-    for (int off = 16; off; off >>= 1) {
-        v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], off));
-        v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], off));
-        v[2] = fmin(v[2], __shfl_xor_sync(0xffffffffu, v[2], off));
-        v[3] = fmax(v[3], __shfl_xor_sync(0xffffffffu, v[3], off));
-        v[4] = fmax(v[4], __shfl_xor_sync(0xffffffffu, v[4], off));
-        v[5] = fmax(v[5], __shfl_xor_sync(0xffffffffu, v[5], off));
-    }
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off; off >>= 1)
+        for (int i = 0; i < kStats; i++) {
+            const double o = __shfl_xor_sync(0xffffffffu, v[i], off);
+            v[i] = i < kStatXmax ? fmin(v[i], o) : fmax(v[i], o);
+        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0)
-        for (int i = 0; i < 6; i++) s[i][w] = v[i];
+        for (int i = 0; i < kStats; i++) s[i][w] = v[i];
     __syncthreads();
-    if (w == 0) {
-        for (int i = 0; i < 6; i++) {
-            double init = (i == 0 || i == 2) ? INFINITY : ((i == 1 || i == 3) ? -INFINITY : 0.0);
-            v[i] = lane < nw ? s[i][lane] : init;
-        }
-        for (int off = 16; off; off >>= 1) {
-            v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], off));
-            v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], off));
-            v[2] = fmin(v[2], __shfl_xor_sync(0xffffffffu, v[2], off));
-            v[3] = fmax(v[3], __shfl_xor_sync(0xffffffffu, v[3], off));
-            v[4] = fmax(v[4], __shfl_xor_sync(0xffffffffu, v[4], off));
-            v[5] = fmax(v[5], __shfl_xor_sync(0xffffffffu, v[5], off));
-        }
-        if (lane == 0) {
-            out->xmin = v[0]; out->xmax = v[1]; out->ymin = v[2]; out->ymax = v[3];
-            out->rmax = v[4]; out->hmax = v[5];
-        }
+    if (threadIdx.x < kStats) {
+        const int i = threadIdx.x;
+        double r = s[i][0];
+        for (int k = 1; k < nw; k++) r = i < kStatXmax ? fmin(r, s[i][k]) : fmax(r, s[i][k]);
+        if (i < kStatXmax) atomicMin(&key[i], stat_key(r));
+        else atomicMax(&key[i], stat_key(r));
     }
 }
 
@@ -263,25 +268,23 @@ __global__ void k_candidates(int K, Grid g, float delta, const float4 *__restric
     int64_t out = pass ? ptr[a] : 0;
     const int y0 = max(cy - g.m, 0), y1 = min(cy + g.m, g.ny - 1);
     const int x0 = max(cx - g.m, 0), x1 = min(cx + g.m, g.nx - 1);
+    // the cells x0..x1 of one row are contiguous in the bucket array: one range per row
     for (int yy = y0; yy <= y1; yy++) {
-        for (int xx = x0; xx <= x1; xx++) {
-            int c = yy * g.nx + xx;
-            int64_t s = start[c], e = start[c + 1];
-            for (int64_t base = s; base < e; base += 32) {
-                int64_t k = base + lane;
-                bool hit = false;
-                int b = -1;
-                if (k < e) {
-                    b = bucket[k];
-                    const float4 cb = cf[b];
-                    const float ddx = cb.x - ax, ddy = cb.y - ay;
-                    const float R = (delta + (ra + cb.z)) * (1.0f + 1e-5f);   // symmetric in (a, b)
-                    hit = ddx * ddx + ddy * ddy <= R * R;
-                }
-                unsigned m = __ballot_sync(0xffffffffu, hit);
-                if (pass && hit) idx[out + n + __popc(m & ((1u << lane) - 1u))] = b;
-                n += __popc(m);
+        const int64_t s = start[yy * g.nx + x0], e = start[yy * g.nx + x1 + 1];
+        for (int64_t base = s; base < e; base += 32) {
+            const int64_t k = base + lane;
+            bool hit = false;
+            int b = -1;
+            if (k < e) {
+                b = bucket[k];
+                const float4 cb = cf[b];
+                const float ddx = cb.x - ax, ddy = cb.y - ay;
+                const float R = (delta + (ra + cb.z)) * (1.0f + 1e-5f);   // symmetric in (a, b)
+                hit = ddx * ddx + ddy * ddy <= R * R;
             }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (pass && hit) idx[out + n + __popc(m & ((1u << lane) - 1u))] = b;
+            n += __popc(m);
         }
     }
     if (!pass && lane == 0) cnt[a] = n;
@@ -482,7 +485,7 @@ struct nl_prep {
     bool own_vx = false, own_vy = false, own_tri = false;
     double *diam = nullptr;
     int *bad = nullptr;
-    MeshStats *st = nullptr;
+    unsigned long long *st = nullptr;   // k_mesh_stats keys
     float4 *cf = nullptr;
     Grid g{};
     int ncell = 0;
@@ -560,7 +563,9 @@ nl_status nl_prepare_a(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, n
     }
     NL_CK(cudaMallocAsync((void **)&T->diam, sizeof(double) * K, ctx->stream));
     NL_CK(cudaMallocAsync((void **)&T->bad, sizeof(int), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&T->st, sizeof(MeshStats), ctx->stream));
+    NL_CK(cudaMallocAsync((void **)&T->st, sizeof(unsigned long long) * kStats, ctx->stream));
+    NL_CK(cudaMemsetAsync(T->st, 0xff, sizeof(unsigned long long) * kStatXmax, ctx->stream));
+    NL_CK(cudaMemsetAsync(T->st + kStatXmax, 0, sizeof(unsigned long long) * (kStats - kStatXmax), ctx->stream));
     NL_CK(cudaMemsetAsync(T->bad, 0, sizeof(int), ctx->stream));
     NL_CK(cudaMallocAsync((void **)&T->cf, sizeof(float4) * K, ctx->stream));
     k_prepare<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, J, (const int32_t *)T->dtri, (const double *)T->dvx,
@@ -569,10 +574,14 @@ nl_status nl_prepare_a(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, n
                                                         T->bad); ++ctx->launches;
     k_hilo<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->tx, P->ty, P->bx, P->by, P->hl); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    k_mesh_stats<<<1, 1024, 0, ctx->stream>>>(K, P->bx, P->by, P->rad, T->diam, T->st); ++ctx->launches;
+    {
+        const int nb = (K + 255) / 256;
+        k_mesh_stats<<<nb < 608 ? nb : 608, 256, 0, ctx->stream>>>(K, P->bx, P->by, P->rad, T->diam, T->st);
+        ++ctx->launches;
+    }
     NL_CK(cudaGetLastError());
-    static_assert(sizeof(MeshStats) == sizeof(h->mesh), "mesh statistics slot");
-    NL_CK(cudaMemcpyAsync(h->mesh, T->st, sizeof(MeshStats), cudaMemcpyDeviceToHost, ctx->stream));
+    static_assert(sizeof(unsigned long long) * kStats == sizeof(h->mesh), "mesh statistics slot");
+    NL_CK(cudaMemcpyAsync(h->mesh, T->st, sizeof h->mesh, cudaMemcpyDeviceToHost, ctx->stream));
     NL_CK(cudaMemcpyAsync(&h->bad, T->bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     return NL_OK;
 }
@@ -592,7 +601,12 @@ nl_status nl_prepare_b(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_host_slot *h)
         free_async(T->diam, st); free_async(T->bad, st); free_async(T->st, st);
     }
     MeshStats hst;
-    memcpy(&hst, h->mesh, sizeof hst);
+    hst.xmin = stat_value(h->mesh[kStatXmin]);
+    hst.xmax = stat_value(h->mesh[kStatXmax]);
+    hst.ymin = stat_value(h->mesh[kStatYmin]);
+    hst.ymax = stat_value(h->mesh[kStatYmax]);
+    hst.rmax = stat_value(h->mesh[kStatRmax]);
+    hst.hmax = stat_value(h->mesh[kStatHmax]);
     if (h->bad)
         return nl_fail(ctx, NL_EGEOM, std::to_string(h->bad) +
                                           " triangles are degenerate, clockwise or index a missing vertex");

@@ -13,6 +13,8 @@
 // from the final W + W^T pass through the transposed-slot map.
 #include <cuda_runtime.h>
 
+#include <stdlib.h>
+
 #include <new>
 
 #include "internal.cuh"
@@ -43,23 +45,65 @@ __device__ __forceinline__ int64_t find_in(const int32_t *idx, int64_t lo, int64
     return -1;
 }
 
-// symmetric flag: pair (a, b) or (b, a) interacts; warp per a.  Each candidate list
-// holds two sorted segments (interior, boundary) split at split[b].
-__global__ void k_symflag(int K, const int64_t *ptr, const int64_t *split, const int32_t *idx, const uint8_t *flag,
-                          uint8_t *sym)
+constexpr int kSymWarps = 8;
+
+// sym[e] for a pair (a, b) that does not interact in direction a: the flag of (b, a), found
+// in T_b's list (two sorted segments, interior then boundary, split at split[b]; a triangle
+// appears once).  A pair that fails in one direction lies near the edge of the horizon, so
+// T_a is looked up in the boundary segment first.
+__device__ __forceinline__ void sym_lookup(const int64_t *ptr, const int64_t *split, const int32_t *idx,
+                                           const uint8_t *flag, uint8_t *sym, int a, int64_t e, int b)
 {
-    int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (a >= K) return;
-    for (int64_t e = ptr[a] + lane; e < ptr[a + 1]; e += 32) {
-        int b = idx[e];
-        uint8_t f = flag[e];
-        if (!f) {
-            int64_t m = find_in(idx, ptr[b], split[b], a);
-            if (m < 0) m = find_in(idx, split[b], ptr[b + 1], a);
-            if (m >= 0) f = flag[m];
+    int64_t m = find_in(idx, split[b], ptr[b + 1], a);
+    if (m < 0) m = find_in(idx, ptr[b], split[b], a);
+    sym[e] = m >= 0 ? flag[m] : (uint8_t)0;
+}
+
+// symmetric flag: pair (a, b) or (b, a) interacts; warp per a.  The lanes whose pair does not
+// interact in direction a queue it in shared memory, and the warp runs the lookups 32 at a
+// time, so a round of the list never waits on one lane's binary searches.
+__global__ void __launch_bounds__(kSymWarps * 32) k_symflag(int K, const int64_t *ptr, const int64_t *split,
+                                                             const int32_t *idx, const uint8_t *flag, uint8_t *sym)
+{
+    __shared__ int32_t qoff[kSymWarps][64], qb[kSymWarps][64];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a = blockIdx.x * kSymWarps + w;
+    if (a >= K) return;   // the whole warp: no block barrier follows
+    const int64_t e0 = ptr[a], e1 = ptr[a + 1];
+    int nq = 0;   // queued lookups, < 32 between rounds
+    for (int64_t eb = e0; eb < e1; eb += 32) {
+        const int64_t e = eb + lane;
+        const bool in = e < e1;
+        const int b = in ? idx[e] : 0;
+        const uint8_t f = in ? flag[e] : (uint8_t)1;
+        const bool need = in && !f;
+        if (in && f) sym[e] = f;
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (need) {
+            const int p = nq + __popc(m & ((1u << lane) - 1u));
+            qoff[w][p] = (int32_t)(e - e0);
+            qb[w][p] = b;
         }
-        sym[e] = f;
+        nq += __popc(m);
+        __syncwarp();
+        if (nq >= 32) {
+            sym_lookup(ptr, split, idx, flag, sym, a, e0 + qoff[w][lane], qb[w][lane]);
+            const int rest = nq - 32;
+            int o2 = 0, b2 = 0;
+            if (lane < rest) {
+                o2 = qoff[w][32 + lane];
+                b2 = qb[w][32 + lane];
+            }
+            __syncwarp();
+            if (lane < rest) {
+                qoff[w][lane] = o2;
+                qb[w][lane] = b2;
+            }
+            nq = rest;
+            __syncwarp();
+        }
     }
+    if (lane < nq) sym_lookup(ptr, split, idx, flag, sym, a, e0 + qoff[w][lane], qb[w][lane]);
 }
 
 __global__ void k_node_count(int K, const int32_t *tri, int64_t *cnt)
@@ -82,6 +126,7 @@ __global__ void k_node_fill(int K, const int32_t *tri, const int64_t *start, int
 
 constexpr int kRowThreads = 256;
 constexpr int kListCap = NL_HASH_CAP / 2;   // longest row (columns) the pattern accepts, plus one
+constexpr int kRowWaveBlocks = 152 * 8;   // one wave of k_rows blocks on 152 SMs (the rebuild pass)
 
 // insert c into the shared hash set tab (mask + 1 slots): 1 new, 0 present, -1 set full
 __device__ __forceinline__ int set_insert(int32_t *tab, unsigned mask, int c)
@@ -96,24 +141,67 @@ __device__ __forceinline__ int set_insert(int32_t *tab, unsigned mask, int c)
     return -1;
 }
 
+// The n columns held in the hash set tab (H slots, -1 empty) in ascending order at out[0, n):
+// compacted into lst (2^lbits >= n slots, shared), padded to a power of two and sorted by a
+// bitonic network.  Called by every thread of the block; s_n is the block's shared counter.
+__device__ __forceinline__ void set_sorted(const int32_t *tab, int H, int32_t *lst, int n, int *s_n, int32_t *out)
+{
+    const int lane = threadIdx.x & 31;
+    __syncthreads();   // every thread has read the column count before the counter is reused
+    if (threadIdx.x == 0) *s_n = 0;
+    __syncthreads();
+    for (int i0 = 0; i0 < H; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const int val = i < H ? tab[i] : -1;
+        const unsigned bal = __ballot_sync(0xffffffffu, val >= 0);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(s_n, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (val >= 0) lst[base + __popc(bal & ((1u << lane) - 1u))] = val;
+    }
+    int p = 1;
+    while (p < n) p <<= 1;
+    for (int i = n + threadIdx.x; i < p; i += blockDim.x) lst[i] = 0x7fffffff;
+    __syncthreads();
+    for (int k = 2; k <= p; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < p; i += blockDim.x) {
+                const int l = i ^ jj;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const int u = lst[i], w = lst[l];
+                    if ((u > w) == up) {
+                        lst[i] = w;
+                        lst[l] = u;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = lst[i];
+}
+
 // Block per row j: the distinct nodes of the interacting candidates of the triangles around
 // node j, in a shared hash set of 2^hbits slots.  Rows come from `list` (its length at *nlist,
-// grid-stride) or are the block indices.  pass 0 counts (a row whose set fills up is appended
-// to ovf_list for a second count with a larger set, or, without ovf_list, counted as an
-// overflow); pass 1 writes the sorted columns at row_ptr[j] (lst: 2^lbits slots).  Each thread
-// issues the loads of four candidates before inserting their nodes.
+// grid-stride) or are the block indices.  Each thread issues the loads of four candidates
+// before inserting their nodes.
+//   pass 0 counts.  A row whose set fills up is appended to ovf_list for a second count with
+//   a larger set (without ovf_list it counts as an overflow).  With buf, a row of fewer than
+//   2^lbits columns also leaves them sorted in its buffer row buf[j << lbits] (bflag[j] = 1),
+//   and every other row is appended to rlist for pass 1.
+//   pass 1 writes the sorted columns at row_ptr[j] (lst: 2^lbits slots).
 __global__ void __launch_bounds__(kRowThreads) k_rows(int J, const int64_t *nt_ptr, const int32_t *ntri,
                                                       const int32_t *tri, const int64_t *ptr, const int32_t *idx,
                                                       const uint8_t *sym, int hbits, int lbits, const int *list,
                                                       const int *nlist, int64_t *cnt, const int64_t *row_ptr,
                                                       int32_t *col, int *ovf_list, int *ovf_n, int *overflow,
-                                                      int pass)
+                                                      int32_t *buf, uint8_t *bflag, int *rlist, int *rn, int pass)
 {
     extern __shared__ int32_t sm[];
     const int H = 1 << hbits;
     const unsigned mask = (unsigned)H - 1u;
     int32_t *tab = sm;        // [H]
-    int32_t *lst = sm + H;    // [2^lbits] (pass 1)
+    int32_t *lst = sm + H;    // [2^lbits] (pass 1, and pass 0 with buf)
     __shared__ int s_n, s_ovf;
     const int nrows = list ? *nlist : J;
     const int lane = threadIdx.x & 31;
@@ -161,6 +249,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(int J, const int64_t *nt_p
         __syncthreads();
         const int n = s_n;
         const bool ovf = s_ovf != 0 || n >= kListCap;
+        const bool keep = pass == 0 && buf && !ovf && n < (1 << lbits);
         if (ovf) {
             if (threadIdx.x == 0) {
                 if (ovf_list) ovf_list[atomicAdd(ovf_n, 1)] = j;
@@ -168,43 +257,27 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(int J, const int64_t *nt_p
             }
         } else if (pass == 0) {
             if (threadIdx.x == 0) cnt[j] = n;
+            if (keep) set_sorted(tab, H, lst, n, &s_n, buf + ((int64_t)j << lbits));
         } else {
-            __syncthreads();   // every thread has read the column count before the counter is reused
-            if (threadIdx.x == 0) s_n = 0;
-            __syncthreads();
-            for (int i0 = 0; i0 < H; i0 += blockDim.x) {
-                const int i = i0 + threadIdx.x;
-                const int val = i < H ? tab[i] : -1;
-                const unsigned bal = __ballot_sync(0xffffffffu, val >= 0);
-                int base = 0;
-                if (lane == 0 && bal) base = atomicAdd(&s_n, __popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (val >= 0) lst[base + __popc(bal & ((1u << lane) - 1u))] = val;
-            }
-            int p = 1;
-            while (p < n) p <<= 1;
-            for (int i = n + threadIdx.x; i < p; i += blockDim.x) lst[i] = 0x7fffffff;
-            __syncthreads();
-            for (int k = 2; k <= p; k <<= 1)
-                for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                    for (int i = threadIdx.x; i < p; i += blockDim.x) {
-                        const int l = i ^ jj;
-                        if (l > i) {
-                            const bool up = (i & k) == 0;
-                            const int u = lst[i], w = lst[l];
-                            if ((u > w) == up) {
-                                lst[i] = w;
-                                lst[l] = u;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                }
-            const int64_t o = row_ptr[j];
-            for (int i = threadIdx.x; i < n; i += blockDim.x) col[o + i] = lst[i];
+            set_sorted(tab, H, lst, n, &s_n, col + row_ptr[j]);
+        }
+        if (pass == 0 && buf && threadIdx.x == 0) {
+            bflag[j] = keep ? 1 : 0;
+            if (!keep) rlist[atomicAdd(rn, 1)] = j;
         }
         __syncthreads();   // the set and the counters are reused by the next row
     }
+}
+
+// the columns of the rows pass 0 kept sorted in their buffer rows; warp per row
+__global__ void k_row_copy(int J, const uint8_t *bflag, const int32_t *buf, int lbits, const int64_t *row_ptr,
+                           int32_t *col)
+{
+    const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= J || !bflag[j]) return;
+    const int64_t o = row_ptr[j], n = row_ptr[j + 1] - o;
+    const int32_t *src = buf + ((int64_t)j << lbits);
+    for (int64_t i = lane; i < n; i += 32) col[o + i] = src[i];
 }
 
 // slots of the six upper local pairs (00, 11, 22, 01, 02, 12) of each triangle
@@ -538,6 +611,10 @@ struct nl_pat {
     int32_t *ntri = nullptr;
     int *ovf = nullptr;
     int *olist = nullptr, *on = nullptr;   // rows whose first count filled its hash set
+    int32_t *buf = nullptr;                // rows sorted by the first count: J rows of 2^lbits
+    uint8_t *bflag = nullptr;              // row j is in buf
+    int *rlist = nullptr, *rn = nullptr;   // the other rows, rebuilt by the column write
+    int lbits = 0;
     unsigned long long *st = nullptr;
 };
 
@@ -558,6 +635,7 @@ void nl_pat_delete(nl_pat *T, cudaStream_t s)
     free_async(T->sym, s); free_async(T->ncnt, s); free_async(T->nptr, s); free_async(T->ncur, s);
     free_async(T->rcnt, s); free_async(T->ntri, s); free_async(T->ovf, s); free_async(T->st, s);
     free_async(T->olist, s); free_async(T->on, s);
+    free_async(T->buf, s); free_async(T->bflag, s); free_async(T->rlist, s); free_async(T->rn, s);
     delete T;
 }
 
@@ -598,16 +676,32 @@ nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_
     NL_CK(cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(sizeof(int32_t) * (NL_HASH_CAP + kListCap))));
     // first count with a set of about 3x the expected row (0.6 x the candidates per triangle);
-    // rows that fill it are counted again with the full set
-    const int hb0 = row_set_bits(P->K > 0 ? 2 * P->E / P->K : 1);
-    k_rows<<<J, kRowThreads, sizeof(int32_t) << hb0, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx,
-                                                           T->sym, hb0, 0, nullptr, nullptr, T->rcnt, nullptr,
-                                                           nullptr, T->olist, T->on, T->ovf, 0); ++ctx->launches;
+    // rows that fill it are counted again with the full set.  The first count also leaves every
+    // row of fewer than half its set's slots sorted in a buffer row of that size, so that the
+    // column write copies those rows instead of building their sets again.
+    int hb0 = row_set_bits(P->K > 0 ? 2 * P->E / P->K : 1);
+    // NL_ROW_SET_BITS in the environment (6..13) sets the first count's set size instead: a
+    // small set sends rows through the second count and the rebuild; the pattern is the same
+    if (const char *v = getenv("NL_ROW_SET_BITS")) {
+        const int b = atoi(v);
+        if (b >= 6 && (1 << b) <= NL_HASH_CAP) hb0 = b;
+    }
+    const int lb0 = hb0 - 1;
+    T->lbits = lb0;
+    NL_CK(cudaMallocAsync((void **)&T->buf, sizeof(int32_t) * ((size_t)J << lb0), st));
+    NL_CK(cudaMallocAsync((void **)&T->bflag, (size_t)J + 1, st));
+    NL_CK(cudaMallocAsync((void **)&T->rlist, sizeof(int) * (J + 1), st));
+    NL_CK(cudaMallocAsync((void **)&T->rn, sizeof(int), st));
+    NL_CK(cudaMemsetAsync(T->rn, 0, sizeof(int), st));
+    k_rows<<<J, kRowThreads, sizeof(int32_t) * ((1u << hb0) + (1u << lb0)), st>>>(
+        J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx, T->sym, hb0, lb0, nullptr, nullptr, T->rcnt, nullptr,
+        nullptr, T->olist, T->on, T->ovf, T->buf, T->bflag, T->rlist, T->rn, 0); ++ctx->launches;
     NL_CK(cudaGetLastError());
     const int hbf = row_set_bits(NL_HASH_CAP);
     k_rows<<<256, kRowThreads, sizeof(int32_t) << hbf, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx,
                                                             T->sym, hbf, 0, T->olist, T->on, T->rcnt, nullptr,
-                                                            nullptr, nullptr, nullptr, T->ovf, 0); ++ctx->launches;
+                                                            nullptr, nullptr, nullptr, T->ovf, nullptr, nullptr,
+                                                            nullptr, nullptr, 0); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_alloc(ctx, &out->row_ptr, (size_t)J + 1)) != NL_OK) return s;
     if ((s = nl_scan_i64(ctx, T->rcnt, out->row_ptr, J)) != NL_OK) return s;
@@ -638,12 +732,18 @@ nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl
     P->max_row = (int64_t)h->pat[3];
     if ((s = nl_alloc(ctx, &out->col_idx, (size_t)nnz)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &out->val, (size_t)nnz)) != NL_OK) return s;
-    // every row has at most max_row columns: a set of 2 max_row slots never fills
+    // the rows the first count kept sorted are copied; the others (usually none) are built again,
+    // and every row has at most max_row columns: a set of 2 max_row slots never fills
+    k_row_copy<<<(unsigned)(((int64_t)J * 32 + 255) / 256), 256, 0, st>>>(J, T->bflag, T->buf, T->lbits,
+                                                                         out->row_ptr, out->col_idx);
+    ++ctx->launches;
     const int hb1 = row_set_bits(2 * P->max_row), lb1 = row_set_bits(P->max_row);
     const size_t smem1 = sizeof(int32_t) * (((size_t)1 << hb1) + ((size_t)1 << lb1));
-    k_rows<<<J, kRowThreads, smem1, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx, T->sym, hb1, lb1,
-                                          nullptr, nullptr, nullptr, out->row_ptr, out->col_idx, nullptr, nullptr,
-                                          T->ovf, 1); ++ctx->launches;
+    const unsigned g1 = J < kRowWaveBlocks ? (unsigned)J : (unsigned)kRowWaveBlocks;
+    k_rows<<<g1, kRowThreads, smem1, st>>>(J, T->nptr, T->ntri, P->tri, P->nbr_ptr, P->nbr_idx,
+                                                            T->sym, hb1, lb1, T->rlist, T->rn, nullptr, out->row_ptr,
+                                                            out->col_idx, nullptr, nullptr, T->ovf, nullptr, nullptr,
+                                                            nullptr, nullptr, 1); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_alloc(ctx, &P->lslot, 6 * (size_t)K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->mbb, 6 * (size_t)K)) != NL_OK) return s;

@@ -217,6 +217,58 @@ def test_ragged_and_tiny(nl, ctx):
     compare(Dg, O.to_csr(out), "fp64")
 
 
+def refined_patch_mesh(n=48, frac=0.25, width=0.05):
+    """Split-square grid over (-0.1, 1.1)^2 whose first frac*n grid lines in each direction are
+    packed into [-0.1, -0.1 + width]: a refined corner patch, so that the matrix rows of its nodes
+    are far longer than the mean candidate list of the mesh."""
+    m = I.split_square_mesh(-0.1, 1.1, n)
+    k = int(round(frac * n))
+    lines = np.concatenate([-0.1 + width * np.arange(k) / k,
+                            -0.1 + width + (1.2 - width) * np.arange(n - k + 1) / (n - k)])
+    vx = lines[np.rint((m.vx + 0.1) / m.h).astype(int)]
+    vy = lines[np.rint((m.vy + 0.1) / m.h).astype(int)]
+    node_in = ((vx > 0) & (vx < 1) & (vy > 0) & (vy < 1)).astype(np.uint8)
+    bx, by = vx[m.tri].mean(axis=1), vy[m.tri].mean(axis=1)
+    elem_in = ((bx > 0) & (bx < 1) & (by > 0) & (by < 1)).astype(np.uint8)
+    return I.Mesh(vx=np.ascontiguousarray(vx), vy=np.ascontiguousarray(vy), tri=m.tri, node_in_omega=node_in,
+                  elem_in_omega=elem_in, h=m.h, lo=m.lo, hi=m.hi, n=n)
+
+
+@pytest.mark.parametrize("bits", [None, "6", "7"])
+def test_pattern_long_rows(nl, ctx, monkeypatch, bits):
+    """The symbolic phase counts each row in a hash set of the smallest power of two >= twice the
+    mean candidate list (at least 64) slots and keeps the rows of fewer than half its slots
+    sorted for the column write; longer rows are built again, and rows that fill the set are
+    counted again in a full one.  A refined corner patch gives rows of half the set and more,
+    and a small first set (NL_ROW_SET_BITS) sends most rows through the second count: the
+    pattern and the values match the oracle either way."""
+    m = refined_patch_mesh()
+    d = 0.1
+    p = I.Problem("patch_48", m, d, "const", I.const_kernel_c(d), "nocaps", "dunavant7", "dunavant7")
+    if bits is None:
+        monkeypatch.delenv("NL_ROW_SET_BITS", raising=False)
+    else:
+        monkeypatch.setenv("NL_ROW_SET_BITS", bits)
+    out = O.assemble(m, oracle_cfg(p))
+    Dg, stats = gpu_assemble(nl, ctx, p, "fp64")
+    compare(Dg, O.to_csr(out), "fp64")
+    assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
+    # the mesh does what it is for: rows of half the first set and more (the candidate test
+    # |bary_a - bary_b| <= delta + r_a + r_b, here in FP64; 2 E / K is far from a power of two)
+    xy = np.stack([m.vx[m.tri], m.vy[m.tri]], -1)
+    b = xy.mean(axis=1)
+    r = np.sqrt(((xy - b[:, None]) ** 2).sum(-1)).max(axis=1)
+    dist = np.sqrt(((b[:, None] - b[None]) ** 2).sum(-1))
+    n_cand = int((dist <= d + r[:, None] + r[None]).sum())
+    h0 = 64
+    while h0 < 2 * n_cand // m.nt:
+        h0 *= 2
+    rows = np.diff(Dg.indptr)
+    assert (rows >= h0 // 2).sum() > 20
+    if bits is not None:
+        assert (rows > (1 << int(bits))).sum() > m.nv // 4
+
+
 def test_device_pointer_inputs(nl, ctx):
     torch = pytest.importorskip("torch")
     p = small_problem("approxcaps", n=24)
