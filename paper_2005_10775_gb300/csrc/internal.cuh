@@ -15,6 +15,36 @@
 #define NL_MAXCAND 4096     // candidate neighbours per triangle (sorted in shared memory)
 #define NL_HASH_CAP 8192    // per-row column hash set (shared memory) in the symbolic phase
 
+// exclusive prefix sum of v over a block of NT threads (a multiple of 32, at most 1024);
+// *total = the sum.  wsum: NT / 32 + 1 ints of shared memory.  Every thread of the block calls it.
+template <int NT>
+__device__ __forceinline__ int nl_block_scan(int v, int *wsum, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = lane < NT / 32 ? wsum[lane] : 0;
+        int t = w;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += y;
+        }
+        if (lane < NT / 32) wsum[lane] = t - w;
+        if (lane == NT / 32 - 1) wsum[NT / 32] = t;
+    }
+    __syncthreads();
+    const int r = wsum[warp] + x - v;
+    *total = wsum[NT / 32];
+    __syncthreads();
+    return r;
+}
+
 // Small results of the device phases that the host needs (sizes, statistics, error
 // words).  The phases copy them, stream-ordered, into pinned slots owned by the
 // context; the host reads a slot only after synchronising the stream, so a batch of

@@ -318,34 +318,6 @@ __device__ __forceinline__ bool interior_cand(const float4 &ca, const float4 &cb
     return in;
 }
 
-// exclusive block prefix sum of v (kSortThreads threads); *total = the sum
-__device__ __forceinline__ int block_scan(int v, int *wsum, int *total)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int x = v;
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        const int w = lane < kSortThreads / 32 ? wsum[lane] : 0;
-        int t = w;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, t, off);
-            if (lane >= off) t += y;
-        }
-        if (lane < kSortThreads / 32) wsum[lane] = t - w;
-        if (lane == kSortThreads / 32 - 1) wsum[kSortThreads / 32] = t;
-    }
-    __syncthreads();
-    const int r = wsum[warp] + x - v;
-    *total = wsum[kSortThreads / 32];
-    __syncthreads();
-    return r;
-}
-
 __global__ void __launch_bounds__(kSortThreads) k_sort_lists(const int64_t *ptr, int32_t *idx, int64_t *split,
                                                              const float4 *cf, int mode, float lim, float far_margin,
                                                              int *overflow)
@@ -409,8 +381,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_lists(const int64_t *ptr,
             c1 += __popc(bm[1][w]);
         }
         int t0 = 0, t1 = 0;
-        int p0 = block_scan(c0, wsum, &t0);
-        int p1 = block_scan(c1, wsum, &t1) + t0;
+        int p0 = nl_block_scan<kSortThreads>(c0, wsum, &t0);
+        int p1 = nl_block_scan<kSortThreads>(c1, wsum, &t1) + t0;
         for (int w = w0; w < w1; w++) {
             for (uint32_t m = bm[0][w]; m; m &= m - 1) idx[b0 + p0++] = lo + (w << 5) + __ffs(m) - 1;
             for (uint32_t m = bm[1][w]; m; m &= m - 1) idx[b0 + p1++] = lo + (w << 5) + __ffs(m) - 1;

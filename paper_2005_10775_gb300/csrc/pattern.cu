@@ -141,21 +141,75 @@ __device__ __forceinline__ int set_insert(int32_t *tab, unsigned mask, int c)
     return -1;
 }
 
-// The n columns held in the hash set tab (H slots, -1 empty) in ascending order at out[0, n):
-// compacted into lst (2^lbits >= n slots, shared), padded to a power of two and sorted by a
-// bitonic network.  Called by every thread of the block; s_n is the block's shared counter.
-__device__ __forceinline__ void set_sorted(const int32_t *tab, int H, int32_t *lst, int n, int *s_n, int32_t *out)
+// Block scratch of set_sorted (shared memory)
+struct SortScratch {
+    int n, lo, hi;
+    int wsum[kRowThreads / 32 + 1];
+};
+
+// The n columns held in the hash set tab (H slots, -1 empty) in ascending order at out[0, n),
+// with lst (2^lbits ints of shared memory) as scratch.  The columns of a row are the nodes near
+// node j, so they usually span few indices: one bit per column in a bitmap over [min, max]
+// (lst as 2^lbits words), written in order through prefix counts over the words.  A wider span
+// takes a bitonic sort of the compacted columns (2^lbits >= n slots).  Every thread of the
+// block calls it.
+__device__ __forceinline__ void set_sorted(const int32_t *tab, int H, int32_t *lst, int lbits, int n, SortScratch &sc,
+                                           int32_t *out)
 {
     const int lane = threadIdx.x & 31;
-    __syncthreads();   // every thread has read the column count before the counter is reused
-    if (threadIdx.x == 0) *s_n = 0;
+    __syncthreads();   // every thread has read the column count before the scratch is reused
+    if (threadIdx.x == 0) {
+        sc.n = 0;
+        sc.lo = 0x7fffffff;
+        sc.hi = -1;
+    }
     __syncthreads();
+    int lo = 0x7fffffff, hi = -1;
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        const int v = tab[i];
+        if (v >= 0) {
+            lo = min(lo, v);
+            hi = max(hi, v);
+        }
+    }
+    for (int off = 16; off; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    if (lane == 0) {
+        atomicMin(&sc.lo, lo);
+        atomicMax(&sc.hi, hi);
+    }
+    __syncthreads();
+    lo = sc.lo;
+    const int64_t span = n > 0 ? (int64_t)sc.hi - lo + 1 : 0;
+    if (span <= ((int64_t)32 << lbits)) {
+        uint32_t *bm = reinterpret_cast<uint32_t *>(lst);
+        const int nw = (int)((span + 31) >> 5);
+        for (int w = threadIdx.x; w < nw; w += blockDim.x) bm[w] = 0u;
+        __syncthreads();
+        for (int i = threadIdx.x; i < H; i += blockDim.x) {
+            const int v = tab[i];
+            if (v >= 0) atomicOr(&bm[(v - lo) >> 5], 1u << ((v - lo) & 31));
+        }
+        __syncthreads();
+        // each thread owns a run of consecutive words
+        const int per = (nw + kRowThreads - 1) / kRowThreads;
+        const int w0 = min(nw, (int)threadIdx.x * per), w1 = min(nw, w0 + per);
+        int c = 0;
+        for (int w = w0; w < w1; w++) c += __popc(bm[w]);
+        int total = 0;
+        int p = nl_block_scan<kRowThreads>(c, sc.wsum, &total);
+        for (int w = w0; w < w1; w++)
+            for (uint32_t m = bm[w]; m; m &= m - 1) out[p++] = lo + (w << 5) + __ffs(m) - 1;
+        return;
+    }
     for (int i0 = 0; i0 < H; i0 += blockDim.x) {
         const int i = i0 + threadIdx.x;
         const int val = i < H ? tab[i] : -1;
         const unsigned bal = __ballot_sync(0xffffffffu, val >= 0);
         int base = 0;
-        if (lane == 0 && bal) base = atomicAdd(s_n, __popc(bal));
+        if (lane == 0 && bal) base = atomicAdd(&sc.n, __popc(bal));
         base = __shfl_sync(0xffffffffu, base, 0);
         if (val >= 0) lst[base + __popc(bal & ((1u << lane) - 1u))] = val;
     }
@@ -203,6 +257,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(int J, const int64_t *nt_p
     int32_t *tab = sm;        // [H]
     int32_t *lst = sm + H;    // [2^lbits] (pass 1, and pass 0 with buf)
     __shared__ int s_n, s_ovf;
+    __shared__ SortScratch sc;
     const int nrows = list ? *nlist : J;
     const int lane = threadIdx.x & 31;
     for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
@@ -257,9 +312,9 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(int J, const int64_t *nt_p
             }
         } else if (pass == 0) {
             if (threadIdx.x == 0) cnt[j] = n;
-            if (keep) set_sorted(tab, H, lst, n, &s_n, buf + ((int64_t)j << lbits));
+            if (keep) set_sorted(tab, H, lst, lbits, n, sc, buf + ((int64_t)j << lbits));
         } else {
-            set_sorted(tab, H, lst, n, &s_n, col + row_ptr[j]);
+            set_sorted(tab, H, lst, lbits, n, sc, col + row_ptr[j]);
         }
         if (pass == 0 && buf && threadIdx.x == 0) {
             bflag[j] = keep ? 1 : 0;
@@ -585,9 +640,19 @@ __global__ void k_sum_stats(int K, int64_t E, const uint8_t *flag, const int64_t
                             unsigned long long *out)
 {
     unsigned long long p = 0, q = 0, c = 0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
-        p += flag[e];
-    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < K; a += (int64_t)gridDim.x * blockDim.x) {
+    // the flags are bytes of 0 or 1: 16 at a time from the first 16-byte boundary, summed by bit
+    // counts; the bytes before it and after the last full 16 one at a time
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t head = min(E, (int64_t)((16u - ((uintptr_t)flag & 15u)) & 15u));
+    const int64_t n16 = (E - head) >> 4;
+    const uint4 *f16 = reinterpret_cast<const uint4 *>(flag + head);
+    for (int64_t v = tid; v < n16; v += nth) {
+        const uint4 w = f16[v];
+        p += __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
+    }
+    if (tid < head) p += flag[tid];
+    for (int64_t e = head + (n16 << 4) + tid; e < E; e += nth) p += flag[e];
+    for (int64_t a = tid; a < K; a += nth) {
         q += qp[a];
         c += cnt[a];
     }
