@@ -136,7 +136,10 @@ const char *nl_last_error(nl_ctx *ctx);
    pairs with a non-empty region) and the numeric scatter.  *out receives a new
    library-owned n x n CSR (n = mesh->nv).  Synchronises the stream three times (to
    size the candidate-search grid, the candidate lists and the pattern); device memory
-   comes from the device's stream-ordered pool on the context's stream. */
+   comes from the device's stream-ordered pool on the context's stream.  The pattern's
+   first row count uses a hash set of 2^b slots, b from the mean candidate list;
+   NL_ROW_SET_BITS=b (6..13) in the environment sets it instead (the pattern does not
+   depend on it: rows that fill the set are counted again in a full one). */
 nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl_csr *out);
 
 /* Recompute the values of an nl_assemble result for the same mesh and configuration
