@@ -427,6 +427,13 @@ void nl_destroy(nl_ctx *ctx)
     for (int i = 0; i < 5; i++)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (int k = 0; k < nl_ctx::kSideStreams; k++)
+        if (ctx->side[k]) {
+            cudaStreamSynchronize(ctx->side[k]);
+            cudaStreamDestroy(ctx->side[k]);
+        }
+    for (int k = 0; k <= nl_ctx::kSideStreams; k++)
+        if (ctx->side_ev[k]) cudaEventDestroy(ctx->side_ev[k]);
     if (ctx->slots) cudaFreeHost(ctx->slots);
     nl_tune_cache_free(ctx->tune);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -317,6 +317,49 @@ nl_status sync(nl_ctx *ctx)
     return NL_OK;
 }
 
+nl_status side_streams(nl_ctx *ctx)
+{
+    for (int k = 0; k < nl_ctx::kSideStreams; k++)
+        if (!ctx->side[k]) NL_CK(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
+    for (int k = 0; k <= nl_ctx::kSideStreams; k++)
+        if (!ctx->side_ev[k]) NL_CK(cudaEventCreateWithFlags(&ctx->side_ev[k], cudaEventDisableTiming));
+    return NL_OK;
+}
+
+// One stage of the preparation or symbolic phase for problems 0..n-1: stage(i) runs with
+// ctx->stream set to side stream i mod kSideStreams, so that the small kernels of different
+// problems overlap.  The side streams start after the work already on the context's stream,
+// and that stream waits for all of them before anything that follows (also after a failure,
+// so that no buffer it frees is still in use).  A problem keeps its side stream in every
+// stage, so its buffers stay stream-ordered between stages as well.
+template <class Stage>
+nl_status fan_out(nl_ctx *ctx, int n, int *fail_at, Stage stage)
+{
+    nl_status s = side_streams(ctx);
+    if (s != NL_OK) return s;
+    cudaStream_t st = ctx->stream;
+    const int ns = nl_ctx::kSideStreams;
+    NL_CK(cudaEventRecord(ctx->side_ev[ns], st));
+    for (int k = 0; k < ns; k++) NL_CK(cudaStreamWaitEvent(ctx->side[k], ctx->side_ev[ns], 0));
+    for (int i = 0; i < n && s == NL_OK; i++) {
+        ctx->stream = ctx->side[i % ns];
+        s = stage(i);
+        if (s != NL_OK) *fail_at = i;
+    }
+    ctx->stream = st;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < ns; k++) {
+        cudaError_t e1 = cudaEventRecord(ctx->side_ev[k], ctx->side[k]);
+        if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(st, ctx->side_ev[k], 0);
+        if (e1 != cudaSuccess) {
+            cudaStreamSynchronize(ctx->side[k]);   // no ordering event: wait on the host instead
+            if (e == cudaSuccess) e = e1;
+        }
+    }
+    if (s == NL_OK && e != cudaSuccess) return nl_cuda_fail(ctx, e, "joining the side streams");
+    return s;
+}
+
 // NL_SYNC_CHECK=1 in the environment: synchronise and check after every phase of
 // nl_batch_create, so that a device error is reported with the phase that raised it
 bool sync_check_enabled()
@@ -400,25 +443,21 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
         b->out.push_back(&outs[i]);
     }
     if (cudaEventRecord(ctx->ev[0], st) != cudaSuccess) return fail(nl_fail(ctx, NL_ECUDA, "cudaEventRecord"));
-    // ---- preparation, all problems per stage ----
-    for (int i = 0; i < n; i++)
-        if ((s = nl_prepare_a(ctx, &meshes[i], &cfgs[i], b->P[i], T[i], &h[i])) != NL_OK) {
-            fail_at = i;
-            return fail(s);
-        }
+    // ---- preparation, all problems per stage, spread over the side streams ----
+    if ((s = fan_out(ctx, n, &fail_at, [&](int i) {
+             return nl_prepare_a(ctx, &meshes[i], &cfgs[i], b->P[i], T[i], &h[i]);
+         })) != NL_OK)
+        return fail(s);
+    for (int i = 0; i < n; i++) b->P[i]->stream = st;   // the plans' buffers are freed on the context's stream
     if ((s = sync(ctx)) != NL_OK) return fail(s);
-    for (int i = 0; i < n; i++)
-        if ((s = nl_prepare_b(ctx, b->P[i], T[i], &h[i])) != NL_OK) {
-            fail_at = i;
-            return fail(s);
-        }
+    if ((s = fan_out(ctx, n, &fail_at, [&](int i) { return nl_prepare_b(ctx, b->P[i], T[i], &h[i]); })) != NL_OK)
+        return fail(s);
     if ((s = sync(ctx)) != NL_OK) return fail(s);
-    for (int i = 0; i < n; i++)
-        if ((s = nl_prepare_c(ctx, b->P[i], T[i], &h[i])) != NL_OK ||
-            (s = nl_alloc_numeric(ctx, b->P[i])) != NL_OK) {
-            fail_at = i;
-            return fail(s);
-        }
+    if ((s = fan_out(ctx, n, &fail_at, [&](int i) {
+             nl_status r = nl_prepare_c(ctx, b->P[i], T[i], &h[i]);
+             return r == NL_OK ? nl_alloc_numeric(ctx, b->P[i]) : r;
+         })) != NL_OK)
+        return fail(s);
     // ---- numeric launches: interior per value type, boundary per value type x ball x kernel ----
     for (int f = 0; f < 2; f++) {
         PrecGroup g;
@@ -500,18 +539,16 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
     if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return fail(nl_fail(ctx, NL_ECUDA, "cudaEventRecord"));
     if ((s = launch_numeric(ctx, b, true)) != NL_OK || (s = phase_check(ctx, b, "numeric")) != NL_OK) return fail(s);
     if (cudaEventRecord(ctx->ev[2], st) != cudaSuccess) return fail(nl_fail(ctx, NL_ECUDA, "cudaEventRecord"));
-    // ---- symbolic phase, all problems per stage ----
-    for (int i = 0; i < n; i++)
-        if ((s = nl_pattern_a(ctx, b->P[i], &outs[i], Q[i], &h[i])) != NL_OK) {
-            fail_at = i;
-            return fail(s);
-        }
+    // ---- symbolic phase, all problems per stage, spread over the side streams ----
+    if ((s = fan_out(ctx, n, &fail_at, [&](int i) { return nl_pattern_a(ctx, b->P[i], &outs[i], Q[i], &h[i]); })) !=
+        NL_OK)
+        return fail(s);
     if ((s = sync(ctx)) != NL_OK) return fail(s);
-    for (int i = 0; i < n; i++)
-        if ((s = nl_prepare_check(ctx, &h[i])) != NL_OK || (s = nl_pattern_b(ctx, b->P[i], &outs[i], Q[i], &h[i])) != NL_OK) {
-            fail_at = i;
-            return fail(s);
-        }
+    if ((s = fan_out(ctx, n, &fail_at, [&](int i) {
+             nl_status r = nl_prepare_check(ctx, &h[i]);
+             return r == NL_OK ? nl_pattern_b(ctx, b->P[i], &outs[i], Q[i], &h[i]) : r;
+         })) != NL_OK)
+        return fail(s);
     if ((s = phase_check(ctx, b, "symbolic")) != NL_OK) return fail(s);
     if (cudaEventRecord(ctx->ev[3], st) != cudaSuccess) return fail(nl_fail(ctx, NL_ECUDA, "cudaEventRecord"));
     // ---- scatter arguments ----

@@ -73,6 +73,11 @@ struct nl_ctx {
     int nslots = 0;
     struct nl_tune_cache *tune = nullptr;   // batch schedules picked by the autotuner (batch.cu)
     int64_t last_fp64_items = 0;  // nl_last_fp64_items
+    // side streams of a batch's preparation and symbolic stages (created on first use) and
+    // their ordering events: [k] for side stream k, [kSideStreams] for the fork
+    static constexpr int kSideStreams = 8;
+    cudaStream_t side[kSideStreams] = {};
+    cudaEvent_t side_ev[kSideStreams + 1] = {};
 };
 
 // pinned host slots for n problems (grown on demand; invalidates earlier slot pointers)
