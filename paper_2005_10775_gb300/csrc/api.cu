@@ -380,6 +380,15 @@ nl_status nl_run_numeric(nl_ctx *ctx, nl_plan *P, bool with_hash) { return run_n
 // ---------------------------------------------------------------------------
 // entry points
 // ---------------------------------------------------------------------------
+nl_status nl_side_streams(nl_ctx *ctx)
+{
+    for (int k = 0; k < nl_ctx::kSideStreams; k++)
+        if (!ctx->side[k]) NL_CK(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
+    for (int k = 0; k <= nl_ctx::kSideStreams; k++)
+        if (!ctx->side_ev[k]) NL_CK(cudaEventCreateWithFlags(&ctx->side_ev[k], cudaEventDisableTiming));
+    return NL_OK;
+}
+
 extern "C" {
 
 nl_status nl_create(nl_ctx **out, int device, void *stream)

@@ -317,15 +317,6 @@ nl_status sync(nl_ctx *ctx)
     return NL_OK;
 }
 
-nl_status side_streams(nl_ctx *ctx)
-{
-    for (int k = 0; k < nl_ctx::kSideStreams; k++)
-        if (!ctx->side[k]) NL_CK(cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking));
-    for (int k = 0; k <= nl_ctx::kSideStreams; k++)
-        if (!ctx->side_ev[k]) NL_CK(cudaEventCreateWithFlags(&ctx->side_ev[k], cudaEventDisableTiming));
-    return NL_OK;
-}
-
 // One stage of the preparation or symbolic phase for problems 0..n-1: stage(i) runs with
 // ctx->stream set to side stream i mod kSideStreams, so that the small kernels of different
 // problems overlap.  The side streams start after the work already on the context's stream,
@@ -335,7 +326,7 @@ nl_status side_streams(nl_ctx *ctx)
 template <class Stage>
 nl_status fan_out(nl_ctx *ctx, int n, int *fail_at, Stage stage)
 {
-    nl_status s = side_streams(ctx);
+    nl_status s = nl_side_streams(ctx);
     if (s != NL_OK) return s;
     cudaStream_t st = ctx->stream;
     const int ns = nl_ctx::kSideStreams;

@@ -80,6 +80,9 @@ struct nl_ctx {
     cudaEvent_t side_ev[kSideStreams + 1] = {};
 };
 
+// the context's side streams and their events (created on first use)
+nl_status nl_side_streams(nl_ctx *ctx);
+
 // pinned host slots for n problems (grown on demand; invalidates earlier slot pointers)
 nl_status nl_host_slots(nl_ctx *ctx, int n, nl_host_slot **out);
 

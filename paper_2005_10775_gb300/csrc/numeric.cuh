@@ -647,8 +647,10 @@ __device__ __forceinline__ void warp_reduce(LaneAcc &acc)
 
 // ---------------------------------------------------------------------------
 // Interior pairs: T_b is whole for every outer point of T_a (certified when the
-// candidate lists are built), so there is no per-point classification.  Runs first
-// and initialises the per-triangle M_aa and statistics.
+// candidate lists are built), so there is no per-point classification.  k_interior runs
+// concurrently with k_boundary (it fills the boundary kernel's last wave): both add the
+// per-triangle M_aa and statistics atomically onto zeroed outputs; the batched kernels run
+// one after the other and store, then add.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const OuterPt *sq, int lane, LaneAcc &acc)
@@ -700,14 +702,23 @@ __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const Ou
     }
 }
 
-// warp reduction of the outer triangle's accumulators and their store (add: onto the
-// values an earlier kernel stored, in stream order)
-__device__ __forceinline__ void finish_outer(const NumArgs &A, int a, LaneAcc &acc, int lane, bool add)
+// warp reduction of the outer triangle's accumulators and their store: kStore (the first
+// kernel of the triangle), kAdd (onto the values an earlier kernel stored, in stream order) or
+// kAtomicAdd (onto zeroed outputs, from kernels that run concurrently).  Two atomic addends
+// onto zero give the same sum in either order, so the result does not depend on the schedule.
+enum FinishMode { kStore, kAdd, kAtomicAdd };
+
+__device__ __forceinline__ void finish_outer(const NumArgs &A, int a, LaneAcc &acc, int lane, FinishMode mode)
 {
     warp_reduce(acc);
     if (lane == 0) {
         const int K = A.K;
-        if (add) {
+        if (mode == kAtomicAdd) {
+            for (int i = 0; i < 6; i++) atomicAdd(&A.maa[(int64_t)i * K + a], acc.maa[i]);
+            atomicAdd((unsigned long long *)&A.qp_a[a], (unsigned long long)acc.qp);
+            atomicAdd((unsigned long long *)&A.cnt_a[a], (unsigned long long)acc.cnt);
+            if (A.stats) atomicAdd((unsigned long long *)&A.hash_a[a], (unsigned long long)acc.hsum);
+        } else if (mode == kAdd) {
             for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] += acc.maa[i];
             A.qp_a[a] += acc.qp;
             A.cnt_a[a] += acc.cnt;
@@ -735,7 +746,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float
     LaneAcc acc;
     acc_zero(acc);
     interior_outer<T>(A, a, sq, lane, acc);
-    finish_outer(A, a, acc, lane, false);
+    finish_outer(A, a, acc, lane, kAtomicAdd);
 }
 
 // ---------------------------------------------------------------------------
@@ -1327,8 +1338,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, I
     LaneAcc acc;
     acc_zero(acc);
     boundary_any<BALL, T, INV>(A, a, sh, lane, acc);
-    // k_interior has written this triangle's values; add in stream order
-    finish_outer(A, a, acc, lane, true);
+    // k_interior may be running: add atomically onto the zeroed outputs
+    finish_outer(A, a, acc, lane, kAtomicAdd);
 }
 
 // ---------------------------------------------------------------------------
@@ -1377,7 +1388,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float
             LaneAcc acc;
             acc_zero(acc);
             interior_outer<T>(A, a, sq, lane, acc);
-            finish_outer(A, a, acc, lane, false);
+            finish_outer(A, a, acc, lane, kStore);
             __syncwarp();
         }
     }
@@ -1405,7 +1416,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, I
             LaneAcc acc;
             acc_zero(acc);
             boundary_any<BALL, T, INV>(A, a, sh, lane, acc);
-            finish_outer(A, a, acc, lane, true);
+            finish_outer(A, a, acc, lane, kAdd);
             __syncwarp();
         }
     }
@@ -1504,3 +1515,41 @@ nl_status nl_deferred_blocks(nl_ctx *ctx, int *blocks);
 // resident blocks per SM of the interior launch (ball < 0) or of a boundary launch
 nl_status nl_batch_occupancy_f32(nl_ctx *ctx, int ball, bool inv, int *per_sm);
 nl_status nl_batch_occupancy_f64(nl_ctx *ctx, int ball, bool inv, int *per_sm);
+
+// Single-problem numeric phase: the per-triangle outputs are zeroed, k_boundary is launched on
+// the context's stream and then k_interior on side stream 0 (both add their per-triangle values
+// atomically), so that the interior kernel's blocks fill the boundary kernel's last wave; the
+// context's stream waits for side stream 0 before anything that follows.
+inline nl_status nl_numeric_fork(nl_ctx *ctx, const nlq::NumArgs &A)
+{
+    cudaStream_t st = ctx->stream;
+    const size_t K = (size_t)A.K;
+    NL_CK(cudaMemsetAsync(A.maa, 0, sizeof(double) * 6 * K, st));
+    NL_CK(cudaMemsetAsync(A.qp_a, 0, sizeof(int64_t) * K, st));
+    NL_CK(cudaMemsetAsync(A.cnt_a, 0, sizeof(int64_t) * K, st));
+    NL_CK(cudaMemsetAsync(A.hash_a, 0, sizeof(uint64_t) * K, st));
+    nl_status s = nl_side_streams(ctx);
+    if (s != NL_OK) return s;
+    NL_CK(cudaEventRecord(ctx->side_ev[nl_ctx::kSideStreams], st));
+    NL_CK(cudaStreamWaitEvent(ctx->side[0], ctx->side_ev[nl_ctx::kSideStreams], 0));
+    return NL_OK;
+}
+
+// the interior kernel on side stream 0, then the join (always, so that nothing on the side
+// stream outlives a failure); s: the status of the boundary launch
+template <typename T>
+nl_status nl_numeric_interior_join(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads, nl_status s)
+{
+    if (s == NL_OK) {
+        nlq::k_interior<T><<<grid, threads, 0, ctx->side[0]>>>(A); ++ctx->launches;
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = nl_cuda_fail(ctx, e, "k_interior launch");
+    }
+    cudaError_t e = cudaEventRecord(ctx->side_ev[0], ctx->side[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->side_ev[0], 0);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(ctx->side[0]);   // no ordering event: wait on the host instead
+        if (s == NL_OK) s = nl_cuda_fail(ctx, e, "joining the interior launch");
+    }
+    return s;
+}
