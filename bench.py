@@ -39,7 +39,7 @@ FLOP_PER_INTER = 48.0
 SMS, FP32_LANES = 152, 128
 # DRAM bytes (read + write) of the numeric phase (k_interior + k_boundary + k_deferred) of
 # one assembly, from one ncu capture of the current kernels (profiles/k_boundary_<workload>.md)
-NCU_TRAFFIC = {"ngon32_96": (697.3e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_interior + k_boundary "
+NCU_TRAFFIC = {"ngon32_96": (403.5e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_interior + k_boundary "
                                       "+ k_deferred, profiles/numeric_traffic_ngon32_96.md")}
 
 

@@ -288,6 +288,7 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     }
     A.flag = P->flag;
     A.blk = P->blk;
+    A.mbb = P->mbb;
     A.maa = P->maa;
     A.qp_a = P->qp_a;
     A.cnt_a = P->cnt_a;
@@ -307,8 +308,9 @@ nl_status nl_alloc_numeric(nl_ctx *ctx, nl_plan *P)
     const size_t tsz = P->cfg.prec == NL_PREC_FP64 ? sizeof(double) : sizeof(float);
     if ((s = nl_alloc(ctx, &P->flag, (size_t)P->E)) != NL_OK) return s;
     unsigned char *blk = nullptr;
-    if ((s = nl_alloc(ctx, &blk, tsz * 15 * (size_t)(P->E ? P->E : 1))) != NL_OK) return s;
+    if ((s = nl_alloc(ctx, &blk, tsz * 9 * (size_t)(P->E ? P->E : 1))) != NL_OK) return s;
     P->blk = blk;
+    if ((s = nl_alloc(ctx, &P->mbb, 6 * (size_t)P->K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->maa, 6 * (size_t)P->K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->qp_a, (size_t)P->K)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->cnt_a, (size_t)P->K)) != NL_OK) return s;

@@ -29,6 +29,14 @@
 
 namespace {
 
+// zero the per-triangle M_bb sums of every problem of one argument array (block per problem)
+__global__ void k_zero_mbb_batch(const nlq::NumArgs *__restrict__ As)
+{
+    const nlq::NumArgs &A = As[blockIdx.x];
+    const int64_t n = 6 * (int64_t)A.K;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) A.mbb[i] = 0.0;
+}
+
 struct Sched {
     int chunk = 1;
     int order = 0;
@@ -218,6 +226,11 @@ nl_status launch_numeric(nl_ctx *ctx, nl_batch *b, bool set_attr)
 {
     const size_t nl = b->launches.size();
     NL_CK(cudaMemsetAsync(b->counters, 0, sizeof(int) * 2 * nl, ctx->stream));
+    // the per-triangle M_bb sums start at zero in every numeric run (the autotuner's too)
+    for (const PrecGroup &g : b->pgroups) {
+        k_zero_mbb_batch<<<(unsigned)g.probs.size(), 256, 0, ctx->stream>>>(g.dA); ++ctx->launches;
+        NL_CK(cudaGetLastError());
+    }
     for (size_t k = 0; k < nl; k++) {
         const Launch &l = b->launches[k];
         if (!l.n_items) continue;

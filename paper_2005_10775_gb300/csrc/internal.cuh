@@ -107,13 +107,13 @@ struct nl_plan {
     int64_t *nbr_split = nullptr; // [K] first boundary candidate of each triangle
     // numeric phase outputs
     uint8_t *flag = nullptr;      // [E] directed: some outer point of a sees a non-empty region in b
-    void *blk = nullptr;          // [15][E] pair blocks (float or double)
+    void *blk = nullptr;          // [9][E] pair blocks M_ab (float or double)
     double *maa = nullptr;        // [6][K] outer-triangle self block
     int64_t *qp_a = nullptr, *cnt_a = nullptr;   // [K]
     uint64_t *hash_a = nullptr;   // [K]
     // pattern
     int64_t *lslot = nullptr;     // [6][K] slots of the upper local pairs of each triangle
-    double *mbb = nullptr;        // [6][K] per-triangle sum of the pairs' upper M_bb (zero between scatters)
+    double *mbb = nullptr;        // [6][K] per-triangle sum of the pairs' upper M_bb (numeric phase; zeroed by it)
     int64_t *tslot = nullptr;     // [nnz] slot of the transposed entry
     double *W = nullptr;          // [nnz] one-sided accumulation, D = W + W^T
     int64_t max_row = 0;          // longest row of the pattern
@@ -127,7 +127,7 @@ struct nl_plan {
     void *defer = nullptr;
     int *defer_n = nullptr;
     int defer_cap = 0;
-    int64_t blk_elems() const { return 15 * E; }
+    int64_t blk_elems() const { return 9 * E; }
 };
 
 // ---- error helpers ----

@@ -67,8 +67,10 @@ struct NumArgs {
     double kc;
     nlg::GeoParams geo;
     uint8_t *flag;
-    void *blk;                        // [15][E]
+    void *blk;                        // [9][E]: M_ab of every candidate pair (float or double)
     double *maa;                      // [6][K]
+    double *mbb;                      // [6][K]: per-triangle sums of the pairs' upper M_bb (FP64 atomics;
+                                      // zeroed before the numeric phase)
     int64_t *qp_a, *cnt_a;
     uint64_t *hash_a;
     int stats;
@@ -625,12 +627,16 @@ __device__ __forceinline__ void maa_add(LaneAcc &acc, const T *m)
     }
 }
 
+// the pair's block: M_ab stored (v[0..8]), its upper M_bb (v[9..14]) added onto T_b's sums, its
+// M_aa (v[15..20]) into the lane's sums of T_a
 template <typename T>
-__device__ __forceinline__ void write_pair(const NumArgs &A, int64_t e, bool any, const T *v, LaneAcc &acc)
+__device__ __forceinline__ void write_pair(const NumArgs &A, int64_t e, int b, bool any, const T *v, LaneAcc &acc)
 {
     A.flag[e] = any ? 1 : 0;
     T *blk = (T *)A.blk;
-    for (int i = 0; i < 15; i++) blk[(int64_t)i * A.E + e] = v[i];
+    for (int i = 0; i < 9; i++) blk[(int64_t)i * A.E + e] = v[i];
+    if (any)
+        for (int i = 0; i < 6; i++) atomicAdd(&A.mbb[(int64_t)i * A.K + b], (double)v[9 + i]);
     maa_add<T>(acc, v + 15);
 }
 
@@ -698,7 +704,7 @@ __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const Ou
             acc.cnt++;
             if (A.stats) acc.hsum += nlg::record_hash(a, b, 0, nlg::KIND_WHOLE, 3, 0);
         }
-        write_pair<T>(A, e, q1 > q0, v, acc);
+        write_pair<T>(A, e, b, q1 > q0, v, acc);
     }
 }
 
@@ -1190,7 +1196,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         if (valid) {
             T v[21];
             for (int k = 0; k < 21; k++) v[k] = sh.acc[k][lane];
-            write_pair<T>(A, e, sh.acc[21][lane] != (T)0, v, acc);
+            write_pair<T>(A, e, sh.cand[lane].b, sh.acc[21][lane] != (T)0, v, acc);
         } else if (kLaneMaa) {   // a lane without a candidate in this batch may have integrated items
             T m[6];
             for (int k = 0; k < 6; k++) m[k] = sh.acc[15 + k][lane];
@@ -1299,7 +1305,7 @@ __device__ __forceinline__ void support_boundary(const NumArgs &A, int a, int la
                 }
             }
         }
-        write_pair<T>(A, e, nout > 0, v, acc);
+        write_pair<T>(A, e, b, nout > 0, v, acc);
         if (nout > 0) {
             acc.cnt++;
             acc.qp += nout * nq_in;
@@ -1454,7 +1460,8 @@ __device__ __forceinline__ void deferred_item(const NumArgs &A, const DeferItem 
     for (int k = 0; k < 21; k++) w[k] = 0.f;
     combine<float>(o, S, w);
     float *blk = (float *)A.blk;
-    for (int k = 0; k < 15; k++) atomicAdd(&blk[(int64_t)k * A.E + e], w[k]);
+    for (int k = 0; k < 9; k++) atomicAdd(&blk[(int64_t)k * A.E + e], w[k]);
+    for (int k = 0; k < 6; k++) atomicAdd(&A.mbb[(int64_t)k * K + b], (double)w[9 + k]);
     for (int k = 0; k < 6; k++) atomicAdd(&A.maa[(int64_t)k * K + a], (double)w[15 + k]);
     A.flag[e] = 1;
     atomicAdd((unsigned long long *)&A.qp_a[a], (unsigned long long)nq);
@@ -1528,6 +1535,7 @@ inline nl_status nl_numeric_fork(nl_ctx *ctx, const nlq::NumArgs &A)
     NL_CK(cudaMemsetAsync(A.qp_a, 0, sizeof(int64_t) * K, st));
     NL_CK(cudaMemsetAsync(A.cnt_a, 0, sizeof(int64_t) * K, st));
     NL_CK(cudaMemsetAsync(A.hash_a, 0, sizeof(uint64_t) * K, st));
+    NL_CK(cudaMemsetAsync(A.mbb, 0, sizeof(double) * 6 * K, st));
     nl_status s = nl_side_streams(ctx);
     if (s != NL_OK) return s;
     NL_CK(cudaEventRecord(ctx->side_ev[nl_ctx::kSideStreams], st));

@@ -362,8 +362,8 @@ __global__ void k_tslot(int J, const int64_t *row_ptr, const int32_t *col, int64
 // one FP64 atomic per pair and entry.  The columns of the three rows are indexed by a
 // shared hash table (key: column node; value: the column's position in each of the
 // three rows, 10 bits each), so each node of T_b costs one lookup for all three rows.
-// The upper M_bb of every pair is summed per triangle b (mbb, FP64 atomics); k_local_blocks
-// then adds M_aa + M_bb of every triangle through the local slot map.
+// The upper M_bb of every pair was summed per triangle b by the numeric kernels (mbb, FP64
+// atomics); k_local_blocks adds M_aa + M_bb of every triangle through the local slot map.
 constexpr unsigned kPosAbsent = 1023u;   // 10-bit position field: column not in that row
 constexpr int kMaxCachedRow = 1022;
 
@@ -398,7 +398,7 @@ __device__ __forceinline__ int hash_find(const int32_t *key, int H, int hbits, i
 
 template <typename T>
 __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int32_t *tri, const int64_t *ptr,
-                                              const int32_t *idx, const uint8_t *flag, const T *blk, double *mbb,
+                                              const int32_t *idx, const uint8_t *flag, const T *blk,
                                               const int64_t *row_ptr, const int32_t *col, double *W, int *err,
                                               int cap, int hbits, int a, int lane, T *sacc, int32_t *skey,
                                               uint32_t *spk)
@@ -449,8 +449,8 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
         // every load of the pair first (independent of the flag): one round trip, not a chain
         const uint8_t f = flag[e];
         const int b = idx[e];
-        T v[15];
-        for (int p = 0; p < 15; p++) v[p] = blk[(int64_t)p * E + e];
+        T v[9];
+        for (int p = 0; p < 9; p++) v[p] = blk[(int64_t)p * E + e];
         if (!f) continue;
 #ifdef NL_CHECKS
         if (b < 0 || b >= K) {
@@ -465,7 +465,6 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
             continue;
         }
 #endif
-        for (int p = 0; p < 6; p++) atomicAdd(&mbb[(int64_t)p * K + b], (double)v[9 + p]);
         for (int k = 0; k < 3; k++) {
             if (cached) {
                 const int sl = hash_find(skey, H, hbits, bn[k]);
@@ -537,7 +536,7 @@ __device__ __forceinline__ void scatter_warp_smem(unsigned char *raw, int wib, i
 
 template <typename T>
 __global__ void k_scatter(int K, int J, int64_t E, const int32_t *tri, const int64_t *ptr, const int32_t *idx,
-                          const uint8_t *flag, const T *blk, double *mbb, const int64_t *row_ptr, const int32_t *col,
+                          const uint8_t *flag, const T *blk, const int64_t *row_ptr, const int32_t *col,
                           double *W, int *err, int cap, int hbits)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -548,7 +547,7 @@ __global__ void k_scatter(int K, int J, int64_t E, const int32_t *tri, const int
     uint32_t *spk;
     scatter_warp_smem<T>(smem_raw, wib, cap, hbits, sacc, skey, spk);
     if (a >= K) return;
-    scatter_outer<T>(K, J, E, tri, ptr, idx, flag, blk, mbb, row_ptr, col, W, err, cap, hbits, a, lane, sacc, skey,
+    scatter_outer<T>(K, J, E, tri, ptr, idx, flag, blk, row_ptr, col, W, err, cap, hbits, a, lane, sacc, skey,
                      spk);
 }
 
@@ -579,7 +578,7 @@ __global__ void k_scatter_batch(const ScatterArgs *__restrict__ S, const int64_t
     scatter_warp_smem<T>(smem_raw, wib, cap, hbits, sacc, skey, spk);
     const int p = batch_problem(koff, n, g);
     const ScatterArgs &A = S[p];
-    scatter_outer<T>(A.K, A.J, A.E, A.tri, A.ptr, A.idx, A.flag, (const T *)A.blk, A.mbb, A.row_ptr, A.col, A.W,
+    scatter_outer<T>(A.K, A.J, A.E, A.tri, A.ptr, A.idx, A.flag, (const T *)A.blk, A.row_ptr, A.col, A.W,
                      A.err, cap, hbits, (int)(g - koff[p]), lane, sacc, skey, spk);
 }
 
@@ -811,8 +810,6 @@ nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl
                                                             nullptr, nullptr, 1); ++ctx->launches;
     NL_CK(cudaGetLastError());
     if ((s = nl_alloc(ctx, &P->lslot, 6 * (size_t)K)) != NL_OK) return s;
-    if ((s = nl_alloc(ctx, &P->mbb, 6 * (size_t)K)) != NL_OK) return s;
-    NL_CK(cudaMemsetAsync(P->mbb, 0, sizeof(double) * 6 * (size_t)K, st));   // k_local_blocks re-zeroes it
     if ((s = nl_alloc(ctx, &P->tslot, (size_t)nnz)) != NL_OK) return s;
     if ((s = nl_alloc(ctx, &P->W, (size_t)nnz)) != NL_OK) return s;
     k_local_slots<<<(K + 255) / 256, 256, 0, st>>>(K, P->tri, out->row_ptr, out->col_idx, P->lslot); ++ctx->launches;
@@ -871,7 +868,7 @@ static nl_status launch_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     NL_CK(cudaFuncSetAttribute(k_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(96 * 1024)));
     const unsigned grid = (unsigned)((K + warps - 1) / warps);
     k_scatter<T><<<grid, 32 * warps, smem, ctx->stream>>>(K, P->J, P->E, P->tri, P->nbr_ptr, P->nbr_idx, P->flag,
-                                                           (const T *)P->blk, P->mbb, out->row_ptr, out->col_idx,
+                                                           (const T *)P->blk, out->row_ptr, out->col_idx,
                                                            P->W, P->err, cap, hbits); ++ctx->launches;
     NL_CK(cudaGetLastError());
     k_local_blocks<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->maa, P->mbb, P->lslot, P->W, P->err);
