@@ -497,7 +497,7 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
 }
 
 // M_aa + M_bb of every triangle into W through its local slots (diagonal halved: D = W + W^T),
-// leaving mbb zeroed for the next scatter
+// leaving mbb zeroed (the numeric phase also zeroes it before it sums)
 __device__ __forceinline__ void local_block(int K, int t, const double *maa, double *mbb, const int64_t *lslot,
                                             double *W, int *err)
 {
