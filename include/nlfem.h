@@ -136,7 +136,10 @@ const char *nl_last_error(nl_ctx *ctx);
    pairs with a non-empty region) and the numeric scatter.  *out receives a new
    library-owned n x n CSR (n = mesh->nv).  Synchronises the stream three times (to
    size the candidate-search grid, the candidate lists and the pattern); device memory
-   comes from the device's stream-ordered pool on the context's stream.  The pattern's
+   comes from the device's stream-ordered pool on the context's stream.  The interior
+   candidates' quadrature runs on a second stream of the context, concurrently with the
+   boundary candidates' (ordered after the context's stream's earlier work, which waits
+   for it before anything that follows).  The pattern's
    first row count uses a hash set of 2^b slots, b from the mean candidate list;
    NL_ROW_SET_BITS=b (6..13) in the environment sets it instead (the pattern does not
    depend on it: rows that fill the set are counted again in a full one). */
@@ -144,7 +147,8 @@ nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl
 
 /* Recompute the values of an nl_assemble result for the same mesh and configuration
    on its existing pattern (pair geometry, quadrature and scatter only).  No host
-   synchronisation: can be captured in a CUDA graph. */
+   synchronisation: can be captured in a CUDA graph (the context's second stream joins the
+   capture through events). */
 nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *inout);
 
 /* ---- batches of independent problems ----
@@ -152,7 +156,8 @@ nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *inout);
    assembled exactly as nl_assemble would (same interaction set and pattern, values
    equal up to the order of the FP64 scatter additions), but the batch:
      - runs each preparation and symbolic stage for all problems before synchronising,
-       so the whole batch waits on the host three times, not three times per problem;
+       so the whole batch waits on the host three times, not three times per problem,
+       with the problems spread over eight streams of the context (joined by events);
      - runs the numeric phase (pair geometry + quadrature) of all problems in one pair
        of persistent launches (interior candidates, then boundary candidates) per value
        type x kernel type present: their warps take work items (a run of outer triangles
@@ -164,8 +169,9 @@ nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *inout);
    The work-item order and size are picked by a built-in autotuner: the first batch of
    a given shape (sizes, candidate counts, balls, rules, precisions) times a few
    schedules of the numeric launch and keeps the fastest in the context; later batches
-   of the same shape reuse it.  Every schedule yields the same values: each outer
-   triangle's blocks are produced by one warp in a fixed order. */
+   of the same shape reuse it.  Every schedule yields the same pair blocks: each outer
+   triangle's blocks are produced by one warp in a fixed order (the per-triangle sums
+   taken with FP64 atomics, like the scatter's, may differ in the last bits). */
 typedef struct nl_batch nl_batch;
 
 enum { NL_BATCH_NO_TUNE = 1 };   /* nl_batch_create flag: default schedule, no timing runs */

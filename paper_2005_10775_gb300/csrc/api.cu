@@ -408,6 +408,12 @@ nl_status nl_create(nl_ctx **out, int device, void *stream)
         ctx->own_stream = (e == cudaSuccess);
     }
     for (int i = 0; e == cudaSuccess && i < 5; i++) e = cudaEventCreate(&ctx->ev[i]);
+    // the side streams (the numeric phase's interior launch, the batch's stages) exist from the
+    // start, so that no stream or event is created while the caller captures a graph
+    for (int k = 0; e == cudaSuccess && k < nl_ctx::kSideStreams; k++)
+        e = cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking);
+    for (int k = 0; e == cudaSuccess && k <= nl_ctx::kSideStreams; k++)
+        e = cudaEventCreateWithFlags(&ctx->side_ev[k], cudaEventDisableTiming);
     if (e == cudaSuccess) {
         // keep freed pool memory cached by this process (up to 8 GiB) instead of handing it
         // back to the driver at every synchronisation: later assemblies allocate without
