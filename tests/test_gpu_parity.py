@@ -304,6 +304,42 @@ def test_numeric_reassembly_is_repeatable(nl, ctx):
     assert np.abs(D1.data - D2.data).max() <= 1e-7 * np.abs(D1.data).max()
 
 
+def test_numeric_reassembly_in_a_graph(nl):
+    """nl_assemble_numeric captured in a CUDA graph on the context's stream (the interior
+    kernel's second stream joins the capture through events): after the values are wiped, a
+    replay computes them again."""
+    torch = pytest.importorskip("torch")
+    import ctypes
+    try:
+        rt = ctypes.CDLL("libcudart.so.13")   # the runtime the library is linked against
+    except OSError:
+        rt = ctypes.CDLL("/usr/local/cuda/lib64/libcudart.so.13")
+    p = small_problem("ngon", n=24)
+    s = torch.cuda.Stream()
+    c = nl.nl_create(0, s.cuda_stream)
+    try:
+        keep = nl._Keep()
+        m = nl.nl_assemble(c, nl.make_mesh(p.mesh, keep), nl.config_of(p, keep, prec="fp32c"))
+        try:
+            D0 = nl.to_scipy(c, m)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                nl.nl_assemble_numeric(c, m)
+            assert rt.cudaMemset(ctypes.c_void_p(m.val), 0, ctypes.c_size_t(8 * m.nnz)) == 0
+            assert rt.cudaDeviceSynchronize() == 0
+            assert np.abs(nl.to_scipy(c, m).data).max() == 0.0
+            g.replay()
+            torch.cuda.synchronize()
+            D1 = nl.to_scipy(c, m)
+        finally:
+            nl.nl_csr_free(c, m)
+    finally:
+        nl.nl_destroy(c)
+    np.testing.assert_array_equal(D1.indptr, D0.indptr)
+    np.testing.assert_array_equal(D1.indices, D0.indices)
+    assert np.abs(D1.data - D0.data).max() <= 1e-7 * np.abs(D0.data).max()
+
+
 def test_errors(nl, ctx):
     p = small_problem("nocaps", n=24)
     # delta below the largest triangle diameter
