@@ -367,6 +367,41 @@ def _structure(m, cfg):
     assert ev.min() > -1e-12 * ev.max()
 
 
+def _quadratic_residual(n, ball):
+    """(D U)_j / int phi_j over the nodes whose support and ball lie inside the mesh, U = |x|^2 at
+    the nodes, on the uniform n x n grid over (-delta, 1 + delta)^2 with delta = 0.1 and the
+    constant kernel 4 / (pi delta^4) of Sec. 8."""
+    d = 0.1
+    m = I.split_square_mesh(-d, 1 + d, n)
+    cfg = dict(delta=d, ball=ball, outer="dunavant7", inner="dunavant7", kernel_c=I.const_kernel_c(d))
+    if ball == "ngon":
+        cfg["ngon_off"] = I.ngon_offsets(32, d)
+    D = O.to_csr(O.assemble(m, cfg))
+    U = m.vx ** 2 + m.vy ** 2
+    mass = np.zeros(m.nv)
+    for t in m.tri:
+        mass[t] += _area(np.stack([m.vx[t], m.vy[t]], axis=1)) / 3
+    h = 1.2 / n
+    far = (m.vx > 2 * d + h) & (m.vx < 1 - d - h) & (m.vy > 2 * d + h) & (m.vy < 1 - d - h)
+    assert far.sum() > 100
+    return (D @ U)[far] / mass[far]
+
+
+def test_quadratic_manufactured_solution():
+    # u = |x|^2: -Lu(x) = 2 gamma int_B (|x|^2 - |x + z|^2) dz = -2 gamma int_B |z|^2 dz for a
+    # region B symmetric about x (Eq. (oper)), which is -4 for the Euclidean ball of radius delta
+    # and gamma = 4 / (pi delta^4), and -(2N / (3 pi)) sin(2 pi / N) (2 + cos(2 pi / N)) for the
+    # inscribed regular N-gon (its polar moment).  So (D U)_j = int (-Lu) phi_j is that constant
+    # times int phi_j away from the mesh boundary.  The N-gon's polygonal regions integrate exactly
+    # and reproduce it to rounding; exactcaps' one-point caps converge to -4 under refinement.
+    N = 32
+    ngon = -(2 * N / (3 * math.pi)) * math.sin(2 * math.pi / N) * (2 + math.cos(2 * math.pi / N))
+    np.testing.assert_allclose(_quadratic_residual(24, "ngon"), ngon, rtol=0, atol=1e-10)
+    e24 = np.abs(_quadratic_residual(24, "exactcaps") + 4.0).max()
+    e48 = np.abs(_quadratic_residual(48, "exactcaps") + 4.0).max()
+    assert e24 < 2e-3 and e48 < 2e-4 and e48 < e24 / 8, (e24, e48)
+
+
 @pytest.mark.parametrize("ball", ["bary_nocaps", "bary_approxcaps"])
 def test_outer_support_matrix_structure(ball):
     m, cfg = _small("barycenter", "const")
