@@ -555,6 +555,12 @@ static void add_point(inner_sums *I, const pt *Vb, pt y, double omega)
  * points on each unit panel in u integrates it.  (Duffy's collapse removes the 1/r at
  * the apex; the sinh substitution removes the near-singularity at the foot.)
  */
+/* the near rule's Gauss-Legendre tables hold 1..7 points */
+static int near_rule_ok(const or_cfg *cfg)
+{
+    return cfg->kernel != OR_KERNEL_INV_DIST || (cfg->duffy_n >= 1 && cfg->duffy_n <= 7);
+}
+
 static void near_right_triangle(const or_cfg *cfg, const pt *Vb, pt x, pt F, double ex, double ey,
                                 double d, double tau, double sign, inner_sums *I)
 {
@@ -757,6 +763,7 @@ int or_assemble(const or_mesh *m, const or_cfg *cfg, const int32_t *a_list, int3
 {
     init_rules();
     memset(res, 0, sizeof *res);
+    if (!near_rule_ok(cfg)) return -1;
     if (!rule_of(cfg->inner)) return -1;
     if (cfg->outer != OR_RULE_SWITCH47 && !rule_of(cfg->outer)) return -1;
     if (cfg->shifted && cfg->kernel != OR_KERNEL_CONST) return -1;
@@ -989,6 +996,7 @@ int or_region(const double *tri_xy, double x, double y, const or_cfg *cfg,
 int or_inner(const double *tri_xy, double x, double y, const or_cfg *cfg, double *out, int64_t *nqp)
 {
     init_rules();
+    if (!near_rule_ok(cfg)) return -1;
     pt V[3] = { { tri_xy[0], tri_xy[1] }, { tri_xy[2], tri_xy[3] }, { tri_xy[4], tri_xy[5] } };
     pt X = { x, y };
     region R;

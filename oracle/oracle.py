@@ -213,7 +213,9 @@ def inner(tri_xy, x, cfg_kw):
     t = keep.arr(tri_xy, np.float64).reshape(-1)
     out = np.zeros(13)
     nqp = np.zeros(1, np.int64)
-    L.or_inner(t.ctypes.data, float(x[0]), float(x[1]), ctypes.byref(c), out.ctypes.data, nqp.ctypes.data)
+    rc = L.or_inner(t.ctypes.data, float(x[0]), float(x[1]), ctypes.byref(c), out.ctypes.data, nqp.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the configuration")
     return out[0], out[1:4].copy(), out[4:13].reshape(3, 3).copy(), int(nqp[0])
 
 

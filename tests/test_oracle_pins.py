@@ -367,13 +367,14 @@ def _structure(m, cfg):
     assert ev.min() > -1e-12 * ev.max()
 
 
-def _quadratic_residual(n, ball):
+def _quadratic_residual(n, ball, kernel="const"):
     """(D U)_j / int phi_j over the nodes whose support and ball lie inside the mesh, U = |x|^2 at
     the nodes, on the uniform n x n grid over (-delta, 1 + delta)^2 with delta = 0.1 and the
-    constant kernel 4 / (pi delta^4) of Sec. 8."""
+    constant kernel 4 / (pi delta^4) of Sec. 8 (or the singular kernel 3 / (pi delta^3 |x - y|))."""
     d = 0.1
     m = I.split_square_mesh(-d, 1 + d, n)
-    cfg = dict(delta=d, ball=ball, outer="dunavant7", inner="dunavant7", kernel_c=I.const_kernel_c(d))
+    cfg = dict(delta=d, ball=ball, outer="dunavant7", inner="dunavant7", kernel=kernel,
+               kernel_c=I.const_kernel_c(d) if kernel == "const" else I.inv_dist_kernel_c(d), duffy_n=4)
     if ball == "ngon":
         cfg["ngon_off"] = I.ngon_offsets(32, d)
     D = O.to_csr(O.assemble(m, cfg))
@@ -387,6 +388,18 @@ def _quadratic_residual(n, ball):
     return (D @ U)[far] / mass[far]
 
 
+def test_near_rule_sizes_outside_its_tables_are_rejected():
+    # the near rule's Gauss-Legendre tables hold 1..7 points per panel (as the library's)
+    m, cfg = _small("ngon", kernel="inv_dist")
+    T = np.stack([m.vx[m.tri[0]], m.vy[m.tri[0]]], axis=1)
+    for n in (0, 8):
+        with pytest.raises(ValueError):
+            O.assemble(m, dict(cfg, duffy_n=n))
+        with pytest.raises(ValueError):
+            O.inner(T, T.mean(axis=0), dict(cfg, duffy_n=n))
+    O.inner(T, T.mean(axis=0), dict(cfg, duffy_n=7))
+
+
 def test_quadratic_manufactured_solution():
     # u = |x|^2: -Lu(x) = 2 gamma int_B (|x|^2 - |x + z|^2) dz = -2 gamma int_B |z|^2 dz for a
     # region B symmetric about x (Eq. (oper)), which is -4 for the Euclidean ball of radius delta
@@ -394,9 +407,16 @@ def test_quadratic_manufactured_solution():
     # inscribed regular N-gon (its polar moment).  So (D U)_j = int (-Lu) phi_j is that constant
     # times int phi_j away from the mesh boundary.  The N-gon's polygonal regions integrate exactly
     # and reproduce it to rounding; exactcaps' one-point caps converge to -4 under refinement.
-    N = 32
+    # With psi = 3 / (pi delta^3 |x - y|), -Lu = -2 c int_B |z| dz: -4 on the ball again, and
+    # -2 c (N a^3 / 3) (sec tan + ln(sec + tan)) at pi / N on the N-gon (apothem a), which the
+    # near rule (Duffy collapse, sinh substitution) reaches to its quadrature error.
+    N, d = 32, 0.1
     ngon = -(2 * N / (3 * math.pi)) * math.sin(2 * math.pi / N) * (2 + math.cos(2 * math.pi / N))
     np.testing.assert_allclose(_quadratic_residual(24, "ngon"), ngon, rtol=0, atol=1e-10)
+    a, phi = d * math.cos(math.pi / N), math.pi / N
+    sec, tan = 1 / math.cos(phi), math.tan(phi)
+    ngon_sing = -2 * I.inv_dist_kernel_c(d) * (N * a ** 3 / 3) * (sec * tan + math.log(sec + tan))
+    np.testing.assert_allclose(_quadratic_residual(24, "ngon", "inv_dist"), ngon_sing, rtol=0, atol=1e-6)
     e24 = np.abs(_quadratic_residual(24, "exactcaps") + 4.0).max()
     e48 = np.abs(_quadratic_residual(48, "exactcaps") + 4.0).max()
     assert e24 < 2e-3 and e48 < 2e-4 and e48 < e24 / 8, (e24, e48)
