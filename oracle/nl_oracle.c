@@ -479,6 +479,19 @@ static void disc_region(const pt *V, pt x, const or_cfg *cfg, int ball, region *
     }
 }
 
+/* The inputs the oracle's tables and buffers cover: the near rule's Gauss-Legendre tables hold
+   1..7 points; a region holds at most MAXV vertices (3 + 64 for the N-gon, 6 + 3 (m - 1) for
+   approxcaps with m arc segments, a power of two up to 16). */
+static int cfg_ok(const or_cfg *cfg)
+{
+    if (cfg->kernel == OR_KERNEL_INV_DIST && (cfg->duffy_n < 1 || cfg->duffy_n > 7)) return 0;
+    if (cfg->ball == OR_BALL_NGON && (cfg->ngon_n < 3 || cfg->ngon_n > 64 || !cfg->ngon_off)) return 0;
+    if ((cfg->ball == OR_BALL_APPROXCAPS || cfg->ball == OR_BALL_BARY_APPROXCAPS) &&
+        (cfg->cap_m < 1 || cfg->cap_m > 16 || (cfg->cap_m & (cfg->cap_m - 1)) != 0))
+        return 0;
+    return 1;
+}
+
 /* barycentric coordinates of y in triangle V (P1 basis functions phi_b(y)) */
 static void barycentric(const pt *V, pt y, double *phi)
 {
@@ -555,12 +568,6 @@ static void add_point(inner_sums *I, const pt *Vb, pt y, double omega)
  * points on each unit panel in u integrates it.  (Duffy's collapse removes the 1/r at
  * the apex; the sinh substitution removes the near-singularity at the foot.)
  */
-/* the near rule's Gauss-Legendre tables hold 1..7 points */
-static int near_rule_ok(const or_cfg *cfg)
-{
-    return cfg->kernel != OR_KERNEL_INV_DIST || (cfg->duffy_n >= 1 && cfg->duffy_n <= 7);
-}
-
 static void near_right_triangle(const or_cfg *cfg, const pt *Vb, pt x, pt F, double ex, double ey,
                                 double d, double tau, double sign, inner_sums *I)
 {
@@ -763,7 +770,7 @@ int or_assemble(const or_mesh *m, const or_cfg *cfg, const int32_t *a_list, int3
 {
     init_rules();
     memset(res, 0, sizeof *res);
-    if (!near_rule_ok(cfg)) return -1;
+    if (!cfg_ok(cfg)) return -1;
     if (!rule_of(cfg->inner)) return -1;
     if (cfg->outer != OR_RULE_SWITCH47 && !rule_of(cfg->outer)) return -1;
     if (cfg->shifted && cfg->kernel != OR_KERNEL_CONST) return -1;
@@ -980,6 +987,7 @@ int or_region(const double *tri_xy, double x, double y, const or_cfg *cfg,
               int32_t *kind, int32_t *nverts, double *poly, int32_t *ncaps, double *caps)
 {
     init_rules();
+    if (!cfg_ok(cfg)) return -1;
     pt V[3] = { { tri_xy[0], tri_xy[1] }, { tri_xy[2], tri_xy[3] }, { tri_xy[4], tri_xy[5] } };
     pt X = { x, y };
     region R;
@@ -996,7 +1004,7 @@ int or_region(const double *tri_xy, double x, double y, const or_cfg *cfg,
 int or_inner(const double *tri_xy, double x, double y, const or_cfg *cfg, double *out, int64_t *nqp)
 {
     init_rules();
-    if (!near_rule_ok(cfg)) return -1;
+    if (!cfg_ok(cfg)) return -1;
     pt V[3] = { { tri_xy[0], tri_xy[1] }, { tri_xy[2], tri_xy[3] }, { tri_xy[4], tri_xy[5] } };
     pt X = { x, y };
     region R;

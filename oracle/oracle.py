@@ -200,8 +200,10 @@ def region(tri_xy, x, cfg_kw):
     nc = np.zeros(1, np.int32)
     poly = np.zeros(2 * 128)
     caps = np.zeros(3 * 16)
-    L.or_region(t.ctypes.data, float(x[0]), float(x[1]), ctypes.byref(c), kind.ctypes.data,
-                nv.ctypes.data, poly.ctypes.data, nc.ctypes.data, caps.ctypes.data)
+    rc = L.or_region(t.ctypes.data, float(x[0]), float(x[1]), ctypes.byref(c), kind.ctypes.data,
+                     nv.ctypes.data, poly.ctypes.data, nc.ctypes.data, caps.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected the configuration")
     return int(kind[0]), poly[:2 * nv[0]].reshape(-1, 2).copy(), caps[:3 * nc[0]].reshape(-1, 3).copy()
 
 

@@ -388,16 +388,23 @@ def _quadratic_residual(n, ball, kernel="const"):
     return (D @ U)[far] / mass[far]
 
 
-def test_near_rule_sizes_outside_its_tables_are_rejected():
-    # the near rule's Gauss-Legendre tables hold 1..7 points per panel (as the library's)
+def test_inputs_outside_the_tables_are_rejected():
+    # the oracle covers what the library accepts: near-rule point counts 1..7 (its Gauss-Legendre
+    # tables), 3..64 N-gon vertices, approxcaps arcs of 1..16 segments (a power of two)
     m, cfg = _small("ngon", kernel="inv_dist")
     T = np.stack([m.vx[m.tri[0]], m.vy[m.tri[0]]], axis=1)
-    for n in (0, 8):
+    x = T.mean(axis=0)
+    bad = [dict(cfg, duffy_n=0), dict(cfg, duffy_n=8), dict(cfg, ngon_off=I.ngon_offsets(65, cfg["delta"])),
+           dict(cfg, ball="approxcaps", cap_m=3), dict(cfg, ball="approxcaps", cap_m=32)]
+    for c in bad:
         with pytest.raises(ValueError):
-            O.assemble(m, dict(cfg, duffy_n=n))
+            O.assemble(m, c)
         with pytest.raises(ValueError):
-            O.inner(T, T.mean(axis=0), dict(cfg, duffy_n=n))
-    O.inner(T, T.mean(axis=0), dict(cfg, duffy_n=7))
+            O.inner(T, x, c)
+        with pytest.raises(ValueError):
+            O.region(T, x, c)
+    O.inner(T, x, dict(cfg, duffy_n=7))
+    O.region(T, x, dict(cfg, ball="approxcaps", cap_m=16))
 
 
 def test_quadratic_manufactured_solution():
