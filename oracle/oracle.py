@@ -80,25 +80,31 @@ def lib():
     global _LIB
     if _LIB is None:
         build()
-        L = ctypes.CDLL(SO)
-        L.or_assemble.restype = ctypes.c_int
-        L.or_assemble.argtypes = [ctypes.POINTER(_Mesh), ctypes.POINTER(_Cfg),
-                                  ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
-                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_Res)]
-        L.or_free.argtypes = [ctypes.POINTER(_Res)]
-        L.or_region.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Cfg),
-                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                ctypes.c_void_p]
-        L.or_inner.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Cfg),
-                               ctypes.c_void_p, ctypes.c_void_p]
-        L.or_rule_table.argtypes = [ctypes.c_int32, ctypes.c_void_p]
-        L.or_gauss_legendre.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
-        L.or_record_hash.restype = ctypes.c_uint64
-        L.or_record_hash.argtypes = [ctypes.c_int32] * 6
-        L.or_hmax.restype = ctypes.c_double
-        L.or_hmax.argtypes = [ctypes.POINTER(_Mesh)]
-        _LIB = L
+        _LIB = load(SO)
     return _LIB
+
+
+def load(path: str):
+    """The oracle library at `path` with its entry points typed (lib() loads the built one;
+    a test may load a copy compiled with a planted mistake)."""
+    L = ctypes.CDLL(path)
+    L.or_assemble.restype = ctypes.c_int
+    L.or_assemble.argtypes = [ctypes.POINTER(_Mesh), ctypes.POINTER(_Cfg),
+                              ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_Res)]
+    L.or_free.argtypes = [ctypes.POINTER(_Res)]
+    L.or_region.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Cfg),
+                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                            ctypes.c_void_p]
+    L.or_inner.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Cfg),
+                           ctypes.c_void_p, ctypes.c_void_p]
+    L.or_rule_table.argtypes = [ctypes.c_int32, ctypes.c_void_p]
+    L.or_gauss_legendre.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    L.or_record_hash.restype = ctypes.c_uint64
+    L.or_record_hash.argtypes = [ctypes.c_int32] * 6
+    L.or_hmax.restype = ctypes.c_double
+    L.or_hmax.argtypes = [ctypes.POINTER(_Mesh)]
+    return L
 
 
 def _ptr(a, t):

@@ -1,0 +1,100 @@
+"""The pins catch plausible mistakes (CPU only).  Each case compiles a copy of the oracle with
+one mistake planted in its source (a dropped term, a wrong sign, a wrong index, a transposed
+operand) and checks that the matrix-level pins fail on it: symmetry and zero row sums of D, the
+closed form of a ball that covers the mesh, and the quadratic manufactured solution on the
+N-gon.  The unmodified source passes the same checks."""
+import math
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2005_10775_gb300 import inputs as I
+
+MUTANTS = [
+    ("dropped M_bb block", "hm_add(&maps[tid], (int64_t)bi * m->nv + bk, Mbb[i][k]);", "(void)0;"),
+    ("wrong sign of the transposed M_ab block", "(int64_t)bk * m->nv + ai, -Mab[i][k]",
+     "(int64_t)bk * m->nv + ai, +Mab[i][k]"),
+    ("transposed M_ab operand", "(int64_t)ai * m->nv + bk, -Mab[i][k]", "(int64_t)ai * m->nv + bk, -Mab[k][i]"),
+    ("wrong index in the inner phi_b phi_b sum", "I->S2[i][k] += omega * phi[i] * phi[k];",
+     "I->S2[i][k] += omega * phi[i] * phi[i];"),
+    ("wrong index in the outer phi_a phi_a product", "Maa[i][k] += W * I.s0 * L[i] * L[k];",
+     "Maa[i][k] += W * I.s0 * L[i] * L[i];"),
+    ("dropped barycentric term", "phi[0] = 1.0 - l1 - l2;", "phi[0] = 1.0 - l1;"),
+    ("outer weight without |T_a|", "double W = L[3] * area_a;", "double W = L[3];"),
+]
+
+
+def _compile(tmp_path, name, src):
+    c = tmp_path / f"{name}.c"
+    so = tmp_path / f"lib{name}.so"
+    c.write_text(src)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+                           "-o", str(so), str(c), "-lm"])
+    return O.load(str(so))
+
+
+def _failures():
+    """The matrix-level pins that fail for the oracle currently loaded."""
+    failed = []
+    # symmetry and zero row sums of D (full Omega u Omega_I matrix), N-gon, jittered mesh
+    m = I.split_square_mesh(-0.3, 1.3, 8, jitter=0.2, seed=5)
+    d = 0.45
+    cfg = dict(delta=d, ball="ngon", ngon_off=I.ngon_offsets(32, d), outer="dunavant7", inner="dunavant7",
+               kernel_c=I.const_kernel_c(d))
+    D = O.to_csr(O.assemble(m, cfg)).toarray()
+    scale = np.abs(D).max()
+    if not (np.abs(D - D.T).max() <= 1e-12 * scale and np.abs(D.sum(axis=1)).max() <= 1e-12 * scale):
+        failed.append("structure")
+    # a ball covering the mesh: D = c (2 |Omega| M - 2 m m^T)
+    mc = I.split_square_mesh(0.0, 1.0, 3, jitter=0.2, seed=9, omega=(-1, 2))
+    c = 0.37
+    Dc = O.to_csr(O.assemble(mc, dict(delta=20.0, ball="nocaps", outer="dunavant7", inner="dunavant7",
+                                      kernel_c=c))).toarray()
+    M = np.zeros((mc.nv, mc.nv))
+    mm = np.zeros(mc.nv)
+    tot = 0.0
+    for t in mc.tri:
+        V = np.stack([mc.vx[t], mc.vy[t]], axis=1)
+        A = 0.5 * abs((V[1, 0] - V[0, 0]) * (V[2, 1] - V[0, 1]) - (V[2, 0] - V[0, 0]) * (V[1, 1] - V[0, 1]))
+        tot += A
+        M[np.ix_(t, t)] += A * (np.ones((3, 3)) + np.eye(3)) / 12
+        mm[t] += A / 3
+    ref = c * (2 * tot * M - 2 * np.outer(mm, mm))
+    if not np.abs(Dc - ref).max() <= 1e-12 * np.abs(ref).max():
+        failed.append("covering ball")
+    # u = |x|^2 on the 32-gon: (D U)_j = -(2N / 3 pi) sin(2 pi / N) (2 + cos(2 pi / N)) int phi_j
+    d, N, n = 0.1, 32, 24
+    mq = I.split_square_mesh(-d, 1 + d, n)
+    Dq = O.to_csr(O.assemble(mq, dict(delta=d, ball="ngon", ngon_off=I.ngon_offsets(N, d), outer="dunavant7",
+                                      inner="dunavant7", kernel_c=I.const_kernel_c(d))))
+    mass = np.zeros(mq.nv)
+    for t in mq.tri:
+        V = np.stack([mq.vx[t], mq.vy[t]], axis=1)
+        mass[t] += 0.5 * abs((V[1, 0] - V[0, 0]) * (V[2, 1] - V[0, 1]) - (V[2, 0] - V[0, 0]) * (V[1, 1] - V[0, 1])) / 3
+    h = 1.2 / n
+    far = (mq.vx > 2 * d + h) & (mq.vx < 1 - d - h) & (mq.vy > 2 * d + h) & (mq.vy < 1 - d - h)
+    want = -(2 * N / (3 * math.pi)) * math.sin(2 * math.pi / N) * (2 + math.cos(2 * math.pi / N))
+    got = (Dq @ (mq.vx ** 2 + mq.vy ** 2))[far] / mass[far]
+    if not np.abs(got - want).max() <= 1e-10:
+        failed.append("quadratic")
+    return failed
+
+
+@pytest.fixture(scope="module")
+def source():
+    with open(O.SRC) as f:
+        return f.read()
+
+
+def test_unmodified_oracle_passes(tmp_path, monkeypatch, source):
+    monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "clean", source))
+    assert _failures() == []
+
+
+@pytest.mark.parametrize("what,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(tmp_path, monkeypatch, source, what, old, new):
+    assert source.count(old) >= 1, f"{what}: the line to mutate is not in the oracle"
+    monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "mutant", source.replace(old, new)))
+    assert _failures() != [], f"no pin caught: {what}"
