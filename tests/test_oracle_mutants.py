@@ -98,3 +98,49 @@ def test_planted_mistake_is_caught(tmp_path, monkeypatch, source, what, old, new
     assert source.count(old) >= 1, f"{what}: the line to mutate is not in the oracle"
     monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "mutant", source.replace(old, new)))
     assert _failures() != [], f"no pin caught: {what}"
+
+
+# --------------------------------------------------------------------------
+# geometry mistakes against the region pins
+# --------------------------------------------------------------------------
+
+REGION_MUTANTS = [
+    ("wrong N-gon clip intersection parameter", "double t = ds / (ds - de);", "double t = de / (ds - de);"),
+    ("wrong circle-edge root", "    double l2 = (-bh + s) / a;\n", "    double l2 = (-bh + s) / (2.0 * a);\n"),
+    ("cap area halved", "*area = delta * delta * two_th_minus_sin / (printed ? 4.0 : 2.0);",
+     "*area = delta * delta * two_th_minus_sin / (printed ? 4.0 : 4.0);"),
+    ("arc point off the circle", "double s = delta / sqrt(ux * ux + uy * uy);",
+     "double s = 0.5 * delta / sqrt(ux * ux + uy * uy);"),
+    ("entry and exit roots swapped", "lam[0] = l1; is_entry[0] = 1;", "lam[0] = l1; is_entry[0] = 0;"),
+    ("cap centroid off", "4.0 * delta * st * st * st / (3.0 * two_th_minus_sin)",
+     "2.0 * delta * st * st * st / (3.0 * two_th_minus_sin)"),
+]
+
+
+def _region_failures():
+    """The region-level pins (tests/test_oracle_pins.py) that fail for the oracle loaded."""
+    import test_oracle_pins as P
+    checks = [P.test_nocaps_exactcaps_quarter_disc, P.test_approxcaps_quarter_disc,
+              P.test_ngon_clip_matches_independent_intersection, P.test_support_nesting,
+              P.test_one_edge_cut_twice, P.test_tangent_edge_gives_zero_cap,
+              lambda: P.test_ngon_area_and_moments(0.2), lambda: P.test_exactcaps_and_approxcaps_area(0.2),
+              lambda: P.test_ball_covering_mesh_closed_form("exactcaps", "dunavant7", "dunavant7")]
+    failed = []
+    for k, f in enumerate(checks):
+        try:
+            f()
+        except AssertionError:
+            failed.append(k)
+    return failed
+
+
+def test_unmodified_oracle_passes_the_region_pins(tmp_path, monkeypatch, source):
+    monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "clean", source))
+    assert _region_failures() == []
+
+
+@pytest.mark.parametrize("what,old,new", REGION_MUTANTS, ids=[m[0] for m in REGION_MUTANTS])
+def test_planted_geometry_mistake_is_caught(tmp_path, monkeypatch, source, what, old, new):
+    assert source.count(old) >= 1, f"{what}: the line to mutate is not in the oracle"
+    monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "mutant", source.replace(old, new)))
+    assert _region_failures() != [], f"no pin caught: {what}"
