@@ -144,3 +144,41 @@ def test_planted_geometry_mistake_is_caught(tmp_path, monkeypatch, source, what,
     assert source.count(old) >= 1, f"{what}: the line to mutate is not in the oracle"
     monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "mutant", source.replace(old, new)))
     assert _region_failures() != [], f"no pin caught: {what}"
+
+
+# --------------------------------------------------------------------------
+# near-singular rule mistakes against the singular-kernel pins
+# --------------------------------------------------------------------------
+
+NEAR_MUTANTS = [
+    ("wrong side of the edge's foot", "double sigma = (fx * ey - fy * ex) > 0.0 ? 1.0 : -1.0;",
+     "double sigma = (fx * ey - fy * ex) > 0.0 ? -1.0 : 1.0;"),
+    ("one right triangle of each edge dropped", "        near_right_triangle(cfg, Vb, x, F, ex, ey, d, tA, -sigma, I);\n",
+     "        (void)0;\n"),
+    ("sinh substitution without its Jacobian d", "add_point(I, Vb, y, sign * sg * d * ws * wu * cfg->kernel_c);",
+     "add_point(I, Vb, y, sign * sg * ws * wu * cfg->kernel_c);"),
+    ("Duffy point not scaled in x", "y.x = x.x + sv * wx;", "y.x = x.x + wx;"),
+]
+
+
+def _near_failures():
+    import test_oracle_pins as P
+    failed = []
+    for k, f in enumerate([P.test_singular_kernel_ngon_closed_forms, P.test_quadratic_manufactured_solution]):
+        try:
+            f()
+        except AssertionError:
+            failed.append(k)
+    return failed
+
+
+def test_unmodified_oracle_passes_the_singular_pins(tmp_path, monkeypatch, source):
+    monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "clean", source))
+    assert _near_failures() == []
+
+
+@pytest.mark.parametrize("what,old,new", NEAR_MUTANTS, ids=[m[0] for m in NEAR_MUTANTS])
+def test_planted_near_rule_mistake_is_caught(tmp_path, monkeypatch, source, what, old, new):
+    assert source.count(old) >= 1, f"{what}: the line to mutate is not in the oracle"
+    monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "mutant", source.replace(old, new)))
+    assert _near_failures() != [], f"no pin caught: {what}"
