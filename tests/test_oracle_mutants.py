@@ -182,3 +182,41 @@ def test_planted_near_rule_mistake_is_caught(tmp_path, monkeypatch, source, what
     assert source.count(old) >= 1, f"{what}: the line to mutate is not in the oracle"
     monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "mutant", source.replace(old, new)))
     assert _near_failures() != [], f"no pin caught: {what}"
+
+
+# --------------------------------------------------------------------------
+# the outer-support (barycenter ball, Sec. 6.2) composite against its pins
+# --------------------------------------------------------------------------
+
+SUPPORT_MUTANTS = [
+    ("support M_bb dropped", "                                Mbb[i][k2] += W * I.S2[i][k2];\n", "(void)0;\n"),
+    ("support outer weight without the subtriangle area", "const double W = L[3] * area;",
+     "const double W = L[3];"),
+    ("support outer point from two vertices", "x.x = L[0] * S0.x + L[1] * S1.x + L[2] * S2p.x;",
+     "x.x = L[0] * S0.x + L[1] * S1.x + L[2] * S1.x;"),
+]
+
+
+def _support_failures():
+    import test_oracle_pins as P
+    failed = []
+    checks = [lambda: P.test_outer_support_matrix_structure("bary_nocaps"),
+              lambda: P.test_shifted_ball_equals_barycenter_outer_support("nocaps")]
+    for k, f in enumerate(checks):
+        try:
+            f()
+        except AssertionError:
+            failed.append(k)
+    return failed
+
+
+def test_unmodified_oracle_passes_the_support_pins(tmp_path, monkeypatch, source):
+    monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "clean", source))
+    assert _support_failures() == []
+
+
+@pytest.mark.parametrize("what,old,new", SUPPORT_MUTANTS, ids=[m[0] for m in SUPPORT_MUTANTS])
+def test_planted_support_mistake_is_caught(tmp_path, monkeypatch, source, what, old, new):
+    assert source.count(old) == 1, f"{what}: the line to mutate is not in the oracle once"
+    monkeypatch.setattr(O, "_LIB", _compile(tmp_path, "mutant", source.replace(old, new)))
+    assert _support_failures() != [], f"no pin caught: {what}"
