@@ -154,7 +154,7 @@ nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *inout);
 /* ---- batches of independent problems ----
    Many assemblies of uneven size, delta, ball and rule at once.  Every problem is
    assembled exactly as nl_assemble would (same interaction set and pattern, values
-   equal up to the order of the FP64 scatter additions), but the batch:
+   equal up to the order of the FP64 atomic additions), but the batch:
      - runs each preparation and symbolic stage for all problems before synchronising,
        so the whole batch waits on the host three times, not three times per problem,
        with the problems spread over eight streams of the context (joined by events);
