@@ -377,8 +377,6 @@ nl_status nl_host_slots(nl_ctx *ctx, int n, nl_host_slot **out)
     return NL_OK;
 }
 
-nl_status nl_run_numeric(nl_ctx *ctx, nl_plan *P, bool with_hash) { return run_numeric(ctx, P, with_hash); }
-
 // ---------------------------------------------------------------------------
 // entry points
 // ---------------------------------------------------------------------------

@@ -127,7 +127,6 @@ struct nl_plan {
     void *defer = nullptr;
     int *defer_n = nullptr;
     int defer_cap = 0;
-    int64_t blk_elems() const { return 9 * E; }
 };
 
 // ---- error helpers ----
@@ -213,9 +212,7 @@ void nl_pat_delete(nl_pat *T, cudaStream_t s);
 nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_slot *h);
 // B (slot A read): column indices, slot maps, value buffers
 nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl_host_slot *h);
-nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out);
 
-nl_status nl_run_numeric(nl_ctx *ctx, nl_plan *P, bool with_hash);
 nl_status nl_alloc_numeric(nl_ctx *ctx, nl_plan *P);
 nl_status nl_run_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out);
 

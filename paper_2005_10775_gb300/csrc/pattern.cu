@@ -819,21 +819,6 @@ nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl
     return NL_OK;
 }
 
-nl_status nl_build_pattern(nl_ctx *ctx, nl_plan *P, nl_csr *out)
-{
-    nl_host_slot *h = nullptr;
-    nl_status s = nl_host_slots(ctx, 1, &h);
-    if (s != NL_OK) return s;
-    nl_pat *T = nl_pat_new();
-    if (!T) return nl_fail(ctx, NL_ENOMEM, "host allocation failed");
-    if ((s = nl_pattern_a(ctx, P, out, T, h)) == NL_OK) {
-        cudaError_t e = cudaStreamSynchronize(ctx->stream);
-        s = e == cudaSuccess ? nl_pattern_b(ctx, P, out, T, h) : nl_cuda_fail(ctx, e, "cudaStreamSynchronize");
-    }
-    nl_pat_delete(T, ctx->stream);
-    return s;
-}
-
 // Shared-memory plan of the scatter for rows of at most max_row columns: cap per row (a
 // multiple of 4), a hash table of 2^hbits >= 1.25 cap slots (the three rows of a triangle's
 // nodes share most columns: their union is about 1.15 rows, a load near 0.9 at worst; a
