@@ -10,12 +10,13 @@
 // Eq. (bformhj) over the six local nodes (Sec. 7.2):
 //     M_aa += W s0 phi_a phi_a^T,   M_bb += W S2,   M_ab += W phi_a s1^T
 // (D receives +M_aa, +M_bb, -M_ab and -M_ab^T).  Per candidate pair the lane writes
-// M_ab (9) and M_bb (6, symmetric) to a pair buffer and a directed interaction
-// flag; M_aa is summed over all candidates in FP64 and reduced across the warp.
+// M_ab (9) to a pair buffer and a directed interaction flag, and adds the upper M_bb (6,
+// symmetric) onto T_b's per-triangle sums (FP64 atomics); M_aa is summed over all
+// candidates in FP64 and reduced across the warp.
 //
 // T = double: FP64 quadrature.  T = float: the inner and per-pair sums run in FP32,
-// the long sums (M_aa over all neighbours, and D over all pairs in the scatter) in
-// FP64, which compensates the FP32 rounding of the short sums.
+// the long sums (M_aa over all neighbours, M_bb over all pairs of T_b, and D over all
+// pairs in the scatter) in FP64, which compensates the FP32 rounding of the short sums.
 #pragma once
 
 #include "geometry.cuh"
