@@ -4,7 +4,8 @@
 // Eq. (bformjqqh)) exactly as nl_assemble performs it; what the batch changes is
 // how the work reaches the GPU:
 //   * preparation and symbolic stages run for every problem before the host waits,
-//     so a batch synchronises three times in all;
+//     so a batch synchronises three times in all, with the problems spread over the
+//     context's eight side streams (problem i on stream i mod 8, joined by events);
 //   * the numeric phase of every problem runs in a few persistent launches: the
 //     interior candidates of all problems of a value type (nlq::k_interior_batch), then
 //     the boundary candidates of all problems of a ball mode x kernel type
