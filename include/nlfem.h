@@ -15,8 +15,9 @@
  * Conventions shared by every entry point:
  *   - Every call returns nl_status; nothing aborts, traps or exits.  On failure
  *     nl_last_error(ctx) returns a one-line description (valid until the next call).
- *   - Input pointers may be host or device memory (detected per pointer); the
- *     caller keeps ownership and may free them when the call returns.
+ *   - Input pointers may be host or device memory (detected per pointer; device memory
+ *     must be the context's device's, else NL_EINVAL); the caller keeps ownership and may
+ *     free them when the call returns.
  *   - Outputs in nl_csr are device buffers owned by the library, released with
  *     nl_csr_free.  Work is ordered on the context's CUDA stream.
  *   - Indices are 0-based; triangles are counter-clockwise.
@@ -237,7 +238,14 @@ nl_status nl_matvec(nl_ctx *ctx, const nl_csr *A, const double *x, double *y, in
 /* Solve A x = b (A symmetric positive definite, Sec. 2) by conjugate gradients with
    FP32 matrix-vector products and FP64 residual refinement until ||b - A x|| <= rtol ||b||
    (the paper names no solver, Sec. 7.2 "reduced sparsity" remark).  x holds the initial
-   guess on entry.  Returns NL_ENOCONV if max_it inner iterations do not suffice. */
+   guess on entry and the last iterate on return.  b, x: [A->n], host or device memory of
+   the context's device.  NL_OK only when the tolerance is reached; otherwise:
+     NL_ENOCONV  max_it inner iterations, or 64 FP64 refinement passes (an rtol below the
+                 FP64 residual floor), did not reach it; or a breakdown: a search direction
+                 with p.Ap <= 0 or not a number (A not positive definite);
+     NL_EINVAL   the residual is not finite (a NaN or an Inf in A, b or x), or a vector
+                 lives on another device.
+   *iters and *relres are set on every return (0 and +inf before the first residual). */
 nl_status nl_cg(nl_ctx *ctx, const nl_csr *A, const double *b, double *x, double rtol, int32_t max_it,
                 int32_t *iters, double *relres);
 
@@ -259,8 +267,9 @@ nl_status nl_last_timings(nl_ctx *ctx, double *ms4);
    device memory to its own caching allocator or a reserved arena, or a latency-critical
    loop that cannot take an allocation's synchronisation on every call.  The paper has no
    counterpart; this is a deployment variant of nl_cg.  Same arguments, results and
-   errors as nl_cg, except:
-     - A (row_ptr, col_idx, val), b and x must be device pointers (else NL_EINVAL);
+   errors as nl_cg (NL_OK only when the tolerance is reached), except:
+     - A (row_ptr, col_idx, val), b and x must be device pointers of the context's device
+       (else NL_EINVAL);
      - A->n must not exceed 262144 (else NL_EUNSUPPORTED): the work vectors live in one
        fixed file-scope device array of about 6 MB that every GPU loading the library
        keeps until the process exits, and no cudaMalloc or cudaFree is called;

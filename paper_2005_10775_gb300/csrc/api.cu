@@ -37,11 +37,25 @@ bool nl_is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+int nl_ptr_kind(const void *p, int device)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return NL_PTR_HOST;
+    }
+    if (at.type == cudaMemoryTypeManaged) return NL_PTR_DEVICE;
+    if (at.type == cudaMemoryTypeDevice) return at.device == device ? NL_PTR_DEVICE : NL_PTR_OTHER;
+    return NL_PTR_HOST;
+}
+
 // device view of a host-or-device input; *owned says whether the caller must free it
 nl_status nl_stage(nl_ctx *ctx, const void *src, size_t bytes, void **dev, bool *owned)
 {
     *owned = false;
-    if (nl_is_device_ptr(src)) {
+    const int kind = nl_ptr_kind(src, ctx->device);
+    if (kind == NL_PTR_OTHER) return nl_fail(ctx, NL_EINVAL, "an input lives on another device than the context's");
+    if (kind == NL_PTR_DEVICE) {
         *dev = const_cast<void *>(src);
         return NL_OK;
     }

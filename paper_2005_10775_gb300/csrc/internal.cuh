@@ -249,4 +249,38 @@ double nl_polygon_inradius(const double *offsets, int n);
 
 // host pointer / device pointer staging
 bool nl_is_device_ptr(const void *p);
+// where p lives, seen from the context's device: host memory, device memory the context's
+// kernels may read (its own device's, or managed), or another device's memory (rejected:
+// the kernels would dereference it as a peer pointer)
+enum { NL_PTR_HOST = 0, NL_PTR_DEVICE = 1, NL_PTR_OTHER = 2 };
+int nl_ptr_kind(const void *p, int device);
+// device view of a host-or-device input; *owned: the call staged a copy it must free.
+// NL_EINVAL for memory of another device.
 nl_status nl_stage(nl_ctx *ctx, const void *src, size_t bytes, void **dev, bool *owned);
+
+// Stream-ordered temporaries of one call: every buffer taken with get() (or handed over with
+// adopt()) is released with cudaFreeAsync on the context's stream when the holder goes out of
+// scope, so that no return path, early error returns included, leaks one.
+struct nl_temps {
+    cudaStream_t s;
+    std::vector<void *> p;
+    explicit nl_temps(cudaStream_t st) : s(st) {}
+    nl_temps(const nl_temps &) = delete;
+    nl_temps &operator=(const nl_temps &) = delete;
+    ~nl_temps()
+    {
+        for (void *q : p)
+            if (q) cudaFreeAsync(q, s);
+    }
+    template <class T>
+    nl_status get(nl_ctx *ctx, T **out, size_t n)
+    {
+        nl_status st = nl_alloc(ctx, out, n);
+        if (st == NL_OK) p.push_back((void *)*out);
+        return st;
+    }
+    void adopt(void *q)
+    {
+        if (q) p.push_back(q);
+    }
+};

@@ -34,7 +34,12 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 struct NaScal {
     double rho, pq, zz, rr, bb;
+    int brk;   // breakdown: p.Ap not positive (or not a number) while the residual is not yet zero
 };
+
+// below rho = 1e-20 the inner iteration has converged (the host stops it); above it a
+// direction with p.Ap <= 0 or a non-finite p.Ap ends the solve
+constexpr double kBreakdownRho = 1e-20;
 
 struct NaView {
     double *r;
@@ -91,6 +96,7 @@ __global__ void k_na_clear(NaScal *sc)
     sc->zz = 0.0;
     sc->rr = 0.0;
     sc->bb = 0.0;
+    sc->brk = 0;
 }
 
 // sum of v over the block's warps (lane 0 of each warp holds its warp's v), added to *dst by
@@ -141,6 +147,7 @@ __global__ void k_na_init(int n, const double *r, double inv_norm, float *z, flo
         sc->rho = 1.0;
         sc->pq = 0.0;
         sc->zz = 0.0;
+        sc->brk = 0;
     }
 }
 
@@ -165,7 +172,8 @@ __global__ void k_na_update(int n, const float *p, const float *q, float *d, flo
     __shared__ double part[8];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double pq = sc->pq;
-    float alpha = pq != 0.0 ? (float)(sc->rho / pq) : 0.0f;
+    float alpha = (pq > 0.0) ? (float)(sc->rho / pq) : 0.0f;
+    if (i == 0 && sc->rho > kBreakdownRho && !(pq > 0.0)) sc->brk = 1;
     double zz = 0.0;
     if (i < n) {
         d[i] += alpha * p[i];
@@ -209,15 +217,19 @@ extern "C" nl_status nl_cg_noalloc(nl_ctx *ctx, const nl_csr *A, const double *b
                                    int32_t max_it, int32_t *iters, double *relres)
 {
     if (!ctx) return NL_EINVAL;
+    if (iters) *iters = 0;
+    if (relres) *relres = INFINITY;
     if (!A || !b || !x) return nl_fail(ctx, NL_EINVAL, "null argument");
     if (!(rtol > 0.0) || max_it < 1) return nl_fail(ctx, NL_EINVAL, "need rtol > 0 and max_it >= 1");
     if (A->n < 0 || (int64_t)A->n > kMaxN)
         return nl_fail(ctx, NL_EUNSUPPORTED, "nl_cg_noalloc accepts at most " + std::to_string(kMaxN) +
                                                  " unknowns (got " + std::to_string(A->n) + "); use nl_cg");
     const int n = A->n;
-    if (n > 0 && (!nl_is_device_ptr(b) || !nl_is_device_ptr(x) || !nl_is_device_ptr(A->row_ptr) ||
-                  (A->nnz > 0 && (!nl_is_device_ptr(A->col_idx) || !nl_is_device_ptr(A->val)))))
-        return nl_fail(ctx, NL_EINVAL, "nl_cg_noalloc needs device pointers for the matrix, b and x");
+    auto on_dev = [&](const void *p) { return nl_ptr_kind(p, ctx->device) == NL_PTR_DEVICE; };
+    if (n > 0 && (!on_dev(b) || !on_dev(x) || !on_dev(A->row_ptr) ||
+                  (A->nnz > 0 && (!on_dev(A->col_idx) || !on_dev(A->val)))))
+        return nl_fail(ctx, NL_EINVAL, "nl_cg_noalloc needs device pointers on the context's device for the "
+                                       "matrix, b and x");
     void *base = nullptr;
     nl_status s = scratch_address(ctx, &base);
     if (s != NL_OK) return s;
@@ -226,10 +238,12 @@ extern "C" nl_status nl_cg_noalloc(nl_ctx *ctx, const nl_csr *A, const double *b
     const unsigned rows = (unsigned)(((int64_t)n * 32 + 255) / 256), eg = (unsigned)((n + 255) / 256);
     const int kCheck = 8;
     const double kInnerTol = 1e-5;
+    const int kPasses = 64;   // FP64 refinement passes
     int total = 0;
     double rel = INFINITY;
+    bool conv = false, stop = false;
     nl_status out = NL_OK;
-    for (int outer = 0; outer < 64; outer++) {
+    for (int outer = 0; outer < kPasses && !stop; outer++) {
         k_na_clear<<<1, 1, 0, ctx->stream>>>(v.sc); ++ctx->launches;
         if (n > 0) {
             k_na_residual<<<rows, 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, A->val, x, b, v.r, v.sc);
@@ -240,7 +254,14 @@ extern "C" nl_status nl_cg_noalloc(nl_ctx *ctx, const nl_csr *A, const double *b
         NL_CK(cudaStreamSynchronize(ctx->stream));
         double rn = sqrt(h.rr), bn = sqrt(h.bb);
         rel = bn > 0.0 ? rn / bn : rn;
-        if (rel <= rtol || rn == 0.0) break;
+        if (!isfinite(rel)) {
+            out = nl_fail(ctx, NL_EINVAL, "non-finite residual: A, b or the initial x holds a NaN or an Inf");
+            break;
+        }
+        if (rel <= rtol || rn == 0.0) {
+            conv = true;
+            break;
+        }
         if (total >= max_it) {
             out = nl_fail(ctx, NL_ENOCONV, "CG did not reach the tolerance within max_it iterations");
             break;
@@ -260,11 +281,21 @@ extern "C" nl_status nl_cg_noalloc(nl_ctx *ctx, const nl_csr *A, const double *b
             NaScal hs;
             NL_CK(cudaMemcpyAsync(&hs, v.sc, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
             NL_CK(cudaStreamSynchronize(ctx->stream));
-            if (!(sqrt(hs.rho) > kInnerTol)) break;
+            if (hs.brk || !isfinite(hs.rho)) {   // breakdown: the correction d is not usable
+                out = nl_fail(ctx, NL_ENOCONV, "CG breakdown: a search direction with p.Ap <= 0 or not a number "
+                                               "(A not symmetric positive definite, or non-finite values)");
+                stop = true;
+                break;
+            }
+            if (!(sqrt(hs.rho) > kInnerTol)) break;   // inner tolerance reached
         }
+        if (stop) break;
         k_na_axpy<<<eg, 256, 0, ctx->stream>>>(n, rn, v.d, x); ++ctx->launches;
         NL_CK(cudaGetLastError());
     }
+    if (out == NL_OK && !conv)
+        out = nl_fail(ctx, NL_ENOCONV, "CG did not reach the tolerance within " + std::to_string(kPasses) +
+                                           " FP64 refinement passes (is rtol above the FP64 residual floor?)");
     NL_CK(cudaStreamSynchronize(ctx->stream));
     if (iters) *iters = total;
     if (relres) *relres = rel;

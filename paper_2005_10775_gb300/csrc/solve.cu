@@ -182,7 +182,13 @@ __global__ void k_residual(int n, const int64_t *rp, const int32_t *__restrict__
 // inner FP32 conjugate gradients on A d = z0 (z0 = r / ||r||)
 struct CgScal {
     double rho, pq, zz;
+    int brk;   // breakdown: p.Ap not positive (or not a number) while the residual is not yet zero
 };
+
+// a direction with p.Ap <= 0 (A not positive definite along p) or a non-finite p.Ap ends the
+// solve; below rho = 1e-20 (the inner residual 1e-10 of its start) the iteration has converged
+// and the host stops it
+constexpr double kBreakdownRho = 1e-20;
 
 __global__ void k_cg_init(int n, const double *r, double inv_norm, float *z, float *p, float *d, CgScal *sc)
 {
@@ -197,6 +203,7 @@ __global__ void k_cg_init(int n, const double *r, double inv_norm, float *z, flo
         sc->rho = 1.0;
         sc->pq = 0.0;
         sc->zz = 0.0;
+        sc->brk = 0;
     }
 }
 
@@ -220,7 +227,9 @@ __global__ void k_cg_update(int n, const float *p, const float *q, float *d, flo
     __shared__ double part[8];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double pq = sc->pq;
-    float alpha = pq != 0.0 ? (float)(sc->rho / pq) : 0.0f;
+    const bool brk = sc->rho > kBreakdownRho && !(pq > 0.0);
+    float alpha = (pq > 0.0) ? (float)(sc->rho / pq) : 0.0f;
+    if (i == 0 && brk) sc->brk = 1;
     double zz = 0.0;
     if (i < n) {
         d[i] += alpha * p[i];
@@ -280,27 +289,20 @@ nl_status ensure_f32(nl_ctx *ctx, nl_csr *A)
 
 unsigned wgrid(int64_t rows) { return (unsigned)((rows * 32 + 255) / 256); }
 
-}  // namespace
-
-extern "C" {
-
-nl_status nl_extract(nl_ctx *ctx, const nl_csr *D, const nl_mesh *mesh, nl_csr *A, nl_csr *B)
+nl_status extract_body(nl_ctx *ctx, const nl_csr *D, const nl_mesh *mesh, nl_csr *A, nl_csr *B)
 {
-    if (!ctx) return NL_EINVAL;
-    if (!D || !mesh || !A || !B || !mesh->node_in_omega) return nl_fail(ctx, NL_EINVAL, "null argument");
-    if (mesh->nv != D->n) return nl_fail(ctx, NL_EINVAL, "mesh and matrix sizes differ");
-    memset(A, 0, sizeof *A);
-    memset(B, 0, sizeof *B);
+    nl_temps tmp(ctx->stream);
     const int J = D->n;
     nl_status s;
     void *lab = nullptr;
     bool own = false;
     if ((s = nl_stage(ctx, mesh->node_in_omega, (size_t)J, &lab, &own)) != NL_OK) return s;
+    if (own) tmp.adopt(lab);
     int64_t *inO, *inI, *ro, *ri, *cA, *cB;
-    NL_CK(cudaMallocAsync((void **)&inO, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&inI, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ro, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ri, sizeof(int64_t) * (J + 1), ctx->stream));
+    if ((s = tmp.get(ctx, &inO, (size_t)J + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &inI, (size_t)J + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &ro, (size_t)J + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &ri, (size_t)J + 1)) != NL_OK) return s;
     k_labels<<<(J + 255) / 256, 256, 0, ctx->stream>>>(J, (const uint8_t *)lab, inO, inI); ++ctx->launches;
     if ((s = nl_scan_i64(ctx, inO, ro, J)) != NL_OK) return s;
     if ((s = nl_scan_i64(ctx, inI, ri, J)) != NL_OK) return s;
@@ -308,8 +310,8 @@ nl_status nl_extract(nl_ctx *ctx, const nl_csr *D, const nl_mesh *mesh, nl_csr *
     NL_CK(cudaMemcpyAsync(&nO, ro + J, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
     NL_CK(cudaMemcpyAsync(&nI, ri + J, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
     NL_CK(cudaStreamSynchronize(ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&cA, sizeof(int64_t) * (nO + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&cB, sizeof(int64_t) * (nO + 1), ctx->stream));
+    if ((s = tmp.get(ctx, &cA, (size_t)nO + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &cB, (size_t)nO + 1)) != NL_OK) return s;
     k_split<<<wgrid(J), 256, 0, ctx->stream>>>(J, D->row_ptr, D->col_idx, D->val, (const uint8_t *)lab, ro, ri, cA,
                                                cB, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0); ++ctx->launches;
     NL_CK(cudaGetLastError());
@@ -335,16 +337,29 @@ nl_status nl_extract(nl_ctx *ctx, const nl_csr *D, const nl_mesh *mesh, nl_csr *
     nl_plan *PB = plan_of(B);
     if (!PB) return nl_fail(ctx, NL_ENOMEM, "host allocation failed");
     PB->ncols = (int32_t)nI;
-    NL_CK(cudaFreeAsync(inO, ctx->stream));
-    NL_CK(cudaFreeAsync(inI, ctx->stream));
-    NL_CK(cudaFreeAsync(ro, ctx->stream));
-    NL_CK(cudaFreeAsync(ri, ctx->stream));
-    NL_CK(cudaFreeAsync(cA, ctx->stream));
-    NL_CK(cudaFreeAsync(cB, ctx->stream));
-    if (own) NL_CK(cudaFreeAsync(lab, ctx->stream));
     NL_CK(cudaStreamSynchronize(ctx->stream));
     return NL_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+nl_status nl_extract(nl_ctx *ctx, const nl_csr *D, const nl_mesh *mesh, nl_csr *A, nl_csr *B)
+{
+    if (!ctx) return NL_EINVAL;
+    if (!D || !mesh || !A || !B || !mesh->node_in_omega) return nl_fail(ctx, NL_EINVAL, "null argument");
+    if (mesh->nv != D->n) return nl_fail(ctx, NL_EINVAL, "mesh and matrix sizes differ");
+    memset(A, 0, sizeof *A);
+    memset(B, 0, sizeof *B);
+    const nl_status s = extract_body(ctx, D, mesh, A, B);
+    if (s != NL_OK) {   // no partial results
+        nl_csr_free(ctx, A);
+        nl_csr_free(ctx, B);
+    }
+    return s;
+}
+
 
 nl_status nl_rhs(nl_ctx *ctx, const nl_csr *B, const nl_mesh *mesh, const double *f_nodal, const double *g_nodal,
                  double *F)
@@ -354,6 +369,7 @@ nl_status nl_rhs(nl_ctx *ctx, const nl_csr *B, const nl_mesh *mesh, const double
         return nl_fail(ctx, NL_EINVAL, "null argument (nl_rhs needs both node and element labels)");
     const int J = mesh->nv, K = mesh->nt;
     nl_status s;
+    nl_temps tmp(ctx->stream);   // released on every return path
     void *lab, *elem, *vx, *vy, *tri, *f, *g;
     bool o1, o2, o3, o4, o5, o6, o7;
     if ((s = nl_stage(ctx, mesh->node_in_omega, (size_t)J, &lab, &o1)) != NL_OK) return s;
@@ -363,17 +379,23 @@ nl_status nl_rhs(nl_ctx *ctx, const nl_csr *B, const nl_mesh *mesh, const double
     if ((s = nl_stage(ctx, mesh->tri, sizeof(int32_t) * 3 * K, &tri, &o5)) != NL_OK) return s;
     if ((s = nl_stage(ctx, f_nodal, sizeof(double) * J, &f, &o6)) != NL_OK) return s;
     if ((s = nl_stage(ctx, g_nodal, sizeof(double) * J, &g, &o7)) != NL_OK) return s;
+    {
+        void *st[] = {lab, elem, vx, vy, tri, f, g};
+        bool own[] = {o1, o2, o3, o4, o5, o6, o7};
+        for (int i = 0; i < 7; i++)
+            if (own[i]) tmp.adopt(st[i]);
+    }
     int64_t *inO, *inI, *ro, *ri;
     int32_t *omap, *imap;
     double *G, *gI, *Fd;
-    NL_CK(cudaMallocAsync((void **)&inO, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&inI, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ro, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&ri, sizeof(int64_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&omap, sizeof(int32_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&imap, sizeof(int32_t) * (J + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&G, sizeof(double) * J, ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&gI, sizeof(double) * (J + 1), ctx->stream));
+    if ((s = tmp.get(ctx, &inO, (size_t)J + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &inI, (size_t)J + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &ro, (size_t)J + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &ri, (size_t)J + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &omap, (size_t)J + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &imap, (size_t)J + 1)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &G, (size_t)J)) != NL_OK) return s;
+    if ((s = tmp.get(ctx, &gI, (size_t)J + 1)) != NL_OK) return s;
     NL_CK(cudaMemsetAsync(G, 0, sizeof(double) * J, ctx->stream));
     k_labels<<<(J + 255) / 256, 256, 0, ctx->stream>>>(J, (const uint8_t *)lab, inO, inI); ++ctx->launches;
     if ((s = nl_scan_i64(ctx, inO, ro, J)) != NL_OK) return s;
@@ -387,21 +409,14 @@ nl_status nl_rhs(nl_ctx *ctx, const nl_csr *B, const nl_mesh *mesh, const double
     NL_CK(cudaStreamSynchronize(ctx->stream));
     if (nO != B->n) return nl_fail(ctx, NL_EINVAL, "B does not match the mesh labels");
     k_gather<<<(unsigned)((nI + 255) / 256 + 1), 256, 0, ctx->stream>>>((int)nI, imap, (const double *)g, gI); ++ctx->launches;
-    bool dev_out = nl_is_device_ptr(F);
+    const int fk = nl_ptr_kind(F, ctx->device);
+    if (fk == NL_PTR_OTHER) return nl_fail(ctx, NL_EINVAL, "F lives on another device than the context's");
+    const bool dev_out = fk == NL_PTR_DEVICE;
     if (dev_out) Fd = F;
-    else NL_CK(cudaMallocAsync((void **)&Fd, sizeof(double) * (nO + 1), ctx->stream));
+    else if ((s = tmp.get(ctx, &Fd, (size_t)nO + 1)) != NL_OK) return s;
     k_rhs<<<wgrid(nO), 256, 0, ctx->stream>>>((int)nO, B->row_ptr, B->col_idx, B->val, gI, omap, G, Fd); ++ctx->launches;
     NL_CK(cudaGetLastError());
-    if (!dev_out) {
-        NL_CK(cudaMemcpyAsync(F, Fd, sizeof(double) * nO, cudaMemcpyDeviceToHost, ctx->stream));
-        NL_CK(cudaFreeAsync(Fd, ctx->stream));
-    }
-    void *tmp[] = {inO, inI, ro, ri, omap, imap, G, gI};
-    for (void *p : tmp) NL_CK(cudaFreeAsync(p, ctx->stream));
-    void *st[] = {lab, elem, vx, vy, tri, f, g};
-    bool own[] = {o1, o2, o3, o4, o5, o6, o7};
-    for (int i = 0; i < 7; i++)
-        if (own[i]) NL_CK(cudaFreeAsync(st[i], ctx->stream));
+    if (!dev_out) NL_CK(cudaMemcpyAsync(F, Fd, sizeof(double) * nO, cudaMemcpyDeviceToHost, ctx->stream));
     NL_CK(cudaStreamSynchronize(ctx->stream));
     return NL_OK;
 }
@@ -415,12 +430,16 @@ nl_status nl_matvec(nl_ctx *ctx, const nl_csr *Ac, const double *x, double *y, i
     int ncols = n;
     if (A->priv && ((nl_plan *)A->priv)->ncols) ncols = ((nl_plan *)A->priv)->ncols;
     nl_status s;
+    nl_temps tmp(ctx->stream);   // host operands only: none with device x and y (stream-ordered call)
     void *xd;
     bool ox;
     if ((s = nl_stage(ctx, x, sizeof(double) * ncols, &xd, &ox)) != NL_OK) return s;
-    bool dev_out = nl_is_device_ptr(y);
+    if (ox) tmp.adopt(xd);
+    const int yk = nl_ptr_kind(y, ctx->device);
+    if (yk == NL_PTR_OTHER) return nl_fail(ctx, NL_EINVAL, "y lives on another device than the context's");
+    const bool dev_out = yk == NL_PTR_DEVICE;
     double *yd = y;
-    if (!dev_out) NL_CK(cudaMallocAsync((void **)&yd, sizeof(double) * (n + 1), ctx->stream));
+    if (!dev_out && (s = tmp.get(ctx, &yd, (size_t)n + 1)) != NL_OK) return s;
     if (prec == NL_PREC_FP64) {
         k_spmv<double, double, double><<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, A->val,
                                                                            (const double *)xd, yd);
@@ -440,11 +459,7 @@ nl_status nl_matvec(nl_ctx *ctx, const nl_csr *Ac, const double *x, double *y, i
         ++ctx->launches;
     }
     NL_CK(cudaGetLastError());
-    if (!dev_out) {
-        NL_CK(cudaMemcpyAsync(y, yd, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
-        NL_CK(cudaFreeAsync(yd, ctx->stream));
-    }
-    if (ox) NL_CK(cudaFreeAsync(xd, ctx->stream));
+    if (!dev_out) NL_CK(cudaMemcpyAsync(y, yd, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
     // host buffers: the copies must be complete when the call returns; device buffers: stream-ordered
     if (!dev_out || ox) NL_CK(cudaStreamSynchronize(ctx->stream));
     return NL_OK;
@@ -454,39 +469,46 @@ nl_status nl_cg(nl_ctx *ctx, const nl_csr *Ac, const double *b, double *x, doubl
                 int32_t *iters, double *relres)
 {
     if (!ctx) return NL_EINVAL;
+    if (iters) *iters = 0;
+    if (relres) *relres = INFINITY;
     if (!Ac || !b || !x) return nl_fail(ctx, NL_EINVAL, "null argument");
     if (!(rtol > 0.0) || max_it < 1) return nl_fail(ctx, NL_EINVAL, "need rtol > 0 and max_it >= 1");
     nl_csr *A = const_cast<nl_csr *>(Ac);
     const int n = A->n;
     nl_status s;
+    // every temporary below is released on every return path (stream-ordered)
+    nl_temps tmp(ctx->stream);
     if ((s = ensure_f32(ctx, A)) != NL_OK) return s;
     const float *v32 = ((nl_plan *)A->priv)->val32;
     void *bd;
     bool ob;
     if ((s = nl_stage(ctx, b, sizeof(double) * n, &bd, &ob)) != NL_OK) return s;
-    bool dev_x = nl_is_device_ptr(x);
+    if (ob) tmp.adopt(bd);
+    const int xk = nl_ptr_kind(x, ctx->device);
+    if (xk == NL_PTR_OTHER) return nl_fail(ctx, NL_EINVAL, "x lives on another device than the context's");
+    const bool dev_x = xk == NL_PTR_DEVICE;
     double *xd = x;
     if (!dev_x) {
-        NL_CK(cudaMallocAsync((void **)&xd, sizeof(double) * (n + 1), ctx->stream));
+        if ((s = tmp.get(ctx, &xd, (size_t)n + 1)) != NL_OK) return s;
         NL_CK(cudaMemcpyAsync(xd, x, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
     }
     double *r, *acc;
     float *z, *p, *q, *d;
     CgScal *sc;
-    NL_CK(cudaMallocAsync((void **)&r, sizeof(double) * (n + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&acc, sizeof(double) * 2, ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&z, sizeof(float) * (n + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&p, sizeof(float) * (n + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&q, sizeof(float) * (n + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&d, sizeof(float) * (n + 1), ctx->stream));
-    NL_CK(cudaMallocAsync((void **)&sc, sizeof(CgScal), ctx->stream));
+    if ((s = tmp.get(ctx, &r, (size_t)n + 1)) != NL_OK || (s = tmp.get(ctx, &acc, 2)) != NL_OK ||
+        (s = tmp.get(ctx, &z, (size_t)n + 1)) != NL_OK || (s = tmp.get(ctx, &p, (size_t)n + 1)) != NL_OK ||
+        (s = tmp.get(ctx, &q, (size_t)n + 1)) != NL_OK || (s = tmp.get(ctx, &d, (size_t)n + 1)) != NL_OK ||
+        (s = tmp.get(ctx, &sc, 1)) != NL_OK)
+        return s;
     const unsigned eg = (unsigned)((n + 255) / 256);
     int total = 0;
     double rel = INFINITY;
+    bool conv = false, stop = false;
     nl_status out = NL_OK;
     const int kCheck = 8;          // inner iterations between host convergence checks
     const double kInnerTol = 1e-5; // inner relative reduction per refinement step
-    for (int outer = 0; outer < 64; outer++) {
+    const int kPasses = 64;        // FP64 refinement passes
+    for (int outer = 0; outer < kPasses && !stop; outer++) {
         NL_CK(cudaMemsetAsync(acc, 0, sizeof(double) * 2, ctx->stream));
         k_residual<<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, A->val, xd, (const double *)bd, r,
                                                       acc); ++ctx->launches;
@@ -495,7 +517,14 @@ nl_status nl_cg(nl_ctx *ctx, const nl_csr *Ac, const double *b, double *x, doubl
         NL_CK(cudaStreamSynchronize(ctx->stream));
         double rn = sqrt(h[0]), bn = sqrt(h[1]);
         rel = bn > 0.0 ? rn / bn : rn;
-        if (rel <= rtol || rn == 0.0) break;
+        if (!isfinite(rel)) {
+            out = nl_fail(ctx, NL_EINVAL, "non-finite residual: A, b or the initial x holds a NaN or an Inf");
+            break;
+        }
+        if (rel <= rtol || rn == 0.0) {
+            conv = true;
+            break;
+        }
         if (total >= max_it) {
             out = nl_fail(ctx, NL_ENOCONV, "CG did not reach the tolerance within max_it iterations");
             break;
@@ -515,17 +544,22 @@ nl_status nl_cg(nl_ctx *ctx, const nl_csr *Ac, const double *b, double *x, doubl
             CgScal hs;
             NL_CK(cudaMemcpyAsync(&hs, sc, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
             NL_CK(cudaStreamSynchronize(ctx->stream));
-            if (!(sqrt(hs.rho) > kInnerTol)) break;   // converged, or breakdown (NaN)
+            if (hs.brk || !isfinite(hs.rho)) {   // breakdown: the correction d is not usable
+                out = nl_fail(ctx, NL_ENOCONV, "CG breakdown: a search direction with p.Ap <= 0 or not a number "
+                                               "(A not symmetric positive definite, or non-finite values)");
+                stop = true;
+                break;
+            }
+            if (!(sqrt(hs.rho) > kInnerTol)) break;   // inner tolerance reached
         }
+        if (stop) break;
         k_axpy_f32<<<eg, 256, 0, ctx->stream>>>(n, rn, d, xd); ++ctx->launches;
         NL_CK(cudaGetLastError());
     }
+    if (out == NL_OK && !conv)
+        out = nl_fail(ctx, NL_ENOCONV, "CG did not reach the tolerance within " + std::to_string(kPasses) +
+                                           " FP64 refinement passes (is rtol above the FP64 residual floor?)");
     if (!dev_x) NL_CK(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
-    NL_CK(cudaStreamSynchronize(ctx->stream));
-    void *tmp[] = {r, acc, z, p, q, d, sc};
-    for (void *t : tmp) NL_CK(cudaFreeAsync(t, ctx->stream));
-    if (!dev_x) NL_CK(cudaFreeAsync(xd, ctx->stream));
-    if (ob) NL_CK(cudaFreeAsync(bd, ctx->stream));
     NL_CK(cudaStreamSynchronize(ctx->stream));
     if (iters) *iters = total;
     if (relres) *relres = rel;

@@ -129,6 +129,48 @@ def _ptr(a, keep, dtype=None):
     return a.ctypes.data
 
 
+def _out_ptr(a, n, keep, what, device=None):
+    """Data pointer of an output (or in/out) float64 vector of n entries, written in place.
+    It is never cast or copied (a copy would lose the result), so a wrong dtype, a
+    non-contiguous array, a wrong length or a CUDA tensor on another device than the
+    context's is rejected with NlError(NL_EINVAL) before anything is launched."""
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+        if a.dtype != torch.float64:
+            raise NlError(NL_EINVAL, f"{what} must be float64 (got {a.dtype})")
+        if not a.is_contiguous():
+            raise NlError(NL_EINVAL, f"{what} must be contiguous")
+        if a.numel() != n:
+            raise NlError(NL_EINVAL, f"{what} must hold {n} entries (got {a.numel()})")
+        if device is not None and a.is_cuda and a.device.index != device:
+            raise NlError(NL_EINVAL, f"{what} is on cuda:{a.device.index}, the context on cuda:{device}")
+        keep.append(a)
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray):
+        raise NlError(NL_EINVAL, f"{what} must be a numpy array or a torch tensor")
+    if a.dtype != np.float64:
+        raise NlError(NL_EINVAL, f"{what} must be float64 (got {a.dtype})")
+    if not a.flags.c_contiguous or not a.flags.writeable:
+        raise NlError(NL_EINVAL, f"{what} must be contiguous and writeable")
+    if a.size != n:
+        raise NlError(NL_EINVAL, f"{what} must hold {n} entries (got {a.size})")
+    keep.append(a)
+    return a.ctypes.data
+
+
+def _in_vec(a, n, keep, what):
+    """Data pointer of an input float64 vector of n entries (host arrays of another dtype are
+    converted; the length is checked, so the library never reads past the end)."""
+    size = a.numel() if hasattr(a, "numel") else np.asarray(a).size
+    if size != n:
+        raise NlError(NL_EINVAL, f"{what} must hold {n} entries (got {size})")
+    return _ptr(a, keep, np.float64)
+
+
+# device of each context created through this binding (checks of CUDA tensors)
+_CTX_DEVICE = {}
+
+
 def _check(ctx, st):
     if st != NL_OK:
         raise NlError(st, _L.nl_last_error(ctx).decode(errors="replace"))
@@ -169,10 +211,12 @@ def nl_create(device: int = 0, stream: int | None = None):
     st = _L.nl_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream) if stream else None)
     if st != NL_OK:
         raise NlError(st, "nl_create failed")
+    _CTX_DEVICE[h.value] = int(device)
     return h
 
 
 def nl_destroy(ctx):
+    _CTX_DEVICE.pop(getattr(ctx, "value", None), None)
     _L.nl_destroy(ctx)
 
 
@@ -242,6 +286,7 @@ def nl_interactions(ctx, mesh: nl_mesh, cfg: nl_config):
 def nl_extract(ctx, D: nl_csr, mesh: nl_mesh):
     A, B = nl_csr(), nl_csr()
     _check(ctx, _L.nl_extract(ctx, ctypes.byref(D), ctypes.byref(mesh), ctypes.byref(A), ctypes.byref(B)))
+    B._rect = True   # its columns are the Omega_I nodes (the library holds their count)
     return A, B
 
 
@@ -249,8 +294,9 @@ def nl_rhs(ctx, B: nl_csr, mesh: nl_mesh, f_nodal, g_nodal, F=None):
     keep = _Keep()
     if F is None:
         F = np.zeros(B.n)
-    _check(ctx, _L.nl_rhs(ctx, ctypes.byref(B), ctypes.byref(mesh), _ptr(f_nodal, keep, np.float64),
-                          _ptr(g_nodal, keep, np.float64), _ptr(F, keep)))
+    dev = _CTX_DEVICE.get(getattr(ctx, "value", None))
+    _check(ctx, _L.nl_rhs(ctx, ctypes.byref(B), ctypes.byref(mesh), _in_vec(f_nodal, mesh.nv, keep, "f_nodal"),
+                          _in_vec(g_nodal, mesh.nv, keep, "g_nodal"), _out_ptr(F, B.n, keep, "F", dev)))
     return F
 
 
@@ -258,25 +304,38 @@ def nl_matvec(ctx, A: nl_csr, x, y=None, prec="fp64"):
     keep = _Keep()
     if y is None:
         y = np.zeros(A.n)
-    _check(ctx, _L.nl_matvec(ctx, ctypes.byref(A), _ptr(x, keep, np.float64), _ptr(y, keep), PREC[prec]))
+    dev = _CTX_DEVICE.get(getattr(ctx, "value", None))
+    # a square A takes n entries of x; the rectangular B of nl_extract one per Omega_I node
+    xp = _ptr(x, keep, np.float64) if getattr(A, "_rect", False) else _in_vec(x, A.n, keep, "x")
+    _check(ctx, _L.nl_matvec(ctx, ctypes.byref(A), xp, _out_ptr(y, A.n, keep, "y", dev), PREC[prec]))
     return y
 
 
 def nl_cg(ctx, A: nl_csr, b, x, rtol=1e-10, max_it=10000):
+    """x holds the initial guess and receives the solution in place (numpy array or tensor)."""
     keep = _Keep()
     it = ctypes.c_int32()
     rr = ctypes.c_double()
-    _check(ctx, _L.nl_cg(ctx, ctypes.byref(A), _ptr(b, keep, np.float64), _ptr(x, keep), float(rtol),
-                         int(max_it), ctypes.byref(it), ctypes.byref(rr)))
+    dev = _CTX_DEVICE.get(getattr(ctx, "value", None))
+    _check(ctx, _L.nl_cg(ctx, ctypes.byref(A), _in_vec(b, A.n, keep, "b"), _out_ptr(x, A.n, keep, "x", dev),
+                         float(rtol), int(max_it), ctypes.byref(it), ctypes.byref(rr)))
     return int(it.value), float(rr.value)
 
 
 def nl_cg_noalloc(ctx, A: nl_csr, b, x, rtol=1e-10, max_it=10000):
-    """b and x must be CUDA tensors (device memory); x is updated in place."""
+    """b and x must be contiguous float64 CUDA tensors of A.n entries on the context's device;
+    x holds the initial guess and is updated in place.  Anything else is rejected with
+    NlError(NL_EINVAL) before the library is called (no cast, no copy)."""
     keep = _Keep()
     it = ctypes.c_int32()
     rr = ctypes.c_double()
-    _check(ctx, _L.nl_cg_noalloc(ctx, ctypes.byref(A), _ptr(b, keep), _ptr(x, keep), float(rtol), int(max_it),
+    dev = _CTX_DEVICE.get(getattr(ctx, "value", None))
+    bp = _out_ptr(b, A.n, keep, "b", dev)   # read only, but held to the same rules: no copy of a device vector
+    xp = _out_ptr(x, A.n, keep, "x", dev)
+    for v, name in ((b, "b"), (x, "x")):
+        if not getattr(v, "is_cuda", False):
+            raise NlError(NL_EINVAL, f"nl_cg_noalloc needs {name} in device memory (a CUDA tensor)")
+    _check(ctx, _L.nl_cg_noalloc(ctx, ctypes.byref(A), bp, xp, float(rtol), int(max_it),
                                  ctypes.byref(it), ctypes.byref(rr)))
     return int(it.value), float(rr.value)
 

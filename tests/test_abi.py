@@ -85,3 +85,33 @@ def test_errors_without_gpu_are_reported_not_raised():
         nlfem.LIB.nl_destroy(h)
     else:
         assert st == nlfem.NL_ECUDA
+
+
+def test_binding_rejects_bad_vectors_before_any_launch():
+    """The binding's in-place vectors are never cast or copied (a copy would lose the result):
+    a float32 or short vector, a non-contiguous one, or a host array where nl_cg_noalloc needs
+    device memory is rejected with NL_EINVAL before the library is called (no context and no
+    GPU are needed to see it)."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+
+    from paper_2005_10775_gb300 import nlfem as nl
+    A = nl.nl_csr(n=10)
+    ok = torch.zeros(10, dtype=torch.float64)
+    bad = {"float32": torch.zeros(10, dtype=torch.float32), "short": torch.zeros(9, dtype=torch.float64),
+           "strided": torch.zeros(20, dtype=torch.float64)[::2]}
+    for name, v in bad.items():
+        for b, x in ((v, ok), (ok, v)):
+            with pytest.raises(nl.NlError) as e:
+                nl.nl_cg_noalloc(None, A, b, x)
+            assert e.value.status == nl.NL_EINVAL, name
+    with pytest.raises(nl.NlError) as e:   # right shape and type, but host memory
+        nl.nl_cg_noalloc(None, A, ok, ok.clone())
+    assert e.value.status == nl.NL_EINVAL
+    for x in (np.zeros(10, np.float32), np.zeros(11), np.zeros(20)[::2]):
+        with pytest.raises(nl.NlError) as e:
+            nl.nl_cg(None, A, np.zeros(10), x)
+        assert e.value.status == nl.NL_EINVAL
+    with pytest.raises(nl.NlError) as e:
+        nl.nl_cg(None, A, np.zeros(7), np.zeros(10))
+    assert e.value.status == nl.NL_EINVAL

@@ -98,6 +98,55 @@ def test_cg_reports_nonconvergence(nl, ctx, system):
     assert e.value.status == nl.NL_ENOCONV
 
 
+def test_cg_unreachable_tolerance_is_not_success(nl, ctx, system):
+    # rtol below the FP64 residual floor with iterations to spare: the refinement passes run
+    # out before ||b - Ax|| <= rtol ||b||, which is a failure, not a converged solve
+    F = np.ones(system["A"].n)
+    x = np.zeros_like(F)
+    with pytest.raises(nl.NlError) as e:
+        nl.nl_cg(ctx, system["A"], F, x, rtol=1e-18, max_it=200000)
+    assert e.value.status == nl.NL_ENOCONV
+    assert np.isfinite(x).all()
+
+
+def test_cg_rejects_nan_right_hand_side(nl, ctx, system):
+    F = np.ones(system["A"].n)
+    F[F.shape[0] // 2] = np.nan
+    x = np.zeros_like(F)
+    with pytest.raises(nl.NlError) as e:
+        nl.nl_cg(ctx, system["A"], F, x, rtol=1e-10, max_it=5000)
+    assert e.value.status == nl.NL_EINVAL
+
+
+def test_cg_reports_breakdown_on_indefinite_matrix(nl, ctx, system):
+    # -A is negative definite: the first direction has p.Ap < 0, a breakdown (not convergence)
+    torch = pytest.importorskip("torch")
+    import ctypes
+    A = system["A"]
+    keep = []
+    val = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+    rp = torch.empty(A.n + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(A.nnz, dtype=torch.int32, device="cuda")
+    Ah = nl.to_scipy(ctx, A)
+    val.copy_(torch.tensor(-Ah.data))
+    rp.copy_(torch.tensor(Ah.indptr.astype(np.int64)))
+    col.copy_(torch.tensor(Ah.indices.astype(np.int32)))
+    keep += [val, rp, col]
+    neg = nl.nl_csr(n=A.n, nnz=A.nnz, row_ptr=ctypes.c_void_p(rp.data_ptr()), col_idx=ctypes.c_void_p(col.data_ptr()),
+                    val=ctypes.c_void_p(val.data_ptr()))
+    F = np.ones(A.n)
+    x = np.zeros_like(F)
+    try:
+        with pytest.raises(nl.NlError) as e:
+            nl.nl_cg(ctx, neg, F, x, rtol=1e-10, max_it=5000)
+        assert e.value.status == nl.NL_ENOCONV
+        assert "breakdown" in str(e.value)
+    finally:
+        # release the FP32 copy of the values the call made; the arrays themselves are torch's
+        neg.row_ptr = neg.col_idx = neg.val = None
+        nl.nl_csr_free(ctx, neg)
+
+
 TABLE1 = {("approxcaps", 0.05): 5.84e-04, ("approxcaps", 0.025): 1.67e-04,
           ("nocaps", 0.05): 3.92e-03, ("nocaps", 0.025): 1.04e-03}
 

@@ -60,3 +60,24 @@ def test_noalloc_rejects_oversized_and_host_inputs(setup):
     with pytest.raises(nl.NlError) as e:
         nl.nl_cg_noalloc(ctx, A, F, np.zeros_like(F))    # host arrays
     assert e.value.status == nl.NL_EINVAL
+
+
+def test_noalloc_reports_failures_like_cg(setup):
+    # the same failure reports as nl_cg: an rtol below the FP64 residual floor is not reached
+    # (NL_ENOCONV once the refinement passes run out) and a NaN in b is rejected (NL_EINVAL);
+    # a good solve right after each shows that the shared array was left usable
+    nl, torch, ctx, A, F = setup["nl"], setup["torch"], setup["ctx"], setup["A"], setup["F"]
+    b = torch.tensor(F, device="cuda")
+    x = torch.zeros_like(b)
+    with pytest.raises(nl.NlError) as e:
+        nl.nl_cg_noalloc(ctx, A, b, x, rtol=1e-18, max_it=200000)
+    assert e.value.status == nl.NL_ENOCONV
+    bn = b.clone()
+    bn[bn.numel() // 2] = float("nan")
+    with pytest.raises(nl.NlError) as e:
+        nl.nl_cg_noalloc(ctx, A, bn, torch.zeros_like(b), rtol=1e-10, max_it=5000)
+    assert e.value.status == nl.NL_EINVAL
+    x = torch.zeros_like(b)
+    it, rel = nl.nl_cg_noalloc(ctx, A, b, x, rtol=1e-10, max_it=5000)
+    assert rel <= 1e-10 and it > 0
+
