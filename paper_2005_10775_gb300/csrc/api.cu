@@ -310,6 +310,7 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     A.stats = stats ? 1 : 0;
     A.err = P->err;
     A.defer = nullptr;
+    A.dval = nullptr;
     A.defer_n = nullptr;
     A.defer_cap = 0;
     A.prob = 0;
@@ -345,12 +346,13 @@ nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats)
     if (!P->defer) {
         const int cap = nl_defer_cap(P->E);
         nlq::DeferItem *q = nullptr;
-        if ((s = nl_alloc(ctx, &q, (size_t)cap)) != NL_OK) return s;
+        if ((s = nl_alloc(ctx, &q, nlq::defer_alloc_items(cap))) != NL_OK) return s;
         P->defer = q;
         if ((s = nl_alloc(ctx, &P->defer_n, 1)) != NL_OK) return s;
         P->defer_cap = cap;
     }
     A.defer = (nlq::DeferItem *)P->defer;
+    A.dval = nlq::defer_values(A.defer, P->defer_cap);
     A.defer_n = P->defer_n;
     A.defer_cap = P->defer_cap;
     return nl_launch_numeric_f32(ctx, A, P->cfg.ball);

@@ -504,7 +504,7 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
         int64_t E = 0;
         for (int i : l.probs) E += b->P[i]->E;
         l.defer_cap = nl_defer_cap(E);
-        if ((s = nl_alloc(ctx, &l.defer, (size_t)l.defer_cap)) != NL_OK) return fail(s);
+        if ((s = nl_alloc(ctx, &l.defer, nlq::defer_alloc_items(l.defer_cap))) != NL_OK) return fail(s);
     }
     for (int pg = 0; pg < (int)b->pgroups.size(); pg++) {
         PrecGroup &g = b->pgroups[pg];
@@ -518,6 +518,7 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
                     std::find(l.probs.begin(), l.probs.end(), g.probs[k]) == l.probs.end())
                     continue;
                 args[k].defer = l.defer;
+                args[k].dval = nlq::defer_values(l.defer, l.defer_cap);
                 args[k].defer_n = b->counters + nlaunch + j;
                 args[k].defer_cap = l.defer_cap;
                 args[k].prob = (int)k;

@@ -41,6 +41,15 @@ struct DeferItem {
     int32_t qp;    // outer point q (bits 0-7) and problem index in a batched launch (bits 8-31)
 };
 
+// A queue of cap items is one allocation: the items, then the M_ab values (9 floats a slot,
+// value-major: [9][cap]) that k_deferred computes and k_defer_merge adds onto the pairs.
+constexpr int kDeferVals = 9;
+inline size_t defer_alloc_items(int cap)
+{
+    return (size_t)cap + ((size_t)cap * kDeferVals * sizeof(float) + sizeof(DeferItem) - 1) / sizeof(DeferItem);
+}
+__host__ __device__ inline float *defer_values(DeferItem *q, int cap) { return q ? (float *)(q + cap) : nullptr; }
+
 struct NumArgs {
     int K;
     int64_t E;
@@ -77,6 +86,7 @@ struct NumArgs {
     int stats;
     int *err;                         // device error word: bit 0 = region buffer bound hit
     DeferItem *defer;                 // FP32 path: queue of the items the FP64 geometry decides (null: inline)
+    float *dval;                      // [9][defer_cap]: each queued item's M_ab (k_deferred -> k_defer_merge)
     int *defer_n;                     // its fill count (zeroed before the boundary launch; may exceed the cap)
     int defer_cap;
     int prob;                         // index of this problem in a batched launch's argument array
@@ -853,6 +863,7 @@ struct BoundaryShared {
                                // the disc balls rows 15-20, M_aa, are per integrating lane instead),
                                // value-major: the owners of one atomic instruction hit distinct banks
     unsigned short queue[32 * NL_MAXQ];    // undecided items (owner lane << 8 | q)
+    unsigned dmask[32];        // outer points of each lane's candidate whose item the deferred kernel takes
     // whole items from the front; whole items in the singular kernel's near field from the back
     // (a batch holds at most 32 x n_q items in all)
     unsigned short wqueue[32 * NL_MAXQ];
@@ -984,16 +995,16 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
     return true;
 }
 
-// Add a block w (its first NV values) to owner own's column of the shared accumulator; am = the lanes of
-// the round that add a block (all of them call this).  Lanes with the same owner first sum
-// their blocks by shuffles (the leader takes its peers'
-// values one by one), so one lane per owner adds: no shared atomics colliding on one address.
+// Add a block w (its first NV values) to owner own's column of the shared accumulator; am = the
+// lanes that call this (all of them do; own < 0: a lane without a block).  Lanes with the same
+// owner first sum their blocks by shuffles (the leader takes its peers' values one by one, in
+// lane order), so one lane per owner adds: no shared atomics colliding on one address.
 template <typename T, int NV>
 __device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane, T *w, unsigned am)
 {
     __syncwarp(am);
     const unsigned peers = __match_any_sync(am, own);
-    const int m = __popc(peers), leader = __ffs(peers) - 1;
+    const int m = own >= 0 ? __popc(peers) : 0, leader = __ffs(peers) - 1;
     const int mmax = (int)__reduce_max_sync(am, (unsigned)m);
     for (int t = 1; t < mmax; t++) {
         unsigned rest = peers;
@@ -1005,22 +1016,68 @@ __device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane
             if (take) w[k] += x;
         }
     }
-    if (lane == leader) {
+    if (own >= 0 && lane == leader) {
         for (int k = 0; k < NV; k++) atomicAdd(&accum[k][own], w[k]);
         accum[21][own] = (T)1;
     }
 }
 
-// Queue an item for k_deferred: false (the caller runs the FP64 code itself) for FP64 sums,
-// without a queue, or when the queue is full.
+// Mark an item (owner own, outer point q) for k_deferred: false (the caller runs the FP64 code
+// itself) for FP64 sums or without a queue.  The marks of a round are queued together by
+// defer_flush, in (owner, q) order.
 template <typename T>
-__device__ __forceinline__ bool defer_item(const NumArgs &A, int64_t e, int a, int q)
+__device__ __forceinline__ bool defer_mark(const NumArgs &A, BoundaryShared<T> &sh, int own, int q)
 {
     if (sizeof(T) != sizeof(float) || !A.defer) return false;
-    const int slot = atomicAdd(A.defer_n, 1);
-    if (slot >= A.defer_cap) return false;
-    A.defer[slot] = DeferItem{e, a, (A.prob << 8) | q};
+    atomicOr(&sh.dmask[own], 1u << q);
     return true;
+}
+
+// Queue the round's marked items with one reservation for the warp, ordered by owner lane and
+// outer point: the items of one pair are contiguous and in q order, so k_defer_merge adds them
+// onto the pair in a fixed order (run-to-run identical FP32 values).  Items past the queue's
+// capacity are integrated here, by their owner lane with the FP64 geometry, into its column of
+// the accumulator.
+template <int BALL, typename T>
+__device__ __forceinline__ void defer_flush(const NumArgs &A, int a, int64_t base, BoundaryShared<T> &sh, int lane,
+                                            LaneAcc &acc)
+{
+    const unsigned m = sh.dmask[lane];
+    const int cnt = __popc(m);
+    int inc = cnt;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    if (total == 0) return;
+    sh.dmask[lane] = 0;
+    int slot0 = 0;
+    if (lane == 0) slot0 = atomicAdd(A.defer_n, total);
+    slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+    int slot = slot0 + inc - cnt;
+    for (unsigned rest = m; rest; rest &= rest - 1, slot++) {
+        const int q = __ffs(rest) - 1;
+        if (slot < A.defer_cap) {
+            A.defer[slot] = DeferItem{base + lane, a, (A.prob << 8) | q};
+            continue;
+        }
+        // queue full: this lane integrates its own item
+        const CandData &cd = sh.cand[lane];
+        const OuterPt &o = sh.sq[q];
+        Sums<T> S;
+        int64_t nq = 0;
+        int kind, nv, ncap;
+        if (!exact_item_fp64<BALL, T>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane)) continue;
+        T w[21];
+        for (int k = 0; k < 21; k++) w[k] = 0;
+        combine<T>(o, S, w);
+        for (int k = 0; k < 21; k++) sh.acc[k][lane] += w[k];
+        sh.acc[21][lane] = (T)1;
+        acc.cnt++;
+        acc.qp += nq;
+        if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
+    }
 }
 
 // The boundary candidates of outer triangle a (outer points staged in sh.sq).
@@ -1057,6 +1114,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             sh.cand[lane] = c;
         }
         for (int i = 0; i < 22; i++) sh.acc[i][lane] = 0;
+        sh.dmask[lane] = 0;
         int nqueue = 0;
         __syncwarp();
         // phase 1: classify every (q, b) in lockstep; queue whole and undecided items
@@ -1161,7 +1219,11 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             acc.qp += nq;
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
         }
-        // phase 2b: undecided items with all lanes
+        // phase 2b: undecided items with all lanes.  The loop does not converge the warp between
+        // items: lanes at different items run the same parts of the clip together.  So the order
+        // in which their blocks reach an owner's column depends on the scheduling, and an FP32
+        // block value may differ in its last bits between runs (FP64 blocks: in the last bits of
+        // FP64).
         for (int i = lane; i < nqueue; i += 32) {
             const unsigned it = sh.queue[i];
             const int own = it >> 8, q = it & 0xff;
@@ -1172,7 +1234,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             int kind, nv, ncap;
             int r = exact_item_f32<BALL, T, INV>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane);
             if (r < 0) {
-                if (defer_item<T>(A, base + own, a, q)) continue;
+                if (defer_mark<T>(A, sh, own, q)) continue;
                 r = exact_item_fp64<BALL, T>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane) ? 1 : 0;
             }
             if (r == 0) continue;
@@ -1193,6 +1255,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
         }
         __syncwarp();
+        if (sizeof(T) == sizeof(float) && A.defer) {
+            defer_flush<BALL, T>(A, a, base, sh, lane, acc);
+            __syncwarp();
+        }
         // phase 3: owners merge the queue's contributions and write their pair
         if (valid) {
             T v[21];
@@ -1432,10 +1498,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, I
 // ---------------------------------------------------------------------------
 // Deferred items of the FP32 path (after the boundary launch, in stream order): each
 // thread takes one queued (q, b), builds its region with the FP64 geometry, integrates it
-// in FP32 and adds its block onto the pair's stored values, M_aa and the statistics.
+// in FP32, stores its M_ab in the queue's value slots (dv, column slot of [9][cap]) and adds
+// its M_bb, M_aa (FP64 atomics) and statistics (integer atomics); k_defer_merge then adds
+// the M_ab of each pair's items, which sit side by side in q order, onto the pair's values.
 // ---------------------------------------------------------------------------
 template <int BALL>
-__device__ __forceinline__ void deferred_item(const NumArgs &A, const DeferItem &d, nlg::ClipBuf &cb, int lane)
+__device__ __forceinline__ void deferred_item(const NumArgs &A, const DeferItem &d, float *dv, int cap, int slot,
+                                              nlg::ClipBuf &cb, int lane)
 {
     const int K = A.K, a = d.a, q = d.qp & 0xff;
     const int64_t e = d.e;
@@ -1456,12 +1525,14 @@ __device__ __forceinline__ void deferred_item(const NumArgs &A, const DeferItem 
     Sums<float> S;
     int64_t nq = 0;
     int kind, nv, ncap;
-    if (!exact_item_fp64<BALL, float>(A, c, o, S, nq, kind, nv, ncap, cb, lane)) return;
+    if (!exact_item_fp64<BALL, float>(A, c, o, S, nq, kind, nv, ncap, cb, lane)) {
+        for (int k = 0; k < kDeferVals; k++) dv[(int64_t)k * cap + slot] = 0.f;
+        return;
+    }
     float w[21];
     for (int k = 0; k < 21; k++) w[k] = 0.f;
     combine<float>(o, S, w);
-    float *blk = (float *)A.blk;
-    for (int k = 0; k < 9; k++) atomicAdd(&blk[(int64_t)k * A.E + e], w[k]);
+    for (int k = 0; k < kDeferVals; k++) dv[(int64_t)k * cap + slot] = w[k];
     for (int k = 0; k < 6; k++) atomicAdd(&A.mbb[(int64_t)k * K + b], (double)w[9 + k]);
     for (int k = 0; k < 6; k++) atomicAdd(&A.maa[(int64_t)k * K + a], (double)w[15 + k]);
     A.flag[e] = 1;
@@ -1478,7 +1549,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_deferred(const NumArgs 
     __shared__ nlg::ClipBuf cb[kWarpsPerBlock];
     const int n = min(*A.defer_n, A.defer_cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        deferred_item<BALL>(A, A.defer[i], cb[threadIdx.x >> 5], threadIdx.x & 31);
+        deferred_item<BALL>(A, A.defer[i], A.dval, A.defer_cap, i, cb[threadIdx.x >> 5], threadIdx.x & 31);
 }
 
 // the queue of one batched boundary launch (items of its problems, As indexed by qp >> 8)
@@ -1488,10 +1559,54 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 {
     __shared__ nlg::ClipBuf cb[kWarpsPerBlock];
     const int n = min(*count, cap);
+    float *dv = defer_values(const_cast<DeferItem *>(items), cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const DeferItem d = items[i];
-        deferred_item<BALL>(As[d.qp >> 8], d, cb[threadIdx.x >> 5], threadIdx.x & 31);
+        deferred_item<BALL>(As[d.qp >> 8], d, dv, cap, i, cb[threadIdx.x >> 5], threadIdx.x & 31);
     }
+}
+
+// M_ab of the deferred items onto their pairs: the first slot of each run of one pair (same
+// problem and pair index: a run is one warp's items of one candidate, in q order) sums the run
+// in order and adds the sum once, so the values repeat exactly from run to run.  The pair's
+// stored value is the boundary kernel's, final when this runs.  args(p): the arguments of
+// problem p.
+template <class Args>
+__device__ __forceinline__ void defer_merge(Args args, const DeferItem *__restrict__ items, const int *count, int cap)
+{
+    const int n = min(*count, cap);
+    const float *dv = defer_values(const_cast<DeferItem *>(items), cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const DeferItem d = items[i];
+        if (i > 0) {
+            const DeferItem p = items[i - 1];
+            if (p.e == d.e && (p.qp >> 8) == (d.qp >> 8)) continue;   // inside a run
+        }
+        float sum[kDeferVals];
+        for (int k = 0; k < kDeferVals; k++) sum[k] = dv[(int64_t)k * cap + i];
+        for (int j = i + 1; j < n; j++) {
+            const DeferItem r = items[j];
+            if (r.e != d.e || (r.qp >> 8) != (d.qp >> 8)) break;
+            for (int k = 0; k < kDeferVals; k++) sum[k] += dv[(int64_t)k * cap + j];
+        }
+        const NumArgs &A = args(d.qp >> 8);
+        float *blk = (float *)A.blk;
+        for (int k = 0; k < kDeferVals; k++) blk[(int64_t)k * A.E + d.e] += sum[k];
+    }
+}
+
+// (templates on the value type, float: one kernel in every translation unit that launches it)
+template <typename T>
+__global__ void __launch_bounds__(256) k_defer_merge(const NumArgs A)
+{
+    defer_merge([&](int) -> const NumArgs & { return A; }, A.defer, A.defer_n, A.defer_cap);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_defer_merge_batch(const NumArgs *__restrict__ As, const DeferItem *__restrict__ items, const int *count, int cap)
+{
+    defer_merge([&](int p) -> const NumArgs & { return As[p]; }, items, count, cap);
 }
 
 }  // namespace nlq

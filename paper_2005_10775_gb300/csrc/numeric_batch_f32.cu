@@ -93,6 +93,7 @@ nl_status nl_launch_deferred_batch_f32(nl_ctx *ctx, int ball, const nlq::NumArgs
     default: return nl_fail(ctx, NL_EINVAL, "no deferred items for this ball mode");
     }
     ++ctx->launches;
+    nlq::k_defer_merge_batch<float><<<blocks, 256, 0, ctx->stream>>>(dA, items, count, cap); ++ctx->launches;
     NL_CK(cudaGetLastError());
     return NL_OK;
 }

@@ -25,6 +25,7 @@ nl_status launch_boundary_k(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, u
             nl_status s = nl_deferred_blocks(ctx, &blocks);
             if (s != NL_OK) return s;
             nlq::k_deferred<BALL><<<blocks, threads, 0, ctx->stream>>>(A); ++ctx->launches;
+            nlq::k_defer_merge<float><<<blocks, 256, 0, ctx->stream>>>(A); ++ctx->launches;
             NL_CK(cudaGetLastError());
         }
     }
