@@ -582,9 +582,6 @@ nl_status nl_prepare_b(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_host_slot *h)
     if (h->bad)
         return nl_fail(ctx, NL_EGEOM, std::to_string(h->bad) +
                                           " triangles are degenerate, clockwise or index a missing vertex");
-    if (!(cfg->delta > hst.hmax))
-        return nl_fail(ctx, NL_EGEOM, "delta must exceed the largest triangle diameter (" +
-                                          std::to_string(hst.hmax) + ")");
     P->hmax = hst.hmax;
     P->rmax = hst.rmax;
     // grid for the candidate search

@@ -144,9 +144,11 @@ def test_batch_schedule_info_and_cache(nl, ctx, mixed):
 def test_batch_rejects_a_bad_problem(nl, ctx):
     keep = nl._Keep()
     good = I.split_square_mesh(-0.1, 1.1, 24, jitter=0.2, seed=3)
-    coarse = I.split_square_mesh(-0.1, 1.1, 6)            # diameter 0.28 > delta = 0.1
+    # the same mesh with its triangles clockwise
+    bad = I.Mesh(vx=good.vx, vy=good.vy, tri=good.tri[:, ::-1].copy(), node_in_omega=good.node_in_omega,
+                 elem_in_omega=good.elem_in_omega, h=good.h, lo=good.lo, hi=good.hi, n=good.n)
     p = I.Problem("g", good, 0.1, "const", I.const_kernel_c(0.1), "nocaps", "dunavant7", "dunavant7")
-    meshes = [nl.make_mesh(good, keep), nl.make_mesh(coarse, keep)]
+    meshes = [nl.make_mesh(good, keep), nl.make_mesh(bad, keep)]
     cfgs = [nl.config_of(p, keep, prec="fp32c"), nl.config_of(p, keep, prec="fp32c")]
     with pytest.raises(nl.NlError) as e:
         nl.nl_batch_create(ctx, meshes, cfgs)
