@@ -1,6 +1,8 @@
 """Right-hand side and solve on the GPU (through the C ABI) against the oracle's
 numpy/scipy steps: A = D[Omega, Omega], B = D[Omega, Omega_I], F = G - B g,
 matrix-vector products and the mixed-precision CG solve."""
+import os
+
 import numpy as np
 import pytest
 
@@ -147,20 +149,24 @@ def test_cg_reports_breakdown_on_indefinite_matrix(nl, ctx, system):
         nl.nl_csr_free(ctx, neg)
 
 
-TABLE1 = {("approxcaps", 0.05): 5.84e-04, ("approxcaps", 0.025): 1.67e-04,
-          ("nocaps", 0.05): 3.92e-03, ("nocaps", 0.025): 1.04e-03}
+def _golden(name):
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            rows[(f[0], float(f[1]))] = float(f[2])
+    return rows
 
 
-@pytest.mark.parametrize("ball,h", list(TABLE1))
-def test_paper_table1_end_to_end_on_gpu(nl, ctx, ball, h):
-    # Sec. 8: the whole pipeline on the GPU (assembly with the paper's rule protocol, extraction,
-    # right-hand side, CG) reproduces the L2 errors printed in Table 1 (values in tests/golden)
+def gpu_l2_error(nl, ctx, m, ball, outer, inner, prec="fp32c", **over):
+    """The whole pipeline on the GPU (assembly, extraction, right-hand side, CG to 1e-10) for the
+    manufactured solution u = x1^2 x2 + x2^2 of Sec. 8; the L2(Omega) error of u_h."""
     d = 0.1
-    m = I.paper_grid(h)
-    p = I.Problem("paper", m, d, "const", I.const_kernel_c(d), ball, "switch47", "gauss3")
+    p = I.Problem("paper", m, d, "const", I.const_kernel_c(d), ball, outer, inner)
     keep = nl._Keep()
     mesh = nl.make_mesh(m, keep)
-    D = nl.nl_assemble(ctx, mesh, nl.config_of(p, keep, prec="fp32c"))
+    D = nl.nl_assemble(ctx, mesh, nl.config_of(p, keep, prec=prec, **over))
     A, B = nl.nl_extract(ctx, D, mesh)
     try:
         u = I.manufactured_u(m.vx, m.vy)
@@ -172,8 +178,57 @@ def test_paper_table1_end_to_end_on_gpu(nl, ctx, ball, h):
             nl.nl_csr_free(ctx, z)
     U = u.copy()
     U[m.node_in_omega.astype(bool)] = x
-    err = O.l2_error_omega(m, U, I.manufactured_u)
-    assert err == pytest.approx(TABLE1[(ball, h)], rel=0.15)
+    return O.l2_error_omega(m, U, I.manufactured_u)
+
+
+# Table 1 (Sec. 8) end to end on the GPU with the paper's rule protocol (outer gauss4 / paper7 by
+# the switch, inner gauss3, caps one centroid point with the printed weight), against the printed
+# L2 errors (tests/golden/paper_table1.txt) within 15 %, from h = delta = 0.1 (diameters above
+# delta) to the finest grid h = 0.00625 (K = 73728).  Not listed: the barycenter column (not
+# reproduced, a documented reading) and nocaps at h = 0.1 (checked against the oracle below).
+TABLE1_GPU = ([("exactcaps", h) for h in (0.1, 0.05, 0.025, 0.0125)] +
+              [("approxcaps", h) for h in (0.1, 0.05, 0.025, 0.0125, 0.00625)] +
+              [("nocaps", h) for h in (0.05, 0.025, 0.0125, 0.00625)] +
+              [("overlap", h) for h in (0.1, 0.05, 0.025, 0.0125)])
+
+
+@pytest.mark.parametrize("ball,h", TABLE1_GPU)
+def test_paper_table1_end_to_end_on_gpu(nl, ctx, ball, h):
+    over = {"cap_printed": 1} if ball == "exactcaps" else {}
+    err = gpu_l2_error(nl, ctx, I.paper_grid(h), ball, "switch47", "gauss3", **over)
+    assert err == pytest.approx(_golden("paper_table1.txt")[(ball, h)], rel=0.15)
+
+
+def test_paper_table1_nocaps_coarsest_grid_matches_oracle(nl, ctx):
+    # nocaps at h = delta = 0.1: the oracle's L2 error is 0.66 x the printed one (a documented
+    # reading); the GPU pipeline reproduces the oracle's value
+    m = I.paper_grid(0.1)
+    err = gpu_l2_error(nl, ctx, m, "nocaps", "switch47", "gauss3", prec="fp64")
+    d = 0.1
+    cfg = dict(delta=d, ball="nocaps", outer="switch47", inner="gauss3", kernel_c=I.const_kernel_c(d))
+    ref = O.l2_error_omega(m, O.solve(O.to_csr(O.assemble(m, cfg)), m, I.manufactured_f(m.vx, m.vy),
+                                      I.manufactured_u(m.vx, m.vy)), I.manufactured_u)
+    assert err == pytest.approx(ref, rel=1e-6)
+
+
+@pytest.mark.parametrize("ball", ["bary_nocaps", "bary_approxcaps"])
+def test_paper_table4b_nonuniform_grid_on_gpu(nl, ctx, ball):
+    # grid (b) of Sec. 8 (x2 -> x2^2 inside (0, 1); h_max 0.2147, 0.1096, 0.0553 against delta = 0.1),
+    # barycenter ball with the outer integral over its support, gauss4 outer / gauss3 inner (Table 4(b)):
+    # the GPU pipeline gives the oracle's L2 errors at every grid, and their second-order rate
+    errs = []
+    d = 0.1
+    for h in (0.1, 0.05, 0.025):
+        m = I.paper_grid(h, warped=True)
+        err = gpu_l2_error(nl, ctx, m, ball, "gauss4", "gauss3", prec="fp64")
+        cfg = dict(delta=d, ball=ball, outer="gauss4", inner="gauss3", kernel_c=I.const_kernel_c(d))
+        ref = O.l2_error_omega(m, O.solve(O.to_csr(O.assemble(m, cfg)), m, I.manufactured_f(m.vx, m.vy),
+                                          I.manufactured_u(m.vx, m.vy)), I.manufactured_u)
+        assert err == pytest.approx(ref, rel=1e-6), h
+        errs.append(err)
+    assert 1.6 < np.log2(errs[1] / errs[2]) < 2.4
+    printed = _golden("paper_table4b.txt")
+    assert 0.3 < errs[2] / printed[(ball, 0.025)] < 3.0
 
 
 def test_paper_table2_shifted_nocaps_on_gpu(nl, ctx):
