@@ -37,7 +37,7 @@ typedef enum {
     NL_EINVAL = 1,        /* bad argument (null pointer, size, enum value) */
     NL_ENOMEM = 2,        /* device allocation failed */
     NL_ECUDA = 3,         /* a CUDA runtime call failed */
-    NL_EGEOM = 4,         /* degenerate / clockwise triangle, or delta <= largest triangle diameter */
+    NL_EGEOM = 4,         /* degenerate or clockwise triangle, or an index past the vertex array */
     NL_ETIMEOUT = 5,      /* a bounded device-side wait expired */
     NL_ENOCONV = 6,       /* the iterative solver did not reach the tolerance */
     NL_EUNSUPPORTED = 7   /* valid but not implemented combination / size limit exceeded */
@@ -95,7 +95,8 @@ typedef struct {
 } nl_mesh;
 
 typedef struct {
-    double delta;                   /* horizon, > largest triangle diameter (Sec. 7.1 task 6 assumes it) */
+    double delta;                   /* horizon > 0; any size relative to the triangles (Sec. 8 runs delta = h,
+                                       and delta below the largest diameter on grid (b)) */
     double kernel_c;                /* kernel constant c */
     int32_t kernel;                 /* nl_kernel */
     int32_t ball;                   /* nl_ball */
@@ -280,6 +281,13 @@ nl_status nl_last_timings(nl_ctx *ctx, double *ms4);
 nl_status nl_cg_noalloc(nl_ctx *ctx, const nl_csr *A, const double *b, double *x, double rtol, int32_t max_it,
                         int32_t *iters, double *relres);
 
+/* Measured fused multiply-add throughput of the context's GPU (TFLOP/s, 2 flop per FMA) in
+   FP32 (NL_PREC_FP32_COMP) or FP64 (NL_PREC_FP64): independent FMA chains on every SM, best of
+   three timed launches after a warm-up.  The paper has no counterpart: a measurement aid, the ALU
+   roofline against which the pair quadrature (FP32 path) and the FP64 path are reported.
+   Synchronises the context's stream. */
+nl_status nl_fma_peak(nl_ctx *ctx, int32_t prec, double *tflops);
+
 /* Number of CUDA kernels this context has launched so far (all entry points). */
 int64_t nl_launch_count(nl_ctx *ctx);
 
@@ -288,9 +296,13 @@ int64_t nl_launch_count(nl_ctx *ctx);
    singular kernel's near field, balls without an FP32 region.  The boundary kernel
    queues them and a second kernel integrates the queue with every lane busy; a full
    queue (capacity E/16, at least 4096; NL_DEFER_CAP in the environment overrides it, 0
-   disables the queue) leaves the excess to the boundary kernel's own lanes.  Their
-   blocks are added with FP32 atomics, so FP32-path values may differ between runs in
-   the last bits.  0 for the FP64 path; -1 for a null context. */
+   disables the queue) leaves the excess to the boundary kernel's own lanes.  Each warp
+   queues its items in (pair, outer point) order and a merge kernel adds the items of a
+   pair onto it in that order (no atomics).  Run to run, FP32-path pair blocks may still
+   differ in their last bits (the boundary kernel's lanes add their blocks in a
+   scheduling-dependent order; measured up to 6e-9 of max|D|), and the sums taken with FP64
+   atomics (M_aa, M_bb, the scatter into D) in theirs (about 1e-16 relative).  0 for the
+   FP64 path; -1 for a null context. */
 int64_t nl_last_fp64_items(nl_ctx *ctx);
 
 #ifdef __cplusplus

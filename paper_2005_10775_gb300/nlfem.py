@@ -92,6 +92,7 @@ def _load():
         "nl_csr_free": (None, [ctypes.c_void_p, P(nl_csr)]),
         "nl_last_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
         "nl_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+        "nl_fma_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_double)]),
         "nl_last_fp64_items": (ctypes.c_int64, [ctypes.c_void_p]),
         "nl_cg_noalloc": (ctypes.c_int, [ctypes.c_void_p, P(nl_csr), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_double, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_double)]),
@@ -356,6 +357,13 @@ def nl_last_timings(ctx):
     t = np.zeros(4)
     _check(ctx, _L.nl_last_timings(ctx, t.ctypes.data))
     return t
+
+
+def nl_fma_peak(ctx, prec="fp32c") -> float:
+    """Measured FMA throughput of the context's GPU in TFLOP/s (FP32 for "fp32c", FP64 for "fp64")."""
+    t = ctypes.c_double()
+    _check(ctx, _L.nl_fma_peak(ctx, PREC[prec], ctypes.byref(t)))
+    return float(t.value)
 
 
 def nl_launch_count(ctx) -> int:
