@@ -37,6 +37,7 @@ UNIT = "qp-pairs/s"
 FLOP_PER_QP = 37.0
 FLOP_PER_INTER = 48.0
 SMS, FP32_LANES = 152, 128
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (nominal); the measured one comes from nl_fma_peak
 # DRAM bytes (read + write) of the numeric phase (k_interior + k_boundary + k_deferred) of
 # one assembly, from one ncu capture of the current kernels (profiles/k_boundary_<workload>.md)
 NCU_TRAFFIC = {"ngon32_96": (403.5e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_interior + k_boundary "
@@ -57,6 +58,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--solve", action="store_true",
                     help="after the assembly, extract A, form F and solve A U = F by CG (u = |x|^2)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other benchmark configurations (barycenter_32, singular_128, solve_220, "
+                         "batch64, paper Table 1 balls) reported under 'configs'")
+    ap.add_argument("--peaks-only", action="store_true",
+                    help="print the measured FP32 / FP64 FMA throughput of the GPU and exit")
     return ap.parse_args()
 
 
@@ -203,7 +209,7 @@ def cpu_baseline_batch(problems, seconds):
                       f"triangle of its mesh, {qp} qp-pairs, FP64"}, tt
 
 
-def batch_bench(args, nl, ctx, stream, dev, world, dist, rank):
+def batch_bench(args, nl, ctx, stream, dev, world, dist, rank, cpu_seconds=None):
     """The batched workload: 64 independent assemblies (delta 0.05 .. 0.2, K 2450 .. 38088,
     nocaps / approxcaps) in one nl_assemble_batch, against 64 sequential nl_assemble calls;
     re-assembly by the captured graph (nl_batch_run) against 64 nl_assemble_numeric calls."""
@@ -363,7 +369,7 @@ def batch_bench(args, nl, ctx, stream, dev, world, dist, rank):
         "e2e": e2e,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"], _ = cpu_baseline_batch(probs, args.cpu_seconds)
+        line["cpu_baseline"], _ = cpu_baseline_batch(probs, args.cpu_seconds if cpu_seconds is None else cpu_seconds)
     return line
 
 
@@ -419,7 +425,9 @@ def solve_phase(nl, ctx, m, p, prec, stream, dev, keep):
     out = {"J_omega": int(A.n), "nnz_A": int(A.nnz), "extract_rhs_ms": ev[0].elapsed_time(ev[1]),
            "cg_ms": ev[1].elapsed_time(ev[2]), "cg_inner_iterations": it, "relres": rel,
            "max_nodal_error_vs_u": err, "spmv_fp32_ms": spmv_ms, "spmv_timing": spmv_timing,
-           "spmv_fp32_GBps": spmv_bytes / (spmv_ms * 1e-3) / 1e9}
+           "spmv_fp32_GBps": spmv_bytes / (spmv_ms * 1e-3) / 1e9,
+           "spmv_frac_of_hbm": spmv_bytes / (spmv_ms * 1e-3) / 1e9 / float(measured_peaks()[0].get("hbm_gbs", 6800.0)),
+           "spmv_bytes": int(spmv_bytes)}
     for z in (D, A, B):
         nl.nl_csr_free(ctx, z)
     return out
@@ -453,6 +461,145 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def device_mesh(nl, m, dev, keep):
+    import torch
+    dmesh = type("DevMesh", (), dict(vx=torch.tensor(m.vx, device=dev), vy=torch.tensor(m.vy, device=dev),
+                                     tri=torch.tensor(m.tri, device=dev)))
+    return nl.make_mesh(dmesh, keep)
+
+
+def time_assembly(nl, ctx, mesh, cfg, steps, warmup, stream, flush, dev, dist):
+    """`steps` nl_assemble calls from a mesh in HBM to the finished CSR, each bracketed by CUDA
+    events on the library's stream (L2 flushed before each); the max over ranks of the total."""
+    import numpy as np
+    import torch
+    for _ in range(warmup):
+        out = nl.nl_assemble(ctx, mesh, cfg)
+        nl.nl_csr_free(ctx, out)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    tot = 0.0
+    phase = np.zeros(4)
+    stats = None
+    l0 = nl.nl_launch_count(ctx)
+    wall0 = time.perf_counter()
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = nl.nl_assemble(ctx, mesh, cfg)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+        phase += nl.nl_last_timings(ctx)
+        stats = (out.n_pairs, out.n_qp_pairs, out.n_inter, out.nnz, nl.nl_last_fp64_items(ctx))
+        nl.nl_csr_free(ctx, out)
+    launches = nl.nl_launch_count(ctx) - l0
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    return max_over_ranks(tot, dev, dist), phase / steps, stats, launches, wall
+
+
+def fp32c_vs_fp64_error(nl, ctx, mesh, cfg32, cfg64):
+    """max |D_fp32c - D_fp64| / max |D_fp64| over all entries (the two share their pattern)."""
+    import numpy as np
+    res = []
+    for cfg in (cfg32, cfg64):
+        out = nl.nl_assemble(ctx, mesh, cfg)
+        try:
+            res.append(nl.nl_csr_download(ctx, out))
+        finally:
+            nl.nl_csr_free(ctx, out)
+    (rp32, ci32, v32), (rp64, ci64, v64) = res
+    if not (np.array_equal(rp32, rp64) and np.array_equal(ci32, ci64)):
+        return None
+    return float(np.abs(v32 - v64).max() / np.abs(v64).max())
+
+
+def alu_peaks(nl, ctx):
+    """Derived FP32 FMA peak (the roofline denominator: SMs x lanes x 2 x the maximum SM clock of
+    MEASURED_PEAKS.json), and the FP32 / FP64 FMA throughput measured on this GPU by nl_fma_peak."""
+    peaks, src = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    derived = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    meas32 = nl.nl_fma_peak(ctx, "fp32c")
+    meas64 = nl.nl_fma_peak(ctx, "fp64")
+    return {"fp32_derived_tflops": derived, "fp32_measured_tflops": meas32, "fp64_measured_tflops": meas64,
+            "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS, "sm_max_mhz": sm_mhz, "clock_source": src,
+            "how": "nl_fma_peak: 8 independent FMA chains a thread, 2048 threads a SM, best of 3 launches"}
+
+
+def config_entry(args, nl, ctx, name, stream, dev, dist, flush, world, rank, peaks, steps=5, fp64_steps=2,
+                 cpu_seconds=3.0, solve=False):
+    """One more benchmark configuration, measured like the headline: FP32-compensated and FP64
+    assembly times, qp-pairs/s, the FP32c/FP64 speedup and error, the numeric phase against the
+    FP32 and FP64 FMA rooflines, and a short oracle sample on the host cores."""
+    from paper_2005_10775_gb300 import inputs as I
+    p = I.problem(name)
+    keep = nl._Keep()
+    mesh = device_mesh(nl, p.mesh, dev, keep)
+
+    def cfg_for(prec):
+        return nl.make_config(keep, p.delta, p.ball, p.outer, p.inner, p.kernel, p.kernel_c, p.ngon_off, p.cap_m,
+                              prec)
+    t32, ph32, st32, l32, _ = time_assembly(nl, ctx, mesh, cfg_for("fp32c"), steps, 2, stream, flush, dev, dist)
+    t64, ph64, st64, _, _ = time_assembly(nl, ctx, mesh, cfg_for("fp64"), fp64_steps, 1, stream, flush, dev, dist)
+    n_pairs, n_qp, n_inter, nnz, n_fp64 = st32
+    ms32, ms64 = t32 / steps, t64 / fp64_steps
+    flop = FLOP_PER_QP * n_qp + FLOP_PER_INTER * n_inter
+    a32 = flop / (ph32[1] / 1e3) / 1e12
+    a64 = flop / (ph64[1] / 1e3) / 1e12
+    e = {"workload": name, "K": p.mesh.nt, "ball": f"{p.ball}{p.ngon_n or ''}", "delta": p.delta,
+         "outer": p.outer, "inner": p.inner, "kernel": p.kernel,
+         "n_pairs": n_pairs, "n_qp_pairs": n_qp, "n_inter": n_inter, "nnz": nnz, "fp64_items": n_fp64,
+         "ms_per_matrix": {"fp32c": ms32, "fp64": ms64},
+         "value": {"fp32c": n_qp * world / (ms32 / 1e3), "fp64": n_qp * world / (ms64 / 1e3), "unit": UNIT},
+         "speedup_fp32c_vs_fp64": ms64 / ms32,
+         "phase_ms_fp32c": {"prepare": ph32[0], "numeric": ph32[1], "symbolic": ph32[2], "scatter": ph32[3]},
+         "numeric_ms_fp64": ph64[1],
+         "roofline": {"bound": "alu", "unit": "TFLOP/s",
+                      "achieved_fp32c": a32, "peak_fp32": peaks["fp32_derived_tflops"],
+                      "frac_fp32c": a32 / peaks["fp32_derived_tflops"],
+                      "achieved_fp64": a64, "peak_fp64_measured": peaks["fp64_measured_tflops"],
+                      "frac_fp64_of_measured_fp64": a64 / peaks["fp64_measured_tflops"]},
+         "fp32c_vs_fp64_max_rel_err": fp32c_vs_fp64_error(nl, ctx, mesh, cfg_for("fp32c"), cfg_for("fp64")),
+         "gpu_launches_per_matrix": l32 / steps}
+    if solve:
+        e["solve"] = solve_phase(nl, ctx, p.mesh, p, "fp32c", stream, dev, keep)
+    if rank == 0 and not args.no_cpu_baseline:
+        e["cpu_baseline"], _ = cpu_baseline(p, cpu_seconds)
+    return e
+
+
+def table1_times(nl, ctx, stream, dev, dist, flush, h=0.0125, steps=3):
+    """Assembly time of each ball of the paper's Table 1 on grid (a) with cell size h (K = 18432 at
+    h = 0.0125), with the paper's rule protocol, FP32-compensated, relative to the slowest
+    (exactcaps in the paper, whose times are relative to it too: context only)."""
+    from paper_2005_10775_gb300 import inputs as I
+    m = I.paper_grid(h)
+    keep = nl._Keep()
+    mesh = device_mesh(nl, m, dev, keep)
+    d = 0.1
+    ms = {}
+    for ball in ("exactcaps", "approxcaps", "nocaps", "barycenter", "overlap"):
+        cfg = nl.make_config(keep, d, ball, "switch47", "gauss3", "const", I.const_kernel_c(d), None, 2, "fp32c",
+                             cap_printed=1 if ball == "exactcaps" else 0)
+        t, _, _, _, _ = time_assembly(nl, ctx, mesh, cfg, steps, 1, stream, flush, dev, dist)
+        ms[ball] = t / steps
+    slow = max(ms.values())
+    paper = {"exactcaps": 10.31, "approxcaps": 8.36, "nocaps": 7.76, "barycenter": 4.24, "overlap": 5.23}
+    return {"h": h, "K": m.nt, "ms_per_matrix": ms, "relative_to_slowest_pct": {b: 100 * v / slow for b, v in ms.items()},
+            "paper_pct_of_its_slowest_run": paper,
+            "note": "paper Table 1 times at h = 0.0125 as a percentage of its slowest run (exactcaps, h = 0.00625); "
+                    "hardware unstated"}
+
+
 def main():
     args = parse()
     rank, local, world = dist_env()
@@ -476,6 +623,11 @@ def main():
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = nl.nl_create(local, stream.cuda_stream)
+    if args.peaks_only:
+        if rank == 0:
+            print(json.dumps({"fma_peaks": alu_peaks(nl, ctx), "gpu": torch.cuda.get_device_name(dev)}), flush=True)
+        nl.nl_destroy(ctx)
+        return
     if args.workload == "batch64":
         line = batch_bench(args, nl, ctx, stream, dev, world, dist, rank)
         nl.nl_destroy(ctx)
@@ -487,9 +639,7 @@ def main():
     p = I.problem(args.workload)
     m = p.mesh
     keep = nl._Keep()
-    dmesh = type("DevMesh", (), dict(vx=torch.tensor(m.vx, device=dev), vy=torch.tensor(m.vy, device=dev),
-                                     tri=torch.tensor(m.tri, device=dev)))
-    mesh = nl.make_mesh(dmesh, keep)
+    mesh = device_mesh(nl, m, dev, keep)
     off = None if p.ngon_off is None else torch.tensor(p.ngon_off, device=dev)
 
     def cfg_for(prec):
@@ -498,38 +648,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
 
     def run(prec, steps, warmup):
-        cfg = cfg_for(prec)
-        for _ in range(warmup):
-            out = nl.nl_assemble(ctx, mesh, cfg)
-            nl.nl_csr_free(ctx, out)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        tot = 0.0
-        phase = np.zeros(4)
-        stats = None
-        l0 = nl.nl_launch_count(ctx)
-        wall0 = time.perf_counter()
-        for _ in range(steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            out = nl.nl_assemble(ctx, mesh, cfg)
-            e1.record(stream)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-            phase += nl.nl_last_timings(ctx)
-            stats = (out.n_pairs, out.n_qp_pairs, out.n_inter, out.nnz, nl.nl_last_fp64_items(ctx))
-            nl.nl_csr_free(ctx, out)
-        launches = nl.nl_launch_count(ctx) - l0 - 0
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - wall0
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        return max_over_ranks(tot, dev, dist), phase / steps, stats, launches, wall
+        return time_assembly(nl, ctx, mesh, cfg_for(prec), steps, warmup, stream, flush, dev, dist)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -539,12 +658,15 @@ def main():
     ms_step = tot_ms / args.steps
     value = n_qp * world * args.steps / (tot_ms / 1e3)
 
-    # FP64 path for the FP32-comp vs FP64 comparison
+    # FP64 path for the FP32-comp vs FP64 comparison, and the error of the timed FP32c matrix
+    # against it (both assembled once more, compared entry by entry)
     fp64 = None
+    err32 = None
     if args.fp64_steps > 0 and args.prec != "fp64":
         t64, ph64, _, _, _ = run("fp64", args.fp64_steps, 1)
         fp64 = {"ms_per_step": t64 / args.fp64_steps, "value": n_qp * world * args.fp64_steps / (t64 / 1e3),
                 "numeric_ms": ph64[1]}
+        err32 = fp32c_vs_fp64_error(nl, ctx, mesh, cfg_for("fp32c"), cfg_for("fp64"))
 
     # end to end through the C ABI with host buffers: H2D of the mesh inside, D2H of the CSR
     e2e = None
@@ -578,9 +700,8 @@ def main():
     if args.solve:
         solve = solve_phase(nl, ctx, m, p, args.prec, stream, dev, keep)
 
-    peaks, src = measured_peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    peaks = alu_peaks(nl, ctx)
+    peak = peaks["fp32_derived_tflops"]
     numeric_ms = phase[1]
     achieved = (FLOP_PER_QP * n_qp + FLOP_PER_INTER * n_inter) / (numeric_ms / 1e3) / 1e12
     line = {
@@ -597,19 +718,47 @@ def main():
                    "wall_s_timed": wall},
         "fp64": fp64,
         "speedup_fp32c_vs_fp64": (fp64["ms_per_step"] / ms_step) if fp64 else None,
+        "fp32c_vs_fp64_max_rel_err": err32,
         "roofline": {"bound": "alu", "kernel": "k_interior + k_boundary + k_deferred (pair geometry + quadrature)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 x {sm_mhz:.0f} MHz "
-                                    f"(clock from MEASURED_PEAKS.json, {src})",
+                     "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz "
+                                    f"(clock from MEASURED_PEAKS.json, {peaks['clock_source']})",
+                     "frac_of_measured_fp32": achieved / peaks["fp32_measured_tflops"],
                      "traffic": NCU_TRAFFIC[args.workload][0] if args.workload in NCU_TRAFFIC else None,
                      "traffic_source": NCU_TRAFFIC[args.workload][1] if args.workload in NCU_TRAFFIC else None},
+        "fma_peaks": peaks,
         "clocks": ck,
         "solve": solve,
         "gpu_launches": int(launches),
         "e2e": e2e,
     }
+    if fp64:
+        a64 = (FLOP_PER_QP * n_qp + FLOP_PER_INTER * n_inter) / (fp64["numeric_ms"] / 1e3) / 1e12
+        line["roofline"]["fp64_path"] = {"achieved": a64, "peak_fp64_measured": peaks["fp64_measured_tflops"],
+                                         "frac": a64 / peaks["fp64_measured_tflops"]}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"], _ = cpu_baseline(p, args.cpu_seconds)
+    if not args.no_configs and args.workload == "ngon32_96":
+        # the other benchmark configurations, measured the same way (not the headline)
+        cfgs = {}
+        ck2 = ClockSampler(local)
+        ck2.start()
+        for name, solve_it in (("barycenter_32", False), ("singular_128", False), ("solve_220", True)):
+            cfgs[name] = config_entry(args, nl, ctx, name, stream, dev, dist, flush, world, rank, peaks,
+                                      solve=solve_it)
+        cfgs["paper_table1_times"] = table1_times(nl, ctx, stream, dev, dist, flush)
+        bargs = argparse.Namespace(**vars(args))
+        bargs.steps, bargs.warmup, bargs.fp64_steps, bargs.no_e2e = 3, 1, 1, True
+        bargs.no_cpu_baseline = args.no_cpu_baseline
+        bl = batch_bench(bargs, nl, ctx, stream, dev, world, dist, rank, cpu_seconds=4.0)
+        cfgs["batch64"] = {k: bl[k] for k in ("value", "ms_per_step", "config", "sequential",
+                                              "speedup_batch_vs_sequential", "reassembly", "fp64",
+                                              "speedup_fp32c_vs_fp64", "roofline", "gpu_launches")
+                           if k in bl}
+        if "cpu_baseline" in bl:
+            cfgs["batch64"]["cpu_baseline"] = bl["cpu_baseline"]
+        cfgs["clocks"] = ck2.stop()
+        line["configs"] = cfgs
     nl.nl_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
