@@ -168,10 +168,12 @@ nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *inout);
      - scatters all problems in one launch per value type;
      - captures the numeric phase + scatter of the whole batch in a CUDA graph that
        nl_batch_run replays (re-assembly of the values on unchanged meshes).
-   The work-item order and size are picked by a built-in autotuner: the first batch of
-   a given shape (sizes, candidate counts, balls, rules, precisions) times a few
-   schedules of the numeric launch and keeps the fastest in the context; later batches
-   of the same shape reuse it.  Every schedule yields the same pair blocks: each outer
+   The work-item size and order and the resident blocks per SM of the persistent launches
+   are picked by a built-in autotuner: the first batch of a given shape (sizes, candidate
+   counts, balls, rules, precisions) times eight schedules of the numeric phase (outer
+   triangles per item 1 or 4, problems in input order or costliest first, blocks per SM at
+   the occupancy limit or one fewer), each the median of three runs, and keeps the fastest
+   in the context; later batches of the same shape reuse it.  Every schedule yields the same pair blocks: each outer
    triangle's blocks are produced by one warp in a fixed order (the per-triangle sums
    taken with FP64 atomics, like the scatter's, may differ in the last bits). */
 typedef struct nl_batch nl_batch;
@@ -183,13 +185,14 @@ typedef struct {
     int32_t chunk;        /* outer triangles per work item */
     int32_t order;        /* 0: problems in input order; 1: costliest problems first (estimated
                              candidates x outer points x inner points per triangle) */
-    int32_t blocks;       /* persistent grid of the first boundary-candidate launch (blocks of 128 threads) */
+    int32_t blocks;       /* persistent grid of the first boundary-candidate launch (blocks of 128 threads)
+                             under the chosen schedule */
     int32_t launches;     /* numeric launches per run: one interior launch per value type, one boundary
                              launch per value type x ball x kernel type */
     int32_t source;       /* NL_SCHED_*: how the schedule was chosen */
     int32_t n_tried;      /* schedules timed by the autotuner in this nl_batch_create */
-    double tuned_ms;      /* numeric phase of the batch with the chosen schedule (NL_SCHED_TUNED) */
-    double default_ms;    /* the same with the default schedule (NL_SCHED_TUNED) */
+    double tuned_ms;      /* numeric phase of the batch with the chosen schedule (NL_SCHED_TUNED; median of 3) */
+    double default_ms;    /* the same with the default schedule (NL_SCHED_TUNED; median of 3) */
 } nl_batch_info;
 
 /* Assemble problems i = 0..n-1 (meshes[i], cfgs[i]) into outs[i] (library-owned, freed

@@ -222,7 +222,11 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     for (int j = 0; j < 8; j++) {
         A.glf_x[j] = j < A.duffy_n ? (float)A.gl_x[j] : 0.f;
         A.glf_w[j] = j < A.duffy_n ? (float)A.gl_w[j] : 0.f;
+        A.glf_sh[j] = j < A.duffy_n ? (float)sinh(A.gl_x[j]) : 0.f;
+        A.glf_ch[j] = j < A.duffy_n ? (float)cosh(A.gl_x[j]) : 1.f;
     }
+    A.sh1f = (float)sinh(1.0);
+    A.ch1f = (float)cosh(1.0);
     for (int j = 0; j < 2; j++) {
         A.gl2f_x[j] = (float)A.gl2_x[j];
         A.gl2f_w[j] = (float)A.gl2_w[j];
@@ -355,6 +359,25 @@ nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats)
     A.dval = nlq::defer_values(A.defer, P->defer_cap);
     A.defer_n = P->defer_n;
     A.defer_cap = P->defer_cap;
+    if (P->cfg.kernel == NL_KERNEL_INV_DIST) {
+        if (!P->near_n) {
+            const int cap = nl_near_cap(P->E);
+            nlq::DeferItem *q = nullptr;
+            if (cap > 0 && (s = nl_alloc(ctx, &q, (size_t)cap)) != NL_OK) return s;
+            P->nearq = q;
+            nlq::OuterPt *ot = nullptr;
+            if (cap > 0 && (s = nl_alloc(ctx, &ot, (size_t)P->K * A.outer.n)) != NL_OK) return s;
+            P->otab = ot;
+            if ((s = nl_alloc(ctx, &P->near_n, 1)) != NL_OK) return s;
+            P->near_cap = cap;
+        }
+        if (P->near_cap > 0) {
+            A.nearq = (nlq::DeferItem *)P->nearq;
+            A.near_n = P->near_n;
+            A.near_cap = P->near_cap;
+            A.otab = (nlq::OuterPt *)P->otab;
+        }
+    }
     return nl_launch_numeric_f32(ctx, A, P->cfg.ball);
 }
 
@@ -368,6 +391,7 @@ void nl_plan_free(nl_plan *P, cudaStream_t s)
     nl_free(P->nbr_split, s); nl_free(P->flag, s); nl_free(P->blk, s); nl_free(P->maa, s); nl_free(P->qp_a, s);
     nl_free(P->cnt_a, s); nl_free(P->hash_a, s); nl_free(P->lslot, s); nl_free(P->mbb, s); nl_free(P->tslot, s); nl_free(P->W, s);
     nl_free(P->val32, s); nl_free(P->x32, s); nl_free(P->err, s); nl_free(P->defer, s); nl_free(P->defer_n, s);
+    nl_free(P->nearq, s); nl_free(P->near_n, s); nl_free(P->otab, s);
 }
 
 nl_status nl_host_slots(nl_ctx *ctx, int n, nl_host_slot **out)

@@ -13,8 +13,9 @@
 //     of one problem) from the launch's global counter;
 //   * the scatter of every problem runs in one launch per value type;
 //   * numeric phase + scatter are captured once in a CUDA graph (nl_batch_run).
-// The autotuner times the numeric launch under a few schedules (item size, item
-// order) on the batch itself and keeps the fastest per batch shape in the context.
+// The autotuner times the numeric launches under eight schedules (item size, item order,
+// resident blocks per SM), the median of three runs each, on the batch itself and keeps the
+// fastest per batch shape in the context.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
@@ -41,6 +42,7 @@ __global__ void k_zero_mbb_batch(const nlq::NumArgs *__restrict__ As)
 struct Sched {
     int chunk = 1;
     int order = 0;
+    int fewer = 0;   // resident blocks per SM below the occupancy limit, for every persistent launch
 };
 
 // Host arrays that feed a cudaMemcpyAsync stay alive until the stream has passed the
@@ -62,6 +64,7 @@ struct Launch {                    // one persistent numeric launch
     nlq::BatchItem *items = nullptr;
     int n_items = 0, cap_items = 0;
     int blocks = 0;
+    int per_sm = 1;                    // resident blocks per SM at the occupancy limit
     nlq::DeferItem *defer = nullptr;   // float boundary launches: queue of the FP64-decided items
     int defer_cap = 0;
 };
@@ -186,6 +189,12 @@ double triangle_cost(const nl_plan *P)
     return cand * rule_points(P->cfg.outer) * rule_points(P->cfg.inner);
 }
 
+// persistent grid of every launch under schedule sc (SM count nsm)
+void apply_grid(nl_batch *b, const Sched &sc, int nsm)
+{
+    for (Launch &l : b->launches) l.blocks = std::max(1, l.per_sm - sc.fewer) * nsm;
+}
+
 nl_status build_items(nl_ctx *ctx, nl_batch *b, const Sched &sc)
 {
     // the previous item lists may still be in flight to the device
@@ -264,24 +273,30 @@ nl_status launch_scatter(nl_ctx *ctx, nl_batch *b, bool set_attr)
     return nl_launch_symmetrize_batch(ctx, b->dS_all, b->dzoff, b->n, b->total_nnz);
 }
 
-// device time of one numeric run of the batch under schedule sc
-nl_status time_numeric(nl_ctx *ctx, nl_batch *b, const Sched &sc, double *ms)
+// device time of the numeric phase of the batch under schedule sc: the median of `reps` runs
+nl_status time_numeric(nl_ctx *ctx, nl_batch *b, const Sched &sc, int nsm, int reps, double *ms)
 {
     nl_status s = build_items(ctx, b, sc);
     if (s != NL_OK) return s;
+    apply_grid(b, sc, nsm);
     if (!b->tev[0]) NL_CK(cudaEventCreate(&b->tev[0]));
     if (!b->tev[1]) NL_CK(cudaEventCreate(&b->tev[1]));
-    NL_CK(cudaEventRecord(b->tev[0], ctx->stream));
-    if ((s = launch_numeric(ctx, b, false)) != NL_OK) return s;
-    NL_CK(cudaEventRecord(b->tev[1], ctx->stream));
-    NL_CK(cudaEventSynchronize(b->tev[1]));
-    float f = 0.0f;
-    NL_CK(cudaEventElapsedTime(&f, b->tev[0], b->tev[1]));
-    *ms = f;
+    std::vector<double> t;
+    for (int r = 0; r < reps; r++) {
+        NL_CK(cudaEventRecord(b->tev[0], ctx->stream));
+        if ((s = launch_numeric(ctx, b, false)) != NL_OK) return s;
+        NL_CK(cudaEventRecord(b->tev[1], ctx->stream));
+        NL_CK(cudaEventSynchronize(b->tev[1]));
+        float f = 0.0f;
+        NL_CK(cudaEventElapsedTime(&f, b->tev[0], b->tev[1]));
+        t.push_back(f);
+    }
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
     return NL_OK;
 }
 
-nl_status pick_schedule(nl_ctx *ctx, nl_batch *b, int flags)
+nl_status pick_schedule(nl_ctx *ctx, nl_batch *b, int flags, int nsm)
 {
     const uint64_t sig = batch_signature(b);
     Sched def;   // one outer triangle per item, input order
@@ -296,27 +311,32 @@ nl_status pick_schedule(nl_ctx *ctx, nl_batch *b, int flags)
             b->info.source = NL_SCHED_CACHED;
             return NL_OK;
         }
-    // warm-up (instruction cache, L2, clocks), then every candidate once
+    // warm-up (instruction cache, L2, clocks), then every candidate: the median of three runs.
+    // Candidates: outer triangles per item (1, 4), problem order (input, costliest first) and
+    // resident blocks per SM (the occupancy limit, one fewer: fewer blocks leave each one more
+    // of the SM's L1 and issue slots, more blocks hide more latency)
     double ms = 0.0;
-    nl_status s = time_numeric(ctx, b, def, &ms);
+    nl_status s = time_numeric(ctx, b, def, nsm, 1, &ms);
     if (s != NL_OK) return s;
-    const int chunks[4] = {1, 2, 4, 8};
+    const int chunks[2] = {1, 4};
     double best = INFINITY;
     Sched bs = def;
     int tried = 0;
-    for (int order = 0; order < 2; order++)
-        for (int c : chunks) {
-            Sched sc;
-            sc.chunk = c;
-            sc.order = order;
-            if ((s = time_numeric(ctx, b, sc, &ms)) != NL_OK) return s;
-            tried++;
-            if (c == def.chunk && order == def.order) b->info.default_ms = ms;
-            if (ms < best) {
-                best = ms;
-                bs = sc;
+    for (int fewer = 0; fewer < 2; fewer++)
+        for (int order = 0; order < 2; order++)
+            for (int c : chunks) {
+                Sched sc;
+                sc.chunk = c;
+                sc.order = order;
+                sc.fewer = fewer;
+                if ((s = time_numeric(ctx, b, sc, nsm, 3, &ms)) != NL_OK) return s;
+                tried++;
+                if (c == def.chunk && order == def.order && fewer == def.fewer) b->info.default_ms = ms;
+                if (ms < best) {
+                    best = ms;
+                    bs = sc;
+                }
             }
-        }
     b->sched = bs;
     b->info.source = NL_SCHED_TUNED;
     b->info.n_tried = tried;
@@ -534,14 +554,20 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
         s = b->pgroups[l.prec].f64 ? nl_batch_occupancy_f64(ctx, l.ball, l.inv, &per_sm)
                                    : nl_batch_occupancy_f32(ctx, l.ball, l.inv, &per_sm);
         if (s != NL_OK) return fail(s);
-        l.blocks = std::max(1, per_sm) * nsm;
-        if (l.ball >= 0 && b->info.blocks == 0) b->info.blocks = l.blocks;
+        l.per_sm = std::max(1, per_sm);
+        l.blocks = l.per_sm * nsm;
     }
     b->info.launches = (int)b->launches.size();
-    if ((s = pick_schedule(ctx, b, flags)) != NL_OK) return fail(s);
+    if ((s = pick_schedule(ctx, b, flags, nsm)) != NL_OK) return fail(s);
     b->info.chunk = b->sched.chunk;
     b->info.order = b->sched.order;
     if ((s = build_items(ctx, b, b->sched)) != NL_OK) return fail(s);
+    apply_grid(b, b->sched, nsm);
+    for (const Launch &l : b->launches)
+        if (l.ball >= 0) {
+            b->info.blocks = l.blocks;
+            break;
+        }
     if (cudaEventRecord(ctx->ev[1], st) != cudaSuccess) return fail(nl_fail(ctx, NL_ECUDA, "cudaEventRecord"));
     if ((s = launch_numeric(ctx, b, true)) != NL_OK || (s = phase_check(ctx, b, "numeric")) != NL_OK) return fail(s);
     if (cudaEventRecord(ctx->ev[2], st) != cudaSuccess) return fail(nl_fail(ctx, NL_ECUDA, "cudaEventRecord"));

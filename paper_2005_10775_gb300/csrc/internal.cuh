@@ -127,7 +127,30 @@ struct nl_plan {
     void *defer = nullptr;
     int *defer_n = nullptr;
     int defer_cap = 0;
+    // FP32 path of the singular kernel: queue of the near-field whole items (nlq::DeferItem)
+    // that k_near integrates, and its fill count
+    void *nearq = nullptr;
+    int *near_n = nullptr;
+    int near_cap = 0;
+    void *otab = nullptr;         // [K][outer points] nlq::OuterPt staged by the boundary kernel for k_near
 };
+
+// capacity of the near-field queue of the singular kernel's FP32 path for E candidate pairs:
+// about 27 near-field triangles per outer point on the benchmark meshes, 16 outer points, some
+// 330 candidates per triangle (1.3 E items); a full queue sends the excess to the boundary
+// kernel's own lanes.  NL_NEAR_CAP in the environment sets it (0: no queue, all inline).
+inline int nl_near_cap(int64_t E)
+{
+    const char *v = getenv("NL_NEAR_CAP");
+    if (v && *v) {
+        const long long c = strtoll(v, nullptr, 10);
+        return c < 0 ? 0 : (int)(c > (1ll << 30) ? (1ll << 30) : c);
+    }
+    int64_t c = 2 * E;
+    if (c < 4096) c = 4096;
+    if (c > (int64_t(1) << 30)) c = int64_t(1) << 30;
+    return (int)c;
+}
 
 // ---- error helpers ----
 nl_status nl_fail(nl_ctx *ctx, nl_status s, const std::string &msg);

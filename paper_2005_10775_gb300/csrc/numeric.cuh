@@ -50,6 +50,8 @@ inline size_t defer_alloc_items(int cap)
 }
 __host__ __device__ inline float *defer_values(DeferItem *q, int cap) { return q ? (float *)(q + cap) : nullptr; }
 
+struct OuterPt;
+
 struct NumArgs {
     int K;
     int64_t E;
@@ -65,6 +67,8 @@ struct NumArgs {
     double gl_x[8], gl_w[8];          // Gauss-Legendre on [0,1] with duffy_n points
     double gl2_x[2], gl2_w[2];
     float glf_x[8], glf_w[8];         // the same rules in FP32 (no FP64 conversions in the FP32 path)
+    float glf_sh[8], glf_ch[8];       // sinh and cosh of the duffy_n nodes glf_x (FP32)
+    float sh1f, ch1f;                 // sinh(1), cosh(1) (FP32)
     float gl2f_x[2], gl2f_w[2];
     float kcf;                        // kc in FP32
     int duffy_n;
@@ -89,6 +93,12 @@ struct NumArgs {
     float *dval;                      // [9][defer_cap]: each queued item's M_ab (k_deferred -> k_defer_merge)
     int *defer_n;                     // its fill count (zeroed before the boundary launch; may exceed the cap)
     int defer_cap;
+    DeferItem *nearq;                 // FP32 path, singular kernel: queue of the near-field whole items that
+                                      // k_near integrates (null: the boundary kernel integrates them itself)
+    int *near_n;                      // its fill count (zeroed before the boundary launch; may exceed the cap)
+    int near_cap;
+    OuterPt *otab;                    // [K][outer.n] outer points as the boundary kernel staged them (read by
+                                      // k_near; with the near-field queue only)
     int prob;                         // index of this problem in a batched launch's argument array
 };
 
@@ -499,29 +509,48 @@ __device__ __forceinline__ void near_whole_f32(const NumArgs &A, const nlg::F2 d
         }
         if (skip_edge || d == 0.f) continue;
         const float sigma = (Fx * ey - Fy * ex) > 0.f ? 1.f : -1.f;
-        for (int side = 0; side < 2; side++) {
-            const float tau = side == 0 ? tB : tA, U = side == 0 ? UB : UA;
-            const int npan = side == 0 ? npB : npA;
-            if ((side == 0 ? skipB : skipA) || npan == 0) continue;
-            const float sign = side == 0 ? sigma : -sigma;
+        // The panels of both sides (B, then A) in one loop, so that lanes whose sides split their
+        // panels differently still run the loop body together.  On a full panel [p, p + 1],
+        // sinh(p + x_j) = sinh(p) cosh(x_j) + cosh(p) sinh(x_j), with sinh(p), cosh(p) carried from
+        // panel to panel by the same addition theorem (sinh(1), cosh(1)); the last panel of a side,
+        // [p, U], evaluates sinh directly.  The FP32 point y = s w - v_0 of T_b relative to its
+        // first vertex is linear in s, and so are its barycentrics: l = s l_w - l_0.
+        const int nB = skipB ? 0 : npB, nA = skipA ? 0 : npA;
+        const float l10 = (dl[0].x * e2.y - e2.x * dl[0].y) * inv_det;
+        const float l20 = (e1.x * dl[0].y - dl[0].x * e1.y) * inv_det;
+        float sp = 0.f, cp = 1.f;   // sinh, cosh of the panel start
+        for (int p = 0; p < nB + nA; p++) {
+            const bool sideA = p >= nB;
+            const int pnl = sideA ? p - nB : p, npan = sideA ? nA : nB;
+            const float tau = sideA ? tA : tB, U = sideA ? UA : UB;
+            const float sign = sideA ? -sigma : sigma;
             const float sg = tau > 0.f ? 1.f : -1.f;
-            for (int pnl = 0; pnl < npan; pnl++) {
-                const float u0 = (float)pnl, u1 = (pnl + 1 < npan) ? (float)(pnl + 1) : fmaxf(U, u0);
-                const float hw = u1 - u0;
-                for (int j = 0; j < nu; j++) {
-                    const float u = u0 + hw * A.glf_x[j];
-                    const float wu = hw * A.glf_w[j];
-                    const float sh = sinhf(u);
-                    const float wx = Fx + sg * d * sh * ex, wy = Fy + sg * d * sh * ey;
-                    for (int k = 0; k < 2; k++) {
-                        const float sv = A.gl2f_x[k];
-                        const float rx = sv * wx - dl[0].x, ry = sv * wy - dl[0].y;
-                        const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
-                        const float l2 = (e1.x * ry - rx * e1.y) * inv_det;
-                        sums_add<float>(S, sign * sg * d * A.gl2f_w[k] * wu * kc, 1.f - l1 - l2, l1, l2);
-                        nqp++;
-                    }
+            if (pnl == 0) {
+                sp = 0.f;
+                cp = 1.f;
+            }
+            const bool full = pnl + 1 < npan;
+            const float u0 = (float)pnl, hw = full ? 1.f : fmaxf(U, u0) - u0;
+            const float gdx = sg * d * ex, gdy = sg * d * ey, kcs = sign * sg * d * kc;
+            // the Gauss points of the panel: sinh at the node, then the two points in s
+            auto node = [&](int j, float sh) {
+                const float wj = kcs * (hw * A.glf_w[j]);
+                const float wx = fmaf(sh, gdx, Fx), wy = fmaf(sh, gdy, Fy);
+                const float l1w = (wx * e2.y - e2.x * wy) * inv_det;
+                const float l2w = (e1.x * wy - wx * e1.y) * inv_det;
+                for (int k = 0; k < 2; k++) {
+                    const float sv = A.gl2f_x[k];
+                    const float l1 = sv * l1w - l10, l2 = sv * l2w - l20;
+                    sums_add<float>(S, wj * A.gl2f_w[k], 1.f - l1 - l2, l1, l2);
                 }
+            };
+            for (int j = 0; j < nu; j++)
+                node(j, full ? fmaf(sp, A.glf_ch[j], cp * A.glf_sh[j]) : sinhf(u0 + hw * A.glf_x[j]));
+            nqp += 2 * nu;
+            if (full) {
+                const float sn = fmaf(sp, A.ch1f, cp * A.sh1f);
+                cp = fmaf(cp, A.ch1f, sp * A.sh1f);
+                sp = sn;
             }
         }
     }
@@ -1080,6 +1109,59 @@ __device__ __forceinline__ void defer_flush(const NumArgs &A, int a, int64_t bas
     }
 }
 
+// A near-field whole item integrated by its owner lane into its own column of the shared
+// accumulator (the near-field queue is full).  Not inlined: the boundary kernel's code stays
+// free of the near rule, which runs in k_near.
+template <typename T>
+__device__ __noinline__ int64_t near_inline(const NumArgs &A, const CandData &cd, const OuterPt &o,
+                                            BoundaryShared<T> &sh, int lane)
+{
+    nlg::F2 dl[3];
+    for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
+    Sums<float> S;
+    int64_t nq = 0;
+    const nlg::F2 e1 = {cd.e1x, cd.e1y}, e2 = {cd.e2x, cd.e2y};
+    near_whole_f32(A, dl, cd.b, D2{o.x, o.y}, e1, e2, cd.binv, S, nq);
+    float w[21];
+    for (int k = 0; k < 21; k++) w[k] = 0.f;
+    combine<float>(o, S, w);
+    for (int k = 0; k < 21; k++) sh.acc[k][lane] += (T)w[k];
+    sh.acc[21][lane] = (T)1;
+    return nq;
+}
+
+// Queue the near-field whole items of this lane's candidate (outer points m, bit q) for k_near,
+// one reservation for the warp, in (owner, q) order; past the queue's capacity the lane
+// integrates them itself.
+template <typename T>
+__device__ __forceinline__ void near_flush(const NumArgs &A, int a, int64_t base, unsigned m, BoundaryShared<T> &sh,
+                                           int lane, LaneAcc &acc)
+{
+    const int cnt = __popc(m);
+    int inc = cnt;
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    if (total == 0) return;
+    int slot0 = 0;
+    if (lane == 0) slot0 = atomicAdd(A.near_n, total);
+    slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+    int slot = slot0 + inc - cnt;
+    for (unsigned rest = m; rest; rest &= rest - 1, slot++) {
+        const int q = __ffs(rest) - 1;
+        if (slot < A.near_cap) {
+            A.nearq[slot] = DeferItem{base + lane, a, (A.prob << 8) | q};
+            continue;
+        }
+        const CandData &cd = sh.cand[lane];
+        acc.cnt++;
+        acc.qp += near_inline<T>(A, cd, sh.sq[q], sh, lane);
+        if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
+    }
+}
+
 // The boundary candidates of outer triangle a (outer points staged in sh.sq).
 // INV: the kernel is psi = c/|x - y| (near-field split), else the constant kernel.
 template <int BALL, typename T, bool INV>
@@ -1117,7 +1199,11 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         sh.dmask[lane] = 0;
         int nqueue = 0;
         __syncwarp();
-        // phase 1: classify every (q, b) in lockstep; queue whole and undecided items
+        // phase 1: classify every (q, b) in lockstep; queue whole and undecided items.  With a
+        // near-field queue (FP32 singular kernel), the near-field whole items of this lane's
+        // candidate are only marked (my_near, bit q) and handed to k_near after the round.
+        const bool split_near = INV && sizeof(T) == sizeof(float) && A.nearq != nullptr;
+        unsigned my_near = 0;
         int nwhole = 0, nnear = 0;
         for (int q = 0; q < nq_all; q++) {
             const bool active = valid && q >= q0 && q < q1;
@@ -1130,6 +1216,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
                 if (inv && cls == nlg::CLS_WHOLE) {
                     const int nr = nlg::near_f32(dl, cand_diam(c), A.geo.tau);
                     cls = nr == 0 ? nlg::CLS_WHOLE : (nr == 1 && sizeof(T) == sizeof(float) ? 3 : nlg::CLS_EXACT);
+                    if (cls == 3 && split_near) {
+                        my_near |= 1u << q;
+                        cls = nlg::CLS_EMPTY;
+                    }
                 }
             }
             const unsigned mw = __ballot_sync(0xffffffffu, cls == nlg::CLS_WHOLE);
@@ -1257,6 +1347,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         __syncwarp();
         if (sizeof(T) == sizeof(float) && A.defer) {
             defer_flush<BALL, T>(A, a, base, sh, lane, acc);
+            __syncwarp();
+        }
+        if (split_near) {
+            near_flush<T>(A, a, base, my_near, sh, lane, acc);
             __syncwarp();
         }
         // phase 3: owners merge the queue's contributions and write their pair
@@ -1391,6 +1485,8 @@ __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundarySh
     } else {
         stage_outer(A, a, sh.sq, lane);
         __syncwarp();
+        if (INV && A.otab)   // k_near reads the outer points from here (no FP64 arithmetic per item)
+            for (int q = lane; q < A.outer.n; q += 32) A.otab[(int64_t)a * A.outer.n + q] = sh.sq[q];
         boundary_outer<BALL, T, INV>(A, a, sh, lane, acc);
     }
 }
@@ -1563,6 +1659,107 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const DeferItem d = items[i];
         deferred_item<BALL>(As[d.qp >> 8], d, dv, cap, i, cb[threadIdx.x >> 5], threadIdx.x & 31);
+    }
+}
+
+// Sum v (NV values) over each run of equal keys in lane order (runs of one key are contiguous
+// in lane order; key < 0: a lane without values): the first lane of each run gets its run's sum,
+// by a segmented tree of shuffles (five steps, a fixed order of additions), and the return value
+// says which lanes lead a run.  All 32 lanes call this.
+template <int NV, typename V>
+__device__ __forceinline__ bool warp_run_sum(long long key, int lane, V *v)
+{
+    const long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    // last lane of this lane's run: one before the next head (or lane 31)
+    const unsigned later = heads & ~((2u << lane) - 1u);
+    const int run_end = later ? __ffs(later) - 2 : 31;
+    for (int off = 1; off < 32; off <<= 1)
+        for (int k = 0; k < NV; k++) {
+            const V x = __shfl_down_sync(0xffffffffu, v[k], off);
+            if (lane + off <= run_end) v[k] += x;
+        }
+    return head && key >= 0;
+}
+
+// ---------------------------------------------------------------------------
+// Near-field whole items of the FP32 singular kernel (after the boundary launch, in stream
+// order): the boundary kernel queues every (x_q, T_b) whose whole T_b lies in the near field of
+// x_q (certified in FP32), in (pair, outer point) order; here each lane takes one and runs the
+// near-singular rule (signed apex-x decomposition, Duffy collapse, sinh substitution) on it.
+// The blocks are summed over the lanes of one pair (M_ab onto the pair's stored values with
+// FP32 atomics, M_bb onto T_b's sums) and of one outer triangle (M_aa, statistics), so a warp
+// issues a few atomics per pair instead of one per item.
+// ---------------------------------------------------------------------------
+template <int BALL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_near(const NumArgs A)
+{
+    const int n = min(*A.near_n, A.near_cap);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int K = A.K;
+    for (int64_t base = warp0 * 32; base < n; base += nwarps * 32) {
+        const int64_t i = base + lane;
+        float w[21];
+        for (int k = 0; k < 21; k++) w[k] = 0.f;
+        long long ke = -1, ka = -1;
+        int b = 0, q = 0, q0 = 0;
+        int64_t nq = 0;
+        if (i < n) {
+            const DeferItem d = A.nearq[i];
+            const int a = d.a;
+            q = d.qp & 0xff;
+#ifdef NL_CHECKS
+            if (a < 0 || a >= K || d.e < 0 || d.e >= A.E || q >= A.outer.n) {   // debug build: bad item (bit 128)
+                atomicOr(A.err, 128);
+                ka = -2;
+            }
+#endif
+            if (ka != -2) {
+                b = A.nbr_idx[d.e];
+                const OuterPt o = A.otab[(int64_t)a * A.outer.n + q];
+                const D2 ba = {A.bx[a], A.by[a]};
+                CandData c;
+                int q1;
+                load_cand(A, b, ba, bary_hilo(A, a), c, q1);
+                q0 = c.q0;
+                nlg::F2 dl[3];
+                for (int k = 0; k < 3; k++) { dl[k].x = c.vlx[k] - o.lx; dl[k].y = c.vly[k] - o.ly; }
+                Sums<float> S;
+                const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
+                near_whole_f32(A, dl, b, D2{o.x, o.y}, e1, e2, c.binv, S, nq);
+                combine<float>(o, S, w);
+                A.flag[d.e] = 1;
+                ke = d.e;
+                ka = a;
+            }
+        }
+        // M_ab onto the pair, M_bb onto T_b: one add per run of one pair in the warp (a warp's
+        // items of one pair are adjacent: the queue holds them in (pair, outer point) order)
+        if (warp_run_sum<15>(ke, lane, w)) {
+            float *blk = (float *)A.blk;
+            for (int k = 0; k < 9; k++) atomicAdd(&blk[(int64_t)k * A.E + ke], w[k]);
+            for (int k = 0; k < 6; k++) atomicAdd(&A.mbb[(int64_t)k * K + b], (double)w[9 + k]);
+        }
+        // M_aa and the statistics onto T_a: one add per run of one outer triangle (the lanes' M_aa
+        // summed in FP32, like every short sum of the FP32 path: FP64 arithmetic runs at 1/64 of
+        // the FP32 rate here, and a warp-wide FP64 shuffle sum would occupy the FP64 pipe)
+        float ma[6];
+        for (int k = 0; k < 6; k++) ma[k] = w[15 + k];
+        unsigned long long st[3] = {ka >= 0 ? 1ull : 0ull, (unsigned long long)nq,
+                                    (ka >= 0 && A.stats) ? (unsigned long long)nlg::record_hash(
+                                        (int)ka, b, q - q0, nlg::KIND_WHOLE, 3, 0) : 0ull};
+        const long long kk = ka >= 0 ? ka : -1;
+        const bool lead = warp_run_sum<6>(kk, lane, ma);
+        warp_run_sum<3>(kk, lane, st);
+        if (lead) {
+            for (int k = 0; k < 6; k++) atomicAdd(&A.maa[(int64_t)k * K + kk], (double)ma[k]);
+            atomicAdd((unsigned long long *)&A.cnt_a[kk], st[0]);
+            atomicAdd((unsigned long long *)&A.qp_a[kk], st[1]);
+            if (A.stats) atomicAdd((unsigned long long *)&A.hash_a[kk], st[2]);
+        }
     }
 }
 

@@ -12,12 +12,25 @@ nl_status launch_boundary_k(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, u
     const bool defer = kQueue && A.defer;
     if (stage == 0) {
         if (defer) NL_CK(cudaMemsetAsync(A.defer_n, 0, sizeof(int), ctx->stream));
+        if (A.nearq) NL_CK(cudaMemsetAsync(A.near_n, 0, sizeof(int), ctx->stream));
         const size_t smem = sizeof(nlq::BoundaryShared<float>) * nlq::kWarpsPerBlock;
         NL_CK(cudaFuncSetAttribute(nlq::k_boundary<BALL, float, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
         nlq::k_boundary<BALL, float, INV><<<grid, threads, smem, ctx->stream>>>(A); ++ctx->launches;
         NL_CK(cudaGetLastError());
         return NL_OK;
+    }
+    if constexpr (kQueue && INV) {
+        if (A.nearq) {   // the near-field whole items the boundary kernel queued
+            // one resident wave: every warp strides over the queue, so a second wave of blocks
+            // would only idle while the first finishes
+            int nsm = 0, per_sm = 0;
+            NL_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+            NL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nlq::k_near<BALL>, threads, 0));
+            const int blocks = (nsm > 0 ? nsm : 1) * (per_sm > 0 ? per_sm : 1);
+            nlq::k_near<BALL><<<blocks, threads, 0, ctx->stream>>>(A); ++ctx->launches;
+            NL_CK(cudaGetLastError());
+        }
     }
     if constexpr (kQueue) {
         if (defer) {

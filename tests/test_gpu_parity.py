@@ -162,6 +162,28 @@ def test_fp64_items_queued_or_inline(nl, ctx, monkeypatch, ball, kernel):
         assert counts[None] > 4096
 
 
+@pytest.mark.parametrize("ball", ["ngon", "nocaps"])
+def test_near_field_items_queued_or_inline(nl, ctx, monkeypatch, ball):
+    # FP32 singular kernel: the near-field whole items go to k_near through a queue.  Without the
+    # queue (capacity 0: the boundary kernel integrates them in its own drain) or with a queue of
+    # one item (the rest integrated by their owner lanes), the records and the values are the
+    # oracle's, as with the default queue.
+    p = small_problem(ball, n=24, kernel="inv_dist")
+    out = O.assemble(p.mesh, oracle_cfg(p, duffy_n=4), want_hash=True)
+    for cap in (None, "0", "1"):
+        if cap is None:
+            monkeypatch.delenv("NL_NEAR_CAP", raising=False)
+        else:
+            monkeypatch.setenv("NL_NEAR_CAP", cap)
+        h, c, q = gpu_interactions(nl, ctx, p, prec="fp32c", duffy_n=4)
+        np.testing.assert_array_equal(c, out["count_a"])
+        np.testing.assert_array_equal(q, out["qp_a"])
+        np.testing.assert_array_equal(h, out["hash_a"])
+        Dg, stats = gpu_assemble(nl, ctx, p, "fp32c", duffy_n=4)
+        compare(Dg, O.to_csr(out), "fp32c")
+        assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
+
+
 def test_fp64_items_zero_on_fp64_path(nl, ctx):
     p = small_problem("ngon", n=24, kernel="inv_dist")
     gpu_interactions(nl, ctx, p, prec="fp64", duffy_n=4)
