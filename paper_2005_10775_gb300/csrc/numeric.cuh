@@ -1164,7 +1164,7 @@ __device__ __forceinline__ void near_flush(const NumArgs &A, int a, int64_t base
 
 // The boundary candidates of outer triangle a (outer points staged in sh.sq).
 // INV: the kernel is psi = c/|x - y| (near-field split), else the constant kernel.
-template <int BALL, typename T, bool INV>
+template <int BALL, typename T, bool INV, bool NQ = false>
 __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, BoundaryShared<T> &sh, int lane,
                                                LaneAcc &acc)
 {
@@ -1202,7 +1202,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         // phase 1: classify every (q, b) in lockstep; queue whole and undecided items.  With a
         // near-field queue (FP32 singular kernel), the near-field whole items of this lane's
         // candidate are only marked (my_near, bit q) and handed to k_near after the round.
-        const bool split_near = INV && sizeof(T) == sizeof(float) && A.nearq != nullptr;
+        constexpr bool split_near = INV && NQ && sizeof(T) == sizeof(float);
         unsigned my_near = 0;
         int nwhole = 0, nnear = 0;
         for (int q = 0; q < nq_all; q++) {
@@ -1284,7 +1284,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             for (int k = 0; k < 21; k++) sh.acc[k][lane] += extra[0][k][lane] + extra[1][k][lane];
         __syncwarp();
         // phase 2c: whole items in the singular kernel's near field (FP32 near rule)
-        for (int i = lane; INV && i < nnear; i += 32) {
+        for (int i = lane; INV && !split_near && i < nnear; i += 32) {
             const int left = nnear - (i - lane);   // items of this round
             const unsigned rmask = left >= 32 ? 0xffffffffu : ((1u << left) - 1u);
             const unsigned it = sh.wqueue[kQueueCap - 1 - i];
@@ -1349,7 +1349,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             defer_flush<BALL, T>(A, a, base, sh, lane, acc);
             __syncwarp();
         }
-        if (split_near) {
+        if constexpr (split_near) {
             near_flush<T>(A, a, base, my_near, sh, lane, acc);
             __syncwarp();
         }
@@ -1475,8 +1475,9 @@ __device__ __forceinline__ void support_boundary(const NumArgs &A, int a, int la
     }
 }
 
-// boundary candidates of outer triangle a for the ball mode BALL
-template <int BALL, typename T, bool INV>
+// boundary candidates of outer triangle a for the ball mode BALL (NQ: the singular kernel's
+// near-field whole items go to the near-field queue)
+template <int BALL, typename T, bool INV, bool NQ = false>
 __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundaryShared<T> &sh, int lane, LaneAcc &acc)
 {
     if constexpr (BALL == NL_BALL_BARY_NOCAPS || BALL == NL_BALL_BARY_APPROXCAPS) {
@@ -1487,7 +1488,7 @@ __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundarySh
         __syncwarp();
         if (INV && A.otab)   // k_near reads the outer points from here (no FP64 arithmetic per item)
             for (int q = lane; q < A.outer.n; q += 32) A.otab[(int64_t)a * A.outer.n + q] = sh.sq[q];
-        boundary_outer<BALL, T, INV>(A, a, sh, lane, acc);
+        boundary_outer<BALL, T, INV, NQ>(A, a, sh, lane, acc);
     }
 }
 
@@ -1496,7 +1497,7 @@ __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundarySh
 template <typename T, bool INV>
 constexpr int kBoundaryBlocksPerSm = sizeof(T) == sizeof(float) ? 4 : 3;
 
-template <int BALL, typename T, bool INV>
+template <int BALL, typename T, bool INV, bool NQ = false>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, INV>) k_boundary(const NumArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1506,7 +1507,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, I
     if (a >= A.K) return;
     LaneAcc acc;
     acc_zero(acc);
-    boundary_any<BALL, T, INV>(A, a, sh, lane, acc);
+    boundary_any<BALL, T, INV, NQ>(A, a, sh, lane, acc);
     // k_interior may be running: add atomically onto the zeroed outputs
     finish_outer(A, a, acc, lane, kAtomicAdd);
 }

@@ -14,9 +14,17 @@ nl_status launch_boundary_k(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, u
         if (defer) NL_CK(cudaMemsetAsync(A.defer_n, 0, sizeof(int), ctx->stream));
         if (A.nearq) NL_CK(cudaMemsetAsync(A.near_n, 0, sizeof(int), ctx->stream));
         const size_t smem = sizeof(nlq::BoundaryShared<float>) * nlq::kWarpsPerBlock;
-        NL_CK(cudaFuncSetAttribute(nlq::k_boundary<BALL, float, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-        nlq::k_boundary<BALL, float, INV><<<grid, threads, smem, ctx->stream>>>(A); ++ctx->launches;
+        // the singular kernel with its near-field queue: a kernel without the near rule's code
+        constexpr bool kNQ = INV && kQueue;
+        if (kNQ && A.nearq) {
+            NL_CK(cudaFuncSetAttribute(nlq::k_boundary<BALL, float, INV, kNQ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            nlq::k_boundary<BALL, float, INV, kNQ><<<grid, threads, smem, ctx->stream>>>(A); ++ctx->launches;
+        } else {
+            NL_CK(cudaFuncSetAttribute(nlq::k_boundary<BALL, float, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+            nlq::k_boundary<BALL, float, INV><<<grid, threads, smem, ctx->stream>>>(A); ++ctx->launches;
+        }
         NL_CK(cudaGetLastError());
         return NL_OK;
     }
