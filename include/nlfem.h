@@ -160,25 +160,30 @@ nl_status nl_assemble_numeric(nl_ctx *ctx, nl_csr *inout);
      - runs each preparation and symbolic stage for all problems before synchronising,
        so the whole batch waits on the host three times, not three times per problem,
        with the problems spread over eight streams of the context (joined by events);
-     - runs the numeric phase (pair geometry + quadrature) of all problems in one pair
-       of persistent launches (interior candidates, then boundary candidates) per value
-       type x kernel type present: their warps take work items (a run of outer triangles
-       of one problem) from a global counter, and the ball mode is dispatched per item,
-       so nocaps and approxcaps problems share them;
+     - runs the numeric phase (pair geometry + quadrature) of all problems either in one
+       pair of persistent launches (interior candidates, then boundary candidates) per value
+       type x ball x kernel type present, whose warps take work items (a run of outer
+       triangles of one problem) from a global counter, or as each problem's own kernels
+       over several streams (the autotuner's choice, below);
      - scatters all problems in one launch per value type;
      - captures the numeric phase + scatter of the whole batch in a CUDA graph that
        nl_batch_run replays (re-assembly of the values on unchanged meshes).
-   The work-item size and order and the resident blocks per SM of the persistent launches
-   are picked by a built-in autotuner: the first batch of a given shape (sizes, candidate
-   counts, balls, rules, precisions) times eight schedules of the numeric phase (outer
-   triangles per item 1 or 4, problems in input order or costliest first, blocks per SM at
-   the occupancy limit or one fewer), each the median of three runs, and keeps the fastest
-   in the context; later batches of the same shape reuse it.  Every schedule yields the same pair blocks: each outer
+   The schedule of the numeric phase is picked by a built-in autotuner: the first batch of a
+   given shape (sizes, candidate counts, balls, rules, precisions) times seven schedules,
+   each the median of three runs, and keeps the fastest in the context; later batches of the
+   same shape reuse it.  Candidates: the persistent launches with 1 or 4 outer triangles per
+   work item and the problems in input order or costliest first, or one resident block per SM
+   fewer; or each problem's own kernels (those of nl_assemble_numeric, every kernel of a
+   problem on one stream) with the problems dealt, costliest first, to 4 or 8 streams, so that
+   small problems and the tails of large ones overlap (nl_batch_info.mode).  Every schedule yields the same pair blocks: each outer
    triangle's blocks are produced by one warp in a fixed order (the per-triangle sums
    taken with FP64 atomics, like the scatter's, may differ in the last bits). */
 typedef struct nl_batch nl_batch;
 
-enum { NL_BATCH_NO_TUNE = 1 };   /* nl_batch_create flag: default schedule, no timing runs */
+enum { NL_BATCH_NO_TUNE = 1,       /* nl_batch_create flag: default schedule (persistent launches), no timing runs */
+       NL_BATCH_PER_PROBLEM = 2    /* nl_batch_create flag: each problem's own kernels over all eight side
+                                      streams, costliest first (schedule mode 1), no timing runs */
+};
 enum { NL_SCHED_DEFAULT = 0, NL_SCHED_TUNED = 1, NL_SCHED_CACHED = 2 };
 
 typedef struct {
@@ -193,6 +198,11 @@ typedef struct {
     int32_t n_tried;      /* schedules timed by the autotuner in this nl_batch_create */
     double tuned_ms;      /* numeric phase of the batch with the chosen schedule (NL_SCHED_TUNED; median of 3) */
     double default_ms;    /* the same with the default schedule (NL_SCHED_TUNED; median of 3) */
+    int32_t mode;         /* 0: persistent launches over all problems (chunk, order, blocks apply);
+                             1: each problem's own kernels, as nl_assemble_numeric runs them, the
+                             problems dealt to `streams` streams (costliest first with order 1);
+                             nl_batch_run then also scatters each problem on its stream */
+    int32_t streams;      /* mode 1: streams the problems are dealt to */
 } nl_batch_info;
 
 /* Assemble problems i = 0..n-1 (meshes[i], cfgs[i]) into outs[i] (library-owned, freed

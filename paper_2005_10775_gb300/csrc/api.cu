@@ -8,8 +8,6 @@
 
 #include "numeric.cuh"
 
-nl_status nl_launch_numeric_f64(nl_ctx *ctx, const nlq::NumArgs &A, int ball);
-nl_status nl_launch_numeric_f32(nl_ctx *ctx, const nlq::NumArgs &A, int ball);
 
 // ---------------------------------------------------------------------------
 // errors and staging
@@ -341,12 +339,12 @@ nl_status nl_alloc_numeric(nl_ctx *ctx, nl_plan *P)
 
 namespace {
 
-nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats)
+nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats, bool one_stream = false)
 {
     nlq::NumArgs A;
     nl_status s = nl_fill_args(ctx, P, A, stats);
     if (s != NL_OK) return s;
-    if (P->cfg.prec == NL_PREC_FP64) return nl_launch_numeric_f64(ctx, A, P->cfg.ball);
+    if (P->cfg.prec == NL_PREC_FP64) return nl_launch_numeric_f64(ctx, A, P->cfg.ball, one_stream);
     if (!P->defer) {
         const int cap = nl_defer_cap(P->E);
         nlq::DeferItem *q = nullptr;
@@ -378,10 +376,12 @@ nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats)
             A.otab = (nlq::OuterPt *)P->otab;
         }
     }
-    return nl_launch_numeric_f32(ctx, A, P->cfg.ball);
+    return nl_launch_numeric_f32(ctx, A, P->cfg.ball, one_stream);
 }
 
 }  // namespace
+
+nl_status nl_run_numeric_one_stream(nl_ctx *ctx, nl_plan *P) { return run_numeric(ctx, P, false, true); }
 
 void nl_plan_free(nl_plan *P, cudaStream_t s)
 {

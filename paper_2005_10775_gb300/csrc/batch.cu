@@ -40,9 +40,12 @@ __global__ void k_zero_mbb_batch(const nlq::NumArgs *__restrict__ As)
 }
 
 struct Sched {
-    int chunk = 1;
-    int order = 0;
-    int fewer = 0;   // resident blocks per SM below the occupancy limit, for every persistent launch
+    int mode = 0;    // 0: persistent launches over all problems; 1: each problem's own kernels, the
+                     // problems spread over `streams` of the context's side streams
+    int chunk = 1;   // mode 0: outer triangles per work item
+    int order = 0;   // problems in input order (0) or costliest first (1)
+    int fewer = 0;   // mode 0: resident blocks per SM below the occupancy limit, every persistent launch
+    int streams = 0; // mode 1: side streams
 };
 
 // Host arrays that feed a cudaMemcpyAsync stay alive until the stream has passed the
@@ -232,8 +235,54 @@ nl_status build_items(nl_ctx *ctx, nl_batch *b, const Sched &sc)
     return NL_OK;
 }
 
+// problems in the order of schedule sc
+std::vector<int> problem_order(const nl_batch *b, const Sched &sc)
+{
+    std::vector<int> order(b->n);
+    for (int i = 0; i < b->n; i++) order[i] = i;
+    if (sc.order == 1)
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return triangle_cost(b->P[x]) > triangle_cost(b->P[y]);
+        });
+    return order;
+}
+
+// Schedule mode 1: each problem's numeric phase as nl_assemble_numeric runs it (its kernels on
+// one stream), the problems dealt round-robin to `streams` side streams that start after the
+// context's stream's earlier work and that the context's stream waits for, so that small
+// problems and the tails of large ones overlap.
+nl_status launch_numeric_streams(nl_ctx *ctx, nl_batch *b, const Sched &sc, bool scatter)
+{
+    nl_status s = nl_side_streams(ctx);
+    if (s != NL_OK) return s;
+    const int ns = std::max(1, std::min(sc.streams, (int)nl_ctx::kSideStreams));
+    cudaStream_t st = ctx->stream;
+    NL_CK(cudaEventRecord(ctx->side_ev[nl_ctx::kSideStreams], st));
+    for (int k = 0; k < ns; k++) NL_CK(cudaStreamWaitEvent(ctx->side[k], ctx->side_ev[nl_ctx::kSideStreams], 0));
+    const std::vector<int> order = problem_order(b, sc);
+    for (int j = 0; j < b->n && s == NL_OK; j++) {
+        ctx->stream = ctx->side[j % ns];
+        s = nl_run_numeric_one_stream(ctx, b->P[order[j]]);
+        // the re-assembly: each problem's scatter right after its numeric phase, on its stream
+        if (s == NL_OK && scatter) s = nl_run_scatter(ctx, b->P[order[j]], b->out[order[j]]);
+    }
+    ctx->stream = st;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < ns; k++) {
+        cudaError_t e1 = cudaEventRecord(ctx->side_ev[k], ctx->side[k]);
+        if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(st, ctx->side_ev[k], 0);
+        if (e1 != cudaSuccess) {
+            cudaStreamSynchronize(ctx->side[k]);
+            if (e == cudaSuccess) e = e1;
+        }
+    }
+    if (s == NL_OK && e != cudaSuccess) return nl_cuda_fail(ctx, e, "joining the side streams");
+    return s;
+}
+
 nl_status launch_numeric(nl_ctx *ctx, nl_batch *b, bool set_attr)
 {
+    if (b->sched.mode == 1) return launch_numeric_streams(ctx, b, b->sched, false);
     const size_t nl = b->launches.size();
     NL_CK(cudaMemsetAsync(b->counters, 0, sizeof(int) * 2 * nl, ctx->stream));
     // the per-triangle M_bb sums start at zero in every numeric run (the autotuner's too)
@@ -279,6 +328,7 @@ nl_status time_numeric(nl_ctx *ctx, nl_batch *b, const Sched &sc, int nsm, int r
     nl_status s = build_items(ctx, b, sc);
     if (s != NL_OK) return s;
     apply_grid(b, sc, nsm);
+    b->sched = sc;
     if (!b->tev[0]) NL_CK(cudaEventCreate(&b->tev[0]));
     if (!b->tev[1]) NL_CK(cudaEventCreate(&b->tev[1]));
     std::vector<double> t;
@@ -302,6 +352,12 @@ nl_status pick_schedule(nl_ctx *ctx, nl_batch *b, int flags, int nsm)
     Sched def;   // one outer triangle per item, input order
     b->info.source = NL_SCHED_DEFAULT;
     b->sched = def;
+    if (flags & NL_BATCH_PER_PROBLEM) {   // each problem's own kernels, costliest first, all side streams
+        b->sched.mode = 1;
+        b->sched.order = 1;
+        b->sched.streams = nl_ctx::kSideStreams;
+        return NL_OK;
+    }
     if (flags & NL_BATCH_NO_TUNE) return NL_OK;
     if (!ctx->tune) ctx->tune = new (std::nothrow) nl_tune_cache();
     if (!ctx->tune) return nl_fail(ctx, NL_ENOMEM, "host allocation failed");
@@ -318,25 +374,40 @@ nl_status pick_schedule(nl_ctx *ctx, nl_batch *b, int flags, int nsm)
     double ms = 0.0;
     nl_status s = time_numeric(ctx, b, def, nsm, 1, &ms);
     if (s != NL_OK) return s;
-    const int chunks[2] = {1, 4};
+    std::vector<Sched> cands;
+    for (int order = 0; order < 2; order++)
+        for (int c : {1, 4}) {
+            Sched sc;
+            sc.chunk = c;
+            sc.order = order;
+            cands.push_back(sc);
+        }
+    {
+        Sched sc;   // one resident block per SM fewer
+        sc.order = 1;
+        sc.fewer = 1;
+        cands.push_back(sc);
+    }
+    for (int ns : {4, 8}) {   // each problem's own kernels over ns streams, costliest first
+        Sched sc;
+        sc.mode = 1;
+        sc.order = 1;
+        sc.streams = ns;
+        cands.push_back(sc);
+    }
     double best = INFINITY;
     Sched bs = def;
     int tried = 0;
-    for (int fewer = 0; fewer < 2; fewer++)
-        for (int order = 0; order < 2; order++)
-            for (int c : chunks) {
-                Sched sc;
-                sc.chunk = c;
-                sc.order = order;
-                sc.fewer = fewer;
-                if ((s = time_numeric(ctx, b, sc, nsm, 3, &ms)) != NL_OK) return s;
-                tried++;
-                if (c == def.chunk && order == def.order && fewer == def.fewer) b->info.default_ms = ms;
-                if (ms < best) {
-                    best = ms;
-                    bs = sc;
-                }
-            }
+    for (const Sched &sc : cands) {
+        if ((s = time_numeric(ctx, b, sc, nsm, 3, &ms)) != NL_OK) return s;
+        tried++;
+        if (sc.mode == def.mode && sc.chunk == def.chunk && sc.order == def.order && sc.fewer == def.fewer)
+            b->info.default_ms = ms;
+        if (ms < best) {
+            best = ms;
+            bs = sc;
+        }
+    }
     b->sched = bs;
     b->info.source = NL_SCHED_TUNED;
     b->info.n_tried = tried;
@@ -561,6 +632,8 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
     if ((s = pick_schedule(ctx, b, flags, nsm)) != NL_OK) return fail(s);
     b->info.chunk = b->sched.chunk;
     b->info.order = b->sched.order;
+    b->info.mode = b->sched.mode;
+    b->info.streams = b->sched.streams;
     if ((s = build_items(ctx, b, b->sched)) != NL_OK) return fail(s);
     apply_grid(b, b->sched, nsm);
     for (const Launch &l : b->launches)
@@ -655,8 +728,14 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return fail(nl_cuda_fail(ctx, e, "cudaStreamBeginCapture"));
         const int64_t l0 = ctx->launches;
-        nl_status s1 = launch_numeric(ctx, b, false);
-        nl_status s2 = s1 == NL_OK ? launch_scatter(ctx, b, false) : s1;
+        nl_status s1, s2;
+        if (b->sched.mode == 1) {   // each problem's numeric phase and scatter on its stream
+            s1 = launch_numeric_streams(ctx, b, b->sched, true);
+            s2 = s1;
+        } else {
+            s1 = launch_numeric(ctx, b, false);
+            s2 = s1 == NL_OK ? launch_scatter(ctx, b, false) : s1;
+        }
         // captured, not launched: nl_batch_run counts them per replay
         b->graph_kernels = ctx->launches - l0;
         ctx->launches = l0;

@@ -237,6 +237,9 @@ nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_
 nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl_host_slot *h);
 
 nl_status nl_alloc_numeric(nl_ctx *ctx, nl_plan *P);
+// numeric phase of one assembled problem with every kernel on ctx->stream (api.cu): the first
+// call allocates the problem's FP64-item and near-field queues
+nl_status nl_run_numeric_one_stream(nl_ctx *ctx, nl_plan *P);
 nl_status nl_run_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out);
 
 // ---- batched scatter (pattern.cu): the scatter of every problem of a batch ----

@@ -1822,6 +1822,11 @@ nl_status nl_launch_interior_batch_f32(nl_ctx *ctx, const nlq::NumArgs *dA, cons
                                        int n_items, int *counter, int blocks);
 nl_status nl_launch_interior_batch_f64(nl_ctx *ctx, const nlq::NumArgs *dA, const nlq::BatchItem *items,
                                        int n_items, int *counter, int blocks);
+// single-problem numeric phase (numeric_f32/f64.cu); one_stream: every kernel on the context's
+// stream (else the interior kernel runs on side stream 0, concurrently with the boundary kernel)
+nl_status nl_launch_numeric_f64(nl_ctx *ctx, const nlq::NumArgs &A, int ball, bool one_stream = false);
+nl_status nl_launch_numeric_f32(nl_ctx *ctx, const nlq::NumArgs &A, int ball, bool one_stream = false);
+
 nl_status nl_launch_boundary_batch_f32(nl_ctx *ctx, int ball, bool inv, const nlq::NumArgs *dA,
                                        const nlq::BatchItem *items, int n_items, int *counter, int blocks,
                                        bool set_attr);
@@ -1841,7 +1846,8 @@ nl_status nl_batch_occupancy_f64(nl_ctx *ctx, int ball, bool inv, int *per_sm);
 // the context's stream and then k_interior on side stream 0 (both add their per-triangle values
 // atomically), so that the interior kernel's blocks fill the boundary kernel's last wave; the
 // context's stream waits for side stream 0 before anything that follows.
-inline nl_status nl_numeric_fork(nl_ctx *ctx, const nlq::NumArgs &A)
+// the per-triangle outputs the numeric kernels add onto, zeroed on the context's stream
+inline nl_status nl_numeric_zero(nl_ctx *ctx, const nlq::NumArgs &A)
 {
     cudaStream_t st = ctx->stream;
     const size_t K = (size_t)A.K;
@@ -1850,11 +1856,30 @@ inline nl_status nl_numeric_fork(nl_ctx *ctx, const nlq::NumArgs &A)
     NL_CK(cudaMemsetAsync(A.cnt_a, 0, sizeof(int64_t) * K, st));
     NL_CK(cudaMemsetAsync(A.hash_a, 0, sizeof(uint64_t) * K, st));
     NL_CK(cudaMemsetAsync(A.mbb, 0, sizeof(double) * 6 * K, st));
-    nl_status s = nl_side_streams(ctx);
+    return NL_OK;
+}
+
+inline nl_status nl_numeric_fork(nl_ctx *ctx, const nlq::NumArgs &A)
+{
+    cudaStream_t st = ctx->stream;
+    nl_status s = nl_numeric_zero(ctx, A);
+    if (s != NL_OK) return s;
+    s = nl_side_streams(ctx);
     if (s != NL_OK) return s;
     NL_CK(cudaEventRecord(ctx->side_ev[nl_ctx::kSideStreams], st));
     NL_CK(cudaStreamWaitEvent(ctx->side[0], ctx->side_ev[nl_ctx::kSideStreams], 0));
     return NL_OK;
+}
+
+// the interior kernel on the context's stream after the boundary kernel (no fork: the whole
+// numeric phase of one problem on one stream, so that several problems can run side by side)
+template <typename T>
+nl_status nl_numeric_interior_same(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads, nl_status s)
+{
+    if (s != NL_OK) return s;
+    nlq::k_interior<T><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? NL_OK : nl_cuda_fail(ctx, e, "k_interior launch");
 }
 
 // the interior kernel on side stream 0, then the join (always, so that nothing on the side

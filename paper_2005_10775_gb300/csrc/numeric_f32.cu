@@ -86,15 +86,16 @@ nl_status nl_deferred_blocks(nl_ctx *ctx, int *blocks)
     return NL_OK;
 }
 
-nl_status nl_launch_numeric_f32(nl_ctx *ctx, const nlq::NumArgs &A, int ball)
+nl_status nl_launch_numeric_f32(nl_ctx *ctx, const nlq::NumArgs &A, int ball, bool one_stream)
 {
     const unsigned grid = (unsigned)((A.K + nlq::kWarpsPerBlock - 1) / nlq::kWarpsPerBlock);
     const unsigned threads = nlq::kWarpsPerBlock * 32;
-    nl_status s = nl_numeric_fork(ctx, A);
+    nl_status s = one_stream ? nl_numeric_zero(ctx, A) : nl_numeric_fork(ctx, A);
     if (s != NL_OK) return s;
     // the boundary kernel first, so that its blocks are dispatched before the interior kernel's
     s = launch_ball(ctx, A, ball, grid, threads, 0);
-    s = nl_numeric_interior_join<float>(ctx, A, grid, threads, s);
+    s = one_stream ? nl_numeric_interior_same<float>(ctx, A, grid, threads, s)
+                   : nl_numeric_interior_join<float>(ctx, A, grid, threads, s);
     if (s != NL_OK) return s;
     return launch_ball(ctx, A, ball, grid, threads, 1);
 }

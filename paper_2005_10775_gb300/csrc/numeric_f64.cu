@@ -38,13 +38,14 @@ nl_status launch_ball(nl_ctx *ctx, const nlq::NumArgs &A, int ball, unsigned gri
 
 }  // namespace
 
-nl_status nl_launch_numeric_f64(nl_ctx *ctx, const nlq::NumArgs &A, int ball)
+nl_status nl_launch_numeric_f64(nl_ctx *ctx, const nlq::NumArgs &A, int ball, bool one_stream)
 {
     const unsigned grid = (unsigned)((A.K + nlq::kWarpsPerBlock - 1) / nlq::kWarpsPerBlock);
     const unsigned threads = nlq::kWarpsPerBlock * 32;
-    nl_status s = nl_numeric_fork(ctx, A);
+    nl_status s = one_stream ? nl_numeric_zero(ctx, A) : nl_numeric_fork(ctx, A);
     if (s != NL_OK) return s;
     // the boundary kernel first, so that its blocks are dispatched before the interior kernel's
     s = launch_ball(ctx, A, ball, grid, threads);
-    return nl_numeric_interior_join<double>(ctx, A, grid, threads, s);
+    return one_stream ? nl_numeric_interior_same<double>(ctx, A, grid, threads, s)
+                      : nl_numeric_interior_join<double>(ctx, A, grid, threads, s);
 }

@@ -289,6 +289,36 @@ nl_status ensure_f32(nl_ctx *ctx, nl_csr *A)
 
 unsigned wgrid(int64_t rows) { return (unsigned)((rows * 32 + 255) / 256); }
 
+// A CUDA graph of a fixed sequence of kernel launches on one stream, captured once and replayed
+// (released with its holder).  A capture the runtime refuses (the stream already capturing, a
+// launch error) leaves `failed` set and the caller launches the kernels itself.
+struct ChunkGraph {
+    cudaGraphExec_t exec = nullptr;
+    bool failed = false;
+    template <class Launches>
+    void capture(cudaStream_t st, Launches launches)
+    {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            failed = true;
+            return;
+        }
+        launches();
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+        if (g) cudaGraphDestroy(g);
+        if (!exec) {
+            cudaGetLastError();
+            failed = true;
+        }
+    }
+    ~ChunkGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
+
 nl_status extract_body(nl_ctx *ctx, const nl_csr *D, const nl_mesh *mesh, nl_csr *A, nl_csr *B)
 {
     nl_temps tmp(ctx->stream);
@@ -508,6 +538,7 @@ nl_status nl_cg(nl_ctx *ctx, const nl_csr *Ac, const double *b, double *x, doubl
     const int kCheck = 8;          // inner iterations between host convergence checks
     const double kInnerTol = 1e-5; // inner relative reduction per refinement step
     const int kPasses = 64;        // FP64 refinement passes
+    ChunkGraph graph;              // the captured inner chunk (released with the call)
     for (int outer = 0; outer < kPasses && !stop; outer++) {
         NL_CK(cudaMemsetAsync(acc, 0, sizeof(double) * 2, ctx->stream));
         k_residual<<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, A->val, xd, (const double *)bd, r,
@@ -532,12 +563,28 @@ nl_status nl_cg(nl_ctx *ctx, const nl_csr *Ac, const double *b, double *x, doubl
         k_cg_init<<<eg, 256, 0, ctx->stream>>>(n, r, 1.0 / rn, z, p, d, sc); ++ctx->launches;
         while (total < max_it) {
             const int chunk = (max_it - total) < kCheck ? (max_it - total) : kCheck;
-            for (int c = 0; c < chunk; c++) {
-                k_cg_spmv<<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, v32, p, q, sc);
-                ++ctx->launches;
-                k_cg_update<<<eg, 256, 0, ctx->stream>>>(n, p, q, d, z, sc); ++ctx->launches;
-                k_cg_dir<<<eg, 256, 0, ctx->stream>>>(n, z, p, sc); ++ctx->launches;
-                k_cg_shift<<<1, 1, 0, ctx->stream>>>(sc); ++ctx->launches;
+            auto iterate = [&](int count) {
+                for (int c = 0; c < count; c++) {
+                    k_cg_spmv<<<wgrid(n), 256, 0, ctx->stream>>>(n, A->row_ptr, A->col_idx, v32, p, q, sc);
+                    k_cg_update<<<eg, 256, 0, ctx->stream>>>(n, p, q, d, z, sc);
+                    k_cg_dir<<<eg, 256, 0, ctx->stream>>>(n, z, p, sc);
+                    k_cg_shift<<<1, 1, 0, ctx->stream>>>(sc);
+                }
+                ctx->launches += 4 * count;
+            };
+            // a full chunk is one launch of a graph of its 4 x kCheck kernels (captured at the first
+            // full chunk of the call: its buffers are the call's own), which removes most of the
+            // launch gaps between these short kernels; a capture that fails falls back to launches
+            if (chunk == kCheck && !graph.exec && !graph.failed) {
+                const int64_t l0 = ctx->launches;   // captured, not launched
+                graph.capture(ctx->stream, [&] { iterate(kCheck); });
+                ctx->launches = l0;
+            }
+            if (chunk == kCheck && graph.exec) {
+                NL_CK(cudaGraphLaunch(graph.exec, ctx->stream));
+                ctx->launches += 4 * kCheck;
+            } else {
+                iterate(chunk);
             }
             NL_CK(cudaGetLastError());
             total += chunk;

@@ -52,10 +52,12 @@ class nl_csr(ctypes.Structure):
 class nl_batch_info(ctypes.Structure):
     _fields_ = [("chunk", ctypes.c_int32), ("order", ctypes.c_int32), ("blocks", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("source", ctypes.c_int32), ("n_tried", ctypes.c_int32),
-                ("tuned_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+                ("tuned_ms", ctypes.c_double), ("default_ms", ctypes.c_double),
+                ("mode", ctypes.c_int32), ("streams", ctypes.c_int32)]
 
 
 NL_BATCH_NO_TUNE = 1
+NL_BATCH_PER_PROBLEM = 2
 SCHED_SOURCES = {0: "default", 1: "tuned", 2: "cached"}
 
 

@@ -54,6 +54,7 @@ int main(void) {
     P(nl_mesh, elem_in_omega) P(nl_config, ngon_offsets) P(nl_config, cap_printed) P(nl_config, shifted)
     P(nl_config, prec) P(nl_csr, val) P(nl_csr, priv) P(nl_csr, n_qp_pairs)
     P(nl_batch_info, source) P(nl_batch_info, tuned_ms) P(nl_batch_info, default_ms)
+    P(nl_batch_info, mode) P(nl_batch_info, streams)
     return 0;
 }
 """)

@@ -121,12 +121,15 @@ def test_batch_schedule_info_and_cache(nl, ctx, mixed):
     assert info["source"] in ("tuned", "cached")
     assert info["launches"] == 9 and info["blocks"] > 0
     assert info["chunk"] in (1, 2, 4, 8) and info["order"] in (0, 1)
+    assert info["mode"] in (0, 1) and (info["mode"] == 0 or info["streams"] in (4, 8))
+    assert info["n_tried"] in (0, 7)
     # the same batch shape again: the schedule comes from the context's cache
     h2, outs2 = nl.nl_batch_create(ctx, mixed["meshes"], mixed["cfgs"])
     try:
         info2 = nl.nl_batch_get_info(h2)
         assert info2["source"] == "cached"
-        assert (info2["chunk"], info2["order"]) == (info["chunk"], info["order"])
+        assert (info2["chunk"], info2["order"], info2["mode"], info2["streams"]) == \
+            (info["chunk"], info["order"], info["mode"], info["streams"])
     finally:
         nl.nl_batch_destroy(ctx, h2)
         for o in outs2:
@@ -187,3 +190,30 @@ def test_batch_workload_sampled_against_oracle(nl, ctx):
         nl.nl_batch_destroy(ctx, h)
         for o in outs:
             nl.nl_csr_free(ctx, o)
+
+
+@pytest.mark.parametrize("flags", ["per_problem", "no_tune"])
+def test_batch_each_schedule_family(nl, ctx, mixed, flags):
+    # both schedule families, forced: persistent launches over all problems (NL_BATCH_NO_TUNE)
+    # and each problem's own kernels over the side streams (NL_BATCH_PER_PROBLEM): the same
+    # values as the tuned batch, and a graph replay (numeric phase and scatter) that repeats them
+    f = nl.NL_BATCH_PER_PROBLEM if flags == "per_problem" else nl.NL_BATCH_NO_TUNE
+    h, outs = nl.nl_batch_create(ctx, mixed["meshes"], mixed["cfgs"], flags=f)
+    try:
+        info = nl.nl_batch_get_info(h)
+        assert info["mode"] == (1 if flags == "per_problem" else 0) and info["source"] == "default"
+        ref = [nl.to_scipy(ctx, o) for o in mixed["outs"]]
+        got = [nl.to_scipy(ctx, o) for o in outs]
+        nl.nl_batch_run(ctx, h)
+        again = [nl.to_scipy(ctx, o) for o in outs]
+        for r, g, a, (_, prec) in zip(ref, got, again, mixed["probs"]):
+            np.testing.assert_array_equal(g.indptr, r.indptr)
+            np.testing.assert_array_equal(g.indices, r.indices)
+            scale = np.abs(r.data).max()
+            assert np.abs(g.data - r.data).max() <= TOL[prec] * scale
+            assert np.abs(a.data - g.data).max() <= (1e-14 if prec == "fp64" else 1e-6) * scale
+    finally:
+        nl.nl_batch_destroy(ctx, h)
+        for o in outs:
+            nl.nl_csr_free(ctx, o)
+
