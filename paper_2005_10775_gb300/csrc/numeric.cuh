@@ -248,13 +248,15 @@ __device__ __forceinline__ void rule_pt(const NumArgs &A, int r, T &p0, T &p1, T
     }
 }
 
-// inner sums over the whole triangle T_b: phi_b at the rule points are the rule's barycentrics
-template <typename T>
+// inner sums over the whole triangle T_b: phi_b at the rule points are the rule's barycentrics.
+// KIN: the kernel type when the caller knows it at compile time (0 constant, 1 c/|x - y|), else
+// -1 (read from A.kernel)
+template <typename T, int KIN = -1>
 __device__ __forceinline__ void whole_sums(const NumArgs &A, const D2 V[3], T area_kc, D2 x, Sums<T> &S,
                                            int64_t &nqp, const nlg::F2 *dl = nullptr)
 {
     sums_zero(S);
-    const bool inv = (A.kernel == NL_KERNEL_INV_DIST);
+    const bool inv = KIN < 0 ? (A.kernel == NL_KERNEL_INV_DIST) : (KIN == 1);
     const int n = A.inner.n;
     T ar = area_kc;
     // Every (x_q, T_b) evaluates its inner points: for a constant kernel on a whole T_b
@@ -373,7 +375,9 @@ __device__ __forceinline__ void inner_sums(const NumArgs &A, const nlg::Region &
     }
 }
 
-// inner sums over a fanned polygon given in FP32 coordinates relative to x (FP32 path)
+// inner sums over a fanned polygon given in FP32 coordinates relative to x (FP32 path; KIN as
+// for whole_sums)
+template <int KIN = -1>
 __device__ __forceinline__ void poly_sums_f32(const NumArgs &A, const nlg::F2 *P, int n, const nlg::F2 &d0,
                                               const nlg::F2 &e1, const nlg::F2 &e2, float inv_det,
                                               Sums<float> &S, int64_t &nqp)
@@ -404,7 +408,7 @@ __device__ __forceinline__ void poly_sums_f32(const NumArgs &A, const nlg::F2 *P
             const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
             const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
             float w = f.w * ar;
-            if (A.kernel == NL_KERNEL_INV_DIST) {   // psi = c / |y - x|, coordinates relative to x
+            if (KIN < 0 ? A.kernel == NL_KERNEL_INV_DIST : KIN == 1) {   // psi = c / |y - x|, relative to x
                 const float yx = m0 * s0.x + m1 * s1.x + m2 * s2.x, yy = m0 * s0.y + m1 * s1.y + m2 * s2.y;
                 w *= rsqrtf(yx * yx + yy * yy);
             }
@@ -415,7 +419,8 @@ __device__ __forceinline__ void poly_sums_f32(const NumArgs &A, const nlg::F2 *P
     }
 }
 
-// inner sums over a fanned polygon held in a shared clip buffer (FP32 path)
+// inner sums over a fanned polygon held in a shared clip buffer (FP32 path; KIN as for whole_sums)
+template <int KIN = -1>
 __device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBuf &cb, int which, int lane, int n,
                                              const nlg::F2 &d0, const nlg::F2 &e1, const nlg::F2 &e2, float inv_det,
                                              Sums<float> &S, int64_t &nqp)
@@ -448,7 +453,7 @@ __device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBu
             const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
             const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
             float w = f.w * ar;
-            if (A.kernel == NL_KERNEL_INV_DIST) {   // psi = c / |y - x|, coordinates relative to x
+            if (KIN < 0 ? A.kernel == NL_KERNEL_INV_DIST : KIN == 1) {   // psi = c / |y - x|, relative to x
                 const float yx = m0 * x0 + m1 * xk + m2 * xn, yy = m0 * y0 + m1 * yk + m2 * yn;
                 w *= rsqrtf(yx * yx + yy * yy);
             }
@@ -691,6 +696,15 @@ __device__ __forceinline__ void warp_reduce(LaneAcc &acc)
     }
 }
 
+// whether the kernel accumulates the interaction statistics' record hashes: STS < 0 reads
+// A.stats at run time; 0 / 1 fix it at compile time (the assembly's kernels leave the hash code
+// out of their loops)
+template <int STS>
+__device__ __forceinline__ bool want_stats(const NumArgs &A)
+{
+    return STS < 0 ? A.stats != 0 : STS == 1;
+}
+
 // ---------------------------------------------------------------------------
 // Interior pairs: T_b is whole for every outer point of T_a (certified when the
 // candidate lists are built), so there is no per-point classification.  k_interior runs
@@ -698,7 +712,7 @@ __device__ __forceinline__ void warp_reduce(LaneAcc &acc)
 // per-triangle M_aa and statistics atomically onto zeroed outputs; the batched kernels run
 // one after the other and store, then add.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int STS = -1>
 __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const OuterPt *sq, int lane, LaneAcc &acc)
 {
     const int K = A.K;
@@ -737,12 +751,12 @@ __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const Ou
             acc.qp += nq;
             if (!A.outer_support) {
                 acc.cnt++;
-                if (A.stats) acc.hsum += nlg::record_hash(a, b, q - q0, nlg::KIND_WHOLE, 3, 0);
+                if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, b, q - q0, nlg::KIND_WHOLE, 3, 0);
             }
         }
         if (A.outer_support && q1 > q0) {   // one record per pair: the support is all of T_a
             acc.cnt++;
-            if (A.stats) acc.hsum += nlg::record_hash(a, b, 0, nlg::KIND_WHOLE, 3, 0);
+            if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, b, 0, nlg::KIND_WHOLE, 3, 0);
         }
         write_pair<T>(A, e, b, q1 > q0, v, acc);
     }
@@ -754,6 +768,7 @@ __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const Ou
 // onto zero give the same sum in either order, so the result does not depend on the schedule.
 enum FinishMode { kStore, kAdd, kAtomicAdd };
 
+template <int STS = -1>
 __device__ __forceinline__ void finish_outer(const NumArgs &A, int a, LaneAcc &acc, int lane, FinishMode mode)
 {
     warp_reduce(acc);
@@ -763,23 +778,23 @@ __device__ __forceinline__ void finish_outer(const NumArgs &A, int a, LaneAcc &a
             for (int i = 0; i < 6; i++) atomicAdd(&A.maa[(int64_t)i * K + a], acc.maa[i]);
             atomicAdd((unsigned long long *)&A.qp_a[a], (unsigned long long)acc.qp);
             atomicAdd((unsigned long long *)&A.cnt_a[a], (unsigned long long)acc.cnt);
-            if (A.stats) atomicAdd((unsigned long long *)&A.hash_a[a], (unsigned long long)acc.hsum);
+            if (want_stats<STS>(A)) atomicAdd((unsigned long long *)&A.hash_a[a], (unsigned long long)acc.hsum);
         } else if (mode == kAdd) {
             for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] += acc.maa[i];
             A.qp_a[a] += acc.qp;
             A.cnt_a[a] += acc.cnt;
-            if (A.stats) A.hash_a[a] += acc.hsum;
+            if (want_stats<STS>(A)) A.hash_a[a] += acc.hsum;
         } else {
             for (int i = 0; i < 6; i++) A.maa[(int64_t)i * K + a] = acc.maa[i];
             A.qp_a[a] = acc.qp;
             A.cnt_a[a] = acc.cnt;
-            if (A.stats) A.hash_a[a] = acc.hsum;
+            if (want_stats<STS>(A)) A.hash_a[a] = acc.hsum;
         }
     }
 }
 
 // five resident 4-warp blocks per SM with float sums (96 registers); double sums unconstrained
-template <typename T>
+template <typename T, int STS = -1>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float) ? 5 : 1) k_interior(const NumArgs A)
 {
     __shared__ OuterPt sq_all[kWarpsPerBlock][NL_MAXQ + 8];
@@ -791,8 +806,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float
     __syncwarp();
     LaneAcc acc;
     acc_zero(acc);
-    interior_outer<T>(A, a, sq, lane, acc);
-    finish_outer(A, a, acc, lane, kAtomicAdd);
+    interior_outer<T, STS>(A, a, sq, lane, acc);
+    finish_outer<STS>(A, a, acc, lane, kAtomicAdd);
 }
 
 // ---------------------------------------------------------------------------
@@ -950,10 +965,10 @@ __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &
             ncap = 0;
             if (!cut) {
                 const D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};   // unused: FP32 coordinates dl
-                whole_sums<T>(A, Vb, cand_akc<T>(A, c), D2{o.x, o.y}, S, nq, dl);
+                whole_sums<T, INV>(A, Vb, cand_akc<T>(A, c), D2{o.x, o.y}, S, nq, dl);
             } else {
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
-                poly_sums_sh(A, cb, which, lane, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
+                poly_sums_sh<INV>(A, cb, which, lane, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
             }
             return 1;
         }
@@ -974,10 +989,10 @@ __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &
             ncap = 0;
             if (k == nlg::KIND_WHOLE) {
                 const D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};   // unused: FP32 coordinates dl
-                whole_sums<T>(A, Vb, cand_akc<T>(A, c), D2{o.x, o.y}, S, nq, dl);
+                whole_sums<T, INV>(A, Vb, cand_akc<T>(A, c), D2{o.x, o.y}, S, nq, dl);
             } else {
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
-                poly_sums_f32(A, P, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
+                poly_sums_f32<INV>(A, P, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
             }
             return 1;
         }
@@ -1164,7 +1179,7 @@ __device__ __forceinline__ void near_flush(const NumArgs &A, int a, int64_t base
 
 // The boundary candidates of outer triangle a (outer points staged in sh.sq).
 // INV: the kernel is psi = c/|x - y| (near-field split), else the constant kernel.
-template <int BALL, typename T, bool INV, bool NQ = false>
+template <int BALL, typename T, bool INV, bool NQ = false, int STS = -1>
 __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, BoundaryShared<T> &sh, int lane,
                                                LaneAcc &acc)
 {
@@ -1262,7 +1277,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             nlg::F2 dl[3];
             if (INV)
                 for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
-            whole_sums<T>(A, Vb, cand_akc<T>(A, cd), D2{o.x, o.y}, S, nq, INV ? dl : nullptr);
+            whole_sums<T, INV>(A, Vb, cand_akc<T>(A, cd), D2{o.x, o.y}, S, nq, INV ? dl : nullptr);
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
@@ -1277,7 +1292,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             sh.acc[21][own] = (T)1;
             acc.cnt++;
             acc.qp += nq;
-            if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
+            if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
         }
         __syncwarp();
         if (kCopies && nwhole > 32)
@@ -1307,7 +1322,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             warp_owner_add<T, kLaneMaa ? 15 : 21>(sh.acc, own, lane, w, rmask);
             acc.cnt++;
             acc.qp += nq;
-            if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
+            if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
         }
         // phase 2b: undecided items with all lanes.  The loop does not converge the warp between
         // items: lanes at different items run the same parts of the clip together.  So the order
@@ -1342,7 +1357,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             }
             acc.cnt++;
             acc.qp += nq;
-            if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
+            if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
         }
         __syncwarp();
         if (sizeof(T) == sizeof(float) && A.defer) {
@@ -1477,7 +1492,7 @@ __device__ __forceinline__ void support_boundary(const NumArgs &A, int a, int la
 
 // boundary candidates of outer triangle a for the ball mode BALL (NQ: the singular kernel's
 // near-field whole items go to the near-field queue)
-template <int BALL, typename T, bool INV, bool NQ = false>
+template <int BALL, typename T, bool INV, bool NQ = false, int STS = -1>
 __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundaryShared<T> &sh, int lane, LaneAcc &acc)
 {
     if constexpr (BALL == NL_BALL_BARY_NOCAPS || BALL == NL_BALL_BARY_APPROXCAPS) {
@@ -1488,7 +1503,7 @@ __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundarySh
         __syncwarp();
         if (INV && A.otab)   // k_near reads the outer points from here (no FP64 arithmetic per item)
             for (int q = lane; q < A.outer.n; q += 32) A.otab[(int64_t)a * A.outer.n + q] = sh.sq[q];
-        boundary_outer<BALL, T, INV, NQ>(A, a, sh, lane, acc);
+        boundary_outer<BALL, T, INV, NQ, STS>(A, a, sh, lane, acc);
     }
 }
 
@@ -1497,7 +1512,7 @@ __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundarySh
 template <typename T, bool INV>
 constexpr int kBoundaryBlocksPerSm = sizeof(T) == sizeof(float) ? 4 : 3;
 
-template <int BALL, typename T, bool INV, bool NQ = false>
+template <int BALL, typename T, bool INV, bool NQ = false, int STS = -1>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, INV>) k_boundary(const NumArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1507,9 +1522,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBoundaryBlocksPerSm<T, I
     if (a >= A.K) return;
     LaneAcc acc;
     acc_zero(acc);
-    boundary_any<BALL, T, INV, NQ>(A, a, sh, lane, acc);
+    boundary_any<BALL, T, INV, NQ, STS>(A, a, sh, lane, acc);
     // k_interior may be running: add atomically onto the zeroed outputs
-    finish_outer(A, a, acc, lane, kAtomicAdd);
+    finish_outer<STS>(A, a, acc, lane, kAtomicAdd);
 }
 
 // ---------------------------------------------------------------------------
@@ -1769,8 +1784,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_near(const NumArgs A)
 // in order and adds the sum once, so the values repeat exactly from run to run.  The pair's
 // stored value is the boundary kernel's, final when this runs.  args(p): the arguments of
 // problem p.
-template <class Args>
-__device__ __forceinline__ void defer_merge(Args args, const DeferItem *__restrict__ items, const int *count, int cap)
+template <class Add>
+__device__ __forceinline__ void defer_merge(Add add, const DeferItem *__restrict__ items, const int *count, int cap)
 {
     const int n = min(*count, cap);
     const float *dv = defer_values(const_cast<DeferItem *>(items), cap);
@@ -1787,24 +1802,29 @@ __device__ __forceinline__ void defer_merge(Args args, const DeferItem *__restri
             if (r.e != d.e || (r.qp >> 8) != (d.qp >> 8)) break;
             for (int k = 0; k < kDeferVals; k++) sum[k] += dv[(int64_t)k * cap + j];
         }
-        const NumArgs &A = args(d.qp >> 8);
-        float *blk = (float *)A.blk;
-        for (int k = 0; k < kDeferVals; k++) blk[(int64_t)k * A.E + d.e] += sum[k];
+        add(d.qp >> 8, d.e, sum);
     }
+}
+
+// the sum of one pair's run onto the pair's stored M_ab (problem arguments A)
+__device__ __forceinline__ void defer_add(const NumArgs &A, int64_t e, const float *sum)
+{
+    float *blk = (float *)A.blk;
+    for (int k = 0; k < kDeferVals; k++) blk[(int64_t)k * A.E + e] += sum[k];
 }
 
 // (templates on the value type, float: one kernel in every translation unit that launches it)
 template <typename T>
 __global__ void __launch_bounds__(256) k_defer_merge(const NumArgs A)
 {
-    defer_merge([&](int) -> const NumArgs & { return A; }, A.defer, A.defer_n, A.defer_cap);
+    defer_merge([&](int, int64_t e, const float *sum) { defer_add(A, e, sum); }, A.defer, A.defer_n, A.defer_cap);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_defer_merge_batch(const NumArgs *__restrict__ As, const DeferItem *__restrict__ items, const int *count, int cap)
 {
-    defer_merge([&](int p) -> const NumArgs & { return As[p]; }, items, count, cap);
+    defer_merge([&](int p, int64_t e, const float *sum) { defer_add(As[p], e, sum); }, items, count, cap);
 }
 
 }  // namespace nlq
@@ -1873,22 +1893,22 @@ inline nl_status nl_numeric_fork(nl_ctx *ctx, const nlq::NumArgs &A)
 
 // the interior kernel on the context's stream after the boundary kernel (no fork: the whole
 // numeric phase of one problem on one stream, so that several problems can run side by side)
-template <typename T>
+template <typename T, int STS = -1>
 nl_status nl_numeric_interior_same(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads, nl_status s)
 {
     if (s != NL_OK) return s;
-    nlq::k_interior<T><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches;
+    nlq::k_interior<T, STS><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches;
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? NL_OK : nl_cuda_fail(ctx, e, "k_interior launch");
 }
 
 // the interior kernel on side stream 0, then the join (always, so that nothing on the side
 // stream outlives a failure); s: the status of the boundary launch
-template <typename T>
+template <typename T, int STS = -1>
 nl_status nl_numeric_interior_join(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads, nl_status s)
 {
     if (s == NL_OK) {
-        nlq::k_interior<T><<<grid, threads, 0, ctx->side[0]>>>(A); ++ctx->launches;
+        nlq::k_interior<T, STS><<<grid, threads, 0, ctx->side[0]>>>(A); ++ctx->launches;
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = nl_cuda_fail(ctx, e, "k_interior launch");
     }
