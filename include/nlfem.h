@@ -305,8 +305,10 @@ nl_status nl_fma_peak(nl_ctx *ctx, int32_t prec, double *tflops);
 int64_t nl_launch_count(nl_ctx *ctx);
 
 /* Items (x_q, T_b) of the last nl_assemble or nl_interactions on the FP32-compensated
-   path whose region the FP64 geometry built: FP32 choices it could not certify, the
-   singular kernel's near field, balls without an FP32 region.  The boundary kernel
+   path whose region the FP64 geometry built: FP32 choices it could not certify (a vertex,
+   root or orientation too close to its threshold), the singular kernel's near-field items
+   that FP32 cannot decide, and the cut items of the barycenter and overlap balls (their
+   whole / empty choice is certified in FP32, their regions are whole triangles).  The boundary kernel
    queues them and a second kernel integrates the queue with every lane busy; a full
    queue (capacity E/16, at least 4096; NL_DEFER_CAP in the environment overrides it, 0
    disables the queue) leaves the excess to the boundary kernel's own lanes.  Each warp

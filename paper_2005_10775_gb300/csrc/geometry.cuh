@@ -610,8 +610,10 @@ __device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, cons
 // ---------------------------------------------------------------------------
 constexpr int kBallCap = 16;   // FP32 region vertices (nocaps <= 6; approxcaps 6 + 3 (m - 1))
 
-template <int BALL>
-__device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g, F2 P[kBallCap], int *kind)
+// The certified FP32 walk itself: the walk points W (relative to x), their tags (0 vertex, 1
+// entry, 2 exit) and the count of vertices inside; returns the number of walk points (at most 6),
+// or -1 when a choice is not certain.
+__device__ __forceinline__ int ball_walk_f32(const F2 d[3], const GeoParams &g, F2 W[6], int tag[6], int *n_in)
 {
     const float delta = g.deltaf, d2f = delta * delta;
     bool ins[3];
@@ -624,8 +626,6 @@ __device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g
         else return -1;
         nin += ins[i];
     }
-    F2 W[6];
-    int tag[6];   // 0 vertex, 1 entry, 2 exit
     int n = 0;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
@@ -662,6 +662,18 @@ __device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g
             W[n].x = p.x + l2 * ex; W[n].y = p.y + l2 * ey; tag[n] = 2; n++;
         }
     }
+    *n_in = nin;
+    return n;
+}
+
+template <int BALL>
+__device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g, F2 P[kBallCap], int *kind)
+{
+    const float delta = g.deltaf;
+    F2 W[6];
+    int tag[6], nin;
+    const int n = ball_walk_f32(d, g, W, tag, &nin);
+    if (n < 0) return -1;
     if (BALL == NL_BALL_NOCAPS) {
         if (n < 3) return 0;
         for (int i = 0; i < n; i++) P[i] = W[i];
@@ -699,6 +711,56 @@ __device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g
     *kind = (nin == 3 && n == 3) ? KIND_WHOLE : KIND_PARTIAL;
     return m;
 }
+
+// FP32 region of exactcaps (Sec. 5.2, Eq. (areacap)): the certified FP32 walk as for nocaps (a
+// polygon when it has three points or more) and one cap for every exit followed by an entry,
+// each integrated by one point at its centroid with weight its area, as the FP64 cap rule (the
+// area delta^2 (2 th - sin 2 th) / 2, or / 4 with the printed weight, th = asin(chord / 2 delta);
+// the series of 2 th - sin 2 th below 2 th = 0.5, where the difference loses FP32 digits).
+// Coordinates relative to x.  Returns the polygon's vertex count (0 when under three points),
+// -1 when the walk is not certain; *ncap caps in C (centroid) and Cw (area).
+__device__ __forceinline__ int exactcaps_region_f32(const F2 d[3], const GeoParams &g, F2 P[6], F2 C[3], float Cw[3],
+                                                    int *ncap, int *kind)
+{
+    int tag[6], nin;
+    const int n = ball_walk_f32(d, g, P, tag, &nin);
+    *ncap = 0;
+    if (n < 0) return -1;
+    if (n < 2) return 0;
+    const float delta = g.deltaf;
+    for (int i = 0; i < n; i++) {
+        const int j = i + 1 < n ? i + 1 : 0;
+        if (!(tag[i] == 2 && tag[j] == 1) || *ncap >= 3) continue;
+        const F2 e = P[i], f = P[j];
+        const float cx = f.x - e.x, cy = f.y - e.y;
+        const float chord = sqrtf(cx * cx + cy * cy);
+        const float th = asinf(fminf(chord / (2.f * delta), 1.f));
+        const float u = 2.f * th;
+        float tms;   // 2 th - sin 2 th
+        if (u < 0.5f) {
+            const float u2 = u * u;
+            float term = u * u2 / 6.f, sum = 0.f;
+            for (int k = 1; k <= 6; k++) {
+                sum += term;
+                term *= -u2 / ((2.f * k + 2.f) * (2.f * k + 3.f));
+            }
+            tms = sum;
+        } else {
+            tms = u - sinf(u);
+        }
+        const float st = sinf(th);
+        const float dc = tms > 0.f ? 4.f * delta * st * st * st / (3.f * tms) : delta;
+        const float mx = 0.5f * (e.x + f.x), my = 0.5f * (e.y + f.y);
+        const float im = rsqrtf(mx * mx + my * my);
+        C[*ncap].x = dc * mx * im;
+        C[*ncap].y = dc * my * im;
+        Cw[*ncap] = delta * delta * tms / (g.cap_printed ? 4.f : 2.f);
+        (*ncap)++;
+    }
+    *kind = (nin == 3 && n == 3) ? KIND_WHOLE : KIND_PARTIAL;
+    return n >= 3 ? n : 0;
+}
+
 
 // error of either); otherwise the FP64 test decides.  Returns 0 far, 1 near, -1 undecided.
 __device__ __forceinline__ int near_f32(const F2 dl[3], float diamf, float eta)

@@ -997,6 +997,41 @@ __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &
             return 1;
         }
     }
+    if (sizeof(T) == sizeof(float) && BALL == NL_BALL_EXACTCAPS) {
+        nlg::F2 dl[3];
+        for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
+        if (INV && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
+            return -1;
+        nlg::F2 P[6], C[3];
+        float Cw[3];
+        int nc = 0, k = nlg::KIND_PARTIAL;
+        const int n = nlg::exactcaps_region_f32(dl, A.geo, P, C, Cw, &nc, &k);
+        if (n >= 0) {
+            // certified FP32 walk: the vertex count, the caps and the kind of the FP64 region
+            if (n < 3 && nc == 0) return 0;
+            kind = k;
+            nv = n;
+            ncap = nc;
+            if (k == nlg::KIND_WHOLE) {
+                const D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};   // unused: FP32 coordinates dl
+                whole_sums<T, INV>(A, Vb, cand_akc<T>(A, c), D2{o.x, o.y}, S, nq, dl);
+            } else {
+                Sums<float> &Sf = *(Sums<float> *)&S;
+                const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
+                if (n >= 3) poly_sums_f32<INV>(A, P, n, dl[0], e1, e2, c.binv, Sf, nq);
+                else sums_zero(Sf);
+                for (int j = 0; j < nc; j++) {   // one point per cap: its centroid, weight its area
+                    const float rx = C[j].x - dl[0].x, ry = C[j].y - dl[0].y;
+                    const float l1 = (rx * e2.y - e2.x * ry) * c.binv, l2 = (e1.x * ry - rx * e1.y) * c.binv;
+                    float w = Cw[j] * A.kcf;
+                    if (INV) w *= rsqrtf(C[j].x * C[j].x + C[j].y * C[j].y);
+                    sums_add<float>(Sf, w, 1.f - l1 - l2, l1, l2);
+                    nq++;
+                }
+            }
+            return 1;
+        }
+    }
     return -1;
 }
 

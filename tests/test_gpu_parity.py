@@ -135,8 +135,7 @@ def test_fp64_items_queued_or_inline(nl, ctx, monkeypatch, ball, kernel):
     # FP32 path: the items whose region the FP64 geometry builds are queued for the deferred
     # kernel.  Without a queue (capacity 0: all inline in the boundary kernel) or with a
     # queue of one item (the rest inline), the records are the same and the values stay
-    # within the FP32 bound; exactcaps has no FP32 region, so its default queue (4096
-    # items) overflows here and both routes run in one launch.
+    # within the FP32 bound.
     p = small_problem(ball, n=24, kernel=kernel)
     over = dict(duffy_n=4) if kernel == "inv_dist" else {}
     out = O.assemble(p.mesh, oracle_cfg(p, **over), want_hash=True)
@@ -156,10 +155,25 @@ def test_fp64_items_queued_or_inline(nl, ctx, monkeypatch, ball, kernel):
         assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
         assert nl.nl_last_fp64_items(ctx) == counts[cap]
     assert counts[None] == counts["0"] == counts["1"]
-    if kernel == "inv_dist" or ball == "exactcaps":
+    if kernel == "inv_dist":
         assert counts[None] > 0
-    if ball == "exactcaps":
-        assert counts[None] > 4096
+
+
+@pytest.mark.parametrize("cap_printed", [0, 1])
+def test_exactcaps_fp32_region_certified(nl, ctx, cap_printed):
+    # exactcaps on the FP32 path: the certified FP32 walk builds the nocaps polygon and the caps
+    # (one centroid point each, with the true or the printed area), so only a few items are left
+    # to the FP64 geometry; the records are the oracle's and the values within the FP32 bound
+    p = small_problem("exactcaps", n=24)
+    out = O.assemble(p.mesh, oracle_cfg(p, cap_printed=cap_printed), want_hash=True)
+    h, c, q = gpu_interactions(nl, ctx, p, prec="fp32c", cap_printed=cap_printed)
+    np.testing.assert_array_equal(c, out["count_a"])
+    np.testing.assert_array_equal(q, out["qp_a"])
+    np.testing.assert_array_equal(h, out["hash_a"])
+    assert nl.nl_last_fp64_items(ctx) < 0.01 * out["n_inter"]
+    Dg, stats = gpu_assemble(nl, ctx, p, "fp32c", cap_printed=cap_printed)
+    compare(Dg, O.to_csr(out), "fp32c")
+    assert stats == (out["n_pairs"], out["n_qp_pairs"], out["n_inter"])
 
 
 @pytest.mark.parametrize("ball", ["ngon", "nocaps"])
@@ -334,7 +348,7 @@ def test_numeric_reassembly_is_repeatable(nl, ctx, monkeypatch, ball, kernel, pr
     m = nl.nl_assemble(ctx, mesh, cfg)
     try:
         D1 = nl.to_scipy(ctx, m)
-        if prec == "fp32c" and (ball == "exactcaps" or kernel == "inv_dist"):
+        if prec == "fp32c" and kernel == "inv_dist":
             assert nl.nl_last_fp64_items(ctx) > 0   # the deferred queue is exercised
         nl.nl_assemble_numeric(ctx, m)
         D2 = nl.to_scipy(ctx, m)
