@@ -40,8 +40,8 @@ SMS, FP32_LANES = 152, 128
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (nominal); the measured one comes from nl_fma_peak
 # DRAM bytes (read + write) of the numeric phase (k_interior + k_boundary + k_deferred) of
 # one assembly, from one ncu capture of the current kernels (profiles/k_boundary_<workload>.md)
-NCU_TRAFFIC = {"ngon32_96": (403.5e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_interior + k_boundary "
-                                      "+ k_deferred, profiles/numeric_traffic_ngon32_96.md")}
+NCU_TRAFFIC = {"ngon32_96": (409.6e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_interior + k_boundary "
+                                      "+ k_deferred + k_defer_merge, profiles/numeric_traffic_ngon32_96.md")}
 
 
 def parse():
@@ -719,7 +719,8 @@ def main():
         "fp64": fp64,
         "speedup_fp32c_vs_fp64": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "fp32c_vs_fp64_max_rel_err": err32,
-        "roofline": {"bound": "alu", "kernel": "k_interior + k_boundary + k_deferred (pair geometry + quadrature)",
+        "roofline": {"bound": "alu", "kernel": "k_interior + k_boundary + k_deferred + k_defer_merge (+ k_near for the "
+                               "singular kernel): pair geometry + quadrature",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"FP32 FMA: {SMS} SMs x {FP32_LANES} lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz "
                                     f"(clock from MEASURED_PEAKS.json, {peaks['clock_source']})",

@@ -712,7 +712,7 @@ __device__ __forceinline__ bool want_stats(const NumArgs &A)
 // per-triangle M_aa and statistics atomically onto zeroed outputs; the batched kernels run
 // one after the other and store, then add.
 // ---------------------------------------------------------------------------
-template <typename T, int STS = -1>
+template <typename T, int STS = -1, int KIN = -1>
 __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const OuterPt *sq, int lane, LaneAcc &acc)
 {
     const int K = A.K;
@@ -726,7 +726,7 @@ __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const Ou
             continue;
         }
 #endif
-        const bool inv = A.kernel == NL_KERNEL_INV_DIST;
+        const bool inv = KIN < 0 ? A.kernel == NL_KERNEL_INV_DIST : KIN == 1;
         // the FP64 vertices only where the quadrature uses them (singular kernel)
         D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
         if (inv)
@@ -746,7 +746,7 @@ __device__ __forceinline__ void interior_outer(const NumArgs &A, int a, const Ou
             nlg::F2 dl[3];
             if (inv)
                 for (int i = 0; i < 3; i++) { dl[i].x = vl[i].x - o.lx; dl[i].y = vl[i].y - o.ly; }
-            whole_sums<T>(A, Vb, akc, D2{o.x, o.y}, S, nq, inv ? dl : nullptr);
+            whole_sums<T, KIN>(A, Vb, akc, D2{o.x, o.y}, S, nq, inv ? dl : nullptr);
             combine<T>(o, S, v);
             acc.qp += nq;
             if (!A.outer_support) {
@@ -794,7 +794,7 @@ __device__ __forceinline__ void finish_outer(const NumArgs &A, int a, LaneAcc &a
 }
 
 // five resident 4-warp blocks per SM with float sums (96 registers); double sums unconstrained
-template <typename T, int STS = -1>
+template <typename T, int STS = -1, int KIN = -1>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float) ? 5 : 1) k_interior(const NumArgs A)
 {
     __shared__ OuterPt sq_all[kWarpsPerBlock][NL_MAXQ + 8];
@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, sizeof(T) == sizeof(float
     __syncwarp();
     LaneAcc acc;
     acc_zero(acc);
-    interior_outer<T, STS>(A, a, sq, lane, acc);
+    interior_outer<T, STS, KIN>(A, a, sq, lane, acc);
     finish_outer<STS>(A, a, acc, lane, kAtomicAdd);
 }
 
@@ -1932,7 +1932,9 @@ template <typename T, int STS = -1>
 nl_status nl_numeric_interior_same(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads, nl_status s)
 {
     if (s != NL_OK) return s;
-    nlq::k_interior<T, STS><<<grid, threads, 0, ctx->stream>>>(A); ++ctx->launches;
+    if (A.kernel == NL_KERNEL_INV_DIST) nlq::k_interior<T, STS, 1><<<grid, threads, 0, ctx->stream>>>(A);
+    else nlq::k_interior<T, STS, 0><<<grid, threads, 0, ctx->stream>>>(A);
+    ++ctx->launches;
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? NL_OK : nl_cuda_fail(ctx, e, "k_interior launch");
 }
@@ -1943,7 +1945,9 @@ template <typename T, int STS = -1>
 nl_status nl_numeric_interior_join(nl_ctx *ctx, const nlq::NumArgs &A, unsigned grid, unsigned threads, nl_status s)
 {
     if (s == NL_OK) {
-        nlq::k_interior<T, STS><<<grid, threads, 0, ctx->side[0]>>>(A); ++ctx->launches;
+        if (A.kernel == NL_KERNEL_INV_DIST) nlq::k_interior<T, STS, 1><<<grid, threads, 0, ctx->side[0]>>>(A);
+        else nlq::k_interior<T, STS, 0><<<grid, threads, 0, ctx->side[0]>>>(A);
+        ++ctx->launches;
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) s = nl_cuda_fail(ctx, e, "k_interior launch");
     }
