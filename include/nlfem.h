@@ -308,16 +308,18 @@ int64_t nl_launch_count(nl_ctx *ctx);
    path whose region the FP64 geometry built: FP32 choices it could not certify (a vertex,
    root or orientation too close to its threshold), the singular kernel's near-field items
    that FP32 cannot decide, and the cut items of the barycenter and overlap balls (their
-   whole / empty choice is certified in FP32, their regions are whole triangles).  The boundary kernel
-   queues them and a second kernel integrates the queue with every lane busy; a full
-   queue (capacity E/16, at least 4096; NL_DEFER_CAP in the environment overrides it, 0
-   disables the queue) leaves the excess to the boundary kernel's own lanes.  Each warp
-   queues its items in (pair, outer point) order and a merge kernel adds the items of a
-   pair onto it in that order (no atomics).  Run to run, FP32-path pair blocks may still
-   differ in their last bits (the boundary kernel's lanes add their blocks in a
-   scheduling-dependent order; measured up to 6e-9 of max|D|), and the sums taken with FP64
-   atomics (M_aa, M_bb, the scatter into D) in theirs (about 1e-16 relative).  0 for the
-   FP64 path; -1 for a null context. */
+   whole / empty choice is certified in FP32, their regions are whole triangles).  The
+   boundary kernel queues them and a second kernel integrates the queue with every lane
+   busy.  A full queue (capacity E/16, at least 4096) leaves the excess to the boundary
+   kernel's own lanes; nl_assemble then runs the numeric phase again with a queue that holds
+   every item and keeps it for the plan's re-assemblies (NL_DEFER_CAP in the environment
+   fixes the capacity instead, 0 disables the queue).  Each warp queues its items in (pair,
+   outer point) order and a merge kernel adds the items of a pair onto it in that order (no
+   atomics); the boundary kernel sums the other items of a pair in fixed point (order-free).
+   So run to run the FP32-path pair blocks repeat exactly, except the singular kernel's
+   near-field items, which k_near sums in FP32 in a queue-order grouping (measured up to 3e-8
+   of max|D|), and the sums taken with FP64 atomics (M_aa, M_bb, the scatter into D) differ
+   in their last bits (about 1e-16 relative).  0 for the FP64 path; -1 for a null context. */
 int64_t nl_last_fp64_items(nl_ctx *ctx);
 
 #ifdef __cplusplus

@@ -346,7 +346,7 @@ nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats, bool one_stream = fal
     if (s != NL_OK) return s;
     if (P->cfg.prec == NL_PREC_FP64) return nl_launch_numeric_f64(ctx, A, P->cfg.ball, one_stream);
     if (!P->defer) {
-        const int cap = nl_defer_cap(P->E);
+        const int cap = nl_defer_cap(P->E) > P->defer_min ? nl_defer_cap(P->E) : P->defer_min;
         nlq::DeferItem *q = nullptr;
         if ((s = nl_alloc(ctx, &q, nlq::defer_alloc_items(cap))) != NL_OK) return s;
         P->defer = q;
@@ -359,7 +359,7 @@ nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats, bool one_stream = fal
     A.defer_cap = P->defer_cap;
     if (P->cfg.kernel == NL_KERNEL_INV_DIST) {
         if (!P->near_n) {
-            const int cap = nl_near_cap(P->E);
+            const int cap = nl_near_cap(P->E) > P->near_min ? nl_near_cap(P->E) : P->near_min;
             nlq::DeferItem *q = nullptr;
             if (cap > 0 && (s = nl_alloc(ctx, &q, (size_t)cap)) != NL_OK) return s;
             P->nearq = q;
@@ -532,13 +532,38 @@ nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl
     if ((s = run_numeric(ctx, P, false)) != NL_OK) goto fail;
     if ((e = cudaEventRecord(ctx->ev[2], ctx->stream)) != cudaSuccess) goto cuda_fail;
     h->deferred = 0;
+    h->near = 0;
     if (P->defer_n &&
         (e = cudaMemcpyAsync(&h->deferred, P->defer_n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
+        goto cuda_fail;
+    if (P->near_n &&
+        (e = cudaMemcpyAsync(&h->near, P->near_n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
         goto cuda_fail;
     if ((s = nl_pattern_a(ctx, P, out, Q, h)) != NL_OK) goto fail;
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) goto cuda_fail;
     ctx->last_fp64_items = h->deferred;
     if ((s = nl_prepare_check(ctx, h)) != NL_OK) goto fail;
+    {
+        // A full queue of FP64-decided or near-field items leaves the excess to the boundary
+        // kernel's lanes, and which items those are depends on the scheduling.  Queues that hold
+        // them all (kept for every re-assembly of this plan) make the values independent of it.
+        const bool dfull = P->defer && h->deferred > P->defer_cap && !nl_defer_cap_fixed();
+        const bool nfull = P->near_n && P->near_cap > 0 && h->near > P->near_cap && !nl_near_cap_fixed();
+        if (dfull) {
+            const int64_t want = (int64_t)h->deferred + h->deferred / 4;
+            P->defer_min = (int)(want > (int64_t(1) << 24) ? (int64_t(1) << 24) : want);
+            nl_free(P->defer, ctx->stream);
+            nl_free(P->defer_n, ctx->stream);
+        }
+        if (nfull) {
+            const int64_t want = (int64_t)h->near + h->near / 4;
+            P->near_min = (int)(want > (int64_t(1) << 30) ? (int64_t(1) << 30) : want);
+            nl_free(P->nearq, ctx->stream);
+            nl_free(P->otab, ctx->stream);
+            nl_free(P->near_n, ctx->stream);
+        }
+        if ((dfull || nfull) && (s = run_numeric(ctx, P, false)) != NL_OK) goto fail;
+    }
     if ((s = nl_pattern_b(ctx, P, out, Q, h)) != NL_OK) goto fail;
     if ((e = cudaEventRecord(ctx->ev[3], ctx->stream)) != cudaSuccess) goto cuda_fail;
     if ((s = nl_run_scatter(ctx, P, out)) != NL_OK) goto fail;

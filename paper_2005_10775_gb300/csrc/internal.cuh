@@ -59,6 +59,7 @@ struct nl_host_slot {
     int row_ovf;                  // pattern row overflow
     int err;                      // numeric-phase error word
     int deferred;                 // FP32 path: items the FP64 geometry decided
+    int near;                     // FP32 path, singular kernel: near-field items queued for k_near
 };
 
 struct nl_ctx {
@@ -127,11 +128,13 @@ struct nl_plan {
     void *defer = nullptr;
     int *defer_n = nullptr;
     int defer_cap = 0;
+    int defer_min = 0;            // capacity the next allocation takes at least (a run overflowed)
     // FP32 path of the singular kernel: queue of the near-field whole items (nlq::DeferItem)
     // that k_near integrates, and its fill count
     void *nearq = nullptr;
     int *near_n = nullptr;
     int near_cap = 0;
+    int near_min = 0;             // capacity the next allocation takes at least (a run overflowed)
     void *otab = nullptr;         // [K][outer points] nlq::OuterPt staged by the boundary kernel for k_near
 };
 
@@ -139,6 +142,13 @@ struct nl_plan {
 // about 27 near-field triangles per outer point on the benchmark meshes, 16 outer points, some
 // 330 candidates per triangle (1.3 E items); a full queue sends the excess to the boundary
 // kernel's own lanes.  NL_NEAR_CAP in the environment sets it (0: no queue, all inline).
+// is the capacity of the near-field queue set by NL_NEAR_CAP (fixed, for tests)?
+inline bool nl_near_cap_fixed()
+{
+    const char *v = getenv("NL_NEAR_CAP");
+    return v && *v;
+}
+
 inline int nl_near_cap(int64_t E)
 {
     const char *v = getenv("NL_NEAR_CAP");
@@ -165,6 +175,13 @@ nl_status nl_cuda_fail(nl_ctx *ctx, cudaError_t e, const char *what);
 // capacity of a deferred-item queue for E candidate pairs: the FP64 items are a small
 // fraction of the exact items (about 0.1 % on jittered meshes); a full queue only sends
 // the excess back to the boundary kernel's own lanes
+// is the capacity of the deferred-item queue set by NL_DEFER_CAP (fixed, for tests)?
+inline bool nl_defer_cap_fixed()
+{
+    const char *v = getenv("NL_DEFER_CAP");
+    return v && *v;
+}
+
 inline int nl_defer_cap(int64_t E)
 {
     // NL_DEFER_CAP in the environment sets the capacity (0: no queue, every such item inline)

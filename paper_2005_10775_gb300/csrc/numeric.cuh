@@ -14,10 +14,14 @@
 // symmetric) onto T_b's per-triangle sums (FP64 atomics); M_aa is summed over all
 // candidates in FP64 and reduced across the warp.
 //
-// T = double: FP64 quadrature.  T = float: the inner and per-pair sums run in FP32,
-// the long sums (M_aa over all neighbours, M_bb over all pairs of T_b, and D over all
-// pairs in the scatter) in FP64, which compensates the FP32 rounding of the short sums.
+// T = double: FP64 quadrature.  T = float: the inner sums run in FP32, the boundary
+// kernel's per-pair sums in 32-bit fixed point (exact, order-free integer adds of values
+// rounded to a per-pair grid), and the long sums (M_aa over all neighbours, M_bb over all
+// pairs of T_b, and D over all pairs in the scatter) in FP64, which compensates the FP32
+// rounding of the short sums.
 #pragma once
+
+#include <type_traits>
 
 #include "geometry.cuh"
 
@@ -1074,13 +1078,80 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
     return true;
 }
 
-// Add a block w (its first NV values) to owner own's column of the shared accumulator; am = the
-// lanes that call this (all of them do; own < 0: a lane without a block).  Lanes with the same
-// owner first sum their blocks by shuffles (the leader takes its peers' values one by one, in
-// lane order), so one lane per owner adds: no shared atomics colliding on one address.
-template <typename T, int NV>
-__device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane, T *w, unsigned am)
+// ---------------------------------------------------------------------------
+// Pair sums of the FP32 boundary kernel in fixed point.  The M_ab and upper M_bb sums of a pair
+// (rows 0..14 of the shared accumulator) are 32-bit integers on a grid of 2^-p, a power of two
+// per pair chosen from a bound on the pair's sums.  Every item rounds its 15 values to that
+// grid and adds them with integer arithmetic (native shared-memory atomics), so a pair's sums do
+// not depend on the order in which the lanes add them: the blocks are the same in every run.
+// Bound: an item (x_q, T_b) adds W_q la_i s1_j to M_ab and W_q S2_jk to M_bb; with |la_i| <= L_q
+// (the outer point's barycentrics) and 0 <= S2_jk, s1_j <= s0 (inner barycentrics in [0, 1] up to
+// rounding) every sum of the pair is at most B_a s0max, B_a = sum_q |W_q| max(1, L_q).  The region
+// lies in T_b, so s0max = kc |T_b| for a constant kernel; for c / |x - y| the integral over T_b is
+// at most c 2 sqrt(pi |T_b|) (the disc of the same area centred at x), taken twice more for the
+// quadrature's error.  The bound, rounded up to a power of two 2^e, maps to 2^29: a rounding error
+// of at most 2^-30 of it per item, and sums far from the 2^31 range unless the bound is broken
+// (|sum| >= 2^30 sets error bit 128).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fx_outer_bound(const OuterPt *sq, int n)
 {
+    float b = 0.f;
+    for (int q = 0; q < n; q++) {
+        const float l = fmaxf(1.f, fmaxf(fabsf(sq[q].l0f), fmaxf(fabsf(sq[q].l1f), fabsf(sq[q].l2f))));
+        b += fabsf(sq[q].Wf) * l;
+    }
+    return b * 1.0001f;   // above its own rounding
+}
+
+// grid scale 2^(29 - e) of a pair (outer bound bwa, |T_b| kc = akcf)
+template <bool INV>
+__device__ __forceinline__ float fx_scale(float bwa, float akcf, float kcf)
+{
+    const float r = INV ? bwa * 4.f * sqrtf(3.14159265f * kcf * akcf) : bwa * akcf;
+    const int e = ((__float_as_int(fmaxf(r, 1e-25f)) >> 23) & 0xff) - 126;   // r < 2^e
+    return __int_as_float((127 + 29 - e) << 23);
+}
+
+// rows 0..14 of an item's block w into owner own's column: integer atomics on the grid of scale
+// fxs (FP32 sums), float atomics (FP64 sums)
+template <typename T>
+__device__ __forceinline__ void pair_add_atomic(T (*dst)[32], int own, const T *w, float fxs)
+{
+    if constexpr (sizeof(T) == sizeof(float)) {
+        for (int k = 0; k < 15; k++) atomicAdd(reinterpret_cast<int *>(&dst[k][own]), __float2int_rn(w[k] * fxs));
+    } else {
+        (void)fxs;
+        for (int k = 0; k < 15; k++) atomicAdd(&dst[k][own], w[k]);
+    }
+}
+
+// the same by the owner lane itself, while no other lane adds to its column
+template <typename T>
+__device__ __forceinline__ void pair_add_owner(T (*dst)[32], int own, const T *w, float fxs)
+{
+    if constexpr (sizeof(T) == sizeof(float)) {
+        for (int k = 0; k < 15; k++) *reinterpret_cast<int *>(&dst[k][own]) += __float2int_rn(w[k] * fxs);
+    } else {
+        (void)fxs;
+        for (int k = 0; k < 15; k++) dst[k][own] += w[k];
+    }
+}
+
+// Add rows 0..14 of a block w to owner own's column of the shared accumulator; am = the lanes
+// that call this (all of them do; own < 0: a lane without a block).  Lanes with the same owner
+// first sum their blocks by shuffles (the leader takes its peers' values one by one, in lane
+// order), so one lane per owner adds: no shared atomics colliding on one address.  FP32 sums are
+// rounded to the owner's grid first and summed as integers: the same sum for any grouping.
+template <typename T>
+__device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane, const T *w, float fxs,
+                                               unsigned am)
+{
+    using V = typename std::conditional<sizeof(T) == sizeof(float), int, T>::type;
+    V x[15];
+    for (int k = 0; k < 15; k++) {
+        if constexpr (sizeof(T) == sizeof(float)) x[k] = __float2int_rn(w[k] * fxs);
+        else x[k] = w[k];
+    }
     __syncwarp(am);
     const unsigned peers = __match_any_sync(am, own);
     const int m = own >= 0 ? __popc(peers) : 0, leader = __ffs(peers) - 1;
@@ -1090,13 +1161,13 @@ __device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane
         for (int j = 0; j < t && rest; j++) rest &= rest - 1;
         const bool take = lane == leader && t < m;
         const int src = take ? __ffs(rest) - 1 : lane;
-        for (int k = 0; k < NV; k++) {
-            const T x = __shfl_sync(am, w[k], src);
-            if (take) w[k] += x;
+        for (int k = 0; k < 15; k++) {
+            const V y = __shfl_sync(am, x[k], src);
+            if (take) x[k] += y;
         }
     }
     if (own >= 0 && lane == leader) {
-        for (int k = 0; k < NV; k++) atomicAdd(&accum[k][own], w[k]);
+        for (int k = 0; k < 15; k++) atomicAdd(reinterpret_cast<V *>(&accum[k][own]), x[k]);
         accum[21][own] = (T)1;
     }
 }
@@ -1119,7 +1190,7 @@ __device__ __forceinline__ bool defer_mark(const NumArgs &A, BoundaryShared<T> &
 // the accumulator.
 template <int BALL, typename T>
 __device__ __forceinline__ void defer_flush(const NumArgs &A, int a, int64_t base, BoundaryShared<T> &sh, int lane,
-                                            LaneAcc &acc)
+                                            float fxs, LaneAcc &acc)
 {
     const unsigned m = sh.dmask[lane];
     const int cnt = __popc(m);
@@ -1151,7 +1222,8 @@ __device__ __forceinline__ void defer_flush(const NumArgs &A, int a, int64_t bas
         T w[21];
         for (int k = 0; k < 21; k++) w[k] = 0;
         combine<T>(o, S, w);
-        for (int k = 0; k < 21; k++) sh.acc[k][lane] += w[k];
+        pair_add_owner<T>(sh.acc, lane, w, fxs);
+        for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
         sh.acc[21][lane] = (T)1;
         acc.cnt++;
         acc.qp += nq;
@@ -1164,7 +1236,7 @@ __device__ __forceinline__ void defer_flush(const NumArgs &A, int a, int64_t bas
 // free of the near rule, which runs in k_near.
 template <typename T>
 __device__ __noinline__ int64_t near_inline(const NumArgs &A, const CandData &cd, const OuterPt &o,
-                                            BoundaryShared<T> &sh, int lane)
+                                            BoundaryShared<T> &sh, int lane, float fxs)
 {
     nlg::F2 dl[3];
     for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
@@ -1175,7 +1247,10 @@ __device__ __noinline__ int64_t near_inline(const NumArgs &A, const CandData &cd
     float w[21];
     for (int k = 0; k < 21; k++) w[k] = 0.f;
     combine<float>(o, S, w);
-    for (int k = 0; k < 21; k++) sh.acc[k][lane] += (T)w[k];
+    T wt[21];
+    for (int k = 0; k < 21; k++) wt[k] = (T)w[k];
+    pair_add_owner<T>(sh.acc, lane, wt, fxs);
+    for (int k = 15; k < 21; k++) sh.acc[k][lane] += wt[k];
     sh.acc[21][lane] = (T)1;
     return nq;
 }
@@ -1185,7 +1260,7 @@ __device__ __noinline__ int64_t near_inline(const NumArgs &A, const CandData &cd
 // integrates them itself.
 template <typename T>
 __device__ __forceinline__ void near_flush(const NumArgs &A, int a, int64_t base, unsigned m, BoundaryShared<T> &sh,
-                                           int lane, LaneAcc &acc)
+                                           float fxs, int lane, LaneAcc &acc)
 {
     const int cnt = __popc(m);
     int inc = cnt;
@@ -1207,7 +1282,7 @@ __device__ __forceinline__ void near_flush(const NumArgs &A, int a, int64_t base
         }
         const CandData &cd = sh.cand[lane];
         acc.cnt++;
-        acc.qp += near_inline<T>(A, cd, sh.sq[q], sh, lane);
+        acc.qp += near_inline<T>(A, cd, sh.sq[q], sh, lane, fxs);
         if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
     }
 }
@@ -1222,11 +1297,12 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
     const D2 ba = {A.bx[a], A.by[a]};
     const float4 bah = bary_hilo(A, a);
     const int64_t es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
-    // M_aa belongs to the outer triangle, not to the pair: except for the N-gon (whose rounds
-    // aggregate whole blocks by shuffles), each lane sums the M_aa of the items it integrates in
-    // its own column of rows 15-20 (plain adds), and only M_ab and M_bb take shared atomics
-    constexpr bool kLaneMaa = BALL != NL_BALL_NGON;
+    // M_aa belongs to the outer triangle, not to the pair: each lane sums the M_aa of the items it
+    // integrates in its own column of rows 15-20 (plain adds), and only M_ab and M_bb (rows 0-14)
+    // go to the owner's column
     const int nq_all = A.outer.n;
+    // FP32 sums: the outer bound of the pairs' fixed-point grids
+    const float fx_bwa = sizeof(T) == sizeof(float) ? fx_outer_bound(sh.sq, nq_all) : 0.f;
     const bool inv = INV;
     for (int64_t base = es; base < e1; base += 32) {
         const int64_t e = base + lane;
@@ -1285,18 +1361,6 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             nnear += __popc(mn);
         }
         __syncwarp();
-        // Float sums: the whole items of one owner sit at neighbouring outer points, and up to
-        // four of them share a round; spreading the outer points over three accumulator copies
-        // (two in the clip buffers, unused until phase 2b) cuts the shared atomics that collide
-        // on one address.  The copies are folded into acc before phase 2b.
-        constexpr bool kCopies = sizeof(T) == sizeof(float);
-        T (*extra)[22][32] = reinterpret_cast<T (*)[22][32]>(&sh.clip);
-        if (kCopies && nwhole > 32)
-            for (int k = 0; k < 21; k++) {
-                extra[0][k][lane] = (T)0;
-                extra[1][k][lane] = (T)0;
-            }
-        __syncwarp();
         // phase 2a: whole items with all lanes
         for (int i = lane; i < nwhole; i += 32) {
             const unsigned it = sh.wqueue[i];
@@ -1316,22 +1380,13 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
-            const int cp = (kCopies && nwhole > 32) ? q % 3 : 0;
-            T (*dst)[32] = cp == 0 ? sh.acc : extra[cp - 1];
-            if (kLaneMaa) {
-                for (int k = 0; k < 15; k++) atomicAdd(&dst[k][own], w[k]);
-                for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
-            } else {
-                for (int k = 0; k < 21; k++) atomicAdd(&dst[k][own], w[k]);
-            }
+            pair_add_atomic<T>(sh.acc, own, w, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf));
+            for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
             sh.acc[21][own] = (T)1;
             acc.cnt++;
             acc.qp += nq;
             if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
         }
-        __syncwarp();
-        if (kCopies && nwhole > 32)
-            for (int k = 0; k < 21; k++) sh.acc[k][lane] += extra[0][k][lane] + extra[1][k][lane];
         __syncwarp();
         // phase 2c: whole items in the singular kernel's near field (FP32 near rule)
         for (int i = lane; INV && !split_near && i < nnear; i += 32) {
@@ -1352,9 +1407,8 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             combine<T>(o, S, w);
             // an owner lies in the near field of several outer points of one round: the lanes
             // with the same owner sum their blocks by shuffles, one lane per owner adds
-            if (kLaneMaa)
-                for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
-            warp_owner_add<T, kLaneMaa ? 15 : 21>(sh.acc, own, lane, w, rmask);
+            for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
+            warp_owner_add<T>(sh.acc, own, lane, w, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf), rmask);
             acc.cnt++;
             acc.qp += nq;
             if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
@@ -1381,34 +1435,41 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             T w[21];
             for (int k = 0; k < 21; k++) w[k] = 0;
             combine<T>(o, S, w);
-            // N-gon: a round holds items of a few outer points, so one candidate often owns
-            // several of them (the disc balls' cheaper regions do not repay the shuffles)
-            if (BALL == NL_BALL_NGON) {
-                warp_owner_add<T, 21>(sh.acc, own, lane, w, __activemask());   // the lanes converged here
-            } else {
-                for (int k = 0; k < 15; k++) atomicAdd(&sh.acc[k][own], w[k]);
-                for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
-                sh.acc[21][own] = (T)1;
-            }
+            for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
+            pair_add_atomic<T>(sh.acc, own, w, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf));
+            sh.acc[21][own] = (T)1;
             acc.cnt++;
             acc.qp += nq;
             if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
         }
         __syncwarp();
         if (sizeof(T) == sizeof(float) && A.defer) {
-            defer_flush<BALL, T>(A, a, base, sh, lane, acc);
+            defer_flush<BALL, T>(A, a, base, sh, lane, fx_scale<INV>(fx_bwa, sh.cand[lane].akcf, A.kcf), acc);
             __syncwarp();
         }
         if constexpr (split_near) {
-            near_flush<T>(A, a, base, my_near, sh, lane, acc);
+            near_flush<T>(A, a, base, my_near, sh, fx_scale<INV>(fx_bwa, sh.cand[lane].akcf, A.kcf), lane, acc);
             __syncwarp();
         }
         // phase 3: owners merge the queue's contributions and write their pair
         if (valid) {
             T v[21];
-            for (int k = 0; k < 21; k++) v[k] = sh.acc[k][lane];
+            if constexpr (sizeof(T) == sizeof(float)) {
+                // back from the pair's grid (an exact power of two)
+                const float inv_s = 1.f / fx_scale<INV>(fx_bwa, sh.cand[lane].akcf, A.kcf);
+                bool big = false;
+                for (int k = 0; k < 15; k++) {
+                    const int iv = *reinterpret_cast<const int *>(&sh.acc[k][lane]);
+                    big = big || iv >= (1 << 30) || iv <= -(1 << 30);
+                    v[k] = (T)iv * inv_s;
+                }
+                if (big) atomicOr(A.err, 128);
+            } else {
+                for (int k = 0; k < 15; k++) v[k] = sh.acc[k][lane];
+            }
+            for (int k = 15; k < 21; k++) v[k] = sh.acc[k][lane];
             write_pair<T>(A, e, sh.cand[lane].b, sh.acc[21][lane] != (T)0, v, acc);
-        } else if (kLaneMaa) {   // a lane without a candidate in this batch may have integrated items
+        } else {   // a lane without a candidate in this batch may have integrated items
             T m[6];
             for (int k = 0; k < 6; k++) m[k] = sh.acc[15 + k][lane];
             maa_add<T>(acc, m);
