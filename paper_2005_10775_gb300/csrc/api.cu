@@ -235,6 +235,20 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     A.outer_support = (c.ball == NL_BALL_BARY_NOCAPS || c.ball == NL_BALL_BARY_APPROXCAPS) ? 1 : 0;
     A.kc = c.kernel_c;
     A.kcf = (float)c.kernel_c;
+    {
+        // grid of the boundary kernel's fixed-point sums of s0 per outer point: every region of
+        // an outer point x lies in B(x, delta + h_max) (the shifted, barycenter and overlap
+        // balls included), so the sum is at most kc pi (delta + h_max)^2 for a constant kernel
+        // and c 2 pi (delta + h_max) for c / |x - y| (the integral of 1/r over the disc), here
+        // with a margin of 1.25 (twice that for the singular kernel's quadrature); the bound,
+        // rounded up to a power of two 2^e, maps to 2^30
+        const double r = c.delta + P->hmax, pi = 3.14159265358979323846;
+        const double bound = c.kernel == NL_KERNEL_INV_DIST ? 2.5 * fabs(c.kernel_c) * 2.0 * pi * r
+                                                            : 1.25 * fabs(c.kernel_c) * pi * r * r;
+        int e = 0;
+        frexp(bound > 1e-30 ? bound : 1e-30, &e);   // bound < 2^e
+        A.s0q_grid = (float)ldexp(1.0, 30 - e);
+    }
     A.geo.delta = c.delta;
     A.geo.deltaf = (float)c.delta;
     A.geo.d2 = P->d2;

@@ -104,6 +104,8 @@ struct NumArgs {
     OuterPt *otab;                    // [K][outer.n] outer points as the boundary kernel staged them (read by
                                       // k_near; with the near-field queue only)
     int prob;                         // index of this problem in a batched launch's argument array
+    float s0q_grid;                   // FP32 boundary kernel: scale of the fixed-point sums of s0 per
+                                      // outer point (a power of two; the bound on a sum maps below 2^30)
 };
 
 template <typename T>
@@ -677,8 +679,8 @@ __device__ __forceinline__ void maa_add(LaneAcc &acc, const T *m)
 }
 
 // the pair's block: M_ab stored (v[0..8]), its upper M_bb (v[9..14]) added onto T_b's sums, its
-// M_aa (v[15..20]) into the lane's sums of T_a
-template <typename T>
+// M_aa (v[15..20]) into the lane's sums of T_a (MAA = false: the caller sums M_aa itself)
+template <typename T, bool MAA = true>
 __device__ __forceinline__ void write_pair(const NumArgs &A, int64_t e, int b, bool any, const T *v, LaneAcc &acc)
 {
     A.flag[e] = any ? 1 : 0;
@@ -686,7 +688,7 @@ __device__ __forceinline__ void write_pair(const NumArgs &A, int64_t e, int b, b
     for (int i = 0; i < 9; i++) blk[(int64_t)i * A.E + e] = v[i];
     if (any)
         for (int i = 0; i < 6; i++) atomicAdd(&A.mbb[(int64_t)i * A.K + b], (double)v[9 + i]);
-    maa_add<T>(acc, v + 15);
+    if (MAA) maa_add<T>(acc, v + 15);
 }
 
 __device__ __forceinline__ void warp_reduce(LaneAcc &acc)
@@ -907,9 +909,12 @@ template <typename T>
 struct BoundaryShared {
     OuterPt sq[NL_MAXQ];
     CandData cand[32];
-    T acc[22][32];             // 21 block values and the non-empty flag of each lane's pair (for
-                               // the disc balls rows 15-20, M_aa, are per integrating lane instead),
-                               // value-major: the owners of one atomic instruction hit distinct banks
+    T acc[16][32];             // M_ab (rows 0-8) and upper M_bb (9-14) of each lane's pair (FP32 sums: fixed
+                               // point) and its non-empty flag (row 15), value-major: the owners of one
+                               // atomic instruction hit distinct banks
+    // per outer point x_q: the sum of s0 over the outer triangle's items, from which M_aa =
+    // sum_q W_q phi_a(x_q) phi_a(x_q)^T s0q[q] (FP32 sums: fixed point on the grid s0q_grid)
+    typename std::conditional<sizeof(T) == sizeof(float), int, T>::type s0q[NL_MAXQ];
     unsigned short queue[32 * NL_MAXQ];    // undecided items (owner lane << 8 | q)
     unsigned dmask[32];        // outer points of each lane's candidate whose item the deferred kernel takes
     // whole items from the front; whole items in the singular kernel's near field from the back
@@ -1091,7 +1096,7 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
 // at most c 2 sqrt(pi |T_b|) (the disc of the same area centred at x), taken twice more for the
 // quadrature's error.  The bound, rounded up to a power of two 2^e, maps to 2^29: a rounding error
 // of at most 2^-30 of it per item, and sums far from the 2^31 range unless the bound is broken
-// (|sum| >= 2^30 sets error bit 128).
+// (|sum| >= 2^30 sets error bit 256).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float fx_outer_bound(const OuterPt *sq, int n)
 {
@@ -1137,6 +1142,38 @@ __device__ __forceinline__ void pair_add_owner(T (*dst)[32], int own, const T *w
     }
 }
 
+// An item's s0 onto its outer point's sum (M_aa of the outer triangle): fixed point (FP32 sums)
+template <typename T, typename S0>
+__device__ __forceinline__ void s0q_add(S0 *s0q, int q, T s0, float grid)
+{
+    if constexpr (sizeof(T) == sizeof(float)) atomicAdd(&s0q[q], __float2int_rn(s0 * grid));
+    else atomicAdd(&s0q[q], s0);
+}
+
+// An item's block (combine of its sums S at outer point x_q = o) added as it is formed: rows
+// 0..14 onto owner own's column (as pair_add_atomic), the flag, and s0 onto the outer point's
+// sum.  No 21-value array stays live across the adds.
+template <typename T, typename S0>
+__device__ __forceinline__ void block_add(const OuterPt &o, const Sums<T> &S, T (*accum)[32], S0 *s0q, int own, int q,
+                                          float fxs, float grid)
+{
+    const bool f32 = sizeof(T) == sizeof(float);
+    const T W = f32 ? (T)o.Wf : (T)o.W, la0 = f32 ? (T)o.l0f : (T)o.l0;
+    const T la1 = f32 ? (T)o.l1f : (T)o.l1, la2 = f32 ? (T)o.l2f : (T)o.l2;
+    auto put = [&](int k, T v) {
+        if constexpr (sizeof(T) == sizeof(float)) atomicAdd(reinterpret_cast<int *>(&accum[k][own]), __float2int_rn(v * fxs));
+        else atomicAdd(&accum[k][own], v);
+    };
+    const T wa0 = W * la0, wa1 = W * la1, wa2 = W * la2;
+    put(0, wa0 * S.s1[0]); put(1, wa0 * S.s1[1]); put(2, wa0 * S.s1[2]);
+    put(3, wa1 * S.s1[0]); put(4, wa1 * S.s1[1]); put(5, wa1 * S.s1[2]);
+    put(6, wa2 * S.s1[0]); put(7, wa2 * S.s1[1]); put(8, wa2 * S.s1[2]);
+    put(9, W * S.S2[0]); put(10, W * S.S2[1]); put(11, W * S.S2[2]);
+    put(12, W * S.S2[3]); put(13, W * S.S2[4]); put(14, W * S.S2[5]);
+    accum[15][own] = (T)1;
+    s0q_add<T>(s0q, q, S.s0, grid);
+}
+
 // Add rows 0..14 of a block w to owner own's column of the shared accumulator; am = the lanes
 // that call this (all of them do; own < 0: a lane without a block).  Lanes with the same owner
 // first sum their blocks by shuffles (the leader takes its peers' values one by one, in lane
@@ -1168,7 +1205,7 @@ __device__ __forceinline__ void warp_owner_add(T (*accum)[32], int own, int lane
     }
     if (own >= 0 && lane == leader) {
         for (int k = 0; k < 15; k++) atomicAdd(reinterpret_cast<V *>(&accum[k][own]), x[k]);
-        accum[21][own] = (T)1;
+        accum[15][own] = (T)1;
     }
 }
 
@@ -1223,8 +1260,8 @@ __device__ __forceinline__ void defer_flush(const NumArgs &A, int a, int64_t bas
         for (int k = 0; k < 21; k++) w[k] = 0;
         combine<T>(o, S, w);
         pair_add_owner<T>(sh.acc, lane, w, fxs);
-        for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
-        sh.acc[21][lane] = (T)1;
+        sh.acc[15][lane] = (T)1;
+        s0q_add<T>(sh.s0q, q, S.s0, A.s0q_grid);
         acc.cnt++;
         acc.qp += nq;
         if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
@@ -1235,9 +1272,10 @@ __device__ __forceinline__ void defer_flush(const NumArgs &A, int a, int64_t bas
 // accumulator (the near-field queue is full).  Not inlined: the boundary kernel's code stays
 // free of the near rule, which runs in k_near.
 template <typename T>
-__device__ __noinline__ int64_t near_inline(const NumArgs &A, const CandData &cd, const OuterPt &o,
-                                            BoundaryShared<T> &sh, int lane, float fxs)
+__device__ __noinline__ int64_t near_inline(const NumArgs &A, const CandData &cd, int q, BoundaryShared<T> &sh,
+                                            int lane, float fxs)
 {
+    const OuterPt &o = sh.sq[q];
     nlg::F2 dl[3];
     for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
     Sums<float> S;
@@ -1250,8 +1288,8 @@ __device__ __noinline__ int64_t near_inline(const NumArgs &A, const CandData &cd
     T wt[21];
     for (int k = 0; k < 21; k++) wt[k] = (T)w[k];
     pair_add_owner<T>(sh.acc, lane, wt, fxs);
-    for (int k = 15; k < 21; k++) sh.acc[k][lane] += wt[k];
-    sh.acc[21][lane] = (T)1;
+    sh.acc[15][lane] = (T)1;
+    s0q_add<T>(sh.s0q, q, (T)S.s0, A.s0q_grid);
     return nq;
 }
 
@@ -1282,7 +1320,7 @@ __device__ __forceinline__ void near_flush(const NumArgs &A, int a, int64_t base
         }
         const CandData &cd = sh.cand[lane];
         acc.cnt++;
-        acc.qp += near_inline<T>(A, cd, sh.sq[q], sh, lane, fxs);
+        acc.qp += near_inline<T>(A, cd, q, sh, lane, fxs);
         if (A.stats) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
     }
 }
@@ -1297,13 +1335,15 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
     const D2 ba = {A.bx[a], A.by[a]};
     const float4 bah = bary_hilo(A, a);
     const int64_t es = A.nbr_split[a], e1 = A.nbr_ptr[a + 1];
-    // M_aa belongs to the outer triangle, not to the pair: each lane sums the M_aa of the items it
-    // integrates in its own column of rows 15-20 (plain adds), and only M_ab and M_bb (rows 0-14)
-    // go to the owner's column
+    // M_aa belongs to the outer triangle, not to the pair: it is W_q phi_a phi_a^T times the sum of
+    // s0 over all items of x_q, so the items only add their s0 onto their outer point's sum
+    // (sh.s0q) and M_ab and M_bb (rows 0-14) onto the owner's column
     const int nq_all = A.outer.n;
     // FP32 sums: the outer bound of the pairs' fixed-point grids
     const float fx_bwa = sizeof(T) == sizeof(float) ? fx_outer_bound(sh.sq, nq_all) : 0.f;
     const bool inv = INV;
+    for (int q = lane; q < NL_MAXQ; q += 32) sh.s0q[q] = 0;
+    __syncwarp();
     for (int64_t base = es; base < e1; base += 32) {
         const int64_t e = base + lane;
         const bool valid = e < e1;
@@ -1321,7 +1361,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             q0 = c.q0;
             sh.cand[lane] = c;
         }
-        for (int i = 0; i < 22; i++) sh.acc[i][lane] = 0;
+        for (int i = 0; i < 16; i++) sh.acc[i][lane] = 0;
         sh.dmask[lane] = 0;
         int nqueue = 0;
         __syncwarp();
@@ -1377,12 +1417,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             if (INV)
                 for (int k = 0; k < 3; k++) { dl[k].x = cd.vlx[k] - o.lx; dl[k].y = cd.vly[k] - o.ly; }
             whole_sums<T, INV>(A, Vb, cand_akc<T>(A, cd), D2{o.x, o.y}, S, nq, INV ? dl : nullptr);
-            T w[21];
-            for (int k = 0; k < 21; k++) w[k] = 0;
-            combine<T>(o, S, w);
-            pair_add_atomic<T>(sh.acc, own, w, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf));
-            for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
-            sh.acc[21][own] = (T)1;
+            block_add<T>(o, S, sh.acc, sh.s0q, own, q, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf), A.s0q_grid);
             acc.cnt++;
             acc.qp += nq;
             if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, nlg::KIND_WHOLE, 3, 0);
@@ -1407,7 +1442,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             combine<T>(o, S, w);
             // an owner lies in the near field of several outer points of one round: the lanes
             // with the same owner sum their blocks by shuffles, one lane per owner adds
-            for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
+            s0q_add<T>(sh.s0q, q, S.s0, A.s0q_grid);
             warp_owner_add<T>(sh.acc, own, lane, w, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf), rmask);
             acc.cnt++;
             acc.qp += nq;
@@ -1415,9 +1450,8 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         }
         // phase 2b: undecided items with all lanes.  The loop does not converge the warp between
         // items: lanes at different items run the same parts of the clip together.  So the order
-        // in which their blocks reach an owner's column depends on the scheduling, and an FP32
-        // block value may differ in its last bits between runs (FP64 blocks: in the last bits of
-        // FP64).
+        // in which their blocks reach an owner's column depends on the scheduling: FP32 sums are
+        // integers there (the same for any order), FP64 blocks may differ in their last bits.
         for (int i = lane; i < nqueue; i += 32) {
             const unsigned it = sh.queue[i];
             const int own = it >> 8, q = it & 0xff;
@@ -1432,12 +1466,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
                 r = exact_item_fp64<BALL, T>(A, cd, o, S, nq, kind, nv, ncap, sh.clip, lane) ? 1 : 0;
             }
             if (r == 0) continue;
-            T w[21];
-            for (int k = 0; k < 21; k++) w[k] = 0;
-            combine<T>(o, S, w);
-            for (int k = 15; k < 21; k++) sh.acc[k][lane] += w[k];
-            pair_add_atomic<T>(sh.acc, own, w, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf));
-            sh.acc[21][own] = (T)1;
+            block_add<T>(o, S, sh.acc, sh.s0q, own, q, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf), A.s0q_grid);
             acc.cnt++;
             acc.qp += nq;
             if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, nv, ncap);
@@ -1453,7 +1482,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         }
         // phase 3: owners merge the queue's contributions and write their pair
         if (valid) {
-            T v[21];
+            T v[15];
             if constexpr (sizeof(T) == sizeof(float)) {
                 // back from the pair's grid (an exact power of two)
                 const float inv_s = 1.f / fx_scale<INV>(fx_bwa, sh.cand[lane].akcf, A.kcf);
@@ -1463,18 +1492,22 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
                     big = big || iv >= (1 << 30) || iv <= -(1 << 30);
                     v[k] = (T)iv * inv_s;
                 }
-                if (big) atomicOr(A.err, 128);
+                if (big) atomicOr(A.err, 256);
             } else {
                 for (int k = 0; k < 15; k++) v[k] = sh.acc[k][lane];
             }
-            for (int k = 15; k < 21; k++) v[k] = sh.acc[k][lane];
-            write_pair<T>(A, e, sh.cand[lane].b, sh.acc[21][lane] != (T)0, v, acc);
-        } else {   // a lane without a candidate in this batch may have integrated items
-            T m[6];
-            for (int k = 0; k < 6; k++) m[k] = sh.acc[15 + k][lane];
-            maa_add<T>(acc, m);
+            write_pair<T, false>(A, e, sh.cand[lane].b, sh.acc[15][lane] != (T)0, v, acc);
         }
         __syncwarp();
+    }
+    // M_aa = sum_q W_q phi_a(x_q) phi_a(x_q)^T s0q[q], in FP64, one outer point a lane
+    for (int q = lane; q < nq_all; q += 32) {
+        const OuterPt &o = sh.sq[q];
+        if (sizeof(T) == sizeof(float) && (sh.s0q[q] >= (1 << 30) || sh.s0q[q] <= -(1 << 30))) atomicOr(A.err, 256);
+        const double t = sizeof(T) == sizeof(float) ? (double)sh.s0q[q] / (double)A.s0q_grid : (double)sh.s0q[q];
+        const double ws = o.W * t;
+        acc.maa[0] += ws * o.l0 * o.l0; acc.maa[1] += ws * o.l1 * o.l1; acc.maa[2] += ws * o.l2 * o.l2;
+        acc.maa[3] += ws * o.l0 * o.l1; acc.maa[4] += ws * o.l0 * o.l2; acc.maa[5] += ws * o.l1 * o.l2;
     }
 }
 

@@ -785,6 +785,8 @@ nl_status nl_pattern_b(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, const nl
     cudaStream_t st = ctx->stream;
     nl_status s;
     if (h->row_ovf) return nl_fail(ctx, NL_EUNSUPPORTED, "a matrix row has more than 4095 columns");
+    if (h->err & 256) return nl_fail(ctx, NL_EUNSUPPORTED, "a fixed-point sum left its range (error word " +
+                                                          std::to_string(h->err) + ")");
     if (h->err) return nl_fail(ctx, NL_EUNSUPPORTED, "a region exceeded the vertex buffer (error word " +
                                                        std::to_string(h->err) + ")");
     const int64_t nnz = h->nnz;
