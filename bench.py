@@ -586,15 +586,17 @@ def table1_times(nl, ctx, stream, dev, dist, flush, h=0.0125, steps=3):
     keep = nl._Keep()
     mesh = device_mesh(nl, m, dev, keep)
     d = 0.1
-    ms = {}
+    ms, n64 = {}, {}
     for ball in ("exactcaps", "approxcaps", "nocaps", "barycenter", "overlap"):
         cfg = nl.make_config(keep, d, ball, "switch47", "gauss3", "const", I.const_kernel_c(d), None, 2, "fp32c",
                              cap_printed=1 if ball == "exactcaps" else 0)
         t, _, _, _, _ = time_assembly(nl, ctx, mesh, cfg, steps, 1, stream, flush, dev, dist)
         ms[ball] = t / steps
+        n64[ball] = nl.nl_last_fp64_items(ctx)
     slow = max(ms.values())
     paper = {"exactcaps": 10.31, "approxcaps": 8.36, "nocaps": 7.76, "barycenter": 4.24, "overlap": 5.23}
-    return {"h": h, "K": m.nt, "ms_per_matrix": ms, "relative_to_slowest_pct": {b: 100 * v / slow for b, v in ms.items()},
+    return {"h": h, "K": m.nt, "ms_per_matrix": ms, "fp64_items": n64,
+            "relative_to_slowest_pct": {b: 100 * v / slow for b, v in ms.items()},
             "paper_pct_of_its_slowest_run": paper,
             "note": "paper Table 1 times at h = 0.0125 as a percentage of its slowest run (exactcaps, h = 0.00625); "
                     "hardware unstated"}

@@ -310,10 +310,10 @@ int64_t nl_launch_count(nl_ctx *ctx);
    that FP32 cannot decide, and the cut items of the barycenter and overlap balls (their
    whole / empty choice is certified in FP32, their regions are whole triangles).  The
    boundary kernel queues them and a second kernel integrates the queue with every lane
-   busy.  A full queue (capacity E/16, at least 4096) leaves the excess to the boundary
+   busy.  A full queue (capacity E/4, at least 4096) leaves the excess to the boundary
    kernel's own lanes; nl_assemble then runs the numeric phase again with a queue that holds
    every item and keeps it for the plan's re-assemblies (NL_DEFER_CAP in the environment
-   fixes the capacity instead, 0 disables the queue).  Each warp queues its items in (pair,
+   fixes the capacity instead, 0 disables the queue; NL_DEFER_CAP_INIT sets the first one).  Each warp queues its items in (pair,
    outer point) order and a merge kernel adds the items of a pair onto it in that order (no
    atomics); the boundary kernel sums the other items of a pair in fixed point (order-free).
    So run to run the FP32-path pair blocks repeat exactly, except the singular kernel's

@@ -156,6 +156,12 @@ inline int nl_near_cap(int64_t E)
         const long long c = strtoll(v, nullptr, 10);
         return c < 0 ? 0 : (int)(c > (1ll << 30) ? (1ll << 30) : c);
     }
+    // NL_NEAR_CAP_INIT: the first capacity only (a full queue still grows, for tests)
+    const char *w = getenv("NL_NEAR_CAP_INIT");
+    if (w && *w) {
+        const long long c = strtoll(w, nullptr, 10);
+        return c < 1 ? 1 : (int)(c > (1ll << 30) ? (1ll << 30) : c);
+    }
     int64_t c = 2 * E;
     if (c < 4096) c = 4096;
     if (c > (int64_t(1) << 30)) c = int64_t(1) << 30;
@@ -173,8 +179,11 @@ nl_status nl_cuda_fail(nl_ctx *ctx, cudaError_t e, const char *what);
     } while (0)
 
 // capacity of a deferred-item queue for E candidate pairs: the FP64 items are a small
-// fraction of the exact items (about 0.1 % on jittered meshes); a full queue only sends
-// the excess back to the boundary kernel's own lanes
+// fraction of the exact items on jittered meshes (about 0.1 %), but rules with outer points on
+// the triangles' vertices and edges (the paper's 7-point rule) put x_q on vertices of its
+// neighbours, whose orientations FP32 cannot certify (1.35 M items for E = 10 M on the
+// uniform Table 1 grid h = 0.0125); a full queue sends the excess back to the boundary
+// kernel's own lanes (and nl_assemble to a second numeric run with a larger queue)
 // is the capacity of the deferred-item queue set by NL_DEFER_CAP (fixed, for tests)?
 inline bool nl_defer_cap_fixed()
 {
@@ -190,7 +199,13 @@ inline int nl_defer_cap(int64_t E)
         const long long c = strtoll(v, nullptr, 10);
         return c < 0 ? 0 : (int)(c > (1ll << 24) ? (1ll << 24) : c);
     }
-    int64_t c = E / 16;
+    // NL_DEFER_CAP_INIT: the first capacity only (a full queue still grows, for tests)
+    const char *w = getenv("NL_DEFER_CAP_INIT");
+    if (w && *w) {
+        const long long c = strtoll(w, nullptr, 10);
+        return c < 1 ? 1 : (int)(c > (1ll << 24) ? (1ll << 24) : c);
+    }
+    int64_t c = E / 4;
     if (c < 4096) c = 4096;
     if (c > (int64_t(1) << 24)) c = int64_t(1) << 24;
     return (int)c;

@@ -374,11 +374,13 @@ def test_numeric_reassembly_is_repeatable(nl, ctx, monkeypatch, ball, kernel, pr
 
 @pytest.mark.parametrize("kernel", ["const", "inv_dist"])
 def test_full_queue_reruns_repeatably(nl, ctx, monkeypatch, kernel):
-    # default queue capacities (at least 4096 FP64-decided items): this mesh has more, so the
-    # first numeric run leaves the excess to the boundary kernel's lanes and nl_assemble runs it
-    # again with a queue that holds them all; two assemblies agree to the FP64 atomic order
+    # queues that start with room for 64 items: the first numeric run leaves the excess to the
+    # boundary kernel's lanes and nl_assemble runs it again with queues that hold them all; two
+    # assemblies agree to the FP64 atomic order (and to the oracle)
     monkeypatch.delenv("NL_DEFER_CAP", raising=False)
     monkeypatch.delenv("NL_NEAR_CAP", raising=False)
+    monkeypatch.setenv("NL_DEFER_CAP_INIT", "64")
+    monkeypatch.setenv("NL_NEAR_CAP_INIT", "64")
     p = small_problem("ngon", n=24, kernel=kernel)
     over = dict(duffy_n=4) if kernel == "inv_dist" else {}
     keep = nl._Keep()
@@ -389,8 +391,7 @@ def test_full_queue_reruns_repeatably(nl, ctx, monkeypatch, kernel):
         m = nl.nl_assemble(ctx, mesh, cfg)
         try:
             vals.append(nl.to_scipy(ctx, m))
-            if kernel == "const":
-                assert nl.nl_last_fp64_items(ctx) > 4096
+            assert nl.nl_last_fp64_items(ctx) > 64
         finally:
             nl.nl_csr_free(ctx, m)
     np.testing.assert_array_equal(vals[0].indices, vals[1].indices)
