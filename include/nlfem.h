@@ -218,7 +218,15 @@ nl_status nl_batch_run(nl_ctx *ctx, nl_batch *batch);
 nl_status nl_batch_get_info(const nl_batch *batch, nl_batch_info *info);
 /* Release the handle (not the outs). */
 void nl_batch_destroy(nl_ctx *ctx, nl_batch *batch);
-/* nl_batch_create + nl_batch_destroy: assemble n independent problems. */
+/* Assemble n independent problems once (no handle, no re-assembly graph, no autotuning).
+   Each problem is assembled exactly as nl_assemble assembles it (the same steps and kernels,
+   every kernel of a problem in order on one of the context's eight side streams), pipelined
+   across the problems: where nl_assemble waits on the host (three times a problem), each
+   problem records an event instead, and the host issues a problem's next step once its own
+   event has passed.  So one problem's preparation and symbolic stages run beside other
+   problems' numeric phases.  Returns when every step is enqueued; the context's stream is
+   ordered after all of them.  Errors: those of nl_assemble for the first failing problem
+   (outs all zeroed), NL_EINVAL for n < 1 or null arrays. */
 nl_status nl_assemble_batch(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const nl_config *cfgs,
                             nl_csr *outs);
 
@@ -274,7 +282,8 @@ void nl_csr_free(nl_ctx *ctx, nl_csr *m);
 /* Device time of the phases of the last nl_assemble or nl_batch_create (ms):
    [0] preprocessing + cell list (for a batch: of all problems, plus the autotuner's
    timing runs when it ran), [1] pair geometry + quadrature, [2] symbolic pattern,
-   [3] numeric scatter. */
+   [3] numeric scatter.  After nl_assemble_batch, whose phases overlap, [0..2] are 0 and
+   [3] is the whole batch. */
 nl_status nl_last_timings(nl_ctx *ctx, double *ms4);
 
 /* nl_cg for callers that cannot allocate device memory: a framework that has given all

@@ -397,6 +397,57 @@ nl_status run_numeric(nl_ctx *ctx, nl_plan *P, bool stats, bool one_stream = fal
 
 nl_status nl_run_numeric_one_stream(nl_ctx *ctx, nl_plan *P) { return run_numeric(ctx, P, false, true); }
 
+// The steps of one assembly after the candidate count is known (stage C of the preparation):
+// candidate lists, numeric phase, symbolic stage A; the counts of the queued items and the
+// pattern size go to the host slot.  ev_num / ev_sym (may be null): recorded before and after
+// the numeric phase.  one_stream: every numeric kernel on ctx->stream (the batch's problems).
+nl_status nl_assemble_step_c(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_pat *Q, nl_host_slot *h, nl_csr *out,
+                             bool one_stream, cudaEvent_t ev_num, cudaEvent_t ev_sym)
+{
+    nl_status s;
+    if ((s = nl_prepare_c(ctx, P, T, h)) != NL_OK) return s;
+    if ((s = nl_alloc_numeric(ctx, P)) != NL_OK) return s;
+    if (ev_num) NL_CK(cudaEventRecord(ev_num, ctx->stream));
+    if ((s = run_numeric(ctx, P, false, one_stream)) != NL_OK) return s;
+    if (ev_sym) NL_CK(cudaEventRecord(ev_sym, ctx->stream));
+    h->deferred = 0;
+    h->near = 0;
+    if (P->defer_n) NL_CK(cudaMemcpyAsync(&h->deferred, P->defer_n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    if (P->near_n) NL_CK(cudaMemcpyAsync(&h->near, P->near_n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    return nl_pattern_a(ctx, P, out, Q, h);
+}
+
+// The last steps, once the slot of step C has arrived: checks, a second numeric run if a queue
+// overflowed, symbolic stage B and the scatter.  ev_sct (may be null): recorded before the scatter.
+nl_status nl_assemble_step_d(nl_ctx *ctx, nl_plan *P, nl_pat *Q, const nl_host_slot *h, nl_csr *out,
+                             bool one_stream, cudaEvent_t ev_sct)
+{
+    nl_status s;
+    if ((s = nl_prepare_check(ctx, h)) != NL_OK) return s;
+    // A full queue of FP64-decided or near-field items leaves the excess to the boundary
+    // kernel's lanes, and which items those are depends on the scheduling.  Queues that hold
+    // them all (kept for every re-assembly of this plan) make the values independent of it.
+    const bool dfull = P->defer && h->deferred > P->defer_cap && !nl_defer_cap_fixed();
+    const bool nfull = P->near_n && P->near_cap > 0 && h->near > P->near_cap && !nl_near_cap_fixed();
+    if (dfull) {
+        const int64_t want = (int64_t)h->deferred + h->deferred / 4;
+        P->defer_min = (int)(want > (int64_t(1) << 24) ? (int64_t(1) << 24) : want);
+        nl_free(P->defer, ctx->stream);
+        nl_free(P->defer_n, ctx->stream);
+    }
+    if (nfull) {
+        const int64_t want = (int64_t)h->near + h->near / 4;
+        P->near_min = (int)(want > (int64_t(1) << 30) ? (int64_t(1) << 30) : want);
+        nl_free(P->nearq, ctx->stream);
+        nl_free(P->otab, ctx->stream);
+        nl_free(P->near_n, ctx->stream);
+    }
+    if ((dfull || nfull) && (s = run_numeric(ctx, P, false, one_stream)) != NL_OK) return s;
+    if ((s = nl_pattern_b(ctx, P, out, Q, h)) != NL_OK) return s;
+    if (ev_sct) NL_CK(cudaEventRecord(ev_sct, ctx->stream));
+    return nl_run_scatter(ctx, P, out);
+}
+
 void nl_plan_free(nl_plan *P, cudaStream_t s)
 {
     if (!P) return;
@@ -540,47 +591,10 @@ nl_status nl_assemble(nl_ctx *ctx, const nl_mesh *mesh, const nl_config *cfg, nl
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) goto cuda_fail;
     if ((s = nl_prepare_b(ctx, P, T, h)) != NL_OK) goto fail;
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) goto cuda_fail;
-    if ((s = nl_prepare_c(ctx, P, T, h)) != NL_OK) goto fail;
-    if ((s = nl_alloc_numeric(ctx, P)) != NL_OK) goto fail;
-    if ((e = cudaEventRecord(ctx->ev[1], ctx->stream)) != cudaSuccess) goto cuda_fail;
-    if ((s = run_numeric(ctx, P, false)) != NL_OK) goto fail;
-    if ((e = cudaEventRecord(ctx->ev[2], ctx->stream)) != cudaSuccess) goto cuda_fail;
-    h->deferred = 0;
-    h->near = 0;
-    if (P->defer_n &&
-        (e = cudaMemcpyAsync(&h->deferred, P->defer_n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
-        goto cuda_fail;
-    if (P->near_n &&
-        (e = cudaMemcpyAsync(&h->near, P->near_n, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess)
-        goto cuda_fail;
-    if ((s = nl_pattern_a(ctx, P, out, Q, h)) != NL_OK) goto fail;
+    if ((s = nl_assemble_step_c(ctx, P, T, Q, h, out, false, ctx->ev[1], ctx->ev[2])) != NL_OK) goto fail;
     if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) goto cuda_fail;
     ctx->last_fp64_items = h->deferred;
-    if ((s = nl_prepare_check(ctx, h)) != NL_OK) goto fail;
-    {
-        // A full queue of FP64-decided or near-field items leaves the excess to the boundary
-        // kernel's lanes, and which items those are depends on the scheduling.  Queues that hold
-        // them all (kept for every re-assembly of this plan) make the values independent of it.
-        const bool dfull = P->defer && h->deferred > P->defer_cap && !nl_defer_cap_fixed();
-        const bool nfull = P->near_n && P->near_cap > 0 && h->near > P->near_cap && !nl_near_cap_fixed();
-        if (dfull) {
-            const int64_t want = (int64_t)h->deferred + h->deferred / 4;
-            P->defer_min = (int)(want > (int64_t(1) << 24) ? (int64_t(1) << 24) : want);
-            nl_free(P->defer, ctx->stream);
-            nl_free(P->defer_n, ctx->stream);
-        }
-        if (nfull) {
-            const int64_t want = (int64_t)h->near + h->near / 4;
-            P->near_min = (int)(want > (int64_t(1) << 30) ? (int64_t(1) << 30) : want);
-            nl_free(P->nearq, ctx->stream);
-            nl_free(P->otab, ctx->stream);
-            nl_free(P->near_n, ctx->stream);
-        }
-        if ((dfull || nfull) && (s = run_numeric(ctx, P, false)) != NL_OK) goto fail;
-    }
-    if ((s = nl_pattern_b(ctx, P, out, Q, h)) != NL_OK) goto fail;
-    if ((e = cudaEventRecord(ctx->ev[3], ctx->stream)) != cudaSuccess) goto cuda_fail;
-    if ((s = nl_run_scatter(ctx, P, out)) != NL_OK) goto fail;
+    if ((s = nl_assemble_step_d(ctx, P, Q, h, out, false, ctx->ev[3])) != NL_OK) goto fail;
     if ((e = cudaEventRecord(ctx->ev[4], ctx->stream)) != cudaSuccess) goto cuda_fail;
     nl_prep_delete(T, ctx->stream);
     nl_pat_delete(Q, ctx->stream);

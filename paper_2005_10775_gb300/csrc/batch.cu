@@ -22,7 +22,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <new>
+#include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -485,6 +488,147 @@ nl_status phase_check(nl_ctx *ctx, nl_batch *b, const char *phase)
     return NL_OK;
 }
 
+// nl_assemble_batch: each problem's assembly exactly as nl_assemble performs it (the same steps,
+// every kernel of a problem in order on one of the context's side streams), pipelined across
+// the problems.  The problems are dealt to the streams costliest first, each to the stream with
+// the least cost so far (cost K^2 delta^2: candidate pairs on a mesh of the unit square's scale),
+// and issued in that order.  nl_assemble waits on the host three times (the
+// candidate-search grid, the candidate count, the pattern size); here each problem records an
+// event after each of those steps, and the host polls the events and issues a problem's next
+// step as soon as its own values have arrived.  So one problem's preparation and symbolic
+// stages (small, latency-bound kernels) run beside other problems' numeric phases instead of
+// the whole batch waiting at each synchronisation.  No autotuning and no re-assembly graph
+// (nl_batch_create builds those).
+nl_status assemble_pipelined(nl_ctx *ctx, int n, const nl_mesh *meshes, const nl_config *cfgs, nl_csr *outs)
+{
+    nl_status s = nl_side_streams(ctx);
+    if (s != NL_OK) return s;
+    cudaStream_t st = ctx->stream;
+    const int ns = nl_ctx::kSideStreams;
+    std::vector<nl_prep *> T(n, nullptr);
+    std::vector<nl_pat *> Q(n, nullptr);
+    std::vector<cudaEvent_t> ev(n, nullptr);
+    std::vector<int> step(n, 0), sidx(n, 0), order(n);
+    {
+        std::vector<double> cost(n), load(ns, 0.0);
+        for (int i = 0; i < n; i++) {
+            order[i] = i;
+            const double K = (double)meshes[i].nt, d = cfgs[i].delta;
+            cost[i] = K * K * d * d;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        for (int i : order) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            sidx[i] = k;
+            load[k] += cost[i];
+        }
+    }
+    nl_host_slot *h = nullptr;
+    int fail_at = -1;
+    bool forked = false;
+    auto finish = [&](nl_status code) {
+        ctx->stream = st;
+        if (forked)   // the context's stream continues after every side stream
+            for (int k = 0; k < ns; k++) {
+                cudaError_t e = cudaEventRecord(ctx->side_ev[k], ctx->side[k]);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->side_ev[k], 0);
+                if (e != cudaSuccess) cudaStreamSynchronize(ctx->side[k]);
+            }
+        if (code != NL_OK) cudaStreamSynchronize(st);
+        for (int i = 0; i < n; i++) {
+            nl_prep_delete(T[i], st);
+            nl_pat_delete(Q[i], st);
+            if (ev[i]) cudaEventDestroy(ev[i]);
+            if (code != NL_OK) {
+                nl_csr_free(ctx, &outs[i]);
+            } else if (outs[i].priv) {
+                ((nl_plan *)outs[i].priv)->stream = st;   // the plans' buffers are freed on the context's stream
+            }
+        }
+        if (code != NL_OK && fail_at >= 0) ctx->err = "problem " + std::to_string(fail_at) + ": " + ctx->err;
+        return code;
+    };
+    if ((s = nl_host_slots(ctx, n, &h)) != NL_OK) return finish(s);
+    for (int i = 0; i < n; i++) {
+        nl_plan *P = new (std::nothrow) nl_plan();
+        T[i] = nl_prep_new();
+        Q[i] = nl_pat_new();
+        if (!P || !T[i] || !Q[i]) {
+            delete P;
+            return finish(nl_fail(ctx, NL_ENOMEM, "host allocation failed"));
+        }
+        outs[i].priv = P;
+        if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            ev[i] = nullptr;
+            return finish(nl_fail(ctx, NL_ECUDA, "cudaEventCreate"));
+        }
+    }
+    // the phases overlap: nl_last_timings reports the whole batch as its last phase
+    for (int k = 0; k < 4; k++)
+        if (cudaEventRecord(ctx->ev[k], st) != cudaSuccess) return finish(nl_fail(ctx, NL_ECUDA, "cudaEventRecord"));
+    if (cudaEventRecord(ctx->side_ev[ns], st) != cudaSuccess) return finish(nl_fail(ctx, NL_ECUDA, "cudaEventRecord"));
+    for (int k = 0; k < ns; k++)
+        if (cudaStreamWaitEvent(ctx->side[k], ctx->side_ev[ns], 0) != cudaSuccess)
+            return finish(nl_fail(ctx, NL_ECUDA, "cudaStreamWaitEvent"));
+    forked = true;
+    // step k of problem i (k = 0 .. 3); the steps before 3 end with an event
+    auto issue = [&](int i) -> nl_status {
+        ctx->stream = ctx->side[sidx[i]];
+        nl_plan *P = (nl_plan *)outs[i].priv;
+        nl_status r = NL_OK;
+        switch (step[i]) {
+        case 0: r = nl_prepare_a(ctx, &meshes[i], &cfgs[i], P, T[i], &h[i]); break;
+        case 1: r = nl_prepare_b(ctx, P, T[i], &h[i]); break;
+        case 2: r = nl_assemble_step_c(ctx, P, T[i], Q[i], &h[i], &outs[i], true, nullptr, nullptr); break;
+        default:
+            r = nl_assemble_step_d(ctx, P, Q[i], &h[i], &outs[i], true, nullptr);
+            if (r == NL_OK) {
+                nl_prep_delete(T[i], ctx->stream);
+                nl_pat_delete(Q[i], ctx->stream);
+                T[i] = nullptr;
+                Q[i] = nullptr;
+            }
+        }
+        if (r == NL_OK && step[i] < 3 && cudaEventRecord(ev[i], ctx->stream) != cudaSuccess)
+            r = nl_fail(ctx, NL_ECUDA, "cudaEventRecord");
+        ctx->stream = st;
+        step[i]++;
+        return r;
+    };
+    for (int i : order)
+        if ((s = issue(i)) != NL_OK) {
+            fail_at = i;
+            return finish(s);
+        }
+    int64_t fp64_items = 0;
+    for (;;) {
+        int open = 0;
+        bool moved = false;
+        for (int i : order) {
+            if (step[i] > 3) continue;
+            open++;
+            const cudaError_t q = cudaEventQuery(ev[i]);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                fail_at = i;
+                return finish(nl_cuda_fail(ctx, q, "a batch problem's stream"));
+            }
+            if (step[i] == 3) fp64_items += h[i].deferred;
+            if ((s = issue(i)) != NL_OK) {
+                fail_at = i;
+                return finish(s);
+            }
+            moved = true;
+        }
+        if (!open) break;
+        if (!moved) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    s = finish(NL_OK);
+    if (cudaEventRecord(ctx->ev[4], st) != cudaSuccess) return nl_fail(ctx, NL_ECUDA, "cudaEventRecord");
+    ctx->last_fp64_items = fp64_items;
+    return s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -788,11 +932,18 @@ void nl_batch_destroy(nl_ctx *ctx, nl_batch *b)
 
 nl_status nl_assemble_batch(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const nl_config *cfgs, nl_csr *outs)
 {
-    nl_batch *b = nullptr;
-    nl_status s = nl_batch_create(ctx, n, meshes, cfgs, outs, 0, &b);
-    if (s != NL_OK) return s;
-    nl_batch_destroy(ctx, b);
-    return NL_OK;
+    if (!ctx) return NL_EINVAL;
+    if (n < 1 || !meshes || !cfgs || !outs) return nl_fail(ctx, NL_EINVAL, "need n >= 1 and non-null arrays");
+    nl_status s;
+    for (int i = 0; i < n; i++) {
+        if ((s = nl_validate(ctx, &meshes[i], &cfgs[i])) != NL_OK) {
+            ctx->err = "problem " + std::to_string(i) + ": " + ctx->err;
+            return s;
+        }
+    }
+    NL_CK(cudaSetDevice(ctx->device));
+    for (int i = 0; i < n; i++) memset(&outs[i], 0, sizeof outs[i]);
+    return assemble_pipelined(ctx, n, meshes, cfgs, outs);
 }
 
 }  // extern "C"

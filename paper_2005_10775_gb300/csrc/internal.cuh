@@ -273,6 +273,13 @@ nl_status nl_alloc_numeric(nl_ctx *ctx, nl_plan *P);
 // call allocates the problem's FP64-item and near-field queues
 nl_status nl_run_numeric_one_stream(nl_ctx *ctx, nl_plan *P);
 nl_status nl_run_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out);
+// the steps of nl_assemble after the preparation's stage B (api.cu): C = stage C, numeric phase,
+// symbolic stage A (slot: queue counts, pattern size); D (slot C read) = checks, a second numeric
+// run if a queue overflowed, symbolic stage B, scatter.  Events (may be null) mark the phases.
+nl_status nl_assemble_step_c(nl_ctx *ctx, nl_plan *P, nl_prep *T, nl_pat *Q, nl_host_slot *h, nl_csr *out,
+                             bool one_stream, cudaEvent_t ev_num, cudaEvent_t ev_sym);
+nl_status nl_assemble_step_d(nl_ctx *ctx, nl_plan *P, nl_pat *Q, const nl_host_slot *h, nl_csr *out,
+                             bool one_stream, cudaEvent_t ev_sct);
 
 // ---- batched scatter (pattern.cu): the scatter of every problem of a batch ----
 struct ScatterArgs {   // one problem

@@ -217,3 +217,44 @@ def test_batch_each_schedule_family(nl, ctx, mixed, flags):
         for o in outs:
             nl.nl_csr_free(ctx, o)
 
+
+
+def test_assemble_batch_pipelined_matches_single_assembly(nl, ctx, mixed):
+    # nl_assemble_batch: each problem's nl_assemble steps, pipelined over the side streams;
+    # the same interaction set and pattern as nl_assemble, values to the FP64 atomic order
+    outs = nl.nl_assemble_batch(ctx, mixed["meshes"], mixed["cfgs"])
+    try:
+        for (p, prec), mesh, cfg, out in zip(mixed["probs"], mixed["meshes"], mixed["cfgs"], outs):
+            single = nl.nl_assemble(ctx, mesh, cfg)
+            try:
+                S = nl.to_scipy(ctx, single)
+                st = (single.n_pairs, single.n_qp_pairs, single.n_inter)
+            finally:
+                nl.nl_csr_free(ctx, single)
+            B = nl.to_scipy(ctx, out)
+            assert (out.n_pairs, out.n_qp_pairs, out.n_inter) == st
+            np.testing.assert_array_equal(B.indptr, S.indptr)
+            np.testing.assert_array_equal(B.indices, S.indices)
+            tol = 1e-13 if (prec == "fp64" or p.kernel == "const") else 1e-6
+            assert np.abs(B.data - S.data).max() <= tol * np.abs(S.data).max()
+        ref = O.assemble(mixed["probs"][0][0].mesh, oracle_cfg(mixed["probs"][0][0]))
+        compare(nl.to_scipy(ctx, outs[0]), O.to_csr(ref), TOL[mixed["probs"][0][1]])
+    finally:
+        for o in outs:
+            nl.nl_csr_free(ctx, o)
+
+
+def test_assemble_batch_pipelined_rejects_a_bad_problem(nl, ctx):
+    keep = nl._Keep()
+    good = I.split_square_mesh(-0.1, 1.1, 24, jitter=0.2, seed=3)
+    bad = I.Mesh(vx=good.vx, vy=good.vy, tri=good.tri[:, ::-1].copy(), node_in_omega=good.node_in_omega,
+                 elem_in_omega=good.elem_in_omega, h=good.h, lo=good.lo, hi=good.hi, n=good.n)
+    p = I.Problem("g", good, 0.1, "const", I.const_kernel_c(0.1), "nocaps", "dunavant7", "dunavant7")
+    meshes = [nl.make_mesh(good, keep), nl.make_mesh(bad, keep), nl.make_mesh(good, keep)]
+    cfgs = [nl.config_of(p, keep, prec="fp32c") for _ in range(3)]
+    with pytest.raises(nl.NlError) as e:
+        nl.nl_assemble_batch(ctx, meshes, cfgs)
+    assert e.value.status == nl.NL_EGEOM
+    assert "problem 1" in str(e.value)
+    out = nl.nl_assemble(ctx, meshes[0], cfgs[0])   # the context stays usable
+    nl.nl_csr_free(ctx, out)
