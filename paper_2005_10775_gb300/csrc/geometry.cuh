@@ -610,10 +610,22 @@ __device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, cons
 // ---------------------------------------------------------------------------
 constexpr int kBallCap = 16;   // FP32 region vertices (nocaps <= 6; approxcaps 6 + 3 (m - 1))
 
-// The certified FP32 walk itself: the walk points W (relative to x), their tags (0 vertex, 1
-// entry, 2 exit) and the count of vertices inside; returns the number of walk points (at most 6),
-// or -1 when a choice is not certain.
-__device__ __forceinline__ int ball_walk_f32(const F2 d[3], const GeoParams &g, F2 W[6], int tag[6], int *n_in)
+// Element k of the calling lane in a shared-memory array laid out [slot][32 lanes] (a column per
+// lane: the lanes of a warp never share a bank).  The FP32 regions below keep their vertex lists
+// in the lane's column of the clip buffer: arrays indexed by a run-time count would live in
+// local memory, which the shared-memory carve-out leaves little L1 for.
+struct Col {
+    float *p;
+    __device__ __forceinline__ float &operator[](int k) const { return p[k << 5]; }
+};
+// slot k of a ClipBuf coordinate array read flat (16 slots: [2][8])
+__device__ __forceinline__ Col col(float (&a)[2][kClipCap][32], int lane) { return Col{&a[0][0][lane]}; }
+
+// The certified FP32 walk itself: the walk points W (relative to x) into wx / wy, their tags (0
+// vertex, 1 entry, 2 exit; two bits a point in *tags) and the count of vertices inside; returns the
+// number of walk points (at most 6), or -1 when a choice is not certain.
+__device__ __forceinline__ int ball_walk_f32(const F2 d[3], const GeoParams &g, Col wx, Col wy, unsigned *tags,
+                                             int *n_in)
 {
     const float delta = g.deltaf, d2f = delta * delta;
     bool ins[3];
@@ -627,10 +639,11 @@ __device__ __forceinline__ int ball_walk_f32(const F2 d[3], const GeoParams &g, 
         nin += ins[i];
     }
     int n = 0;
+    unsigned tg = 0;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         const F2 p = d[i], q = d[(i + 1) % 3];
-        if (ins[i]) { W[n] = p; tag[n] = 0; n++; }
+        if (ins[i]) { wx[n] = p.x; wy[n] = p.y; n++; }   // tag 0
         const bool qin = ins[(i + 1) % 3];
         if (ins[i] && qin) continue;
         const float ex = q.x - p.x, ey = q.y - p.y;
@@ -656,55 +669,75 @@ __device__ __forceinline__ int ball_walk_f32(const F2 d[3], const GeoParams &g, 
         float l1 = __fdividef(tt, a), l2 = __fdividef(c, tt);
         if (l1 > l2) { const float z = l1; l1 = l2; l2 = z; }
         if (nr == 2 || !ins[i]) {   // entry at the smaller root
-            W[n].x = p.x + l1 * ex; W[n].y = p.y + l1 * ey; tag[n] = 1; n++;
+            wx[n] = p.x + l1 * ex; wy[n] = p.y + l1 * ey; tg |= 1u << (2 * n); n++;
         }
         if (nr == 2 || ins[i]) {    // exit at the larger root
-            W[n].x = p.x + l2 * ex; W[n].y = p.y + l2 * ey; tag[n] = 2; n++;
+            wx[n] = p.x + l2 * ex; wy[n] = p.y + l2 * ey; tg |= 2u << (2 * n); n++;
         }
     }
+    *tags = tg;
     *n_in = nin;
     return n;
 }
 
+__device__ __forceinline__ unsigned walk_tag(unsigned tags, int k) { return (tags >> (2 * k)) & 3u; }
+
+// the unit-radius-delta point in the direction of u (the normalised sum of two arc points)
+__device__ __forceinline__ F2 arc_dir(float ux, float uy, float delta)
+{
+    const float sc = delta * rsqrtf(ux * ux + uy * uy);
+    return F2{ux * sc, uy * sc};
+}
+
+// FP32 region (nocaps, approxcaps) of T_b (d relative to x) in the lane's clip-buffer columns:
+// the polygon's vertices in x / y slots 0 .. n-1 (approxcaps keeps the walk points in the e
+// slots 0-5 and 8-13).  Returns n, 0 for an empty or degenerate region, -1 when a choice is not
+// certain (or an approxcaps level above 2, left to the FP64 geometry).
 template <int BALL>
-__device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g, F2 P[kBallCap], int *kind)
+__device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g, ClipBuf &cb, int lane, int *kind)
 {
     const float delta = g.deltaf;
-    F2 W[6];
-    int tag[6], nin;
-    const int n = ball_walk_f32(d, g, W, tag, &nin);
-    if (n < 0) return -1;
+    const Col px = col(cb.x, lane), py = col(cb.y, lane);
+    unsigned tags;
+    int nin;
     if (BALL == NL_BALL_NOCAPS) {
+        const int n = ball_walk_f32(d, g, px, py, &tags, &nin);
+        if (n < 0) return -1;
         if (n < 3) return 0;
-        for (int i = 0; i < n; i++) P[i] = W[i];
         *kind = (nin == 3 && n == 3) ? KIND_WHOLE : KIND_PARTIAL;
         return n;
     }
-    // approxcaps
+    // approxcaps: the walk, then the dyadic arc points between every exit and the next entry
+    const Col ex = col(cb.e, lane);
+    const Col wx = ex, wy = Col{ex.p + (8 << 5)};
+    const int n = ball_walk_f32(d, g, wx, wy, &tags, &nin);
+    if (n < 0) return -1;
     if (n < 2) return 0;
-    const int level = g.cap_level, per = (1 << level) - 1;
+    const int level = g.cap_level;
+    if (level > 2) return -1;
+    const int per = (1 << level) - 1;
     int m = 0;
     for (int i = 0; i < n; i++) {
-        const int j = (i + 1) % n;
+        const int j = i + 1 < n ? i + 1 : 0;
         if (m + 1 > kBallCap) return -1;
-        P[m++] = W[i];
-        if (tag[i] == 2 && tag[j] == 1) {
+        const float x0 = wx[i], y0 = wy[i];
+        px[m] = x0;
+        py[m] = y0;
+        m++;
+        if (walk_tag(tags, i) == 2 && walk_tag(tags, j) == 1 && level > 0) {
             if (m + per > kBallCap) return -1;
-            // dyadic bisection of the arc from W[i] to W[j]: point k of 2^level sub-arcs is
-            // built from its two neighbours of the coarser level
-            F2 pts[kBallCap + 1];
-            pts[0] = W[i];
-            pts[1 << level] = W[j];
-            for (int l = level - 1; l >= 0; l--) {
-                const int step = 1 << l;
-                for (int k = step; k < (1 << level); k += 2 * step) {
-                    const float ux = pts[k - step].x + pts[k + step].x, uy = pts[k - step].y + pts[k + step].y;
-                    const float sc = delta * rsqrtf(ux * ux + uy * uy);
-                    pts[k].x = ux * sc;
-                    pts[k].y = uy * sc;
-                }
+            // dyadic bisection of the arc from W[i] to W[j]: each new point from its two
+            // neighbours of the coarser level
+            const float x1 = wx[j], y1 = wy[j];
+            const F2 mid = arc_dir(x0 + x1, y0 + y1, delta);
+            if (level == 1) {
+                px[m] = mid.x; py[m] = mid.y; m++;
+            } else {
+                const F2 q1 = arc_dir(x0 + mid.x, y0 + mid.y, delta), q3 = arc_dir(mid.x + x1, mid.y + y1, delta);
+                px[m] = q1.x; py[m] = q1.y; m++;
+                px[m] = mid.x; py[m] = mid.y; m++;
+                px[m] = q3.x; py[m] = q3.y; m++;
             }
-            for (int k = 1; k < (1 << level); k++) P[m++] = pts[k];
         }
     }
     if (m < 3) return 0;
@@ -717,21 +750,25 @@ __device__ __forceinline__ int ball_region_f32(const F2 d[3], const GeoParams &g
 // each integrated by one point at its centroid with weight its area, as the FP64 cap rule (the
 // area delta^2 (2 th - sin 2 th) / 2, or / 4 with the printed weight, th = asin(chord / 2 delta);
 // the series of 2 th - sin 2 th below 2 th = 0.5, where the difference loses FP32 digits).
-// Coordinates relative to x.  Returns the polygon's vertex count (0 when under three points),
-// -1 when the walk is not certain; *ncap caps in C (centroid) and Cw (area).
-__device__ __forceinline__ int exactcaps_region_f32(const F2 d[3], const GeoParams &g, F2 P[6], F2 C[3], float Cw[3],
+// Coordinates relative to x, in the lane's clip-buffer columns: the polygon in x / y slots 0-5,
+// the caps' centroids in x / y slots 8-10 and their areas in e slots 0-2.  Returns the polygon's
+// vertex count (0 when under three points), -1 when the walk is not certain; *ncap caps.
+__device__ __forceinline__ int exactcaps_region_f32(const F2 d[3], const GeoParams &g, ClipBuf &cb, int lane,
                                                     int *ncap, int *kind)
 {
-    int tag[6], nin;
-    const int n = ball_walk_f32(d, g, P, tag, &nin);
+    const Col px = col(cb.x, lane), py = col(cb.y, lane), pe = col(cb.e, lane);
+    unsigned tags;
+    int nin;
+    const int n = ball_walk_f32(d, g, px, py, &tags, &nin);
     *ncap = 0;
     if (n < 0) return -1;
     if (n < 2) return 0;
     const float delta = g.deltaf;
+    int nc = 0;
     for (int i = 0; i < n; i++) {
         const int j = i + 1 < n ? i + 1 : 0;
-        if (!(tag[i] == 2 && tag[j] == 1) || *ncap >= 3) continue;
-        const F2 e = P[i], f = P[j];
+        if (!(walk_tag(tags, i) == 2 && walk_tag(tags, j) == 1) || nc >= 3) continue;
+        const F2 e = {px[i], py[i]}, f = {px[j], py[j]};
         const float cx = f.x - e.x, cy = f.y - e.y;
         const float chord = sqrtf(cx * cx + cy * cy);
         const float th = asinf(fminf(chord / (2.f * delta), 1.f));
@@ -752,15 +789,15 @@ __device__ __forceinline__ int exactcaps_region_f32(const F2 d[3], const GeoPara
         const float dc = tms > 0.f ? 4.f * delta * st * st * st / (3.f * tms) : delta;
         const float mx = 0.5f * (e.x + f.x), my = 0.5f * (e.y + f.y);
         const float im = rsqrtf(mx * mx + my * my);
-        C[*ncap].x = dc * mx * im;
-        C[*ncap].y = dc * my * im;
-        Cw[*ncap] = delta * delta * tms / (g.cap_printed ? 4.f : 2.f);
-        (*ncap)++;
+        px[8 + nc] = dc * mx * im;
+        py[8 + nc] = dc * my * im;
+        pe[nc] = delta * delta * tms / (g.cap_printed ? 4.f : 2.f);
+        nc++;
     }
+    *ncap = nc;
     *kind = (nin == 3 && n == 3) ? KIND_WHOLE : KIND_PARTIAL;
     return n >= 3 ? n : 0;
 }
-
 
 // error of either); otherwise the FP64 test decides.  Returns 0 far, 1 near, -1 undecided.
 __device__ __forceinline__ int near_f32(const F2 dl[3], float diamf, float eta)

@@ -381,74 +381,31 @@ __device__ __forceinline__ void inner_sums(const NumArgs &A, const nlg::Region &
     }
 }
 
-// inner sums over a fanned polygon given in FP32 coordinates relative to x (FP32 path; KIN as
-// for whole_sums)
+// inner sums over a fanned polygon in FP32 coordinates relative to x, held in the lane's columns
+// px / py of a shared buffer (FP32 path; KIN as for whole_sums)
 template <int KIN = -1>
-__device__ __forceinline__ void poly_sums_f32(const NumArgs &A, const nlg::F2 *P, int n, const nlg::F2 &d0,
+__device__ __forceinline__ void poly_sums_col(const NumArgs &A, nlg::Col px, nlg::Col py, int n, const nlg::F2 &d0,
                                               const nlg::F2 &e1, const nlg::F2 &e2, float inv_det,
                                               Sums<float> &S, int64_t &nqp)
 {
     sums_zero(S);
     const int nr = A.inner.n;
     const float kc = A.kcf;
-    auto phi = [&](const nlg::F2 &p, float f[3]) {
-        const float rx = p.x - d0.x, ry = p.y - d0.y;
+    auto phi = [&](float x, float y, float f[3]) {
+        const float rx = x - d0.x, ry = y - d0.y;
         const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
         const float l2 = (e1.x * ry - rx * e1.y) * inv_det;
         f[0] = 1.f - l1 - l2;
         f[1] = l1;
         f[2] = l2;
     };
-    float f0[3], fk[3];
-    phi(P[0], f0);
-    phi(P[1], fk);
-    for (int k = 1; k + 1 < n; k++) {
-        const nlg::F2 s0 = P[0], s1 = P[k], s2 = P[k + 1];
-        const float ar = 0.5f * fabsf((s1.x - s0.x) * (s2.y - s0.y) - (s2.x - s0.x) * (s1.y - s0.y)) * kc;
-        float fn[3];
-        phi(s2, fn);
-        for (int r = 0; r < nr; r++) {
-            const float4 f = A.fin[r];
-            const float m0 = f.x, m1 = f.y, m2 = f.z;
-            const float p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
-            const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
-            const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
-            float w = f.w * ar;
-            if (KIN < 0 ? A.kernel == NL_KERNEL_INV_DIST : KIN == 1) {   // psi = c / |y - x|, relative to x
-                const float yx = m0 * s0.x + m1 * s1.x + m2 * s2.x, yy = m0 * s0.y + m1 * s1.y + m2 * s2.y;
-                w *= rsqrtf(yx * yx + yy * yy);
-            }
-            sums_add<float>(S, w, p0, p1, p2);
-        }
-        nqp += nr;
-        fk[0] = fn[0]; fk[1] = fn[1]; fk[2] = fn[2];
-    }
-}
-
-// inner sums over a fanned polygon held in a shared clip buffer (FP32 path; KIN as for whole_sums)
-template <int KIN = -1>
-__device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBuf &cb, int which, int lane, int n,
-                                             const nlg::F2 &d0, const nlg::F2 &e1, const nlg::F2 &e2, float inv_det,
-                                             Sums<float> &S, int64_t &nqp)
-{
-    sums_zero(S);
-    const int nr = A.inner.n;
-    const float kc = A.kcf;
-    auto phi = [&](float px, float py, float f[3]) {
-        const float rx = px - d0.x, ry = py - d0.y;
-        const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
-        const float l2 = (e1.x * ry - rx * e1.y) * inv_det;
-        f[0] = 1.f - l1 - l2;
-        f[1] = l1;
-        f[2] = l2;
-    };
-    const float x0 = cb.x[which][0][lane], y0 = cb.y[which][0][lane];
-    float xk = cb.x[which][1][lane], yk = cb.y[which][1][lane];
+    const float x0 = px[0], y0 = py[0];
+    float xk = px[1], yk = py[1];
     float f0[3], fk[3];
     phi(x0, y0, f0);
     phi(xk, yk, fk);
     for (int k = 1; k + 1 < n; k++) {
-        const float xn = cb.x[which][k + 1][lane], yn = cb.y[which][k + 1][lane];
+        const float xn = px[k + 1], yn = py[k + 1];
         const float ar = 0.5f * fabsf((xk - x0) * (yn - y0) - (xn - x0) * (yk - y0)) * kc;
         float fn[3];
         phi(xn, yn, fn);
@@ -469,6 +426,17 @@ __device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBu
         fk[0] = fn[0]; fk[1] = fn[1]; fk[2] = fn[2];
         xk = xn; yk = yn;
     }
+}
+
+// the same over buffer `which` of a clip buffer (the N-gon clip's output)
+template <int KIN = -1>
+__device__ __forceinline__ void poly_sums_sh(const NumArgs &A, const nlg::ClipBuf &cb, int which, int lane, int n,
+                                             const nlg::F2 &d0, const nlg::F2 &e1, const nlg::F2 &e2, float inv_det,
+                                             Sums<float> &S, int64_t &nqp)
+{
+    nlg::ClipBuf &c = const_cast<nlg::ClipBuf &>(cb);
+    poly_sums_col<KIN>(A, nlg::Col{&c.x[which][0][lane]}, nlg::Col{&c.y[which][0][lane]}, n, d0, e1, e2, inv_det, S,
+                       nqp);
 }
 
 // FP32 version of the near-singular rule (FP32-compensated path) for the whole triangle
@@ -987,9 +955,8 @@ __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &
         for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
         if (INV && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
             return -1;
-        nlg::F2 P[nlg::kBallCap];
         int k = nlg::KIND_PARTIAL;
-        const int n = nlg::ball_region_f32<BALL>(dl, A.geo, P, &k);
+        const int n = nlg::ball_region_f32<BALL>(dl, A.geo, cb, lane, &k);
         if (n >= 0) {
             // certified FP32 walk: same vertex count and kind as the FP64 walk
             if (n < 3) return 0;
@@ -1001,7 +968,8 @@ __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &
                 whole_sums<T, INV>(A, Vb, cand_akc<T>(A, c), D2{o.x, o.y}, S, nq, dl);
             } else {
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
-                poly_sums_f32<INV>(A, P, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
+                poly_sums_col<INV>(A, nlg::col(cb.x, lane), nlg::col(cb.y, lane), n, dl[0], e1, e2, c.binv,
+                                   *(Sums<float> *)&S, nq);
             }
             return 1;
         }
@@ -1011,10 +979,9 @@ __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &
         for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
         if (INV && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
             return -1;
-        nlg::F2 P[6], C[3];
-        float Cw[3];
         int nc = 0, k = nlg::KIND_PARTIAL;
-        const int n = nlg::exactcaps_region_f32(dl, A.geo, P, C, Cw, &nc, &k);
+        const int n = nlg::exactcaps_region_f32(dl, A.geo, cb, lane, &nc, &k);
+        const nlg::Col px = nlg::col(cb.x, lane), py = nlg::col(cb.y, lane), pe = nlg::col(cb.e, lane);
         if (n >= 0) {
             // certified FP32 walk: the vertex count, the caps and the kind of the FP64 region
             if (n < 3 && nc == 0) return 0;
@@ -1027,13 +994,14 @@ __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &
             } else {
                 Sums<float> &Sf = *(Sums<float> *)&S;
                 const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
-                if (n >= 3) poly_sums_f32<INV>(A, P, n, dl[0], e1, e2, c.binv, Sf, nq);
+                if (n >= 3) poly_sums_col<INV>(A, px, py, n, dl[0], e1, e2, c.binv, Sf, nq);
                 else sums_zero(Sf);
                 for (int j = 0; j < nc; j++) {   // one point per cap: its centroid, weight its area
-                    const float rx = C[j].x - dl[0].x, ry = C[j].y - dl[0].y;
+                    const float cx = px[8 + j], cy = py[8 + j];
+                    const float rx = cx - dl[0].x, ry = cy - dl[0].y;
                     const float l1 = (rx * e2.y - e2.x * ry) * c.binv, l2 = (e1.x * ry - rx * e1.y) * c.binv;
-                    float w = Cw[j] * A.kcf;
-                    if (INV) w *= rsqrtf(C[j].x * C[j].x + C[j].y * C[j].y);
+                    float w = pe[j] * A.kcf;
+                    if (INV) w *= rsqrtf(cx * cx + cy * cy);
                     sums_add<float>(Sf, w, 1.f - l1 - l2, l1, l2);
                     nq++;
                 }
@@ -1518,7 +1486,7 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
 // certified FP32 walk, else the FP64 walk), fanned from its first point; the outer rule runs on
 // every subtriangle with phi_a taken at each outer point.  One record per pair with a non-empty S.
 template <int BALL, typename T>
-__device__ __forceinline__ void support_boundary(const NumArgs &A, int a, int lane, LaneAcc &acc)
+__device__ __forceinline__ void support_boundary(const NumArgs &A, int a, int lane, nlg::ClipBuf &cb, LaneAcc &acc)
 {
     constexpr int DISC = (BALL == NL_BALL_BARY_NOCAPS) ? NL_BALL_NOCAPS : NL_BALL_APPROXCAPS;
     const int K = A.K;
@@ -1550,16 +1518,16 @@ __device__ __forceinline__ void support_boundary(const NumArgs &A, int a, int la
             const float cbx = (float)(bb.x - ba.x), cby = (float)(bb.y - ba.y);
             nlg::F2 d[3];   // T_a relative to bary_b
             for (int i = 0; i < 3; i++) { d[i].x = va[i].x - cbx; d[i].y = va[i].y - cby; }
-            nlg::F2 P[nlg::kBallCap];
             int k = nlg::KIND_PARTIAL;
-            const int n = nlg::ball_region_f32<DISC>(d, A.geo, P, &k);
+            const int n = nlg::ball_region_f32<DISC>(d, A.geo, cb, lane, &k);
             if (n >= 0) {
                 done = true;
                 if (n >= 3) {
                     kind = k;
                     nv = n;
+                    const nlg::Col px = nlg::col(cb.x, lane), py = nlg::col(cb.y, lane);
                     for (int t = 1; t + 1 < n; t++) {
-                        const nlg::F2 s0 = P[0], s1 = P[t], s2 = P[t + 1];
+                        const nlg::F2 s0 = {px[0], py[0]}, s1 = {px[t], py[t]}, s2 = {px[t + 1], py[t + 1]};
                         const float ar = 0.5f * fabsf((s1.x - s0.x) * (s2.y - s0.y) - (s2.x - s0.x) * (s1.y - s0.y));
                         for (int q = q0; q < q1; q++) {
                             const float4 f = A.fout[q];
@@ -1625,8 +1593,7 @@ template <int BALL, typename T, bool INV, bool NQ = false, int STS = -1>
 __device__ __forceinline__ void boundary_any(const NumArgs &A, int a, BoundaryShared<T> &sh, int lane, LaneAcc &acc)
 {
     if constexpr (BALL == NL_BALL_BARY_NOCAPS || BALL == NL_BALL_BARY_APPROXCAPS) {
-        (void)sh;
-        support_boundary<BALL, T>(A, a, lane, acc);
+        support_boundary<BALL, T>(A, a, lane, sh.clip, acc);
     } else {
         stage_outer(A, a, sh.sq, lane);
         __syncwarp();
