@@ -548,7 +548,7 @@ constexpr int kWarpsPerBlock = 4;
 struct LaneAcc {
     double maa[6];
     float mf[6], mc[6];
-    int64_t cnt, qp;
+    uint32_t cnt, qp;   // per outer triangle and lane: far below 2^32
     uint64_t hsum;
 };
 
@@ -1798,15 +1798,140 @@ __device__ __forceinline__ bool warp_run_sum(long long key, int lane, V *v)
 // ---------------------------------------------------------------------------
 // Near-field whole items of the FP32 singular kernel (after the boundary launch, in stream
 // order): the boundary kernel queues every (x_q, T_b) whose whole T_b lies in the near field of
-// x_q (certified in FP32), in (pair, outer point) order; here each lane takes one and runs the
-// near-singular rule (signed apex-x decomposition, Duffy collapse, sinh substitution) on it.
-// The blocks are summed over the lanes of one pair (M_ab onto the pair's stored values with
+// x_q (certified in FP32), in (pair, outer point) order; here each warp takes 32 of them and
+// runs the near-singular rule (signed apex-x decomposition, Duffy collapse, sinh substitution,
+// as near_whole_f32) with its lanes spread over the items' panels instead of the items: the
+// items have 3 to 30 panels (11 on average at the singular workload), so a lane per item left
+// most lanes idle while the longest item ran.  A lane per item first sets up its six sides
+// (two per edge: panel count, U, the scaled foot-point direction) in shared memory; the warp then
+// takes the panels of all 32 items 32 at a time, sums each item's panels by a segmented shuffle
+// tree and adds the sums onto the item's column; a lane per item finally combines its item.  The
+// blocks are then summed over the lanes of one pair (M_ab onto the pair's stored values with
 // FP32 atomics, M_bb onto T_b's sums) and of one outer triangle (M_aa, statistics), so a warp
 // issues a few atomics per pair instead of one per item.
 // ---------------------------------------------------------------------------
+struct NearSide {              // one side (edge, end A or B) of a near-field item
+    float gdx, gdy;            // sg d e: the foot point's scaled edge direction
+    float fx, fy;              // foot point F of x on the edge's line, relative to x
+    float kcs;                 // sign sg d kc
+    float u;                   // U = asinh(|t| / d), the last panel's end
+};
+
+struct NearShared {            // per warp
+    NearSide side[6][32];
+    unsigned short npan[6][32];   // up to about 710 on a side (FP64 panel counts)
+    float e1x[32], e1y[32], e2x[32], e2y[32], inv[32], l10[32], l20[32];
+    int start[32];             // first panel of each lane's item in the warp's panel list
+    float acc[10][32];         // each item's sums (s0, s1, S2) over its panels
+};
+
+// the six sides of an item (vertices dl relative to x): panel counts (0 for a degenerate side),
+// by the same FP32 rule with FP64 fallback as near_whole_f32
+__device__ __forceinline__ int near_setup_f32(const NumArgs &A, const nlg::F2 dl[3], int tb, D2 x, NearShared &sh,
+                                              int lane)
+{
+    const float kc = A.kcf;
+    int total = 0;
+    for (int i = 0; i < 3; i++) {
+        const nlg::F2 a = dl[i], b = dl[(i + 1) % 3];
+        float ex = b.x - a.x, ey = b.y - a.y;
+        const float L = sqrtf(ex * ex + ey * ey);
+        ex /= L;
+        ey /= L;
+        const float tA = a.x * ex + a.y * ey, tB = b.x * ex + b.y * ey;
+        const float Fx = a.x - tA * ex, Fy = a.y - tA * ey;
+        const float d = sqrtf(Fx * Fx + Fy * Fy);
+        const float UA = asinhf(fabsf(tA) / d), UB = asinhf(fabsf(tB) / d);
+        const float th = 1e-4f * L;
+        const float M = fmaxf(fmaxf(fabsf(a.x) + fabsf(a.y), fabsf(b.x) + fabsf(b.y)), L) + L;
+        auto near_int = [&](float U, float t) {
+            const float eps = 1e-6f * M * (1.f / d + 1.f / fabsf(t)) + 1e-5f * fmaxf(U, 1.f);
+            return fabsf(U - rintf(U)) < eps;
+        };
+        bool skip_edge = false, skipA = false, skipB = false;
+        int npA, npB;
+        if (!(d >= th) || !(fabsf(tA) >= th) || !(fabsf(tB) >= th) || near_int(UA, tA) || near_int(UB, tB)) {
+            const int i1 = (i + 1) % 3;
+            const D2 Vi = {A.tx[i * A.K + tb], A.ty[i * A.K + tb]}, Vj = {A.tx[i1 * A.K + tb], A.ty[i1 * A.K + tb]};
+            const NearEdge64 q = near_edge64(Vi, Vj, x);
+            skip_edge = (q.d == 0.0);
+            skipA = (q.tA == 0.0);
+            skipB = (q.tB == 0.0);
+            npA = skip_edge || skipA ? 0 : near_panels64(q.tA, q.d);
+            npB = skip_edge || skipB ? 0 : near_panels64(q.tB, q.d);
+        } else {
+            npA = (int)ceilf(UA);
+            npB = (int)ceilf(UB);
+            npA = npA < 1 ? 1 : npA;
+            npB = npB < 1 ? 1 : npB;
+        }
+        if (skip_edge || d == 0.f) npA = npB = 0;
+        if (skipA) npA = 0;
+        if (skipB) npB = 0;
+        const float sigma = (Fx * ey - Fy * ex) > 0.f ? 1.f : -1.f;
+        for (int sd = 0; sd < 2; sd++) {   // side B, then side A
+            const bool sideA = sd == 1;
+            const float tau = sideA ? tA : tB;
+            const float sg = tau > 0.f ? 1.f : -1.f, sign = sideA ? -sigma : sigma;
+            NearSide &S = sh.side[2 * i + sd][lane];
+            S.gdx = sg * d * ex;
+            S.gdy = sg * d * ey;
+            S.fx = Fx;
+            S.fy = Fy;
+            S.kcs = sign * sg * d * kc;
+            S.u = sideA ? UA : UB;
+            const int np = sideA ? npA : npB;
+            sh.npan[2 * i + sd][lane] = (unsigned short)np;
+            total += np;
+        }
+    }
+    return total;
+}
+
+// the item data of a near-field item that its panels use (barycentric frame of T_b)
+struct NearItem {
+    float e1x, e1y, e2x, e2y, inv, l10, l20;
+};
+
+// panel pnl of a side with npan panels (side data sd, item frame it) added onto S
+__device__ __forceinline__ void near_panel_f32(const NumArgs &A, const NearSide &sd, int npan, const NearItem &it,
+                                               int pnl, float S[10])
+{
+    const bool full = pnl + 1 < npan;
+    const float u0 = (float)pnl, hw = full ? 1.f : fmaxf(sd.u, u0) - u0;
+    // on a full panel [p, p + 1], sinh(p + x_j) = sinh(p) cosh(x_j) + cosh(p) sinh(x_j); the last
+    // panel [p, U] evaluates sinh directly
+    float sp = 0.f, cp = 1.f;
+    if (full && pnl > 0) {
+        const float ep = expf(u0), em = 1.f / ep;
+        sp = 0.5f * (ep - em);
+        cp = 0.5f * (ep + em);
+    }
+    const int nu = A.duffy_n;
+    for (int j = 0; j < nu; j++) {
+        const float sh_ = full ? fmaf(sp, A.glf_ch[j], cp * A.glf_sh[j]) : sinhf(u0 + hw * A.glf_x[j]);
+        const float wj = sd.kcs * (hw * A.glf_w[j]);
+        const float wx = fmaf(sh_, sd.gdx, sd.fx), wy = fmaf(sh_, sd.gdy, sd.fy);
+        const float l1w = (wx * it.e2y - it.e2x * wy) * it.inv;
+        const float l2w = (it.e1x * wy - wx * it.e1y) * it.inv;
+        for (int k = 0; k < 2; k++) {
+            const float sv = A.gl2f_x[k];
+            const float l1 = sv * l1w - it.l10, l2 = sv * l2w - it.l20, l0 = 1.f - l1 - l2;
+            const float w = wj * A.gl2f_w[k];
+            const float w0 = w * l0, w1 = w * l1, w2 = w * l2;
+            S[0] += w;
+            S[1] += w0; S[2] += w1; S[3] += w2;
+            S[4] += w0 * l0; S[5] += w1 * l1; S[6] += w2 * l2;
+            S[7] += w0 * l1; S[8] += w0 * l2; S[9] += w1 * l2;
+        }
+    }
+}
+
 template <int BALL>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_near(const NumArgs A)
 {
+    __shared__ NearShared near_sh[kWarpsPerBlock];
+    NearShared &sh = near_sh[threadIdx.x >> 5];
     const int n = min(*A.near_n, A.near_cap);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1814,13 +1939,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_near(const NumArgs A)
     const int K = A.K;
     for (int64_t base = warp0 * 32; base < n; base += nwarps * 32) {
         const int64_t i = base + lane;
-        float w[21];
-        for (int k = 0; k < 21; k++) w[k] = 0.f;
         long long ke = -1, ka = -1;
-        int b = 0, q = 0, q0 = 0;
-        int64_t nq = 0;
+        int b = 0, q = 0, q0 = 0, np = 0;
+        DeferItem d = {0, 0, 0};
+        OuterPt o;
         if (i < n) {
-            const DeferItem d = A.nearq[i];
+            d = A.nearq[i];
             const int a = d.a;
             q = d.qp & 0xff;
 #ifdef NL_CHECKS
@@ -1831,7 +1955,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_near(const NumArgs A)
 #endif
             if (ka != -2) {
                 b = A.nbr_idx[d.e];
-                const OuterPt o = A.otab[(int64_t)a * A.outer.n + q];
+                o = A.otab[(int64_t)a * A.outer.n + q];
                 const D2 ba = {A.bx[a], A.by[a]};
                 CandData c;
                 int q1;
@@ -1839,15 +1963,68 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_near(const NumArgs A)
                 q0 = c.q0;
                 nlg::F2 dl[3];
                 for (int k = 0; k < 3; k++) { dl[k].x = c.vlx[k] - o.lx; dl[k].y = c.vly[k] - o.ly; }
-                Sums<float> S;
-                const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
-                near_whole_f32(A, dl, b, D2{o.x, o.y}, e1, e2, c.binv, S, nq);
-                combine<float>(o, S, w);
-                A.flag[d.e] = 1;
+                sh.e1x[lane] = c.e1x;
+                sh.e1y[lane] = c.e1y;
+                sh.e2x[lane] = c.e2x;
+                sh.e2y[lane] = c.e2y;
+                sh.inv[lane] = c.binv;
+                sh.l10[lane] = (dl[0].x * c.e2y - c.e2x * dl[0].y) * c.binv;
+                sh.l20[lane] = (c.e1x * dl[0].y - dl[0].x * c.e1y) * c.binv;
+                np = near_setup_f32(A, dl, b, D2{o.x, o.y}, sh, lane);
                 ke = d.e;
                 ka = a;
             }
         }
+        // the warp's panel list: item j's panels start at start[j]
+        int incl = np;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        sh.start[lane] = incl - np;
+        for (int k = 0; k < 10; k++) sh.acc[k][lane] = 0.f;
+        __syncwarp();
+        for (int t0 = 0; t0 < total; t0 += 32) {
+            const int t = t0 + lane;
+            float S[10];
+            for (int k = 0; k < 10; k++) S[k] = 0.f;
+            long long key = -1;
+            int it = 0;
+            if (t < total) {
+                // the last item whose panels start at or before t (an item without panels shares
+                // its start with the next one)
+                int lo = 0, hi = 31;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sh.start[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                it = lo;
+                int r = t - sh.start[it], side = 0;
+                while (side < 5 && r >= (int)sh.npan[side][it]) r -= (int)sh.npan[side++][it];
+                const NearItem itd = {sh.e1x[it], sh.e1y[it], sh.e2x[it], sh.e2y[it], sh.inv[it], sh.l10[it],
+                                      sh.l20[it]};
+                near_panel_f32(A, sh.side[side][it], (int)sh.npan[side][it], itd, r, S);
+                key = it;
+            }
+            // the panels of one item are adjacent: one shared add per item and pass
+            if (warp_run_sum<10>(key, lane, S))
+                for (int k = 0; k < 10; k++) sh.acc[k][it] += S[k];
+            __syncwarp();
+        }
+        float w[21];
+        for (int k = 0; k < 21; k++) w[k] = 0.f;
+        int64_t nq = 0;
+        if (ka >= 0) {
+            Sums<float> S;
+            S.s0 = sh.acc[0][lane];
+            for (int k = 0; k < 3; k++) S.s1[k] = sh.acc[1 + k][lane];
+            for (int k = 0; k < 6; k++) S.S2[k] = sh.acc[4 + k][lane];
+            combine<float>(o, S, w);
+            nq = 2 * (int64_t)A.duffy_n * np;
+            A.flag[d.e] = 1;
+        }
+        __syncwarp();
         // M_ab onto the pair, M_bb onto T_b: one add per run of one pair in the warp (a warp's
         // items of one pair are adjacent: the queue holds them in (pair, outer point) order)
         if (warp_run_sum<15>(ke, lane, w)) {
