@@ -888,6 +888,8 @@ struct BoundaryShared {
     // whole items from the front; whole items in the singular kernel's near field from the back
     // (a batch holds at most 32 x n_q items in all)
     unsigned short wqueue[32 * NL_MAXQ];
+    int fstart[32];            // spread fans: first fan triangle of each lane's item in the round's list
+    unsigned char fwhich[32];  // spread fans: the clip buffer that holds each lane's polygon
     nlg::ClipBuf clip;         // per-lane FP32 clip buffers
 };
 
@@ -916,6 +918,69 @@ template <int BALL, typename T>
 __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
                                              int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb,
                                              int lane);
+
+// inner sums over fan triangle k (vertices 0, k, k + 1) of a polygon held in columns px / py, in
+// FP32 coordinates relative to x (FP32 path; KIN as for whole_sums)
+template <int KIN = -1>
+__device__ __forceinline__ void fan_tri_sums(const NumArgs &A, nlg::Col px, nlg::Col py, int k, const nlg::F2 &d0,
+                                             const nlg::F2 &e1, const nlg::F2 &e2, float inv_det, Sums<float> &S)
+{
+    sums_zero(S);
+    const float kc = A.kcf;
+    auto phi = [&](float x, float y, float f[3]) {
+        const float rx = x - d0.x, ry = y - d0.y;
+        const float l1 = (rx * e2.y - e2.x * ry) * inv_det;
+        const float l2 = (e1.x * ry - rx * e1.y) * inv_det;
+        f[0] = 1.f - l1 - l2;
+        f[1] = l1;
+        f[2] = l2;
+    };
+    const float x0 = px[0], y0 = py[0], xk = px[k], yk = py[k], xn = px[k + 1], yn = py[k + 1];
+    float f0[3], fk[3], fn[3];
+    phi(x0, y0, f0);
+    phi(xk, yk, fk);
+    phi(xn, yn, fn);
+    const float ar = 0.5f * fabsf((xk - x0) * (yn - y0) - (xn - x0) * (yk - y0)) * kc;
+    const int nr = A.inner.n;
+    for (int r = 0; r < nr; r++) {
+        const float4 f = A.fin[r];
+        const float m0 = f.x, m1 = f.y, m2 = f.z;
+        const float p0 = m0 * f0[0] + m1 * fk[0] + m2 * fn[0];
+        const float p1 = m0 * f0[1] + m1 * fk[1] + m2 * fn[1];
+        const float p2 = m0 * f0[2] + m1 * fk[2] + m2 * fn[2];
+        float w = f.w * ar;
+        if (KIN < 0 ? A.kernel == NL_KERNEL_INV_DIST : KIN == 1) {   // psi = c / |y - x|, relative to x
+            const float yx = m0 * x0 + m1 * xk + m2 * xn, yy = m0 * y0 + m1 * yk + m2 * yn;
+            w *= rsqrtf(yx * yx + yy * yy);
+        }
+        sums_add<float>(S, w, p0, p1, p2);
+    }
+}
+
+// FP32 region of one undecided (q, b) of the balls whose region is a polygon (N-gon, nocaps,
+// approxcaps), left in the lane's clip-buffer column (buffer *which): 1 with its vertex count n
+// and kind, 0 empty, -1 the FP64 geometry decides (as exact_item_f32)
+template <int BALL, bool INV>
+__device__ __forceinline__ int exact_region_f32(const NumArgs &A, const CandData &c, const OuterPt &o,
+                                                nlg::ClipBuf &cb, int lane, int &n, int &kind, int &which)
+{
+    nlg::F2 dl[3];
+    for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
+    if (INV && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0) return -1;
+    which = 0;
+    if (BALL == NL_BALL_NGON) {
+        bool cut = false;
+        n = nlg::clip_ngon_f32_sh(dl, A.geo.err0, A.geo, cb, lane, &which, &cut);
+        if (n < 0) return -1;
+        if (n < 3) return 0;
+        kind = cut ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
+        return 1;
+    }
+    kind = nlg::KIND_PARTIAL;
+    n = nlg::ball_region_f32<BALL>(dl, A.geo, cb, lane, &kind);
+    if (n < 0) return -1;
+    return n >= 3 ? 1 : 0;
+}
 
 // FP32 region and quadrature of one undecided (q, b): 1 done (S holds its sums), 0 empty
 // region, -1 the FP64 geometry decides (the singular kernel's near field, an uncertified
@@ -1420,7 +1485,74 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         // items: lanes at different items run the same parts of the clip together.  So the order
         // in which their blocks reach an owner's column depends on the scheduling: FP32 sums are
         // integers there (the same for any order), FP64 blocks may differ in their last bits.
-        for (int i = lane; i < nqueue; i += 32) {
+        // FP32 polygon regions of nocaps and the N-gon (constant kernel): a round of 32 items
+        // builds its regions (a lane per item), then the warp spreads the fan triangles of all 32
+        // polygons over its lanes, each adding its triangle's block onto the owner's column
+        // (integer sums: any order), so the lanes stay busy although the fans have 1 to 4
+        // triangles (nocaps boundary kernel of a K = 23328 problem 3.43 -> 2.20 ms; the N-gon's
+        // numeric phase 5.63 -> 5.51 ms).  The approxcaps fans (up to 13 triangles with the arc
+        // points) keep the lane-per-item drain: a triangle's lookup and block add then cost about
+        // as much as its quadrature (2.68 -> 3.08 ms spread).
+        constexpr bool kSpread = sizeof(T) == sizeof(float) && !INV &&
+                                 (BALL == NL_BALL_NOCAPS || BALL == NL_BALL_NGON);
+        if constexpr (kSpread)
+        for (int r0 = 0; r0 < nqueue; r0 += 32) {
+            const int i = r0 + lane;
+            int m = 0, which = 0;
+            if (i < nqueue) {
+                const unsigned it = sh.queue[i];
+                const int own = it >> 8, q = it & 0xff;
+                const CandData &cd = sh.cand[own];
+                const OuterPt &o = sh.sq[q];
+                int n = 0, kind = nlg::KIND_PARTIAL;
+                const int r = exact_region_f32<BALL, INV>(A, cd, o, sh.clip, lane, n, kind, which);
+                if (r > 0) {
+                    m = n - 2;
+                    acc.cnt++;
+                    acc.qp += (uint32_t)(m * A.inner.n);
+                    if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kind, n, 0);
+                } else if (r < 0 && !defer_mark<T>(A, sh, own, q)) {
+                    Sums<T> S;
+                    int64_t nq = 0;
+                    int kd, nv, ncap;
+                    if (exact_item_fp64<BALL, T>(A, cd, o, S, nq, kd, nv, ncap, sh.clip, lane)) {
+                        block_add<T>(o, S, sh.acc, sh.s0q, own, q, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf), A.s0q_grid);
+                        acc.cnt++;
+                        acc.qp += (uint32_t)nq;
+                        if (want_stats<STS>(A)) acc.hsum += nlg::record_hash(a, cd.b, q - cd.q0, kd, nv, ncap);
+                    }
+                }
+            }
+            int incl = m;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            sh.fstart[lane] = incl - m;
+            sh.fwhich[lane] = (unsigned char)which;
+            __syncwarp();
+            for (int t = lane; t < total; t += 32) {
+                int lo = 0, hi = 31;   // the last lane whose triangles start at or before t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sh.fstart[mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                const int k = t - sh.fstart[lo] + 1;
+                const unsigned it = sh.queue[r0 + lo];
+                const int own = it >> 8, q = it & 0xff;
+                const CandData &cd = sh.cand[own];
+                const OuterPt &o = sh.sq[q];
+                const int w = sh.fwhich[lo];
+                const nlg::F2 d0 = {cd.vlx[0] - o.lx, cd.vly[0] - o.ly}, e1 = {cd.e1x, cd.e1y}, e2 = {cd.e2x, cd.e2y};
+                Sums<float> S;
+                fan_tri_sums<INV>(A, nlg::Col{&sh.clip.x[w][0][lo]}, nlg::Col{&sh.clip.y[w][0][lo]}, k, d0, e1, e2,
+                                  cd.binv, S);
+                block_add<float>(o, S, sh.acc, sh.s0q, own, q, fx_scale<INV>(fx_bwa, cd.akcf, A.kcf), A.s0q_grid);
+            }
+            __syncwarp();
+        }
+        for (int i = lane; !kSpread && i < nqueue; i += 32) {
             const unsigned it = sh.queue[i];
             const int own = it >> 8, q = it & 0xff;
             const CandData &cd = sh.cand[own];
