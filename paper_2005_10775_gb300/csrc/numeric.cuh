@@ -1485,16 +1485,16 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         // items: lanes at different items run the same parts of the clip together.  So the order
         // in which their blocks reach an owner's column depends on the scheduling: FP32 sums are
         // integers there (the same for any order), FP64 blocks may differ in their last bits.
-        // FP32 polygon regions of nocaps and the N-gon (constant kernel): a round of 32 items
+        // FP32 polygon regions of the N-gon (either kernel) and nocaps: a round of 32 items
         // builds its regions (a lane per item), then the warp spreads the fan triangles of all 32
         // polygons over its lanes, each adding its triangle's block onto the owner's column
         // (integer sums: any order), so the lanes stay busy although the fans have 1 to 4
         // triangles (nocaps boundary kernel of a K = 23328 problem 3.43 -> 2.20 ms; the N-gon's
-        // numeric phase 5.63 -> 5.51 ms).  The approxcaps fans (up to 13 triangles with the arc
+        // numeric phase 5.63 -> 5.51 ms, with the singular kernel 15.9 -> 14.8 ms).  The fan is
+        // the one the lane-per-item drain integrates (from the polygon's first vertex).  The approxcaps fans (up to 13 triangles with the arc
         // points) keep the lane-per-item drain: a triangle's lookup and block add then cost about
         // as much as its quadrature (2.68 -> 3.08 ms spread).
-        constexpr bool kSpread = sizeof(T) == sizeof(float) && !INV &&
-                                 (BALL == NL_BALL_NOCAPS || BALL == NL_BALL_NGON);
+        constexpr bool kSpread = sizeof(T) == sizeof(float) && (BALL == NL_BALL_NGON || (!INV && BALL == NL_BALL_NOCAPS));
         if constexpr (kSpread)
         for (int r0 = 0; r0 < nqueue; r0 += 32) {
             const int i = r0 + lane;
