@@ -1491,9 +1491,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         // (integer sums: any order), so the lanes stay busy although the fans have 1 to 4
         // triangles (nocaps boundary kernel of a K = 23328 problem 3.43 -> 2.20 ms; the N-gon's
         // numeric phase 5.63 -> 5.51 ms, with the singular kernel 15.9 -> 14.8 ms).  The fan is
-        // the one the lane-per-item drain integrates (from the polygon's first vertex).  The approxcaps fans (up to 13 triangles with the arc
-        // points) keep the lane-per-item drain: a triangle's lookup and block add then cost about
-        // as much as its quadrature (2.68 -> 3.08 ms spread).
+        // the one the lane-per-item drain integrates (from the polygon's first vertex).  The
+        // approxcaps fans (up to 13 triangles with the arc points) keep the lane-per-item drain:
+        // a triangle's lookup and block add then cost about as much as its quadrature (2.68 ->
+        // 3.08 ms spread; tasks of two to five triangles of one fan did not pay either).
         constexpr bool kSpread = sizeof(T) == sizeof(float) && (BALL == NL_BALL_NGON || (!INV && BALL == NL_BALL_NOCAPS));
         if constexpr (kSpread)
         for (int r0 = 0; r0 < nqueue; r0 += 32) {
