@@ -1110,6 +1110,12 @@ __device__ __noinline__ bool exact_item_fp64(const NumArgs &A, const CandData &c
         const nlg::F2 d0 = {(float)(Vb[0].x - x.x), (float)(Vb[0].y - x.y)};
         const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
         poly_sums_sh(A, cb, 0, lane, R.nv, d0, e1, e2, c.binv, *(Sums<float> *)&S, nq);
+    } else if (sizeof(T) == sizeof(float) && A.kernel == NL_KERNEL_INV_DIST && R.kind == nlg::KIND_WHOLE &&
+               R.ncap == 0) {
+        // a whole T_b in the singular kernel's near field (decided by the FP64 test): the FP32
+        // near rule, as k_near integrates the near-field items that FP32 decides
+        const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
+        near_whole_f32(A, dl, c.b, x, e1, e2, c.binv, *(Sums<float> *)&S, nq);
     } else {
         inner_sums<T>(A, R, Vb, c64.area, x, S, nq);
     }
