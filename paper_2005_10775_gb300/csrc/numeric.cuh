@@ -873,6 +873,10 @@ __device__ __forceinline__ float cand_diam(const CandData &c)
 
 // Per-warp shared memory of the boundary kernel, sized for outer rules of at most NL_MAXQ
 // points (14.2 KB with float sums: four 4-warp blocks fit an SM).
+// fan triangles of a round of 32 polygon regions at most: a region has at most nlg::kBallCap = 16
+// vertices (approxcaps with m <= 4 has 15, nocaps 6, an N-gon clip kClipCap = 8), 14 triangles
+constexpr int kFanTasks = 32 * (nlg::kBallCap - 2);
+
 template <typename T>
 struct BoundaryShared {
     OuterPt sq[NL_MAXQ];
@@ -890,6 +894,7 @@ struct BoundaryShared {
     unsigned short wqueue[32 * NL_MAXQ];
     int fstart[32];            // spread fans: first fan triangle of each lane's item in the round's list
     unsigned char fwhich[32];  // spread fans: the clip buffer that holds each lane's polygon
+    unsigned char ftask[kFanTasks];   // spread fans: the lane whose item holds each fan triangle
     nlg::ClipBuf clip;         // per-lane FP32 clip buffers
 };
 
@@ -1500,7 +1505,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
         // the one the lane-per-item drain integrates (from the polygon's first vertex).  The
         // approxcaps fans (up to 13 triangles with the arc points) keep the lane-per-item drain:
         // a triangle's lookup and block add then cost about as much as its quadrature (2.68 ->
-        // 3.08 ms spread; tasks of two to five triangles of one fan did not pay either).
+        // 3.08 ms spread, 2.95 ms with the owner table; tasks of two to five triangles of one fan
+        // did not pay either).  The owner of each triangle comes from a per-round table
+        // (`ftask`) instead of a binary search over the lanes' first triangles (the N-gon's
+        // numeric phase 5.51 -> 5.38 ms).
         constexpr bool kSpread = sizeof(T) == sizeof(float) && (BALL == NL_BALL_NGON || (!INV && BALL == NL_BALL_NOCAPS));
         if constexpr (kSpread)
         for (int r0 = 0; r0 < nqueue; r0 += 32) {
@@ -1538,13 +1546,10 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             const int total = __shfl_sync(0xffffffffu, incl, 31);
             sh.fstart[lane] = incl - m;
             sh.fwhich[lane] = (unsigned char)which;
+            for (int j = incl - m; j < incl; j++) sh.ftask[j] = (unsigned char)lane;   // total <= kFanTasks
             __syncwarp();
             for (int t = lane; t < total; t += 32) {
-                int lo = 0, hi = 31;   // the last lane whose triangles start at or before t
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (sh.fstart[mid] <= t) lo = mid; else hi = mid - 1;
-                }
+                const int lo = sh.ftask[t];   // the lane whose item holds triangle t
                 const int k = t - sh.fstart[lo] + 1;
                 const unsigned it = sh.queue[r0 + lo];
                 const int own = it >> 8, q = it & 0xff;
