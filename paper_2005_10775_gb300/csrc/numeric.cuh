@@ -987,39 +987,14 @@ __device__ __forceinline__ int exact_region_f32(const NumArgs &A, const CandData
     return n >= 3 ? 1 : 0;
 }
 
-// FP32 region and quadrature of one undecided (q, b): 1 done (S holds its sums), 0 empty
-// region, -1 the FP64 geometry decides (the singular kernel's near field, an uncertified
-// FP32 choice, FP64 sums or a ball without an FP32 region)
+// FP32 region and quadrature of one undecided (q, b) of the balls the boundary kernel drains a
+// lane per item (the N-gon's items go through exact_region_f32 and the spread fans): 1 done (S
+// holds its sums), 0 empty region, -1 the FP64 geometry decides (the singular kernel's near
+// field, an uncertified FP32 choice, FP64 sums or a ball without an FP32 region)
 template <int BALL, typename T, bool INV>
 __device__ __forceinline__ int exact_item_f32(const NumArgs &A, const CandData &c, const OuterPt &o, Sums<T> &S,
                                               int64_t &nq, int &kind, int &nv, int &ncap, nlg::ClipBuf &cb, int lane)
 {
-    if (sizeof(T) == sizeof(float) && BALL == NL_BALL_NGON) {
-        nlg::F2 dl[3];
-        for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
-        // the singular kernel's near field needs the FP64 path; a region inside T_b is far
-        // when T_b is (certified in FP32)
-        if (INV && nlg::near_f32(dl, cand_diam(c), A.geo.tau) != 0)
-            return -1;
-        bool cut = false;
-        int which = 0;
-        const int n = nlg::clip_ngon_f32_sh(dl, A.geo.err0, A.geo, cb, lane, &which, &cut);
-        if (n >= 0) {
-            // certified FP32 clip: same vertex count and kind as the FP64 clip
-            if (n < 3) return 0;
-            kind = cut ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
-            nv = n;
-            ncap = 0;
-            if (!cut) {
-                const D2 Vb[3] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};   // unused: FP32 coordinates dl
-                whole_sums<T, INV>(A, Vb, cand_akc<T>(A, c), D2{o.x, o.y}, S, nq, dl);
-            } else {
-                const nlg::F2 e1 = {c.e1x, c.e1y}, e2 = {c.e2x, c.e2y};
-                poly_sums_sh<INV>(A, cb, which, lane, n, dl[0], e1, e2, c.binv, *(Sums<float> *)&S, nq);
-            }
-            return 1;
-        }
-    }
     if (sizeof(T) == sizeof(float) && (BALL == NL_BALL_NOCAPS || BALL == NL_BALL_APPROXCAPS)) {
         nlg::F2 dl[3];
         for (int i = 0; i < 3; i++) { dl[i].x = c.vlx[i] - o.lx; dl[i].y = c.vly[i] - o.ly; }
@@ -1564,7 +1539,8 @@ __device__ __forceinline__ void boundary_outer(const NumArgs &A, int a, Boundary
             }
             __syncwarp();
         }
-        for (int i = lane; !kSpread && i < nqueue; i += 32) {
+        if constexpr (!kSpread)
+        for (int i = lane; i < nqueue; i += 32) {
             const unsigned it = sh.queue[i];
             const int own = it >> 8, q = it & 0xff;
             const CandData &cd = sh.cand[own];
