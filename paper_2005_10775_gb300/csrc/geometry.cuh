@@ -543,21 +543,25 @@ __device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, cons
         mask &= mask - 1;
         const float ox = g.of[k][0], oy = g.of[k][1], ex = g.ef[k][0], ey = g.ef[k][1];
         const float el = g.mk[k] * g.inv_tau;   // |e_k|
+        const float elu = el * kU9, elc = el * kU3o;
+        // a pass over a convex polygon keeps at most n + 1 vertices (certified signs keep the exact
+        // combinatorics), so a list of fewer than kClipCap vertices cannot outgrow the buffer
+        if (n >= kClipCap) return -1;
         const int nxt = cur ^ 1;
         int m = 0;
         bool all_in = true;
         float sx = cb.x[cur][n - 1][lane], sy = cb.y[cur][n - 1][lane], se = cb.e[cur][n - 1][lane];
         float so = ex * (sy - oy) - ey * (sx - ox);
-        float su = el * (se + kU3o + kU9 * (fabsf(sx - ox) + fabsf(sy - oy)));
+        float su = fmaf(el, se, fmaf(elu, fabsf(sx - ox) + fabsf(sy - oy), elc));
         for (int i = 0; i < n; i++) {
             const float px = cb.x[cur][i][lane], py = cb.y[cur][i][lane], pe = cb.e[cur][i][lane];
             const float po = ex * (py - oy) - ey * (px - ox);
-            const float pu = el * (pe + kU3o + kU9 * (fabsf(px - ox) + fabsf(py - oy)));
+            // |e_k| (err + 3 u |o_k|_1 + 9 u |r|_1), the bound above
+            const float pu = fmaf(el, pe, fmaf(elu, fabsf(px - ox) + fabsf(py - oy), elc));
             if (!(fabsf(po) > pu)) return -1;
             const bool p_in = po > 0.f, s_in = so > 0.f;
             all_in = all_in && p_in;
             if (p_in != s_in) {
-                if (m >= kClipCap) return -1;
                 // t by the fast division (within 2 ulp): its error is in the rounding term
                 const float t = __fdividef(so, so - po);
                 const float dx = px - sx, dy = py - sy;
@@ -572,7 +576,6 @@ __device__ __forceinline__ int clip_ngon_f32_sh(const F2 dl[3], float err0, cons
                 m++;
             }
             if (p_in) {
-                if (m >= kClipCap) return -1;
                 cb.x[nxt][m][lane] = px;
                 cb.y[nxt][m][lane] = py;
                 cb.e[nxt][m][lane] = pe;
