@@ -40,7 +40,7 @@ SMS, FP32_LANES = 152, 128
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (nominal); the measured one comes from nl_fma_peak
 # DRAM bytes (read + write) of the numeric phase (k_interior + k_boundary + k_deferred) of
 # one assembly, from one ncu capture of the current kernels (profiles/k_boundary_<workload>.md)
-NCU_TRAFFIC = {"ngon32_96": (383.9e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_interior + k_boundary "
+NCU_TRAFFIC = {"ngon32_96": (380.4e6, "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_interior + k_boundary "
                                       "+ k_deferred + k_defer_merge, profiles/numeric_traffic_ngon32_96.md")}
 
 
