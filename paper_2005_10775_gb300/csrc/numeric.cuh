@@ -975,7 +975,7 @@ __device__ __forceinline__ int exact_region_f32(const NumArgs &A, const CandData
     which = 0;
     if (BALL == NL_BALL_NGON) {
         bool cut = false;
-        n = nlg::clip_ngon_f32_sh(dl, A.geo.err0, A.geo, cb, lane, &which, &cut);
+        n = nlg::clip_ngon_f32_sh<!INV>(dl, A.geo.err0, A.geo, cb, lane, &which, &cut);
         if (n < 0) return -1;
         if (n < 3) return 0;
         kind = cut ? nlg::KIND_PARTIAL : nlg::KIND_WHOLE;
