@@ -271,7 +271,11 @@ nl_status nl_matvec(nl_ctx *ctx, const nl_csr *A, const double *x, double *y, in
 nl_status nl_cg(nl_ctx *ctx, const nl_csr *A, const double *b, double *x, double rtol, int32_t max_it,
                 int32_t *iters, double *relres);
 
-/* Copy a CSR to host arrays row_ptr[n+1], col_idx[nnz], val[nnz] (any may be NULL). */
+/* Copy a CSR to host arrays row_ptr[n+1], col_idx[nnz], val[nnz] (any may be NULL).
+   Waits on the context's stream.  For an assembled matrix it also reads the device error word
+   of the numeric phase and the scatter, which run after nl_assemble's last host
+   synchronisation: NL_EUNSUPPORTED if one of them failed (a fixed-point sum beyond its bound,
+   a missing pattern slot); the arrays are then filled but the values are not valid. */
 nl_status nl_csr_download(nl_ctx *ctx, const nl_csr *m, int64_t *row_ptr, int32_t *col_idx, double *val);
 
 /* Release the device buffers of m (safe on a zeroed nl_csr).  Stream-ordered on the

@@ -183,6 +183,36 @@ nl_status nl_validate(nl_ctx *ctx, const nl_mesh *m, const nl_config *c)
     return NL_OK;
 }
 
+// Bound on the sum over all T_b of s0(x, T_b) = int_{region(x) cap T_b} gamma(x, y) dy at any
+// outer point x: every region of x lies in B(x, delta + h_max) (the shifted, barycenter and
+// overlap balls included), so the sum is at most kc pi (delta + h_max)^2 for a constant kernel
+// and c 2 pi (delta + h_max) for c / |x - y| (the integral of 1/r over the disc); here with a
+// margin of 1.25 (twice that for the singular kernel's quadrature).
+static double s0_sum_bound(const nl_config &c, double hmax)
+{
+    const double r = c.delta + hmax, pi = 3.14159265358979323846;
+    return c.kernel == NL_KERNEL_INV_DIST ? 2.5 * fabs(c.kernel_c) * 2.0 * pi * r
+                                          : 1.25 * fabs(c.kernel_c) * pi * r * r;
+}
+
+static double abs_weight_sum(int rule)
+{
+    nlq::RuleTab t;
+    memset(&t, 0, sizeof t);
+    if (!fill_rule(rule, &t)) return 0.0;   // unreachable: the rule was checked when the plan was made
+    double ws = 0.0;
+    for (int q = 0; q < t.n; q++) ws += fabs(t.w[q]);
+    return ws;
+}
+
+float nl_outer_abs_weight(const nl_plan *P)
+{
+    // the switching rule integrates each pair with one of its two rules
+    if (P->cfg.outer == NL_RULE_SWITCH47)
+        return (float)fmax(abs_weight_sum(NL_RULE_GAUSS4), abs_weight_sum(NL_RULE_PAPER7));
+    return (float)abs_weight_sum(P->cfg.outer);
+}
+
 nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stats)
 {
     memset(&A, 0, sizeof A);
@@ -236,15 +266,9 @@ nl_status nl_fill_args(nl_ctx *ctx, const nl_plan *P, nlq::NumArgs &A, bool stat
     A.kc = c.kernel_c;
     A.kcf = (float)c.kernel_c;
     {
-        // grid of the boundary kernel's fixed-point sums of s0 per outer point: every region of
-        // an outer point x lies in B(x, delta + h_max) (the shifted, barycenter and overlap
-        // balls included), so the sum is at most kc pi (delta + h_max)^2 for a constant kernel
-        // and c 2 pi (delta + h_max) for c / |x - y| (the integral of 1/r over the disc), here
-        // with a margin of 1.25 (twice that for the singular kernel's quadrature); the bound,
+        // grid of the boundary kernel's fixed-point sums of s0 per outer point: the bound,
         // rounded up to a power of two 2^e, maps to 2^30
-        const double r = c.delta + P->hmax, pi = 3.14159265358979323846;
-        const double bound = c.kernel == NL_KERNEL_INV_DIST ? 2.5 * fabs(c.kernel_c) * 2.0 * pi * r
-                                                            : 1.25 * fabs(c.kernel_c) * pi * r * r;
+        const double bound = s0_sum_bound(c, P->hmax);
         int e = 0;
         frexp(bound > 1e-30 ? bound : 1e-30, &e);   // bound < 2^e
         A.s0q_grid = (float)ldexp(1.0, 30 - e);
@@ -456,7 +480,7 @@ void nl_plan_free(nl_plan *P, cudaStream_t s)
     nl_free(P->nbr_split, s); nl_free(P->flag, s); nl_free(P->blk, s); nl_free(P->maa, s); nl_free(P->qp_a, s);
     nl_free(P->cnt_a, s); nl_free(P->hash_a, s); nl_free(P->lslot, s); nl_free(P->mbb, s); nl_free(P->tslot, s); nl_free(P->W, s);
     nl_free(P->val32, s); nl_free(P->x32, s); nl_free(P->err, s); nl_free(P->defer, s); nl_free(P->defer_n, s);
-    nl_free(P->nearq, s); nl_free(P->near_n, s); nl_free(P->otab, s);
+    nl_free(P->nearq, s); nl_free(P->near_n, s); nl_free(P->otab, s); nl_free(P->nexp, s);
 }
 
 nl_status nl_host_slots(nl_ctx *ctx, int n, nl_host_slot **out)
@@ -656,7 +680,18 @@ nl_status nl_csr_download(nl_ctx *ctx, const nl_csr *m, int64_t *row_ptr, int32_
         NL_CK(cudaMemcpyAsync(col_idx, m->col_idx, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToHost, ctx->stream));
     if (val && m->nnz)
         NL_CK(cudaMemcpyAsync(val, m->val, sizeof(double) * m->nnz, cudaMemcpyDeviceToHost, ctx->stream));
+    // the error word of the last numeric phase and scatter, which ran after nl_assemble's last
+    // host synchronisation (or in nl_assemble_numeric / nl_batch_run, which have none)
+    const nl_plan *P = (const nl_plan *)m->priv;
+    int herr = 0;
+    if (P && P->err) NL_CK(cudaMemcpyAsync(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     NL_CK(cudaStreamSynchronize(ctx->stream));
+    if (herr & 256)
+        return nl_fail(ctx, NL_EUNSUPPORTED, "a fixed-point sum left its range (error word " +
+                                                 std::to_string(herr) + ")");
+    if (herr)
+        return nl_fail(ctx, NL_EUNSUPPORTED, "the numeric phase or the scatter failed (error word " +
+                                                 std::to_string(herr) + ")");
     return NL_OK;
 }
 

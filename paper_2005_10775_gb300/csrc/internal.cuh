@@ -118,6 +118,7 @@ struct nl_plan {
     int64_t *tslot = nullptr;     // [nnz] slot of the transposed entry
     double *W = nullptr;          // [nnz] one-sided accumulation, D = W + W^T
     int64_t max_row = 0;          // longest row of the pattern
+    int8_t *nexp = nullptr;       // [J] FP32 plans: e with the scatter's column bound of node j below 2^(e+1)
     // extracted sub-matrix state (nl_extract)
     float *val32 = nullptr;       // FP32 copy of the values (nl_matvec / nl_cg), lazily built
     float *x32 = nullptr;         // [ncols] nl_matvec's x rounded to FP32
@@ -273,6 +274,9 @@ nl_status nl_alloc_numeric(nl_ctx *ctx, nl_plan *P);
 // call allocates the problem's FP64-item and near-field queues
 nl_status nl_run_numeric_one_stream(nl_ctx *ctx, nl_plan *P);
 nl_status nl_run_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out);
+// sum_q |w_q| of the outer rule (the larger of the switching rule's two; api.cu): the FP32
+// scatter's bound on a row sum per unit of |T_a|
+float nl_outer_abs_weight(const nl_plan *P);
 // the steps of nl_assemble after the preparation's stage B (api.cu): C = stage C, numeric phase,
 // symbolic stage A (slot: queue counts, pattern size); D (slot C read) = checks, a second numeric
 // run if a queue overflowed, symbolic stage B, scatter.  Events (may be null) mark the phases.
@@ -298,6 +302,9 @@ struct ScatterArgs {   // one problem
     const int64_t *tslot;
     double *val;
     int *err;
+    const double *area;   // [K] |T_a| (the FP32 scatter's fixed-point grids)
+    const int8_t *nexp;   // [J] per-column bound exponents (nl_plan::nexp)
+    float ws;             // nl_outer_abs_weight
 };
 // W = 0 over all problems (zoff: prefix sums of nnz, device, n + 1 entries; total = zoff[n])
 nl_status nl_launch_zero_batch(nl_ctx *ctx, const ScatterArgs *dS, const int64_t *dzoff, int n, int64_t total);

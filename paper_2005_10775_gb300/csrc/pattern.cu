@@ -16,6 +16,7 @@
 #include <stdlib.h>
 
 #include <new>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -122,6 +123,28 @@ __global__ void k_node_fill(int K, const int32_t *tri, const int64_t *start, int
         int64_t pos = start[v] + (int64_t)atomicAdd((unsigned long long *)&cursor[v], 1ull);
         ntri[pos] = t;
     }
+}
+
+// FP32 scatter: exponent of a bound on what node j's column of a row of T_a receives per unit
+// of sum_q |W_q| (that is, per |T_a| sum_q |w_q|).  Each triangle T_b at j adds at most
+// s0max(T_b), a bound on int_{S cap T_b} gamma(x, y) dy over all points x and sets S: kc |T_b|
+// for a constant kernel, c 2 sqrt(pi |T_b|) for c / |x - y| (1/r integrated over the disc of
+// area |T_b| centred at x, the largest such integral), each with the per-point margin of the
+// numeric phase (1.25, 2.5 for the singular quadrature).  The bound taken, (triangles at j) x
+// max s0max, is order-free and so the same in every run; nexp[j] = floor(log2) of it in FP32.
+__global__ void k_node_exp(int J, const int64_t *nptr, const int32_t *ntri, const double *area, int inv, double c,
+                           int8_t *nexp)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= J) return;
+    double m = 0.0;
+    for (int64_t s = nptr[j]; s < nptr[j + 1]; s++) {
+        const double A = area[ntri[s]];
+        m = fmax(m, inv ? 2.5 * c * 2.0 * sqrt(3.14159265358979323846 * A) : 1.25 * c * A);
+    }
+    const double nb = (double)(nptr[j + 1] - nptr[j]) * m;
+    int e = nb < 1e38 ? ((__float_as_int((float)nb) >> 23) & 255) - 127 : 126;
+    nexp[j] = (int8_t)(e < -126 ? -126 : (e > 126 ? 126 : e));
 }
 
 constexpr int kRowThreads = 256;
@@ -396,17 +419,94 @@ __device__ __forceinline__ int hash_find(const int32_t *key, int H, int hbits, i
     return -1;
 }
 
+// FP32 blocks: the shared row sums are 32-bit fixed point on a power-of-two grid from their
+// bound (fx_row_shift), added with native integer atomics, so they do not depend on the order
+// of the adds; a sum beyond its bound sets error bit 256.  FP64 blocks: FP64 shared sums.
+// 2^s as an FP32 number (s in [-126, 126]: a normal power of two, built from its bits)
+__device__ __forceinline__ float pow2f(int s) { return __int_as_float((s + 127) << 23); }
+
+// floor(log2 x) of a positive normal FP32 number, from its exponent field, clamped to [-126, 126]
+__device__ __forceinline__ int exp2_floor(float x)
+{
+    const int e = ((__float_as_int(x) >> 23) & 255) - 127;
+    return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+
+// Fixed-point shift of the rows of T_a: the sum a column of node j receives is below
+// 2^(ea + 1) 2^(nexp[j] + 1) (ea: exponent of |T_a| sum_q |w_q|), so with ej the largest nexp
+// over the rows' columns every sum scaled by 2^s stays below 2^30.
+__device__ __forceinline__ int fx_row_shift(int ea, int ej)
+{
+    const int s = 28 - ea - ej;
+    return s < -126 ? -126 : (s > 126 ? 126 : s);
+}
+
+// One pair (a, b) of the scatter: flag f, its M_ab block v, added to the three rows of T_a's
+// nodes (shared sums, fixed point for FP32 blocks, when cached; else FP64 atomics on W).
+template <typename T, typename Acc>
+__device__ __forceinline__ void scatter_pair(uint8_t f, int b, const T *v, int K, int J, const int32_t *tri,
+                                             const int64_t *row_ptr, const int32_t *col, double *W, int *err,
+                                             bool cached, int H, int hbits, const int *ar, const int *len, int cap,
+                                             float sc, Acc *sacc, const int32_t *skey, const uint32_t *spk)
+{
+    if (!f) return;
+#ifdef NL_CHECKS
+    const int64_t nnz_chk = row_ptr[J];
+    if (b < 0 || b >= K) {
+        atomicOr(err, 64);
+        return;
+    }
+#endif
+    const int bn[3] = {tri[3 * b], tri[3 * b + 1], tri[3 * b + 2]};
+#ifdef NL_CHECKS
+    if (bn[0] < 0 || bn[0] >= J || bn[1] < 0 || bn[1] >= J || bn[2] < 0 || bn[2] >= J) {
+        atomicOr(err, 64);
+        return;
+    }
+#endif
+    for (int k = 0; k < 3; k++) {
+        if (cached) {
+            const int sl = hash_find(skey, H, hbits, bn[k]);
+            const unsigned pk = sl >= 0 ? spk[sl] : 0xffffffffu;
+            for (int i = 0; i < 3; i++) {
+                const unsigned pos = (pk >> (10 * i)) & kPosAbsent;
+                if (pos < (unsigned)len[i]) {
+                    if constexpr (sizeof(T) == sizeof(float))
+                        atomicAdd(&sacc[i * cap + pos], -__float2int_rn(v[3 * i + k] * sc));
+                    else
+                        atomicAdd(&sacc[i * cap + pos], -v[3 * i + k]);
+                } else {
+                    atomicOr(err, 2);
+                }
+            }
+        } else {
+            for (int i = 0; i < 3; i++) {
+                const int64_t sl = find_slot(row_ptr, col, ar[i], bn[k]);
+#ifdef NL_CHECKS
+                if (sl >= nnz_chk) {
+                    atomicOr(err, 64);
+                    continue;
+                }
+#endif
+                if (sl >= 0) atomicAdd(&W[sl], -(double)v[3 * i + k]); else atomicOr(err, 2);
+            }
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int32_t *tri, const int64_t *ptr,
                                               const int32_t *idx, const uint8_t *flag, const T *blk,
                                               const int64_t *row_ptr, const int32_t *col, double *W, int *err,
-                                              int cap, int hbits, int a, int lane, T *sacc, int32_t *skey,
-                                              uint32_t *spk)
+                                              int cap, int hbits, int a, int lane, T *sacc_t, int32_t *skey,
+                                              uint32_t *spk, const double *area, const int8_t *nexp, float ws)
 {
+    constexpr bool kFx = sizeof(T) == sizeof(float);
+    using Acc = typename std::conditional<kFx, int, T>::type;
+    Acc *sacc = reinterpret_cast<Acc *>(sacc_t);
     const int ar[3] = {tri[3 * a], tri[3 * a + 1], tri[3 * a + 2]};
 #ifdef NL_CHECKS
     // debug build: indices checked, a bad one recorded (bit 64) and its access skipped
-    const int64_t nnz_chk = row_ptr[J];
     for (int i = 0; i < 3; i++)
         if (ar[i] < 0 || ar[i] >= J) {
             atomicOr(err, 64);
@@ -425,17 +525,21 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
         len[i] = (int)(row_ptr[ar[i] + 1] - r0[i]);
     }
     bool cached = cap > 0 && len[0] <= cap && len[1] <= cap && len[2] <= cap;
+    int shift = 0;   // FP32 blocks: fixed-point shift of the shared row sums
     if (cached) {
         for (int k = lane; k < H; k += 32) {
             skey[k] = -1;
             spk[k] = 0xffffffffu;
         }
-        for (int k = lane; k < 3 * cap; k += 32) sacc[k] = (T)0;
+        for (int k = lane; k < 3 * cap; k += 32) sacc[k] = (Acc)0;
         __syncwarp();
         bool full = false;
+        int ej = -126;
         for (int i = 0; i < 3; i++)
             for (int k = lane; k < len[i]; k += 32) {
-                const int sl = hash_insert(skey, H, hbits, col[r0[i] + k]);
+                const int c = col[r0[i] + k];
+                if constexpr (kFx) ej = max(ej, (int)nexp[c]);
+                const int sl = hash_insert(skey, H, hbits, c);
                 if (sl < 0) {
                     full = true;
                     continue;
@@ -443,57 +547,58 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
                 atomicAnd(&spk[sl], ~((kPosAbsent ^ (unsigned)k) << (10 * i)));
             }
         cached = !__any_sync(0xffffffffu, full);   // a full table: this triangle searches in global memory
+        if constexpr (kFx) {
+            ej = __reduce_max_sync(0xffffffffu, ej);
+            shift = fx_row_shift(exp2_floor((float)(area[a] * (double)ws)), ej);
+        }
         __syncwarp();
     }
-    for (int64_t e = ptr[a] + lane; e < ptr[a + 1]; e += 32) {
-        // every load of the pair first (independent of the flag): one round trip, not a chain
-        const uint8_t f = flag[e];
-        const int b = idx[e];
-        T v[9];
+    const float sc = pow2f(shift);
+    // the next pair's loads are issued before this pair's lookups and adds: the DRAM latency
+    // of one iteration overlaps the shared-memory work of the previous one
+    const int64_t e_end = ptr[a + 1];
+    int64_t e = ptr[a] + lane;
+    uint8_t f = 0;
+    int b = 0;
+    T v[9];
+    if (e < e_end) {
+        f = flag[e];
+        b = idx[e];
         for (int p = 0; p < 9; p++) v[p] = blk[(int64_t)p * E + e];
-        if (!f) continue;
-#ifdef NL_CHECKS
-        if (b < 0 || b >= K) {
-            atomicOr(err, 64);
-            continue;
+    }
+    for (; e < e_end; e += 32) {
+        const int64_t en = e + 32;
+        uint8_t fn = 0;
+        int bnx = 0;
+        T vn[9];
+        if (en < e_end) {
+            fn = flag[en];
+            bnx = idx[en];
+            for (int p = 0; p < 9; p++) vn[p] = blk[(int64_t)p * E + en];
+        } else {
+            for (int p = 0; p < 9; p++) vn[p] = (T)0;
         }
-#endif
-        const int bn[3] = {tri[3 * b], tri[3 * b + 1], tri[3 * b + 2]};
-#ifdef NL_CHECKS
-        if (bn[0] < 0 || bn[0] >= J || bn[1] < 0 || bn[1] >= J || bn[2] < 0 || bn[2] >= J) {
-            atomicOr(err, 64);
-            continue;
-        }
-#endif
-        for (int k = 0; k < 3; k++) {
-            if (cached) {
-                const int sl = hash_find(skey, H, hbits, bn[k]);
-                const unsigned pk = sl >= 0 ? spk[sl] : 0xffffffffu;
-                for (int i = 0; i < 3; i++) {
-                    const unsigned pos = (pk >> (10 * i)) & kPosAbsent;
-                    if (pos < (unsigned)len[i]) atomicAdd(&sacc[i * cap + pos], -v[3 * i + k]); else atomicOr(err, 2);
-                }
-            } else {
-                for (int i = 0; i < 3; i++) {
-                    const int64_t sl = find_slot(row_ptr, col, ar[i], bn[k]);
-#ifdef NL_CHECKS
-                    if (sl >= nnz_chk) {
-                        atomicOr(err, 64);
-                        continue;
-                    }
-#endif
-                    if (sl >= 0) atomicAdd(&W[sl], -(double)v[3 * i + k]); else atomicOr(err, 2);
-                }
-            }
-        }
+        scatter_pair<T, Acc>(f, b, v, K, J, tri, row_ptr, col, W, err, cached, H, hbits, ar, len, cap, sc, sacc,
+                             skey, spk);
+        f = fn;
+        b = bnx;
+        for (int p = 0; p < 9; p++) v[p] = vn[p];
     }
     __syncwarp();
-    if (cached)
+    if (cached) {
+        const double inv = (double)pow2f(-shift);
         for (int i = 0; i < 3; i++)
             for (int k = lane; k < len[i]; k += 32) {
-                const T v = sacc[i * cap + k];
-                if (v != (T)0) atomicAdd(&W[r0[i] + k], (double)v);
+                const Acc x = sacc[i * cap + k];
+                if (x == (Acc)0) continue;
+                if constexpr (kFx) {
+                    if (x > (1 << 30) || x < -(1 << 30)) atomicOr(err, 256);
+                    atomicAdd(&W[r0[i] + k], (double)x * inv);
+                } else {
+                    atomicAdd(&W[r0[i] + k], (double)x);
+                }
             }
+    }
 }
 
 // M_aa + M_bb of every triangle into W through its local slots (diagonal halved: D = W + W^T),
@@ -537,7 +642,8 @@ __device__ __forceinline__ void scatter_warp_smem(unsigned char *raw, int wib, i
 template <typename T>
 __global__ void k_scatter(int K, int J, int64_t E, const int32_t *tri, const int64_t *ptr, const int32_t *idx,
                           const uint8_t *flag, const T *blk, const int64_t *row_ptr, const int32_t *col,
-                          double *W, int *err, int cap, int hbits)
+                          double *W, int *err, int cap, int hbits, const double *area, const int8_t *nexp,
+                          float ws)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -548,7 +654,7 @@ __global__ void k_scatter(int K, int J, int64_t E, const int32_t *tri, const int
     scatter_warp_smem<T>(smem_raw, wib, cap, hbits, sacc, skey, spk);
     if (a >= K) return;
     scatter_outer<T>(K, J, E, tri, ptr, idx, flag, blk, row_ptr, col, W, err, cap, hbits, a, lane, sacc, skey,
-                     spk);
+                     spk, area, nexp, ws);
 }
 
 // ---- batched scatter: every problem of a batch in one launch per value type ----
@@ -579,7 +685,7 @@ __global__ void k_scatter_batch(const ScatterArgs *__restrict__ S, const int64_t
     const int p = batch_problem(koff, n, g);
     const ScatterArgs &A = S[p];
     scatter_outer<T>(A.K, A.J, A.E, A.tri, A.ptr, A.idx, A.flag, (const T *)A.blk, A.row_ptr, A.col, A.W,
-                     A.err, cap, hbits, (int)(g - koff[p]), lane, sacc, skey, spk);
+                     A.err, cap, hbits, (int)(g - koff[p]), lane, sacc, skey, spk, A.area, A.nexp, A.ws);
 }
 
 // M_aa + M_bb of every triangle of every problem (koff: prefix sums of K)
@@ -737,6 +843,13 @@ nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_
     NL_CK(cudaGetLastError());
     if ((s = nl_scan_i64(ctx, T->ncnt, T->nptr, J)) != NL_OK) return s;
     k_node_fill<<<(K + 255) / 256, 256, 0, st>>>(K, P->tri, T->nptr, T->ncur, T->ntri); ++ctx->launches;
+    if (P->cfg.prec != NL_PREC_FP64 && J > 0) {
+        nl_free(P->nexp, st);
+        if ((s = nl_alloc(ctx, &P->nexp, (size_t)J)) != NL_OK) return s;
+        k_node_exp<<<(J + 255) / 256, 256, 0, st>>>(J, T->nptr, T->ntri, P->area,
+                                                    P->cfg.kernel == NL_KERNEL_INV_DIST ? 1 : 0,
+                                                    fabs(P->cfg.kernel_c), P->nexp); ++ctx->launches;
+    }
     NL_CK(cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(sizeof(int32_t) * (NL_HASH_CAP + kListCap))));
     // first count with a set of about 3x the expected row (0.6 x the candidates per triangle);
@@ -856,7 +969,8 @@ static nl_status launch_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     const unsigned grid = (unsigned)((K + warps - 1) / warps);
     k_scatter<T><<<grid, 32 * warps, smem, ctx->stream>>>(K, P->J, P->E, P->tri, P->nbr_ptr, P->nbr_idx, P->flag,
                                                            (const T *)P->blk, out->row_ptr, out->col_idx,
-                                                           P->W, P->err, cap, hbits); ++ctx->launches;
+                                                           P->W, P->err, cap, hbits, P->area, P->nexp,
+                                                           nl_outer_abs_weight(P)); ++ctx->launches;
     NL_CK(cudaGetLastError());
     k_local_blocks<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->maa, P->mbb, P->lslot, P->W, P->err);
     ++ctx->launches;
