@@ -480,7 +480,7 @@ void nl_plan_free(nl_plan *P, cudaStream_t s)
     nl_free(P->nbr_split, s); nl_free(P->flag, s); nl_free(P->blk, s); nl_free(P->maa, s); nl_free(P->qp_a, s);
     nl_free(P->cnt_a, s); nl_free(P->hash_a, s); nl_free(P->lslot, s); nl_free(P->mbb, s); nl_free(P->tslot, s); nl_free(P->W, s);
     nl_free(P->val32, s); nl_free(P->x32, s); nl_free(P->err, s); nl_free(P->defer, s); nl_free(P->defer_n, s);
-    nl_free(P->nearq, s); nl_free(P->near_n, s); nl_free(P->otab, s); nl_free(P->nexp, s);
+    nl_free(P->nearq, s); nl_free(P->near_n, s); nl_free(P->otab, s); nl_free(P->fxe, s);
 }
 
 nl_status nl_host_slots(nl_ctx *ctx, int n, nl_host_slot **out)

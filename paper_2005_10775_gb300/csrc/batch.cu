@@ -827,7 +827,7 @@ nl_status nl_batch_create(nl_ctx *ctx, int32_t n, const nl_mesh *meshes, const n
             a.val = outs[i].val;
             a.err = P->err;
             a.area = P->area;
-            a.nexp = P->nexp;
+            a.fxe = P->fxe;
             a.ws = nl_outer_abs_weight(P);
             zoff[i + 1] = zoff[i] + outs[i].nnz;
         }

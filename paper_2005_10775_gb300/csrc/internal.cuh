@@ -118,7 +118,8 @@ struct nl_plan {
     int64_t *tslot = nullptr;     // [nnz] slot of the transposed entry
     double *W = nullptr;          // [nnz] one-sided accumulation, D = W + W^T
     int64_t max_row = 0;          // longest row of the pattern
-    int8_t *nexp = nullptr;       // [J] FP32 plans: e with the scatter's column bound of node j below 2^(e+1)
+    int *fxe = nullptr;           // FP32 plans: 128 + e with every scatter column bound per unit of
+                                  // |T_a| sum_q |w_q| below 2^(e+1) (k_node_exp)
     // extracted sub-matrix state (nl_extract)
     float *val32 = nullptr;       // FP32 copy of the values (nl_matvec / nl_cg), lazily built
     float *x32 = nullptr;         // [ncols] nl_matvec's x rounded to FP32
@@ -303,7 +304,7 @@ struct ScatterArgs {   // one problem
     double *val;
     int *err;
     const double *area;   // [K] |T_a| (the FP32 scatter's fixed-point grids)
-    const int8_t *nexp;   // [J] per-column bound exponents (nl_plan::nexp)
+    const int *fxe;       // nl_plan::fxe
     float ws;             // nl_outer_abs_weight
 };
 // W = 0 over all problems (zoff: prefix sums of nnz, device, n + 1 entries; total = zoff[n])

@@ -131,9 +131,10 @@ __global__ void k_node_fill(int K, const int32_t *tri, const int64_t *start, int
 // for a constant kernel, c 2 sqrt(pi |T_b|) for c / |x - y| (1/r integrated over the disc of
 // area |T_b| centred at x, the largest such integral), each with the per-point margin of the
 // numeric phase (1.25, 2.5 for the singular quadrature).  The bound taken, (triangles at j) x
-// max s0max, is order-free and so the same in every run; nexp[j] = floor(log2) of it in FP32.
+// max s0max, is order-free and so the same in every run.  fxe (zeroed) receives 128 + the
+// largest floor(log2) of it in FP32 over the nodes (an integer maximum: the same in every run).
 __global__ void k_node_exp(int J, const int64_t *nptr, const int32_t *ntri, const double *area, int inv, double c,
-                           int8_t *nexp)
+                           int *fxe)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= J) return;
@@ -144,7 +145,8 @@ __global__ void k_node_exp(int J, const int64_t *nptr, const int32_t *ntri, cons
     }
     const double nb = (double)(nptr[j + 1] - nptr[j]) * m;
     int e = nb < 1e38 ? ((__float_as_int((float)nb) >> 23) & 255) - 127 : 126;
-    nexp[j] = (int8_t)(e < -126 ? -126 : (e > 126 ? 126 : e));
+    e = e < -126 ? -126 : (e > 126 ? 126 : e);
+    atomicMax(fxe, e + 128);
 }
 
 constexpr int kRowThreads = 256;
@@ -433,8 +435,8 @@ __device__ __forceinline__ int exp2_floor(float x)
 }
 
 // Fixed-point shift of the rows of T_a: the sum a column of node j receives is below
-// 2^(ea + 1) 2^(nexp[j] + 1) (ea: exponent of |T_a| sum_q |w_q|), so with ej the largest nexp
-// over the rows' columns every sum scaled by 2^s stays below 2^30.
+// 2^(ea + 1) 2^(ej + 1) (ea: exponent of |T_a| sum_q |w_q|, ej the largest node exponent of
+// k_node_exp), so every sum scaled by 2^s stays below 2^30.
 __device__ __forceinline__ int fx_row_shift(int ea, int ej)
 {
     const int s = 28 - ea - ej;
@@ -499,7 +501,7 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
                                               const int32_t *idx, const uint8_t *flag, const T *blk,
                                               const int64_t *row_ptr, const int32_t *col, double *W, int *err,
                                               int cap, int hbits, int a, int lane, T *sacc_t, int32_t *skey,
-                                              uint32_t *spk, const double *area, const int8_t *nexp, float ws)
+                                              uint32_t *spk, const double *area, const int *fxe, float ws)
 {
     constexpr bool kFx = sizeof(T) == sizeof(float);
     using Acc = typename std::conditional<kFx, int, T>::type;
@@ -534,12 +536,9 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
         for (int k = lane; k < 3 * cap; k += 32) sacc[k] = (Acc)0;
         __syncwarp();
         bool full = false;
-        int ej = -126;
         for (int i = 0; i < 3; i++)
             for (int k = lane; k < len[i]; k += 32) {
-                const int c = col[r0[i] + k];
-                if constexpr (kFx) ej = max(ej, (int)nexp[c]);
-                const int sl = hash_insert(skey, H, hbits, c);
+                const int sl = hash_insert(skey, H, hbits, col[r0[i] + k]);
                 if (sl < 0) {
                     full = true;
                     continue;
@@ -547,10 +546,7 @@ __device__ __forceinline__ void scatter_outer(int K, int J, int64_t E, const int
                 atomicAnd(&spk[sl], ~((kPosAbsent ^ (unsigned)k) << (10 * i)));
             }
         cached = !__any_sync(0xffffffffu, full);   // a full table: this triangle searches in global memory
-        if constexpr (kFx) {
-            ej = __reduce_max_sync(0xffffffffu, ej);
-            shift = fx_row_shift(exp2_floor((float)(area[a] * (double)ws)), ej);
-        }
+        if constexpr (kFx) shift = fx_row_shift(exp2_floor((float)(area[a] * (double)ws)), *fxe - 128);
         __syncwarp();
     }
     const float sc = pow2f(shift);
@@ -642,7 +638,7 @@ __device__ __forceinline__ void scatter_warp_smem(unsigned char *raw, int wib, i
 template <typename T>
 __global__ void k_scatter(int K, int J, int64_t E, const int32_t *tri, const int64_t *ptr, const int32_t *idx,
                           const uint8_t *flag, const T *blk, const int64_t *row_ptr, const int32_t *col,
-                          double *W, int *err, int cap, int hbits, const double *area, const int8_t *nexp,
+                          double *W, int *err, int cap, int hbits, const double *area, const int *fxe,
                           float ws)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -654,7 +650,7 @@ __global__ void k_scatter(int K, int J, int64_t E, const int32_t *tri, const int
     scatter_warp_smem<T>(smem_raw, wib, cap, hbits, sacc, skey, spk);
     if (a >= K) return;
     scatter_outer<T>(K, J, E, tri, ptr, idx, flag, blk, row_ptr, col, W, err, cap, hbits, a, lane, sacc, skey,
-                     spk, area, nexp, ws);
+                     spk, area, fxe, ws);
 }
 
 // ---- batched scatter: every problem of a batch in one launch per value type ----
@@ -685,7 +681,7 @@ __global__ void k_scatter_batch(const ScatterArgs *__restrict__ S, const int64_t
     const int p = batch_problem(koff, n, g);
     const ScatterArgs &A = S[p];
     scatter_outer<T>(A.K, A.J, A.E, A.tri, A.ptr, A.idx, A.flag, (const T *)A.blk, A.row_ptr, A.col, A.W,
-                     A.err, cap, hbits, (int)(g - koff[p]), lane, sacc, skey, spk, A.area, A.nexp, A.ws);
+                     A.err, cap, hbits, (int)(g - koff[p]), lane, sacc, skey, spk, A.area, A.fxe, A.ws);
 }
 
 // M_aa + M_bb of every triangle of every problem (koff: prefix sums of K)
@@ -844,11 +840,12 @@ nl_status nl_pattern_a(nl_ctx *ctx, nl_plan *P, nl_csr *out, nl_pat *T, nl_host_
     if ((s = nl_scan_i64(ctx, T->ncnt, T->nptr, J)) != NL_OK) return s;
     k_node_fill<<<(K + 255) / 256, 256, 0, st>>>(K, P->tri, T->nptr, T->ncur, T->ntri); ++ctx->launches;
     if (P->cfg.prec != NL_PREC_FP64 && J > 0) {
-        nl_free(P->nexp, st);
-        if ((s = nl_alloc(ctx, &P->nexp, (size_t)J)) != NL_OK) return s;
+        nl_free(P->fxe, st);
+        if ((s = nl_alloc(ctx, &P->fxe, 1)) != NL_OK) return s;
+        NL_CK(cudaMemsetAsync(P->fxe, 0, sizeof(int), st));
         k_node_exp<<<(J + 255) / 256, 256, 0, st>>>(J, T->nptr, T->ntri, P->area,
                                                     P->cfg.kernel == NL_KERNEL_INV_DIST ? 1 : 0,
-                                                    fabs(P->cfg.kernel_c), P->nexp); ++ctx->launches;
+                                                    fabs(P->cfg.kernel_c), P->fxe); ++ctx->launches;
     }
     NL_CK(cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(sizeof(int32_t) * (NL_HASH_CAP + kListCap))));
@@ -969,7 +966,7 @@ static nl_status launch_scatter(nl_ctx *ctx, nl_plan *P, nl_csr *out)
     const unsigned grid = (unsigned)((K + warps - 1) / warps);
     k_scatter<T><<<grid, 32 * warps, smem, ctx->stream>>>(K, P->J, P->E, P->tri, P->nbr_ptr, P->nbr_idx, P->flag,
                                                            (const T *)P->blk, out->row_ptr, out->col_idx,
-                                                           P->W, P->err, cap, hbits, P->area, P->nexp,
+                                                           P->W, P->err, cap, hbits, P->area, P->fxe,
                                                            nl_outer_abs_weight(P)); ++ctx->launches;
     NL_CK(cudaGetLastError());
     k_local_blocks<<<(K + 255) / 256, 256, 0, ctx->stream>>>(K, P->maa, P->mbb, P->lslot, P->W, P->err);
