@@ -672,3 +672,57 @@ def test_singular_kernel_second_order_convergence():
         errs.append(O.l2_error_omega(m, U, I.manufactured_u))
     rate = math.log2(errs[0] / errs[1])
     assert 1.6 < rate < 2.6, (errs, rate)
+
+
+# --------------------------------------------------------------------------
+# Bounds behind the FP32 path's fixed-point sums.  The boundary kernel sums s0 per outer point
+# on a grid sized by kc pi (delta + h_max)^2 (constant kernel) or 2.5 c 2 pi (delta + h_max)
+# (c / |x - y|); the scatter sizes its row grids by s0(x, T) <= 1.25 kc |T| (constant) or
+# 2.5 c 2 sqrt(pi |T|) (c / |x - y|) for every x and T.  Both premises hold for the oracle's
+# inner sums over every ball (the regions lie in T and in B(x, delta + h_max); the integral of
+# 1/r over a set of area A is largest on the disc of area A centred at x).
+# --------------------------------------------------------------------------
+BOUND_CASES = [("ngon", "const"), ("nocaps", "const"), ("approxcaps", "const"), ("exactcaps", "const"),
+               ("barycenter", "const"), ("overlap", "const"), ("ngon", "inv_dist"), ("nocaps", "inv_dist"),
+               ("approxcaps", "inv_dist"), ("barycenter", "inv_dist")]
+
+
+@pytest.mark.parametrize("ball,kernel", BOUND_CASES)
+def test_inner_sums_within_the_fixed_point_bounds(ball, kernel):
+    delta, c = 0.12, 2.3
+    m = _local_mesh(n=12, hh=0.04, jitter=0.25, seed=11)
+    hm = O.hmax(m)
+    cfg = dict(delta=delta, ball=ball, inner="dunavant7", kernel=kernel, kernel_c=c, duffy_n=4)
+    if ball == "ngon":
+        cfg["ngon_off"] = I.ngon_offsets(24, delta)
+    rng = np.random.default_rng(5)
+    # x at the origin, on the mesh vertex nearest to it, and at two random points of the centre
+    j = int(np.argmin(m.vx ** 2 + m.vy ** 2))
+    pts = [np.zeros(2), np.array([m.vx[j], m.vy[j]])] + [rng.uniform(-0.05, 0.05, 2) for _ in range(2)]
+    for x in pts:
+        total = 0.0
+        for t in m.tri:
+            V = np.stack([m.vx[t], m.vy[t]], axis=1)
+            s0 = O.inner(V, x, cfg)[0]
+            A = abs(_area(V))
+            cap = c * A if kernel == "const" else 2.0 * c * math.sqrt(math.pi * A)
+            # the exact bound for the constant kernel; the singular rule may overshoot the
+            # exact integral slightly, which the product's 2.5 margin covers
+            assert s0 <= cap * (1 + 1e-12 if kernel == "const" else 1.05), (x, t, s0, cap)
+            assert s0 >= 0.0
+            total += s0
+        r = delta + hm
+        per_point = c * math.pi * r * r if kernel == "const" else c * 2.0 * math.pi * r
+        assert total <= per_point * (1 + 1e-12 if kernel == "const" else 1.05), (x, total, per_point)
+
+
+def test_exactcaps_printed_weight_within_the_fixed_point_bounds():
+    # the printed cap weight is half the cap area: the region's integral stays below |T| kc
+    delta, c = 0.12, 2.3
+    m = _local_mesh(n=12, hh=0.04, jitter=0.25, seed=11)
+    cfg = dict(delta=delta, ball="exactcaps", inner="dunavant7", kernel_c=c, cap_printed=1)
+    j = int(np.argmin(m.vx ** 2 + m.vy ** 2))
+    for x in [np.zeros(2), np.array([m.vx[j], m.vy[j]])]:
+        for t in m.tri:
+            V = np.stack([m.vx[t], m.vy[t]], axis=1)
+            assert O.inner(V, x, cfg)[0] <= c * abs(_area(V)) * (1 + 1e-12)
