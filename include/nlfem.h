@@ -328,8 +328,8 @@ int64_t nl_launch_count(nl_ctx *ctx);
    every item and keeps it for the plan's re-assemblies (NL_DEFER_CAP in the environment
    fixes the capacity instead, 0 disables the queue; NL_DEFER_CAP_INIT sets the first one).  Each warp queues its items in (pair,
    outer point) order and a merge kernel adds the items of a pair onto it in that order (no
-   atomics); the boundary kernel sums the other items of a pair in fixed point (order-free).
-   So run to run the FP32-path pair blocks repeat exactly, except the singular kernel's
+   atomics); the boundary kernel sums the other items of a pair in fixed point (order-free),
+   and so does the scatter with the pairs' blocks in each outer triangle's rows.  So run to run the FP32-path pair blocks repeat exactly, except the singular kernel's
    near-field items, which k_near sums in FP32 in a queue-order grouping (measured up to 3e-8
    of max|D|), and the sums taken with FP64 atomics (M_aa, M_bb, the scatter into D) differ
    in their last bits (about 1e-16 relative).  0 for the FP64 path; -1 for a null context. */
