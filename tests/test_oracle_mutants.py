@@ -114,6 +114,11 @@ REGION_MUTANTS = [
     ("entry and exit roots swapped", "lam[0] = l1; is_entry[0] = 1;", "lam[0] = l1; is_entry[0] = 0;"),
     ("cap centroid off", "4.0 * delta * st * st * st / (3.0 * two_th_minus_sin)",
      "2.0 * delta * st * st * st / (3.0 * two_th_minus_sin)"),
+    ("overlap test without its edge-crossing branch",
+     "if ((l1 >= 0.0 && l1 <= 1.0) || (l2 >= 0.0 && l2 <= 1.0)) return 1;", "(void)l1; (void)l2;"),
+    ("overlap test without its enclosing branch", "int in = 1;", "int in = 0;"),
+    ("overlap test with a strict vertex test", "for (int i = 0; i < 3; i++) if (in_ball(V[i], x, d2)) return 1;",
+     "for (int i = 0; i < 3; i++) if (in_ball(V[i], x, 0.25 * d2)) return 1;"),
 ]
 
 
@@ -124,7 +129,8 @@ def _region_failures():
               P.test_ngon_clip_matches_independent_intersection, P.test_support_nesting,
               P.test_one_edge_cut_twice, P.test_tangent_edge_gives_zero_cap,
               lambda: P.test_ngon_area_and_moments(0.2), lambda: P.test_exactcaps_and_approxcaps_area(0.2),
-              lambda: P.test_ball_covering_mesh_closed_form("exactcaps", "dunavant7", "dunavant7")]
+              lambda: P.test_ball_covering_mesh_closed_form("exactcaps", "dunavant7", "dunavant7"),
+              P.test_overlap_ball_is_the_distance_test]
     failed = []
     for k, f in enumerate(checks):
         try:

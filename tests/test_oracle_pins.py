@@ -726,3 +726,62 @@ def test_exactcaps_printed_weight_within_the_fixed_point_bounds():
         for t in m.tri:
             V = np.stack([m.vx[t], m.vy[t]], axis=1)
             assert O.inner(V, x, cfg)[0] <= c * abs(_area(V)) * (1 + 1e-12)
+
+
+def _dist_point_segment(p, q, x):
+    t = np.clip(np.dot(x - p, q - p) / np.dot(q - p, q - p), 0.0, 1.0)
+    return float(np.linalg.norm(x - (p + t * (q - p))))
+
+
+def _dist_point_triangle(T, x):
+    """Euclidean distance from x to the closed triangle T (counter-clockwise; numpy)."""
+    inside = all(((T[(i + 1) % 3] - T[i])[0] * (x - T[i])[1] - (T[(i + 1) % 3] - T[i])[1] * (x - T[i])[0]) >= 0
+                 for i in range(3))
+    if inside:
+        return 0.0
+    return min(_dist_point_segment(T[i], T[(i + 1) % 3], x) for i in range(3))
+
+
+def test_overlap_ball_is_the_distance_test():
+    # Eq. (overlap): T_b counts whole iff it meets B_delta(x), i.e. dist(x, T_b) <= delta, with
+    # the edge-crossing branch (every vertex outside, an edge through the disc) and the
+    # enclosing branch (x inside T_b, every vertex outside) drawn on purpose.  exactcaps has the
+    # same support (Sec. 6.2) unless the disc lies inside T_b: its walk then finds no crossing
+    # and the region is empty (a reading: the method assumes the circle crosses the edges)
+    rng = np.random.default_rng(17)
+    delta = 0.3
+    x = np.zeros(2)
+    n_edge = n_enclose = 0
+    for k in range(4000):
+        if k % 4 == 0:
+            # a long thin triangle whose vertices lie outside the disc
+            a = rng.uniform(0, 2 * np.pi)
+            u = np.array([np.cos(a), np.sin(a)])
+            w = np.array([-u[1], u[0]])
+            off = rng.uniform(-0.45, 0.45)
+            T = np.stack([off * w - 0.8 * u, off * w + 0.8 * u, (off + rng.choice([-1, 1]) * 0.05) * w])
+        elif k % 4 == 1:
+            # a large triangle around x
+            T = rng.uniform(-1.5, 1.5, (3, 2))
+        else:
+            T = rng.uniform(-0.55, 0.55, 2) + rng.uniform(-0.2, 0.2, (3, 2))
+        if _area(T) < 0:
+            T = T[::-1]
+        if abs(_area(T)) < 1e-6:
+            continue
+        d = _dist_point_triangle(T, x)
+        if abs(d - delta) < 1e-9:
+            continue
+        got = O.region(T, x, dict(delta=delta, ball="overlap"))[0] != 0
+        assert got == (d <= delta), (T, d)
+        edge_d = min(_dist_point_segment(T[i], T[(i + 1) % 3], x) for i in range(3))
+        enclosed = d == 0.0 and edge_d > delta + 1e-9
+        ex = O.region(T, x, dict(delta=delta, ball="exactcaps"))[0] != 0
+        assert ex == (got and not enclosed), (T, enclosed)
+        vin = np.linalg.norm(T, axis=1) <= delta
+        if got and not vin.any():
+            if d == 0.0:
+                n_enclose += 1
+            else:
+                n_edge += 1
+    assert n_edge > 100 and n_enclose > 50, (n_edge, n_enclose)
